@@ -1,0 +1,397 @@
+"""Benchmark: butterfly Legendre stage of the SHT at l = 1024 on one GB300.
+
+One step = one synthesis (beta -> G at the 2l Gauss-Legendre nodes, all
+orders m) plus one analysis (G -> beta, the transposed butterfly) of one
+synthetic field, through the C ABI, with the float64 butterfly (eps_id =
+1e-12).  value = Legendre-stage transforms per second (a synthesis and an
+analysis each count as one transform), whole job over all ranks.
+
+Prints ONE JSON line (rank 0).  Launch: python bench.py [--gpus N --steps K
+--warmup W]; for N > 1 under torch.distributed.run (one process per GPU,
+each rank transforms its own field: weak scaling, no collective on the data
+path).  --impl reference times the float64 oracle on the host cores instead.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 float64 (vector and tensor), nominal
+METRIC = "SHT/s at l=1024, butterfly vs direct FP64 on GPU (Legendre-stage transforms per second)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--l", type=int, default=1024)
+    ap.add_argument("--leaf-cols", type=int, default=64)
+    ap.add_argument("--eps", type=float, default=1e-12)
+    ap.add_argument("--no-extras", action="store_true", help="skip the split32/fp32/direct legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--cpu-stride", type=int, default=8, help="oracle samples every stride-th order")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_leg(l, stride, seed, outputs_path=None, err_stride=64):
+    """Runs the float64 oracle (one thread, in a subprocess) on the orders
+    m = 0, stride, 2*stride, ... and returns its timing.  If GPU outputs are
+    given (npz with <path>_G and <path>_beta arrays), also returns, on the
+    orders m = 0, err_stride, ..., the relative l2 error of each path's
+    synthesis against the oracle synthesis of the same beta, and of its
+    analysis against the oracle analysis of that path's own G."""
+    code = r"""
+import json, sys, time, os
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+from paper_0910_5435_gb300 import inputs
+l, stride, seed, err_stride = int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[6])
+ms = list(range(0, 2 * l, stride))
+beta = inputs.random_beta(l, seed=seed, decay=True)
+t0 = time.perf_counter()
+Go = oracle.legendre_synthesis(beta, l, orders=ms)
+t1 = time.perf_counter()
+bo = oracle.legendre_analysis(Go, l, orders=ms)
+t2 = time.perf_counter()
+out = {"orders": len(ms), "t_synth": t1 - t0, "t_analysis": t2 - t1}
+path = sys.argv[5]
+if path != "-":
+    d = np.load(path)
+    me = list(range(0, 2 * l, err_stride))
+    off = oracle.triangle_offsets(l)
+    sel = np.concatenate([np.arange(off[m], off[m + 1]) for m in me])
+    for name in sorted({k.rsplit("_", 1)[0] for k in d.files}):
+        G, b = d[name + "_G"], d[name + "_beta"]
+        out["rel_synth_" + name] = float(np.linalg.norm(G[me] - Go[me]) / np.linalg.norm(Go[me]))
+        ba = oracle.legendre_analysis(G, l, orders=me)
+        out["rel_analysis_" + name] = float(np.linalg.norm(b[sel] - ba[sel]) / np.linalg.norm(ba[sel]))
+print(json.dumps(out))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code, ROOT, str(l), str(stride), str(seed),
+                        outputs_path or "-", str(err_stride)],
+                       stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle leg failed: " + r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    # stratified estimate of the full transform: every stride-th order stands for stride orders
+    res["t_full_est"] = (res["t_synth"] + res["t_analysis"]) * stride
+    return res
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    res = None
+    for _ in range(args.steps):
+        res = cpu_oracle_leg(args.l, args.cpu_stride * 8, 3)
+    wall = time.perf_counter() - t0
+    value = 2.0 / res["t_full_est"]
+    line = {
+        "impl": "reference", "metric": METRIC,
+        "value": value, "unit": "transforms/s", "higher_is_better": True, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"Legendre stage synthesis+analysis, one field, l={args.l}, beta ~ N(0,1)/(k+1)"},
+        "cpu_baseline": {"value": value, "unit": "transforms/s", "cores": 1, "kind": "oracle",
+                         "sample": f"orders m = 0, {args.cpu_stride * 8}, ... of l={args.l}, scaled by the stride"},
+        "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0910_5435_gb300 import inputs, sht
+
+    l = args.l
+    t0 = time.perf_counter()
+    plan = sht.Plan(l, args.eps, leaf_cols=args.leaf_cols)
+    t_plan = time.perf_counter() - t0
+    st = plan.stats()
+
+    beta_h = inputs.random_beta(l, seed=3 + rank, decay=True)
+    beta = torch.from_numpy(beta_h).to(dev)
+    G = torch.empty((2 * l, 2 * l), dtype=torch.complex128, device=dev)
+    back = torch.empty_like(beta)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def time_path(prec, steps, warmup, b, g, bk, synth_fn=None, ana_fn=None):
+        synth_fn = synth_fn or (lambda: sht.sht_legendre_synthesize(plan, prec, b, g, stream))
+        ana_fn = ana_fn or (lambda: sht.sht_legendre_analyze(plan, prec, g, bk, stream))
+        for _ in range(warmup):
+            synth_fn()
+            ana_fn()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        start.record(stream)
+        for i in range(steps):
+            ev[i][0].record(stream)
+            synth_fn()
+            ev[i][1].record(stream)
+            ana_fn()
+            ev[i][2].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        total = start.elapsed_time(end)
+        ts = [e[0].elapsed_time(e[1]) for e in ev]
+        ta = [e[1].elapsed_time(e[2]) for e in ev]
+        return total, float(np.mean(ts)), float(np.mean(ta))
+
+    # ---- headline: float64 butterfly
+    clocks = ClockSampler(local)
+    for _ in range(args.warmup):
+        sht.sht_legendre_synthesize(plan, sht.SHT_FP64, beta, G, stream)
+        sht.sht_legendre_analyze(plan, sht.SHT_FP64, G, back, stream)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    total_ms, ms_syn, ms_ana = time_path(sht.SHT_FP64, args.steps, 0, beta, G, back)
+    clk = clocks.stop()
+    status = sht.sht_last_device_status(plan, stream)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * 2.0 * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+    eps_inv64 = float(torch.linalg.vector_norm(back - beta) / torch.linalg.vector_norm(beta))
+    G64 = G.cpu().numpy()
+    back64 = back.cpu().numpy()
+
+    # ---- end to end through the C ABI with pinned host buffers
+    beta_pin = torch.from_numpy(beta_h).pin_memory()
+    out_pin = torch.empty_like(beta_pin).pin_memory()
+
+    def e2e_step():
+        beta.copy_(beta_pin, non_blocking=True)
+        sht.sht_legendre_synthesize(plan, sht.SHT_FP64, beta, G, stream)
+        sht.sht_legendre_analyze(plan, sht.SHT_FP64, G, back, stream)
+        out_pin.copy_(back, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * 2.0 * args.steps / (e2e_ms / 1e3)
+    nbytes = beta.numel() * beta.element_size()
+
+    # ---- roofline of the dominant kernel (the float64 sweep)
+    flops = 4.0 * st["factor_values"]  # 2 real right-hand sides x (mul + add) per stored value
+    achieved = flops / (0.5 * (ms_syn + ms_ana) / 1e3) / 1e12
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    stream_gbs = st["stream_bytes_fp64"] / (0.5 * (ms_syn + ms_ana) / 1e3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": "bfly_sweep_kernel<TF64>",
+                "peak_source": "nominal GB300 float64 rate (no measured float64 peak on this pool)",
+                "hbm_view": {"stream_bytes_per_launch": st["stream_bytes_fp64"], "achieved_gbs": stream_gbs,
+                             "peak_gbs": hbm or HBM_FALLBACK_GBS,
+                             "frac": stream_gbs / (hbm or HBM_FALLBACK_GBS),
+                             "peak_source": "measured" if hbm else "fallback"}}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        for name, prec, cdt in (("split32", sht.SHT_SPLIT32, torch.complex128), ("fp32", sht.SHT_FP32, torch.complex64)):
+            t0 = time.perf_counter()
+            plan.prepare(prec)
+            tprep = time.perf_counter() - t0
+            b = beta.to(cdt)
+            g = torch.empty((2 * l, 2 * l), dtype=cdt, device=dev)
+            bk = torch.empty_like(b)
+            tot, s_ms, a_ms = time_path(prec, args.steps, 2, b, g, bk)
+            st2 = plan.stats()
+            sb = st2["stream_bytes_fp32" if name == "fp32" else "stream_bytes_split32"]
+            extras[name] = {
+                "transforms_per_s": 2.0 * args.steps / (tot / 1e3), "ms_synthesis": s_ms, "ms_analysis": a_ms,
+                "stream_bytes": sb, "achieved_gbs": sb / (0.5 * (s_ms + a_ms) / 1e3) / 1e9,
+                "hbm_frac": sb / (0.5 * (s_ms + a_ms) / 1e3) / 1e9 / (hbm or HBM_FALLBACK_GBS),
+                "eps_inv": float(torch.linalg.vector_norm((bk - b).to(torch.complex128))
+                                 / torch.linalg.vector_norm(b.to(torch.complex128))),
+                "prepare_s": tprep,
+            }
+            extras[name + "_G"] = g.to(torch.complex128).cpu().numpy()
+            extras[name + "_beta"] = bk.to(torch.complex128).cpu().numpy()
+        # direct float64 baseline (dense operator in HBM)
+        t0 = time.perf_counter()
+        sht.sht_direct_prepare(plan)
+        tprep = time.perf_counter() - t0
+        g = torch.empty_like(G)
+        bk = torch.empty_like(beta)
+        tot, s_ms, a_ms = time_path(
+            None, max(2, args.steps // 2), 1, beta, g, bk,
+            synth_fn=lambda: sht.sht_direct_synthesize(plan, beta, g, stream),
+            ana_fn=lambda: sht.sht_direct_analyze(plan, g, bk, stream))
+        extras["direct_fp64"] = {
+            "transforms_per_s": 2.0 * max(2, args.steps // 2) / (tot / 1e3), "ms_synthesis": s_ms,
+            "ms_analysis": a_ms, "prepare_s": tprep,
+            "eps_inv": float(torch.linalg.vector_norm(bk - beta) / torch.linalg.vector_norm(beta)),
+        }
+        extras["direct_G"] = g.cpu().numpy()
+        extras["direct_beta"] = bk.cpu().numpy()
+
+    cpu = None
+    rel = {}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        with tempfile.TemporaryDirectory() as td:
+            op = os.path.join(td, "outputs.npz")
+            arrays = {"fp64_G": G64, "fp64_beta": back64}
+            for k in ("split32", "fp32", "direct"):
+                if k + "_G" in extras:
+                    arrays[k + "_G"] = extras[k + "_G"]
+                    arrays[k + "_beta"] = extras[k + "_beta"]
+            np.savez(op, **arrays)
+            res = cpu_oracle_leg(l, args.cpu_stride, 3, op)
+        cpu = {"value": 2.0 / res["t_full_est"], "unit": "transforms/s", "cores": 1, "kind": "oracle",
+               "sample": f"{res['orders']} of {2 * l} orders (m = 0, {args.cpu_stride}, ...), synthesis + analysis, "
+                         f"scaled by the stride; {res['t_synth'] + res['t_analysis']:.1f} s of CPU"}
+        rel = {k: v for k, v in res.items() if k.startswith("rel_")}
+    for k in list(extras):
+        if k.endswith("_G") or k.endswith("_beta"):
+            extras.pop(k)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value, "unit": "transforms/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Legendre stage, one field per GPU: synthesis + analysis at l={l} "
+                                   f"(2l={2 * l} GL nodes, orders m=0..{2 * l - 1}), FP64 butterfly eps_id={args.eps}, "
+                                   f"leaf_cols={args.leaf_cols}, beta ~ N(0,1)/(k+1)",
+                       "l": l, "eps_id": args.eps, "parallelism": f"replicas x{world}",
+                       "l2": f"no flush: the factor stream ({st['stream_bytes_fp64'] / 1e9:.2f} GB per launch) "
+                             "is far larger than L2"},
+            "ms_synthesis": ms_syn, "ms_analysis": ms_ana,
+            "eps_inv": eps_inv64, "rel_l2_vs_oracle_sampled": rel,
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": 2 * args.steps, "clocks": clk, "device_status": status,
+            "plan": {"t_plan_s": t_plan, "k_max": st["k_max"], "k_avg": st["k_avg"], "k_sigma": st["k_sigma"],
+                     "factor_values": st["factor_values"], "dense_values": st["dense_values"],
+                     "rows_kept_frac": st["rows_kept"] / max(1, st["rows_total"]),
+                     "levels": st["max_levels"], "t_comp": st["t_comp"]},
+            "paths": extras,
+        }
+        if "direct_fp64" in extras:
+            line["butterfly_vs_direct_fp64"] = value / extras["direct_fp64"]["transforms_per_s"]
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

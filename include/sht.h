@@ -1,0 +1,220 @@
+/*
+ * sht.h -- C ABI of the GB300 butterfly spherical harmonic transform.
+ *
+ * Method: M. Tygert, "Fast algorithms for spherical harmonic expansions, III".
+ * The library applies the associated-Legendre stage of the spherical
+ * harmonic transform (the sums over k of Section 2, eq. alternate_expansion)
+ * through a precomputed multilevel butterfly of interpolative decompositions
+ * (Section 2.1 Lemma interpolation_lemma / Remark QR_algorithm; Section 2.2
+ * eqs. 1-6, top, bottom; Section 3 depth-first precomputation), per order m,
+ * with the even/odd parity split of Section 2.3 taken from the symmetric
+ * Gauss-Legendre nodes (Section 2, eq. thetas).  The transposed application
+ * (Section 2.2, remark after Figure multi) gives the analysis direction.
+ *
+ * Conventions shared by every entry point:
+ *   - l is the bandlimit parameter: degrees k = 0..2l-1, orders m = 0..2l-1
+ *     (Section 2, eq. expansion); the grid has 2l Gauss-Legendre nodes
+ *     x_0 < ... < x_{2l-1} (zeros of P-bar^0_{2l}) and 4l-1 equispaced
+ *     phi_j = 2 pi (j + 1/2) / (4l - 1) (eq. phis).
+ *   - P-bar^m_k is the normalized associated Legendre function of Section 2.3,
+ *     eq. association (orthonormal on (-1,1), no Condon-Shortley sign).
+ *   - beta (coefficients): a REAL field is assumed, so only m >= 0 is stored;
+ *     beta^{-m}_k = conj(beta^m_k) and beta^0_k is real.  Storage is an
+ *     m-major triangle of complex numbers (interleaved re, im):
+ *     beta^m_k at index offset(m) + (k - m), offset(m) = sum_{m'<m} (2l - m'),
+ *     k = m..2l-1; 2l(2l+1)/2 entries.
+ *   - G (Legendre-stage values): G^m(x_i) = sum_{k=m}^{2l-1} beta^m_k
+ *     P-bar^m_k(x_i), a [2l][2l] complex array, row m, column i (nodes
+ *     ascending).
+ *   - values (grid): real f(theta_i, phi_j), a [2l][4l-1] array, row i
+ *     (cos(theta_i) = x_i ascending), column j.
+ *   - Precision selects the factor format and arithmetic:
+ *       SHT_FP64    float64 factors, float64 arithmetic; complex128 beta/G,
+ *                   float64 values.
+ *       SHT_SPLIT32 factors stored as hi/lo float32 pairs (hi = fl32(a),
+ *                   lo = fl32(a - hi)) applied with compensated (double-float)
+ *                   float32 arithmetic; same I/O types as SHT_FP64.
+ *       SHT_FP32    float32 factors and arithmetic; complex64 beta/G,
+ *                   float32 values.
+ *   - All device pointers are caller-owned, must be 16-byte aligned
+ *     (8-byte for SHT_FP32), and are only read/written asynchronously on the
+ *     given stream.  Entry points never synchronize the stream unless stated.
+ *   - Errors are returned as sht_status; nothing aborts or throws.  Argument
+ *     checks happen on the host before any launch; a failed check launches
+ *     nothing and leaves outputs untouched.
+ */
+#ifndef SHT_H
+#define SHT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sht_plan_s* sht_plan_t;
+/* Same object as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* sht_stream_t;
+
+typedef enum {
+  SHT_FP64 = 0,
+  SHT_FP32 = 1,
+  SHT_SPLIT32 = 2
+} sht_precision;
+
+typedef enum {
+  SHT_OK = 0,
+  SHT_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, misaligned pointer */
+  SHT_ERR_OOM = 2,           /* host or device allocation failed */
+  SHT_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  SHT_ERR_PLAN_CORRUPT = 4,  /* plan file truncated, wrong version, bad checksum */
+  SHT_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (see sht_last_device_status) */
+  SHT_ERR_UNSUPPORTED = 6,   /* e.g. a compute call on a host-only plan */
+  SHT_ERR_NO_DEVICE = 7      /* no CUDA device is visible */
+} sht_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* sht_status_string(sht_status s);
+
+/* ------------------------------------------------------------------ plans */
+
+typedef struct {
+  /* Leaf width C of the first butterfly level (Section 2.2: blocks of
+   * n x floor(C) columns; Section 5 uses C = 60).  Default 64. */
+  int leaf_cols;
+  /* Rows i of unit (m, p) whose weighted row norm ||A_{i,:}||_2 is below
+   * trim_eps / sqrt(l) are dropped (output 0 there); the dropped rows'
+   * total Frobenius norm is <= trim_eps.  < 0 selects eps_id; 0 disables. */
+  double trim_eps;
+  /* A butterfly level is only added while every row band keeps at least
+   * this many rows.  Default leaf_cols / 2. */
+  int min_band_rows;
+  /* 1: build the factorization on the host only (no CUDA calls at all);
+   * compute entry points then return SHT_ERR_UNSUPPORTED.  Used by
+   * host-side tests and tools. */
+  int host_only;
+  /* Host threads for the precomputation; 0 = all hardware threads. */
+  int num_threads;
+  /* Bytes per streamed factor page (TMA bulk-copy unit, multiple of 1024,
+   * 4096..49152); 0 = default (16384). */
+  int page_bytes;
+  /* eps used for the IDs of the SHT_FP32 factors; <= 0 selects
+   * max(eps_id, 1e-7).  (FP32 cannot use ranks below its own precision.) */
+  double eps_fp32;
+} sht_plan_opts;
+
+typedef struct {
+  int l;
+  double eps_id;
+  int leaf_cols;
+  int n_units;           /* orders m = 0..2l-1 */
+  int n_blocks;          /* IDs in all butterflies (both parities, all m) */
+  int k_max;             /* max ID rank (Section 5 tables: k_max) */
+  double k_avg;          /* mean ID rank (k_avg) */
+  double k_sigma;        /* std. deviation of ID ranks (k_sigma) */
+  double max_abs_T;      /* largest |entry| of any interpolation matrix (Remark QR_algorithm bound: 2) */
+  int max_levels;        /* deepest butterfly (number of merge levels) */
+  int n_direct_units;    /* (m, p) blocks stored dense because compression did not pay */
+  long long rows_total;  /* sum over (m, p) of l */
+  long long rows_kept;   /* sum over (m, p) of kept rows after trimming */
+  long long dense_values;    /* sum over (m, p) of l * n_{m,p}: the dense operator */
+  long long factor_values;   /* stored factor values (one direction, eps_id factors) */
+  long long index_bytes;     /* skeleton/redundant index bytes (one direction) */
+  long long stream_bytes_fp64;   /* device bytes streamed per transform, per direction */
+  long long stream_bytes_split32;
+  long long stream_bytes_fp32;
+  long long factor_values_fp32;  /* stored factor values of the eps_fp32 factorization */
+  double t_quad;         /* seconds: Gauss-Legendre nodes and weights */
+  double t_comp;         /* seconds: columns + IDs + butterflies (host, all threads) */
+  double t_upload;       /* seconds: device upload of the prepared precisions */
+  long long m_max_words; /* peak float64 words held by one unit's depth-first build */
+  int smem_bytes;        /* dynamic shared memory of the sweep kernels */
+} sht_plan_stats;
+
+/* Fills *opts with the defaults listed above. */
+sht_status sht_plan_opts_default(sht_plan_opts* opts);
+
+/* Builds the plan for bandlimit l (1 <= l <= 1024) and ID precision eps_id
+ * (0 < eps_id < 1): Gauss-Legendre nodes, the parity-split weighted Legendre
+ * blocks A^{m,p}_{ij} = sqrt(2 w_{l+i}) P-bar^m_{m+p+2j}(x_{l+i}) (the GL form
+ * of Section 4, eqs. transform/transform2) generated column by column with
+ * the x^2 recurrence of Section 2.3 (eqs. c_rec, d_rec, recurrence0,
+ * recurrence) with exponent tracking, compressed by the depth-first
+ * butterfly of Section 3.  The FP64 factor streams are built and (unless
+ * host_only) uploaded; other precisions are built at first use or by
+ * sht_prepare.  *out receives the plan, or NULL on error.  Allocates host
+ * and device memory owned by the plan. */
+sht_status sht_plan_create(int l, double eps_id, sht_plan_t* out);
+sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, sht_plan_t* out);
+
+/* Frees the plan and all memory it owns.  NULL is a no-op.  The caller must
+ * ensure no work using the plan is still in flight. */
+sht_status sht_plan_destroy(sht_plan_t plan);
+
+/* Copies the plan statistics into *out. */
+sht_status sht_plan_get_stats(sht_plan_t plan, sht_plan_stats* out);
+
+/* Builds (host) and uploads (device) the factor streams of one precision.
+ * Synchronous.  Idempotent. */
+sht_status sht_prepare(sht_plan_t plan, sht_precision prec);
+
+/* The plan's Gauss-Legendre nodes x[2l] (ascending) and weights w[2l] (host
+ * arrays owned by the caller). */
+sht_status sht_plan_nodes(sht_plan_t plan, double* x, double* w);
+
+/* Host copy of the factor stream of one precision and direction (0 =
+ * synthesis, 1 = analysis), for inspection and host-side verification.
+ * The layout is documented in paper_0910_5435_gb300/csrc/sht_stream.h.
+ * With dst == NULL only *bytes is set. */
+sht_status sht_plan_stream(sht_plan_t plan, sht_precision prec, int direction,
+                           void* dst, size_t* bytes);
+
+/* ----------------------------------------------- Legendre stage (hot path) */
+
+/* Synthesis: G^m(x_i) = sum_{k=m}^{2l-1} beta^m_k P-bar^m_k(x_i) for all m and
+ * all 2l nodes (Section 2, eq. alternate_expansion, the sums over k), through
+ * the butterfly (Section 2.2) of each parity block, followed by the parity
+ * unfold G(x_{l+i}) = E_i + O_i, G(x_{l-1-i}) = E_i - O_i (Section 2.3).
+ * beta: device, triangle layout (complex128, or complex64 for SHT_FP32).
+ * G:    device, [2l][2l] complex.  Asynchronous on stream. */
+sht_status sht_legendre_synthesize(sht_plan_t plan, sht_precision prec,
+                                   const void* beta, void* G, sht_stream_t stream);
+
+/* Analysis: beta^m_k = sum_{i=0}^{2l-1} w_i P-bar^m_k(x_i) G^m(x_i) (the
+ * Gauss-Legendre quadrature that inverts synthesis on band-limited data),
+ * applied as the transposed butterfly (Section 2.2, remark after Figure
+ * multi; Section 4: the per-order maps are unitary, so the inverse is the
+ * transpose).  G: device [2l][2l] complex; beta: device triangle. */
+sht_status sht_legendre_analyze(sht_plan_t plan, sht_precision prec,
+                                const void* G, void* beta, sht_stream_t stream);
+
+/* Adjoint of synthesis (no quadrature weights): beta-hat^m_k =
+ * sum_i P-bar^m_k(x_i) G-hat^m(x_i).  Same layouts as analysis.  Used as the
+ * backward pass of synthesis. */
+sht_status sht_legendre_synthesize_adjoint(sht_plan_t plan, sht_precision prec,
+                                           const void* G, void* beta, sht_stream_t stream);
+
+/* Device status word of the plan's last launches: SHT_OK, or SHT_ERR_TIMEOUT
+ * if a bounded wait inside a kernel gave up (the kernel then stopped early
+ * and its outputs are undefined).  Synchronizes the stream, then clears the
+ * word. */
+sht_status sht_last_device_status(sht_plan_t plan, sht_stream_t stream);
+
+/* ------------------------------------- direct float64 baseline (K3-style) */
+
+/* Stores the dense operator P-bar^m_{m+p+2j}(x_{l+i}) (float64, kept rows
+ * only) on the device: sum over (m,p) of rows * n_{m,p} * 8 bytes
+ * (about 17.2 GB at l = 1024).  Synchronous. */
+sht_status sht_direct_prepare(sht_plan_t plan);
+/* Same results as the SHT_FP64 Legendre entry points, computed as dense
+ * float64 products with the stored operator (the O(l^3) direct method of
+ * Section 2).  Asynchronous on stream. */
+sht_status sht_direct_synthesize(sht_plan_t plan, const void* beta, void* G, sht_stream_t stream);
+sht_status sht_direct_analyze(sht_plan_t plan, const void* G, void* beta, sht_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHT_H */

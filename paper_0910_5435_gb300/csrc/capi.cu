@@ -1,0 +1,562 @@
+// capi.cu -- the C ABI of include/sht.h: plan lifecycle, device upload and
+// launches.  All arguments are validated on the host before any launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <stdexcept>
+#include <thread>
+#include <vector>
+
+#include "../../include/sht.h"
+#include "kernels.h"
+#include "plan_host.h"
+
+using sht::PlanHost;
+using sht::UnitFact;
+
+namespace {
+
+constexpr int kNumPrec = 3;
+constexpr int kMaxStages = 16;
+
+// Launch kinds that own a work-queue counter: synthesis, analysis, adjoint.
+enum { KIND_SYN = 0, KIND_ANA = 1, KIND_ADJ = 2, KIND_COUNT = 3 };
+
+struct DevStream {
+  uint8_t* pages = nullptr;
+  sht::UnitEntry* units = nullptr;
+  size_t bytes = 0;
+  int n_units = 0;
+  unsigned long long quit_page = 0;
+  int buf_ab = 0;
+};
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int prec_index(sht_precision p) {
+  switch (p) {
+    case SHT_FP64: return sht::PREC_FP64;
+    case SHT_FP32: return sht::PREC_FP32;
+    case SHT_SPLIT32: return sht::PREC_SPLIT32;
+    default: return -1;
+  }
+}
+
+}  // namespace
+
+struct sht_plan_s {
+  PlanHost H;
+  sht_plan_opts opts{};
+  bool host_only = false;
+  int device = -1;
+  int num_sms = 0;
+  int nstages = 4;
+  DevStream dev[kNumPrec][2];
+  bool dev_ready[kNumPrec] = {false, false, false};
+  size_t smem[kNumPrec] = {0, 0, 0};
+  double* d_inv_w = nullptr;   // 1 / w_{l+i}: the adjoint's fold prescale
+  double* d_w_pos = nullptr;   // w_{l+i}
+  unsigned* d_scratch = nullptr;  // [kNumPrec * KIND_COUNT] queue counters, then the status word
+  // direct baseline
+  double* d_dense = nullptr;
+  long long* d_dense_off = nullptr;
+  int* d_dense_rows = nullptr;
+  int* d_dense_ncol = nullptr;
+  size_t dense_bytes = 0;
+  sht_plan_stats stats{};
+  std::mutex mu;
+};
+
+namespace {
+
+sht_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return SHT_OK;
+  if (e == cudaErrorMemoryAllocation) return SHT_ERR_OOM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return SHT_ERR_NO_DEVICE;
+  return SHT_ERR_CUDA;
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e__ = (call);                     \
+    if (e__ != cudaSuccess) return cuda_status(e__); \
+  } while (0)
+
+void free_dev(sht_plan_t P) {
+  if (P->host_only) return;
+  for (int q = 0; q < kNumPrec; ++q)
+    for (int d = 0; d < 2; ++d) {
+      cudaFree(P->dev[q][d].pages);
+      cudaFree(P->dev[q][d].units);
+      P->dev[q][d] = DevStream();
+    }
+  cudaFree(P->d_inv_w);
+  cudaFree(P->d_w_pos);
+  cudaFree(P->d_scratch);
+  cudaFree(P->d_dense);
+  cudaFree(P->d_dense_off);
+  cudaFree(P->d_dense_rows);
+  cudaFree(P->d_dense_ncol);
+  P->d_inv_w = P->d_w_pos = nullptr;
+  P->d_scratch = nullptr;
+  P->d_dense = nullptr;
+  P->d_dense_off = nullptr;
+  P->d_dense_rows = P->d_dense_ncol = nullptr;
+}
+
+void fill_stats(sht_plan_t P) {
+  const PlanHost& H = P->H;
+  sht_plan_stats& s = P->stats;
+  s.l = H.l;
+  s.eps_id = H.eps_id;
+  s.leaf_cols = H.leaf_cols;
+  s.n_units = 2 * H.l;
+  long long nb = 0, sumk = 0, dense = 0, fv = 0, ib = 0, rows = 0, kept = 0, peak = 0;
+  double sumk2 = 0, maxT = 0;
+  int kmax = 0, lev = 0, ndir = 0;
+  for (const UnitFact& U : H.fact64) {
+    dense += (long long)H.l * U.n;
+    rows += (U.n > 0) ? H.l : 0;
+    kept += (U.n > 0) ? U.rows : 0;
+    fv += U.values;
+    ib += 2 * U.idx;
+    peak = std::max(peak, U.peak_words);
+    if (U.n > 0 && U.direct) ++ndir;
+    lev = std::max(lev, U.levels);
+    for (const auto& b : U.blocks) {
+      ++nb;
+      sumk += b.k;
+      sumk2 += (double)b.k * b.k;
+      kmax = std::max(kmax, b.k);
+      for (double t : b.T) maxT = std::max(maxT, std::fabs(t));
+    }
+  }
+  s.n_blocks = (int)nb;
+  s.k_max = kmax;
+  s.k_avg = nb ? (double)sumk / nb : 0.0;
+  s.k_sigma = nb ? std::sqrt(std::max(0.0, sumk2 / nb - s.k_avg * s.k_avg)) : 0.0;
+  s.max_abs_T = maxT;
+  s.max_levels = lev;
+  s.n_direct_units = ndir;
+  s.rows_total = rows;
+  s.rows_kept = kept;
+  s.dense_values = dense;
+  s.factor_values = fv;
+  s.index_bytes = ib;
+  s.m_max_words = peak;
+  long long fv32 = 0;
+  for (const UnitFact& U : H.fact32) fv32 += U.values;
+  s.factor_values_fp32 = fv32;
+  s.stream_bytes_fp64 = (long long)H.streams[0][0].bytes.size();
+  s.stream_bytes_fp32 = (long long)H.streams[1][0].bytes.size();
+  s.stream_bytes_split32 = (long long)H.streams[2][0].bytes.size();
+  s.t_quad = H.t_quad;
+  s.t_comp = H.t_comp;
+  s.smem_bytes = (int)std::max({P->smem[0], P->smem[1], P->smem[2]});
+}
+
+// Host build of one precision's streams (factorization + page encoding).
+sht_status build_host(sht_plan_t P, int q) {
+  PlanHost& H = P->H;
+  if (H.built[q]) return SHT_OK;
+  try {
+    const double t0 = now_s();
+    if (q == sht::PREC_FP32) {
+      if (H.fact32.empty()) sht::build_factorizations(H, true);
+    } else if (H.fact64.empty()) {
+      sht::build_factorizations(H, false);
+    }
+    sht::emit_streams(H, q);
+    H.t_comp += now_s() - t0;
+  } catch (const std::bad_alloc&) {
+    return SHT_ERR_OOM;
+  } catch (...) {
+    return SHT_ERR_INVALID_ARG;
+  }
+  return SHT_OK;
+}
+
+sht_status upload(sht_plan_t P, int q) {
+  if (P->dev_ready[q]) return SHT_OK;
+  const double t0 = now_s();
+  CK(cudaSetDevice(P->device));
+  int buf_ab = 0;
+  for (int d = 0; d < 2; ++d) {
+    const sht::Stream& S = P->H.streams[q][d];
+    DevStream& D = P->dev[q][d];
+    D.bytes = S.bytes.size();
+    D.n_units = (int)S.units.size();
+    D.quit_page = S.bytes.size() / P->H.page_bytes - 1;
+    D.buf_ab = std::max(S.max_buf_ab, 1);
+    buf_ab = std::max(buf_ab, D.buf_ab);
+    CK(cudaMalloc(&D.pages, D.bytes));
+    CK(cudaMalloc(&D.units, sizeof(sht::UnitEntry) * std::max<size_t>(1, S.units.size())));
+    CK(cudaMemcpy(D.pages, S.bytes.data(), D.bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(D.units, S.units.data(), sizeof(sht::UnitEntry) * S.units.size(), cudaMemcpyHostToDevice));
+  }
+  size_t smem = sht::sweep_smem_bytes(q, P->H.page_bytes, P->nstages, buf_ab, P->H.l);
+  int optin = 0;
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+  // fewer stages if the vectors of a large l leave too little room
+  while (smem > (size_t)optin && P->nstages > 2) {
+    --P->nstages;
+    smem = sht::sweep_smem_bytes(q, P->H.page_bytes, P->nstages, buf_ab, P->H.l);
+  }
+  if (smem > (size_t)optin) return SHT_ERR_UNSUPPORTED;
+  P->dev[q][0].buf_ab = P->dev[q][1].buf_ab = buf_ab;
+  P->smem[q] = smem;
+  CK(sht::sweep_configure(q, smem));
+  P->dev_ready[q] = true;
+  P->H.t_quad += 0;  // (nodes are timed at creation)
+  P->stats.t_upload += now_s() - t0;
+  return SHT_OK;
+}
+
+sht_status ensure_prec(sht_plan_t P, int q) {
+  std::lock_guard<std::mutex> g(P->mu);
+  sht_status s = build_host(P, q);
+  if (s != SHT_OK) return s;
+  if (!P->host_only) {
+    s = upload(P, q);
+    if (s != SHT_OK) return s;
+  }
+  fill_stats(P);
+  return SHT_OK;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, const void* in, void* out,
+                        const double* prescale, sht_stream_t stream) {
+  if (!P || !in || !out) return SHT_ERR_INVALID_ARG;
+  const int q = prec_index(prec);
+  if (q < 0) return SHT_ERR_INVALID_ARG;
+  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  const size_t al = (q == sht::PREC_FP32) ? 8 : 16;
+  if (!aligned(in, al) || !aligned(out, al)) return SHT_ERR_INVALID_ARG;
+  sht_status s = ensure_prec(P, q);
+  if (s != SHT_OK) return s;
+  CK(cudaSetDevice(P->device));
+  const DevStream& D = P->dev[q][dir];
+  sht::SweepArgs a;
+  a.pages = D.pages;
+  a.units = D.units;
+  a.n_units = D.n_units;
+  a.page_bytes = P->H.page_bytes;
+  a.nstages = P->nstages;
+  a.l = P->H.l;
+  a.buf_ab = D.buf_ab;
+  a.quit_page = D.quit_page;
+  a.in = in;
+  a.out = out;
+  a.prescale = prescale;
+  a.counter = P->d_scratch + (q * KIND_COUNT + kind);
+  a.status = P->d_scratch + kNumPrec * KIND_COUNT;
+  const int grid = std::max(1, std::min(P->num_sms, D.n_units));
+  CK(sht::sweep_launch(q, a, grid, P->smem[q], reinterpret_cast<cudaStream_t>(stream)));
+  return SHT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sht_status_string(sht_status s) {
+  switch (s) {
+    case SHT_OK: return "SHT_OK";
+    case SHT_ERR_INVALID_ARG: return "SHT_ERR_INVALID_ARG";
+    case SHT_ERR_OOM: return "SHT_ERR_OOM";
+    case SHT_ERR_CUDA: return "SHT_ERR_CUDA";
+    case SHT_ERR_PLAN_CORRUPT: return "SHT_ERR_PLAN_CORRUPT";
+    case SHT_ERR_TIMEOUT: return "SHT_ERR_TIMEOUT";
+    case SHT_ERR_UNSUPPORTED: return "SHT_ERR_UNSUPPORTED";
+    case SHT_ERR_NO_DEVICE: return "SHT_ERR_NO_DEVICE";
+  }
+  return "SHT_ERR_UNKNOWN";
+}
+
+sht_status sht_plan_opts_default(sht_plan_opts* o) {
+  if (!o) return SHT_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->leaf_cols = 64;
+  o->trim_eps = -1.0;
+  o->min_band_rows = 32;
+  o->host_only = 0;
+  o->num_threads = 0;
+  o->page_bytes = 16384;
+  o->eps_fp32 = 0.0;
+  return SHT_OK;
+}
+
+sht_status sht_plan_create(int l, double eps_id, sht_plan_t* out) {
+  return sht_plan_create_ex(l, eps_id, nullptr, out);
+}
+
+sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, sht_plan_t* out) {
+  if (!out) return SHT_ERR_INVALID_ARG;
+  *out = nullptr;
+  sht_plan_opts o;
+  if (opts) {
+    o = *opts;
+  } else {
+    sht_plan_opts_default(&o);
+  }
+  if (o.page_bytes == 0) o.page_bytes = 16384;
+  if (o.min_band_rows <= 0) o.min_band_rows = std::max(1, o.leaf_cols / 2);
+  if (l < 1 || l > 1024 || !(eps_id > 0.0) || !(eps_id < 1.0)) return SHT_ERR_INVALID_ARG;
+  if (o.leaf_cols < 2 || o.leaf_cols > 1024) return SHT_ERR_INVALID_ARG;
+  if (o.page_bytes < 4096 || o.page_bytes > 49152 || (o.page_bytes % 1024) != 0) return SHT_ERR_INVALID_ARG;
+  if (o.num_threads < 0) return SHT_ERR_INVALID_ARG;
+
+  sht_plan_t P = new (std::nothrow) sht_plan_s();
+  if (!P) return SHT_ERR_OOM;
+  P->opts = o;
+  P->host_only = o.host_only != 0;
+  PlanHost& H = P->H;
+  H.l = l;
+  H.eps_id = eps_id;
+  H.eps_fp32 = o.eps_fp32 > 0.0 ? o.eps_fp32 : std::max(eps_id, 1e-7);
+  H.trim_eps = o.trim_eps < 0.0 ? eps_id : o.trim_eps;
+  H.leaf_cols = o.leaf_cols;
+  H.min_band_rows = o.min_band_rows;
+  H.num_threads = o.num_threads;
+  H.page_bytes = o.page_bytes;
+
+  if (!P->host_only) {
+    int dev = 0, count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) {
+      delete P;
+      return SHT_ERR_NO_DEVICE;
+    }
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      delete P;
+      return SHT_ERR_CUDA;
+    }
+    P->device = dev;
+    cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  try {
+    const double t0 = now_s();
+    sht::gl_nodes(2 * l, H.x, H.w, H.theta_pos);
+    H.t_quad = now_s() - t0;
+  } catch (...) {
+    delete P;
+    return SHT_ERR_INVALID_ARG;
+  }
+  sht_status s = build_host(P, sht::PREC_FP64);
+  if (s != SHT_OK) {
+    delete P;
+    return s;
+  }
+  if (!P->host_only) {
+    std::vector<double> invw(l), wpos(l);
+    for (int i = 0; i < l; ++i) {
+      wpos[i] = H.w[l + i];
+      invw[i] = 1.0 / H.w[l + i];
+    }
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&P->d_inv_w, sizeof(double) * l);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_w_pos, sizeof(double) * l);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_scratch, sizeof(unsigned) * (kNumPrec * KIND_COUNT + 1));
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_inv_w, invw.data(), sizeof(double) * l, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_w_pos, wpos.data(), sizeof(double) * l, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(P->d_scratch, 0, sizeof(unsigned) * (kNumPrec * KIND_COUNT + 1));
+    if (e != cudaSuccess) {
+      free_dev(P);
+      delete P;
+      return cuda_status(e);
+    }
+    s = upload(P, sht::PREC_FP64);
+    if (s != SHT_OK) {
+      free_dev(P);
+      delete P;
+      return s;
+    }
+  }
+  fill_stats(P);
+  *out = P;
+  return SHT_OK;
+}
+
+sht_status sht_plan_destroy(sht_plan_t P) {
+  if (!P) return SHT_OK;
+  if (!P->host_only && P->device >= 0) cudaSetDevice(P->device);
+  free_dev(P);
+  delete P;
+  return SHT_OK;
+}
+
+sht_status sht_plan_get_stats(sht_plan_t P, sht_plan_stats* out) {
+  if (!P || !out) return SHT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(P->mu);
+  fill_stats(P);
+  *out = P->stats;
+  return SHT_OK;
+}
+
+sht_status sht_prepare(sht_plan_t P, sht_precision prec) {
+  if (!P) return SHT_ERR_INVALID_ARG;
+  const int q = prec_index(prec);
+  if (q < 0) return SHT_ERR_INVALID_ARG;
+  return ensure_prec(P, q);
+}
+
+sht_status sht_plan_nodes(sht_plan_t P, double* x, double* w) {
+  if (!P || !x || !w) return SHT_ERR_INVALID_ARG;
+  std::memcpy(x, P->H.x.data(), sizeof(double) * P->H.x.size());
+  std::memcpy(w, P->H.w.data(), sizeof(double) * P->H.w.size());
+  return SHT_OK;
+}
+
+sht_status sht_plan_stream(sht_plan_t P, sht_precision prec, int direction, void* dst, size_t* bytes) {
+  if (!P || !bytes || direction < 0 || direction > 1) return SHT_ERR_INVALID_ARG;
+  const int q = prec_index(prec);
+  if (q < 0) return SHT_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> g(P->mu);
+    sht_status s = build_host(P, q);
+    if (s != SHT_OK) return s;
+    fill_stats(P);
+  }
+  const sht::Stream& S = P->H.streams[q][direction];
+  if (!dst) {
+    *bytes = S.bytes.size();
+    return SHT_OK;
+  }
+  if (*bytes < S.bytes.size()) return SHT_ERR_INVALID_ARG;
+  std::memcpy(dst, S.bytes.data(), S.bytes.size());
+  *bytes = S.bytes.size();
+  return SHT_OK;
+}
+
+sht_status sht_legendre_synthesize(sht_plan_t P, sht_precision prec, const void* beta, void* G,
+                                   sht_stream_t stream) {
+  return launch_sweep(P, prec, 0, KIND_SYN, beta, G, nullptr, stream);
+}
+
+sht_status sht_legendre_analyze(sht_plan_t P, sht_precision prec, const void* G, void* beta,
+                                sht_stream_t stream) {
+  return launch_sweep(P, prec, 1, KIND_ANA, G, beta, nullptr, stream);
+}
+
+sht_status sht_legendre_synthesize_adjoint(sht_plan_t P, sht_precision prec, const void* G, void* beta,
+                                           sht_stream_t stream) {
+  if (!P) return SHT_ERR_INVALID_ARG;
+  return launch_sweep(P, prec, 1, KIND_ADJ, G, beta, P->d_inv_w, stream);
+}
+
+sht_status sht_last_device_status(sht_plan_t P, sht_stream_t stream) {
+  if (!P) return SHT_ERR_INVALID_ARG;
+  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  CK(cudaSetDevice(P->device));
+  CK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  unsigned st = 0;
+  CK(cudaMemcpy(&st, P->d_scratch + kNumPrec * KIND_COUNT, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    // a kernel stopped early: its queue counter may not have been reset
+    CK(cudaMemset(P->d_scratch, 0, sizeof(unsigned) * (kNumPrec * KIND_COUNT + 1)));
+    return (sht_status)st;
+  }
+  return SHT_OK;
+}
+
+sht_status sht_direct_prepare(sht_plan_t P) {
+  if (!P) return SHT_ERR_INVALID_ARG;
+  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> g(P->mu);
+  if (P->d_dense) return SHT_OK;
+  const PlanHost& H = P->H;
+  const int l = H.l, NU = 4 * l;
+  std::vector<long long> off(NU);
+  std::vector<int> rows(NU), ncol(NU);
+  long long tot = 0;
+  for (int u = 0; u < NU; ++u) {
+    off[u] = tot;
+    rows[u] = H.fact64[u].rows;
+    ncol[u] = H.fact64[u].n;
+    tot += (long long)rows[u] * ncol[u];
+  }
+  CK(cudaSetDevice(P->device));
+  CK(cudaMalloc(&P->d_dense, sizeof(double) * std::max<long long>(1, tot)));
+  CK(cudaMalloc(&P->d_dense_off, sizeof(long long) * NU));
+  CK(cudaMalloc(&P->d_dense_rows, sizeof(int) * NU));
+  CK(cudaMalloc(&P->d_dense_ncol, sizeof(int) * NU));
+  CK(cudaMemcpy(P->d_dense_off, off.data(), sizeof(long long) * NU, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P->d_dense_rows, rows.data(), sizeof(int) * NU, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(P->d_dense_ncol, ncol.data(), sizeof(int) * NU, cudaMemcpyHostToDevice));
+  P->dense_bytes = sizeof(double) * (size_t)tot;
+  // generate P-bar blocks with the x^2 recurrence (unweighted), in parallel
+  std::atomic<int> next(0);
+  std::atomic<int> err(0);
+  int nt = H.num_threads > 0 ? H.num_threads : (int)std::thread::hardware_concurrency();
+  nt = std::max(1, std::min(nt, 64));
+  auto worker = [&]() {
+    cudaSetDevice(P->device);
+    std::vector<double> blk;
+    for (;;) {
+      const int u = next.fetch_add(1);
+      if (u >= NU || err.load()) break;
+      const int r = rows[u], n = ncol[u];
+      if (r == 0 || n == 0) continue;
+      blk.resize((size_t)r * n);
+      sht::ColumnStream cs(H, u / 2, u % 2, r);
+      for (int j = 0; j < n; ++j) cs.next(blk.data() + (size_t)j * r);
+      for (int i = 0; i < r; ++i) {
+        const double s = 1.0 / std::sqrt(2.0 * H.w[l + i]);
+        for (int j = 0; j < n; ++j) blk[(size_t)j * r + i] *= s;
+      }
+      if (cudaMemcpy(P->d_dense + off[u], blk.data(), sizeof(double) * blk.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+        err.store(1);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(worker);
+  worker();
+  for (auto& t : th) t.join();
+  if (err.load()) return SHT_ERR_CUDA;
+  return SHT_OK;
+}
+
+static sht::DirectArgs direct_args(sht_plan_t P, const void* in, void* out) {
+  sht::DirectArgs a;
+  a.dense = P->d_dense;
+  a.off = P->d_dense_off;
+  a.rows = P->d_dense_rows;
+  a.ncol = P->d_dense_ncol;
+  a.w_pos = P->d_w_pos;
+  a.l = P->H.l;
+  a.in = in;
+  a.out = out;
+  return a;
+}
+
+sht_status sht_direct_synthesize(sht_plan_t P, const void* beta, void* G, sht_stream_t stream) {
+  if (!P || !beta || !G) return SHT_ERR_INVALID_ARG;
+  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  if (!P->d_dense) return SHT_ERR_INVALID_ARG;
+  if (!aligned(beta, 16) || !aligned(G, 16)) return SHT_ERR_INVALID_ARG;
+  CK(cudaSetDevice(P->device));
+  CK(sht::direct_synth_launch(direct_args(P, beta, G), reinterpret_cast<cudaStream_t>(stream)));
+  return SHT_OK;
+}
+
+sht_status sht_direct_analyze(sht_plan_t P, const void* G, void* beta, sht_stream_t stream) {
+  if (!P || !beta || !G) return SHT_ERR_INVALID_ARG;
+  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  if (!P->d_dense) return SHT_ERR_INVALID_ARG;
+  if (!aligned(beta, 16) || !aligned(G, 16)) return SHT_ERR_INVALID_ARG;
+  CK(cudaSetDevice(P->device));
+  CK(sht::direct_analysis_launch(direct_args(P, G, beta), reinterpret_cast<cudaStream_t>(stream)));
+  return SHT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,49 @@
+// kernels.h -- host-side launch interface of the CUDA kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "sht_stream.h"
+
+namespace sht {
+
+// Arguments of the persistent butterfly sweep (one launch = one direction of
+// the Legendre stage for every order m).
+struct SweepArgs {
+  const uint8_t* pages;        // stream pages (device)
+  const UnitEntry* units;      // LPT-ordered unit table (device)
+  int n_units;
+  int page_bytes;
+  int nstages;                 // pages in flight per CTA (TMA ring depth)
+  int l;
+  int buf_ab;                  // elements of shared vectors A and B
+  unsigned long long quit_page;
+  const void* in;              // synthesis: beta; analysis: G
+  void* out;                   // synthesis: G; analysis: beta
+  const double* prescale;      // FOLD: per positive node scale (l entries) or nullptr
+  unsigned* counter;           // work-queue counter (self-resetting; 0 between launches)
+  unsigned* status;            // device status word (0 = ok)
+};
+
+enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2 };
+
+size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int l);
+cudaError_t sweep_configure(int prec, size_t smem);
+cudaError_t sweep_launch(int prec, const SweepArgs& a, int grid, size_t smem, cudaStream_t st);
+
+// Direct float64 baseline: dense P-bar blocks, [j][i] per (m, p), i fastest.
+struct DirectArgs {
+  const double* dense;         // all blocks
+  const long long* off;        // [2l * 2] offsets (doubles) of block (m, p)
+  const int* rows;             // [2l * 2] kept rows
+  const int* ncol;             // [2l * 2] columns n_{m,p}
+  const double* w_pos;         // l positive-node weights
+  int l;
+  const void* in;
+  void* out;
+};
+cudaError_t direct_synth_launch(const DirectArgs& a, cudaStream_t st);
+cudaError_t direct_analysis_launch(const DirectArgs& a, cudaStream_t st);
+
+}  // namespace sht

@@ -1,0 +1,919 @@
+// plan_build.cpp -- host precomputation of the butterfly factor streams.
+//
+//   gl_nodes              Section 2, eq. thetas (Gauss-Legendre nodes/weights)
+//   ColumnStream          Section 2.3 eqs. c_rec, d_rec, recurrence0, recurrence
+//                         (x^2 recurrence) with exponent tracking (Section 4)
+//   interp_decomp         Section 2.1, Remark QR_algorithm (pivoted-QR ID)
+//   factor_unit           Section 2.2 eqs. 1-6, top, bottom (butterfly) built in
+//                         the depth-first order of Section 3
+//   emit_streams          page encoding of sht_stream.h
+//
+// All arithmetic is float64; nothing here runs on the hot path.
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <stdexcept>
+#include <thread>
+
+#include "plan_host.h"
+
+namespace sht {
+
+namespace {
+
+// ------------------------------------------------------------ GL nodes
+
+// Normalized Legendre P-bar^0_n(x) and its derivative, from the normalized
+// three-term recurrence P-bar_{j+1} = a_{j+1} x P-bar_j - (a_{j+1}/a_j) P-bar_{j-1},
+// a_j = sqrt(4j^2 - 1)/j, and (1-x^2) P-bar_n' = n (sqrt((2n+1)/(2n-1)) P-bar_{n-1} - x P-bar_n).
+void pbar0(int n, double x, double one_m_x2, double& p, double& dp) {
+  double pm1 = 0.0, pj = 1.0 / std::sqrt(2.0), aj = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double jj = j + 1.0;
+    const double an = std::sqrt(4.0 * jj * jj - 1.0) / jj;
+    const double pn = (j == 0) ? an * x * pj : an * x * pj - (an / aj) * pm1;
+    pm1 = pj;
+    pj = pn;
+    aj = an;
+  }
+  p = pj;
+  dp = n * (std::sqrt((2.0 * n + 1.0) / (2.0 * n - 1.0)) * pm1 - x * pj) / one_m_x2;
+}
+
+}  // namespace
+
+void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& theta_pos) {
+  if (npts < 2 || (npts & 1)) throw std::invalid_argument("gl_nodes: npts must be even");
+  const int n = npts, half = n / 2;
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  theta_pos.assign(half, 0.0);
+  for (int k = 1; k <= half; ++k) {
+    // Tricomi-type start: phi = pi (k - 1/4)/(n + 1/2), theta ~ phi + cot(phi) / (8 (n + 1/2)^2)
+    const double phi = M_PI * (k - 0.25) / (n + 0.5);
+    double th = phi + 1.0 / (std::tan(phi) * 8.0 * (n + 0.5) * (n + 0.5));
+    double dp_exact = 0.0;
+    for (int it = 0; it < 60; ++it) {
+      const double xr = std::cos(th);
+      // delta = cos(th) - xr without cancellation (th < pi/2: cos = 1 - 2 sin^2(th/2))
+      const double sh = std::sin(0.5 * th);
+      const double delta = (1.0 - xr) - 2.0 * sh * sh;
+      const double omx2 = (1.0 - xr) * (1.0 + xr);
+      double p, dp;
+      pbar0(n, xr, omx2, p, dp);
+      // Legendre's equation (eq. sturm-liouville_Leg, m = 0): (1-x^2) P'' = 2 x P' - n(n+1) P
+      const double d2p = (2.0 * xr * dp - n * (n + 1.0) * p) / omx2;
+      const double p_exact = p + dp * delta;
+      dp_exact = dp + d2p * delta;
+      const double step = p_exact / (std::sin(th) * dp_exact);  // d/dth P(cos th) = -sin(th) P'
+      th += step;
+      if (std::fabs(step) < 1e-18 && it > 1) break;
+    }
+    {
+      // final derivative at the converged angle
+      const double xr = std::cos(th);
+      const double sh = std::sin(0.5 * th);
+      const double delta = (1.0 - xr) - 2.0 * sh * sh;
+      const double omx2 = (1.0 - xr) * (1.0 + xr);
+      double p, dp;
+      pbar0(n, xr, omx2, p, dp);
+      const double d2p = (2.0 * xr * dp - n * (n + 1.0) * p) / omx2;
+      dp_exact = dp + d2p * delta;
+    }
+    const double s = std::sin(th);
+    // w = 2 / ((1-x^2) P_n'^2) with P_n = sqrt(2/(2n+1)) P-bar_n
+    const double wk = (2.0 * n + 1.0) / (s * s * dp_exact * dp_exact);
+    const double xk = std::cos(th);
+    // k = 1 is the largest node; positive nodes sit at indices half..n-1 ascending
+    x[n - k] = xk;
+    x[k - 1] = -xk;
+    w[n - k] = wk;
+    w[k - 1] = wk;
+    theta_pos[half - k] = th;
+  }
+}
+
+// ------------------------------------------------------- column stream
+
+namespace {
+inline double rec_c(int k, int m) {  // eq. c_rec
+  const double a = (double)(k - m + 1) * (k - m + 2) * (double)(k + m + 1) * (k + m + 2);
+  const double b = (2.0 * k + 1.0) * (2.0 * k + 3.0) * (2.0 * k + 3.0) * (2.0 * k + 5.0);
+  return std::sqrt(a / b);
+}
+inline double rec_d(int k, int m) {  // eq. d_rec
+  return (2.0 * k * (k + 1.0) - 2.0 * (double)m * m - 1.0) / ((2.0 * k - 1.0) * (2.0 * k + 3.0));
+}
+inline void renorm(double& v, int& e) {
+  if (v == 0.0) return;
+  int t;
+  v = std::frexp(v, &t);
+  e += t;
+}
+}  // namespace
+
+ColumnStream::ColumnStream(const PlanHost& P, int m, int p, int rows)
+    : m_(m), p_(p), rows_(rows), j_(0) {
+  const int l = P.l;
+  x2_.resize(rows);
+  sq2w_.resize(rows);
+  a_.assign(rows, 0.0);
+  b_.resize(rows);
+  e_.resize(rows);
+  // c_m = (1/sqrt 2) prod_{j=1}^m sqrt((2j+1)/(2j)): P-bar^m_m(x) = c_m (1-x^2)^{m/2}
+  // (eq. association with d^m P_m / dx^m = (2m)! / (2^m m!))
+  double cm = 1.0 / std::sqrt(2.0);
+  int ecm = 0;
+  for (int j = 1; j <= m; ++j) {
+    cm *= std::sqrt((2.0 * j + 1.0) / (2.0 * j));
+    renorm(cm, ecm);
+  }
+  for (int i = 0; i < rows; ++i) {
+    const double xi = P.x[l + i];
+    const double s = std::sin(P.theta_pos[i]);
+    x2_[i] = xi * xi;
+    sq2w_[i] = std::sqrt(2.0 * P.w[l + i]);
+    // s^m by binary powering with tracked exponents
+    int eb;
+    double base = std::frexp(s, &eb);
+    double res = 1.0;
+    int er = 0;
+    for (int q = m; q; q >>= 1) {
+      if (q & 1) {
+        res *= base;
+        er += eb;
+        renorm(res, er);
+      }
+      base *= base;
+      eb *= 2;
+      renorm(base, eb);
+    }
+    double v = res * cm;
+    int ev = er + ecm;
+    if (p == 1) v *= std::sqrt(2.0 * m + 3.0) * xi;  // P-bar^m_{m+1} = sqrt(2m+3) x P-bar^m_m
+    renorm(v, ev);
+    b_[i] = v;
+    e_[i] = ev;
+  }
+}
+
+void ColumnStream::next(double* col) {
+  const int k = m_ + p_ + 2 * j_;
+  for (int i = 0; i < rows_; ++i) col[i] = sq2w_[i] * std::ldexp(b_[i], e_[i]);
+  // advance P-bar_k -> P-bar_{k+2}: x^2 P_k = c_{k-2} P_{k-2} + d_k P_k + c_k P_{k+2}
+  const double ck = rec_c(k, m_), dk = rec_d(k, m_);
+  const double ckm2 = (j_ > 0) ? rec_c(k - 2, m_) : 0.0;  // eq. recurrence0 for j = 0
+  const double inv_ck = 1.0 / ck;
+  for (int i = 0; i < rows_; ++i) {
+    const double nb = ((x2_[i] - dk) * b_[i] - ckm2 * a_[i]) * inv_ck;
+    a_[i] = b_[i];
+    b_[i] = nb;
+    const double big = std::max(std::fabs(a_[i]), std::fabs(b_[i]));
+    if (big > 0x1p400 || (big < 0x1p-400 && big > 0.0)) {
+      const int t = std::ilogb(big);
+      a_[i] = std::ldexp(a_[i], -t);
+      b_[i] = std::ldexp(b_[i], -t);
+      e_[i] += t;
+    }
+  }
+  ++j_;
+}
+
+// ------------------------------------------------------------------ ID
+
+int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm, std::vector<double>& T) {
+  perm.resize(w);
+  std::iota(perm.begin(), perm.end(), 0);
+  T.clear();
+  if (w == 0) return 0;
+  std::vector<double> nrm(w), ref(w);
+  for (int j = 0; j < w; ++j) {
+    const double* c = A + (size_t)j * h;
+    double s = 0.0;
+    for (int r = 0; r < h; ++r) s += c[r] * c[r];
+    nrm[j] = ref[j] = s;
+  }
+  const double eps2 = eps * eps;
+  const int kmax = std::min(h, w);
+  int k = 0;
+  auto exact_norm = [&](int j, int i0) {
+    const double* c = A + (size_t)j * h;
+    double s = 0.0;
+    for (int r = i0; r < h; ++r) s += c[r] * c[r];
+    return s;
+  };
+  for (int i = 0; i < kmax; ++i) {
+    int p = i;
+    for (int j = i + 1; j < w; ++j)
+      if (nrm[j] > nrm[p]) p = j;  // ties: lowest index
+    nrm[p] = exact_norm(p, i);
+    if (nrm[p] <= eps2) {
+      // the downdated norms may have drifted: recompute all before stopping
+      for (int j = i; j < w; ++j) nrm[j] = ref[j] = exact_norm(j, i);
+      p = i;
+      for (int j = i + 1; j < w; ++j)
+        if (nrm[j] > nrm[p]) p = j;
+      if (nrm[p] <= eps2) break;
+    }
+    if (p != i) {
+      std::swap_ranges(A + (size_t)i * h, A + (size_t)i * h + h, A + (size_t)p * h);
+      std::swap(nrm[i], nrm[p]);
+      std::swap(ref[i], ref[p]);
+      std::swap(perm[i], perm[p]);
+    }
+    // Householder reflector for A[i:h, i]
+    double* ci = A + (size_t)i * h;
+    const double alpha = ci[i];
+    double sigma = 0.0;
+    for (int r = i + 1; r < h; ++r) sigma += ci[r] * ci[r];
+    double tau = 0.0;
+    if (sigma != 0.0 || alpha < 0.0) {
+      const double nx = std::sqrt(alpha * alpha + sigma);
+      const double beta = (alpha <= 0.0) ? nx : -nx;
+      tau = (beta - alpha) / beta;
+      const double sc = 1.0 / (alpha - beta);
+      for (int r = i + 1; r < h; ++r) ci[r] *= sc;
+      ci[i] = beta;
+    }
+    if (tau != 0.0) {
+      for (int j = i + 1; j < w; ++j) {
+        double* cj = A + (size_t)j * h;
+        double dot = cj[i];
+        for (int r = i + 1; r < h; ++r) dot += ci[r] * cj[r];
+        dot *= tau;
+        cj[i] -= dot;
+        for (int r = i + 1; r < h; ++r) cj[r] -= dot * ci[r];
+      }
+    }
+    for (int j = i + 1; j < w; ++j) {
+      const double rij = A[(size_t)j * h + i];
+      nrm[j] -= rij * rij;
+      if (nrm[j] < 1e-4 * ref[j]) nrm[j] = ref[j] = exact_norm(j, i + 1);
+    }
+    k = i + 1;
+  }
+  // T = R11^{-1} R12 by back substitution, column by column
+  const int nred = w - k;
+  T.assign((size_t)k * nred, 0.0);
+  for (int s = 0; s < nred; ++s) {
+    const double* rc = A + (size_t)(k + s) * h;
+    double* tc = T.data() + (size_t)s * k;
+    for (int t = k - 1; t >= 0; --t) {
+      double v = rc[t];
+      for (int t2 = t + 1; t2 < k; ++t2) v -= A[(size_t)t2 * h + t] * tc[t2];
+      tc[t] = v / A[(size_t)t * h + t];
+    }
+  }
+  // redundant columns in ascending order (T columns follow)
+  std::vector<int> ord(nred);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return perm[k + a] < perm[k + b]; });
+  std::vector<int> red(nred);
+  std::vector<double> T2(T.size());
+  for (int s = 0; s < nred; ++s) {
+    red[s] = perm[k + ord[s]];
+    std::copy(T.begin() + (size_t)ord[s] * k, T.begin() + (size_t)(ord[s] + 1) * k, T2.begin() + (size_t)s * k);
+  }
+  std::copy(red.begin(), red.end(), perm.begin() + k);
+  T.swap(T2);
+  return k;
+}
+
+// ------------------------------------------------------- butterflies
+
+namespace {
+
+struct BandData {
+  int r0 = 0, r1 = 0, k = 0;
+  std::vector<double> Ask;  // (r1 - r0) x k, column-major: the skeleton columns
+};
+struct Group {
+  int level = 0, g = 0;
+  std::vector<BandData> bands;
+};
+
+long long group_words(const std::vector<Group>& st) {
+  long long s = 0;
+  for (const auto& g : st)
+    for (const auto& b : g.bands) s += (long long)b.Ask.size();
+  return s;
+}
+
+UnitFact factor_unit(const PlanHost& P, int m, int p, double eps) {
+  UnitFact U;
+  U.m = m;
+  U.p = p;
+  const int l = P.l, L = 2 * l;
+  const int n = std::max(0, (L - m - p + 1) / 2);
+  U.n = n;
+  if (n == 0) return U;
+
+  // trimming: rows whose weighted norm is below trim/sqrt(l) (a suffix) are dropped
+  int rows = l;
+  std::vector<double> col(l);
+  if (P.trim_eps > 0.0) {
+    ColumnStream cs(P, m, p, l);
+    std::vector<double> nr(l, 0.0);
+    for (int j = 0; j < n; ++j) {
+      cs.next(col.data());
+      for (int i = 0; i < l; ++i) nr[i] += col[i] * col[i];
+    }
+    const double thr = P.trim_eps / std::sqrt((double)l);
+    rows = 0;
+    for (int i = 0; i < l; ++i)
+      if (nr[i] >= thr * thr) rows = i + 1;
+  }
+  U.rows = rows;
+  if (rows == 0) return U;
+
+  const int C = P.leaf_cols;
+  int lam = 0;
+  while ((n >> lam) > C) ++lam;  // 2^lam leaves of width <= ~C
+  if (n > C && (n + (1 << lam) - 1) / (1 << lam) > C) ++lam;
+  while (lam > 0 && (rows >> lam) < P.min_band_rows) --lam;
+  const int nleaves = 1 << lam;
+
+  // depth-first construction (Section 3): each full-height leaf is built only
+  // after everything to its left has been merged as far as possible.
+  ColumnStream cs(P, m, p, rows);
+  std::vector<Group> stack;
+  std::vector<int> perm;
+  std::vector<double> T;
+  long long peak = 0;
+  for (int g = 0; g < nleaves; ++g) {
+    const int c0 = (int)((long long)g * n / nleaves), c1 = (int)((long long)(g + 1) * n / nleaves);
+    const int wd = c1 - c0;
+    std::vector<double> leaf((size_t)rows * wd);
+    for (int j = 0; j < wd; ++j) cs.next(leaf.data() + (size_t)j * rows);
+    std::vector<double> work(leaf);
+    const int k = interp_decomp(work.data(), rows, wd, eps, perm, T);
+    IdBlock b;
+    b.level = 1;
+    b.band = 0;
+    b.group = g;
+    b.r0 = 0;
+    b.r1 = rows;
+    b.in_off = c0;
+    b.nin = wd;
+    b.k = k;
+    b.skel.assign(perm.begin(), perm.begin() + k);
+    b.red.assign(perm.begin() + k, perm.end());
+    b.T = T;
+    U.blocks.push_back(std::move(b));
+    Group grp;
+    grp.level = 1;
+    grp.g = g;
+    BandData bd;
+    bd.r0 = 0;
+    bd.r1 = rows;
+    bd.k = k;
+    bd.Ask.resize((size_t)rows * k);
+    for (int t = 0; t < k; ++t)
+      std::copy(leaf.begin() + (size_t)perm[t] * rows, leaf.begin() + (size_t)(perm[t] + 1) * rows,
+                bd.Ask.begin() + (size_t)t * rows);
+    grp.bands.push_back(std::move(bd));
+    stack.push_back(std::move(grp));
+    peak = std::max(peak, group_words(stack) + (long long)leaf.size() * 2);
+
+    while (stack.size() >= 2 && stack[stack.size() - 1].level == stack[stack.size() - 2].level) {
+      Group R = std::move(stack.back());
+      stack.pop_back();
+      Group Lg = std::move(stack.back());
+      stack.pop_back();
+      const int j = Lg.level;
+      Group ng;
+      ng.level = j + 1;
+      ng.g = Lg.g / 2;
+      ng.bands.resize(Lg.bands.size() * 2);
+      for (size_t beta = 0; beta < Lg.bands.size(); ++beta) {
+        const BandData& BL = Lg.bands[beta];
+        const BandData& BR = R.bands[beta];
+        const int h = BL.r1 - BL.r0, mid = BL.r0 + h / 2;
+        const int kin = BL.k + BR.k;
+        for (int half = 0; half < 2; ++half) {
+          const int rr0 = half ? mid : BL.r0, rr1 = half ? BL.r1 : mid, hh = rr1 - rr0;
+          std::vector<double> Z((size_t)hh * kin);
+          for (int t = 0; t < BL.k; ++t)
+            std::copy(BL.Ask.begin() + (size_t)t * h + (rr0 - BL.r0), BL.Ask.begin() + (size_t)t * h + (rr1 - BL.r0),
+                      Z.begin() + (size_t)t * hh);
+          for (int t = 0; t < BR.k; ++t)
+            std::copy(BR.Ask.begin() + (size_t)t * h + (rr0 - BL.r0), BR.Ask.begin() + (size_t)t * h + (rr1 - BL.r0),
+                      Z.begin() + (size_t)(BL.k + t) * hh);
+          std::vector<double> Zw(Z);
+          const int k = interp_decomp(Zw.data(), hh, kin, eps, perm, T);
+          IdBlock b;
+          b.level = j + 1;
+          b.band = (int)(2 * beta + half);
+          b.group = ng.g;
+          b.r0 = rr0;
+          b.r1 = rr1;
+          b.nin = kin;
+          b.k = k;
+          b.skel.assign(perm.begin(), perm.begin() + k);
+          b.red.assign(perm.begin() + k, perm.end());
+          b.T = T;
+          U.blocks.push_back(std::move(b));
+          BandData nb;
+          nb.r0 = rr0;
+          nb.r1 = rr1;
+          nb.k = k;
+          nb.Ask.resize((size_t)hh * k);
+          for (int t = 0; t < k; ++t)
+            std::copy(Z.begin() + (size_t)perm[t] * hh, Z.begin() + (size_t)(perm[t] + 1) * hh,
+                      nb.Ask.begin() + (size_t)t * hh);
+          ng.bands[2 * beta + half] = std::move(nb);
+        }
+      }
+      stack.push_back(std::move(ng));
+      peak = std::max(peak, group_words(stack));
+    }
+  }
+  U.peak_words = peak;
+  U.levels = lam;
+
+  // layouts: level j holds its blocks band-major, group-minor
+  U.width.assign(lam + 2, 0);
+  std::vector<std::vector<int>> at(lam + 2);
+  for (int bi = 0; bi < (int)U.blocks.size(); ++bi) at[U.blocks[bi].level].push_back(bi);
+  for (int j = 1; j <= lam + 1; ++j) {
+    auto& v = at[j];
+    std::sort(v.begin(), v.end(), [&](int a, int b) {
+      const IdBlock &A = U.blocks[a], &B = U.blocks[b];
+      return A.band != B.band ? A.band < B.band : A.group < B.group;
+    });
+    int off = 0;
+    for (int bi : v) {
+      U.blocks[bi].out_off = off;
+      off += U.blocks[bi].k;
+    }
+    U.width[j] = off;
+  }
+  // input offsets of merge blocks: z = [y(L); y(R)] of the parent band, groups 2g and 2g+1
+  for (int j = 2; j <= lam + 1; ++j) {
+    for (int bi : at[j]) {
+      IdBlock& B = U.blocks[bi];
+      const int pb = B.band / 2;
+      int found = -1;
+      for (int ci : at[j - 1])
+        if (U.blocks[ci].band == pb && U.blocks[ci].group == 2 * B.group) found = ci;
+      if (found < 0) throw std::logic_error("butterfly layout: missing left child");
+      B.in_off = U.blocks[found].out_off;
+    }
+  }
+  // top level: one group, 2^lam bands whose stored skeleton columns are the final blocks
+  const Group& top = stack.back();
+  for (size_t beta = 0; beta < top.bands.size(); ++beta) {
+    FinalBlock f;
+    f.band = (int)beta;
+    f.r0 = top.bands[beta].r0;
+    f.r1 = top.bands[beta].r1;
+    f.k = top.bands[beta].k;
+    f.S = top.bands[beta].Ask;  // column-major h x k == S[t * h + i]
+    for (int bi : at[lam + 1])
+      if (U.blocks[bi].band == (int)beta) f.in_off = U.blocks[bi].out_off;
+    U.finals.push_back(std::move(f));
+  }
+  for (const auto& b : U.blocks) {
+    U.values += (long long)b.k * (b.nin - b.k);
+    U.idx += b.nin;
+  }
+  for (const auto& f : U.finals) U.values += (long long)f.k * (f.r1 - f.r0);
+
+  // a dense block is cheaper when compression does not pay
+  const double bfly_bytes = 8.0 * U.values + 2.0 * U.idx + 48.0 * (U.blocks.size() + U.finals.size());
+  const double dense_bytes = 8.0 * rows * (double)n;
+  if (dense_bytes <= bfly_bytes) {
+    U.direct = true;
+    U.blocks.clear();
+    U.finals.clear();
+    U.width.clear();
+    U.levels = 0;
+    U.values = (long long)rows * n;
+    U.idx = 0;
+    U.D.resize((size_t)rows * n);
+    ColumnStream cs2(P, m, p, rows);
+    for (int j = 0; j < n; ++j) cs2.next(U.D.data() + (size_t)j * rows);
+  }
+  U.cost = std::min(bfly_bytes, dense_bytes);
+  return U;
+}
+
+}  // namespace
+
+void build_factorizations(PlanHost& P, bool fp32) {
+  const int l = P.l, L = 2 * l;
+  const double eps = fp32 ? P.eps_fp32 : P.eps_id;
+  std::vector<UnitFact>& out = fp32 ? P.fact32 : P.fact64;
+  out.assign((size_t)L * 2, UnitFact());
+  std::vector<int> order(L * 2);
+  std::iota(order.begin(), order.end(), 0);
+  // biggest first (n_{m,p} ~ (2l - m)/2)
+  std::sort(order.begin(), order.end(), [](int a, int b) { return (a / 2) < (b / 2); });
+  std::atomic<int> next(0);
+  int nt = P.num_threads > 0 ? P.num_threads : (int)std::thread::hardware_concurrency();
+  nt = std::max(1, std::min(nt, 256));
+  std::vector<std::string> errors(nt);
+  auto worker = [&](int tid) {
+    try {
+      for (;;) {
+        const int q = next.fetch_add(1);
+        if (q >= (int)order.size()) break;
+        const int u = order[q];
+        out[u] = factor_unit(P, u / 2, u % 2, eps);
+      }
+    } catch (const std::exception& e) {
+      errors[tid] = e.what();
+      next.store((int)order.size());
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(worker, t);
+  worker(0);
+  for (auto& t : th) t.join();
+  for (auto& e : errors)
+    if (!e.empty()) throw std::runtime_error(e);
+}
+
+// --------------------------------------------------------------- pages
+
+namespace {
+
+inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
+
+struct PageWriter {
+  std::vector<uint8_t>& buf;
+  size_t PB;
+  size_t page_start = 0, pos = 0;
+  bool open = false;
+  PageWriter(std::vector<uint8_t>& b, size_t pb) : buf(b), PB(pb) {}
+  void new_page() {
+    page_start = buf.size();
+    buf.resize(buf.size() + PB, 0);
+    pos = 0;
+    open = true;
+  }
+  size_t space() const { return open ? PB - pos : 0; }
+  uint8_t* alloc(size_t bytes) {
+    if (bytes > PB) throw std::logic_error("op larger than a page");
+    if (bytes > space()) new_page();
+    uint8_t* p = buf.data() + page_start + pos;
+    pos += bytes;
+    return p;
+  }
+};
+
+// value encodings per precision: 0 = FP64 (double), 1 = FP32 (float), 2 = SPLIT32 (float hi, float lo)
+inline size_t value_size(int prec) { return prec == 1 ? 4 : 8; }
+inline void put_value(uint8_t* dst, int prec, size_t i, double v) {
+  if (prec == 0) {
+    reinterpret_cast<double*>(dst)[i] = v;
+  } else if (prec == 1) {
+    reinterpret_cast<float*>(dst)[i] = (float)v;
+  } else {
+    const float hi = (float)v;
+    const float lo = (float)(v - (double)hi);
+    reinterpret_cast<float*>(dst)[2 * i] = hi;
+    reinterpret_cast<float*>(dst)[2 * i + 1] = lo;
+  }
+}
+
+struct Emitter {
+  PageWriter& W;
+  int prec;
+  size_t vs;
+  Emitter(PageWriter& w, int p) : W(w), prec(p), vs(value_size(p)) {}
+
+  OpHdr hdr(uint8_t kind, uint8_t flags) {
+    OpHdr h;
+    std::memset(&h, 0, sizeof(h));
+    h.kind = kind;
+    h.flags = flags;
+    return h;
+  }
+  void control(OpHdr h) {
+    h.bytes = sizeof(OpHdr);
+    h.idx_bytes = 0;
+    std::memcpy(W.alloc(sizeof(OpHdr)), &h, sizeof(OpHdr));
+  }
+  size_t bytes_of(size_t nidx, size_t nval) const { return sizeof(OpHdr) + pad16(2 * nidx) + pad16(vs * nval); }
+
+  // largest piece of outputs (<= cap) that fits in the current page; 0 if none
+  template <class F>
+  int fit(int remaining, F bytes_for) {
+    int lo = 0, hi = std::min(remaining, kMaxM);
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (bytes_for(mid) <= W.space()) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  }
+  template <class F>
+  int piece(int remaining, F bytes_for) {
+    const int want = std::min(remaining, 16);
+    int mp = fit(remaining, bytes_for);
+    if (mp < want) {
+      W.new_page();
+      mp = fit(remaining, bytes_for);
+    }
+    if (mp <= 0) throw std::logic_error("op does not fit in a page");
+    return mp;
+  }
+  void write(OpHdr h, const std::vector<uint16_t>& idx, size_t nval, const std::vector<double>& vals) {
+    h.idx_bytes = (uint32_t)pad16(2 * idx.size());
+    h.bytes = (uint32_t)bytes_of(idx.size(), nval);
+    uint8_t* p = W.alloc(h.bytes);
+    std::memcpy(p, &h, sizeof(OpHdr));
+    if (!idx.empty()) std::memcpy(p + sizeof(OpHdr), idx.data(), 2 * idx.size());
+    uint8_t* v = p + sizeof(OpHdr) + h.idx_bytes;
+    for (size_t i = 0; i < nval; ++i) put_value(v, prec, i, vals[i]);
+  }
+
+  // y[oo + o] = z[io + skel[o]] + sum_s T[s][o] z[io + red[s]]; wide inner
+  // dimensions are split into chunks accumulated with F_ACCUM (the skeleton
+  // pass-through rides on the first chunk only).
+  void syn_interp(const IdBlock& b, uint8_t in_buf, uint8_t out_buf, bool sync) {
+    const int k = b.k, K = b.nin - b.k;
+    const int mk = std::min(k, 32);
+    int Kc = std::max(K, 1);
+    while (Kc > 1 && bytes_of((size_t)Kc + mk, (size_t)Kc * mk) > W.PB) Kc = Kc * 3 / 4;
+    for (int k0 = 0; k0 == 0 || k0 < K; k0 += Kc) {
+      const int kc = std::min(Kc, K - k0);
+      const bool first_chunk = (k0 == 0);
+      for (int o0 = 0; o0 < k;) {
+        const int mp = piece(k - o0, [&](int M) {
+          return bytes_of((size_t)kc + (first_chunk ? M : 0), (size_t)kc * M);
+        });
+        OpHdr h = hdr(OP_SYN_INTERP, (sync ? F_SYNC_BEFORE : 0) | (first_chunk ? 0 : F_ACCUM));
+        sync = false;
+        h.in_buf = in_buf;
+        h.out_buf = out_buf;
+        h.M = (uint16_t)mp;
+        h.K = (uint16_t)kc;
+        h.nskel = (uint16_t)(first_chunk ? mp : 0);
+        h.io = (uint16_t)b.in_off;
+        h.oo = (uint16_t)(b.out_off + o0);
+        std::vector<uint16_t> idx(b.red.begin() + k0, b.red.begin() + k0 + kc);
+        if (first_chunk) idx.insert(idx.end(), b.skel.begin() + o0, b.skel.begin() + o0 + mp);
+        std::vector<double> vals((size_t)kc * mp);
+        for (int s2 = 0; s2 < kc; ++s2)
+          for (int o = 0; o < mp; ++o) vals[(size_t)s2 * mp + o] = b.T[(size_t)(k0 + s2) * k + o0 + o];
+        write(h, idx, vals.size(), vals);
+        o0 += mp;
+      }
+      if (K == 0) break;
+    }
+  }
+
+  // out[oo + o] (=|+=) sum_s V(s, o) in[io + s], o < M, s < K; split over K with F_ACCUM if needed
+  template <class GetV>
+  void dense(int M, int K, GetV getv, uint8_t in_buf, int io, uint8_t out_buf, int oo, bool sync, bool accum = false) {
+    const size_t maxk_rows = std::min(M, 32);
+    int Kc = K;
+    if (K > 0 && bytes_of(0, (size_t)K * maxk_rows) > W.PB)
+      Kc = (int)((W.PB - sizeof(OpHdr) - 16) / (vs * maxk_rows));
+    for (int k0 = 0; k0 < std::max(K, 1); k0 += std::max(Kc, 1)) {
+      const int kc = std::min(Kc, K - k0);
+      for (int o0 = 0; o0 < M;) {
+        const int mp = piece(M - o0, [&](int Mp) { return bytes_of(0, (size_t)std::max(kc, 0) * Mp); });
+        OpHdr h = hdr(OP_DENSE, (sync ? F_SYNC_BEFORE : 0) | ((accum || k0 > 0) ? F_ACCUM : 0));
+        sync = false;
+        h.in_buf = in_buf;
+        h.out_buf = out_buf;
+        h.M = (uint16_t)mp;
+        h.K = (uint16_t)std::max(kc, 0);
+        h.io = (uint16_t)(io + k0);
+        h.oo = (uint16_t)(oo + o0);
+        std::vector<double> vals((size_t)std::max(kc, 0) * mp);
+        for (int s = 0; s < kc; ++s)
+          for (int o = 0; o < mp; ++o) vals[(size_t)s * mp + o] = getv(k0 + s, o0 + o);
+        write(h, {}, vals.size(), vals);
+        o0 += mp;
+      }
+      if (K == 0) break;
+    }
+  }
+
+  // z[oo + red[o]] += sum_t T[o][t] y[io + t]; z[oo + skel[t]] += y[io + t]
+  void ana_interp(const IdBlock& b, uint8_t in_buf, uint8_t out_buf, bool sync) {
+    const int k = b.k, nred = b.nin - b.k;
+    if (k == 0) return;
+    bool skel_done = false;
+    for (int o0 = 0; o0 < nred || !skel_done;) {
+      const int rem = nred - o0;
+      int mp;
+      if (rem > 0) {
+        const size_t extra = skel_done ? 0 : (size_t)k;
+        mp = piece(rem, [&](int M) { return bytes_of((size_t)M + extra, (size_t)k * M); });
+      } else {
+        mp = 0;
+        if (bytes_of(k, 0) > W.space()) W.new_page();
+      }
+      OpHdr h = hdr(OP_ANA_INTERP, (sync ? F_SYNC_BEFORE : 0) | (skel_done ? 0 : F_SKEL));
+      sync = false;
+      h.in_buf = in_buf;
+      h.out_buf = out_buf;
+      h.M = (uint16_t)mp;
+      h.K = (uint16_t)k;
+      h.nskel = (uint16_t)(skel_done ? 0 : k);
+      h.io = (uint16_t)b.out_off;
+      h.oo = (uint16_t)b.in_off;
+      std::vector<uint16_t> idx(b.red.begin() + o0, b.red.begin() + o0 + mp);
+      if (!skel_done) idx.insert(idx.end(), b.skel.begin(), b.skel.end());
+      std::vector<double> vals((size_t)k * mp);
+      for (int t = 0; t < k; ++t)
+        for (int o = 0; o < mp; ++o) vals[(size_t)t * mp + o] = b.T[(size_t)(o0 + o) * k + t];
+      write(h, idx, vals.size(), vals);
+      skel_done = true;
+      o0 += mp;
+      if (o0 >= nred) break;
+    }
+  }
+};
+
+inline uint8_t level_buf(int j) { return (j & 1) ? BUF_B : BUF_A; }
+
+void emit_unit(PlanHost& P, int prec, int dir, int m, std::vector<uint8_t>& out) {
+  const int l = P.l;
+  const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
+  PageWriter W(out, (size_t)P.page_bytes);
+  W.new_page();
+  Emitter E(W, prec);
+  std::vector<double> inv_sq2w(l), sqw2(l);
+  for (int i = 0; i < l; ++i) {
+    inv_sq2w[i] = 1.0 / std::sqrt(2.0 * P.w[l + i]);
+    sqw2[i] = std::sqrt(0.5 * P.w[l + i]);
+  }
+  if (dir == 0) {
+    int rows[2] = {0, 0};
+    for (int p = 0; p < 2; ++p) {
+      const UnitFact& U = F[(size_t)m * 2 + p];
+      if (U.n == 0 || U.rows == 0) continue;
+      rows[p] = U.rows;
+      const uint8_t outE = p ? BUF_O : BUF_E;
+      OpHdr g = E.hdr(OP_GATHER, F_SYNC_BEFORE);
+      g.a0 = (uint16_t)p;
+      g.a1 = (uint32_t)m;
+      g.M = (uint16_t)U.n;
+      g.out_buf = BUF_A;
+      g.oo = 0;
+      E.control(g);
+      if (U.direct) {
+        // E_i = sum_j P-bar(x_i) x_j: weighted values divided by sqrt(2 w_i)
+        E.dense(U.rows, U.n, [&](int s, int o) { return U.D[(size_t)s * U.rows + o] * inv_sq2w[o]; },
+                BUF_A, 0, outE, 0, true);
+      } else {
+        for (int j = 1; j <= U.levels + 1; ++j) {
+          bool first = true;
+          std::vector<const IdBlock*> v;
+          for (const auto& b : U.blocks)
+            if (b.level == j) v.push_back(&b);
+          std::sort(v.begin(), v.end(), [](const IdBlock* a, const IdBlock* b) { return a->out_off < b->out_off; });
+          for (const IdBlock* b : v) {
+            if (b->k == 0) continue;
+            E.syn_interp(*b, j == 1 ? BUF_A : level_buf(j - 1), level_buf(j), first);
+            first = false;
+          }
+        }
+        bool first = true;
+        const uint8_t top = level_buf(U.levels + 1);
+        for (const auto& f : U.finals) {
+          const int h = f.r1 - f.r0;
+          E.dense(h, f.k, [&](int s, int o) { return f.S[(size_t)s * h + o] * inv_sq2w[f.r0 + o]; },
+                  top, f.in_off, outE, f.r0, first);
+          first = false;
+        }
+      }
+    }
+    OpHdr u = E.hdr(OP_UNFOLD, F_SYNC_BEFORE);
+    u.a1 = (uint32_t)m;
+    u.M = (uint16_t)rows[0];
+    u.K = (uint16_t)rows[1];
+    E.control(u);
+  } else {
+    OpHdr f = E.hdr(OP_FOLD, F_SYNC_BEFORE);
+    f.a1 = (uint32_t)m;
+    E.control(f);
+    for (int p = 0; p < 2; ++p) {
+      const UnitFact& U = F[(size_t)m * 2 + p];
+      if (U.n == 0) continue;
+      const uint8_t src = p ? BUF_O : BUF_E;
+      if (U.rows == 0) {
+        OpHdr c = E.hdr(OP_CLEAR, F_SYNC_BEFORE);
+        c.out_buf = BUF_A;
+        c.M = (uint16_t)U.n;
+        E.control(c);
+      } else if (U.direct) {
+        // x_j = sum_i w_i P-bar(x_i) F_i: weighted values times sqrt(w_i / 2)
+        E.dense(U.n, U.rows, [&](int s, int o) { return U.D[(size_t)o * U.rows + s] * sqw2[s]; },
+                src, 0, BUF_A, 0, true);
+      } else {
+        const uint8_t top = level_buf(U.levels + 1);
+        bool first = true;
+        bool any_top = false;
+        for (const auto& fb : U.finals) {
+          if (fb.k == 0) continue;
+          const int h = fb.r1 - fb.r0;
+          E.dense(fb.k, h, [&](int s, int o) { return fb.S[(size_t)o * h + s] * sqw2[fb.r0 + s]; },
+                  src, fb.r0, top, fb.in_off, first);
+          first = false;
+          any_top = true;
+        }
+        if (!any_top && U.width[U.levels + 1] > 0) {
+          OpHdr c = E.hdr(OP_CLEAR, F_SYNC_BEFORE);
+          c.out_buf = top;
+          c.M = (uint16_t)U.width[U.levels + 1];
+          E.control(c);
+        }
+        for (int j = U.levels + 1; j >= 1; --j) {
+          const uint8_t dst = (j == 1) ? BUF_A : level_buf(j - 1);
+          OpHdr c = E.hdr(OP_CLEAR, F_SYNC_BEFORE);
+          c.out_buf = dst;
+          c.M = (uint16_t)(j == 1 ? U.n : U.width[j - 1]);
+          E.control(c);
+          std::vector<const IdBlock*> v;
+          for (const auto& b : U.blocks)
+            if (b.level == j) v.push_back(&b);
+          std::sort(v.begin(), v.end(), [](const IdBlock* a, const IdBlock* b) { return a->out_off < b->out_off; });
+          for (const IdBlock* b : v) E.ana_interp(*b, level_buf(j), dst, false);
+        }
+      }
+      OpHdr s = E.hdr(OP_SCATTER, F_SYNC_BEFORE);
+      s.a0 = (uint16_t)p;
+      s.a1 = (uint32_t)m;
+      s.M = (uint16_t)U.n;
+      s.in_buf = BUF_A;
+      s.io = 0;
+      E.control(s);
+    }
+  }
+}
+
+}  // namespace
+
+void emit_streams(PlanHost& P, int prec) {
+  const int L = 2 * P.l;
+  const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<std::vector<uint8_t>> per(L);
+    std::atomic<int> next(0);
+    int nt = P.num_threads > 0 ? P.num_threads : (int)std::thread::hardware_concurrency();
+    nt = std::max(1, std::min(nt, 256));
+    std::vector<std::string> errors(nt);
+    auto worker = [&](int tid) {
+      try {
+        for (;;) {
+          const int m = next.fetch_add(1);
+          if (m >= L) break;
+          emit_unit(P, prec, dir, m, per[m]);
+        }
+      } catch (const std::exception& e) {
+        errors[tid] = e.what();
+        next.store(L);
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(worker, t);
+    worker(0);
+    for (auto& t : th) t.join();
+    for (auto& e : errors)
+      if (!e.empty()) throw std::runtime_error(e);
+
+    Stream& S = P.streams[prec][dir];
+    S.bytes.clear();
+    S.units.clear();
+    std::vector<int> order(L);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
+    size_t pages = 0;
+    for (int m : order) {
+      UnitEntry e;
+      e.first_page = pages;
+      e.n_pages = (uint32_t)(per[m].size() / P.page_bytes);
+      e.m = (uint32_t)m;
+      S.units.push_back(e);
+      S.bytes.insert(S.bytes.end(), per[m].begin(), per[m].end());
+      pages += e.n_pages;
+    }
+    // trailing QUIT page: a single op of kind 0xFF ends the consumer loop
+    std::vector<uint8_t> quit((size_t)P.page_bytes, 0);
+    OpHdr q;
+    std::memset(&q, 0, sizeof(q));
+    q.bytes = sizeof(OpHdr);
+    q.kind = 0xFF;
+    std::memcpy(quit.data(), &q, sizeof(q));
+    S.bytes.insert(S.bytes.end(), quit.begin(), quit.end());
+    int mx = 0;
+    for (int u = 0; u < L * 2; ++u) {
+      mx = std::max(mx, F[u].n);
+      for (int wdt : F[u].width) mx = std::max(mx, wdt);
+    }
+    S.max_buf_ab = mx;
+  }
+  P.built[prec] = true;
+}
+
+}  // namespace sht

@@ -1,0 +1,119 @@
+// plan_host.h -- host-side precomputation of the butterfly factorization.
+//
+// Everything here runs on the host in float64 (the precomputation of Section
+// 3 and Section 4 is not on the hot path); the results are encoded into the
+// page streams of sht_stream.h and uploaded by capi.cu.
+#pragma once
+
+#include <stdint.h>
+
+#include <array>
+#include <atomic>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "sht_stream.h"
+
+namespace sht {
+
+// One interpolative decomposition inside a butterfly (Section 2.1, eq. 2.1;
+// Section 2.2 eqs. 1-6): the block's input vector z (length nin) is replaced
+// by y = z[skel] + T z[red] (length k).
+struct IdBlock {
+  int level = 0;      // 1 = leaf (a column block of full height), 2.. = merge levels
+  int band = 0;       // row band index at this level (2^{level-1} bands)
+  int group = 0;      // column group index at this level
+  int r0 = 0, r1 = 0; // rows of the band
+  int in_off = 0;     // offset of z: leaf -> first column; merge -> offset in the level-1 layout
+  int nin = 0;
+  int k = 0;
+  int out_off = 0;    // offset of y in this level's layout
+  std::vector<uint16_t> skel;  // k positions in z
+  std::vector<uint16_t> red;   // nin - k positions in z, ascending
+  std::vector<double> T;       // k x (nin - k), T[s * k + t]
+};
+
+// Stored skeleton columns of one row band of the top level: the
+// "unprocessed" blocks of Section 3 (their k columns of A are kept).
+struct FinalBlock {
+  int band = 0;
+  int r0 = 0, r1 = 0;
+  int k = 0;
+  int in_off = 0;              // offset of y in the top-level layout
+  std::vector<double> S;       // k x h weighted values, S[t * h + (i - r0)] = A[i][skel_t]
+};
+
+// Factorization of one parity block A^{m,p} (rows x n, weighted).
+struct UnitFact {
+  int m = 0, p = 0;
+  int n = 0;          // columns n_{m,p}
+  int rows = 0;       // rows kept after trimming (a prefix of the l positive nodes)
+  bool direct = false;
+  std::vector<double> D;     // direct: n x rows weighted values, D[j * rows + i]
+  int levels = 0;            // merge levels Lambda (leaf level excluded)
+  std::vector<int> width;    // width[j] = length of the level-j layout, j = 1..levels+1
+  std::vector<IdBlock> blocks;
+  std::vector<FinalBlock> finals;
+  long long values = 0;      // stored factor values
+  long long idx = 0;         // stored index entries
+  long long peak_words = 0;  // peak float64 words held during the depth-first build
+  double cost = 0;           // estimated apply cost (bytes), for LPT ordering
+};
+
+struct Stream {
+  std::vector<uint8_t> bytes;        // n_pages * page_bytes
+  std::vector<UnitEntry> units;      // LPT order
+  int max_buf_ab = 0;                // elements needed in BUF_A / BUF_B
+};
+
+struct PlanHost {
+  int l = 0;
+  double eps_id = 0, eps_fp32 = 0, trim_eps = 0;
+  int leaf_cols = 64, min_band_rows = 32, num_threads = 0, page_bytes = 16384;
+  // Gauss-Legendre nodes (all 2l, ascending), weights, and the angle of each
+  // positive node (theta_{l+i} in (0, pi/2)).
+  std::vector<double> x, w, theta_pos;
+  // factorizations: [m * 2 + p]; fp64 uses eps_id, fp32 uses eps_fp32
+  std::vector<UnitFact> fact64, fact32;
+  // streams: [prec][direction]; prec 0 = FP64, 1 = FP32, 2 = SPLIT32
+  Stream streams[3][2];
+  bool built[3] = {false, false, false};
+  double t_quad = 0, t_comp = 0;
+};
+
+// Section 2, eq. thetas: 2l Gauss-Legendre nodes/weights.
+void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& theta);
+
+// Columns of A^{m,p}_{ij} = sqrt(2 w_{l+i}) P-bar^m_{m+p+2j}(x_{l+i}), i < rows,
+// generated left to right with the x^2 recurrence of Section 2.3 (eqs.
+// c_rec, d_rec, recurrence0, recurrence) and explicit exponent tracking
+// (Section 4).
+class ColumnStream {
+ public:
+  ColumnStream(const PlanHost& P, int m, int p, int rows);
+  // writes column next_col() into col[0..rows)
+  void next(double* col);
+  int next_col() const { return j_; }
+ private:
+  int m_, p_, rows_, j_;
+  std::vector<double> x2_, sq2w_, a_, b_;  // a = P-bar_{k-2}, b = P-bar_k mantissas
+  std::vector<int> e_;
+};
+
+// Interpolative decomposition by column-pivoted Householder QR (Remark
+// QR_algorithm).  A is h x w column-major (destroyed).  Returns the rank k:
+// the smallest k with max remaining column norm <= eps.  perm[0..k) are
+// the skeleton columns, perm[k..w) the rest (ascending); T is k x (w-k)
+// with T[s * k + t], such that A[:, perm[k+s]] ~= sum_t T(t, s) A[:, perm[t]].
+int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm,
+                  std::vector<double>& T);
+
+// Builds the factorization of every parity block with threshold eps
+// (Section 3, depth-first).  fp32 selects fact32 instead of fact64.
+void build_factorizations(PlanHost& P, bool fp32);
+
+// Encodes one precision's factor streams (both directions) into pages.
+void emit_streams(PlanHost& P, int prec);
+
+}  // namespace sht

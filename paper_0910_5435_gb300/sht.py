@@ -1,0 +1,235 @@
+"""Thin ctypes binding of the C ABI in ``include/sht.h``.
+
+Names follow the C entry points.  This module only marshals arguments:
+every step of the transform runs in ``libsht.so`` (host precomputation,
+CUDA kernels).  Loading fails loudly if the library has not been built
+(``python -m paper_0910_5435_gb300.build``); there is no fallback.
+
+Device buffers are passed as torch CUDA tensors (PyTorch provides device
+memory and streams only) or as raw integer addresses.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libsht.so")
+
+SHT_FP64, SHT_FP32, SHT_SPLIT32 = 0, 1, 2
+PRECISIONS = {"fp64": SHT_FP64, "fp32": SHT_FP32, "split32": SHT_SPLIT32}
+
+STATUS = {
+    0: "SHT_OK", 1: "SHT_ERR_INVALID_ARG", 2: "SHT_ERR_OOM", 3: "SHT_ERR_CUDA",
+    4: "SHT_ERR_PLAN_CORRUPT", 5: "SHT_ERR_TIMEOUT", 6: "SHT_ERR_UNSUPPORTED", 7: "SHT_ERR_NO_DEVICE",
+}
+
+# Every symbol declared in include/sht.h.
+EXPORTS = [
+    "sht_status_string", "sht_plan_opts_default", "sht_plan_create", "sht_plan_create_ex",
+    "sht_plan_destroy", "sht_plan_get_stats", "sht_prepare", "sht_plan_nodes", "sht_plan_stream",
+    "sht_legendre_synthesize", "sht_legendre_analyze", "sht_legendre_synthesize_adjoint",
+    "sht_last_device_status", "sht_direct_prepare", "sht_direct_synthesize", "sht_direct_analyze",
+]
+
+
+class ShtError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class sht_plan_opts(ctypes.Structure):
+    _fields_ = [
+        ("leaf_cols", ctypes.c_int),
+        ("trim_eps", ctypes.c_double),
+        ("min_band_rows", ctypes.c_int),
+        ("host_only", ctypes.c_int),
+        ("num_threads", ctypes.c_int),
+        ("page_bytes", ctypes.c_int),
+        ("eps_fp32", ctypes.c_double),
+    ]
+
+
+class sht_plan_stats(ctypes.Structure):
+    _fields_ = [
+        ("l", ctypes.c_int),
+        ("eps_id", ctypes.c_double),
+        ("leaf_cols", ctypes.c_int),
+        ("n_units", ctypes.c_int),
+        ("n_blocks", ctypes.c_int),
+        ("k_max", ctypes.c_int),
+        ("k_avg", ctypes.c_double),
+        ("k_sigma", ctypes.c_double),
+        ("max_abs_T", ctypes.c_double),
+        ("max_levels", ctypes.c_int),
+        ("n_direct_units", ctypes.c_int),
+        ("rows_total", ctypes.c_longlong),
+        ("rows_kept", ctypes.c_longlong),
+        ("dense_values", ctypes.c_longlong),
+        ("factor_values", ctypes.c_longlong),
+        ("index_bytes", ctypes.c_longlong),
+        ("stream_bytes_fp64", ctypes.c_longlong),
+        ("stream_bytes_split32", ctypes.c_longlong),
+        ("stream_bytes_fp32", ctypes.c_longlong),
+        ("factor_values_fp32", ctypes.c_longlong),
+        ("t_quad", ctypes.c_double),
+        ("t_comp", ctypes.c_double),
+        ("t_upload", ctypes.c_double),
+        ("m_max_words", ctypes.c_longlong),
+        ("smem_bytes", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libsht.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_0910_5435_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, c_int, c_double = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.sht_status_string.restype = ctypes.c_char_p
+    L.sht_status_string.argtypes = [c_int]
+    L.sht_plan_opts_default.argtypes = [ctypes.POINTER(sht_plan_opts)]
+    L.sht_plan_create.argtypes = [c_int, c_double, ctypes.POINTER(vp)]
+    L.sht_plan_create_ex.argtypes = [c_int, c_double, ctypes.POINTER(sht_plan_opts), ctypes.POINTER(vp)]
+    L.sht_plan_destroy.argtypes = [vp]
+    L.sht_plan_get_stats.argtypes = [vp, ctypes.POINTER(sht_plan_stats)]
+    L.sht_prepare.argtypes = [vp, c_int]
+    L.sht_plan_nodes.argtypes = [vp, vp, vp]
+    L.sht_plan_stream.argtypes = [vp, c_int, c_int, vp, ctypes.POINTER(ctypes.c_size_t)]
+    for name in ["sht_legendre_synthesize", "sht_legendre_analyze", "sht_legendre_synthesize_adjoint"]:
+        getattr(L, name).argtypes = [vp, c_int, vp, vp, vp]
+    L.sht_last_device_status.argtypes = [vp, vp]
+    L.sht_direct_prepare.argtypes = [vp]
+    L.sht_direct_synthesize.argtypes = [vp, vp, vp, vp]
+    L.sht_direct_analyze.argtypes = [vp, vp, vp, vp]
+    for name in EXPORTS:
+        if name != "sht_status_string":
+            getattr(L, name).restype = c_int
+    _lib = L
+    return L
+
+
+def _check(code, where):
+    if code != 0:
+        raise ShtError(code, where)
+
+
+def _ptr(t):
+    """Device address of a torch tensor (or an int address)."""
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def triangle_size(l):
+    return (2 * l) * (2 * l + 1) // 2
+
+
+class Plan:
+    """Owns an ``sht_plan_t`` (``sht_plan_create_ex`` / ``sht_plan_destroy``)."""
+
+    def __init__(self, l, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, host_only=False,
+                 num_threads=0, page_bytes=0, eps_fp32=0.0):
+        L = lib()
+        opts = sht_plan_opts()
+        _check(L.sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
+        opts.leaf_cols = leaf_cols
+        opts.trim_eps = trim_eps
+        opts.min_band_rows = min_band_rows
+        opts.host_only = 1 if host_only else 0
+        opts.num_threads = num_threads
+        opts.page_bytes = page_bytes
+        opts.eps_fp32 = eps_fp32
+        h = ctypes.c_void_p()
+        _check(L.sht_plan_create_ex(int(l), float(eps_id), ctypes.byref(opts), ctypes.byref(h)),
+               "sht_plan_create_ex")
+        self.handle = h
+        self.l = int(l)
+        self.host_only = host_only
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sht_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self):
+        s = sht_plan_stats()
+        _check(lib().sht_plan_get_stats(self.handle, ctypes.byref(s)), "sht_plan_get_stats")
+        return s.as_dict()
+
+    def prepare(self, prec):
+        _check(lib().sht_prepare(self.handle, int(prec)), "sht_prepare")
+
+    def nodes(self):
+        x = np.zeros(2 * self.l)
+        w = np.zeros(2 * self.l)
+        _check(lib().sht_plan_nodes(self.handle, x.ctypes.data, w.ctypes.data), "sht_plan_nodes")
+        return x, w
+
+    def stream(self, prec, direction):
+        n = ctypes.c_size_t(0)
+        _check(lib().sht_plan_stream(self.handle, int(prec), int(direction), None, ctypes.byref(n)),
+               "sht_plan_stream")
+        buf = np.zeros(n.value, dtype=np.uint8)
+        _check(lib().sht_plan_stream(self.handle, int(prec), int(direction), buf.ctypes.data, ctypes.byref(n)),
+               "sht_plan_stream")
+        return buf
+
+
+def sht_legendre_synthesize(plan, prec, beta, G, stream=None):
+    _check(lib().sht_legendre_synthesize(plan.handle, int(prec), _ptr(beta), _ptr(G), _stream(stream)),
+           "sht_legendre_synthesize")
+
+
+def sht_legendre_analyze(plan, prec, G, beta, stream=None):
+    _check(lib().sht_legendre_analyze(plan.handle, int(prec), _ptr(G), _ptr(beta), _stream(stream)),
+           "sht_legendre_analyze")
+
+
+def sht_legendre_synthesize_adjoint(plan, prec, G, beta, stream=None):
+    _check(lib().sht_legendre_synthesize_adjoint(plan.handle, int(prec), _ptr(G), _ptr(beta), _stream(stream)),
+           "sht_legendre_synthesize_adjoint")
+
+
+def sht_last_device_status(plan, stream=None):
+    return lib().sht_last_device_status(plan.handle, _stream(stream))
+
+
+def sht_direct_prepare(plan):
+    _check(lib().sht_direct_prepare(plan.handle), "sht_direct_prepare")
+
+
+def sht_direct_synthesize(plan, beta, G, stream=None):
+    _check(lib().sht_direct_synthesize(plan.handle, _ptr(beta), _ptr(G), _stream(stream)),
+           "sht_direct_synthesize")
+
+
+def sht_direct_analyze(plan, G, beta, stream=None):
+    _check(lib().sht_direct_analyze(plan.handle, _ptr(G), _ptr(beta), _stream(stream)), "sht_direct_analyze")

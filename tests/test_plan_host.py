@@ -1,0 +1,122 @@
+"""Host-side checks of the product's precomputation (no GPU): the library is
+driven through its C ABI with host-only plans, and its factor streams are
+decoded and applied by tests/stream_emulator.py, then compared with the oracle.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0910_5435_gb300 import inputs, sht
+from tests.stream_emulator import emulate, iter_ops
+
+PB = 16384
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("l", [1, 2, 8, 64, 300])
+def test_nodes_match_oracle(l):
+    """The product's Gauss-Legendre nodes (Section 2, eq. thetas), computed by
+    its own code, agree with the oracle's to a few ulp (weights: the n-scaled
+    roundoff of the degree recurrence near the poles)."""
+    P = sht.Plan(l, 1e-12, host_only=True)
+    x, w = P.nodes()
+    xo, wo = oracle.gl_nodes_weights(2 * l)
+    assert np.max(np.abs(x - xo)) < 4e-16
+    assert np.max(np.abs(w / wo - 1)) < 4e-15 * 2 * l
+
+
+@pytest.mark.parametrize("l,C", [(1, 4), (4, 2), (16, 4), (64, 16), (64, 64), (128, 16)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (2, 1e-10), (1, 2e-5)])
+def test_streams_reproduce_oracle(l, C, prec, tol):
+    """Synthesis, analysis and the adjoint, applied from the decoded factor
+    streams, match the direct oracle transform (Section 2) within the stated
+    tolerance of each precision (rel. l2; float64 factors at eps_id = 1e-12)."""
+    P = sht.Plan(l, 1e-12, leaf_cols=C, host_only=True)
+    beta = inputs.random_beta(l, seed=l + C)
+    Go = oracle.legendre_synthesis(beta, l)
+    G = emulate(P.stream(prec, 0), PB, l, prec, 0, beta)
+    assert rel(G, Go) < tol
+    Gin = inputs.random_G(l, seed=7)
+    bo = oracle.legendre_analysis(Gin, l)
+    b = emulate(P.stream(prec, 1), PB, l, prec, 1, Gin)
+    assert rel(b, bo) < tol
+    _, w = P.nodes()
+    ba = emulate(P.stream(prec, 1), PB, l, prec, 1, Gin, prescale=1.0 / w[l:])
+    assert rel(ba, oracle.legendre_adjoint(Gin, l)) < tol
+
+
+def test_butterfly_levels_are_exercised():
+    """l = 128 with C = 16 must build multi-level butterflies (Section 2.2,
+    Figure multi) and compress the operator."""
+    P = sht.Plan(128, 1e-12, leaf_cols=16, host_only=True)
+    s = P.stats()
+    assert s["max_levels"] >= 3
+    assert s["n_blocks"] > 100
+    assert s["factor_values"] < s["dense_values"]
+    assert 0 < s["k_avg"] <= s["k_max"] <= 128
+    kinds = {int(h["kind"]) for h, _, _ in iter_ops(P.stream(0, 0), PB)}
+    assert {1, 3, 6, 7} <= kinds  # gather, unfold, interpolation, dense final blocks
+
+
+def test_rank_property_grows_with_eps():
+    """Remark adaptivity: looser eps gives smaller adaptive ranks."""
+    a = sht.Plan(128, 1e-12, leaf_cols=16, host_only=True).stats()
+    b = sht.Plan(128, 1e-6, leaf_cols=16, host_only=True).stats()
+    assert b["k_avg"] < a["k_avg"]
+    assert b["factor_values"] < a["factor_values"]
+
+
+def test_trimming_bounds_dropped_rows():
+    """With trimming, dropped rows (a suffix near the poles) have total
+    Frobenius norm <= trim_eps, so the transform error stays ~eps."""
+    l = 64
+    P = sht.Plan(l, 1e-12, leaf_cols=16, trim_eps=1e-8, host_only=True)
+    s = P.stats()
+    assert s["rows_kept"] < s["rows_total"]
+    beta = inputs.random_beta(l, seed=3)
+    G = emulate(P.stream(0, 0), PB, l, 0, 0, beta)
+    assert rel(G, oracle.legendre_synthesis(beta, l)) < 1e-7
+
+
+@pytest.mark.parametrize("args", [(0, 1e-12), (1025, 1e-12), (8, 0.0), (8, 1.0), (8, -1e-3), (8, float("nan"))])
+def test_invalid_arguments_are_rejected(args):
+    with pytest.raises(sht.ShtError) as e:
+        sht.Plan(*args, host_only=True)
+    assert e.value.code == 1
+
+
+def test_invalid_options_are_rejected():
+    for kw in [dict(leaf_cols=1), dict(page_bytes=1000), dict(page_bytes=65536), dict(num_threads=-1)]:
+        with pytest.raises(sht.ShtError):
+            sht.Plan(8, 1e-12, host_only=True, **kw)
+
+
+def test_host_only_plan_refuses_compute():
+    P = sht.Plan(8, 1e-12, host_only=True)
+    with pytest.raises(sht.ShtError) as e:
+        sht.sht_legendre_synthesize(P, 0, 16, 16, stream=0)
+    assert e.value.code == 6
+
+
+def test_stats_follow_paper_columns():
+    """Plan statistics mirror the paper's table columns (Section 5: k_max,
+    k_avg, k_sigma, t_quad, t_comp, m_max)."""
+    s = sht.Plan(64, 1e-12, leaf_cols=16, host_only=True).stats()
+    assert s["l"] == 64 and s["n_units"] == 128
+    assert s["t_quad"] >= 0 and s["t_comp"] > 0
+    assert s["m_max_words"] > 0
+    assert s["k_sigma"] >= 0
+    assert s["max_abs_T"] < 1e3
+    assert math.isfinite(s["k_avg"])
