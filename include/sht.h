@@ -201,6 +201,43 @@ sht_status sht_legendre_synthesize_adjoint(sht_plan_t plan, sht_precision prec,
  * word. */
 sht_status sht_last_device_status(sht_plan_t plan, sht_stream_t stream);
 
+/* ---------------------------------------------- phi stage and full SHT */
+
+/* Bytes of the caller-provided workspace of the entry points below for this
+ * precision: one [2l][2l] complex array (16 bytes per entry, 8 for
+ * SHT_FP32). */
+size_t sht_workspace_bytes(sht_plan_t plan, sht_precision prec);
+
+/* Sums over m of Section 2, eq. alternate_expansion, for a real field:
+ * values[i][j] = sum_{m=-(2l-1)}^{2l-1} G^m(x_i) e^{i m phi_j}, G^{-m} = conj(G^m),
+ * phi_j = 2 pi (j + 1/2)/(4l - 1) (eq. phis).  Computed as the half-sample
+ * phase e^{i pi m/(4l-1)} applied to G (into the workspace) followed by one
+ * complex-to-real FFT of length 4l-1 per node (cuFFT; Section 2 notes that
+ * FFTs evaluate the sums over m).  G: device [2l][2l] complex (read only);
+ * values: device [2l][4l-1] real.  The imaginary part of G^0 is ignored. */
+sht_status sht_phi_synthesize(sht_plan_t plan, sht_precision prec, const void* G, void* values,
+                              void* workspace, sht_stream_t stream);
+
+/* Inverse of sht_phi_synthesize on band-limited data:
+ * G^m(x_i) = (1/(4l-1)) sum_j values[i][j] e^{-i m phi_j}, m = 0..2l-1 (a
+ * real-to-complex FFT per node, then the conjugate phase and 1/(4l-1)).
+ * values: device [2l][4l-1] real (read only); G: device [2l][2l] complex. */
+sht_status sht_phi_analyze(sht_plan_t plan, sht_precision prec, const void* values, void* G,
+                           sht_stream_t stream);
+
+/* Full synthesis, coefficients -> grid (Section 2, eq. expansion on the
+ * tensor-product grid): the butterfly Legendre stage with the phase of eq.
+ * phis fused into its unfold, writing the workspace, then the FFTs of
+ * sht_phi_synthesize.  beta: device triangle; values: device [2l][4l-1]. */
+sht_status sht_synthesize(sht_plan_t plan, sht_precision prec, const void* beta, void* values,
+                          void* workspace, sht_stream_t stream);
+
+/* Full analysis, grid -> coefficients: the FFTs of sht_phi_analyze into the
+ * workspace, then the transposed butterfly with the conjugate phase and
+ * 1/(4l-1) fused into its fold.  values: device [2l][4l-1]; beta: triangle. */
+sht_status sht_analyze(sht_plan_t plan, sht_precision prec, const void* values, void* beta,
+                       void* workspace, sht_stream_t stream);
+
 /* ------------------------------------- direct float64 baseline (K3-style) */
 
 /* Stores the dense operator P-bar^m_{m+p+2j}(x_{l+i}) (float64, kept rows

@@ -28,7 +28,7 @@ CXXFLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-func
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
 
 CPP_SOURCES = ["plan_build.cpp"]
-CU_SOURCES = ["capi.cu", "sweep.cu", "direct.cu"]
+CU_SOURCES = ["capi.cu", "sweep.cu", "direct.cu", "phi.cu"]
 HEADERS = ["sht_stream.h", "plan_host.h", "kernels.h"]
 
 
@@ -80,7 +80,7 @@ def build(force=False, verbose=False, extra_nvflags=()):
     objs = [os.path.join(BUILD, n + ".o") for n in CPP_SOURCES + CU_SOURCES]
     tmp = LIB + ".tmp"
     _run([NVCC, "-shared", "-o", tmp] + objs + ARCH + [
-        "-cudart", "shared", "-lpthread",
+        "-cudart", "shared", "-lcufft", "-lpthread",
         "-Xlinker", "-rpath," + os.path.join(CUDA_HOME, "lib64")])
     os.replace(tmp, LIB)
     with open(stamp_file, "w") as f:

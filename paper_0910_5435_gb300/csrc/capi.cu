@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of include/sht.h: plan lifecycle, device upload and
 // launches.  All arguments are validated on the host before any launch.
 #include <cuda_runtime.h>
+#include <cufft.h>
 
 #include <algorithm>
 #include <chrono>
@@ -22,7 +23,6 @@ using sht::UnitFact;
 namespace {
 
 constexpr int kNumPrec = 3;
-constexpr int kMaxStages = 16;
 
 // Launch kinds that own a work-queue counter: synthesis, analysis, adjoint.
 enum { KIND_SYN = 0, KIND_ANA = 1, KIND_ADJ = 2, KIND_COUNT = 3 };
@@ -57,11 +57,17 @@ struct sht_plan_s {
   bool host_only = false;
   int device = -1;
   int num_sms = 0;
-  int nstages = 4;
+  int nstages[kNumPrec] = {4, 4, 4};
+  int ctas_per_sm[kNumPrec] = {1, 1, 1};
   DevStream dev[kNumPrec][2];
   bool dev_ready[kNumPrec] = {false, false, false};
   size_t smem[kNumPrec] = {0, 0, 0};
   double* d_inv_w = nullptr;   // 1 / w_{l+i}: the adjoint's fold prescale
+  double2* d_tw_syn = nullptr; // e^{i pi m / N}, N = 4l - 1 (phi stage, eq. phis)
+  double2* d_tw_ana = nullptr; // e^{-i pi m / N} / N
+  cufftHandle fft_c2r[2] = {0, 0};  // [0] float64 (Z2D), [1] float32 (C2R)
+  cufftHandle fft_r2c[2] = {0, 0};
+  bool fft_ready[2] = {false, false};
   double* d_w_pos = nullptr;   // w_{l+i}
   unsigned* d_scratch = nullptr;  // [kNumPrec * KIND_COUNT] queue counters, then the status word
   // direct baseline
@@ -99,6 +105,15 @@ void free_dev(sht_plan_t P) {
     }
   cudaFree(P->d_inv_w);
   cudaFree(P->d_w_pos);
+  cudaFree(P->d_tw_syn);
+  cudaFree(P->d_tw_ana);
+  P->d_tw_syn = P->d_tw_ana = nullptr;
+  for (int f = 0; f < 2; ++f)
+    if (P->fft_ready[f]) {
+      cufftDestroy(P->fft_c2r[f]);
+      cufftDestroy(P->fft_r2c[f]);
+      P->fft_ready[f] = false;
+    }
   cudaFree(P->d_scratch);
   cudaFree(P->d_dense);
   cudaFree(P->d_dense_off);
@@ -201,25 +216,29 @@ sht_status upload(sht_plan_t P, int q) {
     CK(cudaMemcpy(D.pages, S.bytes.data(), D.bytes, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(D.units, S.units.data(), sizeof(sht::UnitEntry) * S.units.size(), cudaMemcpyHostToDevice));
   }
-  size_t smem = sht::sweep_smem_bytes(q, P->H.page_bytes, P->nstages, buf_ab, P->H.l);
+  int& nst = P->nstages[q];
+  size_t smem = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, P->H.l);
   int optin = 0;
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
   // fewer stages if the vectors of a large l leave too little room
-  while (smem > (size_t)optin && P->nstages > 2) {
-    --P->nstages;
-    smem = sht::sweep_smem_bytes(q, P->H.page_bytes, P->nstages, buf_ab, P->H.l);
+  while (smem > (size_t)optin && nst > 2) {
+    --nst;
+    smem = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, P->H.l);
   }
   if (smem > (size_t)optin) return SHT_ERR_UNSUPPORTED;
   P->dev[q][0].buf_ab = P->dev[q][1].buf_ab = buf_ab;
   P->smem[q] = smem;
   CK(sht::sweep_configure(q, smem));
+  P->ctas_per_sm[q] = sht::sweep_blocks_per_sm(q, smem);
   P->dev_ready[q] = true;
-  P->H.t_quad += 0;  // (nodes are timed at creation)
   P->stats.t_upload += now_s() - t0;
   return SHT_OK;
 }
 
+// Makes precision q ready; cheap once it is (the launch path calls it every
+// time), statistics are refreshed only when something was built.
 sht_status ensure_prec(sht_plan_t P, int q) {
+  if (P->H.built[q] && (P->host_only || P->dev_ready[q])) return SHT_OK;
   std::lock_guard<std::mutex> g(P->mu);
   sht_status s = build_host(P, q);
   if (s != SHT_OK) return s;
@@ -234,7 +253,7 @@ sht_status ensure_prec(sht_plan_t P, int q) {
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, const void* in, void* out,
-                        const double* prescale, sht_stream_t stream) {
+                        const double* prescale, sht_stream_t stream, const double2* twiddle = nullptr) {
   if (!P || !in || !out) return SHT_ERR_INVALID_ARG;
   const int q = prec_index(prec);
   if (q < 0) return SHT_ERR_INVALID_ARG;
@@ -250,16 +269,17 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.units = D.units;
   a.n_units = D.n_units;
   a.page_bytes = P->H.page_bytes;
-  a.nstages = P->nstages;
+  a.nstages = P->nstages[q];
   a.l = P->H.l;
   a.buf_ab = D.buf_ab;
   a.quit_page = D.quit_page;
   a.in = in;
   a.out = out;
   a.prescale = prescale;
+  a.twiddle = twiddle;
   a.counter = P->d_scratch + (q * KIND_COUNT + kind);
   a.status = P->d_scratch + kNumPrec * KIND_COUNT;
-  const int grid = std::max(1, std::min(P->num_sms, D.n_units));
+  const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
   CK(sht::sweep_launch(q, a, grid, P->smem[q], reinterpret_cast<cudaStream_t>(stream)));
   return SHT_OK;
 }
@@ -369,6 +389,20 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
     if (e == cudaSuccess) e = cudaMemcpy(P->d_inv_w, invw.data(), sizeof(double) * l, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->d_w_pos, wpos.data(), sizeof(double) * l, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(P->d_scratch, 0, sizeof(unsigned) * (kNumPrec * KIND_COUNT + 1));
+    if (e == cudaSuccess) {
+      const int L = 2 * l, N = 4 * l - 1;
+      std::vector<double2> ts(L), ta(L);
+      for (int m = 0; m < L; ++m) {
+        // pi m / N < pi / 2 for m < 2l: no range reduction issue
+        const double a = M_PI * (double)m / (double)N;
+        ts[m] = make_double2(std::cos(a), std::sin(a));
+        ta[m] = make_double2(std::cos(a) / N, -std::sin(a) / N);
+      }
+      e = cudaMalloc(&P->d_tw_syn, sizeof(double2) * L);
+      if (e == cudaSuccess) e = cudaMalloc(&P->d_tw_ana, sizeof(double2) * L);
+      if (e == cudaSuccess) e = cudaMemcpy(P->d_tw_syn, ts.data(), sizeof(double2) * L, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(P->d_tw_ana, ta.data(), sizeof(double2) * L, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
       free_dev(P);
       delete P;
@@ -397,7 +431,6 @@ sht_status sht_plan_destroy(sht_plan_t P) {
 sht_status sht_plan_get_stats(sht_plan_t P, sht_plan_stats* out) {
   if (!P || !out) return SHT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(P->mu);
-  fill_stats(P);
   *out = P->stats;
   return SHT_OK;
 }
@@ -466,6 +499,114 @@ sht_status sht_last_device_status(sht_plan_t P, sht_stream_t stream) {
     return (sht_status)st;
   }
   return SHT_OK;
+}
+
+static sht_status ensure_fft(sht_plan_t P, int f) {
+  std::lock_guard<std::mutex> g(P->mu);
+  if (P->fft_ready[f]) return SHT_OK;
+  const int l = P->H.l, L = 2 * l;
+  int n = 4 * l - 1;
+  int cembed = L, rembed = n;
+  // complex side: element (node i, order m) at i + m * 2l, i.e. the [2l][2l] G layout;
+  // real side: values[i][j] at i * N + j
+  cufftResult r = cufftPlanMany(&P->fft_c2r[f], 1, &n, &cembed, L, 1, &rembed, 1, n, f ? CUFFT_C2R : CUFFT_Z2D, L);
+  if (r != CUFFT_SUCCESS) return r == CUFFT_ALLOC_FAILED ? SHT_ERR_OOM : SHT_ERR_CUDA;
+  r = cufftPlanMany(&P->fft_r2c[f], 1, &n, &rembed, 1, n, &cembed, L, 1, f ? CUFFT_R2C : CUFFT_D2Z, L);
+  if (r != CUFFT_SUCCESS) {
+    cufftDestroy(P->fft_c2r[f]);
+    return r == CUFFT_ALLOC_FAILED ? SHT_ERR_OOM : SHT_ERR_CUDA;
+  }
+  P->fft_ready[f] = true;
+  return SHT_OK;
+}
+
+static sht_status fft_c2r(sht_plan_t P, int q, void* H, void* values, sht_stream_t stream) {
+  const int f = (q == sht::PREC_FP32) ? 1 : 0;
+  sht_status s = ensure_fft(P, f);
+  if (s != SHT_OK) return s;
+  cufftHandle h = P->fft_c2r[f];
+  if (cufftSetStream(h, reinterpret_cast<cudaStream_t>(stream)) != CUFFT_SUCCESS) return SHT_ERR_CUDA;
+  const cufftResult r = f ? cufftExecC2R(h, reinterpret_cast<cufftComplex*>(H), reinterpret_cast<cufftReal*>(values))
+                          : cufftExecZ2D(h, reinterpret_cast<cufftDoubleComplex*>(H),
+                                         reinterpret_cast<cufftDoubleReal*>(values));
+  return r == CUFFT_SUCCESS ? SHT_OK : SHT_ERR_CUDA;
+}
+
+static sht_status fft_r2c(sht_plan_t P, int q, const void* values, void* H, sht_stream_t stream) {
+  const int f = (q == sht::PREC_FP32) ? 1 : 0;
+  sht_status s = ensure_fft(P, f);
+  if (s != SHT_OK) return s;
+  cufftHandle h = P->fft_r2c[f];
+  if (cufftSetStream(h, reinterpret_cast<cudaStream_t>(stream)) != CUFFT_SUCCESS) return SHT_ERR_CUDA;
+  // cuFFT does not modify the input of an out-of-place real-to-complex transform
+  const cufftResult r =
+      f ? cufftExecR2C(h, reinterpret_cast<cufftReal*>(const_cast<void*>(values)), reinterpret_cast<cufftComplex*>(H))
+        : cufftExecD2Z(h, reinterpret_cast<cufftDoubleReal*>(const_cast<void*>(values)),
+                       reinterpret_cast<cufftDoubleComplex*>(H));
+  return r == CUFFT_SUCCESS ? SHT_OK : SHT_ERR_CUDA;
+}
+
+static sht_status phi_args_ok(sht_plan_t P, sht_precision prec, const void* a, const void* b, int& q) {
+  if (!P || !a || !b) return SHT_ERR_INVALID_ARG;
+  q = prec_index(prec);
+  if (q < 0) return SHT_ERR_INVALID_ARG;
+  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  const size_t al = (q == sht::PREC_FP32) ? 8 : 16;
+  if (!aligned(a, al) || !aligned(b, al)) return SHT_ERR_INVALID_ARG;
+  if (cudaSetDevice(P->device) != cudaSuccess) return SHT_ERR_CUDA;
+  return SHT_OK;
+}
+
+size_t sht_workspace_bytes(sht_plan_t P, sht_precision prec) {
+  if (!P) return 0;
+  const size_t L = 2 * (size_t)P->H.l;
+  return L * L * (prec == SHT_FP32 ? 8 : 16);
+}
+
+sht_status sht_phi_synthesize(sht_plan_t P, sht_precision prec, const void* G, void* values, void* workspace,
+                              sht_stream_t stream) {
+  int q;
+  sht_status s = phi_args_ok(P, prec, G, values, q);
+  if (s != SHT_OK) return s;
+  if (!workspace || !aligned(workspace, 16)) return SHT_ERR_INVALID_ARG;
+  CK(sht::phase_launch(q == sht::PREC_FP32, G, workspace, P->d_tw_syn, P->H.l, P->num_sms,
+                       reinterpret_cast<cudaStream_t>(stream)));
+  return fft_c2r(P, q, workspace, values, stream);
+}
+
+sht_status sht_phi_analyze(sht_plan_t P, sht_precision prec, const void* values, void* G, sht_stream_t stream) {
+  int q;
+  sht_status s = phi_args_ok(P, prec, values, G, q);
+  if (s != SHT_OK) return s;
+  s = fft_r2c(P, q, values, G, stream);
+  if (s != SHT_OK) return s;
+  CK(sht::phase_launch(q == sht::PREC_FP32, G, G, P->d_tw_ana, P->H.l, P->num_sms,
+                       reinterpret_cast<cudaStream_t>(stream)));
+  return SHT_OK;
+}
+
+sht_status sht_synthesize(sht_plan_t P, sht_precision prec, const void* beta, void* values, void* workspace,
+                          sht_stream_t stream) {
+  int q;
+  sht_status s = phi_args_ok(P, prec, beta, values, q);
+  if (s != SHT_OK) return s;
+  if (!workspace || !aligned(workspace, 16)) return SHT_ERR_INVALID_ARG;
+  s = ensure_fft(P, q == sht::PREC_FP32 ? 1 : 0);
+  if (s != SHT_OK) return s;
+  s = launch_sweep(P, prec, 0, KIND_SYN, beta, workspace, nullptr, stream, P->d_tw_syn);
+  if (s != SHT_OK) return s;
+  return fft_c2r(P, q, workspace, values, stream);
+}
+
+sht_status sht_analyze(sht_plan_t P, sht_precision prec, const void* values, void* beta, void* workspace,
+                       sht_stream_t stream) {
+  int q;
+  sht_status s = phi_args_ok(P, prec, values, beta, q);
+  if (s != SHT_OK) return s;
+  if (!workspace || !aligned(workspace, 16)) return SHT_ERR_INVALID_ARG;
+  s = fft_r2c(P, q, values, workspace, stream);
+  if (s != SHT_OK) return s;
+  return launch_sweep(P, prec, 1, KIND_ANA, workspace, beta, nullptr, stream, P->d_tw_ana);
 }
 
 sht_status sht_direct_prepare(sht_plan_t P) {

@@ -22,6 +22,7 @@ struct SweepArgs {
   const void* in;              // synthesis: beta; analysis: G
   void* out;                   // synthesis: G; analysis: beta
   const double* prescale;      // FOLD: per positive node scale (l entries) or nullptr
+  const double2* twiddle;      // per order m: UNFOLD multiplies its outputs, FOLD its inputs (or nullptr)
   unsigned* counter;           // work-queue counter (self-resetting; 0 between launches)
   unsigned* status;            // device status word (0 = ok)
 };
@@ -30,6 +31,8 @@ enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2 };
 
 size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int l);
 cudaError_t sweep_configure(int prec, size_t smem);
+// resident CTAs per SM for this shared-memory size (>= 1)
+int sweep_blocks_per_sm(int prec, size_t smem);
 cudaError_t sweep_launch(int prec, const SweepArgs& a, int grid, size_t smem, cudaStream_t st);
 
 // Direct float64 baseline: dense P-bar blocks, [j][i] per (m, p), i fastest.
@@ -44,6 +47,9 @@ struct DirectArgs {
   void* out;
 };
 cudaError_t direct_synth_launch(const DirectArgs& a, cudaStream_t st);
+// dst[m][i] = src[m][i] * tw[m] on a [2l][2l] complex array (src == dst allowed)
+cudaError_t phase_launch(bool fp32, const void* src, void* dst, const double2* tw, int l, int num_sms,
+                         cudaStream_t st);
 cudaError_t direct_analysis_launch(const DirectArgs& a, cudaStream_t st);
 
 }  // namespace sht

@@ -611,15 +611,29 @@ struct Emitter {
     }
     return lo;
   }
+  // Size of the next piece of an op with `remaining` outputs: pieces are
+  // balanced (a block that needs two pages is cut in halves, not into a
+  // full page plus a sliver), and a partly used page is filled with a smaller
+  // piece only if that piece still has >= 16 outputs.
   template <class F>
   int piece(int remaining, F bytes_for) {
-    const int want = std::min(remaining, 16);
-    int mp = fit(remaining, bytes_for);
-    if (mp < want) {
-      W.new_page();
-      mp = fit(remaining, bytes_for);
+    int mfresh = 0;
+    {
+      int lo = 0, hi = std::min(remaining, kMaxM);
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (bytes_for(mid) <= W.PB) lo = mid; else hi = mid - 1;
+      }
+      mfresh = lo;
     }
-    if (mp <= 0) throw std::logic_error("op does not fit in a page");
+    if (mfresh <= 0) throw std::logic_error("op does not fit in a page");
+    const int npieces = (remaining + mfresh - 1) / mfresh;
+    const int target = (remaining + npieces - 1) / npieces;
+    int mp = fit(target, bytes_for);
+    if (mp < target && mp < 16) {
+      W.new_page();
+      mp = target;
+    }
     return mp;
   }
   void write(OpHdr h, const std::vector<uint16_t>& idx, size_t nval, const std::vector<double>& vals) {
@@ -736,11 +750,11 @@ struct Emitter {
 
 inline uint8_t level_buf(int j) { return (j & 1) ? BUF_B : BUF_A; }
 
-void emit_unit(PlanHost& P, int prec, int dir, int m, std::vector<uint8_t>& out) {
+// Appends the ops of order m to the page writer (continuing its open page).
+void emit_unit(PlanHost& P, int prec, int dir, int m, PageWriter& W) {
   const int l = P.l;
   const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
-  PageWriter W(out, (size_t)P.page_bytes);
-  W.new_page();
+  if (!W.open) W.new_page();
   Emitter E(W, prec);
   std::vector<double> inv_sq2w(l), sqw2(l);
   for (int i = 0; i < l; ++i) {
@@ -857,45 +871,88 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, std::vector<uint8_t>& out)
 void emit_streams(PlanHost& P, int prec) {
   const int L = 2 * P.l;
   const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
+  const size_t PB = (size_t)P.page_bytes;
+  // Orders whose ops fill fewer than kPackPages pages share pages with other
+  // small orders inside one work item, so the persistent kernel neither
+  // streams padding nor pays a queue pop per tiny order.
+  constexpr size_t kPackPages = 4;
   for (int dir = 0; dir < 2; ++dir) {
     std::vector<std::vector<uint8_t>> per(L);
-    std::atomic<int> next(0);
     int nt = P.num_threads > 0 ? P.num_threads : (int)std::thread::hardware_concurrency();
     nt = std::max(1, std::min(nt, 256));
-    std::vector<std::string> errors(nt);
-    auto worker = [&](int tid) {
-      try {
-        for (;;) {
-          const int m = next.fetch_add(1);
-          if (m >= L) break;
-          emit_unit(P, prec, dir, m, per[m]);
+    auto run_parallel = [&](int count, auto&& body) {
+      std::atomic<int> next(0);
+      std::vector<std::string> errors(nt);
+      auto worker = [&](int tid) {
+        try {
+          for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= count) break;
+            body(i);
+          }
+        } catch (const std::exception& e) {
+          errors[tid] = e.what();
+          next.store(count);
         }
-      } catch (const std::exception& e) {
-        errors[tid] = e.what();
-        next.store(L);
-      }
+      };
+      std::vector<std::thread> th;
+      for (int t = 1; t < nt; ++t) th.emplace_back(worker, t);
+      worker(0);
+      for (auto& t : th) t.join();
+      for (auto& e : errors)
+        if (!e.empty()) throw std::runtime_error(e);
     };
-    std::vector<std::thread> th;
-    for (int t = 1; t < nt; ++t) th.emplace_back(worker, t);
-    worker(0);
-    for (auto& t : th) t.join();
-    for (auto& e : errors)
-      if (!e.empty()) throw std::runtime_error(e);
+    run_parallel(L, [&](int m) {
+      PageWriter W(per[m], PB);
+      emit_unit(P, prec, dir, m, W);
+    });
+    // work items: big orders alone, small orders packed greedily (largest first)
+    std::vector<int> order(L);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
+    std::vector<std::vector<int>> items;
+    std::vector<int> cur;
+    size_t cur_pages = 0;
+    for (int m : order) {
+      const size_t pg = per[m].size() / PB;
+      if (pg >= kPackPages) {
+        items.push_back({m});
+        continue;
+      }
+      cur.push_back(m);
+      cur_pages += pg;
+      if (cur_pages >= kPackPages) {
+        items.push_back(cur);
+        cur.clear();
+        cur_pages = 0;
+      }
+    }
+    if (!cur.empty()) items.push_back(cur);
+    std::vector<std::vector<uint8_t>> item_bytes(items.size());
+    run_parallel((int)items.size(), [&](int it) {
+      if (items[it].size() == 1) {
+        item_bytes[it].swap(per[items[it][0]]);
+        return;
+      }
+      PageWriter W(item_bytes[it], PB);
+      for (int m : items[it]) emit_unit(P, prec, dir, m, W);
+    });
+    std::vector<int> iorder(items.size());
+    std::iota(iorder.begin(), iorder.end(), 0);
+    std::stable_sort(iorder.begin(), iorder.end(),
+                     [&](int a, int b) { return item_bytes[a].size() > item_bytes[b].size(); });
 
     Stream& S = P.streams[prec][dir];
     S.bytes.clear();
     S.units.clear();
-    std::vector<int> order(L);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
     size_t pages = 0;
-    for (int m : order) {
+    for (int it : iorder) {
       UnitEntry e;
       e.first_page = pages;
-      e.n_pages = (uint32_t)(per[m].size() / P.page_bytes);
-      e.m = (uint32_t)m;
+      e.n_pages = (uint32_t)(item_bytes[it].size() / PB);
+      e.m = (uint32_t)items[it][0];
       S.units.push_back(e);
-      S.bytes.insert(S.bytes.end(), per[m].begin(), per[m].end());
+      S.bytes.insert(S.bytes.end(), item_bytes[it].begin(), item_bytes[it].end());
       pages += e.n_pages;
     }
     // trailing QUIT page: a single op of kind 0xFF ends the consumer loop

@@ -119,6 +119,9 @@ struct TF64 {
   __device__ static IO io_add(const IO& a, const IO& b) { return make_double2(a.x + b.x, a.y + b.y); }
   __device__ static IO io_sub(const IO& a, const IO& b) { return make_double2(a.x - b.x, a.y - b.y); }
   __device__ static IO io_scale(const IO& a, double s) { return make_double2(a.x * s, a.y * s); }
+  __device__ static IO io_cmul(const IO& a, const double2& t) {
+    return make_double2(a.x * t.x - a.y * t.y, a.x * t.y + a.y * t.x);
+  }
 };
 
 // hi/lo float32 factors, double-float ("compensated") float32 arithmetic;
@@ -184,6 +187,9 @@ struct TS32 {
   __device__ static IO io_add(const IO& a, const IO& b) { return make_double2(a.x + b.x, a.y + b.y); }
   __device__ static IO io_sub(const IO& a, const IO& b) { return make_double2(a.x - b.x, a.y - b.y); }
   __device__ static IO io_scale(const IO& a, double s) { return make_double2(a.x * s, a.y * s); }
+  __device__ static IO io_cmul(const IO& a, const double2& t) {
+    return make_double2(a.x * t.x - a.y * t.y, a.x * t.y + a.y * t.x);
+  }
 };
 
 // float32 factors and arithmetic; complex64 I/O.
@@ -217,6 +223,10 @@ struct TF32 {
   __device__ static IO io_sub(const IO& a, const IO& b) { return make_float2(a.x - b.x, a.y - b.y); }
   __device__ static IO io_scale(const IO& a, double s) {
     return make_float2((float)(a.x * s), (float)(a.y * s));
+  }
+  __device__ static IO io_cmul(const IO& a, const double2& t) {
+    const float tr = (float)t.x, ti = (float)t.y;
+    return make_float2(a.x * tr - a.y * ti, a.x * ti + a.y * tr);
   }
 };
 
@@ -324,11 +334,17 @@ __device__ __forceinline__ void run_control(const OpHdr& h, const SweepArgs& A, 
       IO* G = reinterpret_cast<IO*>(A.out) + (size_t)m * L;
       const C* E = S.buf(BUF_E);
       const C* O = S.buf(BUF_O);
+      const double2 tw = A.twiddle ? A.twiddle[m] : make_double2(1.0, 0.0);
       for (int i = ct; i < l; i += kConsumerThreads) {
         const IO e = i < h.M ? TR::to_io(E[i]) : TR::io_zero();
         const IO o = i < h.K ? TR::to_io(O[i]) : TR::io_zero();
-        G[l + i] = TR::io_add(e, o);
-        G[l - 1 - i] = TR::io_sub(e, o);
+        IO gp = TR::io_add(e, o), gm = TR::io_sub(e, o);
+        if (A.twiddle) {
+          gp = TR::io_cmul(gp, tw);
+          gm = TR::io_cmul(gm, tw);
+        }
+        G[l + i] = gp;
+        G[l - 1 - i] = gm;
       }
       break;
     }
@@ -336,8 +352,13 @@ __device__ __forceinline__ void run_control(const OpHdr& h, const SweepArgs& A, 
       const IO* G = reinterpret_cast<const IO*>(A.in) + (size_t)m * L;
       C* E = S.buf(BUF_E);
       C* O = S.buf(BUF_O);
+      const double2 tw = A.twiddle ? A.twiddle[m] : make_double2(1.0, 0.0);
       for (int i = ct; i < l; i += kConsumerThreads) {
-        const IO gp = G[l + i], gm = G[l - 1 - i];
+        IO gp = G[l + i], gm = G[l - 1 - i];
+        if (A.twiddle) {
+          gp = TR::io_cmul(gp, tw);
+          gm = TR::io_cmul(gm, tw);
+        }
         IO e = TR::io_add(gp, gm), o = TR::io_sub(gp, gm);
         if (A.prescale) {
           e = TR::io_scale(e, A.prescale[i]);
@@ -406,7 +427,7 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
 }
 
 template <class TR>
-__global__ void __launch_bounds__(kConsumerThreads + 32, 1) bfly_sweep_kernel(const SweepArgs A) {
+__global__ void __launch_bounds__(kConsumerThreads + 32) bfly_sweep_kernel(const SweepArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int NST = A.nstages;
@@ -497,6 +518,18 @@ cudaError_t sweep_configure(int prec, size_t smem) {
     default:
       return cudaFuncSetAttribute(bfly_sweep_kernel<TS32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
+}
+
+int sweep_blocks_per_sm(int prec, size_t smem) {
+  int nb = 0;
+  const int threads = kConsumerThreads + 32;
+  cudaError_t e;
+  switch (prec) {
+    case PREC_FP64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TF64>, threads, smem); break;
+    case PREC_FP32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TF32>, threads, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TS32>, threads, smem); break;
+  }
+  return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
 cudaError_t sweep_launch(int prec, const SweepArgs& a, int grid, size_t smem, cudaStream_t st) {

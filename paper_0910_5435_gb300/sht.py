@@ -30,6 +30,7 @@ EXPORTS = [
     "sht_plan_destroy", "sht_plan_get_stats", "sht_prepare", "sht_plan_nodes", "sht_plan_stream",
     "sht_legendre_synthesize", "sht_legendre_analyze", "sht_legendre_synthesize_adjoint",
     "sht_last_device_status", "sht_direct_prepare", "sht_direct_synthesize", "sht_direct_analyze",
+    "sht_workspace_bytes", "sht_phi_synthesize", "sht_phi_analyze", "sht_synthesize", "sht_analyze",
 ]
 
 
@@ -112,8 +113,14 @@ def lib():
     L.sht_direct_prepare.argtypes = [vp]
     L.sht_direct_synthesize.argtypes = [vp, vp, vp, vp]
     L.sht_direct_analyze.argtypes = [vp, vp, vp, vp]
+    L.sht_workspace_bytes.argtypes = [vp, c_int]
+    L.sht_workspace_bytes.restype = ctypes.c_size_t
+    L.sht_phi_synthesize.argtypes = [vp, c_int, vp, vp, vp, vp]
+    L.sht_phi_analyze.argtypes = [vp, c_int, vp, vp, vp]
+    L.sht_synthesize.argtypes = [vp, c_int, vp, vp, vp, vp]
+    L.sht_analyze.argtypes = [vp, c_int, vp, vp, vp, vp]
     for name in EXPORTS:
-        if name != "sht_status_string":
+        if name not in ("sht_status_string", "sht_workspace_bytes"):
             getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -233,3 +240,27 @@ def sht_direct_synthesize(plan, beta, G, stream=None):
 
 def sht_direct_analyze(plan, G, beta, stream=None):
     _check(lib().sht_direct_analyze(plan.handle, _ptr(G), _ptr(beta), _stream(stream)), "sht_direct_analyze")
+
+
+def sht_workspace_bytes(plan, prec):
+    return int(lib().sht_workspace_bytes(plan.handle, int(prec)))
+
+
+def sht_phi_synthesize(plan, prec, G, values, workspace, stream=None):
+    _check(lib().sht_phi_synthesize(plan.handle, int(prec), _ptr(G), _ptr(values), _ptr(workspace),
+                                    _stream(stream)), "sht_phi_synthesize")
+
+
+def sht_phi_analyze(plan, prec, values, G, stream=None):
+    _check(lib().sht_phi_analyze(plan.handle, int(prec), _ptr(values), _ptr(G), _stream(stream)),
+           "sht_phi_analyze")
+
+
+def sht_synthesize(plan, prec, beta, values, workspace, stream=None):
+    _check(lib().sht_synthesize(plan.handle, int(prec), _ptr(beta), _ptr(values), _ptr(workspace),
+                                _stream(stream)), "sht_synthesize")
+
+
+def sht_analyze(plan, prec, values, beta, workspace, stream=None):
+    _check(lib().sht_analyze(plan.handle, int(prec), _ptr(values), _ptr(beta), _ptr(workspace),
+                             _stream(stream)), "sht_analyze")
