@@ -77,6 +77,10 @@ typedef enum {
 /* Human-readable name of a status code (static string, never NULL). */
 const char* sht_status_string(sht_status s);
 
+/* Text of the last CUDA or cuFFT failure seen by an entry point on the
+ * calling thread ("" if none); valid until the next call on this thread. */
+const char* sht_last_error_detail(void);
+
 /* ------------------------------------------------------------------ plans */
 
 typedef struct {

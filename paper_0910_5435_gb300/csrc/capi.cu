@@ -6,9 +6,11 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 #include <stdexcept>
 #include <thread>
 #include <vector>
@@ -82,8 +84,15 @@ struct sht_plan_s {
 
 namespace {
 
+thread_local char g_err_detail[256] = "";
+
+void set_detail(const char* where, const char* what) {
+  snprintf(g_err_detail, sizeof(g_err_detail), "%s: %s", where, what);
+}
+
 sht_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return SHT_OK;
+  set_detail("cuda", cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return SHT_ERR_OOM;
   if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return SHT_ERR_NO_DEVICE;
   return SHT_ERR_CUDA;
@@ -228,7 +237,9 @@ sht_status upload(sht_plan_t P, int q) {
   if (smem > (size_t)optin) return SHT_ERR_UNSUPPORTED;
   P->dev[q][0].buf_ab = P->dev[q][1].buf_ab = buf_ab;
   P->smem[q] = smem;
-  CK(sht::sweep_configure(q, smem));
+  // the limit is a per-kernel setting shared by every plan: raise it to the
+  // device maximum once instead of to this plan's size
+  CK(sht::sweep_configure(q, (size_t)optin));
   P->ctas_per_sm[q] = sht::sweep_blocks_per_sm(q, smem);
   P->dev_ready[q] = true;
   P->stats.t_upload += now_s() - t0;
@@ -280,6 +291,7 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.counter = P->d_scratch + (q * KIND_COUNT + kind);
   a.status = P->d_scratch + kNumPrec * KIND_COUNT;
   const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
+  (void)cudaGetLastError();  // do not report a stale error left by an earlier call (e.g. inside cuFFT)
   CK(sht::sweep_launch(q, a, grid, P->smem[q], reinterpret_cast<cudaStream_t>(stream)));
   return SHT_OK;
 }
@@ -287,6 +299,8 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
 }  // namespace
 
 extern "C" {
+
+const char* sht_last_error_detail(void) { return g_err_detail; }
 
 const char* sht_status_string(sht_status s) {
   switch (s) {
@@ -510,9 +524,13 @@ static sht_status ensure_fft(sht_plan_t P, int f) {
   // complex side: element (node i, order m) at i + m * 2l, i.e. the [2l][2l] G layout;
   // real side: values[i][j] at i * N + j
   cufftResult r = cufftPlanMany(&P->fft_c2r[f], 1, &n, &cembed, L, 1, &rembed, 1, n, f ? CUFFT_C2R : CUFFT_Z2D, L);
-  if (r != CUFFT_SUCCESS) return r == CUFFT_ALLOC_FAILED ? SHT_ERR_OOM : SHT_ERR_CUDA;
+  if (r != CUFFT_SUCCESS) {
+    set_detail("cufftPlanMany (complex-to-real)", std::to_string((int)r).c_str());
+    return r == CUFFT_ALLOC_FAILED ? SHT_ERR_OOM : SHT_ERR_CUDA;
+  }
   r = cufftPlanMany(&P->fft_r2c[f], 1, &n, &rembed, 1, n, &cembed, L, 1, f ? CUFFT_R2C : CUFFT_D2Z, L);
   if (r != CUFFT_SUCCESS) {
+    set_detail("cufftPlanMany (real-to-complex)", std::to_string((int)r).c_str());
     cufftDestroy(P->fft_c2r[f]);
     return r == CUFFT_ALLOC_FAILED ? SHT_ERR_OOM : SHT_ERR_CUDA;
   }
@@ -529,6 +547,7 @@ static sht_status fft_c2r(sht_plan_t P, int q, void* H, void* values, sht_stream
   const cufftResult r = f ? cufftExecC2R(h, reinterpret_cast<cufftComplex*>(H), reinterpret_cast<cufftReal*>(values))
                           : cufftExecZ2D(h, reinterpret_cast<cufftDoubleComplex*>(H),
                                          reinterpret_cast<cufftDoubleReal*>(values));
+  if (r != CUFFT_SUCCESS) set_detail("cufftExec (complex-to-real)", std::to_string((int)r).c_str());
   return r == CUFFT_SUCCESS ? SHT_OK : SHT_ERR_CUDA;
 }
 
@@ -543,6 +562,7 @@ static sht_status fft_r2c(sht_plan_t P, int q, const void* values, void* H, sht_
       f ? cufftExecR2C(h, reinterpret_cast<cufftReal*>(const_cast<void*>(values)), reinterpret_cast<cufftComplex*>(H))
         : cufftExecD2Z(h, reinterpret_cast<cufftDoubleReal*>(const_cast<void*>(values)),
                        reinterpret_cast<cufftDoubleComplex*>(H));
+  if (r != CUFFT_SUCCESS) set_detail("cufftExec (real-to-complex)", std::to_string((int)r).c_str());
   return r == CUFFT_SUCCESS ? SHT_OK : SHT_ERR_CUDA;
 }
 
@@ -569,6 +589,7 @@ sht_status sht_phi_synthesize(sht_plan_t P, sht_precision prec, const void* G, v
   sht_status s = phi_args_ok(P, prec, G, values, q);
   if (s != SHT_OK) return s;
   if (!workspace || !aligned(workspace, 16)) return SHT_ERR_INVALID_ARG;
+  (void)cudaGetLastError();
   CK(sht::phase_launch(q == sht::PREC_FP32, G, workspace, P->d_tw_syn, P->H.l, P->num_sms,
                        reinterpret_cast<cudaStream_t>(stream)));
   return fft_c2r(P, q, workspace, values, stream);
@@ -580,6 +601,7 @@ sht_status sht_phi_analyze(sht_plan_t P, sht_precision prec, const void* values,
   if (s != SHT_OK) return s;
   s = fft_r2c(P, q, values, G, stream);
   if (s != SHT_OK) return s;
+  (void)cudaGetLastError();
   CK(sht::phase_launch(q == sht::PREC_FP32, G, G, P->d_tw_ana, P->H.l, P->num_sms,
                        reinterpret_cast<cudaStream_t>(stream)));
   return SHT_OK;
@@ -686,6 +708,7 @@ sht_status sht_direct_synthesize(sht_plan_t P, const void* beta, void* G, sht_st
   if (!P->d_dense) return SHT_ERR_INVALID_ARG;
   if (!aligned(beta, 16) || !aligned(G, 16)) return SHT_ERR_INVALID_ARG;
   CK(cudaSetDevice(P->device));
+  (void)cudaGetLastError();
   CK(sht::direct_synth_launch(direct_args(P, beta, G), reinterpret_cast<cudaStream_t>(stream)));
   return SHT_OK;
 }
@@ -696,6 +719,7 @@ sht_status sht_direct_analyze(sht_plan_t P, const void* G, void* beta, sht_strea
   if (!P->d_dense) return SHT_ERR_INVALID_ARG;
   if (!aligned(beta, 16) || !aligned(G, 16)) return SHT_ERR_INVALID_ARG;
   CK(cudaSetDevice(P->device));
+  (void)cudaGetLastError();
   CK(sht::direct_analysis_launch(direct_args(P, G, beta), reinterpret_cast<cudaStream_t>(stream)));
   return SHT_OK;
 }

@@ -119,7 +119,9 @@ cudaError_t direct_synth_launch(const DirectArgs& a, cudaStream_t st) {
   const dim3 grid((l + kRowTile - 1) / kRowTile, 2 * l);
   const size_t smem = sizeof(double2) * (size_t)(2 * l + 1);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(direct_synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // per-kernel setting shared by all plans: never lower it
+    cudaError_t e = cudaFuncSetAttribute(direct_synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(double2) * (2 * 1024 + 1));
     if (e != cudaSuccess) return e;
   }
   direct_synth_kernel<<<grid, kRowTile, smem, st>>>(a);
@@ -131,8 +133,8 @@ cudaError_t direct_analysis_launch(const DirectArgs& a, cudaStream_t st) {
   const dim3 grid(2 * l, 2);
   const size_t smem = sizeof(double2) * (size_t)l;
   if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(direct_analysis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(direct_analysis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(double2) * 1024);
     if (e != cudaSuccess) return e;
   }
   direct_analysis_kernel<<<grid, 256, smem, st>>>(a);

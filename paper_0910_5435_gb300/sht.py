@@ -31,12 +31,16 @@ EXPORTS = [
     "sht_legendre_synthesize", "sht_legendre_analyze", "sht_legendre_synthesize_adjoint",
     "sht_last_device_status", "sht_direct_prepare", "sht_direct_synthesize", "sht_direct_analyze",
     "sht_workspace_bytes", "sht_phi_synthesize", "sht_phi_analyze", "sht_synthesize", "sht_analyze",
+    "sht_last_error_detail",
 ]
 
 
 class ShtError(RuntimeError):
     def __init__(self, code, where):
-        super().__init__(f"{where}: {STATUS.get(code, code)}")
+        detail = ""
+        if code in (2, 3) and _lib is not None:
+            detail = " (" + (_lib.sht_last_error_detail() or b"").decode(errors="replace") + ")"
+        super().__init__(f"{where}: {STATUS.get(code, code)}{detail}")
         self.code = code
 
 
@@ -99,6 +103,8 @@ def lib():
     vp, c_int, c_double = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
     L.sht_status_string.restype = ctypes.c_char_p
     L.sht_status_string.argtypes = [c_int]
+    L.sht_last_error_detail.restype = ctypes.c_char_p
+    L.sht_last_error_detail.argtypes = []
     L.sht_plan_opts_default.argtypes = [ctypes.POINTER(sht_plan_opts)]
     L.sht_plan_create.argtypes = [c_int, c_double, ctypes.POINTER(vp)]
     L.sht_plan_create_ex.argtypes = [c_int, c_double, ctypes.POINTER(sht_plan_opts), ctypes.POINTER(vp)]
@@ -120,7 +126,7 @@ def lib():
     L.sht_synthesize.argtypes = [vp, c_int, vp, vp, vp, vp]
     L.sht_analyze.argtypes = [vp, c_int, vp, vp, vp, vp]
     for name in EXPORTS:
-        if name not in ("sht_status_string", "sht_workspace_bytes"):
+        if name not in ("sht_status_string", "sht_workspace_bytes", "sht_last_error_detail"):
             getattr(L, name).restype = c_int
     _lib = L
     return L
