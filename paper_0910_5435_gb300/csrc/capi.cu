@@ -225,22 +225,30 @@ sht_status upload(sht_plan_t P, int q) {
     CK(cudaMemcpy(D.pages, S.bytes.data(), D.bytes, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(D.units, S.units.data(), sizeof(sht::UnitEntry) * S.units.size(), cudaMemcpyHostToDevice));
   }
-  int& nst = P->nstages[q];
-  size_t smem = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, P->H.l);
+  // Ring depth: prefer two resident CTAs per SM (their warps hide each
+  // other's level boundaries) with at least three pages in flight each; else
+  // one CTA with a deeper ring.
   int optin = 0;
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
-  // fewer stages if the vectors of a large l leave too little room
-  while (smem > (size_t)optin && nst > 2) {
-    --nst;
-    smem = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, P->H.l);
-  }
-  if (smem > (size_t)optin) return SHT_ERR_UNSUPPORTED;
-  P->dev[q][0].buf_ab = P->dev[q][1].buf_ab = buf_ab;
-  P->smem[q] = smem;
   // the limit is a per-kernel setting shared by every plan: raise it to the
   // device maximum once instead of to this plan's size
   CK(sht::sweep_configure(q, (size_t)optin));
-  P->ctas_per_sm[q] = sht::sweep_blocks_per_sm(q, smem);
+  int best_nst = 0, best_ctas = 0;
+  for (int nst = 8; nst >= 2; --nst) {
+    const size_t sm = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, P->H.l);
+    if (sm > (size_t)optin) continue;
+    const int ctas = std::min(2, sht::sweep_blocks_per_sm(q, sm));
+    const bool better = (ctas > best_ctas && (nst >= 3 || best_ctas == 0)) || best_ctas == 0;
+    if (better) {
+      best_nst = nst;
+      best_ctas = ctas;
+    }
+  }
+  if (best_nst == 0) return SHT_ERR_UNSUPPORTED;
+  P->nstages[q] = best_nst;
+  P->ctas_per_sm[q] = best_ctas;
+  P->smem[q] = sht::sweep_smem_bytes(q, P->H.page_bytes, best_nst, buf_ab, P->H.l);
+  P->dev[q][0].buf_ab = P->dev[q][1].buf_ab = buf_ab;
   P->dev_ready[q] = true;
   P->stats.t_upload += now_s() - t0;
   return SHT_OK;

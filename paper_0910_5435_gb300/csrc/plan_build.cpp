@@ -581,30 +581,59 @@ inline void put_value(uint8_t* dst, int prec, size_t i, double v) {
   }
 }
 
+// Writes ops and assigns their ordering field: ops emitted after
+// new_group() may overlap each other but start only after everything
+// emitted before the group has completed.
 struct Emitter {
   PageWriter& W;
   int prec;
   size_t vs;
+  int group_pos = 0;
   Emitter(PageWriter& w, int p) : W(w), prec(p), vs(value_size(p)) {}
 
-  OpHdr hdr(uint8_t kind, uint8_t flags) {
+  void new_group() { group_pos = 0; }
+
+  OpHdr hdr(uint8_t kind, uint8_t flags = 0) {
     OpHdr h;
     std::memset(&h, 0, sizeof(h));
     h.kind = kind;
     h.flags = flags;
     return h;
   }
-  void control(OpHdr h) {
-    h.bytes = sizeof(OpHdr);
-    h.idx_bytes = 0;
-    std::memcpy(W.alloc(sizeof(OpHdr)), &h, sizeof(OpHdr));
-  }
   size_t bytes_of(size_t nidx, size_t nval) const { return sizeof(OpHdr) + pad16(2 * nidx) + pad16(vs * nval); }
 
-  // largest piece of outputs (<= cap) that fits in the current page; 0 if none
+  void write(OpHdr h, const std::vector<uint16_t>& idx, const std::vector<double>& vals) {
+    h.dep = (uint16_t)std::min(group_pos, 65535);
+    ++group_pos;
+    h.idx_bytes = (uint32_t)pad16(2 * idx.size());
+    h.bytes = (uint32_t)bytes_of(idx.size(), vals.size());
+    uint8_t* p = W.alloc(h.bytes);
+    std::memcpy(p, &h, sizeof(OpHdr));
+    if (!idx.empty()) std::memcpy(p + sizeof(OpHdr), idx.data(), 2 * idx.size());
+    uint8_t* v = p + sizeof(OpHdr) + h.idx_bytes;
+    for (size_t i = 0; i < vals.size(); ++i) put_value(v, prec, i, vals[i]);
+  }
+
+  // A control op over [start, start + count), split into up to kCtlPieces warp tasks.
+  void control(OpHdr base, int start, int count) {
+    if (count <= 0) return;
+    const int pieces = std::max(1, std::min(kCtlPieces, (count + 63) / 64));
+    for (int q = 0; q < pieces; ++q) {
+      const int a = start + (int)((long long)count * q / pieces);
+      const int b = start + (int)((long long)count * (q + 1) / pieces);
+      if (b <= a) continue;
+      OpHdr h = base;
+      h.M = (uint16_t)(b - a);
+      h.oo = (uint16_t)a;
+      h.io = (uint16_t)a;
+      write(h, {}, {});
+    }
+  }
+
+  // largest piece (<= cap outputs) that fits the current page
   template <class F>
-  int fit(int remaining, F bytes_for) {
-    int lo = 0, hi = std::min(remaining, kMaxM);
+  int fit(int cap, F bytes_for) {
+    int lo = 0, hi = std::min(cap, kMaxM);
     while (lo < hi) {
       const int mid = (lo + hi + 1) / 2;
       if (bytes_for(mid) <= W.space()) lo = mid; else hi = mid - 1;
@@ -612,122 +641,89 @@ struct Emitter {
     return lo;
   }
   // Size of the next piece of an op with `remaining` outputs: pieces are
-  // balanced (a block that needs two pages is cut in halves, not into a
-  // full page plus a sliver), and a partly used page is filled with a smaller
-  // piece only if that piece still has >= 16 outputs.
+  // balanced (an op that needs two pages is cut in halves, not into a full
+  // page plus a sliver); a partly used page takes a smaller piece only if it
+  // keeps at least 8 outputs.
   template <class F>
   int piece(int remaining, F bytes_for) {
-    int mfresh = 0;
-    {
-      int lo = 0, hi = std::min(remaining, kMaxM);
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) / 2;
-        if (bytes_for(mid) <= W.PB) lo = mid; else hi = mid - 1;
-      }
-      mfresh = lo;
+    int lo = 0, hi = std::min(remaining, kMaxM);
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (bytes_for(mid) <= W.PB) lo = mid; else hi = mid - 1;
     }
+    const int mfresh = lo;
     if (mfresh <= 0) throw std::logic_error("op does not fit in a page");
     const int npieces = (remaining + mfresh - 1) / mfresh;
     const int target = (remaining + npieces - 1) / npieces;
     int mp = fit(target, bytes_for);
-    if (mp < target && mp < 16) {
+    if (mp < target && mp < std::min(target, 8)) {
       W.new_page();
       mp = target;
     }
     return mp;
   }
-  void write(OpHdr h, const std::vector<uint16_t>& idx, size_t nval, const std::vector<double>& vals) {
-    h.idx_bytes = (uint32_t)pad16(2 * idx.size());
-    h.bytes = (uint32_t)bytes_of(idx.size(), nval);
-    uint8_t* p = W.alloc(h.bytes);
-    std::memcpy(p, &h, sizeof(OpHdr));
-    if (!idx.empty()) std::memcpy(p + sizeof(OpHdr), idx.data(), 2 * idx.size());
-    uint8_t* v = p + sizeof(OpHdr) + h.idx_bytes;
-    for (size_t i = 0; i < nval; ++i) put_value(v, prec, i, vals[i]);
-  }
 
-  // y[oo + o] = z[io + skel[o]] + sum_s T[s][o] z[io + red[s]]; wide inner
-  // dimensions are split into chunks accumulated with F_ACCUM (the skeleton
-  // pass-through rides on the first chunk only).
-  void syn_interp(const IdBlock& b, uint8_t in_buf, uint8_t out_buf, bool sync) {
+  // y[oo + o] = z[io + skel[o]] + sum_s T[s][o] z[io + red[s]]
+  void syn_interp(const IdBlock& b, uint8_t in_buf, uint8_t out_buf) {
     const int k = b.k, K = b.nin - b.k;
-    const int mk = std::min(k, 32);
-    int Kc = std::max(K, 1);
-    while (Kc > 1 && bytes_of((size_t)Kc + mk, (size_t)Kc * mk) > W.PB) Kc = Kc * 3 / 4;
-    for (int k0 = 0; k0 == 0 || k0 < K; k0 += Kc) {
-      const int kc = std::min(Kc, K - k0);
-      const bool first_chunk = (k0 == 0);
-      for (int o0 = 0; o0 < k;) {
-        const int mp = piece(k - o0, [&](int M) {
-          return bytes_of((size_t)kc + (first_chunk ? M : 0), (size_t)kc * M);
-        });
-        OpHdr h = hdr(OP_SYN_INTERP, (sync ? F_SYNC_BEFORE : 0) | (first_chunk ? 0 : F_ACCUM));
-        sync = false;
-        h.in_buf = in_buf;
-        h.out_buf = out_buf;
-        h.M = (uint16_t)mp;
-        h.K = (uint16_t)kc;
-        h.nskel = (uint16_t)(first_chunk ? mp : 0);
-        h.io = (uint16_t)b.in_off;
-        h.oo = (uint16_t)(b.out_off + o0);
-        std::vector<uint16_t> idx(b.red.begin() + k0, b.red.begin() + k0 + kc);
-        if (first_chunk) idx.insert(idx.end(), b.skel.begin() + o0, b.skel.begin() + o0 + mp);
-        std::vector<double> vals((size_t)kc * mp);
-        for (int s2 = 0; s2 < kc; ++s2)
-          for (int o = 0; o < mp; ++o) vals[(size_t)s2 * mp + o] = b.T[(size_t)(k0 + s2) * k + o0 + o];
-        write(h, idx, vals.size(), vals);
-        o0 += mp;
-      }
-      if (K == 0) break;
+    for (int o0 = 0; o0 < k;) {
+      const int mp = piece(k - o0, [&](int M) { return bytes_of((size_t)K + M, (size_t)K * M); });
+      OpHdr h = hdr(OP_SYN_INTERP);
+      h.in_buf = in_buf;
+      h.out_buf = out_buf;
+      h.M = (uint16_t)mp;
+      h.K = (uint16_t)K;
+      h.nskel = (uint16_t)mp;
+      h.io = (uint16_t)b.in_off;
+      h.oo = (uint16_t)(b.out_off + o0);
+      std::vector<uint16_t> idx(b.red.begin(), b.red.end());
+      idx.insert(idx.end(), b.skel.begin() + o0, b.skel.begin() + o0 + mp);
+      std::vector<double> vals((size_t)K * mp);
+      for (int s = 0; s < K; ++s)
+        for (int o = 0; o < mp; ++o) vals[(size_t)s * mp + o] = b.T[(size_t)s * k + o0 + o];
+      write(h, idx, vals);
+      o0 += mp;
     }
   }
 
-  // out[oo + o] (=|+=) sum_s V(s, o) in[io + s], o < M, s < K; split over K with F_ACCUM if needed
+  // out[oo + o] = sum_s V(s, o) in[io + s] (kind DENSE or DENSE_G)
   template <class GetV>
-  void dense(int M, int K, GetV getv, uint8_t in_buf, int io, uint8_t out_buf, int oo, bool sync, bool accum = false) {
-    const size_t maxk_rows = std::min(M, 32);
-    int Kc = K;
-    if (K > 0 && bytes_of(0, (size_t)K * maxk_rows) > W.PB)
-      Kc = (int)((W.PB - sizeof(OpHdr) - 16) / (vs * maxk_rows));
-    for (int k0 = 0; k0 < std::max(K, 1); k0 += std::max(Kc, 1)) {
-      const int kc = std::min(Kc, K - k0);
-      for (int o0 = 0; o0 < M;) {
-        const int mp = piece(M - o0, [&](int Mp) { return bytes_of(0, (size_t)std::max(kc, 0) * Mp); });
-        OpHdr h = hdr(OP_DENSE, (sync ? F_SYNC_BEFORE : 0) | ((accum || k0 > 0) ? F_ACCUM : 0));
-        sync = false;
-        h.in_buf = in_buf;
-        h.out_buf = out_buf;
-        h.M = (uint16_t)mp;
-        h.K = (uint16_t)std::max(kc, 0);
-        h.io = (uint16_t)(io + k0);
-        h.oo = (uint16_t)(oo + o0);
-        std::vector<double> vals((size_t)std::max(kc, 0) * mp);
-        for (int s = 0; s < kc; ++s)
-          for (int o = 0; o < mp; ++o) vals[(size_t)s * mp + o] = getv(k0 + s, o0 + o);
-        write(h, {}, vals.size(), vals);
-        o0 += mp;
-      }
-      if (K == 0) break;
+  void dense(uint8_t kind, uint8_t flags, int M, int K, GetV getv, uint8_t in_buf, int io, uint8_t out_buf, int oo,
+             int m = 0) {
+    for (int o0 = 0; o0 < M;) {
+      const int mp = piece(M - o0, [&](int Mp) { return bytes_of(0, (size_t)K * Mp); });
+      OpHdr h = hdr(kind, flags);
+      h.in_buf = in_buf;
+      h.out_buf = out_buf;
+      h.M = (uint16_t)mp;
+      h.K = (uint16_t)K;
+      h.io = (uint16_t)io;
+      h.oo = (uint16_t)(oo + o0);
+      h.a1 = (uint32_t)m;
+      std::vector<double> vals((size_t)K * mp);
+      for (int s = 0; s < K; ++s)
+        for (int o = 0; o < mp; ++o) vals[(size_t)s * mp + o] = getv(s, o0 + o);
+      write(h, {}, vals);
+      o0 += mp;
     }
   }
 
-  // z[oo + red[o]] += sum_t T[o][t] y[io + t]; z[oo + skel[t]] += y[io + t]
-  void ana_interp(const IdBlock& b, uint8_t in_buf, uint8_t out_buf, bool sync) {
+  // z[oo + red[o]] (= or +=) sum_t T[o][t] y[io + t]; z[oo + skel[t]] (= or +=) y[io + t]
+  void ana_interp(const IdBlock& b, uint8_t in_buf, uint8_t out_buf, bool accum) {
     const int k = b.k, nred = b.nin - b.k;
     if (k == 0) return;
     bool skel_done = false;
-    for (int o0 = 0; o0 < nred || !skel_done;) {
+    int o0 = 0;
+    do {
       const int rem = nred - o0;
-      int mp;
+      const size_t extra = skel_done ? 0 : (size_t)k;
+      int mp = 0;
       if (rem > 0) {
-        const size_t extra = skel_done ? 0 : (size_t)k;
         mp = piece(rem, [&](int M) { return bytes_of((size_t)M + extra, (size_t)k * M); });
-      } else {
-        mp = 0;
-        if (bytes_of(k, 0) > W.space()) W.new_page();
+      } else if (bytes_of(extra, 0) > W.space()) {
+        W.new_page();
       }
-      OpHdr h = hdr(OP_ANA_INTERP, (sync ? F_SYNC_BEFORE : 0) | (skel_done ? 0 : F_SKEL));
-      sync = false;
+      OpHdr h = hdr(OP_ANA_INTERP, (uint8_t)((skel_done ? 0 : F_SKEL) | (accum ? F_ACCUM : 0)));
       h.in_buf = in_buf;
       h.out_buf = out_buf;
       h.M = (uint16_t)mp;
@@ -740,15 +736,26 @@ struct Emitter {
       std::vector<double> vals((size_t)k * mp);
       for (int t = 0; t < k; ++t)
         for (int o = 0; o < mp; ++o) vals[(size_t)t * mp + o] = b.T[(size_t)(o0 + o) * k + t];
-      write(h, idx, vals.size(), vals);
+      write(h, idx, vals);
       skel_done = true;
       o0 += mp;
-      if (o0 >= nred) break;
-    }
+    } while (o0 < nred);
   }
 };
 
 inline uint8_t level_buf(int j) { return (j & 1) ? BUF_B : BUF_A; }
+inline uint8_t other_buf(uint8_t b) { return b == BUF_A ? BUF_B : BUF_A; }
+
+std::vector<const IdBlock*> blocks_at(const UnitFact& U, int j) {
+  std::vector<const IdBlock*> v;
+  for (const auto& b : U.blocks)
+    if (b.level == j) v.push_back(&b);
+  // largest first: the warps of a CTA then finish a level together
+  std::stable_sort(v.begin(), v.end(), [](const IdBlock* a, const IdBlock* b) {
+    return (long long)a->k * (a->nin - a->k + 1) > (long long)b->k * (b->nin - b->k + 1);
+  });
+  return v;
+}
 
 // Appends the ops of order m to the page writer (continuing its open page).
 void emit_unit(PlanHost& P, int prec, int dir, int m, PageWriter& W) {
@@ -762,106 +769,132 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, PageWriter& W) {
     sqw2[i] = std::sqrt(0.5 * P.w[l + i]);
   }
   if (dir == 0) {
-    int rows[2] = {0, 0};
-    for (int p = 0; p < 2; ++p) {
-      const UnitFact& U = F[(size_t)m * 2 + p];
-      if (U.n == 0 || U.rows == 0) continue;
-      rows[p] = U.rows;
-      const uint8_t outE = p ? BUF_O : BUF_E;
-      OpHdr g = E.hdr(OP_GATHER, F_SYNC_BEFORE);
-      g.a0 = (uint16_t)p;
-      g.a1 = (uint32_t)m;
-      g.M = (uint16_t)U.n;
-      g.out_buf = BUF_A;
-      g.oo = 0;
-      E.control(g);
-      if (U.direct) {
-        // E_i = sum_j P-bar(x_i) x_j: weighted values divided by sqrt(2 w_i)
-        E.dense(U.rows, U.n, [&](int s, int o) { return U.D[(size_t)s * U.rows + o] * inv_sq2w[o]; },
-                BUF_A, 0, outE, 0, true);
-      } else {
-        for (int j = 1; j <= U.levels + 1; ++j) {
-          bool first = true;
-          std::vector<const IdBlock*> v;
-          for (const auto& b : U.blocks)
-            if (b.level == j) v.push_back(&b);
-          std::sort(v.begin(), v.end(), [](const IdBlock* a, const IdBlock* b) { return a->out_off < b->out_off; });
-          for (const IdBlock* b : v) {
-            if (b->k == 0) continue;
-            E.syn_interp(*b, j == 1 ? BUF_A : level_buf(j - 1), level_buf(j), first);
-            first = false;
-          }
-        }
-        bool first = true;
-        const uint8_t top = level_buf(U.levels + 1);
-        for (const auto& f : U.finals) {
-          const int h = f.r1 - f.r0;
-          E.dense(h, f.k, [&](int s, int o) { return f.S[(size_t)s * h + o] * inv_sq2w[f.r0 + o]; },
-                  top, f.in_off, outE, f.r0, first);
-          first = false;
-        }
-      }
-    }
-    OpHdr u = E.hdr(OP_UNFOLD, F_SYNC_BEFORE);
-    u.a1 = (uint32_t)m;
-    u.M = (uint16_t)rows[0];
-    u.K = (uint16_t)rows[1];
-    E.control(u);
-  } else {
-    OpHdr f = E.hdr(OP_FOLD, F_SYNC_BEFORE);
-    f.a1 = (uint32_t)m;
-    E.control(f);
     for (int p = 0; p < 2; ++p) {
       const UnitFact& U = F[(size_t)m * 2 + p];
       if (U.n == 0) continue;
-      const uint8_t src = p ? BUF_O : BUF_E;
-      if (U.rows == 0) {
-        OpHdr c = E.hdr(OP_CLEAR, F_SYNC_BEFORE);
-        c.out_buf = BUF_A;
-        c.M = (uint16_t)U.n;
-        E.control(c);
-      } else if (U.direct) {
-        // x_j = sum_i w_i P-bar(x_i) F_i: weighted values times sqrt(w_i / 2)
-        E.dense(U.n, U.rows, [&](int s, int o) { return U.D[(size_t)o * U.rows + s] * sqw2[s]; },
-                src, 0, BUF_A, 0, true);
+      const uint8_t gflags = p ? F_ACCUM : 0;
+      E.new_group();
+      OpHdr g = E.hdr(OP_GATHER);
+      g.a0 = (uint16_t)p;
+      g.a1 = (uint32_t)m;
+      g.out_buf = BUF_A;
+      E.control(g, 0, U.n);
+      if (U.rows > 0) {
+        if (U.direct) {
+          // E_i = sum_j P-bar(x_i) x_j: weighted values divided by sqrt(2 w_i)
+          E.new_group();
+          E.dense(OP_DENSE_G, gflags, U.rows, U.n,
+                  [&](int s, int o) { return U.D[(size_t)s * U.rows + o] * inv_sq2w[o]; }, BUF_A, 0, BUF_A, 0, m);
+        } else {
+          for (int j = 1; j <= U.levels + 1; ++j) {
+            E.new_group();
+            for (const IdBlock* b : blocks_at(U, j))
+              if (b->k > 0) E.syn_interp(*b, j == 1 ? BUF_A : level_buf(j - 1), level_buf(j));
+          }
+          E.new_group();
+          const uint8_t top = level_buf(U.levels + 1);
+          std::vector<const FinalBlock*> fs;
+          for (const auto& f : U.finals) fs.push_back(&f);
+          std::stable_sort(fs.begin(), fs.end(), [](const FinalBlock* a, const FinalBlock* b) {
+            return (long long)a->k * (a->r1 - a->r0) > (long long)b->k * (b->r1 - b->r0);
+          });
+          for (const FinalBlock* f : fs) {
+            const int h = f->r1 - f->r0;
+            if (f->k == 0 && p == 1) continue;  // adds nothing
+            E.dense(OP_DENSE_G, gflags, h, f->k,
+                    [&](int s, int o) { return f->S[(size_t)s * h + o] * inv_sq2w[f->r0 + o]; }, top, f->in_off,
+                    BUF_A, f->r0, m);
+          }
+        }
       } else {
-        const uint8_t top = level_buf(U.levels + 1);
-        bool first = true;
-        bool any_top = false;
-        for (const auto& fb : U.finals) {
-          if (fb.k == 0) continue;
-          const int h = fb.r1 - fb.r0;
-          E.dense(fb.k, h, [&](int s, int o) { return fb.S[(size_t)o * h + s] * sqw2[fb.r0 + s]; },
-                  src, fb.r0, top, fb.in_off, first);
-          first = false;
-          any_top = true;
-        }
-        if (!any_top && U.width[U.levels + 1] > 0) {
-          OpHdr c = E.hdr(OP_CLEAR, F_SYNC_BEFORE);
-          c.out_buf = top;
-          c.M = (uint16_t)U.width[U.levels + 1];
-          E.control(c);
-        }
-        for (int j = U.levels + 1; j >= 1; --j) {
-          const uint8_t dst = (j == 1) ? BUF_A : level_buf(j - 1);
-          OpHdr c = E.hdr(OP_CLEAR, F_SYNC_BEFORE);
-          c.out_buf = dst;
-          c.M = (uint16_t)(j == 1 ? U.n : U.width[j - 1]);
-          E.control(c);
-          std::vector<const IdBlock*> v;
-          for (const auto& b : U.blocks)
-            if (b.level == j) v.push_back(&b);
-          std::sort(v.begin(), v.end(), [](const IdBlock* a, const IdBlock* b) { return a->out_off < b->out_off; });
-          for (const IdBlock* b : v) E.ana_interp(*b, level_buf(j), dst, false);
+        E.new_group();
+      }
+      if (p == 0 && U.rows < l) {
+        // node rows past the kept ones hold no even part: zero them in the same group
+        OpHdr z = E.hdr(OP_GZERO);
+        z.a1 = (uint32_t)m;
+        E.control(z, U.rows, l - U.rows);
+      }
+    }
+  } else {
+    for (int p = 0; p < 2; ++p) {
+      const UnitFact& U = F[(size_t)m * 2 + p];
+      if (U.n == 0) continue;
+      if (U.rows == 0) {
+        E.new_group();
+        OpHdr c = E.hdr(OP_CLEAR);
+        c.out_buf = BUF_A;
+        E.control(c, 0, U.n);
+      } else {
+        const uint8_t top = U.direct ? BUF_A : level_buf(U.levels + 1);
+        const uint8_t ubuf = U.direct ? BUF_B : other_buf(top);
+        E.new_group();
+        OpHdr f = E.hdr(OP_FOLD);
+        f.a0 = (uint16_t)p;
+        f.a1 = (uint32_t)m;
+        f.out_buf = ubuf;
+        E.control(f, 0, U.rows);
+        E.new_group();
+        if (U.direct) {
+          // x_j = sum_i w_i P-bar(x_i) u_i: weighted values times sqrt(w_i / 2)
+          E.dense(OP_DENSE, 0, U.n, U.rows, [&](int s, int o) { return U.D[(size_t)o * U.rows + s] * sqw2[s]; },
+                  ubuf, 0, BUF_A, 0);
+        } else {
+          for (const auto& fb : U.finals) {
+            if (fb.k == 0) continue;
+            const int h = fb.r1 - fb.r0;
+            E.dense(OP_DENSE, 0, fb.k, h, [&](int s, int o) { return fb.S[(size_t)o * h + s] * sqw2[fb.r0 + s]; },
+                    ubuf, fb.r0, top, fb.in_off);
+          }
+          for (int j = U.levels + 1; j >= 2; --j) {
+            // blocks of level j come in pairs (top band 2b, bottom band 2b+1) sharing one input
+            // vector z of level j-1; the top halves overwrite z, then the bottom halves add
+            const uint8_t src = level_buf(j), dst = level_buf(j - 1);
+            std::vector<const IdBlock*> tops, bots;
+            for (const IdBlock* b : blocks_at(U, j)) (b->band % 2 == 0 ? tops : bots).push_back(b);
+            auto partner = [&](const IdBlock* t) -> const IdBlock* {
+              for (const IdBlock* b : bots)
+                if (b->band == t->band + 1 && b->group == t->group) return b;
+              return nullptr;
+            };
+            E.new_group();
+            std::vector<const IdBlock*> second;
+            for (const IdBlock* t : tops) {
+              const IdBlock* b = partner(t);
+              if (t->k > 0) {
+                E.ana_interp(*t, src, dst, false);
+                if (b && b->k > 0) second.push_back(b);
+              } else if (b && b->k > 0) {
+                E.ana_interp(*b, src, dst, false);
+              } else if (t->nin > 0) {
+                OpHdr c = E.hdr(OP_CLEAR);
+                c.out_buf = dst;
+                E.control(c, t->in_off, t->nin);
+              }
+            }
+            if (!second.empty()) {
+              E.new_group();
+              for (const IdBlock* b : second) E.ana_interp(*b, src, dst, true);
+            }
+          }
+          E.new_group();
+          for (const IdBlock* b : blocks_at(U, 1)) {
+            if (b->k > 0) {
+              E.ana_interp(*b, BUF_B, BUF_A, false);
+            } else {
+              OpHdr c = E.hdr(OP_CLEAR);
+              c.out_buf = BUF_A;
+              E.control(c, b->in_off, b->nin);
+            }
+          }
         }
       }
-      OpHdr s = E.hdr(OP_SCATTER, F_SYNC_BEFORE);
+      E.new_group();
+      OpHdr s = E.hdr(OP_SCATTER);
       s.a0 = (uint16_t)p;
       s.a1 = (uint32_t)m;
-      s.M = (uint16_t)U.n;
       s.in_buf = BUF_A;
-      s.io = 0;
-      E.control(s);
+      E.control(s, 0, U.n);
     }
   }
 }
@@ -960,12 +993,13 @@ void emit_streams(PlanHost& P, int prec) {
     OpHdr q;
     std::memset(&q, 0, sizeof(q));
     q.bytes = sizeof(OpHdr);
-    q.kind = 0xFF;
+    q.kind = OP_QUIT;
     std::memcpy(quit.data(), &q, sizeof(q));
     S.bytes.insert(S.bytes.end(), quit.begin(), quit.end());
     int mx = 0;
     for (int u = 0; u < L * 2; ++u) {
       mx = std::max(mx, F[u].n);
+      if (dir == 1) mx = std::max(mx, F[u].rows);  // the fold writes the kept rows
       for (int wdt : F[u].width) mx = std::max(mx, wdt);
     }
     S.max_buf_ab = mx;

@@ -6,31 +6,43 @@
 // application, Section 2.2 remark after Figure multi).
 //
 // A stream is a sequence of fixed-size PAGES (page_bytes each, the unit of
-// one TMA bulk copy).  Each order m ("unit") owns a contiguous run of pages;
-// the unit table lists them in decreasing cost (LPT order for the persistent
-// kernel's work queue).  A page holds a sequence of OPS, each 16-byte aligned:
+// one TMA bulk copy).  A work item (one large order m, or several small
+// ones) owns a contiguous run of pages; the item table lists them in
+// decreasing size (LPT order for the persistent kernel's work queue).  A
+// page holds a sequence of OPS, each 16-byte aligned:
 //
 //   [OpHdr 32 B][uint16 index lists, padded to 16 B][values, padded to 16 B]
 //
-// and ends at the first header with bytes == 0 (or at the page end).  Every
-// op applies one small dense matrix V ([K][M] layout, M fastest, so the
-// threads of a warp that own consecutive outputs o read consecutive values)
-// to a vector held in shared memory:
+// and ends at the first header with bytes == 0 (or at the page end).
+//
+// Every op is executed by ONE warp.  Compute ops apply a small dense matrix V
+// ([K][M] layout, M fastest: lanes that own consecutive outputs read
+// consecutive values) to a vector held in shared memory; M <= 32:
 //
 //   SYN_INTERP  out[oo + o] = in[io + skel[o]] + sum_s V[s][o] in[io + red[s]]
-//               (with F_ACCUM: out[oo + o] += ...; the skel term only for o < nskel)
 //               -- one interpolation matrix of an ID (Section 2.1 eq. 2.1,
 //               Section 2.2 eqs. 1-6: y = z[skel] + T z[red]);
-//   DENSE       out[oo + o] (= or +=) sum_s V[s][o] in[io + s]
-//               -- a stored skeleton-column block (the unprocessed blocks of
-//               Section 3) or a dense block;
-//   ANA_INTERP  out[oo + red[o]] += sum_s V[s][o] in[io + s], and, with F_SKEL,
-//               out[oo + skel[t]] += in[io + t]
+//   DENSE       out[oo + o] = sum_s V[s][o] in[io + s]
+//               -- stored skeleton columns (the unprocessed blocks of
+//               Section 3) or a dense block, into shared memory;
+//   DENSE_G     the same, written to the node values of order m: with
+//               v_i = sum_s V[s][o] in[io + s], i = oo + o, the parity unfold
+//               of Section 2.3: G[m][l+i] (= or +=) v_i, G[m][l-1-i] (= or -=) v_i
+//               (F_ACCUM for the odd parity, after the even one has written);
+//   ANA_INTERP  out[oo + red[o]] (= or +=) sum_s V[s][o] in[io + s], and with
+//               F_SKEL also out[oo + skel[t]] (= or +=) in[io + t]
 //               -- the transpose of an interpolation matrix (anterpolation).
 //
-// Control ops carry no values: GATHER / SCATTER move one parity of beta^m
-// between global memory and shared memory, UNFOLD / FOLD apply the parity
-// split of Section 2.3 on the symmetric nodes, CLEAR zeroes an accumulator.
+// Control ops carry no values and cover an element range [start, start + M):
+// GATHER / SCATTER move one parity of beta^m between global and shared
+// memory, FOLD forms u_i = s_i (G[m][l+i] +- G[m][l-1-i]) (the parity fold),
+// CLEAR zeroes a shared range, GZERO zeroes node rows of G.
+//
+// Ordering: ops are numbered in stream order.  Op t may start once every op
+// numbered below t - dep has completed (dep = how many immediately preceding
+// ops it may overlap: the ops of one butterfly level are mutually
+// independent, so the i-th op of a level has dep = i, and dep = 0 acts as a
+// barrier).
 //
 // Values: float64 (SHT_FP64), float2 {hi, lo} (SHT_SPLIT32) or float
 // (SHT_FP32).  Shared-memory vectors hold complex numbers in the working
@@ -44,59 +56,59 @@ namespace sht {
 
 enum OpKind : uint8_t {
   OP_END = 0,
-  OP_GATHER = 1,      // buf[out_buf][oo + j] = beta^m_{m+p+2j}, j < M       (a0 = p, a1 = m)
-  OP_SCATTER = 2,     // beta^m_{m+p+2j} = buf[in_buf][io + j], j < M       (a0 = p, a1 = m)
-  OP_UNFOLD = 3,      // G[m][l+i] = E_i + O_i, G[m][l-1-i] = E_i - O_i; E = buf2 (M = rows kept
-                      //   for p = 0), O = buf3 (K = rows kept for p = 1)    (a1 = m)
-  OP_FOLD = 4,        // buf2[i] = s_i (G[m][l+i] + G[m][l-1-i]), buf3[i] = s_i (G[m][l+i] - G[m][l-1-i]),
-                      //   i < l, s_i = optional per-node prescale        (a1 = m)
-  OP_CLEAR = 5,       // buf[out_buf][oo .. oo + M) = 0
+  OP_GATHER = 1,      // buf[out_buf][oo + j] = beta^m_{m+p+2(oo+j)}, j < M       (a0 = p, a1 = m)
+  OP_SCATTER = 2,     // beta^m_{m+p+2(io+j)} = buf[in_buf][io + j], j < M        (a0 = p, a1 = m)
+  OP_FOLD = 3,        // buf[out_buf][oo + j] = s (G[m][l+r] + (-1)^p G[m][l-1-r]), r = oo + j, j < M
+  OP_CLEAR = 4,       // buf[out_buf][oo + j] = 0, j < M
+  OP_GZERO = 5,       // G[m][l+r] = G[m][l-1-r] = 0, r = oo + j, j < M            (a1 = m)
   OP_SYN_INTERP = 6,
   OP_DENSE = 7,
-  OP_ANA_INTERP = 8,
+  OP_DENSE_G = 8,     // (a1 = m)
+  OP_ANA_INTERP = 9,
+  OP_QUIT = 0xFF,
 };
 
 enum OpFlags : uint8_t {
-  F_SYNC_BEFORE = 1,  // all consumer threads synchronize before the op reads its input
-  F_ACCUM = 2,        // DENSE / SYN_INTERP: accumulate into the output instead of overwriting it
-  F_SKEL = 4,         // ANA_INTERP: also add the skeleton pass-through (nskel entries)
+  F_ACCUM = 2,        // DENSE_G / ANA_INTERP: accumulate instead of overwrite
+  F_SKEL = 4,         // ANA_INTERP: also the skeleton pass-through (nskel entries)
 };
 
 struct alignas(16) OpHdr {
   uint32_t bytes;     // size of this op in bytes (multiple of 16); 0 terminates the page
   uint8_t kind;
   uint8_t flags;
-  uint8_t in_buf;     // shared-memory vector ids 0..3
+  uint8_t in_buf;     // shared-memory vector ids 0..1
   uint8_t out_buf;
-  uint16_t M;         // outputs
+  uint16_t M;         // outputs (compute ops, <= 32) or element count (control ops)
   uint16_t K;         // inner dimension
-  uint16_t nskel;     // SYN_INTERP: M (0 on F_ACCUM chunks); ANA_INTERP with F_SKEL: pass-through inputs
+  uint16_t nskel;     // SYN_INTERP: M; ANA_INTERP with F_SKEL: pass-through inputs
   uint16_t io;        // element offset of the input vector
-  uint16_t oo;        // element offset of the output vector
-  uint16_t a0;        // parity for GATHER/SCATTER
-  uint32_t a1;        // order m for control ops
+  uint16_t oo;        // element offset of the output vector / start of a control range
+  uint16_t dep;       // immediately preceding ops this op may overlap (see above)
+  uint16_t a0;        // parity
+  uint16_t pad0;
+  uint32_t a1;        // order m
   uint32_t idx_bytes; // bytes of the index area (padded to 16)
-  uint32_t pad;
 };
 static_assert(sizeof(OpHdr) == 32, "OpHdr must be 32 bytes");
 
 // Index area contents (uint16, offsets relative to io / oo):
-//   SYN_INTERP: red[K] then skel[nskel] (nskel = M, or 0 on accumulated chunks)
+//   SYN_INTERP: red[K] then skel[M]
 //   ANA_INTERP: red[M] then (F_SKEL) skel[nskel]
 //   others:     none
 
 struct UnitEntry {
-  uint64_t first_page;  // index of the unit's first page in the stream
+  uint64_t first_page;  // index of the item's first page in the stream
   uint32_t n_pages;
-  uint32_t m;
+  uint32_t m;           // first order of the item (informational)
 };
 static_assert(sizeof(UnitEntry) == 16, "UnitEntry must be 16 bytes");
 
 // Shared-memory vector ids used by the emitter.
-enum BufId : uint8_t { BUF_A = 0, BUF_B = 1, BUF_E = 2, BUF_O = 3 };
+enum BufId : uint8_t { BUF_A = 0, BUF_B = 1 };
 
-constexpr int kMaxM = 128;            // outputs per op (4 per lane, 32 lanes)
+constexpr int kMaxM = 32;             // outputs per compute op (one warp)
 constexpr int kConsumerWarps = 8;
-constexpr int kConsumerThreads = kConsumerWarps * 32;
+constexpr int kCtlPieces = 8;         // control ops are split into up to this many warp tasks
 
 }  // namespace sht

@@ -5,18 +5,24 @@
 // butterfly of Section 2.2 per parity block) or analysis (the transposed
 // application, Section 2.2 remark after Figure multi).
 //
-// Each CTA is persistent: a producer warp pops orders m from an LPT-sorted
-// work queue (atomic counter) and streams the order's factor pages from HBM
-// into a ring of shared-memory stages with 1-D TMA bulk copies
-// (cp.async.bulk + mbarrier complete_tx); eight consumer warps walk the ops
-// of each page (see sht_stream.h) on vectors kept in shared memory.  Each op
-// is a small GEMV: lanes own consecutive outputs (coalesced, conflict-free
-// reads of the [K][M] value block), warps split the inner dimension, and
-// partial sums are combined through shared memory after one named barrier.
+// Each CTA is persistent and runs a small dataflow scheduler:
+//   * a producer warp pops work items (orders m) from an LPT-sorted queue
+//     (atomic counter) and streams their factor pages from HBM into a ring of
+//     shared-memory stages with 1-D TMA bulk copies (cp.async.bulk, mbarrier
+//     complete_tx);
+//   * a parser warp numbers the ops of every landed page and publishes them
+//     in an op directory;
+//   * eight consumer warps each claim the next op number, wait until the ops
+//     it depends on have completed (the op's `dep` field: ops of one
+//     butterfly level are independent and run concurrently), and execute it
+//     alone: lanes own consecutive outputs (coalesced reads of the [K][M]
+//     value block), tiny ops split the inner dimension over a few lanes and
+//     reduce with warp shuffles.  No CTA-wide barrier is needed per op; the
+//     last warp to finish an op of a page returns the page to the producer.
 //
 // Every wait is bounded: on timeout the kernel records SHT_ERR_TIMEOUT in the
-// device status word, stops issuing copies, waits (bounded) for the copies it
-// already issued, and returns.
+// device status word, raises the CTA abort flag, stops issuing copies, waits
+// (bounded) for the copies it already issued, and returns.
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -27,7 +33,9 @@
 namespace sht {
 namespace {
 
-constexpr int kOpQuit = 0xFF;
+constexpr int kThreads = (kConsumerWarps + 2) * 32;  // consumers + producer + parser
+constexpr int kMaxStages = 16;
+constexpr int kDir = 1024;                            // op directory entries (ring)
 constexpr long long kTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr unsigned kStatusTimeout = 5;              // SHT_ERR_TIMEOUT
 
@@ -66,9 +74,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
-}
-__device__ __forceinline__ void consumer_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kConsumerThreads) : "memory");
 }
 
 // Bounded wait on an mbarrier phase; on timeout records the status, raises
@@ -113,6 +118,9 @@ struct TF64 {
   }
   __device__ static C to_c(const Acc& a) { return make_double2(a.re, a.im); }
   __device__ static Acc from_c(const C& c) { return {c.x, c.y}; }
+  __device__ static Acc shfl_xor(const Acc& a, int off) {
+    return {__shfl_xor_sync(0xffffffffu, a.re, off), __shfl_xor_sync(0xffffffffu, a.im, off)};
+  }
   __device__ static C from_io(const IO& v) { return v; }
   __device__ static IO to_io(const C& c) { return c; }
   __device__ static IO io_zero() { return make_double2(0.0, 0.0); }
@@ -175,6 +183,10 @@ struct TS32 {
     return make_float4(a.rh, a.rl, a.ih, a.il);
   }
   __device__ static Acc from_c(const C& c) { return {c.x, c.y, c.z, c.w}; }
+  __device__ static Acc shfl_xor(const Acc& a, int off) {
+    return {__shfl_xor_sync(0xffffffffu, a.rh, off), __shfl_xor_sync(0xffffffffu, a.rl, off),
+            __shfl_xor_sync(0xffffffffu, a.ih, off), __shfl_xor_sync(0xffffffffu, a.il, off)};
+  }
   __device__ static C from_io(const IO& v) {
     const float rh = __double2float_rn(v.x);
     const float ih = __double2float_rn(v.y);
@@ -216,6 +228,9 @@ struct TF32 {
   }
   __device__ static C to_c(const Acc& a) { return make_float2(a.re, a.im); }
   __device__ static Acc from_c(const C& c) { return {c.x, c.y}; }
+  __device__ static Acc shfl_xor(const Acc& a, int off) {
+    return {__shfl_xor_sync(0xffffffffu, a.re, off), __shfl_xor_sync(0xffffffffu, a.im, off)};
+  }
   __device__ static C from_io(const IO& v) { return v; }
   __device__ static IO to_io(const C& c) { return c; }
   __device__ static IO io_zero() { return make_float2(0.f, 0.f); }
@@ -230,164 +245,216 @@ struct TF32 {
   }
 };
 
+// ------------------------------------------------------------ scheduler
+
+// Shared scheduling state of one CTA.
+struct Sched {
+  int n_ready;    // ops published by the parser (op numbers 0 .. n_ready-1)
+  int n_claimed;  // next op number to hand to a consumer warp
+  int n_done;     // ops completed
+  int quit;       // number of the QUIT op once parsed, else -1
+  int abort;      // set when a bounded wait gave up
+  int pending[kMaxStages];  // ops of the page in each stage not yet completed
+  uint32_t dir[kDir];       // op number % kDir -> (stage << 16) | (byte offset / 16)
+};
+
+__device__ __forceinline__ int vload(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+__device__ __forceinline__ void vstore(int* p, int v) { *reinterpret_cast<volatile int*>(p) = v; }
+
+// Lane 0 polls until pred() holds (bounded), the warp then agrees on the outcome.
+template <class Pred>
+__device__ __forceinline__ bool warp_wait(Pred pred, Sched* S, unsigned* status, int lane) {
+  int ok = 1;
+  if (lane == 0) {
+    if (!pred()) {
+      const long long t0 = clock64();
+      for (;;) {
+        if (pred()) break;
+        if (vload(&S->abort)) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > kTimeoutCycles) {
+          atomicCAS(status, 0u, kStatusTimeout);
+          vstore(&S->abort, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __threadfence_block();  // acquire what the producing warps wrote before publishing
+  return ok != 0;
+}
+
 // ------------------------------------------------------------ ops
 
 template <class TR>
-struct Smem {
+struct Vecs {
   using C = typename TR::C;
   C* base;
-  int buf_ab, l;
-  __device__ C* buf(int id) const {
-    return id < 2 ? base + (size_t)id * buf_ab : base + 2 * (size_t)buf_ab + (size_t)(id - 2) * l;
-  }
-  __device__ C* part(int area) const { return base + 2 * (size_t)buf_ab + 2 * (size_t)l + (size_t)area * kConsumerThreads; }
+  int buf_ab;
+  __device__ C* buf(int id) const { return base + (size_t)id * buf_ab; }
 };
 
 __device__ __forceinline__ size_t tri_off(int m, int L) { return (size_t)m * L - (size_t)m * (m - 1) / 2; }
 
+// One compute op (SYN_INTERP, DENSE, DENSE_G, ANA_INTERP), executed by one warp.
 template <class TR>
-__device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, const Smem<TR>& S, int area, int ct,
-                                         int cw, int lane) {
+__device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, const Vecs<TR>& S, const SweepArgs& A,
+                                         int lane) {
   using C = typename TR::C;
   using V = typename TR::V;
   using Acc = typename TR::Acc;
+  using IO = typename TR::IO;
   const int M = h.M, K = h.K;
   const uint16_t* idx = reinterpret_cast<const uint16_t*>(op + sizeof(OpHdr));
   const V* val = reinterpret_cast<const V*>(op + sizeof(OpHdr) + h.idx_bytes);
   const C* in = S.buf(h.in_buf) + h.io;
   C* out = S.buf(h.out_buf) + h.oo;
-  C* part = S.part(area);
   const bool gather = (h.kind == OP_SYN_INTERP);
-  int nsl = kConsumerWarps;
+  const bool accum = (h.flags & F_ACCUM) != 0;
   if (M > 0) {
-    const int wo = (M + 31) >> 5;  // 1..4 warps across the outputs
-    nsl = kConsumerWarps / wo;     // warps along the inner dimension
-    const int o = lane + 32 * (cw % wo);
-    const int sl = cw / wo;
-    if (sl < nsl && o < M) {
-      Acc a0 = TR::zero(), a1 = TR::zero();
-      int s = sl;
-      for (; s + nsl < K; s += 2 * nsl) {
-        const int s1 = s + nsl;
-        const int i0 = gather ? (int)idx[s] : s;
-        const int i1 = gather ? (int)idx[s1] : s1;
+    // lanes per output: the largest power of two ks with ks * M <= 32
+    int lks = 0;
+    while (((2 << lks) * M) <= 32) ++lks;
+    const int ks = 1 << lks;
+    const int o = lane >> lks, q = lane & (ks - 1);
+    Acc a0 = TR::zero(), a1 = TR::zero();
+    if (o < M) {
+      int s = q;
+      for (; s + ks < K; s += 2 * ks) {
+        const int s1 = s + ks;
         const V v0 = val[(size_t)s * M + o];
         const V v1 = val[(size_t)s1 * M + o];
-        TR::fma(a0, v0, in[i0]);
-        TR::fma(a1, v1, in[i1]);
+        const C x0 = in[gather ? (int)idx[s] : s];
+        const C x1 = in[gather ? (int)idx[s1] : s1];
+        TR::fma(a0, v0, x0);
+        TR::fma(a1, v1, x1);
       }
-      if (s < K) {
-        const int i0 = gather ? (int)idx[s] : s;
-        TR::fma(a0, val[(size_t)s * M + o], in[i0]);
-      }
+      if (s < K) TR::fma(a0, val[(size_t)s * M + o], in[gather ? (int)idx[s] : s]);
       TR::merge(a0, a1);
-      part[sl * M + o] = TR::to_c(a0);
+    }
+    for (int off = ks >> 1; off > 0; off >>= 1) {
+      const Acc b = TR::shfl_xor(a0, off);
+      TR::merge(a0, b);
+    }
+    if (q == 0 && o < M) {
+      switch (h.kind) {
+        case OP_SYN_INTERP:
+          TR::add(a0, in[idx[K + o]]);
+          out[o] = TR::to_c(a0);
+          break;
+        case OP_DENSE:
+          out[o] = TR::to_c(a0);
+          break;
+        case OP_ANA_INTERP: {
+          const int pos = idx[o];
+          if (accum) TR::add(a0, out[pos]);
+          out[pos] = TR::to_c(a0);
+          break;
+        }
+        case OP_DENSE_G: {
+          const int l = A.l;
+          const int i = h.oo + o;
+          IO v = TR::to_io(TR::to_c(a0));
+          if (A.twiddle) v = TR::io_cmul(v, A.twiddle[h.a1]);
+          IO* G = reinterpret_cast<IO*>(A.out) + (size_t)h.a1 * (2 * l);
+          if (accum) {
+            G[l + i] = TR::io_add(G[l + i], v);
+            G[l - 1 - i] = TR::io_sub(G[l - 1 - i], v);
+          } else {
+            G[l + i] = v;
+            G[l - 1 - i] = v;
+          }
+          break;
+        }
+        default:
+          break;
+      }
     }
   }
-  // indices needed after the barrier are read now (the page may be recycled later)
-  int sk = -1, ri = -1, pt = -1;
-  if (ct < M) {
-    if (gather && ct < h.nskel) sk = idx[K + ct];
-    if (h.kind == OP_ANA_INTERP) ri = idx[ct];
-  }
-  if (h.kind == OP_ANA_INTERP && (h.flags & F_SKEL) && ct < h.nskel) pt = idx[M + ct];
-  consumer_sync();
-  if (ct < M) {
-    Acc r = TR::from_c(part[ct]);
-    for (int q = 1; q < nsl; ++q) TR::add(r, part[q * M + ct]);
-    if (h.kind == OP_ANA_INTERP) {
-      TR::add(r, out[ri]);
-      out[ri] = TR::to_c(r);
-    } else {
-      if (sk >= 0) TR::add(r, in[sk]);
-      if (h.flags & F_ACCUM) TR::add(r, out[ct]);
-      out[ct] = TR::to_c(r);
+  if (h.kind == OP_ANA_INTERP && (h.flags & F_SKEL)) {
+    const uint16_t* skel = idx + M;
+    for (int t = lane; t < h.nskel; t += 32) {
+      const int pos = skel[t];
+      if (accum) {
+        Acc r = TR::from_c(out[pos]);
+        TR::add(r, in[t]);
+        out[pos] = TR::to_c(r);
+      } else {
+        out[pos] = in[t];
+      }
     }
-  }
-  if (pt >= 0) {
-    Acc r = TR::from_c(out[pt]);
-    TR::add(r, in[ct]);
-    out[pt] = TR::to_c(r);
   }
 }
 
+// One control op over the element range [oo, oo + M), executed by one warp.
 template <class TR>
-__device__ __forceinline__ void run_control(const OpHdr& h, const SweepArgs& A, const Smem<TR>& S, int ct) {
+__device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, const SweepArgs& A, int lane) {
   using C = typename TR::C;
   using IO = typename TR::IO;
   const int l = A.l, L = 2 * l;
   const int m = (int)h.a1;
+  const int n = h.M;
   switch (h.kind) {
     case OP_GATHER: {
       const IO* beta = reinterpret_cast<const IO*>(A.in) + tri_off(m, L) + h.a0;
-      C* dst = S.buf(h.out_buf) + h.oo;
-      for (int j = ct; j < h.M; j += kConsumerThreads) dst[j] = TR::from_io(beta[2 * (size_t)j]);
+      C* dst = S.buf(h.out_buf);
+      for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::from_io(beta[2 * (size_t)j]);
       break;
     }
     case OP_SCATTER: {
       IO* beta = reinterpret_cast<IO*>(A.out) + tri_off(m, L) + h.a0;
-      const C* src = S.buf(h.in_buf) + h.io;
-      for (int j = ct; j < h.M; j += kConsumerThreads) beta[2 * (size_t)j] = TR::to_io(src[j]);
-      break;
-    }
-    case OP_UNFOLD: {
-      IO* G = reinterpret_cast<IO*>(A.out) + (size_t)m * L;
-      const C* E = S.buf(BUF_E);
-      const C* O = S.buf(BUF_O);
-      const double2 tw = A.twiddle ? A.twiddle[m] : make_double2(1.0, 0.0);
-      for (int i = ct; i < l; i += kConsumerThreads) {
-        const IO e = i < h.M ? TR::to_io(E[i]) : TR::io_zero();
-        const IO o = i < h.K ? TR::to_io(O[i]) : TR::io_zero();
-        IO gp = TR::io_add(e, o), gm = TR::io_sub(e, o);
-        if (A.twiddle) {
-          gp = TR::io_cmul(gp, tw);
-          gm = TR::io_cmul(gm, tw);
-        }
-        G[l + i] = gp;
-        G[l - 1 - i] = gm;
-      }
+      const C* src = S.buf(h.in_buf);
+      for (int j = h.io + lane; j < h.io + n; j += 32) beta[2 * (size_t)j] = TR::to_io(src[j]);
       break;
     }
     case OP_FOLD: {
       const IO* G = reinterpret_cast<const IO*>(A.in) + (size_t)m * L;
-      C* E = S.buf(BUF_E);
-      C* O = S.buf(BUF_O);
-      const double2 tw = A.twiddle ? A.twiddle[m] : make_double2(1.0, 0.0);
-      for (int i = ct; i < l; i += kConsumerThreads) {
-        IO gp = G[l + i], gm = G[l - 1 - i];
+      C* dst = S.buf(h.out_buf);
+      for (int r = h.oo + lane; r < h.oo + n; r += 32) {
+        IO gp = G[l + r], gm = G[l - 1 - r];
         if (A.twiddle) {
-          gp = TR::io_cmul(gp, tw);
-          gm = TR::io_cmul(gm, tw);
+          gp = TR::io_cmul(gp, A.twiddle[m]);
+          gm = TR::io_cmul(gm, A.twiddle[m]);
         }
-        IO e = TR::io_add(gp, gm), o = TR::io_sub(gp, gm);
-        if (A.prescale) {
-          e = TR::io_scale(e, A.prescale[i]);
-          o = TR::io_scale(o, A.prescale[i]);
-        }
-        E[i] = TR::from_io(e);
-        O[i] = TR::from_io(o);
+        IO e = h.a0 ? TR::io_sub(gp, gm) : TR::io_add(gp, gm);
+        if (A.prescale) e = TR::io_scale(e, A.prescale[r]);
+        dst[r] = TR::from_io(e);
       }
       break;
     }
     case OP_CLEAR: {
-      C* dst = S.buf(h.out_buf) + h.oo;
-      for (int j = ct; j < h.M; j += kConsumerThreads) dst[j] = TR::czero();
+      C* dst = S.buf(h.out_buf);
+      for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::czero();
+      break;
+    }
+    case OP_GZERO: {
+      IO* G = reinterpret_cast<IO*>(A.out) + (size_t)m * L;
+      for (int r = h.oo + lane; r < h.oo + n; r += 32) {
+        G[l + r] = TR::io_zero();
+        G[l - 1 - r] = TR::io_zero();
+      }
       break;
     }
     default:
       break;
   }
-  consumer_sync();
 }
 
-__device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* full, uint64_t* empty,
-                              volatile int* abort_flag) {
+// ------------------------------------------------------------ roles
+
+__device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* full, uint64_t* empty, Sched* S) {
   const uint32_t PB = (uint32_t)A.page_bytes;
   const int NST = A.nstages;
+  volatile int* abort_flag = &S->abort;
   int stage = 0;
   uint32_t phase = 0;
-  int issued_phase[16];
-  for (int s = 0; s < 16; ++s) issued_phase[s] = -1;
+  int issued_phase[kMaxStages];
+  for (int s = 0; s < kMaxStages; ++s) issued_phase[s] = -1;
   bool ok = true;
   for (;;) {
     if (*abort_flag) {
@@ -401,7 +468,7 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
       break;
     }
     const UnitEntry e = A.units[u];
-    for (uint32_t pg = 0; pg < e.n_pages && ok; ++pg) {
+    for (uint32_t pg = 0; pg < e.n_pages; ++pg) {
       if (!wait_bounded(empty + stage, phase ^ 1u, A.status, abort_flag)) {
         ok = false;
         break;
@@ -426,8 +493,96 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
     if (issued_phase[s] >= 0) wait_bounded(full + s, (uint32_t)issued_phase[s], A.status, abort_flag);
 }
 
+__device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* full, Sched* S) {
+  const size_t PB = (size_t)A.page_bytes;
+  const int NST = A.nstages;
+  int stage = 0, ticket = 0;
+  uint32_t phase = 0;
+  for (;;) {
+    if (!wait_bounded(full + stage, phase, A.status, &S->abort)) return;
+    const uint8_t* page = stages + (size_t)stage * PB;
+    int count = 0;
+    bool quit = false;
+    for (size_t off = 0; off + sizeof(OpHdr) <= PB;) {
+      const OpHdr* h = reinterpret_cast<const OpHdr*>(page + off);
+      if (h->bytes == 0) break;
+      if (h->kind == OP_QUIT) {
+        quit = true;
+        break;
+      }
+      ++count;
+      off += h->bytes;
+    }
+    vstore(&S->pending[stage], count);
+    size_t off = 0;
+    for (int i = 0; i < count; ++i) {
+      // keep the directory ring from overwriting entries still in use
+      if (ticket - vload(&S->n_done) >= kDir) {
+        const long long t0 = clock64();
+        while (ticket - vload(&S->n_done) >= kDir) {
+          if (vload(&S->abort)) return;
+          if (clock64() - t0 > kTimeoutCycles) {
+            atomicCAS(A.status, 0u, kStatusTimeout);
+            vstore(&S->abort, 1);
+            return;
+          }
+          __nanosleep(64);
+        }
+      }
+      S->dir[ticket % kDir] = ((uint32_t)stage << 16) | (uint32_t)(off >> 4);
+      ++ticket;
+      __threadfence_block();
+      vstore(&S->n_ready, ticket);
+      off += reinterpret_cast<const OpHdr*>(page + off)->bytes;
+    }
+    if (quit) {
+      __threadfence_block();
+      vstore(&S->quit, ticket);
+      return;
+    }
+    if (++stage == NST) {
+      stage = 0;
+      phase ^= 1u;
+    }
+  }
+}
+
 template <class TR>
-__global__ void __launch_bounds__(kConsumerThreads + 32) bfly_sweep_kernel(const SweepArgs A) {
+__device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* empty, Sched* S,
+                              const Vecs<TR>& V, int lane) {
+  const size_t PB = (size_t)A.page_bytes;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(&S->n_claimed, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (!warp_wait([&] {
+          const int q = vload(&S->quit);
+          return vload(&S->n_ready) > t || (q >= 0 && t >= q);
+        }, S, A.status, lane))
+      return;
+    const int q = vload(&S->quit);
+    if (q >= 0 && t >= q) return;
+    const uint32_t e = S->dir[t % kDir];
+    const int stage = (int)(e >> 16);
+    const uint8_t* op = stages + (size_t)stage * PB + ((size_t)(e & 0xffffu) << 4);
+    const OpHdr h = *reinterpret_cast<const OpHdr*>(op);
+    const int need = t - (int)h.dep;
+    if (!warp_wait([&] { return vload(&S->n_done) >= need; }, S, A.status, lane)) return;
+    if (h.kind >= OP_SYN_INTERP)
+      run_gemv<TR>(h, op, V, A, lane);
+    else
+      run_control<TR>(h, V, A, lane);
+    __threadfence_block();  // release this op's results before counting it done
+    __syncwarp();
+    if (lane == 0) {
+      atomicAdd(&S->n_done, 1);
+      if (atomicSub(&S->pending[stage], 1) == 1) mbar_arrive(empty + stage);
+    }
+  }
+}
+
+template <class TR>
+__global__ void __launch_bounds__(kThreads) bfly_sweep_kernel(const SweepArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int NST = A.nstages;
@@ -435,77 +590,46 @@ __global__ void __launch_bounds__(kConsumerThreads + 32) bfly_sweep_kernel(const
   uint8_t* stages = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * PB);
   uint64_t* empty = full + NST;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NST);
-  const size_t vec_off = ((size_t)NST * PB + 16 * (size_t)NST + 16 + 127) & ~size_t(127);
-  Smem<TR> S{reinterpret_cast<typename TR::C*>(smem + vec_off), A.buf_ab, A.l};
+  Sched* S = reinterpret_cast<Sched*>(empty + NST);
+  const size_t vec_off = ((size_t)NST * PB + 16 * (size_t)NST + sizeof(Sched) + 127) & ~size_t(127);
+  const Vecs<TR> V{reinterpret_cast<typename TR::C*>(smem + vec_off), A.buf_ab};
 
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
-    *abort_flag = 0;
+    S->n_ready = 0;
+    S->n_claimed = 0;
+    S->n_done = 0;
+    S->quit = -1;
+    S->abort = 0;
     fence_mbar_init();
   }
   __syncthreads();
 
   if (warp == kConsumerWarps) {
-    if (lane == 0) producer_loop(A, stages, full, empty, abort_flag);
-    return;
-  }
-
-  // one consumer performs the bounded wait and broadcasts the outcome, so
-  // that all consumers leave together if it gives up (none is left waiting
-  // in a named barrier)
-  volatile int* page_ok = abort_flag + 1;
-  int stage = 0, area = 0;
-  uint32_t phase = 0;
-  for (;;) {
-    if (tid == 0) *page_ok = wait_bounded(full + stage, phase, A.status, abort_flag) ? 1 : 0;
-    consumer_sync();
-    if (!*page_ok) break;
-    mbar_try_wait(full + stage, phase);  // completed already: each thread's own acquire of the page
-    const uint8_t* page = stages + (size_t)stage * PB;
-    bool quit = false;
-    for (size_t off = 0; off + sizeof(OpHdr) <= PB;) {
-      const OpHdr h = *reinterpret_cast<const OpHdr*>(page + off);
-      if (h.bytes == 0) break;
-      if (h.kind == kOpQuit) {
-        quit = true;
-        break;
-      }
-      if (h.flags & F_SYNC_BEFORE) consumer_sync();
-      if (h.kind >= OP_SYN_INTERP) {
-        run_gemv<TR>(h, page + off, S, area, tid, warp, lane);
-        area ^= 1;
-      } else {
-        run_control<TR>(h, A, S, tid);
-      }
-      off += h.bytes;
-    }
-    consumer_sync();  // every consumer is done with this page
-    if (tid == 0) mbar_arrive(empty + stage);
-    if (++stage == NST) {
-      stage = 0;
-      phase ^= 1u;
-    }
-    if (quit) break;
+    if (lane == 0) producer_loop(A, stages, full, empty, S);
+  } else if (warp == kConsumerWarps + 1) {
+    if (lane == 0) parser_loop(A, stages, full, S);
+  } else {
+    consumer_loop<TR>(A, stages, empty, S, V, lane);
   }
 }
 
 template <class TR>
-size_t smem_for(int page_bytes, int nstages, int buf_ab, int l) {
-  const size_t vec_off = ((size_t)nstages * page_bytes + 16 * (size_t)nstages + 16 + 127) & ~size_t(127);
-  return vec_off + sizeof(typename TR::C) * (2 * (size_t)buf_ab + 2 * (size_t)l + 2 * (size_t)kConsumerThreads);
+size_t smem_for(int page_bytes, int nstages, int buf_ab) {
+  const size_t vec_off = ((size_t)nstages * page_bytes + 16 * (size_t)nstages + sizeof(Sched) + 127) & ~size_t(127);
+  return vec_off + sizeof(typename TR::C) * 2 * (size_t)buf_ab;
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int l) {
+size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int /*l*/) {
   switch (prec) {
-    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab, l);
-    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab, l);
-    default: return smem_for<TS32>(page_bytes, nstages, buf_ab, l);
+    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab);
+    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab);
+    default: return smem_for<TS32>(page_bytes, nstages, buf_ab);
   }
 }
 
@@ -522,22 +646,21 @@ cudaError_t sweep_configure(int prec, size_t smem) {
 
 int sweep_blocks_per_sm(int prec, size_t smem) {
   int nb = 0;
-  const int threads = kConsumerThreads + 32;
   cudaError_t e;
   switch (prec) {
-    case PREC_FP64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TF64>, threads, smem); break;
-    case PREC_FP32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TF32>, threads, smem); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TS32>, threads, smem); break;
+    case PREC_FP64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TF64>, kThreads, smem); break;
+    case PREC_FP32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TF32>, kThreads, smem); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TS32>, kThreads, smem); break;
   }
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
 cudaError_t sweep_launch(int prec, const SweepArgs& a, int grid, size_t smem, cudaStream_t st) {
-  const dim3 block(kConsumerThreads + 32);
+  if (a.nstages < 1 || a.nstages > kMaxStages) return cudaErrorInvalidValue;
   switch (prec) {
-    case PREC_FP64: bfly_sweep_kernel<TF64><<<grid, block, smem, st>>>(a); break;
-    case PREC_FP32: bfly_sweep_kernel<TF32><<<grid, block, smem, st>>>(a); break;
-    default: bfly_sweep_kernel<TS32><<<grid, block, smem, st>>>(a); break;
+    case PREC_FP64: bfly_sweep_kernel<TF64><<<grid, kThreads, smem, st>>>(a); break;
+    case PREC_FP32: bfly_sweep_kernel<TF32><<<grid, kThreads, smem, st>>>(a); break;
+    default: bfly_sweep_kernel<TS32><<<grid, kThreads, smem, st>>>(a); break;
   }
   return cudaGetLastError();
 }

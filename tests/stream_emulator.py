@@ -1,25 +1,28 @@
 """Host emulation of the butterfly factor streams (test code).
 
 Decodes the page format documented in paper_0910_5435_gb300/csrc/sht_stream.h
-and applies every op with numpy complex128 arithmetic, in stream order.  It
-separates errors of the host precomputation (nodes, recurrence, IDs, op
-emission) from errors of the CUDA kernels: the kernels must reproduce this
-emulation up to float rounding.
+and applies every op with numpy complex128 arithmetic, in stream order (a
+valid serialization of the kernel's concurrent execution).  It separates
+errors of the host precomputation (nodes, recurrence, IDs, op emission) from
+errors of the CUDA kernels.
+
+``check_races`` verifies the ordering annotations: op t may overlap the ops
+numbered t - dep .. t - 1, so it must neither write anything those ops read or
+write, nor read anything they write.
 """
 
 import numpy as np
 
 OPHDR = np.dtype([
     ("bytes", "<u4"), ("kind", "u1"), ("flags", "u1"), ("in_buf", "u1"), ("out_buf", "u1"),
-    ("M", "<u2"), ("K", "<u2"), ("nskel", "<u2"), ("io", "<u2"), ("oo", "<u2"), ("a0", "<u2"),
-    ("a1", "<u4"), ("idx_bytes", "<u4"), ("pad", "<u4"),
+    ("M", "<u2"), ("K", "<u2"), ("nskel", "<u2"), ("io", "<u2"), ("oo", "<u2"), ("dep", "<u2"),
+    ("a0", "<u2"), ("pad0", "<u2"), ("a1", "<u4"), ("idx_bytes", "<u4"),
 ])
 assert OPHDR.itemsize == 32
 
-OP_GATHER, OP_SCATTER, OP_UNFOLD, OP_FOLD, OP_CLEAR, OP_SYN, OP_DENSE, OP_ANA = range(1, 9)
+OP_GATHER, OP_SCATTER, OP_FOLD, OP_CLEAR, OP_GZERO, OP_SYN, OP_DENSE, OP_DENSE_G, OP_ANA = range(1, 10)
 OP_QUIT = 0xFF
-F_SYNC, F_ACCUM, F_SKEL = 1, 2, 4
-BUF_A, BUF_B, BUF_E, BUF_O = range(4)
+F_ACCUM, F_SKEL = 2, 4
 
 
 def iter_ops(stream, page_bytes):
@@ -50,82 +53,146 @@ def decode_values(vals, prec, n):
     return hl[0::2] + hl[1::2]
 
 
-def emulate(stream, page_bytes, l, prec, direction, inp, prescale=None):
+def _tri(l):
+    L = 2 * l
+    return np.concatenate([[0], np.cumsum(L - np.arange(L))])
+
+
+def emulate(stream, page_bytes, l, prec, direction, inp, prescale=None, twiddle=None):
     """Applies a whole stream.  direction 0: inp = beta triangle -> G (2l, 2l);
     direction 1: inp = G -> beta triangle."""
     L = 2 * l
     size = 8 * L + 64
-    bufs = [np.zeros(size, dtype=np.complex128) for _ in range(4)]
-    tri = np.concatenate([[0], np.cumsum(L - np.arange(L))])
+    bufs = [np.zeros(size, dtype=np.complex128) for _ in range(2)]
+    tri = _tri(l)
     if direction == 0:
-        out = np.zeros((L, L), dtype=np.complex128)
+        G = np.full((L, L), np.nan, dtype=np.complex128)
         beta = np.asarray(inp, dtype=np.complex128)
     else:
-        out = np.zeros(tri[-1], dtype=np.complex128)
+        beta = np.full(tri[-1], np.nan, dtype=np.complex128)
         G = np.asarray(inp, dtype=np.complex128)
     for h, idx, vals in iter_ops(stream, page_bytes):
         kind, M, K = int(h["kind"]), int(h["M"]), int(h["K"])
         io, oo = int(h["io"]), int(h["oo"])
-        m = int(h["a1"])
+        m, p = int(h["a1"]), int(h["a0"])
         src, dst = bufs[int(h["in_buf"])], bufs[int(h["out_buf"])]
+        acc = bool(h["flags"] & F_ACCUM)
+        tw = 1.0 if twiddle is None else twiddle[m]
         if kind == OP_GATHER:
-            p = int(h["a0"])
-            dst[oo:oo + M] = beta[tri[m] + p + 2 * np.arange(M)]
+            dst[oo:oo + M] = beta[tri[m] + p + 2 * (oo + np.arange(M))]
         elif kind == OP_SCATTER:
-            p = int(h["a0"])
-            out[tri[m] + p + 2 * np.arange(M)] = src[io:io + M]
-        elif kind == OP_UNFOLD:
-            E = np.zeros(l, dtype=np.complex128)
-            O = np.zeros(l, dtype=np.complex128)
-            E[:M] = bufs[BUF_E][:M]
-            O[:K] = bufs[BUF_O][:K]
-            out[m, l:] = E + O
-            out[m, :l] = (E - O)[::-1]
+            beta[tri[m] + p + 2 * (io + np.arange(M))] = src[io:io + M]
         elif kind == OP_FOLD:
-            gp = G[m, l:]
-            gm = G[m, :l][::-1]
-            s = np.ones(l) if prescale is None else prescale
-            bufs[BUF_E][:l] = s * (gp + gm)
-            bufs[BUF_O][:l] = s * (gp - gm)
+            r = oo + np.arange(M)
+            sgn = 1.0 if p == 0 else -1.0
+            s = np.ones(M) if prescale is None else prescale[r]
+            dst[oo:oo + M] = s * tw * (G[m, l + r] + sgn * G[m, l - 1 - r])
         elif kind == OP_CLEAR:
             dst[oo:oo + M] = 0
+        elif kind == OP_GZERO:
+            r = oo + np.arange(M)
+            G[m, l + r] = 0
+            G[m, l - 1 - r] = 0
         elif kind == OP_SYN:
             V = decode_values(vals, prec, K * M).reshape(K, M)
             red = idx[:K].astype(int)
-            nsk = int(h["nskel"])
-            skel = idx[K:K + nsk].astype(int)
-            acc = V.T @ src[io + red]
-            if nsk:
-                acc[:nsk] += src[io + skel]
-            if h["flags"] & F_ACCUM:
-                dst[oo:oo + M] += acc
-            else:
-                dst[oo:oo + M] = acc
+            skel = idx[K:K + M].astype(int)
+            dst[oo:oo + M] = V.T @ src[io + red] + src[io + skel]
         elif kind == OP_DENSE:
             V = decode_values(vals, prec, K * M).reshape(K, M)
-            acc = V.T @ src[io:io + K]
-            if h["flags"] & F_ACCUM:
-                dst[oo:oo + M] += acc
+            dst[oo:oo + M] = V.T @ src[io:io + K]
+        elif kind == OP_DENSE_G:
+            V = decode_values(vals, prec, K * M).reshape(K, M)
+            v = tw * (V.T @ src[io:io + K])
+            r = oo + np.arange(M)
+            if acc:
+                G[m, l + r] += v
+                G[m, l - 1 - r] -= v
             else:
-                dst[oo:oo + M] = acc
+                G[m, l + r] = v
+                G[m, l - 1 - r] = v
         elif kind == OP_ANA:
             V = decode_values(vals, prec, K * M).reshape(K, M)
             red = idx[:M].astype(int)
-            acc = V.T @ src[io:io + K]
-            np.add.at(dst, oo + red, acc)
+            res = V.T @ src[io:io + K]
+            if acc:
+                dst[oo + red] += res
+            else:
+                dst[oo + red] = res
             if h["flags"] & F_SKEL:
                 nsk = int(h["nskel"])
                 skel = idx[M:M + nsk].astype(int)
-                np.add.at(dst, oo + skel, src[io:io + nsk])
+                if acc:
+                    dst[oo + skel] += src[io:io + nsk]
+                else:
+                    dst[oo + skel] = src[io:io + nsk]
         else:
             raise ValueError(f"unknown op kind {kind}")
-    return out
+    return G if direction == 0 else beta
+
+
+def _access_sets(h, idx, l):
+    """(reads, writes) of one op as sets of hashable locations."""
+    kind, M, K = int(h["kind"]), int(h["M"]), int(h["K"])
+    io, oo, m, p = int(h["io"]), int(h["oo"]), int(h["a1"]), int(h["a0"])
+    ib, ob = int(h["in_buf"]), int(h["out_buf"])
+    R, W = set(), set()
+    if kind == OP_GATHER:
+        W |= {("buf", ob, oo + j) for j in range(M)}
+        R |= {("beta", m, p + 2 * (oo + j)) for j in range(M)}
+    elif kind == OP_SCATTER:
+        R |= {("buf", ib, io + j) for j in range(M)}
+        W |= {("beta", m, p + 2 * (io + j)) for j in range(M)}
+    elif kind == OP_FOLD:
+        W |= {("buf", ob, oo + j) for j in range(M)}
+        R |= {("G", m, l + oo + j) for j in range(M)} | {("G", m, l - 1 - oo - j) for j in range(M)}
+    elif kind == OP_CLEAR:
+        W |= {("buf", ob, oo + j) for j in range(M)}
+    elif kind == OP_GZERO:
+        W |= {("G", m, l + oo + j) for j in range(M)} | {("G", m, l - 1 - oo - j) for j in range(M)}
+    elif kind == OP_SYN:
+        R |= {("buf", ib, io + int(s)) for s in idx[:K + M]}
+        W |= {("buf", ob, oo + o) for o in range(M)}
+    elif kind == OP_DENSE:
+        R |= {("buf", ib, io + s) for s in range(K)}
+        W |= {("buf", ob, oo + o) for o in range(M)}
+    elif kind == OP_DENSE_G:
+        R |= {("buf", ib, io + s) for s in range(K)}
+        rows = {("G", m, l + oo + o) for o in range(M)} | {("G", m, l - 1 - oo - o) for o in range(M)}
+        W |= rows
+        if h["flags"] & F_ACCUM:
+            R |= rows
+    elif kind == OP_ANA:
+        R |= {("buf", ib, io + s) for s in range(K)}
+        outs = {("buf", ob, oo + int(r)) for r in idx[:M]}
+        if h["flags"] & F_SKEL:
+            nsk = int(h["nskel"])
+            outs |= {("buf", ob, oo + int(s)) for s in idx[M:M + nsk]}
+        W |= outs
+        if h["flags"] & F_ACCUM:
+            R |= outs
+    return R, W
+
+
+def check_races(stream, page_bytes, l):
+    """Returns a list of (t, u) op pairs that may overlap but conflict."""
+    ops = list(iter_ops(stream, page_bytes))
+    sets = [_access_sets(h, idx, l) for h, idx, _ in ops]
+    bad = []
+    for t, (h, _, _) in enumerate(ops):
+        dep = int(h["dep"])
+        Rt, Wt = sets[t]
+        for u in range(max(0, t - dep), t):
+            Ru, Wu = sets[u]
+            if (Wt & (Ru | Wu)) or (Rt & Wu):
+                bad.append((t, u))
+    return bad
 
 
 def op_stats(stream, page_bytes):
-    """Counts ops per kind and value bytes, for plan diagnostics."""
+    """Counts ops per kind, for plan diagnostics."""
     counts = {}
-    for h, _, vals in iter_ops(stream, page_bytes):
+    for h, _, _ in iter_ops(stream, page_bytes):
         k = int(h["kind"])
         counts[k] = counts.get(k, 0) + 1
     return counts

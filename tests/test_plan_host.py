@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_0910_5435_gb300 import inputs, sht
-from tests.stream_emulator import emulate, iter_ops
+from tests.stream_emulator import check_races, emulate, iter_ops
 
 PB = 16384
 
@@ -67,7 +67,9 @@ def test_butterfly_levels_are_exercised():
     assert s["factor_values"] < s["dense_values"]
     assert 0 < s["k_avg"] <= s["k_max"] <= 128
     kinds = {int(h["kind"]) for h, _, _ in iter_ops(P.stream(0, 0), PB)}
-    assert {1, 3, 6, 7} <= kinds  # gather, unfold, interpolation, dense final blocks
+    assert {1, 6, 8} <= kinds  # gather, interpolation, final blocks written to G
+    kinds = {int(h["kind"]) for h, _, _ in iter_ops(P.stream(0, 1), PB)}
+    assert {2, 3, 7, 9} <= kinds  # scatter, fold, final blocks, anterpolation
 
 
 def test_rank_property_grows_with_eps():
@@ -120,3 +122,38 @@ def test_stats_follow_paper_columns():
     assert s["k_sigma"] >= 0
     assert s["max_abs_T"] < 1e3
     assert math.isfinite(s["k_avg"])
+
+
+@pytest.mark.parametrize("l,C", [(4, 2), (16, 4), (64, 16), (64, 64)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_op_ordering_is_race_free(l, C, prec):
+    """Race detection for the concurrent sweep: every op may overlap the ops
+    its `dep` field names; none of them may write what it reads or writes,
+    nor read what it writes (sht_stream.h ordering rule)."""
+    P = sht.Plan(l, 1e-12, leaf_cols=C, host_only=True)
+    for d in (0, 1):
+        assert check_races(P.stream(prec, d), PB, l) == []
+
+
+def test_race_checker_catches_a_planted_overlap():
+    """The checker itself: widening one op's overlap window by one op in a
+    real stream (a gather overlapping the op before it) must be reported."""
+    import numpy as np
+    from tests.stream_emulator import OPHDR
+    P = sht.Plan(16, 1e-12, leaf_cols=4, host_only=True)
+    st = P.stream(0, 0).copy()
+    # find the second gather (first op of the odd parity) and let it overlap its predecessor
+    off, seen = 0, 0
+    for pg in range(len(st) // PB):
+        base = pg * PB
+        off = 0
+        while off + 32 <= PB:
+            h = st[base + off:base + off + 32].view(OPHDR)
+            if h[0]["bytes"] == 0:
+                break
+            if h[0]["kind"] == 1 and h[0]["a0"] == 1 and h[0]["oo"] == 0:
+                h[0]["dep"] = 1
+                assert check_races(st, PB, 16) != []
+                return
+            off += int(h[0]["bytes"])
+    raise AssertionError("no odd-parity gather found")
