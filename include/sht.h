@@ -106,6 +106,9 @@ typedef struct {
   /* eps used for the IDs of the SHT_FP32 factors; <= 0 selects
    * max(eps_id, 1e-7).  (FP32 cannot use ranks below its own precision.) */
   double eps_fp32;
+  /* Warps per CTA of the sweep kernels that execute ops (8 or 16; 0 =
+   * default 16).  A tuning knob; results do not depend on it. */
+  int consumer_warps;
 } sht_plan_opts;
 
 typedef struct {

@@ -59,6 +59,7 @@ struct sht_plan_s {
   bool host_only = false;
   int device = -1;
   int num_sms = 0;
+  int consumer_warps = 16;
   int nstages[kNumPrec] = {4, 4, 4};
   int ctas_per_sm[kNumPrec] = {1, 1, 1};
   DevStream dev[kNumPrec][2];
@@ -237,7 +238,7 @@ sht_status upload(sht_plan_t P, int q) {
   for (int nst = 8; nst >= 2; --nst) {
     const size_t sm = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, P->H.l);
     if (sm > (size_t)optin) continue;
-    const int ctas = std::min(2, sht::sweep_blocks_per_sm(q, sm));
+    const int ctas = std::min(2, sht::sweep_blocks_per_sm(q, P->consumer_warps, sm));
     const bool better = (ctas > best_ctas && (nst >= 3 || best_ctas == 0)) || best_ctas == 0;
     if (better) {
       best_nst = nst;
@@ -300,7 +301,7 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.status = P->d_scratch + kNumPrec * KIND_COUNT;
   const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
   (void)cudaGetLastError();  // do not report a stale error left by an earlier call (e.g. inside cuFFT)
-  CK(sht::sweep_launch(q, a, grid, P->smem[q], reinterpret_cast<cudaStream_t>(stream)));
+  CK(sht::sweep_launch(q, P->consumer_warps, a, grid, P->smem[q], reinterpret_cast<cudaStream_t>(stream)));
   return SHT_OK;
 }
 
@@ -334,6 +335,7 @@ sht_status sht_plan_opts_default(sht_plan_opts* o) {
   o->num_threads = 0;
   o->page_bytes = 16384;
   o->eps_fp32 = 0.0;
+  o->consumer_warps = 16;
   return SHT_OK;
 }
 
@@ -356,11 +358,14 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   if (o.leaf_cols < 2 || o.leaf_cols > 1024) return SHT_ERR_INVALID_ARG;
   if (o.page_bytes < 4096 || o.page_bytes > 49152 || (o.page_bytes % 1024) != 0) return SHT_ERR_INVALID_ARG;
   if (o.num_threads < 0) return SHT_ERR_INVALID_ARG;
+  if (o.consumer_warps == 0) o.consumer_warps = 16;
+  if (o.consumer_warps != 8 && o.consumer_warps != 16) return SHT_ERR_INVALID_ARG;
 
   sht_plan_t P = new (std::nothrow) sht_plan_s();
   if (!P) return SHT_ERR_OOM;
   P->opts = o;
   P->host_only = o.host_only != 0;
+  P->consumer_warps = o.consumer_warps;
   PlanHost& H = P->H;
   H.l = l;
   H.eps_id = eps_id;

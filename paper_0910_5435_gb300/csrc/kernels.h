@@ -31,9 +31,9 @@ enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2 };
 
 size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int l);
 cudaError_t sweep_configure(int prec, size_t smem);
-// resident CTAs per SM for this shared-memory size (>= 1)
-int sweep_blocks_per_sm(int prec, size_t smem);
-cudaError_t sweep_launch(int prec, const SweepArgs& a, int grid, size_t smem, cudaStream_t st);
+// resident CTAs per SM for this shared-memory size (>= 1); nw = consumer warps (8 or 16)
+int sweep_blocks_per_sm(int prec, int nw, size_t smem);
+cudaError_t sweep_launch(int prec, int nw, const SweepArgs& a, int grid, size_t smem, cudaStream_t st);
 
 // Direct float64 baseline: dense P-bar blocks, [j][i] per (m, p), i fastest.
 struct DirectArgs {

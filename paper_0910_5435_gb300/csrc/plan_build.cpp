@@ -15,6 +15,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <memory>
 #include <numeric>
 #include <stdexcept>
 #include <thread>
@@ -640,26 +642,30 @@ struct Emitter {
     }
     return lo;
   }
-  // Size of the next piece of an op with `remaining` outputs: pieces are
-  // balanced (an op that needs two pages is cut in halves, not into a full
-  // page plus a sliver); a partly used page takes a smaller piece only if it
-  // keeps at least 8 outputs.
+  // Size of the next piece of an op with `remaining` outputs.  A warp runs
+  // one piece with one lane per output, or several lanes per output when the
+  // piece has <= 16 outputs, so pieces of 32, 16, 8, ... outputs keep every
+  // lane busy; the last piece takes the remainder.  A partly used page takes
+  // a piece only if it keeps at least min(remaining, 8) outputs.
   template <class F>
   int piece(int remaining, F bytes_for) {
-    int lo = 0, hi = std::min(remaining, kMaxM);
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) / 2;
-      if (bytes_for(mid) <= W.PB) lo = mid; else hi = mid - 1;
-    }
-    const int mfresh = lo;
-    if (mfresh <= 0) throw std::logic_error("op does not fit in a page");
-    const int npieces = (remaining + mfresh - 1) / mfresh;
-    const int target = (remaining + npieces - 1) / npieces;
-    int mp = fit(target, bytes_for);
-    if (mp < target && mp < std::min(target, 8)) {
+    auto best_in = [&](size_t space) {
+      // candidates: the whole remainder if it fits in one warp, then 32, 16, 8, ...
+      int cands[8];
+      int nc = 0;
+      if (remaining <= kMaxM) cands[nc++] = remaining;
+      for (int p2 = kMaxM; p2 >= 1; p2 /= 2)
+        if (p2 < remaining || (p2 == remaining && nc == 0)) cands[nc++] = p2;
+      for (int c = 0; c < nc; ++c)
+        if (bytes_for(cands[c]) <= space) return cands[c];
+      return 0;
+    };
+    int mp = best_in(W.space());
+    if (mp < std::min(remaining, 8)) {
       W.new_page();
-      mp = target;
+      mp = best_in(W.PB);
     }
+    if (mp <= 0) throw std::logic_error("op does not fit in a page");
     return mp;
   }
 
@@ -743,8 +749,12 @@ struct Emitter {
   }
 };
 
-inline uint8_t level_buf(int j) { return (j & 1) ? BUF_B : BUF_A; }
-inline uint8_t other_buf(uint8_t b) { return b == BUF_A ? BUF_B : BUF_A; }
+// Shared vectors: parity p uses the pair (A_p, B_p) = (2p, 2p + 1), so the
+// two independent parity butterflies of an order can run interleaved.
+inline uint8_t buf_a(int p) { return (uint8_t)(2 * p); }
+inline uint8_t buf_b(int p) { return (uint8_t)(2 * p + 1); }
+inline uint8_t level_buf(int j, int p) { return (j & 1) ? buf_b(p) : buf_a(p); }
+inline uint8_t other_buf(uint8_t b) { return (uint8_t)(b ^ 1); }
 
 std::vector<const IdBlock*> blocks_at(const UnitFact& U, int j) {
   std::vector<const IdBlock*> v;
@@ -755,6 +765,19 @@ std::vector<const IdBlock*> blocks_at(const UnitFact& U, int j) {
     return (long long)a->k * (a->nin - a->k + 1) > (long long)b->k * (b->nin - b->k + 1);
   });
   return v;
+}
+
+using Stage = std::function<void(Emitter&)>;
+
+// Emits the stages of both parities interleaved: stage i of parity 0 and
+// stage i of parity 1 share one ordering group (they touch disjoint data).
+void emit_interleaved(Emitter& E, const std::vector<Stage> (&st)[2]) {
+  const size_t n = std::max(st[0].size(), st[1].size());
+  for (size_t i = 0; i < n; ++i) {
+    E.new_group();
+    for (int p = 0; p < 2; ++p)
+      if (i < st[p].size()) st[p][i](E);
+  }
 }
 
 // Appends the ops of order m to the page writer (continuing its open page).
@@ -768,31 +791,37 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, PageWriter& W) {
     inv_sq2w[i] = 1.0 / std::sqrt(2.0 * P.w[l + i]);
     sqw2[i] = std::sqrt(0.5 * P.w[l + i]);
   }
+  std::vector<Stage> st[2];
   if (dir == 0) {
+    // synthesis: gather, butterfly levels, then the final blocks write node
+    // values: the even parity first (G = E), the odd parity after it (G +-= O)
+    Stage fin[2];
     for (int p = 0; p < 2; ++p) {
       const UnitFact& U = F[(size_t)m * 2 + p];
       if (U.n == 0) continue;
+      const uint8_t A = buf_a(p);
       const uint8_t gflags = p ? F_ACCUM : 0;
-      E.new_group();
-      OpHdr g = E.hdr(OP_GATHER);
-      g.a0 = (uint16_t)p;
-      g.a1 = (uint32_t)m;
-      g.out_buf = BUF_A;
-      E.control(g, 0, U.n);
-      if (U.rows > 0) {
-        if (U.direct) {
-          // E_i = sum_j P-bar(x_i) x_j: weighted values divided by sqrt(2 w_i)
-          E.new_group();
-          E.dense(OP_DENSE_G, gflags, U.rows, U.n,
-                  [&](int s, int o) { return U.D[(size_t)s * U.rows + o] * inv_sq2w[o]; }, BUF_A, 0, BUF_A, 0, m);
-        } else {
-          for (int j = 1; j <= U.levels + 1; ++j) {
-            E.new_group();
+      st[p].push_back([&U, A, p, m](Emitter& E) {
+        OpHdr g = E.hdr(OP_GATHER);
+        g.a0 = (uint16_t)p;
+        g.a1 = (uint32_t)m;
+        g.out_buf = A;
+        E.control(g, 0, U.n);
+      });
+      if (U.rows > 0 && !U.direct) {
+        for (int j = 1; j <= U.levels + 1; ++j)
+          st[p].push_back([&U, j, p](Emitter& E) {
             for (const IdBlock* b : blocks_at(U, j))
-              if (b->k > 0) E.syn_interp(*b, j == 1 ? BUF_A : level_buf(j - 1), level_buf(j));
-          }
-          E.new_group();
-          const uint8_t top = level_buf(U.levels + 1);
+              if (b->k > 0) E.syn_interp(*b, j == 1 ? buf_a(p) : level_buf(j - 1, p), level_buf(j, p));
+          });
+      }
+      fin[p] = [&U, A, p, m, l, gflags, &inv_sq2w](Emitter& E) {
+        if (U.rows > 0 && U.direct) {
+          // E_i = sum_j P-bar(x_i) x_j: weighted values divided by sqrt(2 w_i)
+          E.dense(OP_DENSE_G, gflags, U.rows, U.n,
+                  [&](int s, int o) { return U.D[(size_t)s * U.rows + o] * inv_sq2w[o]; }, A, 0, A, 0, m);
+        } else if (U.rows > 0) {
+          const uint8_t top = level_buf(U.levels + 1, p);
           std::vector<const FinalBlock*> fs;
           for (const auto& f : U.finals) fs.push_back(&f);
           std::stable_sort(fs.begin(), fs.end(), [](const FinalBlock* a, const FinalBlock* b) {
@@ -803,99 +832,119 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, PageWriter& W) {
             if (f->k == 0 && p == 1) continue;  // adds nothing
             E.dense(OP_DENSE_G, gflags, h, f->k,
                     [&](int s, int o) { return f->S[(size_t)s * h + o] * inv_sq2w[f->r0 + o]; }, top, f->in_off,
-                    BUF_A, f->r0, m);
+                    A, f->r0, m);
           }
         }
-      } else {
-        E.new_group();
-      }
-      if (p == 0 && U.rows < l) {
-        // node rows past the kept ones hold no even part: zero them in the same group
-        OpHdr z = E.hdr(OP_GZERO);
-        z.a1 = (uint32_t)m;
-        E.control(z, U.rows, l - U.rows);
-      }
+        if (p == 0 && U.rows < l) {
+          // node rows past the kept ones hold no even part
+          OpHdr z = E.hdr(OP_GZERO);
+          z.a1 = (uint32_t)m;
+          E.control(z, U.rows, l - U.rows);
+        }
+      };
     }
+    emit_interleaved(E, st);
+    for (int p = 0; p < 2; ++p)
+      if (fin[p]) {
+        E.new_group();
+        fin[p](E);
+      }
   } else {
     for (int p = 0; p < 2; ++p) {
       const UnitFact& U = F[(size_t)m * 2 + p];
       if (U.n == 0) continue;
+      const uint8_t A = buf_a(p), B = buf_b(p);
       if (U.rows == 0) {
-        E.new_group();
-        OpHdr c = E.hdr(OP_CLEAR);
-        c.out_buf = BUF_A;
-        E.control(c, 0, U.n);
+        st[p].push_back([&U, A](Emitter& E) {
+          OpHdr c = E.hdr(OP_CLEAR);
+          c.out_buf = A;
+          E.control(c, 0, U.n);
+        });
       } else {
-        const uint8_t top = U.direct ? BUF_A : level_buf(U.levels + 1);
-        const uint8_t ubuf = U.direct ? BUF_B : other_buf(top);
-        E.new_group();
-        OpHdr f = E.hdr(OP_FOLD);
-        f.a0 = (uint16_t)p;
-        f.a1 = (uint32_t)m;
-        f.out_buf = ubuf;
-        E.control(f, 0, U.rows);
-        E.new_group();
+        const uint8_t top = U.direct ? A : level_buf(U.levels + 1, p);
+        const uint8_t ubuf = U.direct ? B : other_buf(top);
+        st[p].push_back([&U, ubuf, p, m](Emitter& E) {
+          OpHdr f = E.hdr(OP_FOLD);
+          f.a0 = (uint16_t)p;
+          f.a1 = (uint32_t)m;
+          f.out_buf = ubuf;
+          E.control(f, 0, U.rows);
+        });
         if (U.direct) {
           // x_j = sum_i w_i P-bar(x_i) u_i: weighted values times sqrt(w_i / 2)
-          E.dense(OP_DENSE, 0, U.n, U.rows, [&](int s, int o) { return U.D[(size_t)o * U.rows + s] * sqw2[s]; },
-                  ubuf, 0, BUF_A, 0);
+          st[p].push_back([&U, ubuf, A, &sqw2](Emitter& E) {
+            E.dense(OP_DENSE, 0, U.n, U.rows, [&](int s, int o) { return U.D[(size_t)o * U.rows + s] * sqw2[s]; },
+                    ubuf, 0, A, 0);
+          });
         } else {
-          for (const auto& fb : U.finals) {
-            if (fb.k == 0) continue;
-            const int h = fb.r1 - fb.r0;
-            E.dense(OP_DENSE, 0, fb.k, h, [&](int s, int o) { return fb.S[(size_t)o * h + s] * sqw2[fb.r0 + s]; },
-                    ubuf, fb.r0, top, fb.in_off);
-          }
+          st[p].push_back([&U, ubuf, top, &sqw2](Emitter& E) {
+            for (const auto& fb : U.finals) {
+              if (fb.k == 0) continue;
+              const int h = fb.r1 - fb.r0;
+              E.dense(OP_DENSE, 0, fb.k, h, [&](int s, int o) { return fb.S[(size_t)o * h + s] * sqw2[fb.r0 + s]; },
+                      ubuf, fb.r0, top, fb.in_off);
+            }
+          });
           for (int j = U.levels + 1; j >= 2; --j) {
             // blocks of level j come in pairs (top band 2b, bottom band 2b+1) sharing one input
-            // vector z of level j-1; the top halves overwrite z, then the bottom halves add
-            const uint8_t src = level_buf(j), dst = level_buf(j - 1);
-            std::vector<const IdBlock*> tops, bots;
-            for (const IdBlock* b : blocks_at(U, j)) (b->band % 2 == 0 ? tops : bots).push_back(b);
-            auto partner = [&](const IdBlock* t) -> const IdBlock* {
+            // vector z of level j-1: the top halves overwrite z, then the bottom halves add
+            const uint8_t src = level_buf(j, p), dst = level_buf(j - 1, p);
+            auto tops = std::make_shared<std::vector<const IdBlock*>>();
+            auto second = std::make_shared<std::vector<const IdBlock*>>();
+            std::vector<const IdBlock*> bots;
+            for (const IdBlock* b : blocks_at(U, j)) (b->band % 2 == 0 ? *tops : bots).push_back(b);
+            auto firsts = std::make_shared<std::vector<std::pair<const IdBlock*, int>>>();  // (block or top, mode)
+            for (const IdBlock* t : *tops) {
+              const IdBlock* bp = nullptr;
               for (const IdBlock* b : bots)
-                if (b->band == t->band + 1 && b->group == t->group) return b;
-              return nullptr;
-            };
-            E.new_group();
-            std::vector<const IdBlock*> second;
-            for (const IdBlock* t : tops) {
-              const IdBlock* b = partner(t);
+                if (b->band == t->band + 1 && b->group == t->group) bp = b;
               if (t->k > 0) {
-                E.ana_interp(*t, src, dst, false);
-                if (b && b->k > 0) second.push_back(b);
-              } else if (b && b->k > 0) {
-                E.ana_interp(*b, src, dst, false);
+                firsts->push_back({t, 0});
+                if (bp && bp->k > 0) second->push_back(bp);
+              } else if (bp && bp->k > 0) {
+                firsts->push_back({bp, 0});
               } else if (t->nin > 0) {
-                OpHdr c = E.hdr(OP_CLEAR);
-                c.out_buf = dst;
-                E.control(c, t->in_off, t->nin);
+                firsts->push_back({t, 1});  // nothing interpolates into z: clear it
               }
             }
-            if (!second.empty()) {
-              E.new_group();
-              for (const IdBlock* b : second) E.ana_interp(*b, src, dst, true);
-            }
+            st[p].push_back([firsts, src, dst](Emitter& E) {
+              for (const auto& pr : *firsts) {
+                if (pr.second == 0) {
+                  E.ana_interp(*pr.first, src, dst, false);
+                } else {
+                  OpHdr c = E.hdr(OP_CLEAR);
+                  c.out_buf = dst;
+                  E.control(c, pr.first->in_off, pr.first->nin);
+                }
+              }
+            });
+            if (!second->empty())
+              st[p].push_back([second, src, dst](Emitter& E) {
+                for (const IdBlock* b : *second) E.ana_interp(*b, src, dst, true);
+              });
           }
-          E.new_group();
-          for (const IdBlock* b : blocks_at(U, 1)) {
-            if (b->k > 0) {
-              E.ana_interp(*b, BUF_B, BUF_A, false);
-            } else {
-              OpHdr c = E.hdr(OP_CLEAR);
-              c.out_buf = BUF_A;
-              E.control(c, b->in_off, b->nin);
+          st[p].push_back([&U, A, B](Emitter& E) {
+            for (const IdBlock* b : blocks_at(U, 1)) {
+              if (b->k > 0) {
+                E.ana_interp(*b, B, A, false);
+              } else {
+                OpHdr c = E.hdr(OP_CLEAR);
+                c.out_buf = A;
+                E.control(c, b->in_off, b->nin);
+              }
             }
-          }
+          });
         }
       }
-      E.new_group();
-      OpHdr s = E.hdr(OP_SCATTER);
-      s.a0 = (uint16_t)p;
-      s.a1 = (uint32_t)m;
-      s.in_buf = BUF_A;
-      E.control(s, 0, U.n);
+      st[p].push_back([&U, A, p, m](Emitter& E) {
+        OpHdr s = E.hdr(OP_SCATTER);
+        s.a0 = (uint16_t)p;
+        s.a1 = (uint32_t)m;
+        s.in_buf = A;
+        E.control(s, 0, U.n);
+      });
     }
+    emit_interleaved(E, st);
   }
 }
 

@@ -77,7 +77,7 @@ struct alignas(16) OpHdr {
   uint32_t bytes;     // size of this op in bytes (multiple of 16); 0 terminates the page
   uint8_t kind;
   uint8_t flags;
-  uint8_t in_buf;     // shared-memory vector ids 0..1
+  uint8_t in_buf;     // shared-memory vector ids 0..3
   uint8_t out_buf;
   uint16_t M;         // outputs (compute ops, <= 32) or element count (control ops)
   uint16_t K;         // inner dimension
@@ -104,8 +104,10 @@ struct UnitEntry {
 };
 static_assert(sizeof(UnitEntry) == 16, "UnitEntry must be 16 bytes");
 
-// Shared-memory vector ids used by the emitter.
-enum BufId : uint8_t { BUF_A = 0, BUF_B = 1 };
+// Shared-memory vectors: parity p owns ids 2p (A_p) and 2p + 1 (B_p), each
+// buf_ab complex elements, so both parity butterflies of an order run
+// interleaved.
+constexpr int kNumVecs = 4;
 
 constexpr int kMaxM = 32;             // outputs per compute op (one warp)
 constexpr int kConsumerWarps = 8;

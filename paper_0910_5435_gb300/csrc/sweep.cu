@@ -33,7 +33,8 @@
 namespace sht {
 namespace {
 
-constexpr int kThreads = (kConsumerWarps + 2) * 32;  // consumers + producer + parser
+template <int NW>
+constexpr int threads_for() { return (NW + 2) * 32; }  // consumers + producer + parser
 constexpr int kMaxStages = 16;
 constexpr int kDir = 1024;                            // op directory entries (ring)
 constexpr long long kTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
@@ -322,20 +323,30 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
     while (((2 << lks) * M) <= 32) ++lks;
     const int ks = 1 << lks;
     const int o = lane >> lks, q = lane & (ks - 1);
-    Acc a0 = TR::zero(), a1 = TR::zero();
+    // four independent accumulators: float64 FMA latency on GB300 needs many
+    // FMAs in flight per SMSP
+    Acc a0 = TR::zero(), a1 = TR::zero(), a2 = TR::zero(), a3 = TR::zero();
     if (o < M) {
       int s = q;
-      for (; s + ks < K; s += 2 * ks) {
-        const int s1 = s + ks;
+      for (; s + 3 * ks < K; s += 4 * ks) {
+        const int s1 = s + ks, s2 = s + 2 * ks, s3 = s + 3 * ks;
         const V v0 = val[(size_t)s * M + o];
         const V v1 = val[(size_t)s1 * M + o];
+        const V v2 = val[(size_t)s2 * M + o];
+        const V v3 = val[(size_t)s3 * M + o];
         const C x0 = in[gather ? (int)idx[s] : s];
         const C x1 = in[gather ? (int)idx[s1] : s1];
+        const C x2 = in[gather ? (int)idx[s2] : s2];
+        const C x3 = in[gather ? (int)idx[s3] : s3];
         TR::fma(a0, v0, x0);
         TR::fma(a1, v1, x1);
+        TR::fma(a2, v2, x2);
+        TR::fma(a3, v3, x3);
       }
-      if (s < K) TR::fma(a0, val[(size_t)s * M + o], in[gather ? (int)idx[s] : s]);
+      for (; s < K; s += ks) TR::fma(a0, val[(size_t)s * M + o], in[gather ? (int)idx[s] : s]);
       TR::merge(a0, a1);
+      TR::merge(a2, a3);
+      TR::merge(a0, a2);
     }
     for (int off = ks >> 1; off > 0; off >>= 1) {
       const Acc b = TR::shfl_xor(a0, off);
@@ -581,8 +592,8 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
   }
 }
 
-template <class TR>
-__global__ void __launch_bounds__(kThreads) bfly_sweep_kernel(const SweepArgs A) {
+template <class TR, int NW>
+__global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const SweepArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int NST = A.nstages;
@@ -608,9 +619,9 @@ __global__ void __launch_bounds__(kThreads) bfly_sweep_kernel(const SweepArgs A)
   }
   __syncthreads();
 
-  if (warp == kConsumerWarps) {
+  if (warp == NW) {
     if (lane == 0) producer_loop(A, stages, full, empty, S);
-  } else if (warp == kConsumerWarps + 1) {
+  } else if (warp == NW + 1) {
     if (lane == 0) parser_loop(A, stages, full, S);
   } else {
     consumer_loop<TR>(A, stages, empty, S, V, lane);
@@ -620,7 +631,7 @@ __global__ void __launch_bounds__(kThreads) bfly_sweep_kernel(const SweepArgs A)
 template <class TR>
 size_t smem_for(int page_bytes, int nstages, int buf_ab) {
   const size_t vec_off = ((size_t)nstages * page_bytes + 16 * (size_t)nstages + sizeof(Sched) + 127) & ~size_t(127);
-  return vec_off + sizeof(typename TR::C) * 2 * (size_t)buf_ab;
+  return vec_off + sizeof(typename TR::C) * kNumVecs * (size_t)buf_ab;
 }
 
 }  // namespace
@@ -633,36 +644,40 @@ size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int /
   }
 }
 
-cudaError_t sweep_configure(int prec, size_t smem) {
+// Host dispatch over (precision, consumer warps).
+template <class TR>
+const void* kernel_ptr(int nw) {
+  return nw == 8 ? reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 8>)
+                 : reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 16>);
+}
+const void* kernel_for(int prec, int nw) {
   switch (prec) {
-    case PREC_FP64:
-      return cudaFuncSetAttribute(bfly_sweep_kernel<TF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    case PREC_FP32:
-      return cudaFuncSetAttribute(bfly_sweep_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    default:
-      return cudaFuncSetAttribute(bfly_sweep_kernel<TS32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    case PREC_FP64: return kernel_ptr<TF64>(nw);
+    case PREC_FP32: return kernel_ptr<TF32>(nw);
+    default: return kernel_ptr<TS32>(nw);
   }
 }
 
-int sweep_blocks_per_sm(int prec, size_t smem) {
-  int nb = 0;
-  cudaError_t e;
-  switch (prec) {
-    case PREC_FP64: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TF64>, kThreads, smem); break;
-    case PREC_FP32: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TF32>, kThreads, smem); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bfly_sweep_kernel<TS32>, kThreads, smem); break;
+cudaError_t sweep_configure(int prec, size_t smem) {
+  for (int nw : {8, 16}) {
+    cudaError_t e = cudaFuncSetAttribute(kernel_for(prec, nw), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+int sweep_blocks_per_sm(int prec, int nw, size_t smem) {
+  int nb = 0;
+  const cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(prec, nw), (nw + 2) * 32, smem);
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
-cudaError_t sweep_launch(int prec, const SweepArgs& a, int grid, size_t smem, cudaStream_t st) {
+cudaError_t sweep_launch(int prec, int nw, const SweepArgs& a, int grid, size_t smem, cudaStream_t st) {
   if (a.nstages < 1 || a.nstages > kMaxStages) return cudaErrorInvalidValue;
-  switch (prec) {
-    case PREC_FP64: bfly_sweep_kernel<TF64><<<grid, kThreads, smem, st>>>(a); break;
-    case PREC_FP32: bfly_sweep_kernel<TF32><<<grid, kThreads, smem, st>>>(a); break;
-    default: bfly_sweep_kernel<TS32><<<grid, kThreads, smem, st>>>(a); break;
-  }
-  return cudaGetLastError();
+  if (nw != 8 && nw != 16) return cudaErrorInvalidValue;
+  void* args[] = {const_cast<SweepArgs*>(&a)};
+  return cudaLaunchKernel(kernel_for(prec, nw), dim3(grid), dim3((nw + 2) * 32), args, smem, st);
 }
 
 }  // namespace sht

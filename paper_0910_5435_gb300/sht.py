@@ -53,6 +53,7 @@ class sht_plan_opts(ctypes.Structure):
         ("num_threads", ctypes.c_int),
         ("page_bytes", ctypes.c_int),
         ("eps_fp32", ctypes.c_double),
+        ("consumer_warps", ctypes.c_int),
     ]
 
 
@@ -163,7 +164,7 @@ class Plan:
     """Owns an ``sht_plan_t`` (``sht_plan_create_ex`` / ``sht_plan_destroy``)."""
 
     def __init__(self, l, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, host_only=False,
-                 num_threads=0, page_bytes=0, eps_fp32=0.0):
+                 num_threads=0, page_bytes=0, eps_fp32=0.0, consumer_warps=0):
         L = lib()
         opts = sht_plan_opts()
         _check(L.sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
@@ -174,6 +175,7 @@ class Plan:
         opts.num_threads = num_threads
         opts.page_bytes = page_bytes
         opts.eps_fp32 = eps_fp32
+        opts.consumer_warps = consumer_warps
         h = ctypes.c_void_p()
         _check(L.sht_plan_create_ex(int(l), float(eps_id), ctypes.byref(opts), ctypes.byref(h)),
                "sht_plan_create_ex")

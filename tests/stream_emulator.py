@@ -63,7 +63,7 @@ def emulate(stream, page_bytes, l, prec, direction, inp, prescale=None, twiddle=
     direction 1: inp = G -> beta triangle."""
     L = 2 * l
     size = 8 * L + 64
-    bufs = [np.zeros(size, dtype=np.complex128) for _ in range(2)]
+    bufs = [np.zeros(size, dtype=np.complex128) for _ in range(4)]
     tri = _tri(l)
     if direction == 0:
         G = np.full((L, L), np.nan, dtype=np.complex128)

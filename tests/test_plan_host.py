@@ -136,14 +136,12 @@ def test_op_ordering_is_race_free(l, C, prec):
 
 
 def test_race_checker_catches_a_planted_overlap():
-    """The checker itself: widening one op's overlap window by one op in a
-    real stream (a gather overlapping the op before it) must be reported."""
-    import numpy as np
+    """The checker itself: letting the first interpolation op of a real stream
+    overlap the op just before it (a gather piece that writes its input) must
+    be reported."""
     from tests.stream_emulator import OPHDR
-    P = sht.Plan(16, 1e-12, leaf_cols=4, host_only=True)
+    P = sht.Plan(64, 1e-12, leaf_cols=16, host_only=True)
     st = P.stream(0, 0).copy()
-    # find the second gather (first op of the odd parity) and let it overlap its predecessor
-    off, seen = 0, 0
     for pg in range(len(st) // PB):
         base = pg * PB
         off = 0
@@ -151,9 +149,10 @@ def test_race_checker_catches_a_planted_overlap():
             h = st[base + off:base + off + 32].view(OPHDR)
             if h[0]["bytes"] == 0:
                 break
-            if h[0]["kind"] == 1 and h[0]["a0"] == 1 and h[0]["oo"] == 0:
+            if h[0]["kind"] == 6 and h[0]["dep"] == 0:
+                assert check_races(st, PB, 64) == []
                 h[0]["dep"] = 1
-                assert check_races(st, PB, 16) != []
+                assert check_races(st, PB, 64) != []
                 return
             off += int(h[0]["bytes"])
-    raise AssertionError("no odd-parity gather found")
+    raise AssertionError("no interpolation op found")
