@@ -137,8 +137,8 @@ def test_op_ordering_is_race_free(l, C, prec):
 
 def test_race_checker_catches_a_planted_overlap():
     """The checker itself: letting the first interpolation op of a real stream
-    overlap the op just before it (a gather piece that writes its input) must
-    be reported."""
+    overlap the ops before it (the gather pieces that write its input) must be
+    reported."""
     from tests.stream_emulator import OPHDR
     P = sht.Plan(64, 1e-12, leaf_cols=16, host_only=True)
     st = P.stream(0, 0).copy()
@@ -151,7 +151,7 @@ def test_race_checker_catches_a_planted_overlap():
                 break
             if h[0]["kind"] == 6 and h[0]["dep"] == 0:
                 assert check_races(st, PB, 64) == []
-                h[0]["dep"] = 1
+                h[0]["dep"] = 64
                 assert check_races(st, PB, 64) != []
                 return
             off += int(h[0]["bytes"])
