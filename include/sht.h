@@ -245,6 +245,21 @@ sht_status sht_synthesize(sht_plan_t plan, sht_precision prec, const void* beta,
 sht_status sht_analyze(sht_plan_t plan, sht_precision prec, const void* values, void* beta,
                        void* workspace, sht_stream_t stream);
 
+/* ----------------------------------------------------------------- tracing */
+
+/* Enables (allocating a small device buffer) or disables per-launch cycle
+ * counters in the sweep kernels.  While enabled, every launch adds, summed
+ * over its CTAs, the clock64 cycles that consumer warps spent executing ops,
+ * waiting for an op to be published, waiting for its dependencies, that the
+ * producer spent waiting for a free page and the parser for a landed page,
+ * plus the number of ops executed.  Synchronous. */
+sht_status sht_trace_enable(sht_plan_t plan, int enable);
+
+/* Copies the 8 counters (exec, wait_ready, wait_dep, producer_wait,
+ * parser_wait, ops, 0, 0) to host memory out[8]; reset != 0 zeroes them.
+ * Synchronizes the device.  SHT_ERR_UNSUPPORTED if tracing is disabled. */
+sht_status sht_trace_read(sht_plan_t plan, unsigned long long* out, int reset);
+
 /* ------------------------------------- direct float64 baseline (K3-style) */
 
 /* Stores the dense operator P-bar^m_{m+p+2j}(x_{l+i}) (float64, kept rows

@@ -73,6 +73,7 @@ struct sht_plan_s {
   bool fft_ready[2] = {false, false};
   double* d_w_pos = nullptr;   // w_{l+i}
   unsigned* d_scratch = nullptr;  // [kNumPrec * KIND_COUNT] queue counters, then the status word
+  unsigned long long* d_trace = nullptr;  // sweep cycle counters while tracing is enabled
   // direct baseline
   double* d_dense = nullptr;
   long long* d_dense_off = nullptr;
@@ -125,6 +126,8 @@ void free_dev(sht_plan_t P) {
       P->fft_ready[f] = false;
     }
   cudaFree(P->d_scratch);
+  cudaFree(P->d_trace);
+  P->d_trace = nullptr;
   cudaFree(P->d_dense);
   cudaFree(P->d_dense_off);
   cudaFree(P->d_dense_rows);
@@ -212,9 +215,10 @@ sht_status upload(sht_plan_t P, int q) {
   if (P->dev_ready[q]) return SHT_OK;
   const double t0 = now_s();
   CK(cudaSetDevice(P->device));
-  int buf_ab = 0;
+  int buf_ab = 0, nvecs = 2;
   for (int d = 0; d < 2; ++d) {
     const sht::Stream& S = P->H.streams[q][d];
+    nvecs = std::max(nvecs, S.num_vecs);
     DevStream& D = P->dev[q][d];
     D.bytes = S.bytes.size();
     D.n_units = (int)S.units.size();
@@ -236,7 +240,7 @@ sht_status upload(sht_plan_t P, int q) {
   CK(sht::sweep_configure(q, (size_t)optin));
   int best_nst = 0, best_ctas = 0;
   for (int nst = 8; nst >= 2; --nst) {
-    const size_t sm = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, P->H.l);
+    const size_t sm = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, nvecs);
     if (sm > (size_t)optin) continue;
     const int ctas = std::min(2, sht::sweep_blocks_per_sm(q, P->consumer_warps, sm));
     const bool better = (ctas > best_ctas && (nst >= 3 || best_ctas == 0)) || best_ctas == 0;
@@ -248,7 +252,7 @@ sht_status upload(sht_plan_t P, int q) {
   if (best_nst == 0) return SHT_ERR_UNSUPPORTED;
   P->nstages[q] = best_nst;
   P->ctas_per_sm[q] = best_ctas;
-  P->smem[q] = sht::sweep_smem_bytes(q, P->H.page_bytes, best_nst, buf_ab, P->H.l);
+  P->smem[q] = sht::sweep_smem_bytes(q, P->H.page_bytes, best_nst, buf_ab, nvecs);
   P->dev[q][0].buf_ab = P->dev[q][1].buf_ab = buf_ab;
   P->dev_ready[q] = true;
   P->stats.t_upload += now_s() - t0;
@@ -297,6 +301,7 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.out = out;
   a.prescale = prescale;
   a.twiddle = twiddle;
+  a.trace = P->d_trace;
   a.counter = P->d_scratch + (q * KIND_COUNT + kind);
   a.status = P->d_scratch + kNumPrec * KIND_COUNT;
   const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
@@ -642,6 +647,31 @@ sht_status sht_analyze(sht_plan_t P, sht_precision prec, const void* values, voi
   s = fft_r2c(P, q, values, workspace, stream);
   if (s != SHT_OK) return s;
   return launch_sweep(P, prec, 1, KIND_ANA, workspace, beta, nullptr, stream, P->d_tw_ana);
+}
+
+sht_status sht_trace_enable(sht_plan_t P, int enable) {
+  if (!P) return SHT_ERR_INVALID_ARG;
+  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  CK(cudaSetDevice(P->device));
+  if (enable && !P->d_trace) {
+    CK(cudaMalloc(&P->d_trace, sizeof(unsigned long long) * sht::kTraceSlots));
+    CK(cudaMemset(P->d_trace, 0, sizeof(unsigned long long) * sht::kTraceSlots));
+  } else if (!enable && P->d_trace) {
+    CK(cudaDeviceSynchronize());
+    cudaFree(P->d_trace);
+    P->d_trace = nullptr;
+  }
+  return SHT_OK;
+}
+
+sht_status sht_trace_read(sht_plan_t P, unsigned long long* out, int reset) {
+  if (!P || !out) return SHT_ERR_INVALID_ARG;
+  if (!P->d_trace) return SHT_ERR_UNSUPPORTED;
+  CK(cudaSetDevice(P->device));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(out, P->d_trace, sizeof(unsigned long long) * sht::kTraceSlots, cudaMemcpyDeviceToHost));
+  if (reset) CK(cudaMemset(P->d_trace, 0, sizeof(unsigned long long) * sht::kTraceSlots));
+  return SHT_OK;
 }
 
 sht_status sht_direct_prepare(sht_plan_t P) {

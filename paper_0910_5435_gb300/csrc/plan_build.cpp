@@ -749,10 +749,13 @@ struct Emitter {
   }
 };
 
-// Shared vectors: parity p uses the pair (A_p, B_p) = (2p, 2p + 1), so the
-// two independent parity butterflies of an order can run interleaved.
-inline uint8_t buf_a(int p) { return (uint8_t)(2 * p); }
-inline uint8_t buf_b(int p) { return (uint8_t)(2 * p + 1); }
+// Shared vectors: with interleaved parities, parity p uses the pair
+// (A_p, B_p) = (2p, 2p + 1), so the two independent parity butterflies of an
+// order run interleaved; otherwise both parities reuse (0, 1) one after the
+// other (half the shared memory, so a deeper page ring).
+thread_local bool g_interleave = false;
+inline uint8_t buf_a(int p) { return (uint8_t)(g_interleave ? 2 * p : 0); }
+inline uint8_t buf_b(int p) { return (uint8_t)(g_interleave ? 2 * p + 1 : 1); }
 inline uint8_t level_buf(int j, int p) { return (j & 1) ? buf_b(p) : buf_a(p); }
 inline uint8_t other_buf(uint8_t b) { return (uint8_t)(b ^ 1); }
 
@@ -769,9 +772,18 @@ std::vector<const IdBlock*> blocks_at(const UnitFact& U, int j) {
 
 using Stage = std::function<void(Emitter&)>;
 
-// Emits the stages of both parities interleaved: stage i of parity 0 and
-// stage i of parity 1 share one ordering group (they touch disjoint data).
+// Emits the stages of both parities: interleaved (stage i of parity 0 and
+// stage i of parity 1 share one ordering group; they touch disjoint data), or
+// one parity after the other, one group per stage.
 void emit_interleaved(Emitter& E, const std::vector<Stage> (&st)[2]) {
+  if (!g_interleave) {
+    for (int p = 0; p < 2; ++p)
+      for (const Stage& s : st[p]) {
+        E.new_group();
+        s(E);
+      }
+    return;
+  }
   const size_t n = std::max(st[0].size(), st[1].size());
   for (size_t i = 0; i < n; ++i) {
     E.new_group();
@@ -782,6 +794,7 @@ void emit_interleaved(Emitter& E, const std::vector<Stage> (&st)[2]) {
 
 // Appends the ops of order m to the page writer (continuing its open page).
 void emit_unit(PlanHost& P, int prec, int dir, int m, PageWriter& W) {
+  g_interleave = P.interleave_parities;
   const int l = P.l;
   const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
   if (!W.open) W.new_page();
@@ -843,12 +856,27 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, PageWriter& W) {
         }
       };
     }
-    emit_interleaved(E, st);
-    for (int p = 0; p < 2; ++p)
-      if (fin[p]) {
-        E.new_group();
-        fin[p](E);
+    if (g_interleave) {
+      emit_interleaved(E, st);
+      for (int p = 0; p < 2; ++p)
+        if (fin[p]) {
+          E.new_group();
+          fin[p](E);
+        }
+    } else {
+      // shared buffers: each parity's final blocks read its top level before
+      // the next parity overwrites it
+      for (int p = 0; p < 2; ++p) {
+        for (const Stage& sg : st[p]) {
+          E.new_group();
+          sg(E);
+        }
+        if (fin[p]) {
+          E.new_group();
+          fin[p](E);
+        }
       }
+    }
   } else {
     for (int p = 0; p < 2; ++p) {
       const UnitFact& U = F[(size_t)m * 2 + p];
@@ -1052,6 +1080,7 @@ void emit_streams(PlanHost& P, int prec) {
       for (int wdt : F[u].width) mx = std::max(mx, wdt);
     }
     S.max_buf_ab = mx;
+    S.num_vecs = P.interleave_parities ? 4 : 2;
   }
   P.built[prec] = true;
 }

@@ -64,13 +64,15 @@ struct UnitFact {
 struct Stream {
   std::vector<uint8_t> bytes;        // n_pages * page_bytes
   std::vector<UnitEntry> units;      // LPT order
-  int max_buf_ab = 0;                // elements needed in BUF_A / BUF_B
+  int max_buf_ab = 0;                // elements needed in each shared vector
+  int num_vecs = 2;                  // shared vectors used (4 with interleaved parities)
 };
 
 struct PlanHost {
   int l = 0;
   double eps_id = 0, eps_fp32 = 0, trim_eps = 0;
   int leaf_cols = 64, min_band_rows = 32, num_threads = 0, page_bytes = 16384;
+  bool interleave_parities = false;
   // Gauss-Legendre nodes (all 2l, ascending), weights, and the angle of each
   // positive node (theta_{l+i} in (0, pi/2)).
   std::vector<double> x, w, theta_pos;

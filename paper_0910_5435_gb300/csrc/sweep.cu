@@ -458,6 +458,10 @@ __device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, c
 
 // ------------------------------------------------------------ roles
 
+__device__ __forceinline__ void trace_add(const SweepArgs& A, int slot, unsigned long long v) {
+  if (A.trace && v) atomicAdd(A.trace + slot, v);
+}
+
 __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* full, uint64_t* empty, Sched* S) {
   const uint32_t PB = (uint32_t)A.page_bytes;
   const int NST = A.nstages;
@@ -467,6 +471,7 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
   int issued_phase[kMaxStages];
   for (int s = 0; s < kMaxStages; ++s) issued_phase[s] = -1;
   bool ok = true;
+  unsigned long long c_wait = 0;
   for (;;) {
     if (*abort_flag) {
       ok = false;
@@ -480,10 +485,12 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
     }
     const UnitEntry e = A.units[u];
     for (uint32_t pg = 0; pg < e.n_pages; ++pg) {
+      const long long w0 = clock64();
       if (!wait_bounded(empty + stage, phase ^ 1u, A.status, abort_flag)) {
         ok = false;
         break;
       }
+      c_wait += clock64() - w0;
       mbar_arrive_expect_tx(full + stage, PB);
       bulk_g2s(stages + (size_t)stage * PB, A.pages + (size_t)(e.first_page + pg) * PB, PB, full + stage);
       issued_phase[stage] = (int)phase;
@@ -502,6 +509,7 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
   // never leave the CTA with bulk copies still landing in its shared memory
   for (int s = 0; s < NST; ++s)
     if (issued_phase[s] >= 0) wait_bounded(full + s, (uint32_t)issued_phase[s], A.status, abort_flag);
+  trace_add(A, TR_PROD_WAIT, c_wait);
 }
 
 __device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* full, Sched* S) {
@@ -509,8 +517,11 @@ __device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t*
   const int NST = A.nstages;
   int stage = 0, ticket = 0;
   uint32_t phase = 0;
+  unsigned long long c_wait = 0;
   for (;;) {
+    const long long w0 = clock64();
     if (!wait_bounded(full + stage, phase, A.status, &S->abort)) return;
+    c_wait += clock64() - w0;
     const uint8_t* page = stages + (size_t)stage * PB;
     int count = 0;
     bool quit = false;
@@ -549,6 +560,7 @@ __device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t*
     if (quit) {
       __threadfence_block();
       vstore(&S->quit, ticket);
+      trace_add(A, TR_PARSE_WAIT, c_wait);
       return;
     }
     if (++stage == NST) {
@@ -562,23 +574,27 @@ template <class TR>
 __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* empty, Sched* S,
                               const Vecs<TR>& V, int lane) {
   const size_t PB = (size_t)A.page_bytes;
+  unsigned long long c_exec = 0, c_ready = 0, c_dep = 0, n_ops = 0;
   for (;;) {
     int t = 0;
     if (lane == 0) t = atomicAdd(&S->n_claimed, 1);
     t = __shfl_sync(0xffffffffu, t, 0);
+    const long long t0 = clock64();
     if (!warp_wait([&] {
           const int q = vload(&S->quit);
           return vload(&S->n_ready) > t || (q >= 0 && t >= q);
         }, S, A.status, lane))
-      return;
+      break;
     const int q = vload(&S->quit);
-    if (q >= 0 && t >= q) return;
+    if (q >= 0 && t >= q) break;
     const uint32_t e = S->dir[t % kDir];
     const int stage = (int)(e >> 16);
     const uint8_t* op = stages + (size_t)stage * PB + ((size_t)(e & 0xffffu) << 4);
     const OpHdr h = *reinterpret_cast<const OpHdr*>(op);
     const int need = t - (int)h.dep;
-    if (!warp_wait([&] { return vload(&S->n_done) >= need; }, S, A.status, lane)) return;
+    const long long t1 = clock64();
+    if (!warp_wait([&] { return vload(&S->n_done) >= need; }, S, A.status, lane)) break;
+    const long long t2 = clock64();
     if (h.kind >= OP_SYN_INTERP)
       run_gemv<TR>(h, op, V, A, lane);
     else
@@ -589,6 +605,17 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
       atomicAdd(&S->n_done, 1);
       if (atomicSub(&S->pending[stage], 1) == 1) mbar_arrive(empty + stage);
     }
+    const long long t3 = clock64();
+    c_ready += t1 - t0;
+    c_dep += t2 - t1;
+    c_exec += t3 - t2;
+    ++n_ops;
+  }
+  if (lane == 0) {
+    trace_add(A, TR_EXEC, c_exec);
+    trace_add(A, TR_WAIT_READY, c_ready);
+    trace_add(A, TR_WAIT_DEP, c_dep);
+    trace_add(A, TR_OPS, n_ops);
   }
 }
 
@@ -629,18 +656,18 @@ __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const Swe
 }
 
 template <class TR>
-size_t smem_for(int page_bytes, int nstages, int buf_ab) {
+size_t smem_for(int page_bytes, int nstages, int buf_ab, int num_vecs) {
   const size_t vec_off = ((size_t)nstages * page_bytes + 16 * (size_t)nstages + sizeof(Sched) + 127) & ~size_t(127);
-  return vec_off + sizeof(typename TR::C) * kNumVecs * (size_t)buf_ab;
+  return vec_off + sizeof(typename TR::C) * (size_t)num_vecs * (size_t)buf_ab;
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int /*l*/) {
+size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs) {
   switch (prec) {
-    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab);
-    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab);
-    default: return smem_for<TS32>(page_bytes, nstages, buf_ab);
+    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab, num_vecs);
+    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab, num_vecs);
+    default: return smem_for<TS32>(page_bytes, nstages, buf_ab, num_vecs);
   }
 }
 

@@ -31,7 +31,7 @@ EXPORTS = [
     "sht_legendre_synthesize", "sht_legendre_analyze", "sht_legendre_synthesize_adjoint",
     "sht_last_device_status", "sht_direct_prepare", "sht_direct_synthesize", "sht_direct_analyze",
     "sht_workspace_bytes", "sht_phi_synthesize", "sht_phi_analyze", "sht_synthesize", "sht_analyze",
-    "sht_last_error_detail",
+    "sht_last_error_detail", "sht_trace_enable", "sht_trace_read",
 ]
 
 
@@ -126,6 +126,8 @@ def lib():
     L.sht_phi_analyze.argtypes = [vp, c_int, vp, vp, vp]
     L.sht_synthesize.argtypes = [vp, c_int, vp, vp, vp, vp]
     L.sht_analyze.argtypes = [vp, c_int, vp, vp, vp, vp]
+    L.sht_trace_enable.argtypes = [vp, c_int]
+    L.sht_trace_read.argtypes = [vp, vp, c_int]
     for name in EXPORTS:
         if name not in ("sht_status_string", "sht_workspace_bytes", "sht_last_error_detail"):
             getattr(L, name).restype = c_int
@@ -272,3 +274,16 @@ def sht_synthesize(plan, prec, beta, values, workspace, stream=None):
 def sht_analyze(plan, prec, values, beta, workspace, stream=None):
     _check(lib().sht_analyze(plan.handle, int(prec), _ptr(values), _ptr(beta), _ptr(workspace),
                              _stream(stream)), "sht_analyze")
+
+
+TRACE_FIELDS = ("exec", "wait_ready", "wait_dep", "producer_wait", "parser_wait", "ops")
+
+
+def sht_trace_enable(plan, enable=True):
+    _check(lib().sht_trace_enable(plan.handle, 1 if enable else 0), "sht_trace_enable")
+
+
+def sht_trace_read(plan, reset=True):
+    out = np.zeros(8, dtype=np.uint64)
+    _check(lib().sht_trace_read(plan.handle, out.ctypes.data, 1 if reset else 0), "sht_trace_read")
+    return {name: int(out[i]) for i, name in enumerate(TRACE_FIELDS)}
