@@ -107,8 +107,12 @@ typedef struct {
    * max(eps_id, 1e-7).  (FP32 cannot use ranks below its own precision.) */
   double eps_fp32;
   /* Warps per CTA of the sweep kernels that execute ops (8 or 16; 0 =
-   * default 16).  A tuning knob; results do not depend on it. */
+   * default 8).  A tuning knob; results do not depend on it. */
   int consumer_warps;
+  /* 1: factor values travel inside the TMA-staged pages; 0 (default): they
+   * sit in a separate region that the executing warp streams directly, and
+   * the pages carry only op headers and index lists.  A tuning knob. */
+  int values_inline;
 } sht_plan_opts;
 
 typedef struct {
@@ -171,11 +175,13 @@ sht_status sht_prepare(sht_plan_t plan, sht_precision prec);
 sht_status sht_plan_nodes(sht_plan_t plan, double* x, double* w);
 
 /* Host copy of the factor stream of one precision and direction (0 =
- * synthesis, 1 = analysis), for inspection and host-side verification.
- * The layout is documented in paper_0910_5435_gb300/csrc/sht_stream.h.
- * With dst == NULL only *bytes is set. */
+ * synthesis, 1 = analysis), for inspection and host-side verification: the
+ * page region followed by the value region (layout documented in
+ * paper_0910_5435_gb300/csrc/sht_stream.h).  *bytes receives the total and
+ * *page_bytes_total (if not NULL) the size of the page region.  With
+ * dst == NULL only the sizes are set. */
 sht_status sht_plan_stream(sht_plan_t plan, sht_precision prec, int direction,
-                           void* dst, size_t* bytes);
+                           void* dst, size_t* bytes, size_t* page_bytes_total);
 
 /* ----------------------------------------------- Legendre stage (hot path) */
 

@@ -31,6 +31,7 @@ enum { KIND_SYN = 0, KIND_ANA = 1, KIND_ADJ = 2, KIND_COUNT = 3 };
 
 struct DevStream {
   uint8_t* pages = nullptr;
+  uint8_t* values = nullptr;
   sht::UnitEntry* units = nullptr;
   size_t bytes = 0;
   int n_units = 0;
@@ -111,6 +112,7 @@ void free_dev(sht_plan_t P) {
   for (int q = 0; q < kNumPrec; ++q)
     for (int d = 0; d < 2; ++d) {
       cudaFree(P->dev[q][d].pages);
+      cudaFree(P->dev[q][d].values);
       cudaFree(P->dev[q][d].units);
       P->dev[q][d] = DevStream();
     }
@@ -182,9 +184,9 @@ void fill_stats(sht_plan_t P) {
   long long fv32 = 0;
   for (const UnitFact& U : H.fact32) fv32 += U.values;
   s.factor_values_fp32 = fv32;
-  s.stream_bytes_fp64 = (long long)H.streams[0][0].bytes.size();
-  s.stream_bytes_fp32 = (long long)H.streams[1][0].bytes.size();
-  s.stream_bytes_split32 = (long long)H.streams[2][0].bytes.size();
+  s.stream_bytes_fp64 = (long long)(H.streams[0][0].bytes.size() + H.streams[0][0].values.size());
+  s.stream_bytes_fp32 = (long long)(H.streams[1][0].bytes.size() + H.streams[1][0].values.size());
+  s.stream_bytes_split32 = (long long)(H.streams[2][0].bytes.size() + H.streams[2][0].values.size());
   s.t_quad = H.t_quad;
   s.t_comp = H.t_comp;
   s.smem_bytes = (int)std::max({P->smem[0], P->smem[1], P->smem[2]});
@@ -226,6 +228,10 @@ sht_status upload(sht_plan_t P, int q) {
     D.buf_ab = std::max(S.max_buf_ab, 1);
     buf_ab = std::max(buf_ab, D.buf_ab);
     CK(cudaMalloc(&D.pages, D.bytes));
+    if (!S.values.empty()) {
+      CK(cudaMalloc(&D.values, S.values.size()));
+      CK(cudaMemcpy(D.values, S.values.data(), S.values.size(), cudaMemcpyHostToDevice));
+    }
     CK(cudaMalloc(&D.units, sizeof(sht::UnitEntry) * std::max<size_t>(1, S.units.size())));
     CK(cudaMemcpy(D.pages, S.bytes.data(), D.bytes, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(D.units, S.units.data(), sizeof(sht::UnitEntry) * S.units.size(), cudaMemcpyHostToDevice));
@@ -290,6 +296,7 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   const DevStream& D = P->dev[q][dir];
   sht::SweepArgs a;
   a.pages = D.pages;
+  a.values = D.values;
   a.units = D.units;
   a.n_units = D.n_units;
   a.page_bytes = P->H.page_bytes;
@@ -340,7 +347,8 @@ sht_status sht_plan_opts_default(sht_plan_opts* o) {
   o->num_threads = 0;
   o->page_bytes = 16384;
   o->eps_fp32 = 0.0;
-  o->consumer_warps = 16;
+  o->consumer_warps = 8;
+  o->values_inline = 0;
   return SHT_OK;
 }
 
@@ -363,7 +371,7 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   if (o.leaf_cols < 2 || o.leaf_cols > 1024) return SHT_ERR_INVALID_ARG;
   if (o.page_bytes < 4096 || o.page_bytes > 49152 || (o.page_bytes % 1024) != 0) return SHT_ERR_INVALID_ARG;
   if (o.num_threads < 0) return SHT_ERR_INVALID_ARG;
-  if (o.consumer_warps == 0) o.consumer_warps = 16;
+  if (o.consumer_warps == 0) o.consumer_warps = 8;
   if (o.consumer_warps != 8 && o.consumer_warps != 16) return SHT_ERR_INVALID_ARG;
 
   sht_plan_t P = new (std::nothrow) sht_plan_s();
@@ -380,6 +388,7 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   H.min_band_rows = o.min_band_rows;
   H.num_threads = o.num_threads;
   H.page_bytes = o.page_bytes;
+  for (int q = 0; q < 3; ++q) H.values_apart[q] = (o.values_inline == 0);
 
   if (!P->host_only) {
     int dev = 0, count = 0;
@@ -481,7 +490,8 @@ sht_status sht_plan_nodes(sht_plan_t P, double* x, double* w) {
   return SHT_OK;
 }
 
-sht_status sht_plan_stream(sht_plan_t P, sht_precision prec, int direction, void* dst, size_t* bytes) {
+sht_status sht_plan_stream(sht_plan_t P, sht_precision prec, int direction, void* dst, size_t* bytes,
+                           size_t* page_bytes_total) {
   if (!P || !bytes || direction < 0 || direction > 1) return SHT_ERR_INVALID_ARG;
   const int q = prec_index(prec);
   if (q < 0) return SHT_ERR_INVALID_ARG;
@@ -492,13 +502,16 @@ sht_status sht_plan_stream(sht_plan_t P, sht_precision prec, int direction, void
     fill_stats(P);
   }
   const sht::Stream& S = P->H.streams[q][direction];
+  const size_t total = S.bytes.size() + S.values.size();
+  if (page_bytes_total) *page_bytes_total = S.bytes.size();
   if (!dst) {
-    *bytes = S.bytes.size();
+    *bytes = total;
     return SHT_OK;
   }
-  if (*bytes < S.bytes.size()) return SHT_ERR_INVALID_ARG;
+  if (*bytes < total) return SHT_ERR_INVALID_ARG;
   std::memcpy(dst, S.bytes.data(), S.bytes.size());
-  *bytes = S.bytes.size();
+  if (!S.values.empty()) std::memcpy(static_cast<uint8_t*>(dst) + S.bytes.size(), S.values.data(), S.values.size());
+  *bytes = total;
   return SHT_OK;
 }
 

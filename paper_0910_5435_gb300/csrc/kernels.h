@@ -12,6 +12,7 @@ namespace sht {
 // the Legendre stage for every order m).
 struct SweepArgs {
   const uint8_t* pages;        // stream pages (device)
+  const uint8_t* values;       // value region (device; ops flagged F_VALUES_APART)
   const UnitEntry* units;      // LPT-ordered unit table (device)
   int n_units;
   int page_bytes;

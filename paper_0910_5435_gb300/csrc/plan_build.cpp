@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <unordered_map>
 #include <memory>
 #include <numeric>
 #include <stdexcept>
@@ -583,17 +584,41 @@ inline void put_value(uint8_t* dst, int prec, size_t i, double v) {
   }
 }
 
-// Writes ops and assigns their ordering field: ops emitted after
-// new_group() may overlap each other but start only after everything
-// emitted before the group has completed.
+// Dependency tracking for the op stream of one work item.  Every op lists
+// its predecessors explicitly: the last writer of every shared-memory
+// position or node row it reads or writes (RAW, WAW) and every reader of a
+// position it overwrites since that position was last written (WAR).  Ops
+// with no predecessor depend on the item's opening JOIN, which itself waits
+// for everything before the item; so blocks of one butterfly level, and the
+// tail of one order with the head of the next order of the same item, run
+// concurrently.
+struct Tracker {
+  std::vector<int> last_w[kNumVecs];
+  std::vector<std::vector<int>> readers[kNumVecs];
+  std::unordered_map<long long, int> g_last_w;  // (m, node row) of G
+  int join = -1;
+  void reset(int positions) {
+    for (int b = 0; b < kNumVecs; ++b) {
+      last_w[b].assign(positions, -1);
+      readers[b].assign(positions, {});
+    }
+    g_last_w.clear();
+    join = -1;
+  }
+};
+
+// Writes ops; numbers them within the item and attaches their predecessors.
 struct Emitter {
   PageWriter& W;
   int prec;
   size_t vs;
-  int group_pos = 0;
+  Tracker* T = nullptr;
+  std::vector<uint8_t>* values = nullptr;  // value region of the item, or nullptr: values inline
+  int next_op = 0;  // number of the next op within the item
+  int l = 0;
   Emitter(PageWriter& w, int p) : W(w), prec(p), vs(value_size(p)) {}
 
-  void new_group() { group_pos = 0; }
+  void new_group() {}  // ordering comes from the tracked dependencies
 
   OpHdr hdr(uint8_t kind, uint8_t flags = 0) {
     OpHdr h;
@@ -602,18 +627,156 @@ struct Emitter {
     h.flags = flags;
     return h;
   }
-  size_t bytes_of(size_t nidx, size_t nval) const { return sizeof(OpHdr) + pad16(2 * nidx) + pad16(vs * nval); }
+  // bytes of an op with nidx index entries and nval values, leaving room for
+  // the largest predecessor list (the actual list may be shorter)
+  size_t bytes_of(size_t nidx, size_t nval) const {
+    return sizeof(OpHdr) + pad16(2 * (nidx + kMaxPred)) + pad16(vs * nval);
+  }
 
-  void write(OpHdr h, const std::vector<uint16_t>& idx, const std::vector<double>& vals) {
-    h.dep = (uint16_t)std::min(group_pos, 65535);
-    ++group_pos;
-    h.idx_bytes = (uint32_t)pad16(2 * idx.size());
-    h.bytes = (uint32_t)bytes_of(idx.size(), vals.size());
+  // Reads and writes of one op, as keys: (vec << 20 | pos) for shared
+  // vectors, (1 << 40 | m << 20 | row) for node rows of G.
+  void access(const OpHdr& h, const std::vector<uint16_t>& idx, std::vector<long long>& R,
+              std::vector<long long>& Wr) const {
+    auto vkey = [](int b, int pos) { return ((long long)b << 20) | pos; };
+    auto gkey = [](int m, int row) { return (1LL << 40) | ((long long)m << 20) | row; };
+    const int M = h.M, K = h.K;
+    switch (h.kind) {
+      case OP_GATHER:
+      case OP_FOLD:
+      case OP_CLEAR:
+        for (int j = 0; j < M; ++j) Wr.push_back(vkey(h.out_buf, h.oo + j));
+        break;
+      case OP_SCATTER:
+        for (int j = 0; j < M; ++j) R.push_back(vkey(h.in_buf, h.io + j));
+        break;
+      case OP_GZERO:
+        for (int j = 0; j < M; ++j) Wr.push_back(gkey(h.a1, l + h.oo + j)), Wr.push_back(gkey(h.a1, l - 1 - h.oo - j));
+        break;
+      case OP_SYN_INTERP:
+        for (int s = 0; s < K + M; ++s) R.push_back(vkey(h.in_buf, h.io + idx[s]));
+        for (int o = 0; o < M; ++o) Wr.push_back(vkey(h.out_buf, h.oo + o));
+        break;
+      case OP_DENSE:
+        for (int s = 0; s < K; ++s) R.push_back(vkey(h.in_buf, h.io + s));
+        for (int o = 0; o < M; ++o) Wr.push_back(vkey(h.out_buf, h.oo + o));
+        break;
+      case OP_DENSE_G:
+        for (int s = 0; s < K; ++s) R.push_back(vkey(h.in_buf, h.io + s));
+        for (int o = 0; o < M; ++o) {
+          Wr.push_back(gkey(h.a1, l + h.oo + o));
+          Wr.push_back(gkey(h.a1, l - 1 - h.oo - o));
+        }
+        if (h.flags & F_ACCUM) R.insert(R.end(), Wr.begin(), Wr.end());
+        break;
+      case OP_ANA_INTERP: {
+        for (int s = 0; s < K; ++s) R.push_back(vkey(h.in_buf, h.io + s));
+        for (int o = 0; o < M; ++o) Wr.push_back(vkey(h.out_buf, h.oo + idx[o]));
+        if (h.flags & F_SKEL)
+          for (int t = 0; t < h.nskel; ++t) Wr.push_back(vkey(h.out_buf, h.oo + idx[M + t]));
+        if (h.flags & F_ACCUM) R.insert(R.end(), Wr.begin(), Wr.end());
+        break;
+      }
+      default:
+        break;
+    }
+  }
+
+  std::vector<int> preds_of(const std::vector<long long>& R, const std::vector<long long>& Wr) {
+    std::vector<int> p;
+    auto lw = [&](long long key) -> int {
+      if (key >> 40) {
+        auto it = T->g_last_w.find(key);
+        return it == T->g_last_w.end() ? -1 : it->second;
+      }
+      return T->last_w[key >> 20][key & 0xFFFFF];
+    };
+    for (long long k : R) p.push_back(lw(k));
+    for (long long k : Wr) {
+      p.push_back(lw(k));
+      if (!(k >> 40)) {
+        const auto& rd = T->readers[k >> 20][k & 0xFFFFF];
+        p.insert(p.end(), rd.begin(), rd.end());
+      }
+    }
+    std::sort(p.begin(), p.end());
+    p.erase(std::unique(p.begin(), p.end()), p.end());
+    if (!p.empty() && p.front() < 0) p.erase(p.begin());
+    return p;
+  }
+
+  void record(int t, const std::vector<long long>& R, const std::vector<long long>& Wr) {
+    for (long long k : Wr) {
+      if (k >> 40) {
+        T->g_last_w[k] = t;
+      } else {
+        T->last_w[k >> 20][k & 0xFFFFF] = t;
+        T->readers[k >> 20][k & 0xFFFFF].clear();
+      }
+    }
+    for (long long k : R)
+      if (!(k >> 40)) {
+        auto& rd = T->readers[k >> 20][k & 0xFFFFF];
+        if (rd.empty() || rd.back() != t) rd.push_back(t);
+      }
+  }
+
+  // Writes a raw op with the given predecessor list (numbers within the item).
+  void raw(OpHdr h, const std::vector<int>& preds, const std::vector<uint16_t>& idx,
+           const std::vector<double>& vals) {
+    const int t = next_op++;
+    std::vector<uint16_t> all;
+    all.reserve(preds.size() + idx.size());
+    for (int u : preds) {
+      if (t - u <= 0 || t - u > 65535) throw std::logic_error("predecessor out of range");
+      all.push_back((uint16_t)(t - u));
+    }
+    all.insert(all.end(), idx.begin(), idx.end());
+    h.npred = (uint16_t)preds.size();
+    const size_t ib = pad16(2 * all.size());
+    h.idx16 = (uint16_t)(ib / 16);
+    const size_t vb = pad16(vs * vals.size());
+    const bool apart = values != nullptr && !vals.empty();
+    if (apart) {
+      h.flags |= F_VALUES_APART;
+      h.vref = (uint32_t)(values->size() / 16);  // relative to the item; rebased when items are joined
+      const size_t at = values->size();
+      values->resize(at + vb, 0);
+      for (size_t i = 0; i < vals.size(); ++i) put_value(values->data() + at, prec, i, vals[i]);
+    }
+    h.bytes = (uint32_t)(sizeof(OpHdr) + ib + (apart ? 0 : vb));
     uint8_t* p = W.alloc(h.bytes);
     std::memcpy(p, &h, sizeof(OpHdr));
-    if (!idx.empty()) std::memcpy(p + sizeof(OpHdr), idx.data(), 2 * idx.size());
-    uint8_t* v = p + sizeof(OpHdr) + h.idx_bytes;
-    for (size_t i = 0; i < vals.size(); ++i) put_value(v, prec, i, vals[i]);
+    if (!all.empty()) std::memcpy(p + sizeof(OpHdr), all.data(), 2 * all.size());
+    if (!apart) {
+      uint8_t* v = p + sizeof(OpHdr) + ib;
+      for (size_t i = 0; i < vals.size(); ++i) put_value(v, prec, i, vals[i]);
+    }
+  }
+
+  // Opens a work item: a JOIN that waits for every earlier op of the CTA.
+  void open_item(int positions) {
+    T->reset(positions);
+    next_op = 0;
+    OpHdr h = hdr(OP_JOIN, F_ITEM_START);
+    T->join = next_op;
+    raw(h, {}, {}, {});
+  }
+
+  void write(OpHdr h, const std::vector<uint16_t>& idx, const std::vector<double>& vals) {
+    std::vector<long long> R, Wr;
+    access(h, idx, R, Wr);
+    std::vector<int> preds = preds_of(R, Wr);
+    if (preds.empty()) preds.push_back(T->join);
+    if ((int)preds.size() > kMaxPred) {
+      // fan-in through a JOIN op (no data) so that the op itself stays small
+      OpHdr j = hdr(OP_JOIN);
+      const int tj = next_op;
+      raw(j, preds, {}, {});
+      preds.assign(1, tj);
+    }
+    const int t = next_op;
+    raw(h, preds, idx, vals);
+    record(t, R, Wr);
   }
 
   // A control op over [start, start + count), split into up to kCtlPieces warp tasks.
@@ -792,13 +955,11 @@ void emit_interleaved(Emitter& E, const std::vector<Stage> (&st)[2]) {
   }
 }
 
-// Appends the ops of order m to the page writer (continuing its open page).
-void emit_unit(PlanHost& P, int prec, int dir, int m, PageWriter& W) {
+// Appends the ops of order m to the emitter's current work item.
+void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
   g_interleave = P.interleave_parities;
   const int l = P.l;
   const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
-  if (!W.open) W.new_page();
-  Emitter E(W, prec);
   std::vector<double> inv_sq2w(l), sqw2(l);
   for (int i = 0; i < l; ++i) {
     inv_sq2w[i] = 1.0 / std::sqrt(2.0 * P.w[l + i]);
@@ -982,12 +1143,13 @@ void emit_streams(PlanHost& P, int prec) {
   const int L = 2 * P.l;
   const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
   const size_t PB = (size_t)P.page_bytes;
-  // Orders whose ops fill fewer than kPackPages pages share pages with other
-  // small orders inside one work item, so the persistent kernel neither
-  // streams padding nor pays a queue pop per tiny order.
-  constexpr size_t kPackPages = 4;
+  int positions = 1;
+  for (const UnitFact& U : F) {
+    positions = std::max({positions, U.n, U.rows});
+    for (int wdt : U.width) positions = std::max(positions, wdt);
+  }
+  positions += 1;
   for (int dir = 0; dir < 2; ++dir) {
-    std::vector<std::vector<uint8_t>> per(L);
     int nt = P.num_threads > 0 ? P.num_threads : (int)std::thread::hardware_concurrency();
     nt = std::max(1, std::min(nt, 256));
     auto run_parallel = [&](int count, auto&& body) {
@@ -1012,48 +1174,72 @@ void emit_streams(PlanHost& P, int prec) {
       for (auto& e : errors)
         if (!e.empty()) throw std::runtime_error(e);
     };
-    run_parallel(L, [&](int m) {
-      PageWriter W(per[m], PB);
-      emit_unit(P, prec, dir, m, W);
-    });
-    // work items: big orders alone, small orders packed greedily (largest first)
+    // emits a list of orders as one work item
+    const bool apart = P.values_apart[prec];
+    auto emit_item = [&](const std::vector<int>& ms, std::vector<uint8_t>& out, std::vector<uint8_t>& vals) -> int {
+      PageWriter W(out, PB);
+      W.new_page();
+      Emitter E(W, prec);
+      Tracker T;
+      E.T = &T;
+      E.l = P.l;
+      E.values = apart ? &vals : nullptr;
+      E.open_item(positions);
+      for (int m : ms) emit_unit(P, prec, dir, m, E);
+      return E.next_op;
+    };
+    // pass 1: every order alone (its size decides the packing)
+    std::vector<std::vector<uint8_t>> per(L), per_vals(L);
+    std::vector<int> nops(L);
+    run_parallel(L, [&](int m) { nops[m] = emit_item({m}, per[m], per_vals[m]); });
+    // sizes for packing count the value bytes as if they were in pages
+    auto work_pages = [&](int m) { return (per[m].size() + per_vals[m].size() + PB - 1) / PB; };
+    size_t total_pages = 0;
+    for (int m = 0; m < L; ++m) total_pages += work_pages(m);
+    // Work items: orders in decreasing size, packed so an item has about
+    // total / (4 x 304) pages (several items per CTA for load balance, more
+    // than one order per item so the tail of one overlaps the next), and
+    // fewer than kMaxItemOps ops (the completion-tag window).
+    const size_t target = std::max<size_t>(4, total_pages / (4 * 304));
     std::vector<int> order(L);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work_pages(a) > work_pages(b); });
     std::vector<std::vector<int>> items;
     std::vector<int> cur;
     size_t cur_pages = 0;
+    int cur_ops = 0;
     for (int m : order) {
-      const size_t pg = per[m].size() / PB;
-      if (pg >= kPackPages) {
-        items.push_back({m});
-        continue;
-      }
-      cur.push_back(m);
-      cur_pages += pg;
-      if (cur_pages >= kPackPages) {
+      const size_t pg = work_pages(m);
+      if (!cur.empty() && (cur_pages + pg > target || cur_ops + nops[m] >= kMaxItemOps)) {
         items.push_back(cur);
         cur.clear();
         cur_pages = 0;
+        cur_ops = 0;
       }
+      if (nops[m] >= kMaxItemOps) throw std::runtime_error("an order needs more ops than one work item holds");
+      cur.push_back(m);
+      cur_pages += pg;
+      cur_ops += nops[m];
     }
     if (!cur.empty()) items.push_back(cur);
-    std::vector<std::vector<uint8_t>> item_bytes(items.size());
+    std::vector<std::vector<uint8_t>> item_bytes(items.size()), item_vals(items.size());
     run_parallel((int)items.size(), [&](int it) {
       if (items[it].size() == 1) {
         item_bytes[it].swap(per[items[it][0]]);
+        item_vals[it].swap(per_vals[items[it][0]]);
         return;
       }
-      PageWriter W(item_bytes[it], PB);
-      for (int m : items[it]) emit_unit(P, prec, dir, m, W);
+      emit_item(items[it], item_bytes[it], item_vals[it]);
     });
     std::vector<int> iorder(items.size());
     std::iota(iorder.begin(), iorder.end(), 0);
-    std::stable_sort(iorder.begin(), iorder.end(),
-                     [&](int a, int b) { return item_bytes[a].size() > item_bytes[b].size(); });
+    std::stable_sort(iorder.begin(), iorder.end(), [&](int a, int b) {
+      return item_bytes[a].size() + item_vals[a].size() > item_bytes[b].size() + item_vals[b].size();
+    });
 
     Stream& S = P.streams[prec][dir];
     S.bytes.clear();
+    S.values.clear();
     S.units.clear();
     size_t pages = 0;
     for (int it : iorder) {
@@ -1062,7 +1248,23 @@ void emit_streams(PlanHost& P, int prec) {
       e.n_pages = (uint32_t)(item_bytes[it].size() / PB);
       e.m = (uint32_t)items[it][0];
       S.units.push_back(e);
+      // rebase the value references of this item onto the joined value region
+      const uint32_t base16 = (uint32_t)(S.values.size() / 16);
+      if (base16 && !item_vals[it].empty()) {
+        for (size_t pg = 0; pg < item_bytes[it].size() / PB; ++pg) {
+          uint8_t* page = item_bytes[it].data() + pg * PB;
+          for (size_t off = 0; off + sizeof(OpHdr) <= PB;) {
+            OpHdr* h = reinterpret_cast<OpHdr*>(page + off);
+            if (h->bytes == 0) break;
+            if (h->flags & F_VALUES_APART) h->vref += base16;
+            off += h->bytes;
+          }
+        }
+      }
+      if (S.values.size() / 16 + item_vals[it].size() / 16 > 0xFFFFFFFFull)
+        throw std::runtime_error("value region exceeds 64 GB");
       S.bytes.insert(S.bytes.end(), item_bytes[it].begin(), item_bytes[it].end());
+      S.values.insert(S.values.end(), item_vals[it].begin(), item_vals[it].end());
       pages += e.n_pages;
     }
     // trailing QUIT page: a single op of kind 0xFF ends the consumer loop

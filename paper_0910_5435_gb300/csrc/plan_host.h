@@ -63,6 +63,7 @@ struct UnitFact {
 
 struct Stream {
   std::vector<uint8_t> bytes;        // n_pages * page_bytes
+  std::vector<uint8_t> values;       // value region (ops with F_VALUES_APART)
   std::vector<UnitEntry> units;      // LPT order
   int max_buf_ab = 0;                // elements needed in each shared vector
   int num_vecs = 2;                  // shared vectors used (4 with interleaved parities)
@@ -73,6 +74,7 @@ struct PlanHost {
   double eps_id = 0, eps_fp32 = 0, trim_eps = 0;
   int leaf_cols = 64, min_band_rows = 32, num_threads = 0, page_bytes = 16384;
   bool interleave_parities = false;
+  bool values_apart[3] = {true, true, true};  // per precision: value blocks outside the pages
   // Gauss-Legendre nodes (all 2l, ascending), weights, and the angle of each
   // positive node (theta_{l+i} in (0, pi/2)).
   std::vector<double> x, w, theta_pos;

@@ -6,7 +6,10 @@
 // application, Section 2.2 remark after Figure multi).
 //
 // A stream is a sequence of fixed-size PAGES (page_bytes each, the unit of
-// one TMA bulk copy).  A work item (one large order m, or several small
+// one TMA bulk copy), plus, for plans that keep values apart, a VALUE REGION
+// that the executing warp reads directly (coalesced streaming loads): then
+// pages carry only headers and index lists, so the ring of pages in shared
+// memory spans many more ops.  A work item (one large order m, or several small
 // ones) owns a contiguous run of pages; the item table lists them in
 // decreasing size (LPT order for the persistent kernel's work queue).  A
 // page holds a sequence of OPS, each 16-byte aligned:
@@ -38,11 +41,14 @@
 // memory, FOLD forms u_i = s_i (G[m][l+i] +- G[m][l-1-i]) (the parity fold),
 // CLEAR zeroes a shared range, GZERO zeroes node rows of G.
 //
-// Ordering: ops are numbered in stream order.  Op t may start once every op
-// numbered below t - dep has completed (dep = how many immediately preceding
-// ops it may overlap: the ops of one butterfly level are mutually
-// independent, so the i-th op of a level has dep = i, and dep = 0 acts as a
-// barrier).
+// Ordering: ops are numbered in stream order (per CTA).  Op t lists its
+// predecessors as npred deltas d (op t - d) at the start of its index area:
+// the last writer of every shared position / node row it reads or writes and
+// every reader of a position it overwrites.  It starts once they have all
+// completed, so independent blocks (one butterfly level, the two halves of a
+// merge, consecutive orders of one work item) run concurrently.  A work item
+// opens with a JOIN (F_ITEM_START) that waits for every earlier op; ops with
+// no other predecessor depend on it.  Deltas stay below kDoneWindow.
 //
 // Values: float64 (SHT_FP64), float2 {hi, lo} (SHT_SPLIT32) or float
 // (SHT_FP32).  Shared-memory vectors hold complex numbers in the working
@@ -65,16 +71,20 @@ enum OpKind : uint8_t {
   OP_DENSE = 7,
   OP_DENSE_G = 8,     // (a1 = m)
   OP_ANA_INTERP = 9,
+  OP_JOIN = 10,       // no data; completes when its predecessors have (F_ITEM_START: when
+                      //   every earlier op of the CTA has)
   OP_QUIT = 0xFF,
 };
 
 enum OpFlags : uint8_t {
   F_ACCUM = 2,        // DENSE_G / ANA_INTERP: accumulate instead of overwrite
   F_SKEL = 4,         // ANA_INTERP: also the skeleton pass-through (nskel entries)
+  F_ITEM_START = 8,   // JOIN opening a work item
+  F_VALUES_APART = 16,  // the value block lives in the stream's value region (see vref)
 };
 
 struct alignas(16) OpHdr {
-  uint32_t bytes;     // size of this op in bytes (multiple of 16); 0 terminates the page
+  uint32_t bytes;     // size of this op in the page (multiple of 16); 0 terminates the page
   uint8_t kind;
   uint8_t flags;
   uint8_t in_buf;     // shared-memory vector ids 0..3
@@ -84,15 +94,17 @@ struct alignas(16) OpHdr {
   uint16_t nskel;     // SYN_INTERP: M; ANA_INTERP with F_SKEL: pass-through inputs
   uint16_t io;        // element offset of the input vector
   uint16_t oo;        // element offset of the output vector / start of a control range
-  uint16_t dep;       // immediately preceding ops this op may overlap (see above)
+  uint16_t npred;     // predecessor count; the deltas lead the index area (see above)
   uint16_t a0;        // parity
-  uint16_t pad0;
+  uint16_t idx16;     // bytes of the index area / 16
   uint32_t a1;        // order m
-  uint32_t idx_bytes; // bytes of the index area (padded to 16)
+  uint32_t vref;      // F_VALUES_APART: offset of the value block in the value region, in
+                      //   16-byte units; otherwise the values follow the index area
 };
 static_assert(sizeof(OpHdr) == 32, "OpHdr must be 32 bytes");
 
-// Index area contents (uint16, offsets relative to io / oo):
+// Index area contents (uint16): pred[npred] (deltas), then, with offsets
+// relative to io / oo:
 //   SYN_INTERP: red[K] then skel[M]
 //   ANA_INTERP: red[M] then (F_SKEL) skel[nskel]
 //   others:     none
@@ -110,6 +122,9 @@ static_assert(sizeof(UnitEntry) == 16, "UnitEntry must be 16 bytes");
 constexpr int kNumVecs = 4;
 
 constexpr int kMaxM = 32;             // outputs per compute op (one warp)
+constexpr int kMaxPred = 16;          // predecessors listed by a data op (more: fan-in JOIN)
+constexpr int kDoneWindow = 4096;     // completion-tag ring; an item holds < kMaxItemOps ops
+constexpr int kMaxItemOps = 3584;
 constexpr int kConsumerWarps = 8;
 constexpr int kCtlPieces = 8;         // control ops are split into up to this many warp tasks
 

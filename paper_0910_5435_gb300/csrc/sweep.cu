@@ -7,17 +7,16 @@
 //
 // Each CTA is persistent and runs a small dataflow scheduler:
 //   * a producer warp pops work items (orders m) from an LPT-sorted queue
-//     (atomic counter) and streams their factor pages from HBM into a ring of
-//     shared-memory stages with 1-D TMA bulk copies (cp.async.bulk, mbarrier
-//     complete_tx);
-//   * a parser warp numbers the ops of every landed page and publishes them
-//     in an op directory;
-//   * eight consumer warps each claim the next op number, wait until the ops
-//     it depends on have completed (the op's `dep` field: ops of one
-//     butterfly level are independent and run concurrently), and execute it
-//     alone: lanes own consecutive outputs (coalesced reads of the [K][M]
-//     value block), tiny ops split the inner dimension over a few lanes and
-//     reduce with warp shuffles.  No CTA-wide barrier is needed per op; the
+//     (atomic counter) and streams their factor pages from HBM into any free
+//     stage of a ring in shared memory with 1-D TMA bulk copies
+//     (cp.async.bulk, mbarrier complete_tx), recording the issue order;
+//   * a parser warp follows that order, numbers the ops of every landed page
+//     and publishes them in an op directory;
+//   * the consumer warps each claim the next op number, wait until the op's
+//     listed predecessors have completed (completion tags in shared memory),
+//     and execute it alone: lanes own consecutive outputs (coalesced reads of
+//     the [K][M] value block), tiny ops split the inner dimension over a few
+//     lanes and reduce with warp shuffles.  There is no CTA-wide barrier; the
 //     last warp to finish an op of a page returns the page to the producer.
 //
 // Every wait is bounded: on timeout the kernel records SHT_ERR_TIMEOUT in the
@@ -37,6 +36,8 @@ template <int NW>
 constexpr int threads_for() { return (NW + 2) * 32; }  // consumers + producer + parser
 constexpr int kMaxStages = 16;
 constexpr int kDir = 1024;                            // op directory entries (ring)
+constexpr int kOrd = 64;                              // page issue-order ring (>= stages)
+constexpr int kConsumerWarps16 = 16;                  // upper bound on consumer warps
 constexpr long long kTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr unsigned kStatusTimeout = 5;              // SHT_ERR_TIMEOUT
 
@@ -252,15 +253,22 @@ struct TF32 {
 struct Sched {
   int n_ready;    // ops published by the parser (op numbers 0 .. n_ready-1)
   int n_claimed;  // next op number to hand to a consumer warp
-  int n_done;     // ops completed
+  int n_dir_read; // directory entries consumed by claimers
+  int n_done;     // ops completed (any order)
+  int n_issued;   // pages issued by the producer
   int quit;       // number of the QUIT op once parsed, else -1
   int abort;      // set when a bounded wait gave up
   int pending[kMaxStages];  // ops of the page in each stage not yet completed
+  int order[kOrd];          // stage of the i-th issued page (i % kOrd)
   uint32_t dir[kDir];       // op number % kDir -> (stage << 16) | (byte offset / 16)
+  uint16_t done_tag[kDoneWindow];  // low 16 bits of the last completed op number in each slot
 };
 
 __device__ __forceinline__ int vload(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 __device__ __forceinline__ void vstore(int* p, int v) { *reinterpret_cast<volatile int*>(p) = v; }
+__device__ __forceinline__ unsigned vload16(const uint16_t* p) {
+  return *reinterpret_cast<const volatile uint16_t*>(p);
+}
 
 // Lane 0 polls until pred() holds (bounded), the warp then agrees on the outcome.
 template <class Pred>
@@ -290,6 +298,32 @@ __device__ __forceinline__ bool warp_wait(Pred pred, Sched* S, unsigned* status,
   return ok != 0;
 }
 
+// Every lane polls its own predicate (bounded); returns when all hold.
+template <class Pred>
+__device__ __forceinline__ bool warp_wait_all(Pred pred, Sched* S, unsigned* status) {
+  if (__all_sync(0xffffffffu, pred())) {
+    __threadfence_block();
+    return true;
+  }
+  const long long t0 = clock64();
+  for (;;) {
+    __nanosleep(32);
+    if (__all_sync(0xffffffffu, pred())) break;
+    int bad = 0;
+    if ((threadIdx.x & 31) == 0) {
+      if (vload(&S->abort)) bad = 1;
+      else if (clock64() - t0 > kTimeoutCycles) {
+        atomicCAS(status, 0u, kStatusTimeout);
+        vstore(&S->abort, 1);
+        bad = 1;
+      }
+    }
+    if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+  }
+  __threadfence_block();  // acquire what the predecessor ops wrote
+  return true;
+}
+
 // ------------------------------------------------------------ ops
 
 template <class TR>
@@ -302,6 +336,48 @@ struct Vecs {
 
 __device__ __forceinline__ size_t tri_off(int m, int L) { return (size_t)m * L - (size_t)m * (m - 1) / 2; }
 
+template <bool GLOBAL, class T>
+__device__ __forceinline__ T ldv(const T* p) {
+  if constexpr (GLOBAL) {
+    return __ldcs(p);  // streamed once per launch: evict-first
+  } else {
+    return *p;
+  }
+}
+
+// Accumulates lane o's dot product over the inner indices s = q, q + ks, ...
+template <class TR, bool GLOBAL>
+__device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, const typename TR::C* in,
+                                                     const uint16_t* idx, bool gather, int M, int K, int o, int q,
+                                                     int ks) {
+  using C = typename TR::C;
+  using V = typename TR::V;
+  using Acc = typename TR::Acc;
+  // four independent accumulators; loads are issued ahead of the FMAs
+  Acc a0 = TR::zero(), a1 = TR::zero(), a2 = TR::zero(), a3 = TR::zero();
+  int s = q;
+  for (; s + 3 * ks < K; s += 4 * ks) {
+    const int s1 = s + ks, s2 = s + 2 * ks, s3 = s + 3 * ks;
+    const V v0 = ldv<GLOBAL>(val + (size_t)s * M + o);
+    const V v1 = ldv<GLOBAL>(val + (size_t)s1 * M + o);
+    const V v2 = ldv<GLOBAL>(val + (size_t)s2 * M + o);
+    const V v3 = ldv<GLOBAL>(val + (size_t)s3 * M + o);
+    const C x0 = in[gather ? (int)idx[s] : s];
+    const C x1 = in[gather ? (int)idx[s1] : s1];
+    const C x2 = in[gather ? (int)idx[s2] : s2];
+    const C x3 = in[gather ? (int)idx[s3] : s3];
+    TR::fma(a0, v0, x0);
+    TR::fma(a1, v1, x1);
+    TR::fma(a2, v2, x2);
+    TR::fma(a3, v3, x3);
+  }
+  for (; s < K; s += ks) TR::fma(a0, ldv<GLOBAL>(val + (size_t)s * M + o), in[gather ? (int)idx[s] : s]);
+  TR::merge(a0, a1);
+  TR::merge(a2, a3);
+  TR::merge(a0, a2);
+  return a0;
+}
+
 // One compute op (SYN_INTERP, DENSE, DENSE_G, ANA_INTERP), executed by one warp.
 template <class TR>
 __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, const Vecs<TR>& S, const SweepArgs& A,
@@ -311,8 +387,10 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
   using Acc = typename TR::Acc;
   using IO = typename TR::IO;
   const int M = h.M, K = h.K;
-  const uint16_t* idx = reinterpret_cast<const uint16_t*>(op + sizeof(OpHdr));
-  const V* val = reinterpret_cast<const V*>(op + sizeof(OpHdr) + h.idx_bytes);
+  const uint16_t* idx = reinterpret_cast<const uint16_t*>(op + sizeof(OpHdr)) + h.npred;
+  const bool apart = (h.flags & F_VALUES_APART) != 0;
+  const V* val = apart ? reinterpret_cast<const V*>(A.values + (size_t)h.vref * 16)
+                       : reinterpret_cast<const V*>(op + sizeof(OpHdr) + (size_t)h.idx16 * 16);
   const C* in = S.buf(h.in_buf) + h.io;
   C* out = S.buf(h.out_buf) + h.oo;
   const bool gather = (h.kind == OP_SYN_INTERP);
@@ -323,31 +401,10 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
     while (((2 << lks) * M) <= 32) ++lks;
     const int ks = 1 << lks;
     const int o = lane >> lks, q = lane & (ks - 1);
-    // four independent accumulators: float64 FMA latency on GB300 needs many
-    // FMAs in flight per SMSP
-    Acc a0 = TR::zero(), a1 = TR::zero(), a2 = TR::zero(), a3 = TR::zero();
-    if (o < M) {
-      int s = q;
-      for (; s + 3 * ks < K; s += 4 * ks) {
-        const int s1 = s + ks, s2 = s + 2 * ks, s3 = s + 3 * ks;
-        const V v0 = val[(size_t)s * M + o];
-        const V v1 = val[(size_t)s1 * M + o];
-        const V v2 = val[(size_t)s2 * M + o];
-        const V v3 = val[(size_t)s3 * M + o];
-        const C x0 = in[gather ? (int)idx[s] : s];
-        const C x1 = in[gather ? (int)idx[s1] : s1];
-        const C x2 = in[gather ? (int)idx[s2] : s2];
-        const C x3 = in[gather ? (int)idx[s3] : s3];
-        TR::fma(a0, v0, x0);
-        TR::fma(a1, v1, x1);
-        TR::fma(a2, v2, x2);
-        TR::fma(a3, v3, x3);
-      }
-      for (; s < K; s += ks) TR::fma(a0, val[(size_t)s * M + o], in[gather ? (int)idx[s] : s]);
-      TR::merge(a0, a1);
-      TR::merge(a2, a3);
-      TR::merge(a0, a2);
-    }
+    Acc a0 = TR::zero();
+    if (o < M)
+      a0 = apart ? gemv_dot<TR, true>(val, in, idx, gather, M, K, o, q, ks)
+                 : gemv_dot<TR, false>(val, in, idx, gather, M, K, o, q, ks);
     for (int off = ks >> 1; off > 0; off >>= 1) {
       const Acc b = TR::shfl_xor(a0, off);
       TR::merge(a0, b);
@@ -466,12 +523,38 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
   const uint32_t PB = (uint32_t)A.page_bytes;
   const int NST = A.nstages;
   volatile int* abort_flag = &S->abort;
-  int stage = 0;
-  uint32_t phase = 0;
-  int issued_phase[kMaxStages];
-  for (int s = 0; s < kMaxStages; ++s) issued_phase[s] = -1;
-  bool ok = true;
+  int uses[kMaxStages];  // pages copied into each stage so far
+  for (int s = 0; s < kMaxStages; ++s) uses[s] = 0;
+  int issued = 0;
   unsigned long long c_wait = 0;
+  // any stage whose previous page has been fully consumed may be refilled
+  auto free_stage = [&]() -> int {
+    const long long t0 = clock64();
+    for (int spin = 0;; ++spin) {
+      for (int s = 0; s < NST; ++s)
+        if (mbar_try_wait(empty + s, (uint32_t)((uses[s] & 1) ^ 1))) {
+          c_wait += clock64() - t0;
+          return s;
+        }
+      if (*abort_flag) return -1;
+      if (clock64() - t0 > kTimeoutCycles) {
+        atomicCAS(A.status, 0u, kStatusTimeout);
+        *abort_flag = 1;
+        return -1;
+      }
+      __nanosleep(64);
+    }
+  };
+  auto issue = [&](int s, uint64_t page) {
+    mbar_arrive_expect_tx(full + s, PB);
+    bulk_g2s(stages + (size_t)s * PB, A.pages + (size_t)page * PB, PB, full + s);
+    ++uses[s];
+    S->order[issued % kOrd] = s;
+    ++issued;
+    __threadfence_block();
+    vstore(&S->n_issued, issued);
+  };
+  bool ok = true;
   for (;;) {
     if (*abort_flag) {
       ok = false;
@@ -485,42 +568,47 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
     }
     const UnitEntry e = A.units[u];
     for (uint32_t pg = 0; pg < e.n_pages; ++pg) {
-      const long long w0 = clock64();
-      if (!wait_bounded(empty + stage, phase ^ 1u, A.status, abort_flag)) {
+      const int s = free_stage();
+      if (s < 0) {
         ok = false;
         break;
       }
-      c_wait += clock64() - w0;
-      mbar_arrive_expect_tx(full + stage, PB);
-      bulk_g2s(stages + (size_t)stage * PB, A.pages + (size_t)(e.first_page + pg) * PB, PB, full + stage);
-      issued_phase[stage] = (int)phase;
-      if (++stage == NST) {
-        stage = 0;
-        phase ^= 1u;
-      }
+      issue(s, e.first_page + pg);
     }
     if (!ok) break;
   }
-  if (ok && wait_bounded(empty + stage, phase ^ 1u, A.status, abort_flag)) {
-    mbar_arrive_expect_tx(full + stage, PB);
-    bulk_g2s(stages + (size_t)stage * PB, A.pages + (size_t)A.quit_page * PB, PB, full + stage);
-    issued_phase[stage] = (int)phase;
+  if (ok) {
+    const int s = free_stage();
+    if (s >= 0) issue(s, A.quit_page);
   }
   // never leave the CTA with bulk copies still landing in its shared memory
   for (int s = 0; s < NST; ++s)
-    if (issued_phase[s] >= 0) wait_bounded(full + s, (uint32_t)issued_phase[s], A.status, abort_flag);
+    if (uses[s] > 0) wait_bounded(full + s, (uint32_t)((uses[s] - 1) & 1), A.status, abort_flag);
   trace_add(A, TR_PROD_WAIT, c_wait);
 }
 
 __device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* full, Sched* S) {
   const size_t PB = (size_t)A.page_bytes;
-  const int NST = A.nstages;
-  int stage = 0, ticket = 0;
-  uint32_t phase = 0;
+  int parsed[kMaxStages];  // pages parsed from each stage so far
+  for (int s = 0; s < kMaxStages; ++s) parsed[s] = 0;
+  int ticket = 0;
   unsigned long long c_wait = 0;
-  for (;;) {
+  for (int k = 0;; ++k) {
     const long long w0 = clock64();
-    if (!wait_bounded(full + stage, phase, A.status, &S->abort)) return;
+    // the k-th issued page: which stage, then wait for its bytes
+    while (vload(&S->n_issued) <= k) {
+      if (vload(&S->abort)) return;
+      if (clock64() - w0 > kTimeoutCycles) {
+        atomicCAS(A.status, 0u, kStatusTimeout);
+        vstore(&S->abort, 1);
+        return;
+      }
+      __nanosleep(32);
+    }
+    __threadfence_block();
+    const int stage = vload(&S->order[k % kOrd]);
+    if (!wait_bounded(full + stage, (uint32_t)(parsed[stage] & 1), A.status, &S->abort)) return;
+    ++parsed[stage];
     c_wait += clock64() - w0;
     const uint8_t* page = stages + (size_t)stage * PB;
     int count = 0;
@@ -538,10 +626,10 @@ __device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t*
     vstore(&S->pending[stage], count);
     size_t off = 0;
     for (int i = 0; i < count; ++i) {
-      // keep the directory ring from overwriting entries still in use
-      if (ticket - vload(&S->n_done) >= kDir) {
+      // keep the directory ring from overwriting entries not yet read
+      if (ticket - vload(&S->n_dir_read) >= kDir - kConsumerWarps16) {
         const long long t0 = clock64();
-        while (ticket - vload(&S->n_done) >= kDir) {
+        while (ticket - vload(&S->n_dir_read) >= kDir - kConsumerWarps16) {
           if (vload(&S->abort)) return;
           if (clock64() - t0 > kTimeoutCycles) {
             atomicCAS(A.status, 0u, kStatusTimeout);
@@ -562,10 +650,6 @@ __device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t*
       vstore(&S->quit, ticket);
       trace_add(A, TR_PARSE_WAIT, c_wait);
       return;
-    }
-    if (++stage == NST) {
-      stage = 0;
-      phase ^= 1u;
     }
   }
 }
@@ -588,20 +672,38 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
     const int q = vload(&S->quit);
     if (q >= 0 && t >= q) break;
     const uint32_t e = S->dir[t % kDir];
+    __syncwarp();
+    if (lane == 0) atomicAdd(&S->n_dir_read, 1);
     const int stage = (int)(e >> 16);
     const uint8_t* op = stages + (size_t)stage * PB + ((size_t)(e & 0xffffu) << 4);
     const OpHdr h = *reinterpret_cast<const OpHdr*>(op);
-    const int need = t - (int)h.dep;
     const long long t1 = clock64();
-    if (!warp_wait([&] { return vload(&S->n_done) >= need; }, S, A.status, lane)) break;
+    bool ok;
+    if (h.kind == OP_JOIN && (h.flags & F_ITEM_START)) {
+      // a work item starts once every earlier op of this CTA has completed
+      ok = warp_wait([&] { return vload(&S->n_done) >= t; }, S, A.status, lane);
+    } else {
+      // lanes watch the listed predecessors (32 at a time)
+      const uint16_t* pred = reinterpret_cast<const uint16_t*>(op + sizeof(OpHdr));
+      ok = true;
+      for (int base = 0; base < h.npred && ok; base += 32) {
+        const int i = base + lane;
+        const int u = (i < h.npred) ? t - (int)pred[i] : -1;
+        const unsigned want = (unsigned)(u & 0xffff);
+        const uint16_t* slot = S->done_tag + (u >= 0 ? (u % kDoneWindow) : 0);
+        ok = warp_wait_all([&] { return u < 0 || vload16(slot) == want; }, S, A.status);
+      }
+    }
+    if (!ok) break;
     const long long t2 = clock64();
-    if (h.kind >= OP_SYN_INTERP)
+    if (h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP)
       run_gemv<TR>(h, op, V, A, lane);
-    else
+    else if (h.kind != OP_JOIN)
       run_control<TR>(h, V, A, lane);
-    __threadfence_block();  // release this op's results before counting it done
+    __threadfence_block();  // this op's results are visible before it is marked done
     __syncwarp();
     if (lane == 0) {
+      *reinterpret_cast<volatile uint16_t*>(&S->done_tag[t % kDoneWindow]) = (uint16_t)(t & 0xffff);
       atomicAdd(&S->n_done, 1);
       if (atomicSub(&S->pending[stage], 1) == 1) mbar_arrive(empty + stage);
     }
@@ -639,11 +741,16 @@ __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const Swe
     }
     S->n_ready = 0;
     S->n_claimed = 0;
+    S->n_dir_read = 0;
     S->n_done = 0;
+    S->n_issued = 0;
     S->quit = -1;
     S->abort = 0;
     fence_mbar_init();
   }
+  // completion tags start as "op slot - window", which no op number in the
+  // first window matches
+  for (int i = tid; i < kDoneWindow; i += blockDim.x) S->done_tag[i] = (uint16_t)((i - kDoneWindow) & 0xffff);
   __syncthreads();
 
   if (warp == NW) {

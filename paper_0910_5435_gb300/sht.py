@@ -54,6 +54,7 @@ class sht_plan_opts(ctypes.Structure):
         ("page_bytes", ctypes.c_int),
         ("eps_fp32", ctypes.c_double),
         ("consumer_warps", ctypes.c_int),
+        ("values_inline", ctypes.c_int),
     ]
 
 
@@ -113,7 +114,8 @@ def lib():
     L.sht_plan_get_stats.argtypes = [vp, ctypes.POINTER(sht_plan_stats)]
     L.sht_prepare.argtypes = [vp, c_int]
     L.sht_plan_nodes.argtypes = [vp, vp, vp]
-    L.sht_plan_stream.argtypes = [vp, c_int, c_int, vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.sht_plan_stream.argtypes = [vp, c_int, c_int, vp, ctypes.POINTER(ctypes.c_size_t),
+                                  ctypes.POINTER(ctypes.c_size_t)]
     for name in ["sht_legendre_synthesize", "sht_legendre_analyze", "sht_legendre_synthesize_adjoint"]:
         getattr(L, name).argtypes = [vp, c_int, vp, vp, vp]
     L.sht_last_device_status.argtypes = [vp, vp]
@@ -166,7 +168,7 @@ class Plan:
     """Owns an ``sht_plan_t`` (``sht_plan_create_ex`` / ``sht_plan_destroy``)."""
 
     def __init__(self, l, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, host_only=False,
-                 num_threads=0, page_bytes=0, eps_fp32=0.0, consumer_warps=0):
+                 num_threads=0, page_bytes=0, eps_fp32=0.0, consumer_warps=0, values_inline=0):
         L = lib()
         opts = sht_plan_opts()
         _check(L.sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
@@ -178,6 +180,7 @@ class Plan:
         opts.page_bytes = page_bytes
         opts.eps_fp32 = eps_fp32
         opts.consumer_warps = consumer_warps
+        opts.values_inline = values_inline
         h = ctypes.c_void_p()
         _check(L.sht_plan_create_ex(int(l), float(eps_id), ctypes.byref(opts), ctypes.byref(h)),
                "sht_plan_create_ex")
@@ -211,13 +214,15 @@ class Plan:
         return x, w
 
     def stream(self, prec, direction):
+        """(pages, values): the page region and the value region of a factor stream."""
         n = ctypes.c_size_t(0)
-        _check(lib().sht_plan_stream(self.handle, int(prec), int(direction), None, ctypes.byref(n)),
-               "sht_plan_stream")
+        npg = ctypes.c_size_t(0)
+        _check(lib().sht_plan_stream(self.handle, int(prec), int(direction), None, ctypes.byref(n),
+                                     ctypes.byref(npg)), "sht_plan_stream")
         buf = np.zeros(n.value, dtype=np.uint8)
-        _check(lib().sht_plan_stream(self.handle, int(prec), int(direction), buf.ctypes.data, ctypes.byref(n)),
-               "sht_plan_stream")
-        return buf
+        _check(lib().sht_plan_stream(self.handle, int(prec), int(direction), buf.ctypes.data, ctypes.byref(n),
+                                     ctypes.byref(npg)), "sht_plan_stream")
+        return buf[:npg.value], buf[npg.value:]
 
 
 def sht_legendre_synthesize(plan, prec, beta, G, stream=None):

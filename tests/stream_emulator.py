@@ -6,30 +6,38 @@ valid serialization of the kernel's concurrent execution).  It separates
 errors of the host precomputation (nodes, recurrence, IDs, op emission) from
 errors of the CUDA kernels.
 
-``check_races`` verifies the ordering annotations: op t may overlap the ops
-numbered t - dep .. t - 1, so it must neither write anything those ops read or
-write, nor read anything they write.
+``check_races`` verifies the ordering annotations: within a work item (opened
+by a JOIN that waits for everything before it), op t may overlap every earlier
+op that is not among its transitive predecessors, so it must neither write
+anything such an op reads or writes, nor read anything it writes.
 """
 
 import numpy as np
 
 OPHDR = np.dtype([
     ("bytes", "<u4"), ("kind", "u1"), ("flags", "u1"), ("in_buf", "u1"), ("out_buf", "u1"),
-    ("M", "<u2"), ("K", "<u2"), ("nskel", "<u2"), ("io", "<u2"), ("oo", "<u2"), ("dep", "<u2"),
-    ("a0", "<u2"), ("pad0", "<u2"), ("a1", "<u4"), ("idx_bytes", "<u4"),
+    ("M", "<u2"), ("K", "<u2"), ("nskel", "<u2"), ("io", "<u2"), ("oo", "<u2"), ("npred", "<u2"),
+    ("a0", "<u2"), ("idx16", "<u2"), ("a1", "<u4"), ("vref", "<u4"),
 ])
 assert OPHDR.itemsize == 32
 
-OP_GATHER, OP_SCATTER, OP_FOLD, OP_CLEAR, OP_GZERO, OP_SYN, OP_DENSE, OP_DENSE_G, OP_ANA = range(1, 10)
+OP_GATHER, OP_SCATTER, OP_FOLD, OP_CLEAR, OP_GZERO, OP_SYN, OP_DENSE, OP_DENSE_G, OP_ANA, OP_JOIN = range(1, 11)
 OP_QUIT = 0xFF
-F_ACCUM, F_SKEL = 2, 4
+F_ACCUM, F_SKEL, F_ITEM_START, F_VALUES_APART = 2, 4, 8, 16
 
 
-def iter_ops(stream, page_bytes):
-    """Yields (header, index array, value bytes) for every op, in order."""
-    npages = len(stream) // page_bytes
+def iter_ops(stream, page_bytes, with_preds=False):
+    """Yields (header, index array, value bytes) for every op, in order.
+    ``stream`` is the (pages, values) pair of Plan.stream (or the page region
+    alone); the index array excludes the leading predecessor deltas unless
+    with_preds."""
+    if isinstance(stream, tuple):
+        pages, values = stream
+    else:
+        pages, values = stream, None
+    npages = len(pages) // page_bytes
     for pg in range(npages):
-        page = stream[pg * page_bytes:(pg + 1) * page_bytes]
+        page = pages[pg * page_bytes:(pg + 1) * page_bytes]
         off = 0
         while off + 32 <= page_bytes:
             h = page[off:off + 32].view(OPHDR)[0]
@@ -37,9 +45,14 @@ def iter_ops(stream, page_bytes):
                 break
             if h["kind"] == OP_QUIT:
                 return
-            ib = int(h["idx_bytes"])
+            ib = 16 * int(h["idx16"])
             idx = page[off + 32:off + 32 + ib].view("<u2")
-            vals = page[off + 32 + ib:off + int(h["bytes"])]
+            if not with_preds:
+                idx = idx[int(h["npred"]):]
+            if h["flags"] & F_VALUES_APART:
+                vals = values[16 * int(h["vref"]):]
+            else:
+                vals = page[off + 32 + ib:off + int(h["bytes"])]
             yield h, idx, vals
             off += int(h["bytes"])
 
@@ -78,6 +91,8 @@ def emulate(stream, page_bytes, l, prec, direction, inp, prescale=None, twiddle=
         src, dst = bufs[int(h["in_buf"])], bufs[int(h["out_buf"])]
         acc = bool(h["flags"] & F_ACCUM)
         tw = 1.0 if twiddle is None else twiddle[m]
+        if kind == OP_JOIN:
+            continue
         if kind == OP_GATHER:
             dst[oo:oo + M] = beta[tri[m] + p + 2 * (oo + np.arange(M))]
         elif kind == OP_SCATTER:
@@ -175,17 +190,34 @@ def _access_sets(h, idx, l):
 
 
 def check_races(stream, page_bytes, l):
-    """Returns a list of (t, u) op pairs that may overlap but conflict."""
-    ops = list(iter_ops(stream, page_bytes))
-    sets = [_access_sets(h, idx, l) for h, idx, _ in ops]
+    """Returns (t, u) op pairs (stream positions) that may overlap but conflict."""
+    ops = list(iter_ops(stream, page_bytes, with_preds=True))
     bad = []
-    for t, (h, _, _) in enumerate(ops):
-        dep = int(h["dep"])
-        Rt, Wt = sets[t]
-        for u in range(max(0, t - dep), t):
-            Ru, Wu = sets[u]
-            if (Wt & (Ru | Wu)) or (Rt & Wu):
-                bad.append((t, u))
+    start = 0
+    while start < len(ops):
+        end = start + 1
+        while end < len(ops) and not (ops[end][0]["kind"] == OP_JOIN and ops[end][0]["flags"] & F_ITEM_START):
+            end += 1
+        anc = []  # transitive predecessors (positions within the item) as int bitsets
+        sets = []
+        for t in range(start, end):
+            h, idx, _ = ops[t]
+            npred = int(h["npred"])
+            a = 0
+            for d in idx[:npred]:
+                u = t - int(d) - start
+                assert 0 <= u < t - start, "predecessor outside its work item"
+                a |= anc[u] | (1 << u)
+            anc.append(a)
+            sets.append(_access_sets(h, idx[npred:], l))
+            Rt, Wt = sets[-1]
+            for u in range(t - start):
+                if (a >> u) & 1:
+                    continue
+                Ru, Wu = sets[u]
+                if (Wt & (Ru | Wu)) or (Rt & Wu):
+                    bad.append((t, start + u))
+        start = end
     return bad
 
 

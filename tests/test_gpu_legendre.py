@@ -172,3 +172,18 @@ def test_misaligned_and_null_pointers_rejected(sht):
         sht.sht_legendre_synthesize(P, 0, 0, G)
     with pytest.raises(sht.ShtError):
         sht.sht_legendre_synthesize(P, 7, b, G)
+
+
+@pytest.mark.parametrize("values_inline", [0, 1])
+@pytest.mark.parametrize("prec", [0, 2, 1])
+def test_both_value_layouts_on_gpu(sht, values_inline, prec):
+    """Values streamed by the executing warp, or staged in the TMA pages: same
+    results (float64 layouts agree to rounding; both match the oracle)."""
+    l = 128
+    P = plan(sht, l, 16, values_inline=values_inline)
+    beta = inputs.random_beta(l, seed=31)
+    G = run_synth(sht, P, prec, beta)
+    assert rel(G, oracle.legendre_synthesis(beta, l)) < TOL[prec]
+    Gin = inputs.random_G(l, seed=32)
+    b = run_analysis(sht, P, prec, Gin)
+    assert rel(b, oracle.legendre_analysis(Gin, l)) < TOL[prec]

@@ -136,23 +136,38 @@ def test_op_ordering_is_race_free(l, C, prec):
 
 
 def test_race_checker_catches_a_planted_overlap():
-    """The checker itself: letting the first interpolation op of a real stream
-    overlap the ops before it (the gather pieces that write its input) must be
-    reported."""
+    """The checker itself: dropping the predecessors of the first interpolation
+    op of a real stream (it would no longer wait for the gather that writes its
+    input) must be reported."""
     from tests.stream_emulator import OPHDR
     P = sht.Plan(64, 1e-12, leaf_cols=16, host_only=True)
-    st = P.stream(0, 0).copy()
-    for pg in range(len(st) // PB):
+    pages, values = P.stream(0, 0)
+    st = (pages.copy(), values)
+    for pg in range(len(st[0]) // PB):
         base = pg * PB
         off = 0
         while off + 32 <= PB:
-            h = st[base + off:base + off + 32].view(OPHDR)
+            h = st[0][base + off:base + off + 32].view(OPHDR)
             if h[0]["bytes"] == 0:
                 break
-            if h[0]["kind"] == 6 and h[0]["dep"] == 0:
+            if h[0]["kind"] == 6:
                 assert check_races(st, PB, 64) == []
-                h[0]["dep"] = 64
+                h[0]["npred"] = 0  # no predecessors: may overlap the gathers
                 assert check_races(st, PB, 64) != []
                 return
             off += int(h[0]["bytes"])
     raise AssertionError("no interpolation op found")
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_values_inline_layout_reproduces_oracle(prec):
+    """The alternative layout (values inside the TMA pages) encodes the same
+    operator as the default (values in their own region)."""
+    l = 64
+    P = sht.Plan(l, 1e-12, leaf_cols=16, values_inline=1, host_only=True)
+    pages, values = P.stream(prec, 0)
+    assert values.size == 0
+    beta = inputs.random_beta(l, seed=21)
+    G = emulate((pages, values), PB, l, prec, 0, beta)
+    assert rel(G, oracle.legendre_synthesis(beta, l)) < (2e-5 if prec == 1 else 1e-10)
+    assert check_races(P.stream(prec, 1), PB, l) == []
