@@ -41,8 +41,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--l", type=int, default=1024)
     ap.add_argument("--leaf-cols", type=int, default=32)
-    ap.add_argument("--page-bytes", type=int, default=32768)
-    ap.add_argument("--consumer-warps", type=int, default=8)
+    ap.add_argument("--page-bytes", type=int, default=8192)
+    ap.add_argument("--consumer-warps", type=int, default=0)
     ap.add_argument("--eps", type=float, default=1e-12)
     ap.add_argument("--no-extras", action="store_true", help="skip the split32/fp32/direct legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")

@@ -101,17 +101,20 @@ typedef struct {
   /* Host threads for the precomputation; 0 = all hardware threads. */
   int num_threads;
   /* Bytes per streamed factor page (TMA bulk-copy unit, multiple of 1024,
-   * 4096..49152); 0 = default (16384). */
+   * 4096..49152); 0 = default (8192). */
   int page_bytes;
   /* eps used for the IDs of the SHT_FP32 factors; <= 0 selects
    * max(eps_id, 1e-7).  (FP32 cannot use ranks below its own precision.) */
   double eps_fp32;
   /* Warps per CTA of the sweep kernels that execute ops (8 or 16; 0 =
-   * default 8).  A tuning knob; results do not depend on it. */
+   * per precision: 8 for SHT_FP64 and SHT_SPLIT32, 16 for SHT_FP32).  A
+   * tuning knob; results do not depend on it. */
   int consumer_warps;
   /* 1: factor values travel inside the TMA-staged pages; 0 (default): they
-   * sit in a separate region that the executing warp streams directly, and
-   * the pages carry only op headers and index lists.  A tuning knob. */
+   * sit in a separate region, the pages carry only op headers and index
+   * lists, and each executing warp bulk-copies the value block of its next
+   * op into one of its two shared-memory slots while it runs the current
+   * one (ops hold at most 1024 values).  A tuning knob. */
   int values_inline;
 } sht_plan_opts;
 
@@ -141,6 +144,7 @@ typedef struct {
   double t_upload;       /* seconds: device upload of the prepared precisions */
   long long m_max_words; /* peak float64 words held by one unit's depth-first build */
   int smem_bytes;        /* dynamic shared memory of the sweep kernels */
+  int page_bytes;        /* bytes per factor page (the value in effect) */
 } sht_plan_stats;
 
 /* Fills *opts with the defaults listed above. */

@@ -60,8 +60,10 @@ struct sht_plan_s {
   bool host_only = false;
   int device = -1;
   int num_sms = 0;
-  int consumer_warps = 16;
+  int consumer_warps[kNumPrec] = {8, 8, 8};
   int nstages[kNumPrec] = {4, 4, 4};
+  bool staged[kNumPrec] = {false, false, false};
+  int num_vecs[kNumPrec] = {2, 2, 2};
   int ctas_per_sm[kNumPrec] = {1, 1, 1};
   DevStream dev[kNumPrec][2];
   bool dev_ready[kNumPrec] = {false, false, false};
@@ -190,6 +192,7 @@ void fill_stats(sht_plan_t P) {
   s.t_quad = H.t_quad;
   s.t_comp = H.t_comp;
   s.smem_bytes = (int)std::max({P->smem[0], P->smem[1], P->smem[2]});
+  s.page_bytes = P->H.page_bytes;
 }
 
 // Host build of one precision's streams (factorization + page encoding).
@@ -244,11 +247,15 @@ sht_status upload(sht_plan_t P, int q) {
   // the limit is a per-kernel setting shared by every plan: raise it to the
   // device maximum once instead of to this plan's size
   CK(sht::sweep_configure(q, (size_t)optin));
+  // values kept apart are staged per warp when the slots fit next to a ring
+  // of at least two pages; otherwise the warps stream them from HBM
+  bool staged = P->H.values_apart[q] &&
+                sht::sweep_smem_bytes(q, P->H.page_bytes, 2, buf_ab, nvecs, P->consumer_warps[q], true) <= (size_t)optin;
   int best_nst = 0, best_ctas = 0;
   for (int nst = 8; nst >= 2; --nst) {
-    const size_t sm = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, nvecs);
+    const size_t sm = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, nvecs, P->consumer_warps[q], staged);
     if (sm > (size_t)optin) continue;
-    const int ctas = std::min(2, sht::sweep_blocks_per_sm(q, P->consumer_warps, sm));
+    const int ctas = std::min(2, sht::sweep_blocks_per_sm(q, P->consumer_warps[q], sm));
     const bool better = (ctas > best_ctas && (nst >= 3 || best_ctas == 0)) || best_ctas == 0;
     if (better) {
       best_nst = nst;
@@ -258,7 +265,9 @@ sht_status upload(sht_plan_t P, int q) {
   if (best_nst == 0) return SHT_ERR_UNSUPPORTED;
   P->nstages[q] = best_nst;
   P->ctas_per_sm[q] = best_ctas;
-  P->smem[q] = sht::sweep_smem_bytes(q, P->H.page_bytes, best_nst, buf_ab, nvecs);
+  P->smem[q] = sht::sweep_smem_bytes(q, P->H.page_bytes, best_nst, buf_ab, nvecs, P->consumer_warps[q], staged);
+  P->staged[q] = staged;
+  P->num_vecs[q] = nvecs;
   P->dev[q][0].buf_ab = P->dev[q][1].buf_ab = buf_ab;
   P->dev_ready[q] = true;
   P->stats.t_upload += now_s() - t0;
@@ -309,11 +318,13 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.prescale = prescale;
   a.twiddle = twiddle;
   a.trace = P->d_trace;
+  a.num_vecs = P->num_vecs[q];
+  a.staged = P->staged[q] ? 1 : 0;
   a.counter = P->d_scratch + (q * KIND_COUNT + kind);
   a.status = P->d_scratch + kNumPrec * KIND_COUNT;
   const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
   (void)cudaGetLastError();  // do not report a stale error left by an earlier call (e.g. inside cuFFT)
-  CK(sht::sweep_launch(q, P->consumer_warps, a, grid, P->smem[q], reinterpret_cast<cudaStream_t>(stream)));
+  CK(sht::sweep_launch(q, P->consumer_warps[q], a, grid, P->smem[q], reinterpret_cast<cudaStream_t>(stream)));
   return SHT_OK;
 }
 
@@ -347,7 +358,7 @@ sht_status sht_plan_opts_default(sht_plan_opts* o) {
   o->num_threads = 0;
   o->page_bytes = 16384;
   o->eps_fp32 = 0.0;
-  o->consumer_warps = 8;
+  o->consumer_warps = 0;
   o->values_inline = 0;
   return SHT_OK;
 }
@@ -365,20 +376,22 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   } else {
     sht_plan_opts_default(&o);
   }
-  if (o.page_bytes == 0) o.page_bytes = 16384;
+  if (o.page_bytes == 0) o.page_bytes = 8192;
   if (o.min_band_rows <= 0) o.min_band_rows = std::max(1, o.leaf_cols / 2);
   if (l < 1 || l > 1024 || !(eps_id > 0.0) || !(eps_id < 1.0)) return SHT_ERR_INVALID_ARG;
   if (o.leaf_cols < 2 || o.leaf_cols > 1024) return SHT_ERR_INVALID_ARG;
   if (o.page_bytes < 4096 || o.page_bytes > 49152 || (o.page_bytes % 1024) != 0) return SHT_ERR_INVALID_ARG;
   if (o.num_threads < 0) return SHT_ERR_INVALID_ARG;
-  if (o.consumer_warps == 0) o.consumer_warps = 8;
-  if (o.consumer_warps != 8 && o.consumer_warps != 16) return SHT_ERR_INVALID_ARG;
+  if (o.consumer_warps != 0 && o.consumer_warps != 8 && o.consumer_warps != 16) return SHT_ERR_INVALID_ARG;
 
   sht_plan_t P = new (std::nothrow) sht_plan_s();
   if (!P) return SHT_ERR_OOM;
   P->opts = o;
   P->host_only = o.host_only != 0;
-  P->consumer_warps = o.consumer_warps;
+  // 0 = per precision: float32 ops are short and latency-bound, so that
+  // sweep runs twice the warps (its staging slots are half the size)
+  for (int q = 0; q < kNumPrec; ++q)
+    P->consumer_warps[q] = o.consumer_warps ? o.consumer_warps : (q == sht::PREC_FP32 ? 16 : 8);
   PlanHost& H = P->H;
   H.l = l;
   H.eps_id = eps_id;

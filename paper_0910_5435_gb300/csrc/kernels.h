@@ -27,16 +27,20 @@ struct SweepArgs {
   unsigned* counter;           // work-queue counter (self-resetting; 0 between launches)
   unsigned* status;            // device status word (0 = ok)
   unsigned long long* trace;   // kTraceSlots cycle counters accumulated over all CTAs, or nullptr
+  int num_vecs;                // shared vectors (2, or 4 with interleaved parities)
+  int staged;                  // 1: each consumer warp stages op values in two shared slots
 };
 
 // Trace slots (clock64 cycles summed over CTAs): consumer warps executing ops,
 // waiting for an op to be published, waiting for its dependencies; producer
 // waiting for a free page; parser waiting for a landed page; ops executed.
-enum TraceSlot { TR_EXEC = 0, TR_WAIT_READY, TR_WAIT_DEP, TR_PROD_WAIT, TR_PARSE_WAIT, TR_OPS, kTraceSlots = 8 };
+enum TraceSlot {
+  TR_EXEC = 0, TR_WAIT_READY, TR_WAIT_DEP, TR_PROD_WAIT, TR_PARSE_WAIT, TR_OPS, TR_WAIT_VALUES, kTraceSlots = 8
+};
 
 enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2 };
 
-size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs);
+size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, bool staged);
 cudaError_t sweep_configure(int prec, size_t smem);
 // resident CTAs per SM for this shared-memory size (>= 1); nw = consumer warps (8 or 16)
 int sweep_blocks_per_sm(int prec, int nw, size_t smem);

@@ -627,10 +627,14 @@ struct Emitter {
     h.flags = flags;
     return h;
   }
-  // bytes of an op with nidx index entries and nval values, leaving room for
-  // the largest predecessor list (the actual list may be shorter)
+  // Page bytes of an op with nidx index entries and nval values, leaving room
+  // for the largest predecessor list (the actual list may be shorter).  With
+  // values kept apart the page holds only the header and indices, and the
+  // value block must fit one warp's staging slot (kValueSlotVals values).
   size_t bytes_of(size_t nidx, size_t nval) const {
-    return sizeof(OpHdr) + pad16(2 * (nidx + kMaxPred)) + pad16(vs * nval);
+    const size_t meta = sizeof(OpHdr) + pad16(2 * (nidx + kMaxPred));
+    if (values) return nval <= (size_t)kValueSlotVals ? meta : ~size_t(0) / 2;
+    return meta + pad16(vs * nval);
   }
 
   // Reads and writes of one op, as keys: (vec << 20 | pos) for shared

@@ -72,7 +72,7 @@ struct Stream {
 struct PlanHost {
   int l = 0;
   double eps_id = 0, eps_fp32 = 0, trim_eps = 0;
-  int leaf_cols = 64, min_band_rows = 32, num_threads = 0, page_bytes = 16384;
+  int leaf_cols = 64, min_band_rows = 32, num_threads = 0, page_bytes = 8192;
   bool interleave_parities = false;
   bool values_apart[3] = {true, true, true};  // per precision: value blocks outside the pages
   // Gauss-Legendre nodes (all 2l, ascending), weights, and the angle of each

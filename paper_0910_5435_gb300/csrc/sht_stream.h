@@ -125,6 +125,7 @@ constexpr int kMaxM = 32;             // outputs per compute op (one warp)
 constexpr int kMaxPred = 16;          // predecessors listed by a data op (more: fan-in JOIN)
 constexpr int kDoneWindow = 4096;     // completion-tag ring; an item holds < kMaxItemOps ops
 constexpr int kMaxItemOps = 3584;
+constexpr int kValueSlotVals = 1024;  // F_VALUES_APART: values of one op (one warp staging slot)
 constexpr int kConsumerWarps = 8;
 constexpr int kCtlPieces = 8;         // control ops are split into up to this many warp tasks
 

@@ -70,6 +70,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (bulk copy) writes to it
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -346,6 +351,10 @@ __device__ __forceinline__ T ldv(const T* p) {
 }
 
 // Accumulates lane o's dot product over the inner indices s = q, q + ks, ...
+// Values come from shared memory (pages) or straight from global memory; the
+// global variant keeps 8 rows of loads in flight per lane (the latency of a
+// streamed HBM read is hidden by the loads of the same warp, not only by
+// other warps).
 template <class TR, bool GLOBAL>
 __device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, const typename TR::C* in,
                                                      const uint16_t* idx, bool gather, int M, int K, int o, int q,
@@ -353,44 +362,42 @@ __device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, 
   using C = typename TR::C;
   using V = typename TR::V;
   using Acc = typename TR::Acc;
-  // four independent accumulators; loads are issued ahead of the FMAs
-  Acc a0 = TR::zero(), a1 = TR::zero(), a2 = TR::zero(), a3 = TR::zero();
+  constexpr int U = GLOBAL ? 8 : 4;
+  Acc a[4] = {TR::zero(), TR::zero(), TR::zero(), TR::zero()};
   int s = q;
-  for (; s + 3 * ks < K; s += 4 * ks) {
-    const int s1 = s + ks, s2 = s + 2 * ks, s3 = s + 3 * ks;
-    const V v0 = ldv<GLOBAL>(val + (size_t)s * M + o);
-    const V v1 = ldv<GLOBAL>(val + (size_t)s1 * M + o);
-    const V v2 = ldv<GLOBAL>(val + (size_t)s2 * M + o);
-    const V v3 = ldv<GLOBAL>(val + (size_t)s3 * M + o);
-    const C x0 = in[gather ? (int)idx[s] : s];
-    const C x1 = in[gather ? (int)idx[s1] : s1];
-    const C x2 = in[gather ? (int)idx[s2] : s2];
-    const C x3 = in[gather ? (int)idx[s3] : s3];
-    TR::fma(a0, v0, x0);
-    TR::fma(a1, v1, x1);
-    TR::fma(a2, v2, x2);
-    TR::fma(a3, v3, x3);
+  for (; s + (U - 1) * ks < K; s += U * ks) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = ldv<GLOBAL>(val + (size_t)(s + u * ks) * M + o);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int su = s + u * ks;
+      TR::fma(a[u & 3], v[u], in[gather ? (int)idx[su] : su]);
+    }
   }
-  for (; s < K; s += ks) TR::fma(a0, ldv<GLOBAL>(val + (size_t)s * M + o), in[gather ? (int)idx[s] : s]);
-  TR::merge(a0, a1);
-  TR::merge(a2, a3);
-  TR::merge(a0, a2);
-  return a0;
+  for (; s < K; s += ks) TR::fma(a[0], ldv<GLOBAL>(val + (size_t)s * M + o), in[gather ? (int)idx[s] : s]);
+  TR::merge(a[0], a[1]);
+  TR::merge(a[2], a[3]);
+  TR::merge(a[0], a[2]);
+  return a[0];
 }
 
 // One compute op (SYN_INTERP, DENSE, DENSE_G, ANA_INTERP), executed by one warp.
 template <class TR>
 __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, const Vecs<TR>& S, const SweepArgs& A,
-                                         int lane) {
+                                         int lane, const uint8_t* staged) {
   using C = typename TR::C;
   using V = typename TR::V;
   using Acc = typename TR::Acc;
   using IO = typename TR::IO;
   const int M = h.M, K = h.K;
   const uint16_t* idx = reinterpret_cast<const uint16_t*>(op + sizeof(OpHdr)) + h.npred;
-  const bool apart = (h.flags & F_VALUES_APART) != 0;
-  const V* val = apart ? reinterpret_cast<const V*>(A.values + (size_t)h.vref * 16)
-                       : reinterpret_cast<const V*>(op + sizeof(OpHdr) + (size_t)h.idx16 * 16);
+  // values: staged in this warp's slot, else streamed from the value region,
+  // else inside the page after the index area
+  const bool from_global = staged == nullptr && (h.flags & F_VALUES_APART) != 0;
+  const V* val = staged ? reinterpret_cast<const V*>(staged)
+                        : from_global ? reinterpret_cast<const V*>(A.values + (size_t)h.vref * 16)
+                                      : reinterpret_cast<const V*>(op + sizeof(OpHdr) + (size_t)h.idx16 * 16);
   const C* in = S.buf(h.in_buf) + h.io;
   C* out = S.buf(h.out_buf) + h.oo;
   const bool gather = (h.kind == OP_SYN_INTERP);
@@ -403,8 +410,8 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
     const int o = lane >> lks, q = lane & (ks - 1);
     Acc a0 = TR::zero();
     if (o < M)
-      a0 = apart ? gemv_dot<TR, true>(val, in, idx, gather, M, K, o, q, ks)
-                 : gemv_dot<TR, false>(val, in, idx, gather, M, K, o, q, ks);
+      a0 = from_global ? gemv_dot<TR, true>(val, in, idx, gather, M, K, o, q, ks)
+                       : gemv_dot<TR, false>(val, in, idx, gather, M, K, o, q, ks);
     for (int off = ks >> 1; off > 0; off >>= 1) {
       const Acc b = TR::shfl_xor(a0, off);
       TR::merge(a0, b);
@@ -546,6 +553,7 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
     }
   };
   auto issue = [&](int s, uint64_t page) {
+    fence_proxy_async();
     mbar_arrive_expect_tx(full + s, PB);
     bulk_g2s(stages + (size_t)s * PB, A.pages + (size_t)page * PB, PB, full + s);
     ++uses[s];
@@ -654,41 +662,97 @@ __device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t*
   }
 }
 
+// An op claimed by a consumer warp.
+struct Claim {
+  int t;               // op number
+  int stage;           // ring stage of its page
+  const uint8_t* op;   // header in the page
+  OpHdr h;
+  int slot;            // staging slot of its values (0 / 1), or -1
+};
+
 template <class TR>
 __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* empty, Sched* S,
-                              const Vecs<TR>& V, int lane) {
+                              const Vecs<TR>& V, int lane, uint8_t* my_slots, uint64_t* my_bars) {
+  using Val = typename TR::V;
+  constexpr int kSlotBytes = kValueSlotVals * (int)sizeof(Val);
   const size_t PB = (size_t)A.page_bytes;
-  unsigned long long c_exec = 0, c_ready = 0, c_dep = 0, n_ops = 0;
-  for (;;) {
+  unsigned long long c_exec = 0, c_ready = 0, c_dep = 0, c_val = 0, n_ops = 0;
+  uint32_t slot_phase = 0u;  // bit s: parity of slot s's next completion
+  uint32_t inflight = 0u;    // bit s: a copy into slot s has not been waited for
+  int next_slot = 0;
+
+  // Op numbers are claimed in order; an op is "opened" once it is published:
+  // its header is read and (values kept apart) the bulk copy of its value
+  // block into a free slot starts.  A warp that holds an unexecuted op only
+  // polls for the next one (that op's page may be waiting for the held op's
+  // page to drain); it blocks on publication only when it holds nothing.
+  auto claim_number = [&]() -> int {
     int t = 0;
     if (lane == 0) t = atomicAdd(&S->n_claimed, 1);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    const long long t0 = clock64();
-    if (!warp_wait([&] {
-          const int q = vload(&S->quit);
-          return vload(&S->n_ready) > t || (q >= 0 && t >= q);
-        }, S, A.status, lane))
-      break;
+    return __shfl_sync(0xffffffffu, t, 0);
+  };
+  // 1: opened, 0: t is past the end of the stream, 2: not yet published
+  // (poll only), -1: aborted
+  auto open = [&](int t, Claim& c, bool block) -> int {
+    auto published = [&] {
+      const int q = vload(&S->quit);
+      return vload(&S->n_ready) > t || (q >= 0 && t >= q);
+    };
+    if (block) {
+      const long long t0 = clock64();
+      if (!warp_wait(published, S, A.status, lane)) return -1;
+      c_ready += clock64() - t0;
+    } else {
+      int ok = 0;
+      if (lane == 0) ok = published() ? 1 : 0;
+      if (!__shfl_sync(0xffffffffu, ok, 0)) return 2;
+      __threadfence_block();
+    }
     const int q = vload(&S->quit);
-    if (q >= 0 && t >= q) break;
+    if (q >= 0 && t >= q) return 0;
     const uint32_t e = S->dir[t % kDir];
     __syncwarp();
     if (lane == 0) atomicAdd(&S->n_dir_read, 1);
-    const int stage = (int)(e >> 16);
-    const uint8_t* op = stages + (size_t)stage * PB + ((size_t)(e & 0xffffu) << 4);
-    const OpHdr h = *reinterpret_cast<const OpHdr*>(op);
+    c.t = t;
+    c.stage = (int)(e >> 16);
+    c.op = stages + (size_t)c.stage * PB + ((size_t)(e & 0xffffu) << 4);
+    c.h = *reinterpret_cast<const OpHdr*>(c.op);
+    c.slot = -1;
+    const uint32_t vbytes = (uint32_t)((sizeof(Val) * c.h.M * c.h.K + 15) & ~size_t(15));
+    // a block larger than a slot (not emitted by the planner) is streamed instead
+    if ((c.h.flags & F_VALUES_APART) && my_slots && vbytes <= (uint32_t)kSlotBytes) {
+      c.slot = next_slot;
+      next_slot ^= 1;
+      if (lane == 0) {
+        fence_proxy_async();  // earlier reads of this slot precede the copy into it
+        mbar_arrive_expect_tx(my_bars + c.slot, vbytes);
+        bulk_g2s(my_slots + (size_t)c.slot * kSlotBytes, A.values + (size_t)c.h.vref * 16, vbytes,
+                 my_bars + c.slot);
+      }
+      inflight |= 1u << c.slot;
+    }
+    return 1;
+  };
+
+  Claim cur, nxt;
+  int rc = open(claim_number(), cur, true);
+  while (rc == 1) {
+    const int tn = claim_number();
+    int rn = open(tn, nxt, false);  // the next op's values travel while this one runs
+    if (rn < 0) break;
     const long long t1 = clock64();
     bool ok;
-    if (h.kind == OP_JOIN && (h.flags & F_ITEM_START)) {
+    if (cur.h.kind == OP_JOIN && (cur.h.flags & F_ITEM_START)) {
       // a work item starts once every earlier op of this CTA has completed
-      ok = warp_wait([&] { return vload(&S->n_done) >= t; }, S, A.status, lane);
+      ok = warp_wait([&] { return vload(&S->n_done) >= cur.t; }, S, A.status, lane);
     } else {
       // lanes watch the listed predecessors (32 at a time)
-      const uint16_t* pred = reinterpret_cast<const uint16_t*>(op + sizeof(OpHdr));
+      const uint16_t* pred = reinterpret_cast<const uint16_t*>(cur.op + sizeof(OpHdr));
       ok = true;
-      for (int base = 0; base < h.npred && ok; base += 32) {
+      for (int base = 0; base < cur.h.npred && ok; base += 32) {
         const int i = base + lane;
-        const int u = (i < h.npred) ? t - (int)pred[i] : -1;
+        const int u = (i < cur.h.npred) ? cur.t - (int)pred[i] : -1;
         const unsigned want = (unsigned)(u & 0xffff);
         const uint16_t* slot = S->done_tag + (u >= 0 ? (u % kDoneWindow) : 0);
         ok = warp_wait_all([&] { return u < 0 || vload16(slot) == want; }, S, A.status);
@@ -696,27 +760,46 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
     }
     if (!ok) break;
     const long long t2 = clock64();
-    if (h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP)
-      run_gemv<TR>(h, op, V, A, lane);
-    else if (h.kind != OP_JOIN)
-      run_control<TR>(h, V, A, lane);
+    const uint8_t* staged = nullptr;
+    if (cur.slot >= 0) {
+      uint64_t* bar = my_bars + cur.slot;
+      const uint32_t ph = (slot_phase >> cur.slot) & 1u;
+      if (!warp_wait([&] { return mbar_try_wait(bar, ph); }, S, A.status, lane)) break;
+      mbar_try_wait(bar, ph);  // each lane's own acquire of the copied bytes
+      slot_phase ^= 1u << cur.slot;
+      inflight &= ~(1u << cur.slot);
+      staged = my_slots + (size_t)cur.slot * kSlotBytes;
+    }
+    const long long t3 = clock64();
+    if (cur.h.kind >= OP_SYN_INTERP && cur.h.kind <= OP_ANA_INTERP)
+      run_gemv<TR>(cur.h, cur.op, V, A, lane, staged);
+    else if (cur.h.kind != OP_JOIN)
+      run_control<TR>(cur.h, V, A, lane);
     __threadfence_block();  // this op's results are visible before it is marked done
     __syncwarp();
     if (lane == 0) {
-      *reinterpret_cast<volatile uint16_t*>(&S->done_tag[t % kDoneWindow]) = (uint16_t)(t & 0xffff);
+      *reinterpret_cast<volatile uint16_t*>(&S->done_tag[cur.t % kDoneWindow]) = (uint16_t)(cur.t & 0xffff);
       atomicAdd(&S->n_done, 1);
-      if (atomicSub(&S->pending[stage], 1) == 1) mbar_arrive(empty + stage);
+      if (atomicSub(&S->pending[cur.stage], 1) == 1) mbar_arrive(empty + cur.stage);
     }
-    const long long t3 = clock64();
-    c_ready += t1 - t0;
+    const long long t4 = clock64();
     c_dep += t2 - t1;
-    c_exec += t3 - t2;
+    c_val += t3 - t2;
+    c_exec += t4 - t3;
     ++n_ops;
+    if (rn == 2) rn = open(tn, nxt, true);  // holds nothing now
+    if (rn != 1) break;
+    cur = nxt;
   }
+  // never leave with a bulk copy still landing in this warp's slots
+  for (int s = 0; s < 2; ++s)
+    if (((inflight >> s) & 1u) && lane == 0) wait_bounded(my_bars + s, (slot_phase >> s) & 1u, A.status, &S->abort);
+  __syncwarp();
   if (lane == 0) {
     trace_add(A, TR_EXEC, c_exec);
     trace_add(A, TR_WAIT_READY, c_ready);
     trace_add(A, TR_WAIT_DEP, c_dep);
+    trace_add(A, TR_WAIT_VALUES, c_val);
     trace_add(A, TR_OPS, n_ops);
   }
 }
@@ -730,15 +813,21 @@ __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const Swe
   uint8_t* stages = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * PB);
   uint64_t* empty = full + NST;
-  Sched* S = reinterpret_cast<Sched*>(empty + NST);
-  const size_t vec_off = ((size_t)NST * PB + 16 * (size_t)NST + sizeof(Sched) + 127) & ~size_t(127);
+  uint64_t* slot_bars = empty + NST;  // 2 per consumer warp
+  Sched* S = reinterpret_cast<Sched*>(slot_bars + 2 * NW);
+  const size_t vec_off =
+      ((size_t)NST * PB + 16 * (size_t)NST + 16 * (size_t)NW + sizeof(Sched) + 127) & ~size_t(127);
   const Vecs<TR> V{reinterpret_cast<typename TR::C*>(smem + vec_off), A.buf_ab};
+  uint8_t* slots = A.staged
+                       ? smem + ((vec_off + sizeof(typename TR::C) * (size_t)A.num_vecs * A.buf_ab + 127) & ~size_t(127))
+                       : nullptr;
 
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
+    for (int s = 0; s < 2 * NW; ++s) mbar_init(slot_bars + s, 1);
     S->n_ready = 0;
     S->n_claimed = 0;
     S->n_dir_read = 0;
@@ -758,25 +847,31 @@ __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const Swe
   } else if (warp == NW + 1) {
     if (lane == 0) parser_loop(A, stages, full, S);
   } else {
-    consumer_loop<TR>(A, stages, empty, S, V, lane);
+    consumer_loop<TR>(A, stages, empty, S, V, lane, slots ? slots + (size_t)warp * 2 * kValueSlotVals * sizeof(typename TR::V) : nullptr,
+                      slot_bars + 2 * warp);
   }
 }
 
 template <class TR>
-size_t smem_for(int page_bytes, int nstages, int buf_ab, int num_vecs) {
-  const size_t vec_off = ((size_t)nstages * page_bytes + 16 * (size_t)nstages + sizeof(Sched) + 127) & ~size_t(127);
-  return vec_off + sizeof(typename TR::C) * (size_t)num_vecs * (size_t)buf_ab;
+size_t smem_for(int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, bool staged) {
+  const size_t vec_off =
+      ((size_t)nstages * page_bytes + 16 * (size_t)nstages + 16 * (size_t)nw + sizeof(Sched) + 127) & ~size_t(127);
+  size_t end = vec_off + sizeof(typename TR::C) * (size_t)num_vecs * (size_t)buf_ab;
+  if (staged) end = ((end + 127) & ~size_t(127)) + (size_t)nw * 2 * kValueSlotVals * sizeof(typename TR::V);
+  return end;
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs) {
+size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, bool staged) {
   switch (prec) {
-    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab, num_vecs);
-    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab, num_vecs);
-    default: return smem_for<TS32>(page_bytes, nstages, buf_ab, num_vecs);
+    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab, num_vecs, nw, staged);
+    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab, num_vecs, nw, staged);
+    default: return smem_for<TS32>(page_bytes, nstages, buf_ab, num_vecs, nw, staged);
   }
 }
+
+namespace {
 
 // Host dispatch over (precision, consumer warps).
 template <class TR>
@@ -791,6 +886,8 @@ const void* kernel_for(int prec, int nw) {
     default: return kernel_ptr<TS32>(nw);
   }
 }
+
+}  // namespace
 
 cudaError_t sweep_configure(int prec, size_t smem) {
   for (int nw : {8, 16}) {

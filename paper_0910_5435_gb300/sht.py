@@ -85,6 +85,7 @@ class sht_plan_stats(ctypes.Structure):
         ("t_upload", ctypes.c_double),
         ("m_max_words", ctypes.c_longlong),
         ("smem_bytes", ctypes.c_int),
+        ("page_bytes", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -199,6 +200,11 @@ class Plan:
         except Exception:
             pass
 
+    @property
+    def page_bytes(self):
+        """Bytes per factor page in effect for this plan."""
+        return self.stats()["page_bytes"]
+
     def stats(self):
         s = sht_plan_stats()
         _check(lib().sht_plan_get_stats(self.handle, ctypes.byref(s)), "sht_plan_get_stats")
@@ -281,7 +287,7 @@ def sht_analyze(plan, prec, values, beta, workspace, stream=None):
                              _stream(stream)), "sht_analyze")
 
 
-TRACE_FIELDS = ("exec", "wait_ready", "wait_dep", "producer_wait", "parser_wait", "ops")
+TRACE_FIELDS = ("exec", "wait_ready", "wait_dep", "producer_wait", "parser_wait", "ops", "wait_values")
 
 
 def sht_trace_enable(plan, enable=True):

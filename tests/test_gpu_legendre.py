@@ -93,11 +93,11 @@ def test_fp64_kernel_matches_host_emulation(sht, l, C):
     P = plan(sht, l, C)
     beta = inputs.random_beta(l, seed=5)
     G = run_synth(sht, P, 0, beta)
-    Ge = emulate(P.stream(0, 0), 16384, l, 0, 0, beta)
+    Ge = emulate(P.stream(0, 0), P.page_bytes, l, 0, 0, beta)
     assert rel(G, Ge) < 1e-14
     Gin = inputs.random_G(l, seed=6)
     b = run_analysis(sht, P, 0, Gin)
-    be = emulate(P.stream(0, 1), 16384, l, 0, 1, Gin)
+    be = emulate(P.stream(0, 1), P.page_bytes, l, 0, 1, Gin)
     assert rel(b, be) < 1e-14
 
 

@@ -12,7 +12,6 @@ import oracle
 from paper_0910_5435_gb300 import inputs, sht
 from tests.stream_emulator import check_races, emulate, iter_ops
 
-PB = 16384
 
 
 def rel(a, b):
@@ -46,14 +45,14 @@ def test_streams_reproduce_oracle(l, C, prec, tol):
     P = sht.Plan(l, 1e-12, leaf_cols=C, host_only=True)
     beta = inputs.random_beta(l, seed=l + C)
     Go = oracle.legendre_synthesis(beta, l)
-    G = emulate(P.stream(prec, 0), PB, l, prec, 0, beta)
+    G = emulate(P.stream(prec, 0), P.page_bytes, l, prec, 0, beta)
     assert rel(G, Go) < tol
     Gin = inputs.random_G(l, seed=7)
     bo = oracle.legendre_analysis(Gin, l)
-    b = emulate(P.stream(prec, 1), PB, l, prec, 1, Gin)
+    b = emulate(P.stream(prec, 1), P.page_bytes, l, prec, 1, Gin)
     assert rel(b, bo) < tol
     _, w = P.nodes()
-    ba = emulate(P.stream(prec, 1), PB, l, prec, 1, Gin, prescale=1.0 / w[l:])
+    ba = emulate(P.stream(prec, 1), P.page_bytes, l, prec, 1, Gin, prescale=1.0 / w[l:])
     assert rel(ba, oracle.legendre_adjoint(Gin, l)) < tol
 
 
@@ -66,9 +65,9 @@ def test_butterfly_levels_are_exercised():
     assert s["n_blocks"] > 100
     assert s["factor_values"] < s["dense_values"]
     assert 0 < s["k_avg"] <= s["k_max"] <= 128
-    kinds = {int(h["kind"]) for h, _, _ in iter_ops(P.stream(0, 0), PB)}
+    kinds = {int(h["kind"]) for h, _, _ in iter_ops(P.stream(0, 0), P.page_bytes)}
     assert {1, 6, 8} <= kinds  # gather, interpolation, final blocks written to G
-    kinds = {int(h["kind"]) for h, _, _ in iter_ops(P.stream(0, 1), PB)}
+    kinds = {int(h["kind"]) for h, _, _ in iter_ops(P.stream(0, 1), P.page_bytes)}
     assert {2, 3, 7, 9} <= kinds  # scatter, fold, final blocks, anterpolation
 
 
@@ -88,7 +87,7 @@ def test_trimming_bounds_dropped_rows():
     s = P.stats()
     assert s["rows_kept"] < s["rows_total"]
     beta = inputs.random_beta(l, seed=3)
-    G = emulate(P.stream(0, 0), PB, l, 0, 0, beta)
+    G = emulate(P.stream(0, 0), P.page_bytes, l, 0, 0, beta)
     assert rel(G, oracle.legendre_synthesis(beta, l)) < 1e-7
 
 
@@ -132,7 +131,7 @@ def test_op_ordering_is_race_free(l, C, prec):
     nor read what it writes (sht_stream.h ordering rule)."""
     P = sht.Plan(l, 1e-12, leaf_cols=C, host_only=True)
     for d in (0, 1):
-        assert check_races(P.stream(prec, d), PB, l) == []
+        assert check_races(P.stream(prec, d), P.page_bytes, l) == []
 
 
 def test_race_checker_catches_a_planted_overlap():
@@ -142,6 +141,7 @@ def test_race_checker_catches_a_planted_overlap():
     from tests.stream_emulator import OPHDR
     P = sht.Plan(64, 1e-12, leaf_cols=16, host_only=True)
     pages, values = P.stream(0, 0)
+    PB = P.page_bytes
     st = (pages.copy(), values)
     for pg in range(len(st[0]) // PB):
         base = pg * PB
@@ -168,6 +168,6 @@ def test_values_inline_layout_reproduces_oracle(prec):
     pages, values = P.stream(prec, 0)
     assert values.size == 0
     beta = inputs.random_beta(l, seed=21)
-    G = emulate((pages, values), PB, l, prec, 0, beta)
+    G = emulate((pages, values), P.page_bytes, l, prec, 0, beta)
     assert rel(G, oracle.legendre_synthesis(beta, l)) < (2e-5 if prec == 1 else 1e-10)
-    assert check_races(P.stream(prec, 1), PB, l) == []
+    assert check_races(P.stream(prec, 1), P.page_bytes, l) == []
