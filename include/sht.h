@@ -282,6 +282,35 @@ sht_status sht_direct_prepare(sht_plan_t plan);
 sht_status sht_direct_synthesize(sht_plan_t plan, const void* beta, void* G, sht_stream_t stream);
 sht_status sht_direct_analyze(sht_plan_t plan, const void* G, void* beta, sht_stream_t stream);
 
+/* ------------------------------------------------------ allocation-free call */
+
+/* Static scratch slots of sht_legendre_synthesize_noalloc (32 bytes each). */
+#define SHT_NOALLOC_MAX_SLOTS 32
+
+/* The paper has no counterpart: this is a calling convention for callers
+ * that may not allocate device memory on their compute path.  Computes the
+ * same G as sht_legendre_synthesize (same kernel, same factor streams, same
+ * layouts: beta device triangle, G device [2l][2l]) but allocates nothing,
+ * builds nothing and uploads nothing.  The sweep's scratch (its work-queue
+ * counter and status word) is slot `slot` of a fixed device array of
+ * SHT_NOALLOC_MAX_SLOTS slots (one array per device) instead of memory the
+ * plan allocated.
+ *   slot:   0 <= slot < SHT_NOALLOC_MAX_SLOTS, else SHT_ERR_INVALID_ARG
+ *           (sht_last_error_detail names the limit).
+ *   status: optional caller-owned device word (NULL to skip).  It is zeroed
+ *           in stream order, then receives SHT_ERR_TIMEOUT if a bounded wait
+ *           of the launch gave up (0 otherwise).
+ * The precision must already be on the device (SHT_FP64 is uploaded by
+ * sht_plan_create; others by sht_prepare); otherwise SHT_ERR_UNSUPPORTED.
+ * The first call on a device does a one-time set-up: it looks up the
+ * array's address with the device current.  That step is not stream
+ * ordered, so make the first call before any stream capture.  Calls whose
+ * launches overlap in time (other streams, threads or plans) must use
+ * different slots: two launches on one slot race on its counter.
+ * Asynchronous on stream. */
+sht_status sht_legendre_synthesize_noalloc(sht_plan_t plan, sht_precision prec, const void* beta, void* G,
+                                           int slot, unsigned* status, sht_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

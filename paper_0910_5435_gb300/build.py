@@ -28,8 +28,8 @@ CXXFLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-func
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
 
 CPP_SOURCES = ["plan_build.cpp"]
-CU_SOURCES = ["capi.cu", "sweep.cu", "direct.cu", "phi.cu"]
-HEADERS = ["sht_stream.h", "plan_host.h", "kernels.h"]
+CU_SOURCES = ["capi.cu", "sweep.cu", "direct.cu", "phi.cu", "noalloc.cu"]
+HEADERS = ["sht_stream.h", "plan_host.h", "kernels.h", "plan_access.h"]
 
 
 def _stamp():

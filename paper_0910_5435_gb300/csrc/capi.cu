@@ -17,6 +17,7 @@
 
 #include "../../include/sht.h"
 #include "kernels.h"
+#include "plan_access.h"
 #include "plan_host.h"
 
 using sht::PlanHost;
@@ -329,6 +330,49 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
 }
 
 }  // namespace
+
+void sht::set_error_detail(const char* where, const char* what) { set_detail(where, what); }
+
+sht_status sht::prepared_sweep(sht_plan_t P, sht_precision prec, int dir, const void* in, void* out,
+                               PreparedSweep* L) {
+  if (!P || !in || !out || !L || (dir != 0 && dir != 1)) return SHT_ERR_INVALID_ARG;
+  const int q = prec_index(prec);
+  if (q < 0) return SHT_ERR_INVALID_ARG;
+  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  const size_t al = (q == sht::PREC_FP32) ? 8 : 16;
+  if (!aligned(in, al) || !aligned(out, al)) return SHT_ERR_INVALID_ARG;
+  if (!P->dev_ready[q]) {
+    set_detail("prepared_sweep", "precision not on the device yet (sht_prepare uploads it)");
+    return SHT_ERR_UNSUPPORTED;
+  }
+  const DevStream& D = P->dev[q][dir];
+  sht::SweepArgs& a = L->args;
+  a = sht::SweepArgs{};
+  a.pages = D.pages;
+  a.values = D.values;
+  a.units = D.units;
+  a.n_units = D.n_units;
+  a.page_bytes = P->H.page_bytes;
+  a.nstages = P->nstages[q];
+  a.l = P->H.l;
+  a.buf_ab = D.buf_ab;
+  a.quit_page = D.quit_page;
+  a.in = in;
+  a.out = out;
+  a.prescale = nullptr;
+  a.twiddle = nullptr;
+  a.trace = nullptr;
+  a.counter = nullptr;
+  a.status = nullptr;
+  a.num_vecs = P->num_vecs[q];
+  a.staged = P->staged[q] ? 1 : 0;
+  L->prec = q;
+  L->consumer_warps = P->consumer_warps[q];
+  L->grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
+  L->smem = P->smem[q];
+  L->device = P->device;
+  return SHT_OK;
+}
 
 extern "C" {
 

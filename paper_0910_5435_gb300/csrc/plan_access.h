@@ -1,0 +1,31 @@
+// plan_access.h -- internal: the sweep launch of a plan's precision that is
+// already on the device, for entry points outside capi.cu.
+#pragma once
+
+#include <stddef.h>
+
+#include "../../include/sht.h"
+#include "kernels.h"
+
+namespace sht {
+
+struct PreparedSweep {
+  SweepArgs args;   // counter, status and trace left null for the caller to set
+  int prec = 0;     // SweepPrec
+  int consumer_warps = 8;
+  int grid = 1;
+  size_t smem = 0;
+  int device = 0;
+};
+
+// Validates the arguments like the compute entry points and fills *out for a
+// precision whose streams are already uploaded.  Builds nothing, uploads
+// nothing and allocates nothing: a precision that is not on the device
+// yet gives SHT_ERR_UNSUPPORTED.  dir: 0 synthesis, 1 analysis.
+sht_status prepared_sweep(sht_plan_t plan, sht_precision prec, int dir, const void* in, void* out,
+                          PreparedSweep* out_launch);
+
+// Sets the text returned by sht_last_error_detail on this thread.
+void set_error_detail(const char* where, const char* what);
+
+}  // namespace sht

@@ -31,8 +31,10 @@ EXPORTS = [
     "sht_legendre_synthesize", "sht_legendre_analyze", "sht_legendre_synthesize_adjoint",
     "sht_last_device_status", "sht_direct_prepare", "sht_direct_synthesize", "sht_direct_analyze",
     "sht_workspace_bytes", "sht_phi_synthesize", "sht_phi_analyze", "sht_synthesize", "sht_analyze",
-    "sht_last_error_detail", "sht_trace_enable", "sht_trace_read",
+    "sht_last_error_detail", "sht_trace_enable", "sht_trace_read", "sht_legendre_synthesize_noalloc",
 ]
+
+NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
 
 
 class ShtError(RuntimeError):
@@ -131,6 +133,7 @@ def lib():
     L.sht_analyze.argtypes = [vp, c_int, vp, vp, vp, vp]
     L.sht_trace_enable.argtypes = [vp, c_int]
     L.sht_trace_read.argtypes = [vp, vp, c_int]
+    L.sht_legendre_synthesize_noalloc.argtypes = [vp, c_int, vp, vp, c_int, vp, vp]
     for name in EXPORTS:
         if name not in ("sht_status_string", "sht_workspace_bytes", "sht_last_error_detail"):
             getattr(L, name).restype = c_int
@@ -261,6 +264,15 @@ def sht_direct_synthesize(plan, beta, G, stream=None):
 
 def sht_direct_analyze(plan, G, beta, stream=None):
     _check(lib().sht_direct_analyze(plan.handle, _ptr(G), _ptr(beta), _stream(stream)), "sht_direct_analyze")
+
+
+def sht_legendre_synthesize_noalloc(plan, prec, beta, G, slot=0, status=None, stream=None):
+    """sht_legendre_synthesize without allocation: the sweep's scratch is a
+    static device slot (0 <= slot < NOALLOC_MAX_SLOTS); ``status`` is an
+    optional device uint32 receiving the launch status."""
+    _check(lib().sht_legendre_synthesize_noalloc(plan.handle, int(prec), _ptr(beta), _ptr(G), int(slot),
+                                                 _ptr(status) if status is not None else None,
+                                                 _stream(stream)), "sht_legendre_synthesize_noalloc")
 
 
 def sht_workspace_bytes(plan, prec):
