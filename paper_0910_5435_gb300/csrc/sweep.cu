@@ -128,6 +128,9 @@ struct TF64 {
   __device__ static Acc shfl_xor(const Acc& a, int off) {
     return {__shfl_xor_sync(0xffffffffu, a.re, off), __shfl_xor_sync(0xffffffffu, a.im, off)};
   }
+  __device__ static Acc shfl_down(const Acc& a, int off) {
+    return {__shfl_down_sync(0xffffffffu, a.re, off), __shfl_down_sync(0xffffffffu, a.im, off)};
+  }
   __device__ static C from_io(const IO& v) { return v; }
   __device__ static IO to_io(const C& c) { return c; }
   __device__ static IO io_zero() { return make_double2(0.0, 0.0); }
@@ -194,6 +197,10 @@ struct TS32 {
     return {__shfl_xor_sync(0xffffffffu, a.rh, off), __shfl_xor_sync(0xffffffffu, a.rl, off),
             __shfl_xor_sync(0xffffffffu, a.ih, off), __shfl_xor_sync(0xffffffffu, a.il, off)};
   }
+  __device__ static Acc shfl_down(const Acc& a, int off) {
+    return {__shfl_down_sync(0xffffffffu, a.rh, off), __shfl_down_sync(0xffffffffu, a.rl, off),
+            __shfl_down_sync(0xffffffffu, a.ih, off), __shfl_down_sync(0xffffffffu, a.il, off)};
+  }
   __device__ static C from_io(const IO& v) {
     const float rh = __double2float_rn(v.x);
     const float ih = __double2float_rn(v.y);
@@ -237,6 +244,9 @@ struct TF32 {
   __device__ static Acc from_c(const C& c) { return {c.x, c.y}; }
   __device__ static Acc shfl_xor(const Acc& a, int off) {
     return {__shfl_xor_sync(0xffffffffu, a.re, off), __shfl_xor_sync(0xffffffffu, a.im, off)};
+  }
+  __device__ static Acc shfl_down(const Acc& a, int off) {
+    return {__shfl_down_sync(0xffffffffu, a.re, off), __shfl_down_sync(0xffffffffu, a.im, off)};
   }
   __device__ static C from_io(const IO& v) { return v; }
   __device__ static IO to_io(const C& c) { return c; }
@@ -363,7 +373,9 @@ __device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, 
   using V = typename TR::V;
   using Acc = typename TR::Acc;
   constexpr int U = GLOBAL ? 8 : 4;
-  Acc a[4] = {TR::zero(), TR::zero(), TR::zero(), TR::zero()};
+  // two chains per lane: with two or more warps per scheduler that hides the
+  // FMA latency, and each extra chain costs a merge per op
+  Acc a[2] = {TR::zero(), TR::zero()};
   int s = q;
   for (; s + (U - 1) * ks < K; s += U * ks) {
     V v[U];
@@ -372,13 +384,11 @@ __device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int su = s + u * ks;
-      TR::fma(a[u & 3], v[u], in[gather ? (int)idx[su] : su]);
+      TR::fma(a[u & 1], v[u], in[gather ? (int)idx[su] : su]);
     }
   }
   for (; s < K; s += ks) TR::fma(a[0], ldv<GLOBAL>(val + (size_t)s * M + o), in[gather ? (int)idx[s] : s]);
   TR::merge(a[0], a[1]);
-  TR::merge(a[2], a[3]);
-  TR::merge(a[0], a[2]);
   return a[0];
 }
 
@@ -403,18 +413,19 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
   const bool gather = (h.kind == OP_SYN_INTERP);
   const bool accum = (h.flags & F_ACCUM) != 0;
   if (M > 0) {
-    // lanes per output: the largest power of two ks with ks * M <= 32
-    int lks = 0;
-    while (((2 << lks) * M) <= 32) ++lks;
-    const int ks = 1 << lks;
-    const int o = lane >> lks, q = lane & (ks - 1);
+    // ks = floor(32 / M) lanes per output (not only powers of two, so that
+    // up to 32 - ks + 1 lanes work); lane = o * ks + q
+    const int ks = 32 / M;
+    const int o = lane / ks, q = lane - o * ks;
     Acc a0 = TR::zero();
     if (o < M)
       a0 = from_global ? gemv_dot<TR, true>(val, in, idx, gather, M, K, o, q, ks)
                        : gemv_dot<TR, false>(val, in, idx, gather, M, K, o, q, ks);
-    for (int off = ks >> 1; off > 0; off >>= 1) {
-      const Acc b = TR::shfl_xor(a0, off);
-      TR::merge(a0, b);
+    // segmented tree: after the step with offset d, lane q holds the sum over
+    // q .. min(q + 2d - 1, ks - 1) of its segment
+    for (int off = 1; off < ks; off <<= 1) {
+      const Acc b = TR::shfl_down(a0, off);
+      if (q + off < ks) TR::merge(a0, b);
     }
     if (q == 0 && o < M) {
       switch (h.kind) {
