@@ -260,13 +260,17 @@ sht_status sht_analyze(sht_plan_t plan, sht_precision prec, const void* values, 
 /* Enables (allocating a small device buffer) or disables per-launch cycle
  * counters in the sweep kernels.  While enabled, every launch adds, summed
  * over its CTAs, the clock64 cycles that consumer warps spent executing ops,
- * waiting for an op to be published, waiting for its dependencies, that the
- * producer spent waiting for a free page and the parser for a landed page,
- * plus the number of ops executed.  Synchronous. */
+ * waiting for an op to be published, waiting for its dependencies, waiting
+ * for its staged values, that the producer spent waiting for a free page and
+ * the parser for a landed page, plus the number of ops executed, and the
+ * execution cycles split into compute ops, control ops and completion
+ * marking, with the compute and control op counts.  Synchronous. */
 sht_status sht_trace_enable(sht_plan_t plan, int enable);
 
-/* Copies the 8 counters (exec, wait_ready, wait_dep, producer_wait,
- * parser_wait, ops, 0, 0) to host memory out[8]; reset != 0 zeroes them.
+/* Copies the 16 counters (exec, wait_ready, wait_dep, producer_wait,
+ * parser_wait, ops, wait_values, exec_gemv, exec_control, complete,
+ * n_gemv, n_control, 0, 0, 0, 0) to host memory out[16]; reset != 0 zeroes
+ * them.
  * Synchronizes the device.  SHT_ERR_UNSUPPORTED if tracing is disabled. */
 sht_status sht_trace_read(sht_plan_t plan, unsigned long long* out, int reset);
 

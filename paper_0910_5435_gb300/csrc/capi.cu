@@ -211,6 +211,9 @@ sht_status build_host(sht_plan_t P, int q) {
     H.t_comp += now_s() - t0;
   } catch (const std::bad_alloc&) {
     return SHT_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_detail("plan build", e.what());
+    return SHT_ERR_INVALID_ARG;
   } catch (...) {
     return SHT_ERR_INVALID_ARG;
   }

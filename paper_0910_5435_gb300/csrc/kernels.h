@@ -32,10 +32,17 @@ struct SweepArgs {
 };
 
 // Trace slots (clock64 cycles summed over CTAs): consumer warps executing ops,
-// waiting for an op to be published, waiting for its dependencies; producer
-// waiting for a free page; parser waiting for a landed page; ops executed.
+// waiting for an op to be published, waiting for its dependencies, waiting
+// for staged values; producer waiting for a free page; parser waiting for a
+// landed page; ops executed; execution split by op class.
 enum TraceSlot {
-  TR_EXEC = 0, TR_WAIT_READY, TR_WAIT_DEP, TR_PROD_WAIT, TR_PARSE_WAIT, TR_OPS, TR_WAIT_VALUES, kTraceSlots = 8
+  TR_EXEC = 0, TR_WAIT_READY, TR_WAIT_DEP, TR_PROD_WAIT, TR_PARSE_WAIT, TR_OPS, TR_WAIT_VALUES,
+  TR_EXEC_GEMV,    // cycles in compute ops (part of TR_EXEC)
+  TR_EXEC_CTL,     // cycles in control ops (part of TR_EXEC)
+  TR_COMPLETE,     // cycles marking ops done (part of TR_EXEC)
+  TR_N_GEMV,       // compute ops executed
+  TR_N_CTL,        // control ops executed
+  kTraceSlots = 16
 };
 
 enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2 };

@@ -547,27 +547,57 @@ namespace {
 
 inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
 
+// Fills pages with ops from the front and the op table from the back.
 struct PageWriter {
   std::vector<uint8_t>& buf;
   size_t PB;
   size_t page_start = 0, pos = 0;
+  int n_ops = 0;
   bool open = false;
   PageWriter(std::vector<uint8_t>& b, size_t pb) : buf(b), PB(pb) {}
   void new_page() {
     page_start = buf.size();
     buf.resize(buf.size() + PB, 0);
     pos = 0;
+    n_ops = 0;
     open = true;
   }
-  size_t space() const { return open ? PB - pos : 0; }
+  // bytes an empty page offers one op
+  size_t fresh_space() const { return (PB - page_table_bytes(1)) & ~size_t(15); }
+  // bytes left for one more op (its table entry reserved)
+  size_t space() const {
+    if (!open) return 0;
+    const size_t used = pos + page_table_bytes(n_ops + 1);
+    return used >= PB ? 0 : ((PB - used) & ~size_t(15));
+  }
   uint8_t* alloc(size_t bytes) {
-    if (bytes > PB) throw std::logic_error("op larger than a page");
+    if (bytes + page_table_bytes(1) > PB) throw std::logic_error("op larger than a page");
     if (bytes > space()) new_page();
-    uint8_t* p = buf.data() + page_start + pos;
+    uint8_t* page = buf.data() + page_start;
+    uint8_t* p = page + pos;
+    const uint16_t off16 = (uint16_t)(pos >> 4);
+    std::memcpy(page + PB - 4 - 2 * (size_t)n_ops, &off16, 2);
+    ++n_ops;
+    const uint16_t n = (uint16_t)n_ops;
+    std::memcpy(page + PB - 2, &n, 2);
     pos += bytes;
     return p;
   }
 };
+
+// Offsets (bytes) of the ops of one page, from its op table.
+std::vector<size_t> page_ops(const uint8_t* page, size_t PB) {
+  uint16_t n = 0;
+  std::memcpy(&n, page + PB - 2, 2);
+  std::vector<size_t> offs;
+  if (n == kQuitPage) return offs;
+  for (int i = 0; i < n; ++i) {
+    uint16_t o = 0;
+    std::memcpy(&o, page + PB - 4 - 2 * (size_t)i, 2);
+    offs.push_back((size_t)o << 4);
+  }
+  return offs;
+}
 
 // value encodings per precision: 0 = FP64 (double), 1 = FP32 (float), 2 = SPLIT32 (float hi, float lo)
 inline size_t value_size(int prec) { return prec == 1 ? 4 : 8; }
@@ -614,7 +644,9 @@ struct Emitter {
   size_t vs;
   Tracker* T = nullptr;
   std::vector<uint8_t>* values = nullptr;  // value region of the item, or nullptr: values inline
-  int next_op = 0;  // number of the next op within the item
+  int next_op = 0;    // number of the next op within the item
+  int seg_start = 0;  // first op of the current segment (after its JOIN)
+  int positions = 0;
   int l = 0;
   Emitter(PageWriter& w, int p) : W(w), prec(p), vs(value_size(p)) {}
 
@@ -630,10 +662,10 @@ struct Emitter {
   // Page bytes of an op with nidx index entries and nval values, leaving room
   // for the largest predecessor list (the actual list may be shorter).  With
   // values kept apart the page holds only the header and indices, and the
-  // value block must fit one warp's staging slot (kValueSlotVals values).
+  // value block must fit one warp's staging slot (value_slot_vals values).
   size_t bytes_of(size_t nidx, size_t nval) const {
     const size_t meta = sizeof(OpHdr) + pad16(2 * (nidx + kMaxPred));
-    if (values) return nval <= (size_t)kValueSlotVals ? meta : ~size_t(0) / 2;
+    if (values) return nval <= (size_t)value_slot_vals(prec) ? meta : ~size_t(0) / 2;
     return meta + pad16(vs * nval);
   }
 
@@ -758,15 +790,26 @@ struct Emitter {
   }
 
   // Opens a work item: a JOIN that waits for every earlier op of the CTA.
-  void open_item(int positions) {
-    T->reset(positions);
+  void open_item(int npos) {
+    positions = npos;
     next_op = 0;
+    open_segment();
+  }
+
+  // A JOIN that waits for every earlier op of the CTA.  It starts each item,
+  // and again a segment of an item whose ops would not fit the completion-
+  // tag window: predecessors never reach back past it.
+  void open_segment() {
+    T->reset(positions);
     OpHdr h = hdr(OP_JOIN, F_ITEM_START);
     T->join = next_op;
+    seg_start = next_op;
     raw(h, {}, {}, {});
   }
 
   void write(OpHdr h, const std::vector<uint16_t>& idx, const std::vector<double>& vals) {
+    // room for a fan-in JOIN and the op itself in this segment
+    if (next_op + 2 - seg_start >= kMaxItemOps) open_segment();
     std::vector<long long> R, Wr;
     access(h, idx, R, Wr);
     std::vector<int> preds = preds_of(R, Wr);
@@ -827,10 +870,12 @@ struct Emitter {
         if (bytes_for(cands[c]) <= space) return cands[c];
       return 0;
     };
+    // a fresh page only when this page's space, not the op format (the
+    // value slot), keeps the piece below 8 outputs
     int mp = best_in(W.space());
-    if (mp < std::min(remaining, 8)) {
+    if (mp < std::min(best_in(W.fresh_space()), 8)) {
       W.new_page();
-      mp = best_in(W.PB);
+      mp = best_in(W.space());
     }
     if (mp <= 0) throw std::logic_error("op does not fit in a page");
     return mp;
@@ -1220,7 +1265,6 @@ void emit_streams(PlanHost& P, int prec) {
         cur_pages = 0;
         cur_ops = 0;
       }
-      if (nops[m] >= kMaxItemOps) throw std::runtime_error("an order needs more ops than one work item holds");
       cur.push_back(m);
       cur_pages += pg;
       cur_ops += nops[m];
@@ -1257,11 +1301,9 @@ void emit_streams(PlanHost& P, int prec) {
       if (base16 && !item_vals[it].empty()) {
         for (size_t pg = 0; pg < item_bytes[it].size() / PB; ++pg) {
           uint8_t* page = item_bytes[it].data() + pg * PB;
-          for (size_t off = 0; off + sizeof(OpHdr) <= PB;) {
+          for (size_t off : page_ops(page, PB)) {
             OpHdr* h = reinterpret_cast<OpHdr*>(page + off);
-            if (h->bytes == 0) break;
             if (h->flags & F_VALUES_APART) h->vref += base16;
-            off += h->bytes;
           }
         }
       }
@@ -1271,13 +1313,15 @@ void emit_streams(PlanHost& P, int prec) {
       S.values.insert(S.values.end(), item_vals[it].begin(), item_vals[it].end());
       pages += e.n_pages;
     }
-    // trailing QUIT page: a single op of kind 0xFF ends the consumer loop
+    // trailing QUIT page: op count kQuitPage (and a single op of kind 0xFF)
+    // ends the consumer loop
     std::vector<uint8_t> quit((size_t)P.page_bytes, 0);
     OpHdr q;
     std::memset(&q, 0, sizeof(q));
     q.bytes = sizeof(OpHdr);
     q.kind = OP_QUIT;
     std::memcpy(quit.data(), &q, sizeof(q));
+    std::memcpy(quit.data() + PB - 2, &kQuitPage, 2);
     S.bytes.insert(S.bytes.end(), quit.begin(), quit.end());
     int mx = 0;
     for (int u = 0; u < L * 2; ++u) {

@@ -16,7 +16,11 @@
 //
 //   [OpHdr 32 B][uint16 index lists, padded to 16 B][values, padded to 16 B]
 //
-// and ends at the first header with bytes == 0 (or at the page end).
+// from offset 0 up, and ends with an OP TABLE that grows down from the page
+// end: the uint16 at byte page_bytes - 2 is the op count n (kQuitPage marks
+// the final page), and the uint16 at byte page_bytes - 4 - 2 i is the offset
+// of op i in 16-byte units.  The table lets a whole warp publish a page's
+// ops at once.  Between the last op and the table the page is zero.
 //
 // Every op is executed by ONE warp.  Compute ops apply a small dense matrix V
 // ([K][M] layout, M fastest: lanes that own consecutive outputs read
@@ -123,10 +127,17 @@ constexpr int kNumVecs = 4;
 
 constexpr int kMaxM = 32;             // outputs per compute op (one warp)
 constexpr int kMaxPred = 16;          // predecessors listed by a data op (more: fan-in JOIN)
-constexpr int kDoneWindow = 4096;     // completion-tag ring; an item holds < kMaxItemOps ops
+constexpr int kDoneWindow = 4096;     // completion-tag ring; a segment (ops after an item-start JOIN) holds < kMaxItemOps ops
 constexpr int kMaxItemOps = 3584;
-constexpr int kValueSlotVals = 1024;  // F_VALUES_APART: values of one op (one warp staging slot)
+// F_VALUES_APART: values of one op, which fill one warp's staging slot
+// (prec: 0 float64, 1 float32, 2 split float32).  Smaller slots would let
+// more warps fit, but split the blocks into more ops with more fan-in joins.
+constexpr int value_slot_vals(int prec) { return prec >= 0 ? 1024 : 0; }
 constexpr int kConsumerWarps = 8;
 constexpr int kCtlPieces = 8;         // control ops are split into up to this many warp tasks
+constexpr uint16_t kQuitPage = 0xFFFF;  // op count of the stream's final page
+
+// Op table of a page (see the format above).
+inline size_t page_table_bytes(int n_ops) { return 2 * (size_t)(n_ops + 1); }
 
 }  // namespace sht

@@ -103,6 +103,7 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, uns
 
 // float64 factors and arithmetic; complex128 I/O.
 struct TF64 {
+  static constexpr int kSlotVals = value_slot_vals(0);
   using V = double;
   using C = double2;
   using IO = double2;
@@ -148,6 +149,7 @@ struct TF64 {
 // dropped); sums use Knuth's TwoSum.  The _rn intrinsics keep the compiler
 // from contracting the error-free transformations.
 struct TS32 {
+  static constexpr int kSlotVals = value_slot_vals(2);
   using V = float2;  // {hi, lo}
   using C = float4;  // {re_hi, re_lo, im_hi, im_lo}
   using IO = double2;
@@ -220,6 +222,7 @@ struct TS32 {
 
 // float32 factors and arithmetic; complex64 I/O.
 struct TF32 {
+  static constexpr int kSlotVals = value_slot_vals(1);
   using V = float;
   using C = float2;
   using IO = float2;
@@ -268,7 +271,6 @@ struct TF32 {
 struct Sched {
   int n_ready;    // ops published by the parser (op numbers 0 .. n_ready-1)
   int n_claimed;  // next op number to hand to a consumer warp
-  int n_dir_read; // directory entries consumed by claimers
   int n_done;     // ops completed (any order)
   int n_issued;   // pages issued by the producer
   int quit;       // number of the QUIT op once parsed, else -1
@@ -606,69 +608,76 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
   trace_add(A, TR_PROD_WAIT, c_wait);
 }
 
-__device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* full, Sched* S) {
+// One warp publishes the ops of each landed page, in issue order, from the
+// page's op table: lanes write up to 32 directory entries at once.
+__device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* full, uint64_t* empty,
+                            Sched* S, int lane) {
   const size_t PB = (size_t)A.page_bytes;
-  int parsed[kMaxStages];  // pages parsed from each stage so far
-  for (int s = 0; s < kMaxStages; ++s) parsed[s] = 0;
+  uint32_t parsed_bits = 0;  // bit s: parity of the next completion of stage s
   int ticket = 0;
   unsigned long long c_wait = 0;
   for (int k = 0;; ++k) {
     const long long w0 = clock64();
     // the k-th issued page: which stage, then wait for its bytes
-    while (vload(&S->n_issued) <= k) {
-      if (vload(&S->abort)) return;
-      if (clock64() - w0 > kTimeoutCycles) {
-        atomicCAS(A.status, 0u, kStatusTimeout);
-        vstore(&S->abort, 1);
-        return;
-      }
-      __nanosleep(32);
-    }
-    __threadfence_block();
-    const int stage = vload(&S->order[k % kOrd]);
-    if (!wait_bounded(full + stage, (uint32_t)(parsed[stage] & 1), A.status, &S->abort)) return;
-    ++parsed[stage];
-    c_wait += clock64() - w0;
-    const uint8_t* page = stages + (size_t)stage * PB;
-    int count = 0;
-    bool quit = false;
-    for (size_t off = 0; off + sizeof(OpHdr) <= PB;) {
-      const OpHdr* h = reinterpret_cast<const OpHdr*>(page + off);
-      if (h->bytes == 0) break;
-      if (h->kind == OP_QUIT) {
-        quit = true;
-        break;
-      }
-      ++count;
-      off += h->bytes;
-    }
-    vstore(&S->pending[stage], count);
-    size_t off = 0;
-    for (int i = 0; i < count; ++i) {
-      // keep the directory ring from overwriting entries not yet read
-      if (ticket - vload(&S->n_dir_read) >= kDir - kConsumerWarps16) {
-        const long long t0 = clock64();
-        while (ticket - vload(&S->n_dir_read) >= kDir - kConsumerWarps16) {
-          if (vload(&S->abort)) return;
-          if (clock64() - t0 > kTimeoutCycles) {
+    int stage = 0, ok = 1;
+    if (lane == 0) {
+      while (vload(&S->n_issued) <= k) {
+        if (vload(&S->abort) || clock64() - w0 > kTimeoutCycles) {
+          if (!vload(&S->abort)) {
             atomicCAS(A.status, 0u, kStatusTimeout);
             vstore(&S->abort, 1);
-            return;
           }
-          __nanosleep(64);
+          ok = 0;
+          break;
         }
+        __nanosleep(32);
       }
-      S->dir[ticket % kDir] = ((uint32_t)stage << 16) | (uint32_t)(off >> 4);
-      ++ticket;
-      __threadfence_block();
-      vstore(&S->n_ready, ticket);
-      off += reinterpret_cast<const OpHdr*>(page + off)->bytes;
+      if (ok) {
+        __threadfence_block();
+        stage = vload(&S->order[k % kOrd]);
+        ok = wait_bounded(full + stage, (parsed_bits >> stage) & 1u, A.status, &S->abort) ? 1 : 0;
+      }
     }
-    if (quit) {
-      __threadfence_block();
-      vstore(&S->quit, ticket);
-      trace_add(A, TR_PARSE_WAIT, c_wait);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) return;
+    stage = __shfl_sync(0xffffffffu, stage, 0);
+    mbar_try_wait(full + stage, (parsed_bits >> stage) & 1u);  // each lane's acquire of the page bytes
+    parsed_bits ^= 1u << stage;
+    c_wait += clock64() - w0;
+    const uint8_t* page = stages + (size_t)stage * PB;
+    const int n = *reinterpret_cast<const uint16_t*>(page + PB - 2);
+    if (n == kQuitPage) {
+      if (lane == 0) {
+        __threadfence_block();
+        vstore(&S->quit, ticket);
+        trace_add(A, TR_PARSE_WAIT, c_wait);
+      }
       return;
+    }
+    if (lane == 0) {
+      vstore(&S->pending[stage], n);
+      if (n == 0) mbar_arrive(empty + stage);  // nothing to execute: the stage is free again
+    }
+    __syncwarp();
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      const int cnt = min(32, n - i0);
+      // entry u reuses the slot of op u - kDir: that op must have completed
+      // (so its entry was read); its completion tag says so
+      const int u = ticket + lane;
+      const int prev = (lane < cnt) ? u - kDir : -1;
+      const uint16_t* tag = S->done_tag + (prev >= 0 ? prev % kDoneWindow : 0);
+      const unsigned want = (unsigned)(prev & 0xffff);
+      if (!warp_wait_all([&] { return prev < 0 || vload16(tag) == want; }, S, A.status)) return;
+      if (lane < cnt) {
+        const uint32_t off16 = *reinterpret_cast<const uint16_t*>(page + PB - 4 - 2 * (size_t)(i0 + lane));
+        S->dir[(ticket + lane) % kDir] = ((uint32_t)stage << 16) | off16;
+      }
+      __syncwarp();
+      ticket += cnt;
+      if (lane == 0) {
+        __threadfence_block();
+        vstore(&S->n_ready, ticket);
+      }
     }
   }
 }
@@ -686,9 +695,10 @@ template <class TR>
 __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* empty, Sched* S,
                               const Vecs<TR>& V, int lane, uint8_t* my_slots, uint64_t* my_bars) {
   using Val = typename TR::V;
-  constexpr int kSlotBytes = kValueSlotVals * (int)sizeof(Val);
+  constexpr int kSlotBytes = TR::kSlotVals * (int)sizeof(Val);
   const size_t PB = (size_t)A.page_bytes;
   unsigned long long c_exec = 0, c_ready = 0, c_dep = 0, c_val = 0, n_ops = 0;
+  unsigned long long c_gemv = 0, c_ctl = 0, c_done = 0, n_gemv = 0, n_ctl = 0;
   uint32_t slot_phase = 0u;  // bit s: parity of slot s's next completion
   uint32_t inflight = 0u;    // bit s: a copy into slot s has not been waited for
   int next_slot = 0;
@@ -724,7 +734,6 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
     if (q >= 0 && t >= q) return 0;
     const uint32_t e = S->dir[t % kDir];
     __syncwarp();
-    if (lane == 0) atomicAdd(&S->n_dir_read, 1);
     c.t = t;
     c.stage = (int)(e >> 16);
     c.op = stages + (size_t)c.stage * PB + ((size_t)(e & 0xffffu) << 4);
@@ -782,10 +791,19 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
       staged = my_slots + (size_t)cur.slot * kSlotBytes;
     }
     const long long t3 = clock64();
-    if (cur.h.kind >= OP_SYN_INTERP && cur.h.kind <= OP_ANA_INTERP)
+    const bool is_gemv = cur.h.kind >= OP_SYN_INTERP && cur.h.kind <= OP_ANA_INTERP;
+    if (is_gemv)
       run_gemv<TR>(cur.h, cur.op, V, A, lane, staged);
     else if (cur.h.kind != OP_JOIN)
       run_control<TR>(cur.h, V, A, lane);
+    const long long t3b = clock64();
+    if (is_gemv) {
+      c_gemv += t3b - t3;
+      ++n_gemv;
+    } else {
+      c_ctl += t3b - t3;
+      ++n_ctl;
+    }
     __threadfence_block();  // this op's results are visible before it is marked done
     __syncwarp();
     if (lane == 0) {
@@ -794,6 +812,7 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
       if (atomicSub(&S->pending[cur.stage], 1) == 1) mbar_arrive(empty + cur.stage);
     }
     const long long t4 = clock64();
+    c_done += t4 - t3b;
     c_dep += t2 - t1;
     c_val += t3 - t2;
     c_exec += t4 - t3;
@@ -812,6 +831,11 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
     trace_add(A, TR_WAIT_DEP, c_dep);
     trace_add(A, TR_WAIT_VALUES, c_val);
     trace_add(A, TR_OPS, n_ops);
+    trace_add(A, TR_EXEC_GEMV, c_gemv);
+    trace_add(A, TR_EXEC_CTL, c_ctl);
+    trace_add(A, TR_COMPLETE, c_done);
+    trace_add(A, TR_N_GEMV, n_gemv);
+    trace_add(A, TR_N_CTL, n_ctl);
   }
 }
 
@@ -841,7 +865,6 @@ __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const Swe
     for (int s = 0; s < 2 * NW; ++s) mbar_init(slot_bars + s, 1);
     S->n_ready = 0;
     S->n_claimed = 0;
-    S->n_dir_read = 0;
     S->n_done = 0;
     S->n_issued = 0;
     S->quit = -1;
@@ -856,9 +879,9 @@ __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const Swe
   if (warp == NW) {
     if (lane == 0) producer_loop(A, stages, full, empty, S);
   } else if (warp == NW + 1) {
-    if (lane == 0) parser_loop(A, stages, full, S);
+    parser_loop(A, stages, full, empty, S, lane);
   } else {
-    consumer_loop<TR>(A, stages, empty, S, V, lane, slots ? slots + (size_t)warp * 2 * kValueSlotVals * sizeof(typename TR::V) : nullptr,
+    consumer_loop<TR>(A, stages, empty, S, V, lane, slots ? slots + (size_t)warp * 2 * TR::kSlotVals * sizeof(typename TR::V) : nullptr,
                       slot_bars + 2 * warp);
   }
 }
@@ -868,7 +891,7 @@ size_t smem_for(int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, b
   const size_t vec_off =
       ((size_t)nstages * page_bytes + 16 * (size_t)nstages + 16 * (size_t)nw + sizeof(Sched) + 127) & ~size_t(127);
   size_t end = vec_off + sizeof(typename TR::C) * (size_t)num_vecs * (size_t)buf_ab;
-  if (staged) end = ((end + 127) & ~size_t(127)) + (size_t)nw * 2 * kValueSlotVals * sizeof(typename TR::V);
+  if (staged) end = ((end + 127) & ~size_t(127)) + (size_t)nw * 2 * TR::kSlotVals * sizeof(typename TR::V);
   return end;
 }
 

@@ -299,7 +299,8 @@ def sht_analyze(plan, prec, values, beta, workspace, stream=None):
                              _stream(stream)), "sht_analyze")
 
 
-TRACE_FIELDS = ("exec", "wait_ready", "wait_dep", "producer_wait", "parser_wait", "ops", "wait_values")
+TRACE_FIELDS = ("exec", "wait_ready", "wait_dep", "producer_wait", "parser_wait", "ops", "wait_values",
+                "exec_gemv", "exec_control", "complete", "n_gemv", "n_control")
 
 
 def sht_trace_enable(plan, enable=True):
@@ -307,6 +308,6 @@ def sht_trace_enable(plan, enable=True):
 
 
 def sht_trace_read(plan, reset=True):
-    out = np.zeros(8, dtype=np.uint64)
+    out = np.zeros(16, dtype=np.uint64)
     _check(lib().sht_trace_read(plan.handle, out.ctypes.data, 1 if reset else 0), "sht_trace_read")
     return {name: int(out[i]) for i, name in enumerate(TRACE_FIELDS)}

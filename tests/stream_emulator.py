@@ -26,6 +26,20 @@ OP_QUIT = 0xFF
 F_ACCUM, F_SKEL, F_ITEM_START, F_VALUES_APART = 2, 4, 8, 16
 
 
+QUIT_PAGE = 0xFFFF
+
+
+def page_op_offsets(page, page_bytes):
+    """Byte offsets of a page's ops from its op table (None for the final
+    page): the uint16 at page_bytes - 2 is the count, the uint16 at
+    page_bytes - 4 - 2 i the offset of op i in 16-byte units."""
+    n = int(page[page_bytes - 2:page_bytes].view("<u2")[0])
+    if n == QUIT_PAGE:
+        return None
+    tab = page[page_bytes - 2 - 2 * n:page_bytes - 2].view("<u2")[::-1]
+    return [16 * int(o) for o in tab]
+
+
 def iter_ops(stream, page_bytes, with_preds=False):
     """Yields (header, index array, value bytes) for every op, in order.
     ``stream`` is the (pages, values) pair of Plan.stream (or the page region
@@ -38,13 +52,16 @@ def iter_ops(stream, page_bytes, with_preds=False):
     npages = len(pages) // page_bytes
     for pg in range(npages):
         page = pages[pg * page_bytes:(pg + 1) * page_bytes]
-        off = 0
-        while off + 32 <= page_bytes:
+        offs = page_op_offsets(page, page_bytes)
+        if offs is None:
+            return
+        end = 0
+        for off in offs:
+            assert off == end, "op table does not chain the ops contiguously"
             h = page[off:off + 32].view(OPHDR)[0]
-            if h["bytes"] == 0:
-                break
-            if h["kind"] == OP_QUIT:
-                return
+            assert h["bytes"] > 0 and h["kind"] != OP_QUIT
+            end = off + int(h["bytes"])
+            assert end <= page_bytes - 2 - 2 * len(offs), "op runs into the op table"
             ib = 16 * int(h["idx16"])
             idx = page[off + 32:off + 32 + ib].view("<u2")
             if not with_preds:
@@ -54,7 +71,6 @@ def iter_ops(stream, page_bytes, with_preds=False):
             else:
                 vals = page[off + 32 + ib:off + int(h["bytes"])]
             yield h, idx, vals
-            off += int(h["bytes"])
 
 
 def decode_values(vals, prec, n):

@@ -138,24 +138,20 @@ def test_race_checker_catches_a_planted_overlap():
     """The checker itself: dropping the predecessors of the first interpolation
     op of a real stream (it would no longer wait for the gather that writes its
     input) must be reported."""
-    from tests.stream_emulator import OPHDR
+    from tests.stream_emulator import OPHDR, page_op_offsets
     P = sht.Plan(64, 1e-12, leaf_cols=16, host_only=True)
     pages, values = P.stream(0, 0)
     PB = P.page_bytes
     st = (pages.copy(), values)
     for pg in range(len(st[0]) // PB):
         base = pg * PB
-        off = 0
-        while off + 32 <= PB:
+        for off in page_op_offsets(st[0][base:base + PB], PB) or []:
             h = st[0][base + off:base + off + 32].view(OPHDR)
-            if h[0]["bytes"] == 0:
-                break
             if h[0]["kind"] == 6:
                 assert check_races(st, PB, 64) == []
                 h[0]["npred"] = 0  # no predecessors: may overlap the gathers
                 assert check_races(st, PB, 64) != []
                 return
-            off += int(h[0]["bytes"])
     raise AssertionError("no interpolation op found")
 
 
