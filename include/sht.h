@@ -286,6 +286,58 @@ sht_status sht_direct_prepare(sht_plan_t plan);
 sht_status sht_direct_synthesize(sht_plan_t plan, const void* beta, void* G, sht_stream_t stream);
 sht_status sht_direct_analyze(sht_plan_t plan, const void* G, void* beta, sht_stream_t stream);
 
+/* ------------------------------------------------------------ many fields */
+
+/* The paper transforms one function at a time.  A batch runs the Legendre
+ * stage of many fields, each with its own plan (so its own bandlimit l), in
+ * one persistent launch: the work items of all fields' factor streams form
+ * one queue in decreasing size, so small and large fields share the GPU. */
+typedef struct sht_batch_s* sht_batch_t;
+
+#define SHT_BATCH_MAX_FIELDS 65535
+
+/* Builds a batch of nfields fields; field f uses plans[f] (a plan may appear
+ * any number of times).  Every plan must be a device plan on the same GPU
+ * with the same page_bytes; precision prec is built and uploaded for each
+ * plan if it is not yet (as sht_prepare).  Allocates the batch's item table
+ * and field table on the device.  The plans must outlive the batch. */
+sht_status sht_batch_create(int nfields, const sht_plan_t* plans, sht_precision prec, sht_batch_t* out);
+
+/* Frees the batch (NULL-safe); its plans are untouched. */
+sht_status sht_batch_destroy(sht_batch_t batch);
+
+/* Legendre synthesis of every field: for each f, the same result as
+ * sht_legendre_synthesize(plans[f], prec, beta[f], G[f]).  beta and G are
+ * DEVICE arrays of nfields device pointers (caller-owned, read by the
+ * kernel; each entry 16-byte aligned, 8-byte for SHT_FP32).  The host checks
+ * the arrays themselves; a NULL or misaligned entry is caught on the device
+ * before any of that field's work starts and reported by
+ * sht_batch_last_device_status as SHT_ERR_INVALID_ARG.  One launch,
+ * asynchronous on stream; allocates and copies nothing, so it can be
+ * captured in a CUDA graph.  Calls on one batch must not overlap in time
+ * (they share its work-queue counter). */
+sht_status sht_batch_synthesize(sht_batch_t batch, const void* const* beta, void* const* G, sht_stream_t stream);
+
+/* Legendre analysis of every field (as sht_legendre_analyze per field);
+ * G and beta as in sht_batch_synthesize. */
+sht_status sht_batch_analyze(sht_batch_t batch, const void* const* G, void* const* beta, sht_stream_t stream);
+
+/* Device status word of the batch's launches (synchronizes stream): SHT_OK,
+ * SHT_ERR_TIMEOUT (a bounded wait gave up) or SHT_ERR_INVALID_ARG (a field's
+ * pointer entry was NULL or misaligned).  A non-OK status is cleared. */
+sht_status sht_batch_last_device_status(sht_batch_t batch, sht_stream_t stream);
+
+/* Times each launch shape (8 or 16 consumer warps, page ring depth 2..8,
+ * whatever fits in shared memory) over reps launches of the given direction
+ * (0 synthesis, 1 analysis) with these pointer arrays, and keeps the fastest
+ * for that direction.  Runs the transform (writes the outputs); synchronous. */
+sht_status sht_batch_autotune(sht_batch_t batch, int direction, const void* const* in, void* const* out, int reps,
+                              sht_stream_t stream);
+
+/* Launch shape in use for a direction (any output pointer may be NULL). */
+sht_status sht_batch_get_config(sht_batch_t batch, int direction, int* consumer_warps, int* nstages,
+                                int* ctas_per_sm, int* smem_bytes);
+
 /* ------------------------------------------------------ allocation-free call */
 
 /* Static scratch slots of sht_legendre_synthesize_noalloc (32 bytes each). */

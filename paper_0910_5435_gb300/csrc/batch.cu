@@ -1,0 +1,263 @@
+// batch.cu -- many fields, each with its own plan (so its own bandlimit),
+// through one persistent sweep launch.
+//
+// The work items of every field's factor stream go into one item table,
+// ordered by decreasing size over all fields (longest-processing-time
+// order), so the CTAs of the persistent kernel balance small and large
+// fields together.  Each item carries its field index; the kernel finds the
+// field's pages, values and bandlimit in a device table built here once,
+// and the field's input and output in caller-owned device arrays of
+// pointers.  A call therefore copies and allocates nothing, and the launch
+// can be captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <new>
+#include <vector>
+
+#include "../../include/sht.h"
+#include "kernels.h"
+#include "plan_access.h"
+
+namespace {
+
+struct BatchDir {
+  sht::FieldDesc* d_fields = nullptr;
+  sht::UnitEntry* d_units = nullptr;
+  int n_units = 0;
+  int buf_ab = 1;
+  int num_vecs = 2;
+  const uint8_t* quit_pages = nullptr;  // a stream whose final page ends the launch
+  unsigned long long quit_page = 0;
+  bool want_staged = true;
+  sht::SweepConfig cfg;
+};
+
+}  // namespace
+
+struct sht_batch_s {
+  int n = 0;
+  int q = 0;  // sht::SweepPrec
+  int device = 0;
+  int num_sms = 0;
+  int page_bytes = 0;
+  size_t optin = 0;
+  BatchDir dir[2];
+  unsigned* d_scratch = nullptr;  // queue counter per direction, then the status word
+};
+
+namespace {
+
+#define BCK(x)                                                          \
+  do {                                                                  \
+    const cudaError_t e_ = (x);                                         \
+    if (e_ != cudaSuccess) {                                            \
+      sht::set_error_detail("batch", cudaGetErrorString(e_));           \
+      return SHT_ERR_CUDA;                                              \
+    }                                                                   \
+  } while (0)
+
+void free_batch(sht_batch_t b) {
+  if (!b) return;
+  for (BatchDir& d : b->dir) {
+    cudaFree(d.d_fields);
+    cudaFree(d.d_units);
+  }
+  cudaFree(b->d_scratch);
+  delete b;
+}
+
+sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precision prec) {
+  for (int d = 0; d < 2; ++d) {
+    std::vector<sht::FieldDesc> fields(nfields);
+    std::vector<sht::UnitEntry> units;
+    BatchDir& D = b->dir[d];
+    for (int f = 0; f < nfields; ++f) {
+      sht::StreamView v;
+      const sht_status s = sht::stream_view(plans[f], prec, d, &v);
+      if (s != SHT_OK) return s;
+      if (f == 0) {
+        b->device = v.device;
+        b->num_sms = v.num_sms;
+        b->page_bytes = v.page_bytes;
+        D.quit_pages = v.pages;
+        D.quit_page = v.quit_page;
+        D.cfg.nw = v.consumer_warps;
+      } else if (v.device != b->device || v.page_bytes != b->page_bytes) {
+        sht::set_error_detail("sht_batch_create", "plans differ in device or page_bytes");
+        return SHT_ERR_INVALID_ARG;
+      }
+      fields[f].pages = v.pages;
+      fields[f].values = v.values;
+      fields[f].prescale = nullptr;
+      fields[f].twiddle = nullptr;
+      fields[f].l = v.l;
+      D.buf_ab = std::max(D.buf_ab, v.buf_ab);
+      D.num_vecs = std::max(D.num_vecs, v.num_vecs);
+      D.want_staged = D.want_staged && v.values_apart;
+      for (int u = 0; u < v.n_units; ++u) {
+        sht::UnitEntry e = v.units[u];
+        e.m = (uint32_t)f;
+        units.push_back(e);
+      }
+    }
+    std::stable_sort(units.begin(), units.end(),
+                     [](const sht::UnitEntry& a, const sht::UnitEntry& c) { return a.n_pages > c.n_pages; });
+    D.n_units = (int)units.size();
+    BCK(cudaSetDevice(b->device));
+    BCK(cudaMalloc(&D.d_fields, sizeof(sht::FieldDesc) * fields.size()));
+    BCK(cudaMalloc(&D.d_units, sizeof(sht::UnitEntry) * std::max<size_t>(1, units.size())));
+    BCK(cudaMemcpy(D.d_fields, fields.data(), sizeof(sht::FieldDesc) * fields.size(), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(D.d_units, units.data(), sizeof(sht::UnitEntry) * units.size(), cudaMemcpyHostToDevice));
+  }
+  BCK(cudaMalloc(&b->d_scratch, sizeof(unsigned) * 3));
+  BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * 3));
+  int optin = 0;
+  BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+  b->optin = (size_t)optin;
+  BCK(sht::sweep_configure(b->q, b->optin));
+  for (BatchDir& D : b->dir)
+    if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, D.cfg.nw, D.want_staged, 0, b->optin, &D.cfg))
+      return SHT_ERR_UNSUPPORTED;
+  return SHT_OK;
+}
+
+sht_status launch(sht_batch_t b, int d, const void* const* in, void* const* out, sht_stream_t stream) {
+  if (!b || !in || !out) return SHT_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % alignof(void*)) return SHT_ERR_INVALID_ARG;
+  const BatchDir& D = b->dir[d];
+  BCK(cudaSetDevice(b->device));
+  sht::SweepArgs a{};
+  a.pages = D.quit_pages;
+  a.units = D.d_units;
+  a.n_units = D.n_units;
+  a.page_bytes = b->page_bytes;
+  a.nstages = D.cfg.nstages;
+  a.buf_ab = D.buf_ab;
+  a.quit_page = D.quit_page;
+  a.counter = b->d_scratch + d;
+  a.status = b->d_scratch + 2;
+  a.num_vecs = D.num_vecs;
+  a.staged = D.cfg.staged ? 1 : 0;
+  a.fields = D.d_fields;
+  a.field_in = in;
+  a.field_out = out;
+  a.io_align = (b->q == sht::PREC_FP32) ? 8 : 16;
+  const int grid = std::max(1, std::min(b->num_sms * D.cfg.ctas_per_sm, D.n_units));
+  (void)cudaGetLastError();
+  BCK(sht::sweep_launch(b->q, D.cfg.nw, a, grid, D.cfg.smem, reinterpret_cast<cudaStream_t>(stream)));
+  return SHT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sht_status sht_batch_create(int nfields, const sht_plan_t* plans, sht_precision prec, sht_batch_t* out) {
+  if (!out) return SHT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nfields < 1 || nfields > SHT_BATCH_MAX_FIELDS || !plans) return SHT_ERR_INVALID_ARG;
+  if (prec != SHT_FP64 && prec != SHT_FP32 && prec != SHT_SPLIT32) return SHT_ERR_INVALID_ARG;
+  for (int f = 0; f < nfields; ++f)
+    if (!plans[f]) return SHT_ERR_INVALID_ARG;
+  sht_batch_t b = new (std::nothrow) sht_batch_s();
+  if (!b) return SHT_ERR_OOM;
+  b->n = nfields;
+  b->q = prec == SHT_FP64 ? sht::PREC_FP64 : (prec == SHT_FP32 ? sht::PREC_FP32 : sht::PREC_SPLIT32);
+  const sht_status s = build(b, nfields, plans, prec);
+  if (s != SHT_OK) {
+    free_batch(b);
+    return s;
+  }
+  *out = b;
+  return SHT_OK;
+}
+
+sht_status sht_batch_destroy(sht_batch_t b) {
+  if (b) {
+    cudaSetDevice(b->device);
+    free_batch(b);
+  }
+  return SHT_OK;
+}
+
+sht_status sht_batch_synthesize(sht_batch_t b, const void* const* beta, void* const* G, sht_stream_t stream) {
+  return launch(b, 0, beta, G, stream);
+}
+
+sht_status sht_batch_analyze(sht_batch_t b, const void* const* G, void* const* beta, sht_stream_t stream) {
+  return launch(b, 1, G, beta, stream);
+}
+
+sht_status sht_batch_last_device_status(sht_batch_t b, sht_stream_t stream) {
+  if (!b) return SHT_ERR_INVALID_ARG;
+  BCK(cudaSetDevice(b->device));
+  BCK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  unsigned st = 0;
+  BCK(cudaMemcpy(&st, b->d_scratch + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    // a launch stopped early: its queue counter may not have been reset
+    BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * 3));
+    return (sht_status)st;
+  }
+  return SHT_OK;
+}
+
+sht_status sht_batch_autotune(sht_batch_t b, int direction, const void* const* in, void* const* out, int reps,
+                              sht_stream_t stream) {
+  if (!b || (direction != 0 && direction != 1) || reps < 1) return SHT_ERR_INVALID_ARG;
+  BatchDir& D = b->dir[direction];
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  BCK(cudaSetDevice(b->device));
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  const sht::SweepConfig keep = D.cfg;
+  sht::SweepConfig best = keep;
+  float best_ms = -1.f;
+  sht_status result = SHT_OK;
+  for (int nw : {8, 16}) {
+    for (int nst = 2; nst <= 8 && result == SHT_OK; ++nst) {
+      sht::SweepConfig c;
+      if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, nw, D.want_staged, nst, b->optin, &c)) continue;
+      D.cfg = c;
+      result = launch(b, direction, in, out, stream);  // warm-up
+      if (result != SHT_OK) break;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && result == SHT_OK; ++r) result = launch(b, direction, in, out, stream);
+      cudaEventRecord(e1, st);
+      if (result != SHT_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        result = SHT_ERR_CUDA;
+        break;
+      }
+      result = sht_batch_last_device_status(b, stream);
+      if (result != SHT_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (best_ms < 0.f || ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  D.cfg = (result == SHT_OK) ? best : keep;
+  return result;
+}
+
+sht_status sht_batch_get_config(sht_batch_t b, int direction, int* consumer_warps, int* nstages, int* ctas_per_sm,
+                                int* smem_bytes) {
+  if (!b || (direction != 0 && direction != 1)) return SHT_ERR_INVALID_ARG;
+  const sht::SweepConfig& c = b->dir[direction].cfg;
+  if (consumer_warps) *consumer_warps = c.nw;
+  if (nstages) *nstages = c.nstages;
+  if (ctas_per_sm) *ctas_per_sm = c.ctas_per_sm;
+  if (smem_bytes) *smem_bytes = (int)c.smem;
+  return SHT_OK;
+}
+
+}  // extern "C"

@@ -243,34 +243,22 @@ sht_status upload(sht_plan_t P, int q) {
     CK(cudaMemcpy(D.pages, S.bytes.data(), D.bytes, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(D.units, S.units.data(), sizeof(sht::UnitEntry) * S.units.size(), cudaMemcpyHostToDevice));
   }
-  // Ring depth: prefer two resident CTAs per SM (their warps hide each
-  // other's level boundaries) with at least three pages in flight each; else
+  // Ring depth: two resident CTAs per SM (their warps hide each other's level
+  // boundaries) with at least three pages in flight each if they fit, else
   // one CTA with a deeper ring.
   int optin = 0;
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
   // the limit is a per-kernel setting shared by every plan: raise it to the
   // device maximum once instead of to this plan's size
   CK(sht::sweep_configure(q, (size_t)optin));
-  // values kept apart are staged per warp when the slots fit next to a ring
-  // of at least two pages; otherwise the warps stream them from HBM
-  bool staged = P->H.values_apart[q] &&
-                sht::sweep_smem_bytes(q, P->H.page_bytes, 2, buf_ab, nvecs, P->consumer_warps[q], true) <= (size_t)optin;
-  int best_nst = 0, best_ctas = 0;
-  for (int nst = 8; nst >= 2; --nst) {
-    const size_t sm = sht::sweep_smem_bytes(q, P->H.page_bytes, nst, buf_ab, nvecs, P->consumer_warps[q], staged);
-    if (sm > (size_t)optin) continue;
-    const int ctas = std::min(2, sht::sweep_blocks_per_sm(q, P->consumer_warps[q], sm));
-    const bool better = (ctas > best_ctas && (nst >= 3 || best_ctas == 0)) || best_ctas == 0;
-    if (better) {
-      best_nst = nst;
-      best_ctas = ctas;
-    }
-  }
-  if (best_nst == 0) return SHT_ERR_UNSUPPORTED;
-  P->nstages[q] = best_nst;
-  P->ctas_per_sm[q] = best_ctas;
-  P->smem[q] = sht::sweep_smem_bytes(q, P->H.page_bytes, best_nst, buf_ab, nvecs, P->consumer_warps[q], staged);
-  P->staged[q] = staged;
+  sht::SweepConfig cfg;
+  if (!sht::sweep_choose(q, P->H.page_bytes, buf_ab, nvecs, P->consumer_warps[q], P->H.values_apart[q], 0,
+                         (size_t)optin, &cfg))
+    return SHT_ERR_UNSUPPORTED;
+  P->nstages[q] = cfg.nstages;
+  P->ctas_per_sm[q] = cfg.ctas_per_sm;
+  P->smem[q] = cfg.smem;
+  P->staged[q] = cfg.staged;
   P->num_vecs[q] = nvecs;
   P->dev[q][0].buf_ab = P->dev[q][1].buf_ab = buf_ab;
   P->dev_ready[q] = true;
@@ -307,7 +295,7 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   if (s != SHT_OK) return s;
   CK(cudaSetDevice(P->device));
   const DevStream& D = P->dev[q][dir];
-  sht::SweepArgs a;
+  sht::SweepArgs a{};  // single-field launch: no field table
   a.pages = D.pages;
   a.values = D.values;
   a.units = D.units;
@@ -374,6 +362,32 @@ sht_status sht::prepared_sweep(sht_plan_t P, sht_precision prec, int dir, const 
   L->grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
   L->smem = P->smem[q];
   L->device = P->device;
+  return SHT_OK;
+}
+
+sht_status sht::stream_view(sht_plan_t P, sht_precision prec, int dir, StreamView* v) {
+  if (!P || !v || (dir != 0 && dir != 1)) return SHT_ERR_INVALID_ARG;
+  const int q = prec_index(prec);
+  if (q < 0) return SHT_ERR_INVALID_ARG;
+  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  sht_status s = ensure_prec(P, q);
+  if (s != SHT_OK) return s;
+  const DevStream& D = P->dev[q][dir];
+  const sht::Stream& S = P->H.streams[q][dir];
+  v->pages = D.pages;
+  v->values = D.values;
+  v->units = S.units.data();
+  v->n_units = (int)S.units.size();
+  v->quit_page = D.quit_page;
+  v->buf_ab = D.buf_ab;
+  v->num_vecs = P->num_vecs[q];
+  v->l = P->H.l;
+  v->page_bytes = P->H.page_bytes;
+  v->device = P->device;
+  v->num_sms = P->num_sms;
+  v->values_apart = P->H.values_apart[q];
+  v->consumer_warps = P->consumer_warps[q];
+  v->prescale = P->d_inv_w;
   return SHT_OK;
 }
 

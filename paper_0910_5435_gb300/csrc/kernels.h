@@ -10,6 +10,17 @@ namespace sht {
 
 // Arguments of the persistent butterfly sweep (one launch = one direction of
 // the Legendre stage for every order m).
+// One field of a batched launch: its plan's factor stream (device memory,
+// set when the batch is created).
+struct FieldDesc {
+  const uint8_t* pages;
+  const uint8_t* values;
+  const double* prescale;      // FOLD prescale or nullptr
+  const double2* twiddle;      // per-order phase or nullptr
+  int l;
+  int pad;
+};
+
 struct SweepArgs {
   const uint8_t* pages;        // stream pages (device)
   const uint8_t* values;       // value region (device; ops flagged F_VALUES_APART)
@@ -29,6 +40,23 @@ struct SweepArgs {
   unsigned long long* trace;   // kTraceSlots cycle counters accumulated over all CTAs, or nullptr
   int num_vecs;                // shared vectors (2, or 4 with interleaved parities)
   int staged;                  // 1: each consumer warp stages op values in two shared slots
+  // Batched launches (fields != nullptr): units[u].m is the item's field f;
+  // pages, values, l, prescale and twiddle come from fields[f], the field's
+  // input and output from field_in[f] and field_out[f] (device arrays).
+  const FieldDesc* fields;
+  const void* const* field_in;
+  void* const* field_out;
+  int io_align;                // required alignment (bytes) of field_in / field_out entries
+};
+
+// Launch shape of a sweep: consumer warps, ring depth, resident CTAs per
+// SM, dynamic shared memory, and whether op values are staged per warp.
+struct SweepConfig {
+  int nw = 8;
+  int nstages = 0;
+  int ctas_per_sm = 0;
+  size_t smem = 0;
+  bool staged = false;
 };
 
 // Trace slots (clock64 cycles summed over CTAs): consumer warps executing ops,
@@ -48,6 +76,12 @@ enum TraceSlot {
 enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2 };
 
 size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, bool staged);
+// Picks the ring depth (nstages > 0: exactly that depth) for the given warps:
+// two resident CTAs per SM with at least three pages in flight each if they
+// fit, else one CTA with the deepest ring that fits in optin bytes.  False
+// if nothing fits.
+bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, bool want_staged, int nstages,
+                  size_t optin, SweepConfig* c);
 cudaError_t sweep_configure(int prec, size_t smem);
 // resident CTAs per SM for this shared-memory size (>= 1); nw = consumer warps (8 or 16)
 int sweep_blocks_per_sm(int prec, int nw, size_t smem);

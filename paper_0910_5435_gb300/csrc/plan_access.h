@@ -6,6 +6,7 @@
 
 #include "../../include/sht.h"
 #include "kernels.h"
+#include "sht_stream.h"
 
 namespace sht {
 
@@ -24,6 +25,28 @@ struct PreparedSweep {
 // yet gives SHT_ERR_UNSUPPORTED.  dir: 0 synthesis, 1 analysis.
 sht_status prepared_sweep(sht_plan_t plan, sht_precision prec, int dir, const void* in, void* out,
                           PreparedSweep* out_launch);
+
+// A plan's stream of one precision and direction on the device.
+struct StreamView {
+  const uint8_t* pages = nullptr;
+  const uint8_t* values = nullptr;
+  const UnitEntry* units = nullptr;  // host copy of the item table (LPT order)
+  int n_units = 0;
+  unsigned long long quit_page = 0;
+  int buf_ab = 0;
+  int num_vecs = 2;
+  int l = 0;
+  int page_bytes = 0;
+  int device = 0;
+  int num_sms = 0;
+  bool values_apart = true;
+  int consumer_warps = 8;
+  const double* prescale = nullptr;  // 1 / w_{l+i} (adjoint fold)
+};
+
+// Fills *v, building and uploading the precision first if needed (this may
+// allocate).  dir: 0 synthesis, 1 analysis.
+sht_status stream_view(sht_plan_t plan, sht_precision prec, int dir, StreamView* v);
 
 // Sets the text returned by sht_last_error_detail on this thread.
 void set_error_detail(const char* where, const char* what);

@@ -40,6 +40,7 @@ constexpr int kOrd = 64;                              // page issue-order ring (
 constexpr int kConsumerWarps16 = 16;                  // upper bound on consumer warps
 constexpr long long kTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr unsigned kStatusTimeout = 5;              // SHT_ERR_TIMEOUT
+constexpr unsigned kStatusBadArg = 1;               // SHT_ERR_INVALID_ARG (a field's pointers)
 
 // ------------------------------------------------------------ PTX helpers
 
@@ -277,6 +278,7 @@ struct Sched {
   int abort;      // set when a bounded wait gave up
   int pending[kMaxStages];  // ops of the page in each stage not yet completed
   int order[kOrd];          // stage of the i-th issued page (i % kOrd)
+  uint16_t stage_field[kMaxStages];  // field of the page in each stage (batched launches)
   uint32_t dir[kDir];       // op number % kDir -> (stage << 16) | (byte offset / 16)
   uint16_t done_tag[kDoneWindow];  // low 16 bits of the last completed op number in each slot
 };
@@ -394,9 +396,25 @@ __device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, 
   return a[0];
 }
 
+// What an op needs of its field: the launch's own arguments, or one field
+// of a batched launch.
+struct FieldCtx {
+  const uint8_t* values;
+  const void* in;
+  void* out;
+  const double* prescale;
+  const double2* twiddle;
+  int l;
+};
+__device__ __forceinline__ FieldCtx field_ctx(const SweepArgs& A, int f) {
+  if (!A.fields) return {A.values, A.in, A.out, A.prescale, A.twiddle, A.l};
+  const FieldDesc& d = A.fields[f];
+  return {d.values, A.field_in[f], A.field_out[f], d.prescale, d.twiddle, d.l};
+}
+
 // One compute op (SYN_INTERP, DENSE, DENSE_G, ANA_INTERP), executed by one warp.
 template <class TR>
-__device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, const Vecs<TR>& S, const SweepArgs& A,
+__device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, const Vecs<TR>& S, const FieldCtx& A,
                                          int lane, const uint8_t* staged) {
   using C = typename TR::C;
   using V = typename TR::V;
@@ -481,7 +499,7 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
 
 // One control op over the element range [oo, oo + M), executed by one warp.
 template <class TR>
-__device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, const SweepArgs& A, int lane) {
+__device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, const FieldCtx& A, int lane) {
   using C = typename TR::C;
   using IO = typename TR::IO;
   const int l = A.l, L = 2 * l;
@@ -565,10 +583,11 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
       __nanosleep(64);
     }
   };
-  auto issue = [&](int s, uint64_t page) {
+  auto issue = [&](int s, const uint8_t* pages, uint64_t page, int field) {
+    S->stage_field[s] = (uint16_t)field;  // read by the op's warps while the page is pending
     fence_proxy_async();
     mbar_arrive_expect_tx(full + s, PB);
-    bulk_g2s(stages + (size_t)s * PB, A.pages + (size_t)page * PB, PB, full + s);
+    bulk_g2s(stages + (size_t)s * PB, pages + (size_t)page * PB, PB, full + s);
     ++uses[s];
     S->order[issued % kOrd] = s;
     ++issued;
@@ -588,19 +607,33 @@ __device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* ful
       break;
     }
     const UnitEntry e = A.units[u];
+    const int field = A.fields ? (int)e.m : 0;
+    const uint8_t* pages = A.fields ? A.fields[field].pages : A.pages;
+    if (A.fields) {
+      // a batched field's input and output come from device arrays: check
+      // them before any page of the field is issued
+      const uintptr_t io = reinterpret_cast<uintptr_t>(A.field_in[field]) |
+                           reinterpret_cast<uintptr_t>(A.field_out[field]);
+      if (!A.field_in[field] || !A.field_out[field] || (io & (uintptr_t)(A.io_align - 1))) {
+        atomicCAS(A.status, 0u, kStatusBadArg);
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+    }
     for (uint32_t pg = 0; pg < e.n_pages; ++pg) {
       const int s = free_stage();
       if (s < 0) {
         ok = false;
         break;
       }
-      issue(s, e.first_page + pg);
+      issue(s, pages, e.first_page + pg, field);
     }
     if (!ok) break;
   }
   if (ok) {
     const int s = free_stage();
-    if (s >= 0) issue(s, A.quit_page);
+    if (s >= 0) issue(s, A.pages, A.quit_page, 0);
   }
   // never leave the CTA with bulk copies still landing in its shared memory
   for (int s = 0; s < NST; ++s)
@@ -689,6 +722,7 @@ struct Claim {
   const uint8_t* op;   // header in the page
   OpHdr h;
   int slot;            // staging slot of its values (0 / 1), or -1
+  int field;           // field of its page (batched launches)
 };
 
 template <class TR>
@@ -738,6 +772,7 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
     c.stage = (int)(e >> 16);
     c.op = stages + (size_t)c.stage * PB + ((size_t)(e & 0xffffu) << 4);
     c.h = *reinterpret_cast<const OpHdr*>(c.op);
+    c.field = A.fields ? (int)S->stage_field[c.stage] : 0;
     c.slot = -1;
     const uint32_t vbytes = (uint32_t)((sizeof(Val) * c.h.M * c.h.K + 15) & ~size_t(15));
     // a block larger than a slot (not emitted by the planner) is streamed instead
@@ -747,7 +782,8 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
       if (lane == 0) {
         fence_proxy_async();  // earlier reads of this slot precede the copy into it
         mbar_arrive_expect_tx(my_bars + c.slot, vbytes);
-        bulk_g2s(my_slots + (size_t)c.slot * kSlotBytes, A.values + (size_t)c.h.vref * 16, vbytes,
+        const uint8_t* vals = A.fields ? A.fields[c.field].values : A.values;
+        bulk_g2s(my_slots + (size_t)c.slot * kSlotBytes, vals + (size_t)c.h.vref * 16, vbytes,
                  my_bars + c.slot);
       }
       inflight |= 1u << c.slot;
@@ -793,9 +829,9 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
     const long long t3 = clock64();
     const bool is_gemv = cur.h.kind >= OP_SYN_INTERP && cur.h.kind <= OP_ANA_INTERP;
     if (is_gemv)
-      run_gemv<TR>(cur.h, cur.op, V, A, lane, staged);
+      run_gemv<TR>(cur.h, cur.op, V, field_ctx(A, cur.field), lane, staged);
     else if (cur.h.kind != OP_JOIN)
-      run_control<TR>(cur.h, V, A, lane);
+      run_control<TR>(cur.h, V, field_ctx(A, cur.field), lane);
     const long long t3b = clock64();
     if (is_gemv) {
       c_gemv += t3b - t3;
@@ -936,6 +972,28 @@ int sweep_blocks_per_sm(int prec, int nw, size_t smem) {
   const cudaError_t e =
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(prec, nw), (nw + 2) * 32, smem);
   return (e == cudaSuccess && nb > 0) ? nb : 1;
+}
+
+bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, bool want_staged, int nstages,
+                  size_t optin, SweepConfig* c) {
+  c->nw = nw;
+  // staged values need their slots next to a ring of at least two pages
+  c->staged = want_staged && sweep_smem_bytes(prec, page_bytes, 2, buf_ab, num_vecs, nw, true) <= optin;
+  c->nstages = 0;
+  c->ctas_per_sm = 0;
+  c->smem = 0;
+  for (int nst = (nstages > 0 ? nstages : 8); nst >= (nstages > 0 ? nstages : 2); --nst) {
+    const size_t sm = sweep_smem_bytes(prec, page_bytes, nst, buf_ab, num_vecs, nw, c->staged);
+    if (sm > optin) continue;
+    const int ctas = std::min(2, sweep_blocks_per_sm(prec, nw, sm));
+    const bool better = (ctas > c->ctas_per_sm && (nst >= 3 || c->ctas_per_sm == 0)) || c->ctas_per_sm == 0;
+    if (better) {
+      c->nstages = nst;
+      c->ctas_per_sm = ctas;
+      c->smem = sm;
+    }
+  }
+  return c->nstages > 0;
 }
 
 cudaError_t sweep_launch(int prec, int nw, const SweepArgs& a, int grid, size_t smem, cudaStream_t st) {

@@ -32,6 +32,8 @@ EXPORTS = [
     "sht_last_device_status", "sht_direct_prepare", "sht_direct_synthesize", "sht_direct_analyze",
     "sht_workspace_bytes", "sht_phi_synthesize", "sht_phi_analyze", "sht_synthesize", "sht_analyze",
     "sht_last_error_detail", "sht_trace_enable", "sht_trace_read", "sht_legendre_synthesize_noalloc",
+    "sht_batch_create", "sht_batch_destroy", "sht_batch_synthesize", "sht_batch_analyze",
+    "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -134,6 +136,13 @@ def lib():
     L.sht_trace_enable.argtypes = [vp, c_int]
     L.sht_trace_read.argtypes = [vp, vp, c_int]
     L.sht_legendre_synthesize_noalloc.argtypes = [vp, c_int, vp, vp, c_int, vp, vp]
+    L.sht_batch_create.argtypes = [c_int, vp, c_int, vp]
+    L.sht_batch_destroy.argtypes = [vp]
+    L.sht_batch_synthesize.argtypes = [vp, vp, vp, vp]
+    L.sht_batch_analyze.argtypes = [vp, vp, vp, vp]
+    L.sht_batch_last_device_status.argtypes = [vp, vp]
+    L.sht_batch_autotune.argtypes = [vp, c_int, vp, vp, c_int, vp]
+    L.sht_batch_get_config.argtypes = [vp, c_int, vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("sht_status_string", "sht_workspace_bytes", "sht_last_error_detail"):
             getattr(L, name).restype = c_int
@@ -273,6 +282,63 @@ def sht_legendre_synthesize_noalloc(plan, prec, beta, G, slot=0, status=None, st
     _check(lib().sht_legendre_synthesize_noalloc(plan.handle, int(prec), _ptr(beta), _ptr(G), int(slot),
                                                  _ptr(status) if status is not None else None,
                                                  _stream(stream)), "sht_legendre_synthesize_noalloc")
+
+
+class Batch:
+    """Owns an ``sht_batch_t``: many fields, each with its own plan, through
+    one launch.  Holds references to its plans (they must outlive it)."""
+
+    def __init__(self, plans, prec):
+        self.plans = list(plans)
+        self.prec = int(prec)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib().sht_batch_create(len(self.plans), arr, self.prec, ctypes.byref(h)), "sht_batch_create")
+        self.handle = h.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().sht_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def config(self, direction):
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(lib().sht_batch_get_config(self.handle, int(direction), *[ctypes.byref(x) for x in v]),
+               "sht_batch_get_config")
+        return dict(zip(("consumer_warps", "nstages", "ctas_per_sm", "smem_bytes"), [x.value for x in v]))
+
+
+def pointer_array(tensors, device="cuda"):
+    """Device int64 array of the tensors' addresses (the pointer arrays of
+    the batched calls); keep it alive while a launch may read it."""
+    import torch
+    return torch.tensor([_ptr(t) for t in tensors], dtype=torch.int64, device=device)
+
+
+def sht_batch_synthesize(batch, beta_ptrs, G_ptrs, stream=None):
+    _check(lib().sht_batch_synthesize(batch.handle, _ptr(beta_ptrs), _ptr(G_ptrs), _stream(stream)),
+           "sht_batch_synthesize")
+
+
+def sht_batch_analyze(batch, G_ptrs, beta_ptrs, stream=None):
+    _check(lib().sht_batch_analyze(batch.handle, _ptr(G_ptrs), _ptr(beta_ptrs), _stream(stream)),
+           "sht_batch_analyze")
+
+
+def sht_batch_last_device_status(batch, stream=None):
+    return int(lib().sht_batch_last_device_status(batch.handle, _stream(stream)))
+
+
+def sht_batch_autotune(batch, direction, in_ptrs, out_ptrs, reps=3, stream=None):
+    _check(lib().sht_batch_autotune(batch.handle, int(direction), _ptr(in_ptrs), _ptr(out_ptrs), int(reps),
+                                    _stream(stream)), "sht_batch_autotune")
+    return batch.config(direction)
 
 
 def sht_workspace_bytes(plan, prec):

@@ -1,0 +1,151 @@
+"""Batched Legendre stage (sht_batch_*): many fields, each with its own plan
+and bandlimit, in one launch, through the C ABI.
+
+The batch runs the same op streams with the same per-op arithmetic as the
+single-field entry points, so its outputs equal theirs exactly; a few fields
+are also checked against the float64 oracle (tolerances as in the parity
+tests: float64 1e-10, split float32 1e-9, float32 2e-5, relative l2).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0910_5435_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 2: 1e-9, 1: 2e-5}
+CDT = {0: torch.complex128, 2: torch.complex128, 1: torch.complex64}
+LS = (4, 16, 32, 64, 128)
+
+
+@pytest.fixture(scope="module")
+def sht():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0910_5435_gb300 import sht as _sht
+    assert torch.cuda.is_available()
+    return _sht
+
+
+@pytest.fixture(scope="module")
+def plans(sht):
+    return {l: sht.Plan(l, 1e-12, leaf_cols=16) for l in LS}
+
+
+def rel(a, b):
+    a = torch.as_tensor(a).to(torch.complex128).cpu()
+    b = torch.as_tensor(b).to(torch.complex128).cpu()
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def fields(ls, prec, seed):
+    betas = [torch.from_numpy(inputs.random_beta(l, seed=seed + f, decay=True)).to(CDT[prec]).cuda()
+             for f, l in enumerate(ls)]
+    Gs = [torch.full((2 * l, 2 * l), float("nan"), dtype=CDT[prec], device="cuda") for l in ls]
+    return betas, Gs
+
+
+def field_ls(n, seed):
+    return [int(x) for x in np.random.default_rng(seed).choice(LS, size=n)]
+
+
+@pytest.mark.parametrize("prec", [0, 2, 1])
+def test_batch_equals_per_field_calls_and_oracle(sht, plans, prec):
+    ls = field_ls(11, 4)
+    for l in set(ls):
+        plans[l].prepare(prec)
+    B = sht.Batch([plans[l] for l in ls], prec)
+    betas, Gs = fields(ls, prec, 1000)
+    bp, gp = sht.pointer_array(betas), sht.pointer_array(Gs)
+    sht.sht_batch_synthesize(B, bp, gp)
+    assert sht.sht_batch_last_device_status(B) == 0
+    for l, beta, G in zip(ls, betas, Gs):
+        ref = torch.full_like(G, float("nan"))
+        sht.sht_legendre_synthesize(plans[l], prec, beta, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(G, ref), l
+    for f in (0, len(ls) - 1):
+        l = ls[f]
+        assert rel(Gs[f], oracle.legendre_synthesis(betas[f].cpu().numpy().astype(np.complex128), l)) < TOL[prec]
+    # analysis of the fields just synthesized
+    backs = [torch.full_like(b, float("nan")) for b in betas]
+    sht.sht_batch_analyze(B, gp, sht.pointer_array(backs))
+    assert sht.sht_batch_last_device_status(B) == 0
+    for l, G, back in zip(ls, Gs, backs):
+        ref = torch.full_like(back, float("nan"))
+        sht.sht_legendre_analyze(plans[l], prec, G, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(back, ref), l
+    for f, l in enumerate(ls):
+        assert rel(backs[f], betas[f]) < 2 * TOL[prec]
+    B.close()
+
+
+def test_batch_in_cuda_graph(sht, plans):
+    """The batched launch captured in a CUDA graph and replayed on new inputs
+    written into the same buffers."""
+    ls = field_ls(7, 5)
+    B = sht.Batch([plans[l] for l in ls], 0)
+    betas, Gs = fields(ls, 0, 2000)
+    bp, gp = sht.pointer_array(betas), sht.pointer_array(Gs)
+    sht.sht_batch_synthesize(B, bp, gp)  # first launch outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            sht.sht_batch_synthesize(B, bp, gp, stream=s)
+    for rep in range(2):
+        for f, l in enumerate(ls):
+            betas[f].copy_(torch.from_numpy(inputs.random_beta(l, seed=3000 + 100 * rep + f)))
+        g.replay()
+        torch.cuda.synchronize()
+        assert sht.sht_batch_last_device_status(B) == 0
+        for l, beta, G in zip(ls, betas, Gs):
+            ref = torch.empty_like(G)
+            sht.sht_legendre_synthesize(plans[l], 0, beta, ref)
+            torch.cuda.synchronize()
+            assert torch.equal(G, ref)
+    del g
+    B.close()
+
+
+def test_batch_autotune_keeps_results(sht, plans):
+    ls = field_ls(9, 6)
+    for l in set(ls):
+        plans[l].prepare(2)
+    B = sht.Batch([plans[l] for l in ls], 2)
+    betas, Gs = fields(ls, 2, 4000)
+    bp, gp = sht.pointer_array(betas), sht.pointer_array(Gs)
+    cfg = sht.sht_batch_autotune(B, 0, bp, gp, reps=2)
+    assert cfg["consumer_warps"] in (8, 16) and 2 <= cfg["nstages"] <= 8
+    Gs2 = [torch.full_like(G, float("nan")) for G in Gs]
+    sht.sht_batch_synthesize(B, bp, sht.pointer_array(Gs2))
+    assert sht.sht_batch_last_device_status(B) == 0
+    for l, beta, G in zip(ls, betas, Gs2):
+        ref = torch.empty_like(G)
+        sht.sht_legendre_synthesize(plans[l], 2, beta, ref)
+        torch.cuda.synchronize()
+        assert torch.equal(G, ref)
+    B.close()
+
+
+def test_batch_bad_pointer_entry_is_reported(sht, plans):
+    """A misaligned output pointer of one field is caught on the device before
+    any of that field's pages are issued; the batch works again afterwards."""
+    ls = [16, 32, 64]
+    B = sht.Batch([plans[l] for l in ls], 0)
+    betas, Gs = fields(ls, 0, 5000)
+    bad = [betas[0].data_ptr(), betas[1].data_ptr() + 8, betas[2].data_ptr()]
+    bp = torch.tensor(bad, dtype=torch.int64, device="cuda")
+    sht.sht_batch_synthesize(B, bp, sht.pointer_array(Gs))
+    assert sht.sht_batch_last_device_status(B) == 1
+    bp = sht.pointer_array(betas)
+    sht.sht_batch_synthesize(B, bp, sht.pointer_array(Gs))
+    assert sht.sht_batch_last_device_status(B) == 0
+    for l, beta, G in zip(ls, betas, Gs):
+        assert rel(G, oracle.legendre_synthesis(beta.cpu().numpy(), l)) < TOL[0]
+    B.close()

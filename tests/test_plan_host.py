@@ -167,3 +167,20 @@ def test_values_inline_layout_reproduces_oracle(prec):
     G = emulate((pages, values), P.page_bytes, l, prec, 0, beta)
     assert rel(G, oracle.legendre_synthesis(beta, l)) < (2e-5 if prec == 1 else 1e-10)
     assert check_races(P.stream(prec, 1), P.page_bytes, l) == []
+
+
+def test_batch_argument_checks_on_host():
+    """Batch creation validates its arguments before any CUDA call: empty or
+    missing plan lists, bad precisions, and host-only plans are refused."""
+    import ctypes
+    P = sht.Plan(8, 1e-12, host_only=True)
+    L = sht.lib()
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * 1)(P.handle)
+    assert L.sht_batch_create(0, arr, 0, ctypes.byref(h)) == 1
+    assert L.sht_batch_create(1, None, 0, ctypes.byref(h)) == 1
+    assert L.sht_batch_create(1, arr, 9, ctypes.byref(h)) == 1
+    assert L.sht_batch_create(1, (ctypes.c_void_p * 1)(None), 0, ctypes.byref(h)) == 1
+    assert L.sht_batch_create(1, arr, 0, ctypes.byref(h)) == 6  # host-only plan
+    assert h.value is None
+    assert L.sht_batch_destroy(None) == 0
