@@ -322,6 +322,13 @@ sht_status sht_batch_synthesize(sht_batch_t batch, const void* const* beta, void
  * G and beta as in sht_batch_synthesize. */
 sht_status sht_batch_analyze(sht_batch_t batch, const void* const* G, void* const* beta, sht_stream_t stream);
 
+/* Adjoint of the Legendre synthesis of every field (as
+ * sht_legendre_synthesize_adjoint per field): the transposed butterfly
+ * without quadrature weights, the backward pass of a loss on G.  G and beta
+ * as in sht_batch_synthesize. */
+sht_status sht_batch_synthesize_adjoint(sht_batch_t batch, const void* const* G, void* const* beta,
+                                        sht_stream_t stream);
+
 /* Device status word of the batch's launches (synchronizes stream): SHT_OK,
  * SHT_ERR_TIMEOUT (a bounded wait gave up) or SHT_ERR_INVALID_ARG (a field's
  * pointer entry was NULL or misaligned).  A non-OK status is cleared. */
@@ -329,7 +336,8 @@ sht_status sht_batch_last_device_status(sht_batch_t batch, sht_stream_t stream);
 
 /* Times each launch shape (8 or 16 consumer warps, page ring depth 2..8,
  * whatever fits in shared memory) over reps launches of the given direction
- * (0 synthesis, 1 analysis) with these pointer arrays, and keeps the fastest
+ * (0 synthesis, 1 analysis, 2 adjoint of synthesis) with these pointer
+ * arrays, and keeps the fastest
  * for that direction.  Runs the transform (writes the outputs); synchronous. */
 sht_status sht_batch_autotune(sht_batch_t batch, int direction, const void* const* in, void* const* out, int reps,
                               sht_stream_t stream);

@@ -1,0 +1,81 @@
+"""Differentiable butterfly Legendre stage for PyTorch.
+
+``legendre_synthesis(beta, plan, prec)`` returns G = S beta: the Legendre
+synthesis of Section 2 (the sums over k of eq. alternate_expansion) applied
+through the butterfly, for one field (beta of shape [T], T = 2l(2l+1)/2) or
+a batch of fields (beta of shape [B, T], one launch for the whole batch).
+
+The backward pass is the transposed butterfly without quadrature weights
+(Section 2.2, remark after Figure multi): grad_beta = S^T grad_G, through
+``sht_legendre_synthesize_adjoint`` (or its batched form).  S is real, so in
+PyTorch's convention for complex tensors (grad = dL/dRe + i dL/dIm) the
+gradient of the complex-linear map is S^T applied to the complex incoming
+gradient, and nothing is saved for the backward pass beyond the plan and
+the precision.  Coefficients and G are treated as independent complex
+numbers; a loss on the real grid (which counts orders +m and -m) would add
+its own factor 2 for m > 0 outside this function.
+"""
+
+import torch
+
+from . import sht
+
+_CDT = {sht.SHT_FP64: torch.complex128, sht.SHT_SPLIT32: torch.complex128, sht.SHT_FP32: torch.complex64}
+
+
+def _batch(plan, prec, n):
+    """Batch of n fields of one plan, cached on the plan object."""
+    cache = plan.__dict__.setdefault("_autograd_batches", {})
+    key = (int(prec), int(n))
+    if key not in cache:
+        cache[key] = sht.Batch([plan] * n, prec)
+    return cache[key]
+
+
+def _apply(plan, prec, x, adjoint):
+    l = plan.l
+    T = (2 * l) * (2 * l + 1) // 2
+    if x.dtype != _CDT[prec]:
+        raise TypeError(f"precision {prec} takes {_CDT[prec]}, got {x.dtype}")
+    if not x.is_cuda:
+        raise ValueError("tensors must be on the GPU")
+    x = x.contiguous()
+    stream = torch.cuda.current_stream(x.device)
+    single = x.dim() == (2 if adjoint else 1)
+    xs = x.unsqueeze(0) if single else x
+    n = xs.shape[0]
+    if tuple(xs.shape[1:]) != ((2 * l, 2 * l) if adjoint else (T,)):
+        raise ValueError(f"unexpected shape {tuple(x.shape)} for l={l}")
+    out = torch.empty((n, T) if adjoint else (n, 2 * l, 2 * l), dtype=x.dtype, device=x.device)
+    if n == 1:
+        fn = sht.sht_legendre_synthesize_adjoint if adjoint else sht.sht_legendre_synthesize
+        fn(plan, prec, xs[0], out[0], stream)
+    else:
+        B = _batch(plan, prec, n)
+        ip = sht.pointer_array(list(xs), device=x.device)
+        op = sht.pointer_array(list(out), device=x.device)
+        fn = sht.sht_batch_synthesize_adjoint if adjoint else sht.sht_batch_synthesize
+        fn(B, ip, op, stream)
+        # the pointer arrays must live until the launch has read them
+        ip.record_stream(stream)
+        op.record_stream(stream)
+    return out[0] if single else out
+
+
+class LegendreSynthesis(torch.autograd.Function):
+    """G = S beta with the transposed butterfly as its hand-written backward."""
+
+    @staticmethod
+    def forward(ctx, beta, plan, prec):
+        ctx.plan = plan
+        ctx.prec = int(prec)
+        return _apply(plan, int(prec), beta, adjoint=False)
+
+    @staticmethod
+    def backward(ctx, grad_G):
+        return _apply(ctx.plan, ctx.prec, grad_G, adjoint=True), None, None
+
+
+def legendre_synthesis(beta, plan, prec=sht.SHT_FP64):
+    """Differentiable Legendre synthesis of one field ([T]) or a batch ([B, T])."""
+    return LegendreSynthesis.apply(beta, plan, prec)

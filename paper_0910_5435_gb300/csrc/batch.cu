@@ -44,7 +44,7 @@ struct sht_batch_s {
   int num_sms = 0;
   int page_bytes = 0;
   size_t optin = 0;
-  BatchDir dir[2];
+  BatchDir dir[3];                // synthesis, analysis, adjoint of synthesis
   unsigned* d_scratch = nullptr;  // queue counter per direction, then the status word
 };
 
@@ -69,14 +69,17 @@ void free_batch(sht_batch_t b) {
   delete b;
 }
 
+constexpr int kDirs = 3;
+
 sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precision prec) {
-  for (int d = 0; d < 2; ++d) {
+  for (int d = 0; d < kDirs; ++d) {
     std::vector<sht::FieldDesc> fields(nfields);
     std::vector<sht::UnitEntry> units;
     BatchDir& D = b->dir[d];
     for (int f = 0; f < nfields; ++f) {
       sht::StreamView v;
-      const sht_status s = sht::stream_view(plans[f], prec, d, &v);
+      // the adjoint runs the analysis stream with the 1/w fold prescale
+      const sht_status s = sht::stream_view(plans[f], prec, d == 2 ? 1 : d, &v);
       if (s != SHT_OK) return s;
       if (f == 0) {
         b->device = v.device;
@@ -91,7 +94,7 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
       }
       fields[f].pages = v.pages;
       fields[f].values = v.values;
-      fields[f].prescale = nullptr;
+      fields[f].prescale = d == 2 ? v.prescale : nullptr;
       fields[f].twiddle = nullptr;
       fields[f].l = v.l;
       D.buf_ab = std::max(D.buf_ab, v.buf_ab);
@@ -112,8 +115,8 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
     BCK(cudaMemcpy(D.d_fields, fields.data(), sizeof(sht::FieldDesc) * fields.size(), cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(D.d_units, units.data(), sizeof(sht::UnitEntry) * units.size(), cudaMemcpyHostToDevice));
   }
-  BCK(cudaMalloc(&b->d_scratch, sizeof(unsigned) * 3));
-  BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * 3));
+  BCK(cudaMalloc(&b->d_scratch, sizeof(unsigned) * (kDirs + 1)));
+  BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * (kDirs + 1)));
   int optin = 0;
   BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
   b->optin = (size_t)optin;
@@ -138,7 +141,7 @@ sht_status launch(sht_batch_t b, int d, const void* const* in, void* const* out,
   a.buf_ab = D.buf_ab;
   a.quit_page = D.quit_page;
   a.counter = b->d_scratch + d;
-  a.status = b->d_scratch + 2;
+  a.status = b->d_scratch + kDirs;
   a.num_vecs = D.num_vecs;
   a.staged = D.cfg.staged ? 1 : 0;
   a.fields = D.d_fields;
@@ -191,15 +194,20 @@ sht_status sht_batch_analyze(sht_batch_t b, const void* const* G, void* const* b
   return launch(b, 1, G, beta, stream);
 }
 
+sht_status sht_batch_synthesize_adjoint(sht_batch_t b, const void* const* G, void* const* beta,
+                                        sht_stream_t stream) {
+  return launch(b, 2, G, beta, stream);
+}
+
 sht_status sht_batch_last_device_status(sht_batch_t b, sht_stream_t stream) {
   if (!b) return SHT_ERR_INVALID_ARG;
   BCK(cudaSetDevice(b->device));
   BCK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
   unsigned st = 0;
-  BCK(cudaMemcpy(&st, b->d_scratch + 2, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  BCK(cudaMemcpy(&st, b->d_scratch + kDirs, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (st != 0) {
     // a launch stopped early: its queue counter may not have been reset
-    BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * 3));
+    BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * (kDirs + 1)));
     return (sht_status)st;
   }
   return SHT_OK;
@@ -207,7 +215,7 @@ sht_status sht_batch_last_device_status(sht_batch_t b, sht_stream_t stream) {
 
 sht_status sht_batch_autotune(sht_batch_t b, int direction, const void* const* in, void* const* out, int reps,
                               sht_stream_t stream) {
-  if (!b || (direction != 0 && direction != 1) || reps < 1) return SHT_ERR_INVALID_ARG;
+  if (!b || direction < 0 || direction >= kDirs || reps < 1) return SHT_ERR_INVALID_ARG;
   BatchDir& D = b->dir[direction];
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   BCK(cudaSetDevice(b->device));
@@ -251,7 +259,7 @@ sht_status sht_batch_autotune(sht_batch_t b, int direction, const void* const* i
 
 sht_status sht_batch_get_config(sht_batch_t b, int direction, int* consumer_warps, int* nstages, int* ctas_per_sm,
                                 int* smem_bytes) {
-  if (!b || (direction != 0 && direction != 1)) return SHT_ERR_INVALID_ARG;
+  if (!b || direction < 0 || direction >= kDirs) return SHT_ERR_INVALID_ARG;
   const sht::SweepConfig& c = b->dir[direction].cfg;
   if (consumer_warps) *consumer_warps = c.nw;
   if (nstages) *nstages = c.nstages;

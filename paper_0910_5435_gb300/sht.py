@@ -33,7 +33,7 @@ EXPORTS = [
     "sht_workspace_bytes", "sht_phi_synthesize", "sht_phi_analyze", "sht_synthesize", "sht_analyze",
     "sht_last_error_detail", "sht_trace_enable", "sht_trace_read", "sht_legendre_synthesize_noalloc",
     "sht_batch_create", "sht_batch_destroy", "sht_batch_synthesize", "sht_batch_analyze",
-    "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config",
+    "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config", "sht_batch_synthesize_adjoint",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -140,6 +140,7 @@ def lib():
     L.sht_batch_destroy.argtypes = [vp]
     L.sht_batch_synthesize.argtypes = [vp, vp, vp, vp]
     L.sht_batch_analyze.argtypes = [vp, vp, vp, vp]
+    L.sht_batch_synthesize_adjoint.argtypes = [vp, vp, vp, vp]
     L.sht_batch_last_device_status.argtypes = [vp, vp]
     L.sht_batch_autotune.argtypes = [vp, c_int, vp, vp, c_int, vp]
     L.sht_batch_get_config.argtypes = [vp, c_int, vp, vp, vp, vp]
@@ -329,6 +330,11 @@ def sht_batch_synthesize(batch, beta_ptrs, G_ptrs, stream=None):
 def sht_batch_analyze(batch, G_ptrs, beta_ptrs, stream=None):
     _check(lib().sht_batch_analyze(batch.handle, _ptr(G_ptrs), _ptr(beta_ptrs), _stream(stream)),
            "sht_batch_analyze")
+
+
+def sht_batch_synthesize_adjoint(batch, G_ptrs, beta_ptrs, stream=None):
+    _check(lib().sht_batch_synthesize_adjoint(batch.handle, _ptr(G_ptrs), _ptr(beta_ptrs), _stream(stream)),
+           "sht_batch_synthesize_adjoint")
 
 
 def sht_batch_last_device_status(batch, stream=None):
