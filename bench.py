@@ -52,6 +52,34 @@ def parse():
     return ap.parse_args()
 
 
+def shard_fields(ls, rank, world):
+    """Fields of a batch assigned to one rank: longest-processing-time order
+    with the cost of a field taken as l^2 log l (the butterfly's work), each
+    field to the currently least loaded rank; ties go to the lower rank.
+    Every rank computes the same assignment, so no exchange is needed."""
+    import math
+    order = sorted(range(len(ls)), key=lambda f: (-ls[f] ** 2 * math.log2(max(2, ls[f])), f))
+    load = [0.0] * world
+    mine = []
+    for f in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += ls[f] ** 2 * math.log2(max(2, ls[f]))
+        if r == rank:
+            mine.append(f)
+    return sorted(mine)
+
+
+def max_over_ranks(value, world, dist, device=None):
+    """The largest value over all ranks (the job's time is its slowest
+    rank's); the value itself when there is one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -182,65 +210,81 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def batched_leg(args, sht, inputs, torch, dev, stream, plan):
+def batched_leg(args, sht, inputs, torch, dev, stream, plan, rank=0, world=1, dist=None):
     """Many fields of mixed bandlimits (l drawn uniformly from 64..1024, seed
     4; beta ~ N(0,1)/(k+1), seed 1000 + f) through one batched launch per
     direction, split float32, launch shape autotuned, replayed from a CUDA
-    graph; against a loop of per-field launches on the same buffers."""
-    ls = [int(x) for x in np.random.default_rng(4).choice([64, 128, 256, 512, 1024], size=args.batch_fields)]
-    plans = {}
-    t0 = time.perf_counter()
-    for l in sorted(set(ls)):
-        plans[l] = plan if l == args.l else sht.Plan(l, args.eps, leaf_cols=args.leaf_cols, page_bytes=args.page_bytes,
-                                                     consumer_warps=args.consumer_warps)
-        plans[l].prepare(sht.SHT_SPLIT32)
-    t_plans = time.perf_counter() - t0
-    betas = [torch.from_numpy(inputs.random_beta(l, seed=1000 + f, decay=True)).to(dev) for f, l in enumerate(ls)]
-    Gs = [torch.empty((2 * l, 2 * l), dtype=torch.complex128, device=dev) for l in ls]
-    backs = [torch.empty_like(b) for b in betas]
-    B = sht.Batch([plans[l] for l in ls], sht.SHT_SPLIT32)
-    bp, gp, kp = sht.pointer_array(betas), sht.pointer_array(Gs), sht.pointer_array(backs)
-    cfg_syn = sht.sht_batch_autotune(B, 0, bp, gp, reps=2, stream=stream)
-    cfg_ana = sht.sht_batch_autotune(B, 1, gp, kp, reps=2, stream=stream)
-    graph = torch.cuda.CUDAGraph()
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(stream)
-    with torch.cuda.stream(side):
-        with torch.cuda.graph(graph, stream=side):
-            sht.sht_batch_synthesize(B, bp, gp, side)
-            sht.sht_batch_analyze(B, gp, kp, side)
-    torch.cuda.synchronize()
-
-    def timed(fn, steps):
-        for _ in range(2):
-            fn()
+    graph; against a loop of per-field launches on the same buffers.  With
+    several ranks the fields are sharded (shard_fields) and the times are the
+    slowest rank's: the total work is fixed (strong scaling)."""
+    all_ls = [int(x) for x in np.random.default_rng(4).choice([64, 128, 256, 512, 1024], size=args.batch_fields)]
+    mine = shard_fields(all_ls, rank, world)
+    ls = [all_ls[f] for f in mine]
+    def run_local():
+        plans = {}
+        t0 = time.perf_counter()
+        for l in sorted(set(ls)):
+            plans[l] = plan if l == args.l else sht.Plan(l, args.eps, leaf_cols=args.leaf_cols, page_bytes=args.page_bytes,
+                                                         consumer_warps=args.consumer_warps)
+            plans[l].prepare(sht.SHT_SPLIT32)
+        t_plans = time.perf_counter() - t0
+        betas = [torch.from_numpy(inputs.random_beta(all_ls[f], seed=1000 + f, decay=True)).to(dev) for f in mine]
+        Gs = [torch.empty((2 * l, 2 * l), dtype=torch.complex128, device=dev) for l in ls]
+        backs = [torch.empty_like(b) for b in betas]
+        B = sht.Batch([plans[l] for l in ls], sht.SHT_SPLIT32)
+        bp, gp, kp = sht.pointer_array(betas), sht.pointer_array(Gs), sht.pointer_array(backs)
+        cfg_syn = sht.sht_batch_autotune(B, 0, bp, gp, reps=2, stream=stream)
+        cfg_ana = sht.sht_batch_autotune(B, 1, gp, kp, reps=2, stream=stream)
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                sht.sht_batch_synthesize(B, bp, gp, side)
+                sht.sht_batch_analyze(B, gp, kp, side)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
 
-    steps = max(3, args.steps // 2)
-    ms_batch = timed(graph.replay, steps)
-    status = sht.sht_batch_last_device_status(B, stream)
-    Gb = [g.clone() for g in Gs]
-    kb = [k.clone() for k in backs]
+        def timed(fn, steps):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / steps
 
-    def loop():
-        for l, b, g in zip(ls, betas, Gs):
-            sht.sht_legendre_synthesize(plans[l], sht.SHT_SPLIT32, b, g, stream)
-        for l, g, k in zip(ls, Gs, backs):
-            sht.sht_legendre_analyze(plans[l], sht.SHT_SPLIT32, g, k, stream)
+        steps = max(3, args.steps // 2)
+        ms_batch = timed(graph.replay, steps)
+        status = sht.sht_batch_last_device_status(B, stream)
+        Gb = [g.clone() for g in Gs]
+        kb = [k.clone() for k in backs]
 
-    ms_loop = timed(loop, steps)
-    same = all(torch.equal(a, b) for a, b in zip(Gb, Gs)) and all(torch.equal(a, b) for a, b in zip(kb, backs))
-    eps_inv = max(float(torch.linalg.vector_norm(k - b) / torch.linalg.vector_norm(b)) for k, b in zip(kb, betas))
-    B.close()
+        def loop():
+            for l, b, g in zip(ls, betas, Gs):
+                sht.sht_legendre_synthesize(plans[l], sht.SHT_SPLIT32, b, g, stream)
+            for l, g, k in zip(ls, Gs, backs):
+                sht.sht_legendre_analyze(plans[l], sht.SHT_SPLIT32, g, k, stream)
+
+        ms_loop = timed(loop, steps)
+        same = all(torch.equal(a, b) for a, b in zip(Gb, Gs)) and all(torch.equal(a, b) for a, b in zip(kb, backs))
+        eps_inv = max(float(torch.linalg.vector_norm(k - b) / torch.linalg.vector_norm(b)) for k, b in zip(kb, betas))
+        B.close()
+        return ms_batch, ms_loop, eps_inv, same, status, cfg_syn, cfg_ana, t_plans
+
+    if ls:
+        ms_batch, ms_loop, eps_inv, same, status, cfg_syn, cfg_ana, t_plans = run_local()
+    else:  # more ranks than fields: this rank has nothing to do
+        ms_batch, ms_loop, eps_inv, same, status, cfg_syn, cfg_ana, t_plans = 0.0, 0.0, 0.0, True, 0, None, None, 0.0
+    ms_batch = max_over_ranks(ms_batch, world, dist, dev)
+    ms_loop = max_over_ranks(ms_loop, world, dist, dev)
+    eps_inv = max_over_ranks(eps_inv, world, dist, dev)
+    same = max_over_ranks(0.0 if same else 1.0, world, dist, dev) == 0.0
+    ls = all_ls
     return {
-        "fields": len(ls), "l_counts": {str(l): ls.count(l) for l in sorted(set(ls))},
+        "fields": len(ls), "ranks": world, "l_counts": {str(l): ls.count(l) for l in sorted(set(ls))},
         "field_transforms_per_s": 2.0 * len(ls) / (ms_batch / 1e3),
         "ms_batch_synthesis_plus_analysis": ms_batch, "ms_per_field_loop": ms_loop,
         "speedup_vs_loop": ms_loop / ms_batch, "batch_equals_loop": same, "max_eps_inv": eps_inv,
@@ -323,10 +367,7 @@ def main():
     total_ms, ms_syn, ms_ana = time_path(sht.SHT_FP64, args.steps, 0, beta, G, back)
     clk = clocks.stop()
     status = sht.sht_last_device_status(plan, stream)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dist, dev)
     value = world * 2.0 * args.steps / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
     eps_inv64 = float(torch.linalg.vector_norm(back - beta) / torch.linalg.vector_norm(beta))
@@ -353,11 +394,7 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dist, dev)
     e2e_value = world * 2.0 * args.steps / (e2e_ms / 1e3)
     nbytes = beta.numel() * beta.element_size()
 
@@ -416,8 +453,8 @@ def main():
         extras["direct_G"] = g.cpu().numpy()
         extras["direct_beta"] = bk.cpu().numpy()
 
-    if not args.no_extras and args.batch_fields > 0 and rank == 0:
-        extras["batched_split32"] = batched_leg(args, sht, inputs, torch, dev, stream, plan)
+    if not args.no_extras and args.batch_fields > 0:
+        extras["batched_split32"] = batched_leg(args, sht, inputs, torch, dev, stream, plan, rank, world, dist)
 
     cpu = None
     rel = {}
