@@ -52,6 +52,24 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM traffic of one float64 sweep launch at l = 1024 (leaf_cols 32, 8 KB
+# pages), dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu
+# capture, mean of a synthesis (6.527 GB) and an analysis (6.404 GB) launch
+# (profiles/bfly_sweep_fp64_l1024_dram.md).  Valid only for the kernel and
+# stream-format sources it was taken with: SWEEP_SOURCES_SHA is their hash.
+SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4655e9}
+SWEEP_SOURCES_SHA = "08abd26f3a2f2210"
+
+
+def sweep_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("sweep.cu", "sht_stream.h", "plan_build.cpp", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_0910_5435_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
 def shard_fields(ls, rank, world):
     """Fields of a batch assigned to one rank: longest-processing-time order
     with the cost of a field taken as l^2 log l (the butterfly's work), each
@@ -293,6 +311,50 @@ def batched_leg(args, sht, inputs, torch, dev, stream, plan, rank=0, world=1, di
     }
 
 
+def autograd_leg(args, sht, inputs, torch, dev, stream):
+    """Differentiable Legendre stage: l = 512, a batch of 16 fields, loss
+    ||synthesize(beta) - g||^2 with g the synthesis of an independent
+    band-limited beta_g (seeds 5000 + f and 6000 + f); forward plus the
+    hand-written backward (the transposed butterfly) timed for the float64
+    and split float32 paths.  Gradient accuracy against the oracle and
+    finite differences is covered by the test suite."""
+    from paper_0910_5435_gb300 import autograd as ag
+    l, nb = 512, 16
+    P = sht.Plan(l, args.eps, leaf_cols=args.leaf_cols, page_bytes=args.page_bytes,
+                 consumer_warps=args.consumer_warps)
+    beta0 = torch.from_numpy(np.stack([inputs.random_beta(l, seed=5000 + f, decay=True) for f in range(nb)])).to(dev)
+    beta_g = torch.from_numpy(np.stack([inputs.random_beta(l, seed=6000 + f, decay=True) for f in range(nb)])).to(dev)
+    out = {"l": l, "batch": nb}
+    grads = {}
+    for name, prec in (("fp64", sht.SHT_FP64), ("split32", sht.SHT_SPLIT32)):
+        P.prepare(prec)
+        g = ag.legendre_synthesis(beta_g, P, prec).detach()
+
+        def step():
+            beta = beta0.clone().requires_grad_()
+            loss = (ag.legendre_synthesis(beta, P, prec) - g).abs().pow(2).sum()
+            loss.backward()
+            return beta.grad
+
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        steps = max(3, args.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            gr = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        grads[name] = gr
+        out[name] = {"ms_forward_backward": ms, "field_fwd_bwd_per_s": nb / (ms / 1e3)}
+    out["rel_grad_split32_vs_fp64"] = float(torch.linalg.vector_norm(grads["split32"] - grads["fp64"])
+                                            / torch.linalg.vector_norm(grads["fp64"]))
+    P.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -404,8 +466,14 @@ def main():
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs") if peaks else None
     stream_gbs = st["stream_bytes_fp64"] / (0.5 * (ms_syn + ms_ana) / 1e3) / 1e9
+    traffic = None
+    if (sweep_sources_sha() == SWEEP_SOURCES_SHA and l == SWEEP_TRAFFIC_BYTES["l"]
+            and args.leaf_cols == SWEEP_TRAFFIC_BYTES["leaf_cols"] and args.page_bytes == SWEEP_TRAFFIC_BYTES["page_bytes"]):
+        traffic = SWEEP_TRAFFIC_BYTES["bytes"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                "algorithmic_bytes_per_launch": st["stream_bytes_fp64"] + nbytes + G.numel() * G.element_size(),
                 "kernel": "bfly_sweep_kernel<TF64>",
                 "peak_source": "measured float64 FMA loop on this pool (DESIGN.md); nominal 1.25",
                 "hbm_view": {"stream_bytes_per_launch": st["stream_bytes_fp64"], "achieved_gbs": stream_gbs,
@@ -455,6 +523,8 @@ def main():
 
     if not args.no_extras and args.batch_fields > 0:
         extras["batched_split32"] = batched_leg(args, sht, inputs, torch, dev, stream, plan, rank, world, dist)
+    if not args.no_extras and rank == 0:
+        extras["autograd_l512_b16"] = autograd_leg(args, sht, inputs, torch, dev, stream)
 
     cpu = None
     rel = {}
