@@ -116,6 +116,13 @@ typedef struct {
    * op into one of its two shared-memory slots while it runs the current
    * one (ops hold at most 1024 values).  A tuning knob. */
   int values_inline;
+  /* Tests of failure detection only (default 0): 1 makes the first compute
+   * op of the first order of every stream list itself as its predecessor, a
+   * completion that never comes.  Launches of such a plan end when the
+   * kernel's bounded wait gives up (about 2 s): every wait of the CTA
+   * returns, copies in flight are drained, and sht_last_device_status
+   * reports SHT_ERR_TIMEOUT; the context stays usable. */
+  int debug_unmet_dependency;
 } sht_plan_opts;
 
 typedef struct {

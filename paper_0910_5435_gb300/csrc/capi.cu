@@ -421,6 +421,7 @@ sht_status sht_plan_opts_default(sht_plan_opts* o) {
   o->eps_fp32 = 0.0;
   o->consumer_warps = 0;
   o->values_inline = 0;
+  o->debug_unmet_dependency = 0;
   return SHT_OK;
 }
 
@@ -463,6 +464,7 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   H.num_threads = o.num_threads;
   H.page_bytes = o.page_bytes;
   for (int q = 0; q < 3; ++q) H.values_apart[q] = (o.values_inline == 0);
+  H.debug_unmet_dep = o.debug_unmet_dependency != 0;
 
   if (!P->host_only) {
     int dev = 0, count = 0;

@@ -644,6 +644,7 @@ struct Emitter {
   size_t vs;
   Tracker* T = nullptr;
   std::vector<uint8_t>* values = nullptr;  // value region of the item, or nullptr: values inline
+  bool plant_unmet = false;  // next compute op waits for itself (failure-detection tests)
   int next_op = 0;    // number of the next op within the item
   int seg_start = 0;  // first op of the current segment (after its JOIN)
   int positions = 0;
@@ -765,6 +766,10 @@ struct Emitter {
     for (int u : preds) {
       if (t - u <= 0 || t - u > 65535) throw std::logic_error("predecessor out of range");
       all.push_back((uint16_t)(t - u));
+    }
+    if (plant_unmet && !all.empty() && h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) {
+      all[0] = 0;  // delta 0: the op's own completion, which can never come first
+      plant_unmet = false;
     }
     all.insert(all.end(), idx.begin(), idx.end());
     h.npred = (uint16_t)preds.size();
@@ -1233,6 +1238,7 @@ void emit_streams(PlanHost& P, int prec) {
       E.T = &T;
       E.l = P.l;
       E.values = apart ? &vals : nullptr;
+      E.plant_unmet = P.debug_unmet_dep && std::find(ms.begin(), ms.end(), 0) != ms.end();
       E.open_item(positions);
       for (int m : ms) emit_unit(P, prec, dir, m, E);
       return E.next_op;

@@ -75,6 +75,7 @@ struct PlanHost {
   int leaf_cols = 64, min_band_rows = 32, num_threads = 0, page_bytes = 8192;
   bool interleave_parities = false;
   bool values_apart[3] = {true, true, true};  // per precision: value blocks outside the pages
+  bool debug_unmet_dep = false;  // plant a never-met predecessor (failure-detection tests)
   // Gauss-Legendre nodes (all 2l, ascending), weights, and the angle of each
   // positive node (theta_{l+i} in (0, pi/2)).
   std::vector<double> x, w, theta_pos;

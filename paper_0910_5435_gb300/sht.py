@@ -59,6 +59,7 @@ class sht_plan_opts(ctypes.Structure):
         ("eps_fp32", ctypes.c_double),
         ("consumer_warps", ctypes.c_int),
         ("values_inline", ctypes.c_int),
+        ("debug_unmet_dependency", ctypes.c_int),
     ]
 
 
@@ -182,7 +183,8 @@ class Plan:
     """Owns an ``sht_plan_t`` (``sht_plan_create_ex`` / ``sht_plan_destroy``)."""
 
     def __init__(self, l, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, host_only=False,
-                 num_threads=0, page_bytes=0, eps_fp32=0.0, consumer_warps=0, values_inline=0):
+                 num_threads=0, page_bytes=0, eps_fp32=0.0, consumer_warps=0, values_inline=0,
+                 debug_unmet_dependency=0):
         L = lib()
         opts = sht_plan_opts()
         _check(L.sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
@@ -195,6 +197,7 @@ class Plan:
         opts.eps_fp32 = eps_fp32
         opts.consumer_warps = consumer_warps
         opts.values_inline = values_inline
+        opts.debug_unmet_dependency = debug_unmet_dependency
         h = ctypes.c_void_p()
         _check(L.sht_plan_create_ex(int(l), float(eps_id), ctypes.byref(opts), ctypes.byref(h)),
                "sht_plan_create_ex")

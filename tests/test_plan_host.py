@@ -184,3 +184,19 @@ def test_batch_argument_checks_on_host():
     assert L.sht_batch_create(1, arr, 0, ctypes.byref(h)) == 6  # host-only plan
     assert h.value is None
     assert L.sht_batch_destroy(None) == 0
+
+
+def test_debug_unmet_dependency_plants_one_self_wait():
+    """The failure-detection option marks exactly one compute op per stream
+    as its own predecessor (delta 0); a normal plan has none."""
+    from tests.stream_emulator import OP_ANA, OP_SYN
+    for debug, expected in ((1, 1), (0, 0)):
+        P = sht.Plan(32, 1e-12, leaf_cols=8, host_only=True, debug_unmet_dependency=debug)
+        for d in (0, 1):
+            n = 0
+            for h, idx, _ in iter_ops(P.stream(0, d), P.page_bytes, with_preds=True):
+                npred = int(h["npred"])
+                if any(int(x) == 0 for x in idx[:npred]):
+                    assert OP_SYN <= int(h["kind"]) <= OP_ANA
+                    n += 1
+            assert n == expected, (debug, d, n)
