@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
-# float64 FMA peak of this GB300 pool, measured with a DFMA throughput loop
+# float64 FMA peak of a GB300, measured with a DFMA throughput loop
 # (1.89 FMA thread-ops / clock / SM x 152 SMs x 2.07 GHz x 2 flops); nominal 1.25
 FP64_PEAK_TFLOPS = 1.19
 METRIC = "SHT/s at l=1024, butterfly vs direct FP64 on GPU (Legendre-stage transforms per second)"
@@ -475,7 +475,7 @@ def main():
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "algorithmic_bytes_per_launch": st["stream_bytes_fp64"] + nbytes + G.numel() * G.element_size(),
                 "kernel": "bfly_sweep_kernel<TF64>",
-                "peak_source": "measured float64 FMA loop on this pool (DESIGN.md); nominal 1.25",
+                "peak_source": "measured: float64 FMA throughput loop on a GB300, 1.89 FMA/clk/SM x 152 SMs x 2.07 GHz; nominal 1.25",
                 "hbm_view": {"stream_bytes_per_launch": st["stream_bytes_fp64"], "achieved_gbs": stream_gbs,
                              "peak_gbs": hbm or HBM_FALLBACK_GBS,
                              "frac": stream_gbs / (hbm or HBM_FALLBACK_GBS),

@@ -281,7 +281,7 @@ sht_status sht_trace_enable(sht_plan_t plan, int enable);
  * Synchronizes the device.  SHT_ERR_UNSUPPORTED if tracing is disabled. */
 sht_status sht_trace_read(sht_plan_t plan, unsigned long long* out, int reset);
 
-/* ------------------------------------- direct float64 baseline (K3-style) */
+/* ----------------------------------------------- direct float64 baseline */
 
 /* Stores the dense operator P-bar^m_{m+p+2j}(x_{l+i}) (float64, kept rows
  * only) on the device: sum over (m,p) of rows * n_{m,p} * 8 bytes
