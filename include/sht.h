@@ -106,7 +106,7 @@ typedef struct {
   /* eps used for the IDs of the SHT_FP32 factors; <= 0 selects
    * max(eps_id, 1e-7).  (FP32 cannot use ranks below its own precision.) */
   double eps_fp32;
-  /* Warps per CTA of the sweep kernels that execute ops (8 or 16; 0 =
+  /* Warps per CTA of the sweep kernels that execute ops (8, 12 or 16; 0 =
    * per precision: 8 for SHT_FP64 and SHT_SPLIT32, 16 for SHT_FP32).  A
    * tuning knob; results do not depend on it. */
   int consumer_warps;
@@ -114,7 +114,7 @@ typedef struct {
    * sit in a separate region, the pages carry only op headers and index
    * lists, and each executing warp bulk-copies the value block of its next
    * op into one of its two shared-memory slots while it runs the current
-   * one (ops hold at most 1024 values).  A tuning knob. */
+   * one (ops hold at most slot_values values).  A tuning knob. */
   int values_inline;
   /* Tests of failure detection only (default 0): 1 makes the first compute
    * op of the first order of every stream list itself as its predecessor, a
@@ -123,6 +123,11 @@ typedef struct {
    * returns, copies in flight are drained, and sht_last_device_status
    * reports SHT_ERR_TIMEOUT; the context stays usable. */
   int debug_unmet_dependency;
+  /* Values kept apart: the most values one op may hold, which is the size of
+   * a consumer warp's staging slot (a multiple of 32 in 128..2048; 0 =
+   * default 1024).  Smaller slots let more consumer warps fit in shared
+   * memory, at the cost of splitting blocks into more ops.  A tuning knob. */
+  int slot_values;
 } sht_plan_opts;
 
 typedef struct {

@@ -31,7 +31,7 @@ struct BatchDir {
   int num_vecs = 2;
   const uint8_t* quit_pages = nullptr;  // a stream whose final page ends the launch
   unsigned long long quit_page = 0;
-  bool want_staged = true;
+  int slot_bytes = 0;  // largest staging slot of the fields (0: a field keeps values in its pages)
   sht::SweepConfig cfg;
 };
 
@@ -99,7 +99,7 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
       fields[f].l = v.l;
       D.buf_ab = std::max(D.buf_ab, v.buf_ab);
       D.num_vecs = std::max(D.num_vecs, v.num_vecs);
-      D.want_staged = D.want_staged && v.values_apart;
+      D.slot_bytes = (f == 0 || D.slot_bytes > 0) && v.slot_bytes > 0 ? std::max(D.slot_bytes, v.slot_bytes) : 0;
       for (int u = 0; u < v.n_units; ++u) {
         sht::UnitEntry e = v.units[u];
         e.m = (uint32_t)f;
@@ -122,7 +122,7 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
   b->optin = (size_t)optin;
   BCK(sht::sweep_configure(b->q, b->optin));
   for (BatchDir& D : b->dir)
-    if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, D.cfg.nw, D.want_staged, 0, b->optin, &D.cfg))
+    if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, D.cfg.nw, D.slot_bytes, 0, b->optin, &D.cfg))
       return SHT_ERR_UNSUPPORTED;
   return SHT_OK;
 }
@@ -144,6 +144,7 @@ sht_status launch(sht_batch_t b, int d, const void* const* in, void* const* out,
   a.status = b->d_scratch + kDirs;
   a.num_vecs = D.num_vecs;
   a.staged = D.cfg.staged ? 1 : 0;
+  a.slot_bytes = D.cfg.slot_bytes;
   a.fields = D.d_fields;
   a.field_in = in;
   a.field_out = out;
@@ -226,10 +227,10 @@ sht_status sht_batch_autotune(sht_batch_t b, int direction, const void* const* i
   sht::SweepConfig best = keep;
   float best_ms = -1.f;
   sht_status result = SHT_OK;
-  for (int nw : {8, 16}) {
+  for (int nw : {8, 12, 16}) {
     for (int nst = 2; nst <= 8 && result == SHT_OK; ++nst) {
       sht::SweepConfig c;
-      if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, nw, D.want_staged, nst, b->optin, &c)) continue;
+      if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, nw, D.slot_bytes, nst, b->optin, &c)) continue;
       D.cfg = c;
       result = launch(b, direction, in, out, stream);  // warm-up
       if (result != SHT_OK) break;

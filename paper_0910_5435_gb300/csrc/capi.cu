@@ -64,6 +64,7 @@ struct sht_plan_s {
   int consumer_warps[kNumPrec] = {8, 8, 8};
   int nstages[kNumPrec] = {4, 4, 4};
   bool staged[kNumPrec] = {false, false, false};
+  int slot_bytes[kNumPrec] = {0, 0, 0};
   int num_vecs[kNumPrec] = {2, 2, 2};
   int ctas_per_sm[kNumPrec] = {1, 1, 1};
   DevStream dev[kNumPrec][2];
@@ -252,13 +253,15 @@ sht_status upload(sht_plan_t P, int q) {
   // device maximum once instead of to this plan's size
   CK(sht::sweep_configure(q, (size_t)optin));
   sht::SweepConfig cfg;
-  if (!sht::sweep_choose(q, P->H.page_bytes, buf_ab, nvecs, P->consumer_warps[q], P->H.values_apart[q], 0,
-                         (size_t)optin, &cfg))
+  const int slot_bytes = P->H.values_apart[q] ? P->H.slot_values * (q == sht::PREC_FP32 ? 4 : 8) : 0;
+  if (!sht::sweep_choose(q, P->H.page_bytes, buf_ab, nvecs, P->consumer_warps[q], slot_bytes, 0, (size_t)optin,
+                         &cfg))
     return SHT_ERR_UNSUPPORTED;
   P->nstages[q] = cfg.nstages;
   P->ctas_per_sm[q] = cfg.ctas_per_sm;
   P->smem[q] = cfg.smem;
   P->staged[q] = cfg.staged;
+  P->slot_bytes[q] = cfg.slot_bytes;
   P->num_vecs[q] = nvecs;
   P->dev[q][0].buf_ab = P->dev[q][1].buf_ab = buf_ab;
   P->dev_ready[q] = true;
@@ -312,6 +315,7 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.trace = P->d_trace;
   a.num_vecs = P->num_vecs[q];
   a.staged = P->staged[q] ? 1 : 0;
+  a.slot_bytes = P->slot_bytes[q];
   a.counter = P->d_scratch + (q * KIND_COUNT + kind);
   a.status = P->d_scratch + kNumPrec * KIND_COUNT;
   const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
@@ -357,6 +361,7 @@ sht_status sht::prepared_sweep(sht_plan_t P, sht_precision prec, int dir, const 
   a.status = nullptr;
   a.num_vecs = P->num_vecs[q];
   a.staged = P->staged[q] ? 1 : 0;
+  a.slot_bytes = P->slot_bytes[q];
   L->prec = q;
   L->consumer_warps = P->consumer_warps[q];
   L->grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
@@ -387,6 +392,7 @@ sht_status sht::stream_view(sht_plan_t P, sht_precision prec, int dir, StreamVie
   v->num_sms = P->num_sms;
   v->values_apart = P->H.values_apart[q];
   v->consumer_warps = P->consumer_warps[q];
+  v->slot_bytes = P->H.values_apart[q] ? P->H.slot_values * (q == sht::PREC_FP32 ? 4 : 8) : 0;
   v->prescale = P->d_inv_w;
   return SHT_OK;
 }
@@ -422,6 +428,7 @@ sht_status sht_plan_opts_default(sht_plan_opts* o) {
   o->consumer_warps = 0;
   o->values_inline = 0;
   o->debug_unmet_dependency = 0;
+  o->slot_values = 0;
   return SHT_OK;
 }
 
@@ -444,7 +451,11 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   if (o.leaf_cols < 2 || o.leaf_cols > 1024) return SHT_ERR_INVALID_ARG;
   if (o.page_bytes < 4096 || o.page_bytes > 49152 || (o.page_bytes % 1024) != 0) return SHT_ERR_INVALID_ARG;
   if (o.num_threads < 0) return SHT_ERR_INVALID_ARG;
-  if (o.consumer_warps != 0 && o.consumer_warps != 8 && o.consumer_warps != 16) return SHT_ERR_INVALID_ARG;
+  if (o.consumer_warps != 0 && o.consumer_warps != 8 && o.consumer_warps != 12 && o.consumer_warps != 16)
+    return SHT_ERR_INVALID_ARG;
+  if (o.slot_values != 0 && (o.slot_values < sht::kMinSlotValues || o.slot_values > sht::kMaxSlotValues ||
+                             o.slot_values % 32 != 0))
+    return SHT_ERR_INVALID_ARG;
 
   sht_plan_t P = new (std::nothrow) sht_plan_s();
   if (!P) return SHT_ERR_OOM;
@@ -465,6 +476,7 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   H.page_bytes = o.page_bytes;
   for (int q = 0; q < 3; ++q) H.values_apart[q] = (o.values_inline == 0);
   H.debug_unmet_dep = o.debug_unmet_dependency != 0;
+  H.slot_values = o.slot_values ? o.slot_values : sht::kDefaultSlotValues;
 
   if (!P->host_only) {
     int dev = 0, count = 0;

@@ -40,6 +40,7 @@ struct SweepArgs {
   unsigned long long* trace;   // kTraceSlots cycle counters accumulated over all CTAs, or nullptr
   int num_vecs;                // shared vectors (2, or 4 with interleaved parities)
   int staged;                  // 1: each consumer warp stages op values in two shared slots
+  int slot_bytes;              // bytes of one staging slot (staged launches)
   // Batched launches (fields != nullptr): units[u].m is the item's field f;
   // pages, values, l, prescale and twiddle come from fields[f], the field's
   // input and output from field_in[f] and field_out[f] (device arrays).
@@ -57,6 +58,7 @@ struct SweepConfig {
   int ctas_per_sm = 0;
   size_t smem = 0;
   bool staged = false;
+  int slot_bytes = 0;
 };
 
 // Trace slots (clock64 cycles summed over CTAs): consumer warps executing ops,
@@ -75,12 +77,13 @@ enum TraceSlot {
 
 enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2 };
 
-size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, bool staged);
+size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes);
 // Picks the ring depth (nstages > 0: exactly that depth) for the given warps:
 // two resident CTAs per SM with at least three pages in flight each if they
-// fit, else one CTA with the deepest ring that fits in optin bytes.  False
-// if nothing fits.
-bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, bool want_staged, int nstages,
+// fit, else one CTA with the deepest ring that fits in optin bytes.  Values
+// are staged in two slots of slot_bytes per warp (0: values inline) when the
+// slots fit beside a ring of two pages.  False if nothing fits.
+bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes, int nstages,
                   size_t optin, SweepConfig* c);
 cudaError_t sweep_configure(int prec, size_t smem);
 // resident CTAs per SM for this shared-memory size (>= 1); nw = consumer warps (8 or 16)

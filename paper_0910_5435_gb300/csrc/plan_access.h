@@ -14,6 +14,7 @@ struct PreparedSweep {
   SweepArgs args;   // counter, status and trace left null for the caller to set
   int prec = 0;     // SweepPrec
   int consumer_warps = 8;
+  int slot_bytes = 0;                // staging slot per op (0: values in the pages)
   int grid = 1;
   size_t smem = 0;
   int device = 0;
@@ -41,6 +42,7 @@ struct StreamView {
   int num_sms = 0;
   bool values_apart = true;
   int consumer_warps = 8;
+  int slot_bytes = 0;                // staging slot per op (0: values in the pages)
   const double* prescale = nullptr;  // 1 / w_{l+i} (adjoint fold)
 };
 

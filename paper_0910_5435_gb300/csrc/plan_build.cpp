@@ -645,6 +645,7 @@ struct Emitter {
   Tracker* T = nullptr;
   std::vector<uint8_t>* values = nullptr;  // value region of the item, or nullptr: values inline
   bool plant_unmet = false;  // next compute op waits for itself (failure-detection tests)
+  int slot_values = kDefaultSlotValues;  // cap on an op's values kept apart
   int next_op = 0;    // number of the next op within the item
   int seg_start = 0;  // first op of the current segment (after its JOIN)
   int positions = 0;
@@ -663,10 +664,10 @@ struct Emitter {
   // Page bytes of an op with nidx index entries and nval values, leaving room
   // for the largest predecessor list (the actual list may be shorter).  With
   // values kept apart the page holds only the header and indices, and the
-  // value block must fit one warp's staging slot (value_slot_vals values).
+  // value block must fit one warp's staging slot (slot_values values).
   size_t bytes_of(size_t nidx, size_t nval) const {
     const size_t meta = sizeof(OpHdr) + pad16(2 * (nidx + kMaxPred));
-    if (values) return nval <= (size_t)value_slot_vals(prec) ? meta : ~size_t(0) / 2;
+    if (values) return nval <= (size_t)slot_values ? meta : ~size_t(0) / 2;
     return meta + pad16(vs * nval);
   }
 
@@ -1239,6 +1240,7 @@ void emit_streams(PlanHost& P, int prec) {
       E.l = P.l;
       E.values = apart ? &vals : nullptr;
       E.plant_unmet = P.debug_unmet_dep && std::find(ms.begin(), ms.end(), 0) != ms.end();
+      E.slot_values = P.slot_values;
       E.open_item(positions);
       for (int m : ms) emit_unit(P, prec, dir, m, E);
       return E.next_op;

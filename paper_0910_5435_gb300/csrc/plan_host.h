@@ -73,6 +73,7 @@ struct PlanHost {
   int l = 0;
   double eps_id = 0, eps_fp32 = 0, trim_eps = 0;
   int leaf_cols = 64, min_band_rows = 32, num_threads = 0, page_bytes = 8192;
+  int slot_values = kDefaultSlotValues;  // cap on the values of one op kept apart
   bool interleave_parities = false;
   bool values_apart[3] = {true, true, true};  // per precision: value blocks outside the pages
   bool debug_unmet_dep = false;  // plant a never-met predecessor (failure-detection tests)

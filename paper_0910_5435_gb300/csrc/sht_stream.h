@@ -129,10 +129,12 @@ constexpr int kMaxM = 32;             // outputs per compute op (one warp)
 constexpr int kMaxPred = 16;          // predecessors listed by a data op (more: fan-in JOIN)
 constexpr int kDoneWindow = 4096;     // completion-tag ring; a segment (ops after an item-start JOIN) holds < kMaxItemOps ops
 constexpr int kMaxItemOps = 3584;
-// F_VALUES_APART: values of one op, which fill one warp's staging slot
-// (prec: 0 float64, 1 float32, 2 split float32).  Smaller slots would let
-// more warps fit, but split the blocks into more ops with more fan-in joins.
-constexpr int value_slot_vals(int prec) { return prec >= 0 ? 1024 : 0; }
+// F_VALUES_APART: default cap on the values of one op, which fill one warp's
+// staging slot (a plan option).  Smaller slots let more warps fit in shared
+// memory but split the blocks into more ops.
+constexpr int kDefaultSlotValues = 1024;
+constexpr int kMinSlotValues = 128;
+constexpr int kMaxSlotValues = 2048;
 constexpr int kConsumerWarps = 8;
 constexpr int kCtlPieces = 8;         // control ops are split into up to this many warp tasks
 constexpr uint16_t kQuitPage = 0xFFFF;  // op count of the stream's final page

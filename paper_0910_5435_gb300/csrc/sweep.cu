@@ -104,7 +104,6 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, uns
 
 // float64 factors and arithmetic; complex128 I/O.
 struct TF64 {
-  static constexpr int kSlotVals = value_slot_vals(0);
   using V = double;
   using C = double2;
   using IO = double2;
@@ -150,7 +149,6 @@ struct TF64 {
 // dropped); sums use Knuth's TwoSum.  The _rn intrinsics keep the compiler
 // from contracting the error-free transformations.
 struct TS32 {
-  static constexpr int kSlotVals = value_slot_vals(2);
   using V = float2;  // {hi, lo}
   using C = float4;  // {re_hi, re_lo, im_hi, im_lo}
   using IO = double2;
@@ -223,7 +221,6 @@ struct TS32 {
 
 // float32 factors and arithmetic; complex64 I/O.
 struct TF32 {
-  static constexpr int kSlotVals = value_slot_vals(1);
   using V = float;
   using C = float2;
   using IO = float2;
@@ -729,7 +726,7 @@ template <class TR>
 __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* empty, Sched* S,
                               const Vecs<TR>& V, int lane, uint8_t* my_slots, uint64_t* my_bars) {
   using Val = typename TR::V;
-  constexpr int kSlotBytes = TR::kSlotVals * (int)sizeof(Val);
+  const int kSlotBytes = A.slot_bytes;
   const size_t PB = (size_t)A.page_bytes;
   unsigned long long c_exec = 0, c_ready = 0, c_dep = 0, c_val = 0, n_ops = 0;
   unsigned long long c_gemv = 0, c_ctl = 0, c_done = 0, n_gemv = 0, n_ctl = 0;
@@ -917,27 +914,27 @@ __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const Swe
   } else if (warp == NW + 1) {
     parser_loop(A, stages, full, empty, S, lane);
   } else {
-    consumer_loop<TR>(A, stages, empty, S, V, lane, slots ? slots + (size_t)warp * 2 * TR::kSlotVals * sizeof(typename TR::V) : nullptr,
+    consumer_loop<TR>(A, stages, empty, S, V, lane, slots ? slots + (size_t)warp * 2 * A.slot_bytes : nullptr,
                       slot_bars + 2 * warp);
   }
 }
 
 template <class TR>
-size_t smem_for(int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, bool staged) {
+size_t smem_for(int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes) {
   const size_t vec_off =
       ((size_t)nstages * page_bytes + 16 * (size_t)nstages + 16 * (size_t)nw + sizeof(Sched) + 127) & ~size_t(127);
   size_t end = vec_off + sizeof(typename TR::C) * (size_t)num_vecs * (size_t)buf_ab;
-  if (staged) end = ((end + 127) & ~size_t(127)) + (size_t)nw * 2 * TR::kSlotVals * sizeof(typename TR::V);
+  if (slot_bytes > 0) end = ((end + 127) & ~size_t(127)) + (size_t)nw * 2 * slot_bytes;
   return end;
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, bool staged) {
+size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes) {
   switch (prec) {
-    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab, num_vecs, nw, staged);
-    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab, num_vecs, nw, staged);
-    default: return smem_for<TS32>(page_bytes, nstages, buf_ab, num_vecs, nw, staged);
+    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
+    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
+    default: return smem_for<TS32>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
   }
 }
 
@@ -946,8 +943,11 @@ namespace {
 // Host dispatch over (precision, consumer warps).
 template <class TR>
 const void* kernel_ptr(int nw) {
-  return nw == 8 ? reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 8>)
-                 : reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 16>);
+  switch (nw) {
+    case 8: return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 8>);
+    case 12: return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 12>);
+    default: return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 16>);
+  }
 }
 const void* kernel_for(int prec, int nw) {
   switch (prec) {
@@ -960,7 +960,7 @@ const void* kernel_for(int prec, int nw) {
 }  // namespace
 
 cudaError_t sweep_configure(int prec, size_t smem) {
-  for (int nw : {8, 16}) {
+  for (int nw : {8, 12, 16}) {
     cudaError_t e = cudaFuncSetAttribute(kernel_for(prec, nw), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -974,16 +974,17 @@ int sweep_blocks_per_sm(int prec, int nw, size_t smem) {
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
-bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, bool want_staged, int nstages,
+bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes, int nstages,
                   size_t optin, SweepConfig* c) {
   c->nw = nw;
   // staged values need their slots next to a ring of at least two pages
-  c->staged = want_staged && sweep_smem_bytes(prec, page_bytes, 2, buf_ab, num_vecs, nw, true) <= optin;
+  c->staged = slot_bytes > 0 && sweep_smem_bytes(prec, page_bytes, 2, buf_ab, num_vecs, nw, slot_bytes) <= optin;
+  c->slot_bytes = c->staged ? slot_bytes : 0;
   c->nstages = 0;
   c->ctas_per_sm = 0;
   c->smem = 0;
   for (int nst = (nstages > 0 ? nstages : 8); nst >= (nstages > 0 ? nstages : 2); --nst) {
-    const size_t sm = sweep_smem_bytes(prec, page_bytes, nst, buf_ab, num_vecs, nw, c->staged);
+    const size_t sm = sweep_smem_bytes(prec, page_bytes, nst, buf_ab, num_vecs, nw, c->slot_bytes);
     if (sm > optin) continue;
     const int ctas = std::min(2, sweep_blocks_per_sm(prec, nw, sm));
     const bool better = (ctas > c->ctas_per_sm && (nst >= 3 || c->ctas_per_sm == 0)) || c->ctas_per_sm == 0;
@@ -998,7 +999,7 @@ bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, bo
 
 cudaError_t sweep_launch(int prec, int nw, const SweepArgs& a, int grid, size_t smem, cudaStream_t st) {
   if (a.nstages < 1 || a.nstages > kMaxStages) return cudaErrorInvalidValue;
-  if (nw != 8 && nw != 16) return cudaErrorInvalidValue;
+  if (nw != 8 && nw != 12 && nw != 16) return cudaErrorInvalidValue;
   void* args[] = {const_cast<SweepArgs*>(&a)};
   return cudaLaunchKernel(kernel_for(prec, nw), dim3(grid), dim3((nw + 2) * 32), args, smem, st);
 }

@@ -60,6 +60,7 @@ class sht_plan_opts(ctypes.Structure):
         ("consumer_warps", ctypes.c_int),
         ("values_inline", ctypes.c_int),
         ("debug_unmet_dependency", ctypes.c_int),
+        ("slot_values", ctypes.c_int),
     ]
 
 
@@ -184,7 +185,7 @@ class Plan:
 
     def __init__(self, l, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, host_only=False,
                  num_threads=0, page_bytes=0, eps_fp32=0.0, consumer_warps=0, values_inline=0,
-                 debug_unmet_dependency=0):
+                 debug_unmet_dependency=0, slot_values=0):
         L = lib()
         opts = sht_plan_opts()
         _check(L.sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
@@ -198,6 +199,7 @@ class Plan:
         opts.consumer_warps = consumer_warps
         opts.values_inline = values_inline
         opts.debug_unmet_dependency = debug_unmet_dependency
+        opts.slot_values = slot_values
         h = ctypes.c_void_p()
         _check(L.sht_plan_create_ex(int(l), float(eps_id), ctypes.byref(opts), ctypes.byref(h)),
                "sht_plan_create_ex")
