@@ -104,6 +104,9 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, uns
 
 // float64 factors and arithmetic; complex128 I/O.
 struct TF64 {
+  // one accumulation chain: a full-warp DFMA holds the scheduler's FP64 pipe
+  // longer than its latency, so a second chain only adds merge work
+  static constexpr int kChains = 1;
   using V = double;
   using C = double2;
   using IO = double2;
@@ -149,6 +152,7 @@ struct TF64 {
 // dropped); sums use Knuth's TwoSum.  The _rn intrinsics keep the compiler
 // from contracting the error-free transformations.
 struct TS32 {
+  static constexpr int kChains = 2;
   using V = float2;  // {hi, lo}
   using C = float4;  // {re_hi, re_lo, im_hi, im_lo}
   using IO = double2;
@@ -221,6 +225,7 @@ struct TS32 {
 
 // float32 factors and arithmetic; complex64 I/O.
 struct TF32 {
+  static constexpr int kChains = 2;
   using V = float;
   using C = float2;
   using IO = float2;
@@ -374,9 +379,11 @@ __device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, 
   using V = typename TR::V;
   using Acc = typename TR::Acc;
   constexpr int U = GLOBAL ? 8 : 4;
-  // two chains per lane: with two or more warps per scheduler that hides the
-  // FMA latency, and each extra chain costs a merge per op
-  Acc a[2] = {TR::zero(), TR::zero()};
+  // TR::kChains accumulation chains per lane; each extra chain costs a merge
+  constexpr int NC = TR::kChains;
+  Acc a[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) a[c] = TR::zero();
   int s = q;
   for (; s + (U - 1) * ks < K; s += U * ks) {
     V v[U];
@@ -385,13 +392,18 @@ __device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int su = s + u * ks;
-      TR::fma(a[u & 1], v[u], in[gather ? (int)idx[su] : su]);
+      TR::fma(a[u % NC], v[u], in[gather ? (int)idx[su] : su]);
     }
   }
   for (; s < K; s += ks) TR::fma(a[0], ldv<GLOBAL>(val + (size_t)s * M + o), in[gather ? (int)idx[s] : s]);
-  TR::merge(a[0], a[1]);
+#pragma unroll
+  for (int c = 1; c < NC; ++c) TR::merge(a[0], a[c]);
   return a[0];
 }
+
+// floor(32 / M) for M = 0..32, and ceil(65536 / d) for d = 0..32.
+__constant__ unsigned char c_lanes_per_out[33] = {0, 32, 16, 10, 8, 6, 5, 4, 4, 3, 3, 2, 2, 2, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+__constant__ unsigned c_inv16[33] = {0, 65536, 32768, 21846, 16384, 13108, 10923, 9363, 8192, 7282, 6554, 5958, 5462, 5042, 4682, 4370, 4096, 3856, 3641, 3450, 3277, 3121, 2979, 2850, 2731, 2622, 2521, 2428, 2341, 2260, 2185, 2115, 2048};
 
 // What an op needs of its field: the launch's own arguments, or one field
 // of a batched launch.
@@ -431,9 +443,11 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
   const bool accum = (h.flags & F_ACCUM) != 0;
   if (M > 0) {
     // ks = floor(32 / M) lanes per output (not only powers of two, so that
-    // up to 32 - ks + 1 lanes work); lane = o * ks + q
-    const int ks = 32 / M;
-    const int o = lane / ks, q = lane - o * ks;
+    // up to 32 - ks + 1 lanes work); lane = o * ks + q.  Both divisions come
+    // from a table: lane / ks = (lane * ceil(2^16 / ks)) >> 16 holds exactly
+    // for lane < 32 and ks <= 32.
+    const int ks = c_lanes_per_out[M];
+    const int o = (lane * c_inv16[ks]) >> 16, q = lane - o * ks;
     Acc a0 = TR::zero();
     if (o < M)
       a0 = from_global ? gemv_dot<TR, true>(val, in, idx, gather, M, K, o, q, ks)
@@ -730,6 +744,7 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
   const size_t PB = (size_t)A.page_bytes;
   unsigned long long c_exec = 0, c_ready = 0, c_dep = 0, c_val = 0, n_ops = 0;
   unsigned long long c_gemv = 0, c_ctl = 0, c_done = 0, n_gemv = 0, n_ctl = 0;
+  const bool tracing = A.trace != nullptr;  // cycle counts only while tracing
   uint32_t slot_phase = 0u;  // bit s: parity of slot s's next completion
   uint32_t inflight = 0u;    // bit s: a copy into slot s has not been waited for
   int next_slot = 0;
@@ -794,7 +809,7 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
     const int tn = claim_number();
     int rn = open(tn, nxt, false);  // the next op's values travel while this one runs
     if (rn < 0) break;
-    const long long t1 = clock64();
+    const long long t1 = tracing ? clock64() : 0;
     bool ok;
     if (cur.h.kind == OP_JOIN && (cur.h.flags & F_ITEM_START)) {
       // a work item starts once every earlier op of this CTA has completed
@@ -812,7 +827,7 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
       }
     }
     if (!ok) break;
-    const long long t2 = clock64();
+    const long long t2 = tracing ? clock64() : 0;
     const uint8_t* staged = nullptr;
     if (cur.slot >= 0) {
       uint64_t* bar = my_bars + cur.slot;
@@ -823,19 +838,21 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
       inflight &= ~(1u << cur.slot);
       staged = my_slots + (size_t)cur.slot * kSlotBytes;
     }
-    const long long t3 = clock64();
+    const long long t3 = tracing ? clock64() : 0;
     const bool is_gemv = cur.h.kind >= OP_SYN_INTERP && cur.h.kind <= OP_ANA_INTERP;
     if (is_gemv)
       run_gemv<TR>(cur.h, cur.op, V, field_ctx(A, cur.field), lane, staged);
     else if (cur.h.kind != OP_JOIN)
       run_control<TR>(cur.h, V, field_ctx(A, cur.field), lane);
-    const long long t3b = clock64();
-    if (is_gemv) {
-      c_gemv += t3b - t3;
-      ++n_gemv;
-    } else {
-      c_ctl += t3b - t3;
-      ++n_ctl;
+    const long long t3b = tracing ? clock64() : 0;
+    if (tracing) {
+      if (is_gemv) {
+        c_gemv += t3b - t3;
+        ++n_gemv;
+      } else {
+        c_ctl += t3b - t3;
+        ++n_ctl;
+      }
     }
     __threadfence_block();  // this op's results are visible before it is marked done
     __syncwarp();
@@ -844,12 +861,14 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
       atomicAdd(&S->n_done, 1);
       if (atomicSub(&S->pending[cur.stage], 1) == 1) mbar_arrive(empty + cur.stage);
     }
-    const long long t4 = clock64();
-    c_done += t4 - t3b;
-    c_dep += t2 - t1;
-    c_val += t3 - t2;
-    c_exec += t4 - t3;
-    ++n_ops;
+    const long long t4 = tracing ? clock64() : 0;
+    if (tracing) {
+      c_done += t4 - t3b;
+      c_dep += t2 - t1;
+      c_val += t3 - t2;
+      c_exec += t4 - t3;
+      ++n_ops;
+    }
     if (rn == 2) rn = open(tn, nxt, true);  // holds nothing now
     if (rn != 1) break;
     cur = nxt;
