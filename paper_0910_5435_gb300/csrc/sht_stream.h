@@ -126,7 +126,7 @@ static_assert(sizeof(UnitEntry) == 16, "UnitEntry must be 16 bytes");
 constexpr int kNumVecs = 4;
 
 constexpr int kMaxM = 32;             // outputs per compute op (one warp)
-constexpr int kMaxPred = 16;          // predecessors listed by a data op (more: fan-in JOIN)
+constexpr int kMaxPred = 32;          // predecessors listed by a data op (more: fan-in JOIN); one warp checks 32 at once
 constexpr int kDoneWindow = 4096;     // completion-tag ring; a segment (ops after an item-start JOIN) holds < kMaxItemOps ops
 constexpr int kMaxItemOps = 3584;
 // F_VALUES_APART: default cap on the values of one op, which fill one warp's
