@@ -57,11 +57,11 @@ def parse():
 
 # DRAM traffic of one float64 sweep launch at l = 1024 (leaf_cols 32, 8 KB
 # pages), dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu
-# capture, mean of a synthesis (6.527 GB) and an analysis (6.404 GB) launch
+# capture, mean of a synthesis (6.517 GB) and an analysis (6.404 GB) launch
 # (profiles/bfly_sweep_fp64_l1024_dram.md).  Valid only for the kernel and
 # stream-format sources it was taken with: SWEEP_SOURCES_SHA is their hash.
-SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4655e9}
-SWEEP_SOURCES_SHA = "08abd26f3a2f2210"
+SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4605e9}
+SWEEP_SOURCES_SHA = "ee2c915dba5fa52b"
 
 
 def sweep_sources_sha():

@@ -187,3 +187,32 @@ def test_both_value_layouts_on_gpu(sht, values_inline, prec):
     Gin = inputs.random_G(l, seed=32)
     b = run_analysis(sht, P, prec, Gin)
     assert rel(b, oracle.legendre_analysis(Gin, l)) < TOL[prec]
+
+
+def test_l1024_bench_configuration_sampled_orders(sht):
+    """Full-size parity at the benchmarked configuration: l = 1024, eps_id =
+    1e-12, leaf_cols 32, 8 KB pages, default warps, beta ~ N(0,1)/(k+1) with
+    seed 3 (the bench's field), all three precisions, both directions, on
+    orders the oracle computes one by one (the first, the last, both parities
+    of the middle, and orders near the turning point of the nodes)."""
+    l = 1024
+    P = sht.Plan(l, 1e-12, leaf_cols=32, page_bytes=8192)
+    beta = inputs.random_beta(l, seed=3, decay=True)
+    Gin = inputs.random_G(l, seed=4)
+    ms = [0, 1, 2, 511, 1024, 1025, 1500, 2046, 2047]
+    Go = oracle.legendre_synthesis(beta, l, orders=ms)
+    bo = oracle.legendre_analysis(Gin, l, orders=ms)
+    ba = oracle.legendre_adjoint(Gin, l, orders=ms)
+    off = oracle.triangle_offsets(l)
+    sel = np.concatenate([np.arange(off[m], off[m + 1]) for m in ms])
+    for prec in (0, 2, 1):
+        P.prepare(prec)
+        G = run_synth(sht, P, prec, beta)
+        assert rel(G[ms], Go[ms]) < TOL[prec], prec
+        assert not np.isnan(G).any()
+        b = run_analysis(sht, P, prec, Gin)
+        assert rel(b[sel], bo[sel]) < TOL[prec], prec
+        assert not np.isnan(b).any()
+        b = run_analysis(sht, P, prec, Gin, adjoint=True)
+        assert rel(b[sel], ba[sel]) < TOL[prec], prec
+    P.close()
