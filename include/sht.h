@@ -298,6 +298,43 @@ sht_status sht_direct_prepare(sht_plan_t plan);
 sht_status sht_direct_synthesize(sht_plan_t plan, const void* beta, void* G, sht_stream_t stream);
 sht_status sht_direct_analyze(sht_plan_t plan, const void* G, void* beta, sht_stream_t stream);
 
+/* ---------------------------------------------------- one block, any size */
+
+/* Largest bandlimit sht_unit_stats_compute accepts. */
+#define SHT_UNIT_STATS_MAX_L 20000
+
+typedef struct {
+  int l, m, parity;
+  int n;                 /* columns n_{m,p} */
+  int rows_kept;         /* rows after trimming */
+  int levels;            /* merge levels */
+  int n_blocks;          /* IDs in the butterfly */
+  int k_max;             /* Section 5 tables: k_max */
+  double k_avg;          /* k_avg */
+  double k_sigma;        /* k_sigma (population standard deviation) */
+  double max_abs_T;      /* largest |entry| of an interpolation matrix */
+  long long factor_values, dense_values;
+  long long m_max_words; /* Section 5 tables: m_max, peak float64 words of the build */
+  double t_quad, t_comp; /* seconds: nodes and weights; the depth-first build */
+  double eps_fwd;        /* max |A beta (butterfly) - A beta (direct)|, beta unit-norm U(-1,1) */
+  double eps_inv;        /* max |A^T mu (butterfly) - A^T mu (direct)|, mu unit-norm U(-1,1) */
+  int direct;            /* 1 if the block is stored dense (compression did not pay) */
+} sht_unit_stats;
+
+/* Builds, on the host only, the butterfly of the single parity block
+ * A^{m,parity}_{ij} = sqrt(2 w_{l+i}) P-bar^m_{m+parity+2j}(x_{l+i}) (the
+ * weighted Gauss-Legendre block of a plan with bandlimit l, Section 4) with
+ * threshold eps_id and the leaf width, trimming and band options of opts
+ * (NULL: defaults), 1 <= l <= SHT_UNIT_STATS_MAX_L.  Fills *out with the
+ * rank statistics and precomputation costs the paper tabulates (Section 5,
+ * e.g. Table small_time / small_pre; at m = 0, parity 0 the block is the
+ * matrix of the paper's even-degree transform with n = l) and the max-abs
+ * errors of the butterfly and of its transpose against the direct products
+ * on unit-norm vectors with entries uniform in (-1, 1) (seeded SplitMix64).
+ * No CUDA calls; allocates host memory only for the duration of the call. */
+sht_status sht_unit_stats_compute(int l, int m, int parity, double eps_id, const sht_plan_opts* opts,
+                                  unsigned long long seed, sht_unit_stats* out);
+
 /* ------------------------------------------------------------ many fields */
 
 /* The paper transforms one function at a time.  A batch runs the Legendre

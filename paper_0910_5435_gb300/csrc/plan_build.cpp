@@ -507,6 +507,8 @@ UnitFact factor_unit(const PlanHost& P, int m, int p, double eps) {
 
 }  // namespace
 
+UnitFact factor_single_unit(const PlanHost& P, int m, int p, double eps) { return factor_unit(P, m, p, eps); }
+
 void build_factorizations(PlanHost& P, bool fp32) {
   const int l = P.l, L = 2 * l;
   const double eps = fp32 ? P.eps_fp32 : P.eps_id;

@@ -115,6 +115,10 @@ class ColumnStream {
 int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm,
                   std::vector<double>& T);
 
+// Factorization of the one parity block (m, p) with threshold eps (Section 3,
+// depth-first); P needs only l, the nodes and the build options.
+UnitFact factor_single_unit(const PlanHost& P, int m, int p, double eps);
+
 // Builds the factorization of every parity block with threshold eps
 // (Section 3, depth-first).  fp32 selects fact32 instead of fact64.
 void build_factorizations(PlanHost& P, bool fp32);

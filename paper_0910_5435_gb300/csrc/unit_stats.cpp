@@ -1,0 +1,214 @@
+// unit_stats.cpp -- rank statistics and accuracy of the butterfly of ONE
+// parity block, at bandlimits beyond what a whole plan holds.
+//
+// For m = 0 and p = 0 the block A_{ij} = sqrt(2 w_{l+i}) P-bar^0_{2j}(x_{l+i})
+// (i, j < l) is the matrix of the paper's even-degree transform with n = l
+// (Section 4, eqs. transform / evens with the Gauss-Legendre nodes; its
+// rho_i equal 2 w_{l+i}), so its ID ranks and errors can be set beside the
+// paper's Table small_time / small_pre.  Host only, float64.
+//
+// The factorization is applied on the host exactly as the butterfly defines
+// it (Section 2.2 eqs. 1-6: y = z[skel] + T z[red] level by level, then the
+// stored skeleton columns of each row band, Section 3), and its transpose
+// for the inverse (Section 2.2, remark after Figure multi).  The direct
+// products stream the columns of A with the same x^2 recurrence, so no
+// l x n array is stored.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <exception>
+#include <new>
+#include <vector>
+
+#include "../../include/sht.h"
+#include "plan_host.h"
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): uniform doubles in (-1, 1).
+struct SplitMix64 {
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  double uniform_pm1() { return ((double)(next() >> 11) + 0.5) * (2.0 / 9007199254740992.0) - 1.0; }
+};
+
+std::vector<double> unit_vector(size_t n, uint64_t seed) {
+  SplitMix64 g{seed};
+  std::vector<double> v(n);
+  double s = 0;
+  for (double& x : v) {
+    x = g.uniform_pm1();
+    s += x * x;
+  }
+  const double inv = s > 0 ? 1.0 / std::sqrt(s) : 0.0;
+  for (double& x : v) x *= inv;
+  return v;
+}
+
+// Blocks of each level, in any order (each block reads and writes its own ranges).
+std::vector<std::vector<const sht::IdBlock*>> by_level(const sht::UnitFact& U) {
+  std::vector<std::vector<const sht::IdBlock*>> at(U.levels + 2);
+  for (const auto& b : U.blocks) at[b.level].push_back(&b);
+  return at;
+}
+
+// alpha = A beta through the factorization (alpha has l entries; trimmed rows 0).
+std::vector<double> apply_forward(const sht::UnitFact& U, int l, const std::vector<double>& beta) {
+  std::vector<double> alpha(l, 0.0);
+  if (U.direct) {
+    for (int j = 0; j < U.n; ++j)
+      for (int i = 0; i < U.rows; ++i) alpha[i] += U.D[(size_t)j * U.rows + i] * beta[j];
+    return alpha;
+  }
+  const int top = U.levels + 1;
+  const auto at = by_level(U);
+  std::vector<std::vector<double>> lay(top + 1);
+  for (int j = 1; j <= top; ++j) {
+    lay[j].assign(U.width[j], 0.0);
+    for (const sht::IdBlock* b : at[j]) {
+      const double* z = (j == 1) ? beta.data() + b->in_off : lay[j - 1].data() + b->in_off;
+      const int k = b->k;
+      for (int t = 0; t < k; ++t) {
+        double y = z[b->skel[t]];
+        for (size_t s = 0; s < b->red.size(); ++s) y += b->T[s * k + t] * z[b->red[s]];
+        lay[j][b->out_off + t] = y;
+      }
+    }
+  }
+  for (const sht::FinalBlock& f : U.finals) {
+    const int h = f.r1 - f.r0;
+    for (int i = 0; i < h; ++i) {
+      double a = 0;
+      for (int t = 0; t < f.k; ++t) a += f.S[(size_t)t * h + i] * lay[top][f.in_off + t];
+      alpha[f.r0 + i] = a;
+    }
+  }
+  return alpha;
+}
+
+// nu = A^T mu through the transposed factorization.
+std::vector<double> apply_transpose(const sht::UnitFact& U, const std::vector<double>& mu) {
+  std::vector<double> nu(U.n, 0.0);
+  if (U.direct) {
+    for (int j = 0; j < U.n; ++j)
+      for (int i = 0; i < U.rows; ++i) nu[j] += U.D[(size_t)j * U.rows + i] * mu[i];
+    return nu;
+  }
+  const int top = U.levels + 1;
+  const auto at = by_level(U);
+  std::vector<std::vector<double>> lay(top + 1);
+  for (int j = 1; j <= top; ++j) lay[j].assign(U.width[j], 0.0);
+  for (const sht::FinalBlock& f : U.finals) {
+    const int h = f.r1 - f.r0;
+    for (int t = 0; t < f.k; ++t) {
+      double y = 0;
+      for (int i = 0; i < h; ++i) y += f.S[(size_t)t * h + i] * mu[f.r0 + i];
+      lay[top][f.in_off + t] = y;
+    }
+  }
+  for (int j = top; j >= 1; --j) {
+    for (const sht::IdBlock* b : at[j]) {
+      double* z = (j == 1) ? nu.data() + b->in_off : lay[j - 1].data() + b->in_off;
+      const int k = b->k;
+      for (int t = 0; t < k; ++t) {
+        const double y = lay[j][b->out_off + t];
+        z[b->skel[t]] += y;
+        for (size_t s = 0; s < b->red.size(); ++s) z[b->red[s]] += b->T[s * k + t] * y;
+      }
+    }
+  }
+  return nu;
+}
+
+}  // namespace
+
+extern "C" sht_status sht_unit_stats_compute(int l, int m, int parity, double eps_id, const sht_plan_opts* opts,
+                                             unsigned long long seed, sht_unit_stats* out) {
+  if (!out || l < 1 || l > SHT_UNIT_STATS_MAX_L || m < 0 || m >= 2 * l || (parity != 0 && parity != 1) ||
+      !(eps_id > 0.0) || !(eps_id < 1.0))
+    return SHT_ERR_INVALID_ARG;
+  sht_plan_opts o;
+  if (opts) {
+    o = *opts;
+  } else {
+    sht_plan_opts_default(&o);
+  }
+  if (o.leaf_cols < 2 || o.leaf_cols > 1024) return SHT_ERR_INVALID_ARG;
+  try {
+    sht::PlanHost P;
+    P.l = l;
+    P.eps_id = eps_id;
+    P.trim_eps = o.trim_eps < 0 ? eps_id : o.trim_eps;
+    P.leaf_cols = o.leaf_cols;
+    P.min_band_rows = o.min_band_rows > 0 ? o.min_band_rows : std::max(1, o.leaf_cols / 2);
+    double t0 = now_s();
+    sht::gl_nodes(2 * l, P.x, P.w, P.theta_pos);
+    const double t_quad = now_s() - t0;
+    t0 = now_s();
+    const sht::UnitFact U = sht::factor_single_unit(P, m, parity, eps_id);
+    const double t_comp = now_s() - t0;
+
+    sht_unit_stats s{};
+    s.l = l;
+    s.m = m;
+    s.parity = parity;
+    s.n = U.n;
+    s.rows_kept = U.rows;
+    s.levels = U.levels;
+    s.direct = U.direct ? 1 : 0;
+    double sumk = 0, sumk2 = 0;
+    for (const auto& b : U.blocks) {
+      s.k_max = std::max(s.k_max, b.k);
+      sumk += b.k;
+      sumk2 += (double)b.k * b.k;
+      for (double t : b.T) s.max_abs_T = std::max(s.max_abs_T, std::fabs(t));
+    }
+    s.n_blocks = (int)U.blocks.size();
+    if (s.n_blocks) {
+      s.k_avg = sumk / s.n_blocks;
+      s.k_sigma = std::sqrt(std::max(0.0, sumk2 / s.n_blocks - s.k_avg * s.k_avg));
+    }
+    s.factor_values = U.values;
+    s.dense_values = (long long)l * U.n;
+    s.m_max_words = U.peak_words;
+    s.t_quad = t_quad;
+    s.t_comp = t_comp;
+
+    // accuracy against the direct products, unit-norm U(-1, 1) inputs
+    if (U.n > 0) {
+      const std::vector<double> beta = unit_vector(U.n, seed);
+      const std::vector<double> mu = unit_vector(l, seed + 1);
+      std::vector<double> alpha_d(l, 0.0), nu_d(U.n, 0.0), col(l);
+      sht::ColumnStream cs(P, m, parity, l);
+      for (int j = 0; j < U.n; ++j) {
+        cs.next(col.data());
+        double dot = 0;
+        for (int i = 0; i < l; ++i) {
+          alpha_d[i] += col[i] * beta[j];
+          dot += col[i] * mu[i];
+        }
+        nu_d[j] = dot;
+      }
+      const std::vector<double> alpha = apply_forward(U, l, beta);
+      const std::vector<double> nu = apply_transpose(U, mu);
+      for (int i = 0; i < l; ++i) s.eps_fwd = std::max(s.eps_fwd, std::fabs(alpha[i] - alpha_d[i]));
+      for (int j = 0; j < U.n; ++j) s.eps_inv = std::max(s.eps_inv, std::fabs(nu[j] - nu_d[j]));
+    }
+    *out = s;
+  } catch (const std::bad_alloc&) {
+    return SHT_ERR_OOM;
+  } catch (...) {
+    return SHT_ERR_INVALID_ARG;
+  }
+  return SHT_OK;
+}

@@ -34,6 +34,7 @@ EXPORTS = [
     "sht_last_error_detail", "sht_trace_enable", "sht_trace_read", "sht_legendre_synthesize_noalloc",
     "sht_batch_create", "sht_batch_destroy", "sht_batch_synthesize", "sht_batch_analyze",
     "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config", "sht_batch_synthesize_adjoint",
+    "sht_unit_stats_compute",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -138,6 +139,7 @@ def lib():
     L.sht_trace_enable.argtypes = [vp, c_int]
     L.sht_trace_read.argtypes = [vp, vp, c_int]
     L.sht_legendre_synthesize_noalloc.argtypes = [vp, c_int, vp, vp, c_int, vp, vp]
+    L.sht_unit_stats_compute.argtypes = [c_int, c_int, c_int, ctypes.c_double, vp, ctypes.c_ulonglong, vp]
     L.sht_batch_create.argtypes = [c_int, vp, c_int, vp]
     L.sht_batch_destroy.argtypes = [vp]
     L.sht_batch_synthesize.argtypes = [vp, vp, vp, vp]
@@ -288,6 +290,34 @@ def sht_legendre_synthesize_noalloc(plan, prec, beta, G, slot=0, status=None, st
     _check(lib().sht_legendre_synthesize_noalloc(plan.handle, int(prec), _ptr(beta), _ptr(G), int(slot),
                                                  _ptr(status) if status is not None else None,
                                                  _stream(stream)), "sht_legendre_synthesize_noalloc")
+
+
+class sht_unit_stats(ctypes.Structure):
+    _fields_ = [
+        ("l", ctypes.c_int), ("m", ctypes.c_int), ("parity", ctypes.c_int), ("n", ctypes.c_int),
+        ("rows_kept", ctypes.c_int), ("levels", ctypes.c_int), ("n_blocks", ctypes.c_int), ("k_max", ctypes.c_int),
+        ("k_avg", ctypes.c_double), ("k_sigma", ctypes.c_double), ("max_abs_T", ctypes.c_double),
+        ("factor_values", ctypes.c_longlong), ("dense_values", ctypes.c_longlong), ("m_max_words", ctypes.c_longlong),
+        ("t_quad", ctypes.c_double), ("t_comp", ctypes.c_double), ("eps_fwd", ctypes.c_double),
+        ("eps_inv", ctypes.c_double), ("direct", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def unit_stats(l, m=0, parity=0, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, seed=1):
+    """Rank statistics, costs and errors of one parity block's butterfly
+    (``sht_unit_stats_compute``; host only, any l up to 20000)."""
+    opts = sht_plan_opts()
+    _check(lib().sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
+    opts.leaf_cols = leaf_cols
+    opts.trim_eps = trim_eps
+    opts.min_band_rows = min_band_rows
+    out = sht_unit_stats()
+    _check(lib().sht_unit_stats_compute(int(l), int(m), int(parity), float(eps_id), ctypes.byref(opts),
+                                        int(seed), ctypes.byref(out)), "sht_unit_stats_compute")
+    return out.as_dict()
 
 
 class Batch:
