@@ -45,8 +45,8 @@ def test_block_errors_within_id_precision(l, m, p):
     s = sht.unit_stats(l, m, p, eps_id=eps, leaf_cols=16)
     assert s["n"] == (2 * l - m - p + 1) // 2
     assert s["eps_fwd"] < 50 * eps and s["eps_inv"] < 50 * eps
-    # a merge block's input is its two children's skeletons: rank <= 2 C
-    assert 0 < s["k_max"] <= 2 * 16 or s["direct"] == 1
+    # an ID's rank is at most the block's smaller dimension
+    assert 0 < s["k_max"] <= min(s["n"], s["rows_kept"]) or s["direct"] == 1
 
 
 def test_tighter_threshold_raises_ranks_and_lowers_errors():
