@@ -335,6 +335,26 @@ typedef struct {
 sht_status sht_unit_stats_compute(int l, int m, int parity, double eps_id, const sht_plan_opts* opts,
                                   unsigned long long seed, sht_unit_stats* out);
 
+/* The paper's own quadrature (Section 4, Lemmas zeros and quadratures): the
+ * n positive zeros x[0..n) (ascending) of P-bar^m_{m+parity+2n} and their
+ * weights rho[0..n) (for parity 1 the sigma_j of eq. weights2), such that
+ * sqrt(rho_i) P-bar^m_{m+parity+2j}(x_i), i, j < n, is orthogonal.
+ * Computed as the eigenvalues in x^2 of the Jacobi matrix of the x^2
+ * recurrence (eqs. c_rec, d_rec, recurrence0, recurrence) by Sturm-sequence
+ * bisection, refined by Newton steps on the recurrence; the weights from
+ * the orthonormality of the rows.  Host only; x and rho are host arrays of
+ * n doubles (1 <= n <= SHT_UNIT_STATS_MAX_L). */
+sht_status sht_gauss_jacobi_nodes(int m, int parity, int n, double* x, double* rho);
+
+/* As sht_unit_stats_compute, for the paper's n x n matrix of eq. transform
+ * (parity 0: sqrt(rho_i) P-bar^m_{m+2j}(x_i)) or eq. transform2 (parity 1:
+ * sqrt(sigma_i) P-bar^m_{m+2j+1}(y_i)) at the nodes of
+ * sht_gauss_jacobi_nodes: the matrices of the paper's Tables evens and odds
+ * (m = n) and small (m = 0).  t_quad is the time for those nodes and
+ * weights. */
+sht_status sht_unit_stats_gauss_jacobi(int n, int m, int parity, double eps_id, const sht_plan_opts* opts,
+                                       unsigned long long seed, sht_unit_stats* out);
+
 /* ------------------------------------------------------------ many fields */
 
 /* The paper transforms one function at a time.  A batch runs the Legendre

@@ -103,14 +103,6 @@ void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vec
 // ------------------------------------------------------- column stream
 
 namespace {
-inline double rec_c(int k, int m) {  // eq. c_rec
-  const double a = (double)(k - m + 1) * (k - m + 2) * (double)(k + m + 1) * (k + m + 2);
-  const double b = (2.0 * k + 1.0) * (2.0 * k + 3.0) * (2.0 * k + 3.0) * (2.0 * k + 5.0);
-  return std::sqrt(a / b);
-}
-inline double rec_d(int k, int m) {  // eq. d_rec
-  return (2.0 * k * (k + 1.0) - 2.0 * (double)m * m - 1.0) / ((2.0 * k - 1.0) * (2.0 * k + 3.0));
-}
 inline void renorm(double& v, int& e) {
   if (v == 0.0) return;
   int t;
@@ -135,11 +127,12 @@ ColumnStream::ColumnStream(const PlanHost& P, int m, int p, int rows)
     cm *= std::sqrt((2.0 * j + 1.0) / (2.0 * j));
     renorm(cm, ecm);
   }
+  const bool custom = !P.row_x.empty();
   for (int i = 0; i < rows; ++i) {
-    const double xi = P.x[l + i];
-    const double s = std::sin(P.theta_pos[i]);
+    const double xi = custom ? P.row_x[i] : P.x[l + i];
+    const double s = std::sin(custom ? P.row_theta[i] : P.theta_pos[i]);
     x2_[i] = xi * xi;
-    sq2w_[i] = std::sqrt(2.0 * P.w[l + i]);
+    sq2w_[i] = custom ? P.row_sqw[i] : std::sqrt(2.0 * P.w[l + i]);
     // s^m by binary powering with tracked exponents
     int eb;
     double base = std::frexp(s, &eb);
@@ -311,7 +304,7 @@ UnitFact factor_unit(const PlanHost& P, int m, int p, double eps) {
   U.m = m;
   U.p = p;
   const int l = P.l, L = 2 * l;
-  const int n = std::max(0, (L - m - p + 1) / 2);
+  const int n = P.unit_cols > 0 ? P.unit_cols : std::max(0, (L - m - p + 1) / 2);
   U.n = n;
   if (n == 0) return U;
 

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <array>
+#include <cmath>
 #include <atomic>
 #include <memory>
 #include <string>
@@ -80,6 +81,11 @@ struct PlanHost {
   // Gauss-Legendre nodes (all 2l, ascending), weights, and the angle of each
   // positive node (theta_{l+i} in (0, pi/2)).
   std::vector<double> x, w, theta_pos;
+  // Optional rows of a single block at other nodes (the Gauss-Jacobi form of
+  // Section 4): node x_i, angle theta_i = arccos x_i and the row factor
+  // sqrt(rho_i) for i < l; unit_cols > 0 sets the column count.
+  std::vector<double> row_x, row_theta, row_sqw;
+  int unit_cols = 0;
   // factorizations: [m * 2 + p]; fp64 uses eps_id, fp32 uses eps_fp32
   std::vector<UnitFact> fact64, fact32;
   // streams: [prec][direction]; prec 0 = FP64, 1 = FP32, 2 = SPLIT32
@@ -87,6 +93,23 @@ struct PlanHost {
   bool built[3] = {false, false, false};
   double t_quad = 0, t_comp = 0;
 };
+
+// Coefficients of the x^2 recurrence x^2 P-bar^m_k = c_{k-2} P-bar^m_{k-2}
+// + d_k P-bar^m_k + c_k P-bar^m_{k+2} (Section 2.3, eqs. c_rec, d_rec).
+inline double rec_c(int k, int m) {
+  const double a = (double)(k - m + 1) * (k - m + 2) * (double)(k + m + 1) * (k + m + 2);
+  const double b = (2.0 * k + 1.0) * (2.0 * k + 3.0) * (2.0 * k + 3.0) * (2.0 * k + 5.0);
+  return std::sqrt(a / b);
+}
+inline double rec_d(int k, int m) {
+  return (2.0 * k * (k + 1.0) - 2.0 * (double)m * m - 1.0) / ((2.0 * k - 1.0) * (2.0 * k + 3.0));
+}
+
+// The n positive zeros x_i of P-bar^m_{m+p+2n} (Section 4, Lemma zeros),
+// their angles, and the weights rho_i of the Gauss-Jacobi-type quadrature
+// of Lemma quadratures (for p = 1 the sigma_i of eq. weights2, i < n).
+void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector<double>& theta,
+                        std::vector<double>& rho);
 
 // Section 2, eq. thetas: 2l Gauss-Legendre nodes/weights.
 void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& theta);

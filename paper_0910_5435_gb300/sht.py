@@ -34,7 +34,7 @@ EXPORTS = [
     "sht_last_error_detail", "sht_trace_enable", "sht_trace_read", "sht_legendre_synthesize_noalloc",
     "sht_batch_create", "sht_batch_destroy", "sht_batch_synthesize", "sht_batch_analyze",
     "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config", "sht_batch_synthesize_adjoint",
-    "sht_unit_stats_compute",
+    "sht_unit_stats_compute", "sht_gauss_jacobi_nodes", "sht_unit_stats_gauss_jacobi",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -140,6 +140,8 @@ def lib():
     L.sht_trace_read.argtypes = [vp, vp, c_int]
     L.sht_legendre_synthesize_noalloc.argtypes = [vp, c_int, vp, vp, c_int, vp, vp]
     L.sht_unit_stats_compute.argtypes = [c_int, c_int, c_int, ctypes.c_double, vp, ctypes.c_ulonglong, vp]
+    L.sht_unit_stats_gauss_jacobi.argtypes = [c_int, c_int, c_int, ctypes.c_double, vp, ctypes.c_ulonglong, vp]
+    L.sht_gauss_jacobi_nodes.argtypes = [c_int, c_int, c_int, vp, vp]
     L.sht_batch_create.argtypes = [c_int, vp, c_int, vp]
     L.sht_batch_destroy.argtypes = [vp]
     L.sht_batch_synthesize.argtypes = [vp, vp, vp, vp]
@@ -306,18 +308,31 @@ class sht_unit_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
-def unit_stats(l, m=0, parity=0, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, seed=1):
+def unit_stats(l, m=0, parity=0, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, seed=1,
+               gauss_jacobi=False):
     """Rank statistics, costs and errors of one parity block's butterfly
-    (``sht_unit_stats_compute``; host only, any l up to 20000)."""
+    (``sht_unit_stats_compute``; host only, any l up to 20000).  With
+    gauss_jacobi the block is the paper's n x n matrix at its own nodes, n = l
+    (``sht_unit_stats_gauss_jacobi``)."""
     opts = sht_plan_opts()
     _check(lib().sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
     opts.leaf_cols = leaf_cols
     opts.trim_eps = trim_eps
     opts.min_band_rows = min_band_rows
     out = sht_unit_stats()
-    _check(lib().sht_unit_stats_compute(int(l), int(m), int(parity), float(eps_id), ctypes.byref(opts),
-                                        int(seed), ctypes.byref(out)), "sht_unit_stats_compute")
+    fn = lib().sht_unit_stats_gauss_jacobi if gauss_jacobi else lib().sht_unit_stats_compute
+    _check(fn(int(l), int(m), int(parity), float(eps_id), ctypes.byref(opts), int(seed), ctypes.byref(out)),
+           "sht_unit_stats")
     return out.as_dict()
+
+
+def gauss_jacobi_nodes(m, parity, n):
+    """(x, rho): the paper's nodes and weights (``sht_gauss_jacobi_nodes``)."""
+    x = np.zeros(int(n))
+    rho = np.zeros(int(n))
+    _check(lib().sht_gauss_jacobi_nodes(int(m), int(parity), int(n), x.ctypes.data, rho.ctypes.data),
+           "sht_gauss_jacobi_nodes")
+    return x, rho
 
 
 class Batch:
