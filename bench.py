@@ -61,7 +61,7 @@ def parse():
 # (profiles/bfly_sweep_fp64_l1024_dram.md).  Valid only for the kernel and
 # stream-format sources it was taken with: SWEEP_SOURCES_SHA is their hash.
 SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4605e9}
-SWEEP_SOURCES_SHA = "ee2c915dba5fa52b"
+SWEEP_SOURCES_SHA = "7ffd6d66079d14e6"
 
 
 def sweep_sources_sha():
@@ -314,6 +314,43 @@ def batched_leg(args, sht, inputs, torch, dev, stream, plan, rank=0, world=1, di
     }
 
 
+def full_sht_leg(args, sht, inputs, torch, dev, stream, plan, beta, back):
+    """The whole transform to and from the real grid ([2l][4l-1]: the float64
+    butterfly Legendre stage with the phase fused into its unfold / fold,
+    plus the length-(4l-1) cuFFT per node), and the phi stage alone."""
+    l = args.l
+    ws = torch.empty(sht.sht_workspace_bytes(plan, sht.SHT_FP64) // 8 + 1, dtype=torch.float64, device=dev)
+    values = torch.empty((2 * l, 4 * l - 1), dtype=torch.float64, device=dev)
+    G = torch.empty((2 * l, 2 * l), dtype=torch.complex128, device=dev)
+
+    def timed(fn, steps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    steps = max(3, args.steps // 2)
+    ms_syn = timed(lambda: sht.sht_synthesize(plan, sht.SHT_FP64, beta, values, ws, stream), steps)
+    ms_ana = timed(lambda: sht.sht_analyze(plan, sht.SHT_FP64, values, back, ws, stream), steps)
+    sht.sht_legendre_synthesize(plan, sht.SHT_FP64, beta, G, stream)
+    ms_phi_syn = timed(lambda: sht.sht_phi_synthesize(plan, sht.SHT_FP64, G, values, ws, stream), steps)
+    ms_phi_ana = timed(lambda: sht.sht_phi_analyze(plan, sht.SHT_FP64, values, G, stream), steps)
+    sht.sht_synthesize(plan, sht.SHT_FP64, beta, values, ws, stream)
+    sht.sht_analyze(plan, sht.SHT_FP64, values, back, ws, stream)
+    torch.cuda.synchronize()
+    eps = float(torch.linalg.vector_norm(back - beta) / torch.linalg.vector_norm(beta))
+    return {"grid": [2 * l, 4 * l - 1], "transforms_per_s": 2.0 / ((ms_syn + ms_ana) / 1e3),
+            "ms_synthesis": ms_syn, "ms_analysis": ms_ana, "ms_phi_synthesis": ms_phi_syn,
+            "ms_phi_analysis": ms_phi_ana, "eps_inv": eps,
+            "device_status": sht.sht_last_device_status(plan, stream)}
+
+
 def autograd_leg(args, sht, inputs, torch, dev, stream):
     """Differentiable Legendre stage: l = 512, a batch of 16 fields, loss
     ||synthesize(beta) - g||^2 with g the synthesis of an independent
@@ -395,6 +432,8 @@ def main():
         if world > 1:
             dist.barrier()
 
+    pct = {}
+
     def time_path(prec, steps, warmup, b, g, bk, synth_fn=None, ana_fn=None):
         synth_fn = synth_fn or (lambda: sht.sht_legendre_synthesize(plan, prec, b, g, stream))
         ana_fn = ana_fn or (lambda: sht.sht_legendre_analyze(plan, prec, g, bk, stream))
@@ -419,6 +458,8 @@ def main():
         total = start.elapsed_time(end)
         ts = [e[0].elapsed_time(e[1]) for e in ev]
         ta = [e[1].elapsed_time(e[2]) for e in ev]
+        pct.update({"synthesis_ms_p10_p50_p90": [float(np.percentile(ts, q)) for q in (10, 50, 90)],
+                    "analysis_ms_p10_p50_p90": [float(np.percentile(ta, q)) for q in (10, 50, 90)]})
         return total, float(np.mean(ts)), float(np.mean(ta))
 
     # ---- headline: float64 butterfly
@@ -430,6 +471,7 @@ def main():
     clocks.start()
     time.sleep(0.3)
     total_ms, ms_syn, ms_ana = time_path(sht.SHT_FP64, args.steps, 0, beta, G, back)
+    step_percentiles = dict(pct)
     clk = clocks.stop()
     status = sht.sht_last_device_status(plan, stream)
     total_ms = max_over_ranks(total_ms, world, dist, dev)
@@ -525,6 +567,9 @@ def main():
         extras["direct_G"] = g.cpu().numpy()
         extras["direct_beta"] = bk.cpu().numpy()
 
+    if not args.no_extras and rank == 0:
+        extras["full_sht_fp64"] = full_sht_leg(args, sht, inputs, torch, dev, stream, plan, beta, back)
+
     if not args.no_extras and args.batch_fields > 0:
         extras["batched_split32"] = batched_leg(args, sht, inputs, torch, dev, stream, plan, rank, world, dist)
     if not args.no_extras and rank == 0:
@@ -562,7 +607,7 @@ def main():
                        "l": l, "eps_id": args.eps, "parallelism": f"replicas x{world}",
                        "l2": f"no flush: the factor stream ({st['stream_bytes_fp64'] / 1e9:.2f} GB per launch) "
                              "is far larger than L2"},
-            "ms_synthesis": ms_syn, "ms_analysis": ms_ana,
+            "ms_synthesis": ms_syn, "ms_analysis": ms_ana, "step_ms_percentiles": step_percentiles,
             "eps_inv": eps_inv64, "rel_l2_vs_oracle_sampled": rel,
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": nbytes,

@@ -891,6 +891,17 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
   }
 }
 
+// Shared-memory layout of a sweep CTA, used by the kernel and by the host
+// sizing alike: [pages: nst x pb][full, empty barriers: 2 x nst][slot
+// barriers: 2 x nw][Sched] | 128-aligned vectors | 128-aligned staging
+// slots (nw x 2 x slot_bytes).
+__host__ __device__ inline size_t sweep_vec_offset(int nst, size_t pb, int nw) {
+  return ((size_t)nst * pb + 16 * (size_t)nst + 16 * (size_t)nw + sizeof(Sched) + 127) & ~size_t(127);
+}
+__host__ __device__ inline size_t sweep_slot_offset(size_t vec_off, size_t vec_bytes) {
+  return (vec_off + vec_bytes + 127) & ~size_t(127);
+}
+
 template <class TR, int NW>
 __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const SweepArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -902,12 +913,10 @@ __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const Swe
   uint64_t* empty = full + NST;
   uint64_t* slot_bars = empty + NST;  // 2 per consumer warp
   Sched* S = reinterpret_cast<Sched*>(slot_bars + 2 * NW);
-  const size_t vec_off =
-      ((size_t)NST * PB + 16 * (size_t)NST + 16 * (size_t)NW + sizeof(Sched) + 127) & ~size_t(127);
+  const size_t vec_off = sweep_vec_offset(NST, PB, NW);
   const Vecs<TR> V{reinterpret_cast<typename TR::C*>(smem + vec_off), A.buf_ab};
-  uint8_t* slots = A.staged
-                       ? smem + ((vec_off + sizeof(typename TR::C) * (size_t)A.num_vecs * A.buf_ab + 127) & ~size_t(127))
-                       : nullptr;
+  uint8_t* slots =
+      A.staged ? smem + sweep_slot_offset(vec_off, sizeof(typename TR::C) * (size_t)A.num_vecs * A.buf_ab) : nullptr;
 
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -940,11 +949,10 @@ __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const Swe
 
 template <class TR>
 size_t smem_for(int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes) {
-  const size_t vec_off =
-      ((size_t)nstages * page_bytes + 16 * (size_t)nstages + 16 * (size_t)nw + sizeof(Sched) + 127) & ~size_t(127);
-  size_t end = vec_off + sizeof(typename TR::C) * (size_t)num_vecs * (size_t)buf_ab;
-  if (slot_bytes > 0) end = ((end + 127) & ~size_t(127)) + (size_t)nw * 2 * slot_bytes;
-  return end;
+  const size_t vec_off = sweep_vec_offset(nstages, (size_t)page_bytes, nw);
+  const size_t vec_bytes = sizeof(typename TR::C) * (size_t)num_vecs * (size_t)buf_ab;
+  if (slot_bytes <= 0) return vec_off + vec_bytes;
+  return sweep_slot_offset(vec_off, vec_bytes) + (size_t)nw * 2 * slot_bytes;
 }
 
 }  // namespace
