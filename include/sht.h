@@ -201,6 +201,11 @@ sht_status sht_plan_stream(sht_plan_t plan, sht_precision prec, int direction,
 
 /* ----------------------------------------------- Legendre stage (hot path) */
 
+/* Every launch of a plan uses one work-queue counter per (precision,
+ * direction): launches of the same plan, precision and direction must not
+ * overlap in time (use one stream per plan, or one plan per stream).
+ * Launches of different plans, precisions or directions may overlap. */
+
 /* Synthesis: G^m(x_i) = sum_{k=m}^{2l-1} beta^m_k P-bar^m_k(x_i) for all m and
  * all 2l nodes (Section 2, eq. alternate_expansion, the sums over k), through
  * the butterfly (Section 2.2) of each parity block, followed by the parity

@@ -149,3 +149,30 @@ def test_batch_bad_pointer_entry_is_reported(sht, plans):
     for l, beta, G in zip(ls, betas, Gs):
         assert rel(G, oracle.legendre_synthesis(beta.cpu().numpy(), l)) < TOL[0]
     B.close()
+
+
+def test_batch_with_degenerate_and_single_fields(sht, plans):
+    """Fields of bandlimit 1 and 2 (a handful of coefficients, dense blocks
+    only) batched with larger ones, and a batch of a single field."""
+    tiny = {l: sht.Plan(l, 1e-12, leaf_cols=4) for l in (1, 2)}
+    ls = [1, 64, 2, 4, 1, 128]
+    pl = [tiny[l] if l in tiny else plans[l] for l in ls]
+    for prec in (0, 1):
+        for p in set(pl):
+            p.prepare(prec)
+        B = sht.Batch(pl, prec)
+        betas, Gs = fields(ls, prec, 7000)
+        sht.sht_batch_synthesize(B, sht.pointer_array(betas), sht.pointer_array(Gs))
+        assert sht.sht_batch_last_device_status(B) == 0
+        for l, beta, G in zip(ls, betas, Gs):
+            assert rel(G, oracle.legendre_synthesis(beta.cpu().numpy().astype(np.complex128), l)) < TOL[prec], l
+        B.close()
+    one = sht.Batch([plans[32]], 0)
+    betas, Gs = fields([32], 0, 7100)
+    sht.sht_batch_synthesize(one, sht.pointer_array(betas), sht.pointer_array(Gs))
+    assert sht.sht_batch_last_device_status(one) == 0
+    ref = torch.empty_like(Gs[0])
+    sht.sht_legendre_synthesize(plans[32], 0, betas[0], ref)
+    torch.cuda.synchronize()
+    assert torch.equal(ref, Gs[0])
+    one.close()
