@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--page-bytes", type=int, default=8192)
     ap.add_argument("--consumer-warps", type=int, default=0)
     ap.add_argument("--eps", type=float, default=1e-12)
-    ap.add_argument("--no-extras", action="store_true", help="skip the split32/fp32/direct legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip every leg beside the float64 headline")
+    ap.add_argument("--paths", default="split32,fp32,direct,full,batched,autograd",
+                    help="comma-separated legs to run beside the headline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--batch-fields", type=int, default=96,
                     help="fields of the batched leg (bandlimits drawn from 64..1024); 0 skips it")
@@ -542,8 +544,11 @@ def main():
                              "peak_source": "measured" if hbm else "fallback"}}
 
     extras = {}
-    if not args.no_extras and rank == 0:
+    legs = set() if args.no_extras else {s.strip() for s in args.paths.split(",") if s.strip()}
+    if rank == 0:
         for name, prec, cdt in (("split32", sht.SHT_SPLIT32, torch.complex128), ("fp32", sht.SHT_FP32, torch.complex64)):
+            if name not in legs:
+                continue
             t0 = time.perf_counter()
             plan.prepare(prec)
             tprep = time.perf_counter() - t0
@@ -563,6 +568,7 @@ def main():
             }
             extras[name + "_G"] = g.to(torch.complex128).cpu().numpy()
             extras[name + "_beta"] = bk.to(torch.complex128).cpu().numpy()
+    if rank == 0 and "direct" in legs:
         # direct float64 baseline (dense operator in HBM)
         t0 = time.perf_counter()
         sht.sht_direct_prepare(plan)
@@ -581,12 +587,11 @@ def main():
         extras["direct_G"] = g.cpu().numpy()
         extras["direct_beta"] = bk.cpu().numpy()
 
-    if not args.no_extras and rank == 0:
+    if rank == 0 and "full" in legs:
         extras["full_sht_fp64"] = full_sht_leg(args, sht, inputs, torch, dev, stream, plan, beta, back)
-
-    if not args.no_extras and args.batch_fields > 0:
+    if "batched" in legs and args.batch_fields > 0:
         extras["batched_split32"] = batched_leg(args, sht, inputs, torch, dev, stream, plan, rank, world, dist)
-    if not args.no_extras and rank == 0:
+    if rank == 0 and "autograd" in legs:
         extras["autograd_l512_b16"] = autograd_leg(args, sht, inputs, torch, dev, stream)
 
     cpu = None
