@@ -221,7 +221,7 @@ sht_status build_host(sht_plan_t P, int q) {
   return SHT_OK;
 }
 
-sht_status upload(sht_plan_t P, int q) {
+sht_status upload_streams(sht_plan_t P, int q) {
   if (P->dev_ready[q]) return SHT_OK;
   const double t0 = now_s();
   CK(cudaSetDevice(P->device));
@@ -267,6 +267,21 @@ sht_status upload(sht_plan_t P, int q) {
   P->dev_ready[q] = true;
   P->stats.t_upload += now_s() - t0;
   return SHT_OK;
+}
+
+// Uploads precision q; a failure part-way frees what this precision had
+// allocated, so a later attempt starts clean.
+sht_status upload(sht_plan_t P, int q) {
+  const sht_status s = upload_streams(P, q);
+  if (s != SHT_OK && !P->dev_ready[q]) {
+    for (int d = 0; d < 2; ++d) {
+      cudaFree(P->dev[q][d].pages);
+      cudaFree(P->dev[q][d].values);
+      cudaFree(P->dev[q][d].units);
+      P->dev[q][d] = DevStream();
+    }
+  }
+  return s;
 }
 
 // Makes precision q ready; cheap once it is (the launch path calls it every
