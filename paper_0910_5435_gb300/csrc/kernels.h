@@ -38,7 +38,7 @@ struct SweepArgs {
   unsigned* counter;           // work-queue counter (self-resetting; 0 between launches)
   unsigned* status;            // device status word (0 = ok)
   unsigned long long* trace;   // kTraceSlots cycle counters accumulated over all CTAs, or nullptr
-  int num_vecs;                // shared vectors (2, or 4 with interleaved parities)
+  int num_vecs;                // shared vectors (buffer ids 0 .. num_vecs-1)
   int staged;                  // 1: each consumer warp stages op values in two shared slots
   int slot_bytes;              // bytes of one staging slot (staged launches)
   // Batched launches (fields != nullptr): units[u].m is the item's field f;

@@ -647,8 +647,6 @@ struct Emitter {
   int l = 0;
   Emitter(PageWriter& w, int p) : W(w), prec(p), vs(value_size(p)) {}
 
-  void new_group() {}  // ordering comes from the tracked dependencies
-
   OpHdr hdr(uint8_t kind, uint8_t flags = 0) {
     OpHdr h;
     std::memset(&h, 0, sizeof(h));
@@ -962,14 +960,10 @@ struct Emitter {
   }
 };
 
-// Shared vectors: with interleaved parities, parity p uses the pair
-// (A_p, B_p) = (2p, 2p + 1), so the two independent parity butterflies of an
-// order run interleaved; otherwise both parities reuse (0, 1) one after the
-// other (half the shared memory, so a deeper page ring).
-thread_local bool g_interleave = false;
-inline uint8_t buf_a(int p) { return (uint8_t)(g_interleave ? 2 * p : 0); }
-inline uint8_t buf_b(int p) { return (uint8_t)(g_interleave ? 2 * p + 1 : 1); }
-inline uint8_t level_buf(int j, int p) { return (j & 1) ? buf_b(p) : buf_a(p); }
+// Shared vectors: both parities of an order use the pair (A, B) = (0, 1), one
+// parity after the other, levels alternating between them.
+constexpr uint8_t kBufA = 0, kBufB = 1;
+inline uint8_t level_buf(int j) { return (j & 1) ? kBufB : kBufA; }
 inline uint8_t other_buf(uint8_t b) { return (uint8_t)(b ^ 1); }
 
 std::vector<const IdBlock*> blocks_at(const UnitFact& U, int j) {
@@ -985,29 +979,8 @@ std::vector<const IdBlock*> blocks_at(const UnitFact& U, int j) {
 
 using Stage = std::function<void(Emitter&)>;
 
-// Emits the stages of both parities: interleaved (stage i of parity 0 and
-// stage i of parity 1 share one ordering group; they touch disjoint data), or
-// one parity after the other, one group per stage.
-void emit_interleaved(Emitter& E, const std::vector<Stage> (&st)[2]) {
-  if (!g_interleave) {
-    for (int p = 0; p < 2; ++p)
-      for (const Stage& s : st[p]) {
-        E.new_group();
-        s(E);
-      }
-    return;
-  }
-  const size_t n = std::max(st[0].size(), st[1].size());
-  for (size_t i = 0; i < n; ++i) {
-    E.new_group();
-    for (int p = 0; p < 2; ++p)
-      if (i < st[p].size()) st[p][i](E);
-  }
-}
-
 // Appends the ops of order m to the emitter's current work item.
 void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
-  g_interleave = P.interleave_parities;
   const int l = P.l;
   const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
   std::vector<double> inv_sq2w(l), sqw2(l);
@@ -1023,7 +996,7 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
     for (int p = 0; p < 2; ++p) {
       const UnitFact& U = F[(size_t)m * 2 + p];
       if (U.n == 0) continue;
-      const uint8_t A = buf_a(p);
+      const uint8_t A = kBufA;
       const uint8_t gflags = p ? F_ACCUM : 0;
       st[p].push_back([&U, A, p, m](Emitter& E) {
         OpHdr g = E.hdr(OP_GATHER);
@@ -1036,7 +1009,7 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
         for (int j = 1; j <= U.levels + 1; ++j)
           st[p].push_back([&U, j, p](Emitter& E) {
             for (const IdBlock* b : blocks_at(U, j))
-              if (b->k > 0) E.syn_interp(*b, j == 1 ? buf_a(p) : level_buf(j - 1, p), level_buf(j, p));
+              if (b->k > 0) E.syn_interp(*b, j == 1 ? kBufA : level_buf(j - 1), level_buf(j));
           });
       }
       fin[p] = [&U, A, p, m, l, gflags, &inv_sq2w](Emitter& E) {
@@ -1045,7 +1018,7 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
           E.dense(OP_DENSE_G, gflags, U.rows, U.n,
                   [&](int s, int o) { return U.D[(size_t)s * U.rows + o] * inv_sq2w[o]; }, A, 0, A, 0, m);
         } else if (U.rows > 0) {
-          const uint8_t top = level_buf(U.levels + 1, p);
+          const uint8_t top = level_buf(U.levels + 1);
           std::vector<const FinalBlock*> fs;
           for (const auto& f : U.finals) fs.push_back(&f);
           std::stable_sort(fs.begin(), fs.end(), [](const FinalBlock* a, const FinalBlock* b) {
@@ -1067,32 +1040,17 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
         }
       };
     }
-    if (g_interleave) {
-      emit_interleaved(E, st);
-      for (int p = 0; p < 2; ++p)
-        if (fin[p]) {
-          E.new_group();
-          fin[p](E);
-        }
-    } else {
-      // shared buffers: each parity's final blocks read its top level before
-      // the next parity overwrites it
-      for (int p = 0; p < 2; ++p) {
-        for (const Stage& sg : st[p]) {
-          E.new_group();
-          sg(E);
-        }
-        if (fin[p]) {
-          E.new_group();
-          fin[p](E);
-        }
-      }
+    // shared buffers: each parity's final blocks read its top level before
+    // the next parity overwrites it
+    for (int p = 0; p < 2; ++p) {
+      for (const Stage& sg : st[p]) sg(E);
+      if (fin[p]) fin[p](E);
     }
   } else {
     for (int p = 0; p < 2; ++p) {
       const UnitFact& U = F[(size_t)m * 2 + p];
       if (U.n == 0) continue;
-      const uint8_t A = buf_a(p), B = buf_b(p);
+      const uint8_t A = kBufA, B = kBufB;
       if (U.rows == 0) {
         st[p].push_back([&U, A](Emitter& E) {
           OpHdr c = E.hdr(OP_CLEAR);
@@ -1100,7 +1058,7 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
           E.control(c, 0, U.n);
         });
       } else {
-        const uint8_t top = U.direct ? A : level_buf(U.levels + 1, p);
+        const uint8_t top = U.direct ? A : level_buf(U.levels + 1);
         const uint8_t ubuf = U.direct ? B : other_buf(top);
         st[p].push_back([&U, ubuf, p, m](Emitter& E) {
           OpHdr f = E.hdr(OP_FOLD);
@@ -1127,7 +1085,7 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
           for (int j = U.levels + 1; j >= 2; --j) {
             // blocks of level j come in pairs (top band 2b, bottom band 2b+1) sharing one input
             // vector z of level j-1: the top halves overwrite z, then the bottom halves add
-            const uint8_t src = level_buf(j, p), dst = level_buf(j - 1, p);
+            const uint8_t src = level_buf(j), dst = level_buf(j - 1);
             auto tops = std::make_shared<std::vector<const IdBlock*>>();
             auto second = std::make_shared<std::vector<const IdBlock*>>();
             std::vector<const IdBlock*> bots;
@@ -1183,7 +1141,8 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
         E.control(s, 0, U.n);
       });
     }
-    emit_interleaved(E, st);
+    for (int p = 0; p < 2; ++p)
+      for (const Stage& sg : st[p]) sg(E);
   }
 }
 
@@ -1333,7 +1292,7 @@ void emit_streams(PlanHost& P, int prec) {
       for (int wdt : F[u].width) mx = std::max(mx, wdt);
     }
     S.max_buf_ab = mx;
-    S.num_vecs = P.interleave_parities ? 4 : 2;
+    S.num_vecs = 2;
   }
   P.built[prec] = true;
 }

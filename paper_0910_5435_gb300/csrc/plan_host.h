@@ -67,7 +67,7 @@ struct Stream {
   std::vector<uint8_t> values;       // value region (ops with F_VALUES_APART)
   std::vector<UnitEntry> units;      // LPT order
   int max_buf_ab = 0;                // elements needed in each shared vector
-  int num_vecs = 2;                  // shared vectors used (4 with interleaved parities)
+  int num_vecs = 2;                  // shared vectors used
 };
 
 struct PlanHost {
@@ -75,7 +75,6 @@ struct PlanHost {
   double eps_id = 0, eps_fp32 = 0, trim_eps = 0;
   int leaf_cols = 64, min_band_rows = 32, num_threads = 0, page_bytes = 8192;
   int slot_values = kDefaultSlotValues;  // cap on the values of one op kept apart
-  bool interleave_parities = false;
   bool values_apart[3] = {true, true, true};  // per precision: value blocks outside the pages
   bool debug_unmet_dep = false;  // plant a never-met predecessor (failure-detection tests)
   // Gauss-Legendre nodes (all 2l, ascending), weights, and the angle of each

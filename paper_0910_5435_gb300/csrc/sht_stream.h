@@ -120,10 +120,10 @@ struct UnitEntry {
 };
 static_assert(sizeof(UnitEntry) == 16, "UnitEntry must be 16 bytes");
 
-// Shared-memory vectors: parity p owns ids 2p (A_p) and 2p + 1 (B_p), each
-// buf_ab complex elements, so both parity butterflies of an order run
-// interleaved.
-constexpr int kNumVecs = 4;
+// Shared-memory vectors A (id 0) and B (id 1), each buf_ab complex elements;
+// the butterfly levels alternate between them, and the two parities of an
+// order use them one after the other.
+constexpr int kNumVecs = 2;
 
 constexpr int kMaxM = 32;             // outputs per compute op (one warp)
 constexpr int kMaxPred = 32;          // predecessors listed by a data op (more: fan-in JOIN); one warp checks 32 at once
@@ -135,7 +135,6 @@ constexpr int kMaxItemOps = 3584;
 constexpr int kDefaultSlotValues = 1024;
 constexpr int kMinSlotValues = 128;
 constexpr int kMaxSlotValues = 2048;
-constexpr int kConsumerWarps = 8;
 constexpr int kCtlPieces = 8;         // control ops are split into up to this many warp tasks
 constexpr uint16_t kQuitPage = 0xFFFF;  // op count of the stream's final page
 

@@ -37,7 +37,6 @@ constexpr int threads_for() { return (NW + 2) * 32; }  // consumers + producer +
 constexpr int kMaxStages = 16;
 constexpr int kDir = 1024;                            // op directory entries (ring)
 constexpr int kOrd = 64;                              // page issue-order ring (>= stages)
-constexpr int kConsumerWarps16 = 16;                  // upper bound on consumer warps
 constexpr long long kTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr unsigned kStatusTimeout = 5;              // SHT_ERR_TIMEOUT
 constexpr unsigned kStatusBadArg = 1;               // SHT_ERR_INVALID_ARG (a field's pointers)
