@@ -59,11 +59,11 @@ def parse():
 
 # DRAM traffic of one float64 sweep launch at l = 1024 (leaf_cols 32, 8 KB
 # pages), dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu
-# capture, mean of a synthesis (6.517 GB) and an analysis (6.404 GB) launch
+# capture, mean of a synthesis (6.517 GB) and an analysis (6.405 GB) launch
 # (profiles/bfly_sweep_fp64_l1024_dram.md).  Valid only for the kernel and
 # stream-format sources it was taken with: SWEEP_SOURCES_SHA is their hash.
-SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4605e9}
-SWEEP_SOURCES_SHA = "7ffd6d66079d14e6"
+SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4607e9}
+SWEEP_SOURCES_SHA = "48e9b66fa4e33faf"
 
 
 def sweep_sources_sha():
