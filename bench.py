@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--consumer-warps", type=int, default=0)
     ap.add_argument("--eps", type=float, default=1e-12)
     ap.add_argument("--no-extras", action="store_true", help="skip every leg beside the float64 headline")
-    ap.add_argument("--paths", default="split32,fp32,direct,full,batched,autograd",
+    ap.add_argument("--paths", default="split32,split32acc64,fp32,direct,full,batched,autograd",
                     help="comma-separated legs to run beside the headline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--batch-fields", type=int, default=96,
@@ -62,8 +62,8 @@ def parse():
 # capture, mean of a synthesis (6.517 GB) and an analysis (6.405 GB) launch
 # (profiles/bfly_sweep_fp64_l1024_dram.md).  Valid only for the kernel and
 # stream-format sources it was taken with: SWEEP_SOURCES_SHA is their hash.
-SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4607e9}
-SWEEP_SOURCES_SHA = "48e9b66fa4e33faf"
+SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4588e9}
+SWEEP_SOURCES_SHA = "509c6bf78e225ac6"
 
 
 def sweep_sources_sha():
@@ -546,7 +546,9 @@ def main():
     extras = {}
     legs = set() if args.no_extras else {s.strip() for s in args.paths.split(",") if s.strip()}
     if rank == 0:
-        for name, prec, cdt in (("split32", sht.SHT_SPLIT32, torch.complex128), ("fp32", sht.SHT_FP32, torch.complex64)):
+        for name, prec, cdt in (("split32", sht.SHT_SPLIT32, torch.complex128),
+                                ("split32acc64", sht.SHT_SPLIT32_ACC64, torch.complex128),
+                                ("fp32", sht.SHT_FP32, torch.complex64)):
             if name not in legs:
                 continue
             t0 = time.perf_counter()
@@ -600,7 +602,7 @@ def main():
         with tempfile.TemporaryDirectory() as td:
             op = os.path.join(td, "outputs.npz")
             arrays = {"fp64_G": G64, "fp64_beta": back64}
-            for k in ("split32", "fp32", "direct"):
+            for k in ("split32", "split32acc64", "fp32", "direct"):
                 if k + "_G" in extras:
                     arrays[k + "_G"] = extras[k + "_G"]
                     arrays[k + "_beta"] = extras[k + "_beta"]

@@ -36,6 +36,11 @@
  *                   float32 arithmetic; same I/O types as SHT_FP64.
  *       SHT_FP32    float32 factors and arithmetic; complex64 beta/G,
  *                   float32 values.
+ *       SHT_SPLIT32_ACC64  the SHT_SPLIT32 factors, products formed as
+ *                   float32 error-free pairs (as SHT_SPLIT32) but summed in
+ *                   float64 (the high parts) and float32 (the low parts);
+ *                   same I/O types as SHT_FP64.  It shares the SHT_SPLIT32
+ *                   streams (sht_prepare of either builds both).
  *   - All device pointers are caller-owned, must be 16-byte aligned
  *     (8-byte for SHT_FP32), and are only read/written asynchronously on the
  *     given stream.  Entry points never synchronize the stream unless stated.
@@ -60,7 +65,8 @@ typedef struct CUstream_st* sht_stream_t;
 typedef enum {
   SHT_FP64 = 0,
   SHT_FP32 = 1,
-  SHT_SPLIT32 = 2
+  SHT_SPLIT32 = 2,
+  SHT_SPLIT32_ACC64 = 3
 } sht_precision;
 
 typedef enum {

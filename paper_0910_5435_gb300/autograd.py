@@ -20,7 +20,8 @@ import torch
 
 from . import sht
 
-_CDT = {sht.SHT_FP64: torch.complex128, sht.SHT_SPLIT32: torch.complex128, sht.SHT_FP32: torch.complex64}
+_CDT = {sht.SHT_FP64: torch.complex128, sht.SHT_SPLIT32: torch.complex128, sht.SHT_SPLIT32_ACC64: torch.complex128,
+        sht.SHT_FP32: torch.complex64}
 
 
 def _batch(plan, prec, n):

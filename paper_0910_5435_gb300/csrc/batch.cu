@@ -163,13 +163,17 @@ sht_status sht_batch_create(int nfields, const sht_plan_t* plans, sht_precision 
   if (!out) return SHT_ERR_INVALID_ARG;
   *out = nullptr;
   if (nfields < 1 || nfields > SHT_BATCH_MAX_FIELDS || !plans) return SHT_ERR_INVALID_ARG;
-  if (prec != SHT_FP64 && prec != SHT_FP32 && prec != SHT_SPLIT32) return SHT_ERR_INVALID_ARG;
+  if (prec != SHT_FP64 && prec != SHT_FP32 && prec != SHT_SPLIT32 && prec != SHT_SPLIT32_ACC64)
+    return SHT_ERR_INVALID_ARG;
   for (int f = 0; f < nfields; ++f)
     if (!plans[f]) return SHT_ERR_INVALID_ARG;
   sht_batch_t b = new (std::nothrow) sht_batch_s();
   if (!b) return SHT_ERR_OOM;
   b->n = nfields;
-  b->q = prec == SHT_FP64 ? sht::PREC_FP64 : (prec == SHT_FP32 ? sht::PREC_FP32 : sht::PREC_SPLIT32);
+  b->q = prec == SHT_FP64      ? sht::PREC_FP64
+         : prec == SHT_FP32    ? sht::PREC_FP32
+         : prec == SHT_SPLIT32 ? sht::PREC_SPLIT32
+                               : sht::PREC_SPLIT32_ACC64;
   const sht_status s = build(b, nfields, plans, prec);
   if (s != SHT_OK) {
     free_batch(b);

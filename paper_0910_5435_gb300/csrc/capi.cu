@@ -44,13 +44,20 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Stream format of a precision (SHT_SPLIT32_ACC64 applies the split streams).
 int prec_index(sht_precision p) {
   switch (p) {
     case SHT_FP64: return sht::PREC_FP64;
     case SHT_FP32: return sht::PREC_FP32;
-    case SHT_SPLIT32: return sht::PREC_SPLIT32;
+    case SHT_SPLIT32:
+    case SHT_SPLIT32_ACC64: return sht::PREC_SPLIT32;
     default: return -1;
   }
+}
+
+// Kernel that applies a precision's streams.
+int kernel_prec(sht_precision p) {
+  return p == SHT_SPLIT32_ACC64 ? sht::PREC_SPLIT32_ACC64 : prec_index(p);
 }
 
 }  // namespace
@@ -252,6 +259,7 @@ sht_status upload_streams(sht_plan_t P, int q) {
   // the limit is a per-kernel setting shared by every plan: raise it to the
   // device maximum once instead of to this plan's size
   CK(sht::sweep_configure(q, (size_t)optin));
+  if (q == sht::PREC_SPLIT32) CK(sht::sweep_configure(sht::PREC_SPLIT32_ACC64, (size_t)optin));
   sht::SweepConfig cfg;
   const int slot_bytes = P->H.values_apart[q] ? P->H.slot_values * (q == sht::PREC_FP32 ? 4 : 8) : 0;
   if (!sht::sweep_choose(q, P->H.page_bytes, buf_ab, nvecs, P->consumer_warps[q], slot_bytes, 0, (size_t)optin,
@@ -335,7 +343,8 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.status = P->d_scratch + kNumPrec * KIND_COUNT;
   const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
   (void)cudaGetLastError();  // do not report a stale error left by an earlier call (e.g. inside cuFFT)
-  CK(sht::sweep_launch(q, P->consumer_warps[q], a, grid, P->smem[q], reinterpret_cast<cudaStream_t>(stream)));
+  CK(sht::sweep_launch(kernel_prec(prec), P->consumer_warps[q], a, grid, P->smem[q],
+                       reinterpret_cast<cudaStream_t>(stream)));
   return SHT_OK;
 }
 
@@ -377,7 +386,7 @@ sht_status sht::prepared_sweep(sht_plan_t P, sht_precision prec, int dir, const 
   a.num_vecs = P->num_vecs[q];
   a.staged = P->staged[q] ? 1 : 0;
   a.slot_bytes = P->slot_bytes[q];
-  L->prec = q;
+  L->prec = kernel_prec(prec);
   L->consumer_warps = P->consumer_warps[q];
   L->grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
   L->smem = P->smem[q];

@@ -75,7 +75,9 @@ enum TraceSlot {
   kTraceSlots = 16
 };
 
-enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2 };
+// Kernel precisions: the three stream formats, plus split float32 factors
+// applied with float64 accumulation (same streams as PREC_SPLIT32).
+enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2, PREC_SPLIT32_ACC64 = 3 };
 
 size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes);
 // Picks the ring depth (nstages > 0: exactly that depth) for the given warps:

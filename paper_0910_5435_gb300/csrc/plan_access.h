@@ -12,7 +12,7 @@ namespace sht {
 
 struct PreparedSweep {
   SweepArgs args;   // counter, status and trace left null for the caller to set
-  int prec = 0;     // SweepPrec
+  int prec = 0;     // SweepPrec of the kernel
   int consumer_warps = 8;
   int slot_bytes = 0;                // staging slot per op (0: values in the pages)
   int grid = 1;

@@ -222,6 +222,56 @@ struct TS32 {
   }
 };
 
+// Split float32 factors as TS32, products as float32 error-free pairs, but
+// accumulated in float64: the high parts of the products in a double, their
+// low parts (orders of magnitude smaller) in a float.
+struct TS32A : TS32 {
+  static constexpr int kChains = 1;  // float64 adds: the FP64 pipe hides the chain
+  struct Acc {
+    double re, im;
+    float rl, il;
+  };
+  __device__ static Acc zero() { return {0.0, 0.0, 0.f, 0.f}; }
+  __device__ static void fma1(double& s, float& sl, float2 v, float xh, float xl) {
+    const float p = __fmul_rn(v.x, xh);
+    float e = __fmaf_rn(v.x, xh, -p);
+    e = __fmaf_rn(v.x, xl, e);
+    e = __fmaf_rn(v.y, xh, e);
+    s += (double)p;
+    sl = __fadd_rn(sl, e);
+  }
+  __device__ static void fma(Acc& a, V v, const C& x) {
+    fma1(a.re, a.rl, v, x.x, x.y);
+    fma1(a.im, a.il, v, x.z, x.w);
+  }
+  __device__ static void add(Acc& a, const C& c) {
+    a.re += (double)c.x;
+    a.rl = __fadd_rn(a.rl, c.y);
+    a.im += (double)c.z;
+    a.il = __fadd_rn(a.il, c.w);
+  }
+  __device__ static void merge(Acc& a, const Acc& b) {
+    a.re += b.re;
+    a.im += b.im;
+    a.rl = __fadd_rn(a.rl, b.rl);
+    a.il = __fadd_rn(a.il, b.il);
+  }
+  __device__ static C to_c(const Acc& a) {
+    const double r = a.re + (double)a.rl, i = a.im + (double)a.il;
+    const float rh = __double2float_rn(r), ih = __double2float_rn(i);
+    return make_float4(rh, __double2float_rn(r - (double)rh), ih, __double2float_rn(i - (double)ih));
+  }
+  __device__ static Acc from_c(const C& c) { return {(double)c.x + (double)c.y, (double)c.z + (double)c.w, 0.f, 0.f}; }
+  __device__ static Acc shfl_xor(const Acc& a, int off) {
+    return {__shfl_xor_sync(0xffffffffu, a.re, off), __shfl_xor_sync(0xffffffffu, a.im, off),
+            __shfl_xor_sync(0xffffffffu, a.rl, off), __shfl_xor_sync(0xffffffffu, a.il, off)};
+  }
+  __device__ static Acc shfl_down(const Acc& a, int off) {
+    return {__shfl_down_sync(0xffffffffu, a.re, off), __shfl_down_sync(0xffffffffu, a.im, off),
+            __shfl_down_sync(0xffffffffu, a.rl, off), __shfl_down_sync(0xffffffffu, a.il, off)};
+  }
+};
+
 // float32 factors and arithmetic; complex64 I/O.
 struct TF32 {
   static constexpr int kChains = 2;
@@ -960,6 +1010,7 @@ size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int n
   switch (prec) {
     case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
     case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
+    case PREC_SPLIT32_ACC64: return smem_for<TS32A>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
     default: return smem_for<TS32>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
   }
 }
@@ -979,6 +1030,7 @@ const void* kernel_for(int prec, int nw) {
   switch (prec) {
     case PREC_FP64: return kernel_ptr<TF64>(nw);
     case PREC_FP32: return kernel_ptr<TF32>(nw);
+    case PREC_SPLIT32_ACC64: return kernel_ptr<TS32A>(nw);
     default: return kernel_ptr<TS32>(nw);
   }
 }

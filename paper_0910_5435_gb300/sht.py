@@ -16,8 +16,8 @@ import numpy as np
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libsht.so")
 
-SHT_FP64, SHT_FP32, SHT_SPLIT32 = 0, 1, 2
-PRECISIONS = {"fp64": SHT_FP64, "fp32": SHT_FP32, "split32": SHT_SPLIT32}
+SHT_FP64, SHT_FP32, SHT_SPLIT32, SHT_SPLIT32_ACC64 = 0, 1, 2, 3
+PRECISIONS = {"fp64": SHT_FP64, "fp32": SHT_FP32, "split32": SHT_SPLIT32, "split32acc64": SHT_SPLIT32_ACC64}
 
 STATUS = {
     0: "SHT_OK", 1: "SHT_ERR_INVALID_ARG", 2: "SHT_ERR_OOM", 3: "SHT_ERR_CUDA",

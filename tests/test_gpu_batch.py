@@ -16,8 +16,8 @@ from paper_0910_5435_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 2: 1e-9, 1: 2e-5}
-CDT = {0: torch.complex128, 2: torch.complex128, 1: torch.complex64}
+TOL = {0: 1e-10, 2: 1e-9, 3: 1e-9, 1: 2e-5}
+CDT = {0: torch.complex128, 2: torch.complex128, 3: torch.complex128, 1: torch.complex64}
 LS = (4, 16, 32, 64, 128)
 
 
@@ -52,7 +52,7 @@ def field_ls(n, seed):
     return [int(x) for x in np.random.default_rng(seed).choice(LS, size=n)]
 
 
-@pytest.mark.parametrize("prec", [0, 2, 1])
+@pytest.mark.parametrize("prec", [0, 2, 3, 1])
 def test_batch_equals_per_field_calls_and_oracle(sht, plans, prec):
     ls = field_ls(11, 4)
     for l in set(ls):
@@ -157,7 +157,7 @@ def test_batch_with_degenerate_and_single_fields(sht, plans):
     tiny = {l: sht.Plan(l, 1e-12, leaf_cols=4) for l in (1, 2)}
     ls = [1, 64, 2, 4, 1, 128]
     pl = [tiny[l] if l in tiny else plans[l] for l in ls]
-    for prec in (0, 1):
+    for prec in (0, 3, 1):
         for p in set(pl):
             p.prepare(prec)
         B = sht.Batch(pl, prec)

@@ -15,9 +15,9 @@ from tests.stream_emulator import emulate
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 2: 1e-9, 1: 2e-5}
-CDT = {0: torch.complex128, 2: torch.complex128, 1: torch.complex64}
-NDT = {0: np.complex128, 2: np.complex128, 1: np.complex64}
+TOL = {0: 1e-10, 2: 1e-9, 3: 1e-9, 1: 2e-5}
+CDT = {0: torch.complex128, 2: torch.complex128, 3: torch.complex128, 1: torch.complex64}
+NDT = {0: np.complex128, 2: np.complex128, 3: np.complex128, 1: np.complex64}
 
 
 def rel(a, b):
@@ -67,7 +67,7 @@ def run_analysis(sht, P, prec, G, adjoint=False):
 
 
 @pytest.mark.parametrize("l,C", [(1, 4), (2, 4), (16, 4), (64, 16), (64, 64), (128, 16)])
-@pytest.mark.parametrize("prec", [0, 2, 1])
+@pytest.mark.parametrize("prec", [0, 2, 3, 1])
 def test_synthesis_matches_oracle(sht, l, C, prec):
     P = plan(sht, l, C)
     beta = inputs.random_beta(l, seed=100 + l)
@@ -76,7 +76,7 @@ def test_synthesis_matches_oracle(sht, l, C, prec):
 
 
 @pytest.mark.parametrize("l,C", [(1, 4), (2, 4), (16, 4), (64, 16), (64, 64), (128, 16)])
-@pytest.mark.parametrize("prec", [0, 2, 1])
+@pytest.mark.parametrize("prec", [0, 2, 3, 1])
 def test_analysis_and_adjoint_match_oracle(sht, l, C, prec):
     P = plan(sht, l, C)
     G = inputs.random_G(l, seed=200 + l)
@@ -108,7 +108,7 @@ def test_round_trip_l512_all_precisions(sht):
     l = 512
     P = plan(sht, l, 64)
     beta = inputs.random_beta(l, seed=2, decay=True)
-    for prec in (0, 2, 1):
+    for prec in (0, 2, 3, 1):
         G = run_synth(sht, P, prec, beta)
         back = run_analysis(sht, P, prec, G.astype(np.complex128))
         assert rel(back, beta) < 2 * TOL[prec], prec
@@ -126,7 +126,7 @@ def test_l512_sampled_orders_match_oracle(sht):
     bo = oracle.legendre_analysis(Gin, l, orders=ms)
     off = oracle.triangle_offsets(l)
     sel = np.concatenate([np.arange(off[m], off[m + 1]) for m in ms])
-    for prec in (0, 2, 1):
+    for prec in (0, 2, 3, 1):
         G = run_synth(sht, P, prec, beta)
         assert rel(G[ms], Go[ms]) < TOL[prec], prec
         b = run_analysis(sht, P, prec, Gin)
@@ -175,7 +175,7 @@ def test_misaligned_and_null_pointers_rejected(sht):
 
 
 @pytest.mark.parametrize("values_inline", [0, 1])
-@pytest.mark.parametrize("prec", [0, 2, 1])
+@pytest.mark.parametrize("prec", [0, 2, 3, 1])
 def test_both_value_layouts_on_gpu(sht, values_inline, prec):
     """Values streamed by the executing warp, or staged in the TMA pages: same
     results (float64 layouts agree to rounding; both match the oracle)."""
@@ -192,7 +192,7 @@ def test_both_value_layouts_on_gpu(sht, values_inline, prec):
 def test_l1024_bench_configuration_sampled_orders(sht):
     """Full-size parity at the benchmarked configuration: l = 1024, eps_id =
     1e-12, leaf_cols 32, 8 KB pages, default warps, beta ~ N(0,1)/(k+1) with
-    seed 3 (the bench's field), all three precisions, both directions, on
+    seed 3 (the bench's field), all four precisions, both directions, on
     orders the oracle computes one by one (the first, the last, both parities
     of the middle, and orders near the turning point of the nodes)."""
     l = 1024
@@ -205,7 +205,7 @@ def test_l1024_bench_configuration_sampled_orders(sht):
     ba = oracle.legendre_adjoint(Gin, l, orders=ms)
     off = oracle.triangle_offsets(l)
     sel = np.concatenate([np.arange(off[m], off[m + 1]) for m in ms])
-    for prec in (0, 2, 1):
+    for prec in (0, 2, 3, 1):
         P.prepare(prec)
         G = run_synth(sht, P, prec, beta)
         assert rel(G[ms], Go[ms]) < TOL[prec], prec

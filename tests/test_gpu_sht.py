@@ -12,9 +12,9 @@ from paper_0910_5435_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 2: 1e-9, 1: 2e-5}
-CDT = {0: torch.complex128, 2: torch.complex128, 1: torch.complex64}
-RDT = {0: torch.float64, 2: torch.float64, 1: torch.float32}
+TOL = {0: 1e-10, 2: 1e-9, 3: 1e-9, 1: 2e-5}
+CDT = {0: torch.complex128, 2: torch.complex128, 3: torch.complex128, 1: torch.complex64}
+RDT = {0: torch.float64, 2: torch.float64, 3: torch.float64, 1: torch.float32}
 
 
 def rel(a, b):
@@ -62,7 +62,7 @@ def test_phi_stage_matches_naive_dft(sht, l, prec):
 
 
 @pytest.mark.parametrize("l,C", [(2, 4), (16, 4), (64, 16), (128, 16)])
-@pytest.mark.parametrize("prec", [0, 2, 1])
+@pytest.mark.parametrize("prec", [0, 2, 3, 1])
 def test_full_sht_matches_oracle(sht, l, C, prec):
     P = plan(sht, l, C)
     beta = inputs.random_beta(l, seed=300 + l)
