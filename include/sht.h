@@ -134,6 +134,13 @@ typedef struct {
    * default 1024).  Smaller slots let more consumer warps fit in shared
    * memory, at the cost of splitting blocks into more ops.  A tuning knob. */
   int slot_values;
+  /* 1: compute the factorizations (column generation, IDs, depth-first
+   * merges of Section 3) on the plan's GPU, one CTA per parity block,
+   * instead of on host threads; the host still lays out and encodes the
+   * streams.  The columns are the host builder's bit for bit; ranks can
+   * differ where a residual norm sits at eps_id, since the QR rounds in
+   * another order.  Needs host_only = 0.  Default 0. */
+  int device_build;
 } sht_plan_opts;
 
 typedef struct {
@@ -158,7 +165,8 @@ typedef struct {
   long long stream_bytes_fp32;
   long long factor_values_fp32;  /* stored factor values of the eps_fp32 factorization */
   double t_quad;         /* seconds: Gauss-Legendre nodes and weights */
-  double t_comp;         /* seconds: columns + IDs + butterflies (host, all threads) */
+  double t_comp;         /* seconds: columns + IDs + butterflies (host threads, or the GPU
+                          * with device_build) and stream encoding */
   double t_upload;       /* seconds: device upload of the prepared precisions */
   long long m_max_words; /* peak float64 words held by one unit's depth-first build */
   int smem_bytes;        /* dynamic shared memory of the sweep kernels */

@@ -210,10 +210,12 @@ sht_status build_host(sht_plan_t P, int q) {
   if (H.built[q]) return SHT_OK;
   try {
     const double t0 = now_s();
-    if (q == sht::PREC_FP32) {
-      if (H.fact32.empty()) sht::build_factorizations(H, true);
-    } else if (H.fact64.empty()) {
-      sht::build_factorizations(H, false);
+    const bool fp32 = (q == sht::PREC_FP32);
+    if ((fp32 ? H.fact32 : H.fact64).empty()) {
+      if (P->opts.device_build)
+        sht::build_factorizations_device(H, fp32, P->device);
+      else
+        sht::build_factorizations(H, fp32);
     }
     sht::emit_streams(H, q);
     H.t_comp += now_s() - t0;
@@ -453,6 +455,7 @@ sht_status sht_plan_opts_default(sht_plan_opts* o) {
   o->values_inline = 0;
   o->debug_unmet_dependency = 0;
   o->slot_values = 0;
+  o->device_build = 0;
   return SHT_OK;
 }
 
@@ -475,6 +478,7 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   if (o.leaf_cols < 2 || o.leaf_cols > 1024) return SHT_ERR_INVALID_ARG;
   if (o.page_bytes < 4096 || o.page_bytes > 49152 || (o.page_bytes % 1024) != 0) return SHT_ERR_INVALID_ARG;
   if (o.num_threads < 0) return SHT_ERR_INVALID_ARG;
+  if (o.device_build != 0 && (o.device_build != 1 || o.host_only)) return SHT_ERR_INVALID_ARG;
   if (o.consumer_warps != 0 && o.consumer_warps != 8 && o.consumer_warps != 12 && o.consumer_warps != 16)
     return SHT_ERR_INVALID_ARG;
   if (o.slot_values != 0 && (o.slot_values < sht::kMinSlotValues || o.slot_values > sht::kMaxSlotValues ||

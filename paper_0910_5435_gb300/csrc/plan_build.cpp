@@ -430,7 +430,26 @@ UnitFact factor_unit(const PlanHost& P, int m, int p, double eps) {
   }
   U.peak_words = peak;
   U.levels = lam;
+  // top level: one group, 2^lam bands whose stored skeleton columns are the final blocks
+  std::vector<FinalBlock> top;
+  for (size_t beta = 0; beta < stack.back().bands.size(); ++beta) {
+    BandData& bd = stack.back().bands[beta];
+    FinalBlock f;
+    f.band = (int)beta;
+    f.r0 = bd.r0;
+    f.r1 = bd.r1;
+    f.k = bd.k;
+    f.S = std::move(bd.Ask);  // column-major h x k == S[t * h + i]
+    top.push_back(std::move(f));
+  }
+  finish_unit(P, U, std::move(top));
+  return U;
+}
 
+}  // namespace
+
+void finish_unit(const PlanHost& P, UnitFact& U, std::vector<FinalBlock>&& top) {
+  const int lam = U.levels, rows = U.rows, n = U.n, m = U.m, p = U.p;
   // layouts: level j holds its blocks band-major, group-minor
   U.width.assign(lam + 2, 0);
   std::vector<std::vector<int>> at(lam + 2);
@@ -460,17 +479,9 @@ UnitFact factor_unit(const PlanHost& P, int m, int p, double eps) {
       B.in_off = U.blocks[found].out_off;
     }
   }
-  // top level: one group, 2^lam bands whose stored skeleton columns are the final blocks
-  const Group& top = stack.back();
-  for (size_t beta = 0; beta < top.bands.size(); ++beta) {
-    FinalBlock f;
-    f.band = (int)beta;
-    f.r0 = top.bands[beta].r0;
-    f.r1 = top.bands[beta].r1;
-    f.k = top.bands[beta].k;
-    f.S = top.bands[beta].Ask;  // column-major h x k == S[t * h + i]
+  for (FinalBlock& f : top) {
     for (int bi : at[lam + 1])
-      if (U.blocks[bi].band == (int)beta) f.in_off = U.blocks[bi].out_off;
+      if (U.blocks[bi].band == f.band) f.in_off = U.blocks[bi].out_off;
     U.finals.push_back(std::move(f));
   }
   for (const auto& b : U.blocks) {
@@ -495,10 +506,7 @@ UnitFact factor_unit(const PlanHost& P, int m, int p, double eps) {
     for (int j = 0; j < n; ++j) cs2.next(U.D.data() + (size_t)j * rows);
   }
   U.cost = std::min(bfly_bytes, dense_bytes);
-  return U;
 }
-
-}  // namespace
 
 UnitFact factor_single_unit(const PlanHost& P, int m, int p, double eps) { return factor_unit(P, m, p, eps); }
 

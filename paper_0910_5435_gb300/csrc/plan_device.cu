@@ -1,0 +1,889 @@
+// plan_device.cu -- the depth-first butterfly precomputation of Section 3 on
+// the device.
+//
+// A persistent grid takes parity blocks A^{m,p} from a queue (largest
+// first); one CTA builds one block at a time, exactly in the order of the
+// host builder (plan_build.cpp):
+//   1. columns come from the x^2 recurrence of Section 2.3 (eqs. c_rec,
+//      d_rec, recurrence0, recurrence) with the exponent tracking of Section
+//      4, one row per thread: first over all n columns for the row norms that
+//      trimming needs, then leaf by leaf;
+//   2. each interpolative decomposition (Section 2.1, eq. 2.1) is a
+//      column-pivoted Householder QR (Remark QR_algorithm) run by the whole
+//      CTA: pivot search and norms by block reductions, one warp per trailing
+//      column, the Householder vector in shared memory;
+//   3. neighbouring groups are merged as soon as they have the same level
+//      (Section 3), with the stack of skeleton columns in global scratch.
+// Every ID block and every band of the top level is written as one record
+// into an output arena; the host reads the records back, lays each unit out
+// (finish_unit) and encodes the streams as after a host build.  Nothing here
+// waits on another CTA: the only synchronisation is __syncthreads.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <stdexcept>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "plan_host.h"
+#include "recurrence.h"
+
+namespace sht {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxGroups = 24;
+constexpr unsigned kFull = 0xffffffffu;
+
+enum UnitStatus { kPending = 0, kDone = 1, kNoArena = 2, kNoScratch = 3 };
+
+// One record of the output arena (a multiple of 16 bytes).
+//   kind 0, an ID block: header, int skel[k], int red[nin - k] (ascending),
+//           padding to 16 bytes, double T[k * (nin - k)] (T[s * k + t]);
+//   kind 1, a band of the top level: header, double S[(r1 - r0) * k].
+struct RecHdr {
+  int unit, kind, level, band, group, r0, r1, in_off, nin, k;
+  long long bytes;
+  int pad[4];
+};
+static_assert(sizeof(RecHdr) == 64, "record header size");
+
+struct BandDesc {
+  int r0, r1, k, pad;
+  long long off;  // words into the CTA's stack
+};
+struct GroupDesc {
+  int level, g, nb, d0;  // d0: first band descriptor
+};
+
+struct DevBuildArgs {
+  int l, C, min_band_rows;
+  double eps2;     // eps_id^2
+  double trim2;    // (trim_eps / sqrt l)^2; 0: no trimming
+  const double* xpos;  // x_{l+i}, i < l
+  const double* spos;  // sin(theta_{l+i})
+  const double* sq2w;  // sqrt(2 w_{l+i})
+  const int* queue;    // unit ids u = 2m + p, largest first
+  int n_queue;
+  unsigned* next;      // queue counter
+  double* scratch;     // per CTA: scratch_words
+  long long scratch_words, buf_words, stack_words, desc_cap;
+  unsigned char* arena;
+  unsigned long long arena_bytes;
+  unsigned long long* arena_used;
+  unsigned long long* arena_fail;  // lowest offset of a reservation that did not fit
+  int* stop;                       // the arena is full: take no further units
+  int* status;                     // per unit id
+  long long* info;                 // per unit id: rows, levels, peak words
+};
+
+struct Shared {
+  GroupDesc grp[kMaxGroups];
+  double redv[kWarps];
+  int redi[kWarps];
+  long long rec_off;
+  int q, ngrp, ecm;
+  double cm;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  // xor butterfly: every lane ends with the same bits (a + b == b + a)
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Sum over the CTA; every thread returns the same value.
+__device__ double block_sum(double v, Shared& S) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) S.redv[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) s += S.redv[i];
+  return s;
+}
+
+__device__ int block_max_int(int v, Shared& S) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) S.redi[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int r = S.redi[0];
+#pragma unroll
+  for (int i = 1; i < kWarps; ++i) r = max(r, S.redi[i]);
+  return r;
+}
+
+__device__ __forceinline__ bool better(double a, int ia, double b, int ib) {
+  return a > b || (a == b && ia < ib);
+}
+
+// Index of the largest x[j], i0 <= j < w, the lowest on ties (the host's
+// pivot rule); i0 if none compares larger than -inf.
+__device__ int block_argmax(const double* x, int i0, int w, Shared& S) {
+  double best = -INFINITY;
+  int bi = w;
+  for (int j = i0 + (int)threadIdx.x; j < w; j += kThreads)
+    if (x[j] > best) {
+      best = x[j];
+      bi = j;
+    }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double ob = __shfl_xor_sync(kFull, best, o);
+    const int oi = __shfl_xor_sync(kFull, bi, o);
+    if (better(ob, oi, best, bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    S.redv[threadIdx.x >> 5] = best;
+    S.redi[threadIdx.x >> 5] = bi;
+  }
+  __syncthreads();
+  best = S.redv[0];
+  bi = S.redi[0];
+#pragma unroll
+  for (int i = 1; i < kWarps; ++i)
+    if (better(S.redv[i], S.redi[i], best, bi)) {
+      best = S.redv[i];
+      bi = S.redi[i];
+    }
+  return bi < w ? bi : i0;
+}
+
+__device__ __forceinline__ void renorm(double& v, int& e) {
+  if (v == 0.0) return;
+  int t;
+  v = frexp(v, &t);
+  e += t;
+}
+
+// Per-CTA views of the dynamic shared memory and the global scratch.
+struct Views {
+  // shared
+  double *cinv, *cd, *cm2;  // per column j < n: 1/c_k, d_k, c_{k-2} (0 at j = 0), k = m + p + 2j
+  double *nrm, *ref, *v;
+  int* perm;
+  // global, per CTA
+  double *x2, *sqw, *ga, *gb;
+  int* ge;
+  BandDesc* desc;
+  double *bufZ, *bufW, *stack;
+};
+
+// Generator state of rows 0..rows-1 at column 0: b = P-bar^m_{m+p}(x_i) as a
+// mantissa and exponent, a = 0 (eq. recurrence0 has no k - 2 term).
+__device__ void gen_init(const DevBuildArgs& A, const Views& V, const Shared& S, int m, int p, int rows) {
+  for (int i = threadIdx.x; i < rows; i += kThreads) {
+    const double xi = A.xpos[i];
+    V.x2[i] = xi * xi;
+    V.sqw[i] = A.sq2w[i];
+    // sin(theta)^m by binary powering with tracked exponents
+    int eb;
+    double base = frexp(A.spos[i], &eb);
+    double res = 1.0;
+    int er = 0;
+    for (int q = m; q; q >>= 1) {
+      if (q & 1) {
+        res *= base;
+        er += eb;
+        renorm(res, er);
+      }
+      base *= base;
+      eb *= 2;
+      renorm(base, eb);
+    }
+    double val = res * S.cm;
+    int ev = er + S.ecm;
+    if (p == 1) val *= sqrt(2.0 * m + 3.0) * xi;  // P-bar^m_{m+1} = sqrt(2m+3) x P-bar^m_m
+    renorm(val, ev);
+    V.ga[i] = 0.0;
+    V.gb[i] = val;
+    V.ge[i] = ev;
+  }
+}
+
+// One step of the recurrence for column j: returns the weighted value of
+// column j and advances (a, b, e) to column j + 1.  Products and sums are
+// rounded one by one, in the host's order.
+__device__ __forceinline__ double gen_step(const Views& V, int j, double x2, double sqw, double& a, double& b,
+                                           int& e) {
+  const double col = __dmul_rn(sqw, ldexp(b, e));
+  const double nb = __dmul_rn(__dsub_rn(__dmul_rn(__dsub_rn(x2, V.cd[j]), b), __dmul_rn(V.cm2[j], a)), V.cinv[j]);
+  a = b;
+  b = nb;
+  const double big = fmax(fabs(a), fabs(b));
+  if (big > 0x1p400 || (big < 0x1p-400 && big > 0.0)) {
+    const int t = ilogb(big);
+    a = ldexp(a, -t);
+    b = ldexp(b, -t);
+    e += t;
+  }
+  return col;
+}
+
+// Columns j0 .. j0 + w - 1 into out (rows x w, column-major).
+__device__ void gen_cols(const Views& V, int j0, int w, int rows, double* out) {
+  for (int i = threadIdx.x; i < rows; i += kThreads) {
+    const double x2 = V.x2[i], sqw = V.sqw[i];
+    double a = V.ga[i], b = V.gb[i];
+    int e = V.ge[i];
+    for (int j = 0; j < w; ++j) out[(size_t)j * rows + i] = gen_step(V, j0 + j, x2, sqw, a, b, e);
+    V.ga[i] = a;
+    V.gb[i] = b;
+    V.ge[i] = e;
+  }
+}
+
+// Column-pivoted Householder QR of the h x w column-major W (destroyed) to
+// threshold eps2 on the squared residual column norms, the host's
+// interp_decomp step for step.  Returns the rank k; perm holds the column
+// order (skeleton first).  Every thread returns the same k.
+__device__ int cta_cpqr(double* W, int h, int w, double eps2, const Views& V, Shared& S) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double *nrm = V.nrm, *ref = V.ref, *v = V.v;
+  int* perm = V.perm;
+  for (int j = tid; j < w; j += kThreads) perm[j] = j;
+  for (int j = warp; j < w; j += kWarps) {
+    const double* c = W + (size_t)j * h;
+    double s = 0.0;
+    for (int r = lane; r < h; r += 32) s = fma(c[r], c[r], s);
+    s = warp_sum(s);
+    if (lane == 0) nrm[j] = ref[j] = s;
+  }
+  __syncthreads();
+  const int kmax = min(h, w);
+  int k = 0;
+  for (int i = 0; i < kmax; ++i) {
+    int p = block_argmax(nrm, i, w, S);
+    double e = 0.0;
+    {
+      const double* c = W + (size_t)p * h;
+      for (int r = i + tid; r < h; r += kThreads) e = fma(c[r], c[r], e);
+    }
+    e = block_sum(e, S);
+    if (e <= eps2) {
+      // the downdated norms may have drifted: recompute all before stopping
+      for (int j = i + warp; j < w; j += kWarps) {
+        const double* c = W + (size_t)j * h;
+        double s = 0.0;
+        for (int r = i + lane; r < h; r += 32) s = fma(c[r], c[r], s);
+        s = warp_sum(s);
+        if (lane == 0) nrm[j] = ref[j] = s;
+      }
+      __syncthreads();
+      p = block_argmax(nrm, i, w, S);
+      e = nrm[p];
+      if (e <= eps2) break;
+    }
+    __syncthreads();  // every thread has read nrm[p]
+    if (tid == 0) nrm[p] = e;
+    if (p != i) {
+      double* ci = W + (size_t)i * h;
+      double* cp = W + (size_t)p * h;
+      for (int r = tid; r < h; r += kThreads) {
+        const double t = ci[r];
+        ci[r] = cp[r];
+        cp[r] = t;
+      }
+      if (tid == 0) {
+        const double tn = nrm[i], tr = ref[i];
+        nrm[i] = nrm[p];
+        ref[i] = ref[p];
+        nrm[p] = tn;
+        ref[p] = tr;
+        const int tp = perm[i];
+        perm[i] = perm[p];
+        perm[p] = tp;
+      }
+    }
+    __syncthreads();
+    // Householder reflector for W[i:h, i]
+    double* ci = W + (size_t)i * h;
+    const double alpha = ci[i];
+    double sg = 0.0;
+    for (int r = i + 1 + tid; r < h; r += kThreads) sg = fma(ci[r], ci[r], sg);
+    const double sigma = block_sum(sg, S);  // its barriers order the reads of alpha before the write below
+    double tau = 0.0;
+    if (sigma != 0.0 || alpha < 0.0) {
+      const double nx = sqrt(alpha * alpha + sigma);
+      const double beta = (alpha <= 0.0) ? nx : -nx;
+      tau = (beta - alpha) / beta;
+      const double sc = 1.0 / (alpha - beta);
+      for (int r = i + 1 + tid; r < h; r += kThreads) {
+        const double t = ci[r] * sc;
+        ci[r] = t;
+        v[r] = t;
+      }
+      if (tid == 0) ci[i] = beta;
+    }
+    __syncthreads();
+    // apply it to the trailing columns and downdate their norms, one warp
+    // per column (lane r reads and writes only its own rows)
+    for (int j = i + 1 + warp; j < w; j += kWarps) {
+      double* cj = W + (size_t)j * h;
+      double rij = cj[i];
+      if (tau != 0.0) {
+        double d = 0.0;
+        for (int r = i + 1 + lane; r < h; r += 32) d = fma(v[r], cj[r], d);
+        d = (warp_sum(d) + rij) * tau;
+        for (int r = i + 1 + lane; r < h; r += 32) cj[r] = fma(-d, v[r], cj[r]);
+        rij -= d;
+        if (lane == 0) cj[i] = rij;
+      }
+      double nj = nrm[j] - rij * rij;
+      if (nj < 1e-4 * ref[j]) {
+        double s = 0.0;
+        for (int r = i + 1 + lane; r < h; r += 32) s = fma(cj[r], cj[r], s);
+        nj = warp_sum(s);
+        if (lane == 0) ref[j] = nj;
+      }
+      __syncwarp();
+      if (lane == 0) nrm[j] = nj;
+    }
+    __syncthreads();
+    k = i + 1;
+  }
+  return k;
+}
+
+// Reserves one record; every thread learns whether it fit.
+__device__ unsigned char* reserve(const DevBuildArgs& A, long long bytes, Shared& S) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long off = -1;
+    if (*(volatile int*)A.stop == 0) {
+      const unsigned long long o = atomicAdd(A.arena_used, (unsigned long long)bytes);
+      if (o + (unsigned long long)bytes <= A.arena_bytes) {
+        off = (long long)o;
+      } else {
+        atomicMin(A.arena_fail, o);
+        atomicExch(A.stop, 1);
+      }
+    }
+    S.rec_off = off;
+  }
+  __syncthreads();
+  return S.rec_off < 0 ? nullptr : A.arena + S.rec_off;
+}
+
+__device__ __forceinline__ long long pad16(long long b) { return (b + 15) & ~15LL; }
+
+__device__ __forceinline__ long long block_record_bytes(int nin, int k) {
+  return pad16((long long)sizeof(RecHdr) + pad16(4LL * nin) + 8LL * k * (nin - k));
+}
+
+// Writes the record of one ID block: the skeleton, the redundant columns in
+// ascending order and T = R11^{-1} R12 by back substitution, each column of T
+// placed at the position of its column in that order.
+__device__ void write_block(unsigned char* rec, int unit, int level, int band, int group, int r0, int r1,
+                            int in_off, int nin, int k, const double* W, int h, const Views& V) {
+  RecHdr* H = reinterpret_cast<RecHdr*>(rec);
+  if (threadIdx.x == 0) {
+    RecHdr t{};
+    t.unit = unit;
+    t.kind = 0;
+    t.level = level;
+    t.band = band;
+    t.group = group;
+    t.r0 = r0;
+    t.r1 = r1;
+    t.in_off = in_off;
+    t.nin = nin;
+    t.k = k;
+    t.bytes = block_record_bytes(nin, k);
+    *H = t;
+  }
+  int* skel = reinterpret_cast<int*>(rec + sizeof(RecHdr));
+  int* red = skel + k;
+  double* T = reinterpret_cast<double*>(rec + sizeof(RecHdr) + pad16(4LL * nin));
+  const int* perm = V.perm;
+  for (int t = threadIdx.x; t < k; t += kThreads) skel[t] = perm[t];
+  const int nred = nin - k;
+  for (int s = threadIdx.x; s < nred; s += kThreads) {
+    const int c = perm[k + s];
+    int rank = 0;
+    for (int s2 = 0; s2 < nred; ++s2) rank += perm[k + s2] < c;
+    red[rank] = c;
+    const double* rc = W + (size_t)(k + s) * h;
+    double* tc = T + (size_t)rank * k;
+    for (int t = k - 1; t >= 0; --t) {
+      double x = rc[t];
+      for (int t2 = t + 1; t2 < k; ++t2) x = fma(-W[(size_t)t2 * h + t], tc[t2], x);
+      tc[t] = x / W[(size_t)t * h + t];
+    }
+  }
+}
+
+// Builds unit u; returns its status.
+__device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int u) {
+  const int m = u >> 1, p = u & 1, l = A.l, L = 2 * l, tid = threadIdx.x;
+  const int n = max(0, (L - m - p + 1) / 2);
+  long long* info = A.info + 3LL * u;
+  if (n == 0) {
+    if (tid == 0) info[0] = info[1] = info[2] = 0;
+    return kDone;
+  }
+  // recurrence coefficients of the n columns, and c_m with
+  // P-bar^m_m(x) = c_m (1 - x^2)^{m/2}
+  for (int j = tid; j < n; j += kThreads) {
+    const int k = m + p + 2 * j;
+    V.cinv[j] = 1.0 / rec_c(k, m);
+    V.cd[j] = rec_d(k, m);
+    V.cm2[j] = j > 0 ? rec_c(k - 2, m) : 0.0;
+  }
+  if (tid == 0) {
+    double cm = 1.0 / sqrt(2.0);
+    int ecm = 0;
+    for (int j = 1; j <= m; ++j) {
+      cm *= sqrt((2.0 * j + 1.0) / (2.0 * j));
+      renorm(cm, ecm);
+    }
+    S.cm = cm;
+    S.ecm = ecm;
+  }
+  __syncthreads();
+
+  // trimming: keep rows up to the last whose weighted norm reaches the threshold
+  int rows = l;
+  if (A.trim2 > 0.0) {
+    gen_init(A, V, S, m, p, l);
+    int last = 0;
+    for (int i = tid; i < l; i += kThreads) {
+      const double x2 = V.x2[i], sqw = V.sqw[i];
+      double a = V.ga[i], b = V.gb[i];
+      int e = V.ge[i];
+      double nr = 0.0;
+      for (int j = 0; j < n; ++j) {
+        const double c = gen_step(V, j, x2, sqw, a, b, e);
+        nr = __dadd_rn(nr, __dmul_rn(c, c));
+      }
+      if (nr >= A.trim2) last = i + 1;
+    }
+    rows = block_max_int(last, S);
+  }
+  if (rows == 0) {
+    if (tid == 0) {
+      info[0] = 0;
+      info[1] = 0;
+      info[2] = 0;
+    }
+    return kDone;
+  }
+  const int C = A.C;
+  int lam = 0;
+  while ((n >> lam) > C) ++lam;
+  if (n > C && (n + (1 << lam) - 1) / (1 << lam) > C) ++lam;
+  while (lam > 0 && (rows >> lam) < A.min_band_rows) --lam;
+  if (lam + 2 > kMaxGroups) return kNoScratch;
+  const int nleaves = 1 << lam;
+
+  __syncthreads();
+  gen_init(A, V, S, m, p, rows);
+  __syncthreads();
+  if (tid == 0) S.ngrp = 0;
+  long long sp = 0, peak = 0;
+  int ndesc = 0;
+  for (int g = 0; g < nleaves; ++g) {
+    const int c0 = (int)((long long)g * n / nleaves), c1 = (int)((long long)(g + 1) * n / nleaves);
+    const int wd = c1 - c0;
+    if ((long long)rows * wd > A.buf_words || wd > l) return kNoScratch;
+    gen_cols(V, c0, wd, rows, V.bufZ);
+    __syncthreads();
+    for (long long t = tid; t < (long long)rows * wd; t += kThreads) V.bufW[t] = V.bufZ[t];
+    __syncthreads();
+    const int k = cta_cpqr(V.bufW, rows, wd, A.eps2, V, S);
+    unsigned char* rec = reserve(A, block_record_bytes(wd, k), S);
+    if (!rec) return kNoArena;
+    write_block(rec, u, 1, 0, g, 0, rows, c0, wd, k, V.bufW, rows, V);
+    if (sp + (long long)rows * k > A.stack_words || ndesc + 1 > A.desc_cap) return kNoScratch;
+    for (long long t = tid; t < (long long)rows * k; t += kThreads) {
+      const int c = (int)(t / rows), i = (int)(t - (long long)c * rows);
+      V.stack[sp + t] = V.bufZ[(size_t)V.perm[c] * rows + i];
+    }
+    if (tid == 0) {
+      V.desc[ndesc] = BandDesc{0, rows, k, 0, sp};
+      S.grp[S.ngrp] = GroupDesc{1, g, 1, ndesc};
+      S.ngrp += 1;
+    }
+    sp += (long long)rows * k;
+    ndesc += 1;
+    peak = max(peak, sp + 2LL * rows * wd);
+    __syncthreads();
+
+    while (S.ngrp >= 2 && S.grp[S.ngrp - 1].level == S.grp[S.ngrp - 2].level) {
+      const GroupDesc Lg = S.grp[S.ngrp - 2], Rg = S.grp[S.ngrp - 1];
+      const int j = Lg.level, nb = Lg.nb, ng = Lg.g / 2;
+      const long long base = sp;
+      const int d_new = ndesc;
+      if (ndesc + 2 * nb > A.desc_cap) return kNoScratch;
+      for (int beta = 0; beta < nb; ++beta) {
+        const BandDesc BL = V.desc[Lg.d0 + beta], BR = V.desc[Rg.d0 + beta];
+        const int h = BL.r1 - BL.r0, mid = BL.r0 + h / 2, kin = BL.k + BR.k;
+        for (int half = 0; half < 2; ++half) {
+          const int rr0 = half ? mid : BL.r0, rr1 = half ? BL.r1 : mid, hh = rr1 - rr0;
+          if ((long long)hh * kin > A.buf_words || kin > l) return kNoScratch;
+          // Z = [rows rr0..rr1 of the left band's skeleton columns, then the right's]
+          for (long long t = tid; t < (long long)hh * kin; t += kThreads) {
+            const int c = (int)(t / hh), i = (int)(t - (long long)c * hh);
+            const double z = c < BL.k ? V.stack[BL.off + (long long)c * h + (rr0 - BL.r0) + i]
+                                      : V.stack[BR.off + (long long)(c - BL.k) * h + (rr0 - BL.r0) + i];
+            V.bufZ[t] = z;
+            V.bufW[t] = z;
+          }
+          __syncthreads();
+          const int k = cta_cpqr(V.bufW, hh, kin, A.eps2, V, S);
+          unsigned char* rec = reserve(A, block_record_bytes(kin, k), S);
+          if (!rec) return kNoArena;
+          write_block(rec, u, j + 1, 2 * beta + half, ng, rr0, rr1, 0, kin, k, V.bufW, hh, V);
+          if (sp + (long long)hh * k > A.stack_words) return kNoScratch;
+          for (long long t = tid; t < (long long)hh * k; t += kThreads) {
+            const int c = (int)(t / hh), i = (int)(t - (long long)c * hh);
+            V.stack[sp + t] = V.bufZ[(size_t)V.perm[c] * hh + i];
+          }
+          if (tid == 0) V.desc[ndesc] = BandDesc{rr0, rr1, k, 0, sp};
+          sp += (long long)hh * k;
+          ndesc += 1;
+          __syncthreads();
+        }
+      }
+      // the new group replaces L and R: move its columns and descriptors down
+      // (its words never exceed theirs: each new band keeps k <= kin columns
+      // of half the rows, so source and destination do not overlap)
+      const long long dst = V.desc[Lg.d0].off, words = sp - base, gap = base - dst;
+      if (words > gap) return kNoScratch;
+      for (long long t = tid; t < words; t += kThreads) V.stack[dst + t] = V.stack[base + t];
+      for (int t = tid; t < 2 * nb; t += kThreads) {
+        BandDesc d = V.desc[d_new + t];
+        d.off -= gap;
+        V.desc[Lg.d0 + t] = d;
+      }
+      __syncthreads();
+      sp = dst + words;
+      ndesc = Lg.d0 + 2 * nb;
+      peak = max(peak, sp);
+      if (tid == 0) {
+        S.grp[S.ngrp - 2] = GroupDesc{j + 1, ng, 2 * nb, Lg.d0};
+        S.ngrp -= 1;
+      }
+      __syncthreads();
+    }
+  }
+  if (S.ngrp != 1) return kNoScratch;
+  // the top level's bands: their stored skeleton columns are the final blocks
+  const GroupDesc top = S.grp[0];
+  for (int beta = 0; beta < top.nb; ++beta) {
+    const BandDesc B = V.desc[top.d0 + beta];
+    const long long words = (long long)(B.r1 - B.r0) * B.k;
+    const long long bytes = pad16((long long)sizeof(RecHdr) + 8 * words);
+    unsigned char* rec = reserve(A, bytes, S);
+    if (!rec) return kNoArena;
+    if (tid == 0) {
+      RecHdr t{};
+      t.unit = u;
+      t.kind = 1;
+      t.band = beta;
+      t.r0 = B.r0;
+      t.r1 = B.r1;
+      t.k = B.k;
+      t.bytes = bytes;
+      *reinterpret_cast<RecHdr*>(rec) = t;
+    }
+    double* Sv = reinterpret_cast<double*>(rec + sizeof(RecHdr));
+    for (long long t = tid; t < words; t += kThreads) Sv[t] = V.stack[B.off + t];
+  }
+  if (tid == 0) {
+    info[0] = rows;
+    info[1] = lam;
+    info[2] = peak;
+  }
+  return kDone;
+}
+
+__global__ void __launch_bounds__(kThreads, 4) factor_units_kernel(DevBuildArgs A) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ Shared S;
+  const int l = A.l;
+  Views V;
+  V.cinv = reinterpret_cast<double*>(dyn);
+  V.cd = V.cinv + l;
+  V.cm2 = V.cd + l;
+  V.nrm = V.cm2 + l;
+  V.ref = V.nrm + l;
+  V.v = V.ref + l;
+  V.perm = reinterpret_cast<int*>(V.v + l);
+  double* g = A.scratch + (long long)blockIdx.x * A.scratch_words;
+  V.x2 = g;
+  V.sqw = g + l;
+  V.ga = g + 2 * l;
+  V.gb = g + 3 * l;
+  V.ge = reinterpret_cast<int*>(g + 4 * l);
+  V.desc = reinterpret_cast<BandDesc*>(g + 5 * l);
+  V.bufZ = g + 5 * l + 3 * A.desc_cap;
+  V.bufW = V.bufZ + A.buf_words;
+  V.stack = V.bufW + A.buf_words;
+  for (;;) {
+    if (threadIdx.x == 0) S.q = (*(volatile int*)A.stop) ? A.n_queue : (int)atomicAdd(A.next, 1u);
+    __syncthreads();
+    const int q = S.q;
+    __syncthreads();
+    if (q >= A.n_queue) break;
+    const int u = A.queue[q];
+    const int st = build_unit(A, V, S, u);
+    __syncthreads();
+    if (threadIdx.x == 0) A.status[u] = st;
+  }
+}
+
+size_t dyn_smem(int l) { return (size_t)l * (6 * sizeof(double) + sizeof(int)); }
+
+int leaf_levels(int n, int rows, int C, int mbr) {
+  int lam = 0;
+  while ((n >> lam) > C) ++lam;
+  if (n > C && (n + (1 << lam) - 1) / (1 << lam) > C) ++lam;
+  while (lam > 0 && (rows >> lam) < mbr) --lam;
+  return lam;
+}
+
+struct CudaBuf {
+  void* p = nullptr;
+  ~CudaBuf() { cudaFree(p); }
+};
+
+void check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) throw std::runtime_error(std::string("device build: ") + what + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+void build_factorizations_device(PlanHost& P, bool fp32, int device) {
+  const int l = P.l, L = 2 * l, C = P.leaf_cols, mbr = P.min_band_rows;
+  const double eps = fp32 ? P.eps_fp32 : P.eps_id;
+  std::vector<UnitFact>& out = fp32 ? P.fact32 : P.fact64;
+  out.assign((size_t)L * 2, UnitFact());
+  check(cudaSetDevice(device), "cudaSetDevice");
+
+  // Scratch bounds per CTA, over every unit and every number of kept rows:
+  // leaf and merge blocks hold at most (rows + 2^lam) x (leaf width) values;
+  // the stack holds one group per level, a group at level j at most
+  // rows x min(rows / 2^(j-1) + 1, 2^(j-1) x leaf width), plus the group
+  // being merged.
+  long long buf_words = 1, stack_words = 1;
+  int max_lam = 0;
+  for (int n = 1; n <= l; ++n) {
+    const int lam0 = leaf_levels(n, l, C, 0);
+    for (int lam = 0; lam <= lam0; ++lam) {
+      // the most rows for which the band rule leaves lam levels
+      long long rows = l;
+      if (lam < lam0 && mbr > 0) rows = std::min<long long>(l, (long long)mbr << (lam + 1));
+      const long long wd = (n + (1LL << lam) - 1) >> lam;
+      buf_words = std::max(buf_words, (rows + (1LL << lam)) * wd);
+      long long sum = 0, gmax = 0;
+      for (int j = 1; j <= lam + 1; ++j) {
+        const long long gj = rows * std::min(((rows + (1LL << (j - 1)) - 1) >> (j - 1)) + 1, (1LL << (j - 1)) * wd);
+        sum += gj;
+        gmax = std::max(gmax, gj);
+      }
+      stack_words = std::max(stack_words, sum + gmax);
+      max_lam = std::max(max_lam, lam);
+    }
+  }
+  const long long desc_cap = 3LL << (max_lam + 1);
+  const long long scratch_words = 5LL * l + 3 * desc_cap + 2 * buf_words + stack_words;
+
+  int sms = 0;
+  check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "SM count");
+  const size_t smem = dyn_smem(l);
+  check(cudaFuncSetAttribute(factor_units_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        "shared memory limit");
+  int per_sm = 0;
+  check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, factor_units_kernel, kThreads, smem), "occupancy");
+  per_sm = std::max(1, std::min(per_sm, 4));
+  size_t free_b = 0, total_b = 0;
+  check(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+  long long ctas = std::min<long long>((long long)sms * per_sm, 2LL * L);
+  // scratch at most a quarter of the free memory
+  ctas = std::min<long long>(ctas, (long long)(free_b / 4 / (8 * (size_t)scratch_words)));
+  if (ctas < 1) throw std::runtime_error("device build: not enough device memory for one CTA's scratch");
+  // arena: half the dense operator (the butterflies store about a third of
+  // it at eps_id = 1e-12), at most a quarter of the free memory
+  long long dense = 0;
+  for (int m = 0; m < L; ++m)
+    for (int p = 0; p < 2; ++p) dense += (long long)l * std::max(0, (L - m - p + 1) / 2);
+  unsigned long long arena_bytes =
+      std::min<unsigned long long>(4ULL * dense + (64ULL << 20), free_b / 4);
+  arena_bytes &= ~15ULL;
+
+  // node data, as the host's column generator computes it
+  std::vector<double> xpos(l), spos(l), sq2w(l);
+  for (int i = 0; i < l; ++i) {
+    xpos[i] = P.x[l + i];
+    spos[i] = std::sin(P.theta_pos[i]);
+    sq2w[i] = std::sqrt(2.0 * P.w[l + i]);
+  }
+  std::vector<int> order(2 * L);
+  for (int u = 0; u < 2 * L; ++u) order[u] = u;
+  std::stable_sort(order.begin(), order.end(), [](int a, int b) { return (a / 2) < (b / 2); });
+
+  CudaBuf d_nodes, d_queue, d_ctl, d_status, d_info, d_scratch, d_arena;
+  check(cudaMalloc(&d_nodes.p, 3 * sizeof(double) * l), "cudaMalloc nodes");
+  check(cudaMalloc(&d_queue.p, sizeof(int) * 2 * L), "cudaMalloc queue");
+  check(cudaMalloc(&d_ctl.p, 64), "cudaMalloc control");
+  check(cudaMalloc(&d_status.p, sizeof(int) * 2 * L), "cudaMalloc status");
+  check(cudaMalloc(&d_info.p, sizeof(long long) * 3 * 2 * L), "cudaMalloc info");
+  check(cudaMalloc(&d_scratch.p, 8 * (size_t)scratch_words * ctas), "cudaMalloc scratch");
+  check(cudaMalloc(&d_arena.p, arena_bytes), "cudaMalloc arena");
+  double* dn = static_cast<double*>(d_nodes.p);
+  check(cudaMemcpy(dn, xpos.data(), 8 * l, cudaMemcpyHostToDevice), "copy nodes");
+  check(cudaMemcpy(dn + l, spos.data(), 8 * l, cudaMemcpyHostToDevice), "copy nodes");
+  check(cudaMemcpy(dn + 2 * l, sq2w.data(), 8 * l, cudaMemcpyHostToDevice), "copy nodes");
+  check(cudaMemset(d_status.p, 0, sizeof(int) * 2 * L), "clear status");
+
+  DevBuildArgs A{};
+  A.l = l;
+  A.C = C;
+  A.min_band_rows = mbr;
+  A.eps2 = eps * eps;
+  const double thr = P.trim_eps > 0.0 ? P.trim_eps / std::sqrt((double)l) : 0.0;
+  A.trim2 = thr * thr;
+  A.xpos = dn;
+  A.spos = dn + l;
+  A.sq2w = dn + 2 * l;
+  A.queue = static_cast<int*>(d_queue.p);
+  unsigned char* ctl = static_cast<unsigned char*>(d_ctl.p);
+  A.next = reinterpret_cast<unsigned*>(ctl);
+  A.stop = reinterpret_cast<int*>(ctl + 4);
+  A.arena_used = reinterpret_cast<unsigned long long*>(ctl + 8);
+  A.arena_fail = reinterpret_cast<unsigned long long*>(ctl + 16);
+  A.scratch = static_cast<double*>(d_scratch.p);
+  A.scratch_words = scratch_words;
+  A.buf_words = buf_words;
+  A.stack_words = stack_words;
+  A.desc_cap = desc_cap;
+  A.arena = static_cast<unsigned char*>(d_arena.p);
+  A.arena_bytes = arena_bytes;
+  A.status = static_cast<int*>(d_status.p);
+  A.info = static_cast<long long*>(d_info.p);
+
+  std::vector<int> status(2 * L, kPending);
+  std::vector<long long> info(3 * 2 * L);
+  std::vector<unsigned char> host;
+  std::vector<int> pending = order;
+  while (!pending.empty()) {
+    check(cudaMemcpy(d_queue.p, pending.data(), sizeof(int) * pending.size(), cudaMemcpyHostToDevice), "queue");
+    struct {
+      unsigned next;
+      int stop;
+      unsigned long long used, fail;
+    } c0{0, 0, 0, ~0ULL};
+    check(cudaMemcpy(ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice), "control");
+    A.n_queue = (int)pending.size();
+    const int grid = (int)std::min<long long>(ctas, (long long)pending.size());
+    factor_units_kernel<<<grid, kThreads, smem>>>(A);
+    check(cudaGetLastError(), "launch");
+    check(cudaDeviceSynchronize(), "factor_units_kernel");
+    check(cudaMemcpy(status.data(), d_status.p, sizeof(int) * 2 * L, cudaMemcpyDeviceToHost), "status");
+    check(cudaMemcpy(info.data(), d_info.p, sizeof(long long) * 3 * 2 * L, cudaMemcpyDeviceToHost), "info");
+    check(cudaMemcpy(&c0, ctl, sizeof(c0), cudaMemcpyDeviceToHost), "control");
+    for (int u : pending)
+      if (status[u] == kNoScratch)
+        throw std::runtime_error("device build: unit " + std::to_string(u) + " exceeded its scratch bound");
+    const unsigned long long limit = std::min(c0.used, std::min(c0.fail, arena_bytes));
+    host.resize(limit);
+    if (limit) check(cudaMemcpy(host.data(), d_arena.p, limit, cudaMemcpyDeviceToHost), "arena");
+
+    // records of the units finished in this wave, in emission order
+    std::vector<std::vector<size_t>> recs(2 * L);
+    for (unsigned long long off = 0; off + sizeof(RecHdr) <= limit;) {
+      RecHdr h;
+      std::memcpy(&h, host.data() + off, sizeof h);
+      if (h.bytes < (long long)sizeof(RecHdr) || off + (unsigned long long)h.bytes > limit || h.unit < 0 ||
+          h.unit >= 2 * L)
+        throw std::runtime_error("device build: corrupt record at offset " + std::to_string(off));
+      if (status[h.unit] == kDone) recs[h.unit].push_back(off);
+      off += (unsigned long long)h.bytes;
+    }
+    std::vector<int> done, next_wave;
+    for (int u : pending) (status[u] == kDone ? done : next_wave).push_back(u);
+    if (done.empty()) throw std::runtime_error("device build: the output arena cannot hold one unit");
+
+    std::atomic<int> cursor(0);
+    int nt = P.num_threads > 0 ? P.num_threads : (int)std::thread::hardware_concurrency();
+    nt = std::max(1, std::min(nt, 256));
+    std::vector<std::string> errors(nt);
+    auto worker = [&](int tid) {
+      try {
+        for (;;) {
+          const int q = cursor.fetch_add(1);
+          if (q >= (int)done.size()) break;
+          const int u = done[q];
+          UnitFact U;
+          U.m = u / 2;
+          U.p = u % 2;
+          U.n = std::max(0, (L - U.m - U.p + 1) / 2);
+          U.rows = (int)info[3 * u];
+          U.levels = (int)info[3 * u + 1];
+          U.peak_words = info[3 * u + 2];
+          std::vector<FinalBlock> top;
+          for (size_t off : recs[u]) {
+            RecHdr h;
+            std::memcpy(&h, host.data() + off, sizeof h);
+            const unsigned char* body = host.data() + off + sizeof(RecHdr);
+            if (h.kind == 0) {
+              IdBlock b;
+              b.level = h.level;
+              b.band = h.band;
+              b.group = h.group;
+              b.r0 = h.r0;
+              b.r1 = h.r1;
+              b.in_off = h.in_off;
+              b.nin = h.nin;
+              b.k = h.k;
+              const int* ix = reinterpret_cast<const int*>(body);
+              b.skel.assign(ix, ix + h.k);
+              b.red.assign(ix + h.k, ix + h.nin);
+              b.T.resize((size_t)h.k * (h.nin - h.k));
+              std::memcpy(b.T.data(), body + ((4LL * h.nin + 15) & ~15LL), 8 * b.T.size());
+              U.blocks.push_back(std::move(b));
+            } else {
+              FinalBlock f;
+              f.band = h.band;
+              f.r0 = h.r0;
+              f.r1 = h.r1;
+              f.k = h.k;
+              f.S.resize((size_t)(h.r1 - h.r0) * h.k);
+              std::memcpy(f.S.data(), body, 8 * f.S.size());
+              top.push_back(std::move(f));
+            }
+          }
+          if (U.n > 0 && U.rows > 0) finish_unit(P, U, std::move(top));
+          out[u] = std::move(U);
+        }
+      } catch (const std::exception& e) {
+        errors[tid] = e.what();
+        cursor.store((int)done.size());
+      }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(worker, t);
+    worker(0);
+    for (auto& t : th) t.join();
+    for (auto& e : errors)
+      if (!e.empty()) throw std::runtime_error(e);
+    pending.swap(next_wave);
+  }
+}
+
+}  // namespace sht

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "recurrence.h"
 #include "sht_stream.h"
 
 namespace sht {
@@ -93,17 +94,6 @@ struct PlanHost {
   double t_quad = 0, t_comp = 0;
 };
 
-// Coefficients of the x^2 recurrence x^2 P-bar^m_k = c_{k-2} P-bar^m_{k-2}
-// + d_k P-bar^m_k + c_k P-bar^m_{k+2} (Section 2.3, eqs. c_rec, d_rec).
-inline double rec_c(int k, int m) {
-  const double a = (double)(k - m + 1) * (k - m + 2) * (double)(k + m + 1) * (k + m + 2);
-  const double b = (2.0 * k + 1.0) * (2.0 * k + 3.0) * (2.0 * k + 3.0) * (2.0 * k + 5.0);
-  return std::sqrt(a / b);
-}
-inline double rec_d(int k, int m) {
-  return (2.0 * k * (k + 1.0) - 2.0 * (double)m * m - 1.0) / ((2.0 * k - 1.0) * (2.0 * k + 3.0));
-}
-
 // The n positive zeros x_i of P-bar^m_{m+p+2n} (Section 4, Lemma zeros),
 // their angles, and the weights rho_i of the Gauss-Jacobi-type quadrature
 // of Lemma quadratures (for p = 1 the sigma_i of eq. weights2, i < n).
@@ -137,6 +127,13 @@ class ColumnStream {
 int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm,
                   std::vector<double>& T);
 
+// Completes a unit whose ID blocks (level, band, group, rows, leaf input
+// offsets, ranks, skeletons, interpolation matrices), rows, n and levels are
+// set: lays out each level, links merge blocks to their children, appends the
+// top level's bands (band, rows, k, S) as final blocks, counts values and
+// indices, and stores the unit dense when that is cheaper.
+void finish_unit(const PlanHost& P, UnitFact& U, std::vector<FinalBlock>&& top);
+
 // Factorization of the one parity block (m, p) with threshold eps (Section 3,
 // depth-first); P needs only l, the nodes and the build options.
 UnitFact factor_single_unit(const PlanHost& P, int m, int p, double eps);
@@ -144,6 +141,10 @@ UnitFact factor_single_unit(const PlanHost& P, int m, int p, double eps);
 // Builds the factorization of every parity block with threshold eps
 // (Section 3, depth-first).  fp32 selects fact32 instead of fact64.
 void build_factorizations(PlanHost& P, bool fp32);
+
+// As build_factorizations, computed on CUDA device `device` (plan_device.cu);
+// throws std::runtime_error if the device fails or a bound is exceeded.
+void build_factorizations_device(PlanHost& P, bool fp32, int device);
 
 // Encodes one precision's factor streams (both directions) into pages.
 void emit_streams(PlanHost& P, int prec);
