@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--consumer-warps", type=int, default=0)
     ap.add_argument("--eps", type=float, default=1e-12)
     ap.add_argument("--no-extras", action="store_true", help="skip every leg beside the float64 headline")
-    ap.add_argument("--paths", default="split32,split32acc64,fp32,direct,full,batched,autograd",
+    ap.add_argument("--paths", default="split32,split32acc64,fp32,direct,full,batched,autograd,device_build",
                     help="comma-separated legs to run beside the headline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--batch-fields", type=int, default=96,
@@ -73,6 +73,32 @@ def sweep_sources_sha():
         with open(os.path.join(ROOT, "paper_0910_5435_gb300", "csrc", name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
+
+
+def device_build_leg(args, sht, torch, dev, stream, plan, st, beta):
+    """The same plan with its factorizations built on the GPU: build time
+    beside the host build's, rank statistics, and the two plans' float64
+    syntheses of the bench field compared."""
+    l = plan.l
+    t0 = time.perf_counter()
+    pd = sht.Plan(l, args.eps, leaf_cols=args.leaf_cols, page_bytes=args.page_bytes,
+                  consumer_warps=args.consumer_warps, device_build=True)
+    t_plan = time.perf_counter() - t0
+    sd = pd.stats()
+    gh = torch.empty((2 * l, 2 * l), dtype=torch.complex128, device=dev)
+    gd = torch.empty_like(gh)
+    sht.sht_legendre_synthesize(plan, sht.SHT_FP64, beta, gh, stream)
+    sht.sht_legendre_synthesize(pd, sht.SHT_FP64, beta, gd, stream)
+    torch.cuda.synchronize()
+    out = {"t_plan_s": t_plan, "t_comp": sd["t_comp"], "t_factor": sd["t_factor"],
+           "t_factor_kernel": sd["t_factor_kernel"], "host_t_comp": st["t_comp"], "host_t_factor": st["t_factor"],
+           "factor_speedup_vs_host": st["t_factor"] / max(1e-9, sd["t_factor"]),
+           "k_avg": sd["k_avg"], "k_max": sd["k_max"], "factor_values": sd["factor_values"],
+           "host_factor_values": st["factor_values"],
+           "rel_synthesis_vs_host_plan": float(torch.linalg.vector_norm(gd - gh) / torch.linalg.vector_norm(gh)),
+           "device_status": int(sht.sht_last_device_status(pd))}
+    pd.close()
+    return out
 
 
 def shard_fields(ls, rank, world):
@@ -595,6 +621,8 @@ def main():
         extras["batched_split32"] = batched_leg(args, sht, inputs, torch, dev, stream, plan, rank, world, dist)
     if rank == 0 and "autograd" in legs:
         extras["autograd_l512_b16"] = autograd_leg(args, sht, inputs, torch, dev, stream)
+    if rank == 0 and "device_build" in legs:
+        extras["plan_device_build"] = device_build_leg(args, sht, torch, dev, stream, plan, st, beta)
 
     cpu = None
     rel = {}
@@ -632,7 +660,7 @@ def main():
             "plan": {"t_plan_s": t_plan, "k_max": st["k_max"], "k_avg": st["k_avg"], "k_sigma": st["k_sigma"],
                      "factor_values": st["factor_values"], "dense_values": st["dense_values"],
                      "rows_kept_frac": st["rows_kept"] / max(1, st["rows_total"]),
-                     "levels": st["max_levels"], "t_comp": st["t_comp"]},
+                     "levels": st["max_levels"], "t_comp": st["t_comp"], "t_factor": st["t_factor"]},
             "paths": extras,
         }
         if "direct_fp64" in extras:

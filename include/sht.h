@@ -171,6 +171,10 @@ typedef struct {
   long long m_max_words; /* peak float64 words held by one unit's depth-first build */
   int smem_bytes;        /* dynamic shared memory of the sweep kernels */
   int page_bytes;        /* bytes per factor page (the value in effect) */
+  double t_factor;       /* seconds of t_comp spent on the factorizations (the rest encodes
+                          * the streams) */
+  double t_factor_kernel; /* seconds of t_factor in the device builder's kernels (0 for a
+                           * host build) */
 } sht_plan_stats;
 
 /* Fills *opts with the defaults listed above. */

@@ -200,6 +200,8 @@ void fill_stats(sht_plan_t P) {
   s.stream_bytes_split32 = (long long)(H.streams[2][0].bytes.size() + H.streams[2][0].values.size());
   s.t_quad = H.t_quad;
   s.t_comp = H.t_comp;
+  s.t_factor = H.t_factor;
+  s.t_factor_kernel = H.t_factor_kernel;
   s.smem_bytes = (int)std::max({P->smem[0], P->smem[1], P->smem[2]});
   s.page_bytes = P->H.page_bytes;
 }
@@ -216,6 +218,7 @@ sht_status build_host(sht_plan_t P, int q) {
         sht::build_factorizations_device(H, fp32, P->device);
       else
         sht::build_factorizations(H, fp32);
+      H.t_factor += now_s() - t0;
     }
     sht::emit_streams(H, q);
     H.t_comp += now_s() - t0;

@@ -1256,43 +1256,57 @@ void emit_streams(PlanHost& P, int prec) {
     });
 
     Stream& S = P.streams[prec][dir];
-    S.bytes.clear();
-    S.values.clear();
     S.units.clear();
-    size_t pages = 0;
+    // offsets of every item in the joined page and value regions
+    std::vector<size_t> byte_off(items.size()), val_off(items.size());
+    size_t nbytes = 0, nvals = 0, pages = 0;
     for (int it : iorder) {
+      byte_off[it] = nbytes;
+      val_off[it] = nvals;
       UnitEntry e;
       e.first_page = pages;
       e.n_pages = (uint32_t)(item_bytes[it].size() / PB);
       e.m = (uint32_t)items[it][0];
       S.units.push_back(e);
-      // rebase the value references of this item onto the joined value region
-      const uint32_t base16 = (uint32_t)(S.values.size() / 16);
+      nbytes += item_bytes[it].size();
+      nvals += item_vals[it].size();
+      pages += e.n_pages;
+    }
+    if (nvals / 16 > 0xFFFFFFFFull) throw std::runtime_error("value region exceeds 64 GB");
+    std::vector<uint8_t>().swap(S.bytes);
+    std::vector<uint8_t>().swap(S.values);
+    S.bytes.resize(nbytes + PB);
+    S.values.resize(nvals);
+    // rebase each item's value references onto the joined value region and
+    // copy it into place, items in parallel
+    run_parallel((int)items.size(), [&](int it) {
+      const uint32_t base16 = (uint32_t)(val_off[it] / 16);
+      std::vector<uint8_t>& B = item_bytes[it];
       if (base16 && !item_vals[it].empty()) {
-        for (size_t pg = 0; pg < item_bytes[it].size() / PB; ++pg) {
-          uint8_t* page = item_bytes[it].data() + pg * PB;
+        for (size_t pg = 0; pg < B.size() / PB; ++pg) {
+          uint8_t* page = B.data() + pg * PB;
           for (size_t off : page_ops(page, PB)) {
             OpHdr* h = reinterpret_cast<OpHdr*>(page + off);
             if (h->flags & F_VALUES_APART) h->vref += base16;
           }
         }
       }
-      if (S.values.size() / 16 + item_vals[it].size() / 16 > 0xFFFFFFFFull)
-        throw std::runtime_error("value region exceeds 64 GB");
-      S.bytes.insert(S.bytes.end(), item_bytes[it].begin(), item_bytes[it].end());
-      S.values.insert(S.values.end(), item_vals[it].begin(), item_vals[it].end());
-      pages += e.n_pages;
-    }
+      if (!B.empty()) std::memcpy(S.bytes.data() + byte_off[it], B.data(), B.size());
+      if (!item_vals[it].empty())
+        std::memcpy(S.values.data() + val_off[it], item_vals[it].data(), item_vals[it].size());
+      std::vector<uint8_t>().swap(B);
+      std::vector<uint8_t>().swap(item_vals[it]);
+    });
     // trailing QUIT page: op count kQuitPage (and a single op of kind 0xFF)
     // ends the consumer loop
-    std::vector<uint8_t> quit((size_t)P.page_bytes, 0);
+    uint8_t* quit = S.bytes.data() + nbytes;
+    std::memset(quit, 0, PB);
     OpHdr q;
     std::memset(&q, 0, sizeof(q));
     q.bytes = sizeof(OpHdr);
     q.kind = OP_QUIT;
-    std::memcpy(quit.data(), &q, sizeof(q));
-    std::memcpy(quit.data() + PB - 2, &kQuitPage, 2);
-    S.bytes.insert(S.bytes.end(), quit.begin(), quit.end());
+    std::memcpy(quit, &q, sizeof(q));
+    std::memcpy(quit + PB - 2, &kQuitPage, 2);
     int mx = 0;
     for (int u = 0; u < L * 2; ++u) {
       mx = std::max(mx, F[u].n);

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <limits>
@@ -85,7 +86,8 @@ struct DevBuildArgs {
 
 struct Shared {
   GroupDesc grp[kMaxGroups];
-  double redv[kWarps];
+  double redv[kWarps], red2[kWarps];
+  long long redl[kWarps];
   int redi[kWarps];
   long long rec_off;
   int q, ngrp, ecm;
@@ -99,16 +101,37 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum over the CTA; every thread returns the same value.
+// Sum over the CTA; every thread returns the same value (the warps' partial
+// sums are combined by the same butterfly in every warp).
 __device__ double block_sum(double v, Shared& S) {
+  static_assert(kWarps == 8, "the final butterfly combines 8 warp sums");
   v = warp_sum(v);
   __syncthreads();
   if ((threadIdx.x & 31) == 0) S.redv[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
+  double s = S.redv[threadIdx.x & 7];
 #pragma unroll
-  for (int i = 0; i < kWarps; ++i) s += S.redv[i];
+  for (int o = 4; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
   return s;
+}
+
+// Two sums over the CTA at once.
+__device__ void block_sum2(double& x, double& y, Shared& S) {
+  x = warp_sum(x);
+  y = warp_sum(y);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    S.redv[threadIdx.x >> 5] = x;
+    S.red2[threadIdx.x >> 5] = y;
+  }
+  __syncthreads();
+  x = S.redv[threadIdx.x & 7];
+  y = S.red2[threadIdx.x & 7];
+#pragma unroll
+  for (int o = 4; o; o >>= 1) {
+    x += __shfl_xor_sync(kFull, x, o);
+    y += __shfl_xor_sync(kFull, y, o);
+  }
 }
 
 __device__ int block_max_int(int v, Shared& S) {
@@ -123,23 +146,27 @@ __device__ int block_max_int(int v, Shared& S) {
   return r;
 }
 
-__device__ __forceinline__ bool better(double a, int ia, double b, int ib) {
+__device__ __forceinline__ bool better(long long a, int ia, long long b, int ib) {
   return a > b || (a == b && ia < ib);
 }
 
 // Index of the largest x[j], i0 <= j < w, the lowest on ties (the host's
-// pivot rule); i0 if none compares larger than -inf.
+// pivot rule); i0 if there is none.  The x[j] are squared norms, never
+// negative, so their bit patterns order like their values and the search
+// runs on the integer pipes.
 __device__ int block_argmax(const double* x, int i0, int w, Shared& S) {
-  double best = -INFINITY;
+  long long best = -1;
   int bi = w;
-  for (int j = i0 + (int)threadIdx.x; j < w; j += kThreads)
-    if (x[j] > best) {
-      best = x[j];
+  for (int j = i0 + (int)threadIdx.x; j < w; j += kThreads) {
+    const long long b = __double_as_longlong(x[j]);
+    if (b > best) {
+      best = b;
       bi = j;
     }
+  }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    const double ob = __shfl_xor_sync(kFull, best, o);
+    const long long ob = __shfl_xor_sync(kFull, best, o);
     const int oi = __shfl_xor_sync(kFull, bi, o);
     if (better(ob, oi, best, bi)) {
       best = ob;
@@ -148,16 +175,16 @@ __device__ int block_argmax(const double* x, int i0, int w, Shared& S) {
   }
   __syncthreads();
   if ((threadIdx.x & 31) == 0) {
-    S.redv[threadIdx.x >> 5] = best;
+    S.redl[threadIdx.x >> 5] = best;
     S.redi[threadIdx.x >> 5] = bi;
   }
   __syncthreads();
-  best = S.redv[0];
+  best = S.redl[0];
   bi = S.redi[0];
 #pragma unroll
   for (int i = 1; i < kWarps; ++i)
-    if (better(S.redv[i], S.redi[i], best, bi)) {
-      best = S.redv[i];
+    if (better(S.redl[i], S.redi[i], best, bi)) {
+      best = S.redl[i];
       bi = S.redi[i];
     }
   return bi < w ? bi : i0;
@@ -183,53 +210,71 @@ struct Views {
   double *bufZ, *bufW, *stack;
 };
 
-// Generator state of rows 0..rows-1 at column 0: b = P-bar^m_{m+p}(x_i) as a
-// mantissa and exponent, a = 0 (eq. recurrence0 has no k - 2 term).
-__device__ void gen_init(const DevBuildArgs& A, const Views& V, const Shared& S, int m, int p, int rows) {
-  for (int i = threadIdx.x; i < rows; i += kThreads) {
-    const double xi = A.xpos[i];
-    V.x2[i] = xi * xi;
-    V.sqw[i] = A.sq2w[i];
-    // sin(theta)^m by binary powering with tracked exponents
-    int eb;
-    double base = frexp(A.spos[i], &eb);
-    double res = 1.0;
-    int er = 0;
-    for (int q = m; q; q >>= 1) {
-      if (q & 1) {
-        res *= base;
-        er += eb;
-        renorm(res, er);
-      }
-      base *= base;
-      eb *= 2;
-      renorm(base, eb);
+// Generator state of row i at column 0: b = P-bar^m_{m+p}(x_i) as a
+// mantissa b and exponent e, a = 0 (eq. recurrence0 has no k - 2 term).
+__device__ void row_init(const DevBuildArgs& A, const Shared& S, int m, int p, int i, double& x2, double& sqw,
+                         double& a, double& b, int& e) {
+  const double xi = A.xpos[i];
+  x2 = xi * xi;
+  sqw = A.sq2w[i];
+  // sin(theta)^m by binary powering with tracked exponents
+  int eb;
+  double base = frexp(A.spos[i], &eb);
+  double res = 1.0;
+  int er = 0;
+  for (int q = m; q; q >>= 1) {
+    if (q & 1) {
+      res *= base;
+      er += eb;
+      renorm(res, er);
     }
-    double val = res * S.cm;
-    int ev = er + S.ecm;
-    if (p == 1) val *= sqrt(2.0 * m + 3.0) * xi;  // P-bar^m_{m+1} = sqrt(2m+3) x P-bar^m_m
-    renorm(val, ev);
-    V.ga[i] = 0.0;
-    V.gb[i] = val;
-    V.ge[i] = ev;
+    base *= base;
+    eb *= 2;
+    renorm(base, eb);
   }
+  double val = res * S.cm;
+  int ev = er + S.ecm;
+  if (p == 1) val *= sqrt(2.0 * m + 3.0) * xi;  // P-bar^m_{m+1} = sqrt(2m+3) x P-bar^m_m
+  renorm(val, ev);
+  a = 0.0;
+  b = val;
+  e = ev;
 }
 
+// Generator state of rows 0..rows-1 at column 0, kept in scratch.
+__device__ void gen_init(const DevBuildArgs& A, const Views& V, const Shared& S, int m, int p, int rows) {
+  for (int i = threadIdx.x; i < rows; i += kThreads)
+    row_init(A, S, m, p, i, V.x2[i], V.sqw[i], V.ga[i], V.gb[i], V.ge[i]);
+}
+
+__device__ __forceinline__ int exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+// 2^k for -1022 <= k <= 1023, built from its bits
+__device__ __forceinline__ double pow2(int k) { return __hiloint2double((k + 1023) << 20, 0); }
+
 // One step of the recurrence for column j: returns the weighted value of
-// column j and advances (a, b, e) to column j + 1.  Products and sums are
-// rounded one by one, in the host's order.
+// column j and advances (a, b, e) to column j + 1.  The values are the host
+// generator's bit for bit: products and sums are rounded one by one in its
+// order; b 2^e is one product with an exact power of two where 2^e is a
+// normal number (the same correctly rounded result as ldexp), and the
+// rescaling test reads exponent fields, taking the host's exact rule
+// whenever a value is near its thresholds (rescaling moves powers of two
+// between (a, b) and e, which changes no later value).
 __device__ __forceinline__ double gen_step(const Views& V, int j, double x2, double sqw, double& a, double& b,
                                            int& e) {
-  const double col = __dmul_rn(sqw, ldexp(b, e));
+  const double be = ((unsigned)(e + 1022) <= 2045u) ? __dmul_rn(b, pow2(e)) : ldexp(b, e);
+  const double col = __dmul_rn(sqw, be);
   const double nb = __dmul_rn(__dsub_rn(__dmul_rn(__dsub_rn(x2, V.cd[j]), b), __dmul_rn(V.cm2[j], a)), V.cinv[j]);
   a = b;
   b = nb;
-  const double big = fmax(fabs(a), fabs(b));
-  if (big > 0x1p400 || (big < 0x1p-400 && big > 0.0)) {
-    const int t = ilogb(big);
-    a = ldexp(a, -t);
-    b = ldexp(b, -t);
-    e += t;
+  const int M = max(exp_field(a), exp_field(b));
+  if (M >= 1023 + 400 || M < 1023 - 400) {
+    const double big = fmax(fabs(a), fabs(b));
+    if (big > 0x1p400 || (big < 0x1p-400 && big > 0.0)) {
+      const int t = ilogb(big);
+      a = ldexp(a, -t);
+      b = ldexp(b, -t);
+      e += t;
+    }
   }
   return col;
 }
@@ -268,12 +313,18 @@ __device__ int cta_cpqr(double* W, int h, int w, double eps2, const Views& V, Sh
   int k = 0;
   for (int i = 0; i < kmax; ++i) {
     int p = block_argmax(nrm, i, w, S);
-    double e = 0.0;
+    // exact norm of the pivot's rows i.. and of its rows i+1.. (the
+    // Householder sigma), both before the swap
+    double e = 0.0, sg = 0.0;
     {
       const double* c = W + (size_t)p * h;
-      for (int r = i + tid; r < h; r += kThreads) e = fma(c[r], c[r], e);
+      for (int r = i + tid; r < h; r += kThreads) {
+        const double x = c[r];
+        e = fma(x, x, e);
+        if (r > i) sg = fma(x, x, sg);
+      }
     }
-    e = block_sum(e, S);
+    block_sum2(e, sg, S);
     if (e <= eps2) {
       // the downdated norms may have drifted: recompute all before stopping
       for (int j = i + warp; j < w; j += kWarps) {
@@ -285,73 +336,116 @@ __device__ int cta_cpqr(double* W, int h, int w, double eps2, const Views& V, Sh
       }
       __syncthreads();
       p = block_argmax(nrm, i, w, S);
-      e = nrm[p];
-      if (e <= eps2) break;
+      if (nrm[p] <= eps2) break;
+      e = 0.0;
+      sg = 0.0;
+      const double* c = W + (size_t)p * h;
+      for (int r = i + tid; r < h; r += kThreads) {
+        const double x = c[r];
+        e = fma(x, x, e);
+        if (r > i) sg = fma(x, x, sg);
+      }
+      block_sum2(e, sg, S);
     }
-    __syncthreads();  // every thread has read nrm[p]
-    if (tid == 0) nrm[p] = e;
-    if (p != i) {
+    // Householder reflector for the pivot column's rows i..: every thread
+    // derives the same beta, tau and scale from alpha and sigma
+    const double alpha = W[(size_t)p * h + i];
+    const double sigma = sg;
+    double tau = 0.0, beta = alpha, sc = 1.0;
+    const bool reflect = (sigma != 0.0 || alpha < 0.0);
+    if (reflect) {
+      const double nx = sqrt(alpha * alpha + sigma);
+      beta = (alpha <= 0.0) ? nx : -nx;
+      tau = (beta - alpha) / beta;
+      sc = 1.0 / (alpha - beta);
+    }
+    __syncthreads();  // alpha is read before row i is rewritten
+    // swap columns i and p (each thread its own rows) and store the scaled
+    // reflector in column i and in v
+    {
       double* ci = W + (size_t)i * h;
       double* cp = W + (size_t)p * h;
       for (int r = tid; r < h; r += kThreads) {
-        const double t = ci[r];
-        ci[r] = cp[r];
-        cp[r] = t;
+        const double t = cp[r], u = ci[r];
+        double x = t;
+        if (r == i) {
+          x = beta;
+        } else if (r > i && reflect) {
+          x = t * sc;
+        }
+        if (r > i) v[r] = x;
+        if (p != i) cp[r] = u;
+        ci[r] = x;
       }
       if (tid == 0) {
-        const double tn = nrm[i], tr = ref[i];
-        nrm[i] = nrm[p];
-        ref[i] = ref[p];
-        nrm[p] = tn;
-        ref[p] = tr;
-        const int tp = perm[i];
-        perm[i] = perm[p];
-        perm[p] = tp;
+        nrm[p] = e;
+        if (p != i) {
+          const double tn = nrm[i], tr = ref[i];
+          nrm[i] = nrm[p];
+          ref[i] = ref[p];
+          nrm[p] = tn;
+          ref[p] = tr;
+          const int tp = perm[i];
+          perm[i] = perm[p];
+          perm[p] = tp;
+        }
       }
     }
     __syncthreads();
-    // Householder reflector for W[i:h, i]
-    double* ci = W + (size_t)i * h;
-    const double alpha = ci[i];
-    double sg = 0.0;
-    for (int r = i + 1 + tid; r < h; r += kThreads) sg = fma(ci[r], ci[r], sg);
-    const double sigma = block_sum(sg, S);  // its barriers order the reads of alpha before the write below
-    double tau = 0.0;
-    if (sigma != 0.0 || alpha < 0.0) {
-      const double nx = sqrt(alpha * alpha + sigma);
-      const double beta = (alpha <= 0.0) ? nx : -nx;
-      tau = (beta - alpha) / beta;
-      const double sc = 1.0 / (alpha - beta);
-      for (int r = i + 1 + tid; r < h; r += kThreads) {
-        const double t = ci[r] * sc;
-        ci[r] = t;
-        v[r] = t;
-      }
-      if (tid == 0) ci[i] = beta;
-    }
-    __syncthreads();
-    // apply it to the trailing columns and downdate their norms, one warp
-    // per column (lane r reads and writes only its own rows)
-    for (int j = i + 1 + warp; j < w; j += kWarps) {
-      double* cj = W + (size_t)j * h;
-      double rij = cj[i];
+    // apply the reflector to the trailing columns, four per warp: the four
+    // dot products are reduced together (each butterfly step halves the
+    // columns a lane carries), then each column is updated and its norm
+    // downdated; lane r reads and writes only its own rows
+    for (int j0 = i + 1 + 4 * warp; j0 < w; j0 += 4 * kWarps) {
+      const int nc = min(4, w - j0);
+      double* c0 = W + (size_t)j0 * h;
+      double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
       if (tau != 0.0) {
-        double d = 0.0;
-        for (int r = i + 1 + lane; r < h; r += 32) d = fma(v[r], cj[r], d);
-        d = (warp_sum(d) + rij) * tau;
-        for (int r = i + 1 + lane; r < h; r += 32) cj[r] = fma(-d, v[r], cj[r]);
-        rij -= d;
-        if (lane == 0) cj[i] = rij;
+        for (int r = i + 1 + lane; r < h; r += 32) {
+          const double vr = v[r];
+          d0 = fma(vr, c0[r], d0);
+          if (nc > 1) d1 = fma(vr, c0[h + r], d1);
+          if (nc > 2) d2 = fma(vr, c0[2 * h + r], d2);
+          if (nc > 3) d3 = fma(vr, c0[3 * h + r], d3);
+        }
+        const bool hi16 = (lane & 16) != 0;
+        double k0 = hi16 ? d2 : d0, k1 = hi16 ? d3 : d1;
+        k0 += __shfl_xor_sync(kFull, hi16 ? d0 : d2, 16);
+        k1 += __shfl_xor_sync(kFull, hi16 ? d1 : d3, 16);
+        const bool hi8 = (lane & 8) != 0;
+        double s = hi8 ? k1 : k0;
+        s += __shfl_xor_sync(kFull, hi8 ? k0 : k1, 8);
+#pragma unroll
+        for (int o = 4; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        // column c's sum sits in lanes 16 (c >> 1) + 8 (c & 1) + 0..7
+        d0 = __shfl_sync(kFull, s, 0);
+        d1 = __shfl_sync(kFull, s, 8);
+        d2 = __shfl_sync(kFull, s, 16);
+        d3 = __shfl_sync(kFull, s, 24);
       }
-      double nj = nrm[j] - rij * rij;
-      if (nj < 1e-4 * ref[j]) {
-        double s = 0.0;
-        for (int r = i + 1 + lane; r < h; r += 32) s = fma(cj[r], cj[r], s);
-        nj = warp_sum(s);
-        if (lane == 0) ref[j] = nj;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c >= nc) break;
+        const int j = j0 + c;
+        double* cj = c0 + (size_t)c * h;
+        double rij = cj[i];
+        if (tau != 0.0) {
+          const double dc = c == 0 ? d0 : c == 1 ? d1 : c == 2 ? d2 : d3;
+          const double d = (dc + rij) * tau;
+          for (int r = i + 1 + lane; r < h; r += 32) cj[r] = fma(-d, v[r], cj[r]);
+          rij -= d;
+          if (lane == 0) cj[i] = rij;
+        }
+        double nj = nrm[j] - rij * rij;
+        if (nj < 1e-4 * ref[j]) {
+          double s2 = 0.0;
+          for (int r = i + 1 + lane; r < h; r += 32) s2 = fma(cj[r], cj[r], s2);
+          nj = warp_sum(s2);
+          if (lane == 0) ref[j] = nj;
+        }
+        __syncwarp();
+        if (lane == 0) nrm[j] = nj;
       }
-      __syncwarp();
-      if (lane == 0) nrm[j] = nj;
     }
     __syncthreads();
     k = i + 1;
@@ -456,23 +550,30 @@ __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int 
   }
   __syncthreads();
 
-  // trimming: keep rows up to the last whose weighted norm reaches the threshold
+  // trimming: keep rows up to the last whose weighted norm reaches the
+  // threshold.  Only that last row matters, so rows are tried from the pole
+  // down, 256 at a time, and each row's sum stops once it reaches the
+  // threshold (the sum only grows): the same decision as summing every row.
   int rows = l;
   if (A.trim2 > 0.0) {
-    gen_init(A, V, S, m, p, l);
-    int last = 0;
-    for (int i = tid; i < l; i += kThreads) {
-      const double x2 = V.x2[i], sqw = V.sqw[i];
-      double a = V.ga[i], b = V.gb[i];
-      int e = V.ge[i];
-      double nr = 0.0;
-      for (int j = 0; j < n; ++j) {
-        const double c = gen_step(V, j, x2, sqw, a, b, e);
-        nr = __dadd_rn(nr, __dmul_rn(c, c));
+    rows = 0;
+    for (int top = l; top > 0; top -= kThreads) {
+      const int i = top - 1 - tid;
+      int last = 0;
+      if (i >= 0) {
+        double x2, sqw, a, b;
+        int e;
+        row_init(A, S, m, p, i, x2, sqw, a, b, e);
+        double nr = 0.0;
+        for (int j = 0; j < n && nr < A.trim2; ++j) {
+          const double c = gen_step(V, j, x2, sqw, a, b, e);
+          nr = __dadd_rn(nr, __dmul_rn(c, c));
+        }
+        if (nr >= A.trim2) last = i + 1;
       }
-      if (nr >= A.trim2) last = i + 1;
+      rows = block_max_int(last, S);
+      if (rows > 0) break;
     }
-    rows = block_max_int(last, S);
   }
   if (rows == 0) {
     if (tid == 0) {
@@ -791,9 +892,11 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
     check(cudaMemcpy(ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice), "control");
     A.n_queue = (int)pending.size();
     const int grid = (int)std::min<long long>(ctas, (long long)pending.size());
+    const auto t0 = std::chrono::steady_clock::now();
     factor_units_kernel<<<grid, kThreads, smem>>>(A);
     check(cudaGetLastError(), "launch");
     check(cudaDeviceSynchronize(), "factor_units_kernel");
+    P.t_factor_kernel += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     check(cudaMemcpy(status.data(), d_status.p, sizeof(int) * 2 * L, cudaMemcpyDeviceToHost), "status");
     check(cudaMemcpy(info.data(), d_info.p, sizeof(long long) * 3 * 2 * L, cudaMemcpyDeviceToHost), "info");
     check(cudaMemcpy(&c0, ctl, sizeof(c0), cudaMemcpyDeviceToHost), "control");

@@ -92,6 +92,7 @@ struct PlanHost {
   Stream streams[3][2];
   bool built[3] = {false, false, false};
   double t_quad = 0, t_comp = 0;
+  double t_factor = 0, t_factor_kernel = 0;  // parts of t_comp: factorizations, device kernels
 };
 
 // The n positive zeros x_i of P-bar^m_{m+p+2n} (Section 4, Lemma zeros),

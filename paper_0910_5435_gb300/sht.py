@@ -94,6 +94,8 @@ class sht_plan_stats(ctypes.Structure):
         ("m_max_words", ctypes.c_longlong),
         ("smem_bytes", ctypes.c_int),
         ("page_bytes", ctypes.c_int),
+        ("t_factor", ctypes.c_double),
+        ("t_factor_kernel", ctypes.c_double),
     ]
 
     def as_dict(self):
