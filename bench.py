@@ -93,6 +93,10 @@ def device_build_leg(args, sht, torch, dev, stream, plan, st, beta):
     out = {"t_plan_s": t_plan, "t_comp": sd["t_comp"], "t_factor": sd["t_factor"],
            "t_factor_kernel": sd["t_factor_kernel"], "host_t_comp": st["t_comp"], "host_t_factor": st["t_factor"],
            "factor_speedup_vs_host": st["t_factor"] / max(1e-9, sd["t_factor"]),
+           "factor_flops": sd["factor_flops"],
+           "factor_kernel_tflops": sd["factor_flops"] / max(1e-9, sd["t_factor_kernel"]) / 1e12,
+           "factor_kernel_frac_of_fp64_peak": sd["factor_flops"] / max(1e-9, sd["t_factor_kernel"]) / 1e12
+                                              / FP64_PEAK_TFLOPS,
            "k_avg": sd["k_avg"], "k_max": sd["k_max"], "factor_values": sd["factor_values"],
            "host_factor_values": st["factor_values"],
            "rel_synthesis_vs_host_plan": float(torch.linalg.vector_norm(gd - gh) / torch.linalg.vector_norm(gh)),

@@ -175,6 +175,10 @@ typedef struct {
                           * the streams) */
   double t_factor_kernel; /* seconds of t_factor in the device builder's kernels (0 for a
                            * host build) */
+  double factor_flops;   /* floating-point operations the float64 IDs need (Section 2.1,
+                          * Remark QR_algorithm): per block of h rows, w columns and rank k,
+                          * sum over steps i < k of 4 (h - i - 1)(w - i - 1) for applying
+                          * the reflector, plus k^2 (w - k) for T = R11^{-1} R12 */
 } sht_plan_stats;
 
 /* Fills *opts with the defaults listed above. */

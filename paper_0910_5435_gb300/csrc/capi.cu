@@ -202,6 +202,17 @@ void fill_stats(sht_plan_t P) {
   s.t_comp = H.t_comp;
   s.t_factor = H.t_factor;
   s.t_factor_kernel = H.t_factor_kernel;
+  double flops = 0.0;
+  for (const UnitFact& U : H.fact64) {
+    if (U.direct) continue;
+    for (const auto& b : U.blocks) {
+      const double h = b.r1 - b.r0, w = b.nin, k = b.k;
+      // sum_{i<k} (h-i-1)(w-i-1) in closed form
+      const double s1 = k * (k - 1) / 2.0, s2 = (k - 1) * k * (2 * k - 1) / 6.0;
+      flops += 4.0 * ((h - 1) * (w - 1) * k - (h - 1 + w - 1) * s1 + s2) + k * k * (w - k);
+    }
+  }
+  s.factor_flops = flops;
   s.smem_bytes = (int)std::max({P->smem[0], P->smem[1], P->smem[2]});
   s.page_bytes = P->H.page_bytes;
 }

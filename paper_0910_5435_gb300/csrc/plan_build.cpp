@@ -510,6 +510,37 @@ void finish_unit(const PlanHost& P, UnitFact& U, std::vector<FinalBlock>&& top) 
 
 UnitFact factor_single_unit(const PlanHost& P, int m, int p, double eps) { return factor_unit(P, m, p, eps); }
 
+long long depth_first_peak(const UnitFact& U) {
+  const int lam = U.levels, nleaves = 1 << lam;
+  // words kept by each group (level j, group g), and the leaves' widths
+  std::vector<std::vector<long long>> words(lam + 2);
+  for (int j = 1; j <= lam + 1; ++j) words[j].assign(std::max(1, nleaves >> (j - 1)), 0);
+  std::vector<long long> width(nleaves, 0);
+  for (const IdBlock& b : U.blocks) {
+    if (b.level < 1 || b.level > lam + 1 || b.group < 0 || b.group >= (int)words[b.level].size())
+      throw std::logic_error("butterfly layout: block outside its level");
+    words[b.level][b.group] += (long long)(b.r1 - b.r0) * b.k;
+    if (b.level == 1) width[b.group] = b.nin;
+  }
+  long long total = 0, peak = 0;
+  std::vector<std::pair<int, int>> stack;  // (level, group)
+  for (int g = 0; g < nleaves; ++g) {
+    stack.push_back({1, g});
+    total += words[1][g];
+    peak = std::max(peak, total + 2LL * U.rows * width[g]);
+    while (stack.size() >= 2 && stack[stack.size() - 1].first == stack[stack.size() - 2].first) {
+      const int j = stack.back().first, gr = stack.back().second;
+      stack.pop_back();
+      stack.pop_back();
+      total -= words[j][gr] + words[j][gr - 1];
+      total += words[j + 1][gr / 2];
+      stack.push_back({j + 1, gr / 2});
+      peak = std::max(peak, total);
+    }
+  }
+  return peak;
+}
+
 void build_factorizations(PlanHost& P, bool fp32) {
   const int l = P.l, L = 2 * l;
   const double eps = fp32 ? P.eps_fp32 : P.eps_id;

@@ -9,11 +9,15 @@
 //      4, one row per thread: first over all n columns for the row norms that
 //      trimming needs, then leaf by leaf;
 //   2. each interpolative decomposition (Section 2.1, eq. 2.1) is a
-//      column-pivoted Householder QR (Remark QR_algorithm) run by the whole
-//      CTA: pivot search and norms by block reductions, one warp per trailing
-//      column, the Householder vector in shared memory;
-//   3. neighbouring groups are merged as soon as they have the same level
-//      (Section 3), with the stack of skeleton columns in global scratch.
+//      column-pivoted Householder QR (Remark QR_algorithm) run by one warp:
+//      rows across the lanes, pivot search and norms by warp shuffles, the
+//      dot products of four trailing columns reduced together; the CTA's
+//      eight warps factor independent blocks at once;
+//   3. leaves are built eight at a time, one per warp, and merged with the
+//      same pairing as the host's depth-first build (Section 3): every round
+//      merges all pairs of same-level groups at the top of the stack, whose
+//      ID blocks (two per band) are again shared among the warps.  The stack
+//      of skeleton columns lives in global scratch.
 // Every ID block and every band of the top level is written as one record
 // into an output arena; the host reads the records back, lays each unit out
 // (finish_unit) and encodes the streams as after a host build.  Nothing here
@@ -29,6 +33,7 @@
 #include <stdexcept>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "plan_host.h"
@@ -40,6 +45,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxGroups = 24;
+constexpr int kBatch = kWarps;  // leaves factored at once, one per warp
 constexpr unsigned kFull = 0xffffffffu;
 
 enum UnitStatus { kPending = 0, kDone = 1, kNoArena = 2, kNoScratch = 3 };
@@ -74,23 +80,23 @@ struct DevBuildArgs {
   int n_queue;
   unsigned* next;      // queue counter
   double* scratch;     // per CTA: scratch_words
-  long long scratch_words, buf_words, stack_words, desc_cap;
+  long long scratch_words, buf_words, stack_words, desc_cap, warp_words;
   unsigned char* arena;
   unsigned long long arena_bytes;
   unsigned long long* arena_used;
   unsigned long long* arena_fail;  // lowest offset of a reservation that did not fit
   int* stop;                       // the arena is full: take no further units
   int* status;                     // per unit id
-  long long* info;                 // per unit id: rows, levels, peak words
+  long long* info;                 // per unit id: rows, levels
 };
 
 struct Shared {
   GroupDesc grp[kMaxGroups];
-  double redv[kWarps], red2[kWarps];
-  long long redl[kWarps];
   int redi[kWarps];
-  long long rec_off;
-  int q, ngrp, ecm;
+  int kres[kWarps];  // ranks of the leaves of the current batch
+  unsigned long long tmp_sp;
+  long long new_sp;
+  int q, ngrp, ecm, fail;
   double cm;
 };
 
@@ -99,39 +105,6 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
-}
-
-// Sum over the CTA; every thread returns the same value (the warps' partial
-// sums are combined by the same butterfly in every warp).
-__device__ double block_sum(double v, Shared& S) {
-  static_assert(kWarps == 8, "the final butterfly combines 8 warp sums");
-  v = warp_sum(v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) S.redv[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double s = S.redv[threadIdx.x & 7];
-#pragma unroll
-  for (int o = 4; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-  return s;
-}
-
-// Two sums over the CTA at once.
-__device__ void block_sum2(double& x, double& y, Shared& S) {
-  x = warp_sum(x);
-  y = warp_sum(y);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) {
-    S.redv[threadIdx.x >> 5] = x;
-    S.red2[threadIdx.x >> 5] = y;
-  }
-  __syncthreads();
-  x = S.redv[threadIdx.x & 7];
-  y = S.red2[threadIdx.x & 7];
-#pragma unroll
-  for (int o = 4; o; o >>= 1) {
-    x += __shfl_xor_sync(kFull, x, o);
-    y += __shfl_xor_sync(kFull, y, o);
-  }
 }
 
 __device__ int block_max_int(int v, Shared& S) {
@@ -153,11 +126,11 @@ __device__ __forceinline__ bool better(long long a, int ia, long long b, int ib)
 // Index of the largest x[j], i0 <= j < w, the lowest on ties (the host's
 // pivot rule); i0 if there is none.  The x[j] are squared norms, never
 // negative, so their bit patterns order like their values and the search
-// runs on the integer pipes.
-__device__ int block_argmax(const double* x, int i0, int w, Shared& S) {
+// runs on the integer pipes.  Every lane returns the same index.
+__device__ __forceinline__ int warp_argmax(const double* x, int i0, int w, int lane) {
   long long best = -1;
   int bi = w;
-  for (int j = i0 + (int)threadIdx.x; j < w; j += kThreads) {
+  for (int j = i0 + lane; j < w; j += 32) {
     const long long b = __double_as_longlong(x[j]);
     if (b > best) {
       best = b;
@@ -173,21 +146,38 @@ __device__ int block_argmax(const double* x, int i0, int w, Shared& S) {
       bi = oi;
     }
   }
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) {
-    S.redl[threadIdx.x >> 5] = best;
-    S.redi[threadIdx.x >> 5] = bi;
-  }
-  __syncthreads();
-  best = S.redl[0];
-  bi = S.redi[0];
-#pragma unroll
-  for (int i = 1; i < kWarps; ++i)
-    if (better(S.redl[i], S.redi[i], best, bi)) {
-      best = S.redl[i];
-      bi = S.redi[i];
-    }
   return bi < w ? bi : i0;
+}
+
+// Warp sums of four per-lane partial sums at once: each butterfly step
+// halves the values a lane carries (column c ends in lanes 16 (c >> 1) +
+// 8 (c & 1) + 0..7, all with the same bits), then every lane gets all four.
+__device__ __forceinline__ void reduce4(double& d0, double& d1, double& d2, double& d3, int lane) {
+  const bool hi16 = (lane & 16) != 0;
+  double k0 = hi16 ? d2 : d0, k1 = hi16 ? d3 : d1;
+  k0 += __shfl_xor_sync(kFull, hi16 ? d0 : d2, 16);
+  k1 += __shfl_xor_sync(kFull, hi16 ? d1 : d3, 16);
+  const bool hi8 = (lane & 8) != 0;
+  double s = hi8 ? k1 : k0;
+  s += __shfl_xor_sync(kFull, hi8 ? k0 : k1, 8);
+#pragma unroll
+  for (int o = 4; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  d0 = __shfl_sync(kFull, s, 0);
+  d1 = __shfl_sync(kFull, s, 8);
+  d2 = __shfl_sync(kFull, s, 16);
+  d3 = __shfl_sync(kFull, s, 24);
+}
+
+// Warp sums of two per-lane partial sums (the first step splits them
+// between the half-warps).
+__device__ __forceinline__ void reduce2(double& x, double& y, int lane) {
+  const bool hi16 = (lane & 16) != 0;
+  double s = hi16 ? y : x;
+  s += __shfl_xor_sync(kFull, hi16 ? x : y, 16);
+#pragma unroll
+  for (int o = 8; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+  x = __shfl_sync(kFull, s, 0);
+  y = __shfl_sync(kFull, s, 16);
 }
 
 __device__ __forceinline__ void renorm(double& v, int& e) {
@@ -201,14 +191,31 @@ __device__ __forceinline__ void renorm(double& v, int& e) {
 struct Views {
   // shared
   double *cinv, *cd, *cm2;  // per column j < n: 1/c_k, d_k, c_{k-2} (0 at j = 0), k = m + p + 2j
-  double *nrm, *ref, *v;
-  int* perm;
   // global, per CTA
   double *x2, *sqw, *ga, *gb;
   int* ge;
   BandDesc* desc;
-  double *bufZ, *bufW, *stack;
+  double* warps;  // kWarps x warp_words: each warp's Z, W, nrm, ref, perm
+  long long warp_words;
+  double* stack;
 };
+
+// One warp's buffers: the block Z (kept), its working copy W (destroyed by
+// the QR), the squared column norms and the column order.
+struct WarpBuf {
+  double *Z, *W, *nrm, *ref;
+  int* perm;
+};
+__device__ __forceinline__ WarpBuf warp_buf(const DevBuildArgs& A, const Views& V, int warp) {
+  double* b = V.warps + (long long)warp * V.warp_words;
+  WarpBuf B;
+  B.Z = b;
+  B.W = b + A.buf_words;
+  B.nrm = B.W + A.buf_words;
+  B.ref = B.nrm + A.l;
+  B.perm = reinterpret_cast<int*>(B.ref + A.l);
+  return B;
+}
 
 // Generator state of row i at column 0: b = P-bar^m_{m+p}(x_i) as a
 // mantissa b and exponent e, a = 0 (eq. recurrence0 has no k - 2 term).
@@ -279,93 +286,110 @@ __device__ __forceinline__ double gen_step(const Views& V, int j, double x2, dou
   return col;
 }
 
-// Columns j0 .. j0 + w - 1 into out (rows x w, column-major).
-__device__ void gen_cols(const Views& V, int j0, int w, int rows, double* out) {
+// Columns of leaves g0 .. g0 + nb - 1 (consecutive column ranges), leaf
+// g0 + q into warp q's Z (rows x width, column-major).
+__device__ void gen_leaves(const DevBuildArgs& A, const Views& V, int g0, int nb, int nleaves, int n, int rows) {
   for (int i = threadIdx.x; i < rows; i += kThreads) {
     const double x2 = V.x2[i], sqw = V.sqw[i];
     double a = V.ga[i], b = V.gb[i];
     int e = V.ge[i];
-    for (int j = 0; j < w; ++j) out[(size_t)j * rows + i] = gen_step(V, j0 + j, x2, sqw, a, b, e);
+    for (int q = 0; q < nb; ++q) {
+      const int g = g0 + q;
+      const int c0 = (int)((long long)g * n / nleaves), c1 = (int)((long long)(g + 1) * n / nleaves);
+      double* out = warp_buf(A, V, q).Z;
+      for (int j = c0; j < c1; ++j) out[(size_t)(j - c0) * rows + i] = gen_step(V, j, x2, sqw, a, b, e);
+    }
     V.ga[i] = a;
     V.gb[i] = b;
     V.ge[i] = e;
   }
 }
 
-// Column-pivoted Householder QR of the h x w column-major W (destroyed) to
-// threshold eps2 on the squared residual column norms, the host's
-// interp_decomp step for step.  Returns the rank k; perm holds the column
-// order (skeleton first).  Every thread returns the same k.
-__device__ int cta_cpqr(double* W, int h, int w, double eps2, const Views& V, Shared& S) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double *nrm = V.nrm, *ref = V.ref, *v = V.v;
-  int* perm = V.perm;
-  for (int j = tid; j < w; j += kThreads) perm[j] = j;
-  for (int j = warp; j < w; j += kWarps) {
-    const double* c = W + (size_t)j * h;
-    double s = 0.0;
-    for (int r = lane; r < h; r += 32) s = fma(c[r], c[r], s);
-    s = warp_sum(s);
-    if (lane == 0) nrm[j] = ref[j] = s;
+// Squared norms of rows r0.. of columns c0 .. w-1 into nrm and ref.
+__device__ void warp_norms(const double* W, int h, int w, int c0, int r0, double* nrm, double* ref, int lane) {
+  for (int j0 = c0; j0 < w; j0 += 4) {
+    const int nc = min(4, w - j0);
+    const double* c = W + (size_t)j0 * h;
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+    for (int r = r0 + lane; r < h; r += 32) {
+      double x = c[r];
+      d0 = fma(x, x, d0);
+      if (nc > 1) {
+        x = c[h + r];
+        d1 = fma(x, x, d1);
+      }
+      if (nc > 2) {
+        x = c[2 * h + r];
+        d2 = fma(x, x, d2);
+      }
+      if (nc > 3) {
+        x = c[3 * h + r];
+        d3 = fma(x, x, d3);
+      }
+    }
+    reduce4(d0, d1, d2, d3, lane);
+    if (lane < nc) {
+      const double s = lane == 0 ? d0 : lane == 1 ? d1 : lane == 2 ? d2 : d3;
+      nrm[j0 + lane] = s;
+      ref[j0 + lane] = s;
+    }
   }
-  __syncthreads();
+}
+
+// Squared norm of column p's rows i.. (e) and rows i+1.. (sg).
+__device__ __forceinline__ void pivot_sums(const double* W, int h, int p, int i, double& e, double& sg, int lane) {
+  const double* c = W + (size_t)p * h;
+  e = 0.0;
+  sg = 0.0;
+  for (int r = i + lane; r < h; r += 32) {
+    const double x = c[r];
+    e = fma(x, x, e);
+    if (r > i) sg = fma(x, x, sg);
+  }
+  reduce2(e, sg, lane);
+}
+
+// Column-pivoted Householder QR of the h x w column-major W (destroyed) by
+// one warp, to threshold eps2 on the squared residual column norms: the
+// host's interp_decomp step for step.  Returns the rank k (every lane the
+// same); perm holds the column order (skeleton first).  Within a step each
+// lane owns the rows i+1+lane, i+33+lane, ...; __syncwarp separates steps
+// and phases.
+__device__ int warp_cpqr(double* W, int h, int w, double eps2, const WarpBuf& B, int lane) {
+  double *nrm = B.nrm, *ref = B.ref;
+  int* perm = B.perm;
+  for (int j = lane; j < w; j += 32) perm[j] = j;
+  warp_norms(W, h, w, 0, 0, nrm, ref, lane);
+  __syncwarp();
   const int kmax = min(h, w);
   int k = 0;
   for (int i = 0; i < kmax; ++i) {
-    int p = block_argmax(nrm, i, w, S);
-    // exact norm of the pivot's rows i.. and of its rows i+1.. (the
-    // Householder sigma), both before the swap
-    double e = 0.0, sg = 0.0;
-    {
-      const double* c = W + (size_t)p * h;
-      for (int r = i + tid; r < h; r += kThreads) {
-        const double x = c[r];
-        e = fma(x, x, e);
-        if (r > i) sg = fma(x, x, sg);
-      }
-    }
-    block_sum2(e, sg, S);
+    int p = warp_argmax(nrm, i, w, lane);
+    double e, sg;
+    pivot_sums(W, h, p, i, e, sg, lane);
     if (e <= eps2) {
       // the downdated norms may have drifted: recompute all before stopping
-      for (int j = i + warp; j < w; j += kWarps) {
-        const double* c = W + (size_t)j * h;
-        double s = 0.0;
-        for (int r = i + lane; r < h; r += 32) s = fma(c[r], c[r], s);
-        s = warp_sum(s);
-        if (lane == 0) nrm[j] = ref[j] = s;
-      }
-      __syncthreads();
-      p = block_argmax(nrm, i, w, S);
+      warp_norms(W, h, w, i, i, nrm, ref, lane);
+      __syncwarp();
+      p = warp_argmax(nrm, i, w, lane);
       if (nrm[p] <= eps2) break;
-      e = 0.0;
-      sg = 0.0;
-      const double* c = W + (size_t)p * h;
-      for (int r = i + tid; r < h; r += kThreads) {
-        const double x = c[r];
-        e = fma(x, x, e);
-        if (r > i) sg = fma(x, x, sg);
-      }
-      block_sum2(e, sg, S);
+      pivot_sums(W, h, p, i, e, sg, lane);
     }
-    // Householder reflector for the pivot column's rows i..: every thread
-    // derives the same beta, tau and scale from alpha and sigma
+    // Householder reflector for the pivot column's rows i..
     const double alpha = W[(size_t)p * h + i];
-    const double sigma = sg;
     double tau = 0.0, beta = alpha, sc = 1.0;
-    const bool reflect = (sigma != 0.0 || alpha < 0.0);
+    const bool reflect = (sg != 0.0 || alpha < 0.0);
     if (reflect) {
-      const double nx = sqrt(alpha * alpha + sigma);
+      const double nx = sqrt(alpha * alpha + sg);
       beta = (alpha <= 0.0) ? nx : -nx;
       tau = (beta - alpha) / beta;
       sc = 1.0 / (alpha - beta);
     }
-    __syncthreads();  // alpha is read before row i is rewritten
-    // swap columns i and p (each thread its own rows) and store the scaled
-    // reflector in column i and in v
+    __syncwarp();  // alpha is read before row i is rewritten
+    double* ci = W + (size_t)i * h;
     {
-      double* ci = W + (size_t)i * h;
       double* cp = W + (size_t)p * h;
-      for (int r = tid; r < h; r += kThreads) {
+      for (int r = lane; r < h; r += 32) {
         const double t = cp[r], u = ci[r];
         double x = t;
         if (r == i) {
@@ -373,11 +397,10 @@ __device__ int cta_cpqr(double* W, int h, int w, double eps2, const Views& V, Sh
         } else if (r > i && reflect) {
           x = t * sc;
         }
-        if (r > i) v[r] = x;
         if (p != i) cp[r] = u;
         ci[r] = x;
       }
-      if (tid == 0) {
+      if (lane == 0) {
         nrm[p] = e;
         if (p != i) {
           const double tn = nrm[i], tr = ref[i];
@@ -391,37 +414,22 @@ __device__ int cta_cpqr(double* W, int h, int w, double eps2, const Views& V, Sh
         }
       }
     }
-    __syncthreads();
-    // apply the reflector to the trailing columns, four per warp: the four
-    // dot products are reduced together (each butterfly step halves the
-    // columns a lane carries), then each column is updated and its norm
-    // downdated; lane r reads and writes only its own rows
-    for (int j0 = i + 1 + 4 * warp; j0 < w; j0 += 4 * kWarps) {
+    __syncwarp();
+    // apply the reflector to the trailing columns, four at a time, and
+    // downdate their norms
+    for (int j0 = i + 1; j0 < w; j0 += 4) {
       const int nc = min(4, w - j0);
       double* c0 = W + (size_t)j0 * h;
       double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
       if (tau != 0.0) {
         for (int r = i + 1 + lane; r < h; r += 32) {
-          const double vr = v[r];
+          const double vr = ci[r];
           d0 = fma(vr, c0[r], d0);
           if (nc > 1) d1 = fma(vr, c0[h + r], d1);
           if (nc > 2) d2 = fma(vr, c0[2 * h + r], d2);
           if (nc > 3) d3 = fma(vr, c0[3 * h + r], d3);
         }
-        const bool hi16 = (lane & 16) != 0;
-        double k0 = hi16 ? d2 : d0, k1 = hi16 ? d3 : d1;
-        k0 += __shfl_xor_sync(kFull, hi16 ? d0 : d2, 16);
-        k1 += __shfl_xor_sync(kFull, hi16 ? d1 : d3, 16);
-        const bool hi8 = (lane & 8) != 0;
-        double s = hi8 ? k1 : k0;
-        s += __shfl_xor_sync(kFull, hi8 ? k0 : k1, 8);
-#pragma unroll
-        for (int o = 4; o; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        // column c's sum sits in lanes 16 (c >> 1) + 8 (c & 1) + 0..7
-        d0 = __shfl_sync(kFull, s, 0);
-        d1 = __shfl_sync(kFull, s, 8);
-        d2 = __shfl_sync(kFull, s, 16);
-        d3 = __shfl_sync(kFull, s, 24);
+        reduce4(d0, d1, d2, d3, lane);
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -432,45 +440,28 @@ __device__ int cta_cpqr(double* W, int h, int w, double eps2, const Views& V, Sh
         if (tau != 0.0) {
           const double dc = c == 0 ? d0 : c == 1 ? d1 : c == 2 ? d2 : d3;
           const double d = (dc + rij) * tau;
-          for (int r = i + 1 + lane; r < h; r += 32) cj[r] = fma(-d, v[r], cj[r]);
+          for (int r = i + 1 + lane; r < h; r += 32) cj[r] = fma(-d, ci[r], cj[r]);
           rij -= d;
-          if (lane == 0) cj[i] = rij;
         }
         double nj = nrm[j] - rij * rij;
-        if (nj < 1e-4 * ref[j]) {
+        const bool exact = nj < 1e-4 * ref[j];
+        if (exact) {
           double s2 = 0.0;
           for (int r = i + 1 + lane; r < h; r += 32) s2 = fma(cj[r], cj[r], s2);
           nj = warp_sum(s2);
-          if (lane == 0) ref[j] = nj;
         }
-        __syncwarp();
-        if (lane == 0) nrm[j] = nj;
+        __syncwarp();  // every lane has read cj[i], nrm[j] and ref[j]
+        if (lane == 0) {
+          if (tau != 0.0) cj[i] = rij;
+          if (exact) ref[j] = nj;
+          nrm[j] = nj;
+        }
       }
     }
-    __syncthreads();
+    __syncwarp();
     k = i + 1;
   }
   return k;
-}
-
-// Reserves one record; every thread learns whether it fit.
-__device__ unsigned char* reserve(const DevBuildArgs& A, long long bytes, Shared& S) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    long long off = -1;
-    if (*(volatile int*)A.stop == 0) {
-      const unsigned long long o = atomicAdd(A.arena_used, (unsigned long long)bytes);
-      if (o + (unsigned long long)bytes <= A.arena_bytes) {
-        off = (long long)o;
-      } else {
-        atomicMin(A.arena_fail, o);
-        atomicExch(A.stop, 1);
-      }
-    }
-    S.rec_off = off;
-  }
-  __syncthreads();
-  return S.rec_off < 0 ? nullptr : A.arena + S.rec_off;
 }
 
 __device__ __forceinline__ long long pad16(long long b) { return (b + 15) & ~15LL; }
@@ -479,13 +470,28 @@ __device__ __forceinline__ long long block_record_bytes(int nin, int k) {
   return pad16((long long)sizeof(RecHdr) + pad16(4LL * nin) + 8LL * k * (nin - k));
 }
 
+// Reserves one record for the warp; nullptr when the arena is full.
+__device__ unsigned char* warp_reserve(const DevBuildArgs& A, long long bytes, int lane) {
+  long long off = -1;
+  if (lane == 0 && *(volatile int*)A.stop == 0) {
+    const unsigned long long o = atomicAdd(A.arena_used, (unsigned long long)bytes);
+    if (o + (unsigned long long)bytes <= A.arena_bytes) {
+      off = (long long)o;
+    } else {
+      atomicMin(A.arena_fail, o);
+      atomicExch(A.stop, 1);
+    }
+  }
+  off = __shfl_sync(kFull, off, 0);
+  return off < 0 ? nullptr : A.arena + off;
+}
+
 // Writes the record of one ID block: the skeleton, the redundant columns in
 // ascending order and T = R11^{-1} R12 by back substitution, each column of T
 // placed at the position of its column in that order.
-__device__ void write_block(unsigned char* rec, int unit, int level, int band, int group, int r0, int r1,
-                            int in_off, int nin, int k, const double* W, int h, const Views& V) {
-  RecHdr* H = reinterpret_cast<RecHdr*>(rec);
-  if (threadIdx.x == 0) {
+__device__ void warp_write_block(unsigned char* rec, int unit, int level, int band, int group, int r0, int r1,
+                                 int in_off, int nin, int k, const double* W, int h, const int* perm, int lane) {
+  if (lane == 0) {
     RecHdr t{};
     t.unit = unit;
     t.kind = 0;
@@ -498,15 +504,14 @@ __device__ void write_block(unsigned char* rec, int unit, int level, int band, i
     t.nin = nin;
     t.k = k;
     t.bytes = block_record_bytes(nin, k);
-    *H = t;
+    *reinterpret_cast<RecHdr*>(rec) = t;
   }
   int* skel = reinterpret_cast<int*>(rec + sizeof(RecHdr));
   int* red = skel + k;
   double* T = reinterpret_cast<double*>(rec + sizeof(RecHdr) + pad16(4LL * nin));
-  const int* perm = V.perm;
-  for (int t = threadIdx.x; t < k; t += kThreads) skel[t] = perm[t];
+  for (int t = lane; t < k; t += 32) skel[t] = perm[t];
   const int nred = nin - k;
-  for (int s = threadIdx.x; s < nred; s += kThreads) {
+  for (int s = lane; s < nred; s += 32) {
     const int c = perm[k + s];
     int rank = 0;
     for (int s2 = 0; s2 < nred; ++s2) rank += perm[k + s2] < c;
@@ -521,13 +526,16 @@ __device__ void write_block(unsigned char* rec, int unit, int level, int band, i
   }
 }
 
+// Marks the unit failed (first reason wins).
+__device__ __forceinline__ void set_fail(Shared& S, int why) { atomicCAS(&S.fail, 0, why); }
+
 // Builds unit u; returns its status.
 __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int u) {
-  const int m = u >> 1, p = u & 1, l = A.l, L = 2 * l, tid = threadIdx.x;
+  const int m = u >> 1, p = u & 1, l = A.l, L = 2 * l, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = max(0, (L - m - p + 1) / 2);
-  long long* info = A.info + 3LL * u;
+  long long* info = A.info + 2LL * u;
   if (n == 0) {
-    if (tid == 0) info[0] = info[1] = info[2] = 0;
+    if (tid == 0) info[0] = info[1] = 0;
     return kDone;
   }
   // recurrence coefficients of the n columns, and c_m with
@@ -547,6 +555,8 @@ __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int 
     }
     S.cm = cm;
     S.ecm = ecm;
+    S.ngrp = 0;
+    S.fail = 0;
   }
   __syncthreads();
 
@@ -576,11 +586,7 @@ __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int 
     }
   }
   if (rows == 0) {
-    if (tid == 0) {
-      info[0] = 0;
-      info[1] = 0;
-      info[2] = 0;
-    }
+    if (tid == 0) info[0] = info[1] = 0;
     return kDone;
   }
   const int C = A.C;
@@ -588,110 +594,167 @@ __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int 
   while ((n >> lam) > C) ++lam;
   if (n > C && (n + (1 << lam) - 1) / (1 << lam) > C) ++lam;
   while (lam > 0 && (rows >> lam) < A.min_band_rows) --lam;
-  if (lam + 2 > kMaxGroups) return kNoScratch;
   const int nleaves = 1 << lam;
+  const int NB = min(kWarps, nleaves);
+  if (lam + 1 + NB > kMaxGroups) return kNoScratch;
+  for (int g = 0; g < nleaves; ++g) {
+    const int wd = (int)((long long)(g + 1) * n / nleaves) - (int)((long long)g * n / nleaves);
+    if ((long long)rows * wd > A.buf_words || wd > l) return kNoScratch;
+  }
 
-  __syncthreads();
   gen_init(A, V, S, m, p, rows);
   __syncthreads();
-  if (tid == 0) S.ngrp = 0;
-  long long sp = 0, peak = 0;
+  long long sp = 0;
   int ndesc = 0;
-  for (int g = 0; g < nleaves; ++g) {
-    const int c0 = (int)((long long)g * n / nleaves), c1 = (int)((long long)(g + 1) * n / nleaves);
-    const int wd = c1 - c0;
-    if ((long long)rows * wd > A.buf_words || wd > l) return kNoScratch;
-    gen_cols(V, c0, wd, rows, V.bufZ);
+  for (int g0 = 0; g0 < nleaves; g0 += NB) {
+    // the batch's columns, then its leaf IDs, one per warp
+    gen_leaves(A, V, g0, NB, nleaves, n, rows);
     __syncthreads();
-    for (long long t = tid; t < (long long)rows * wd; t += kThreads) V.bufW[t] = V.bufZ[t];
+    if (warp < NB) {
+      const int g = g0 + warp;
+      const int c0 = (int)((long long)g * n / nleaves), wd = (int)((long long)(g + 1) * n / nleaves) - c0;
+      const WarpBuf B = warp_buf(A, V, warp);
+      for (long long t = lane; t < (long long)rows * wd; t += 32) B.W[t] = B.Z[t];
+      __syncwarp();
+      const int k = warp_cpqr(B.W, rows, wd, A.eps2, B, lane);
+      unsigned char* rec = warp_reserve(A, block_record_bytes(wd, k), lane);
+      if (rec) {
+        warp_write_block(rec, u, 1, 0, g, 0, rows, c0, wd, k, B.W, rows, B.perm, lane);
+      } else if (lane == 0) {
+        set_fail(S, kNoArena);
+      }
+      if (lane == 0) S.kres[warp] = k;
+    }
     __syncthreads();
-    const int k = cta_cpqr(V.bufW, rows, wd, A.eps2, V, S);
-    unsigned char* rec = reserve(A, block_record_bytes(wd, k), S);
-    if (!rec) return kNoArena;
-    write_block(rec, u, 1, 0, g, 0, rows, c0, wd, k, V.bufW, rows, V);
-    if (sp + (long long)rows * k > A.stack_words || ndesc + 1 > A.desc_cap) return kNoScratch;
-    for (long long t = tid; t < (long long)rows * k; t += kThreads) {
-      const int c = (int)(t / rows), i = (int)(t - (long long)c * rows);
-      V.stack[sp + t] = V.bufZ[(size_t)V.perm[c] * rows + i];
+    if (S.fail) return S.fail;
+    // push the leaves in order: their skeleton columns go on the stack
+    for (int q = 0; q < NB; ++q) {
+      const int k = S.kres[q];
+      if (sp + (long long)rows * k > A.stack_words || ndesc + 1 > A.desc_cap) return kNoScratch;
+      const WarpBuf B = warp_buf(A, V, q);
+      for (long long t = tid; t < (long long)rows * k; t += kThreads) {
+        const int c = (int)(t / rows), i = (int)(t - (long long)c * rows);
+        V.stack[sp + t] = B.Z[(size_t)B.perm[c] * rows + i];
+      }
+      if (tid == 0) {
+        V.desc[ndesc] = BandDesc{0, rows, k, 0, sp};
+        S.grp[S.ngrp] = GroupDesc{1, g0 + q, 1, ndesc};
+        S.ngrp += 1;
+      }
+      sp += (long long)rows * k;
+      ndesc += 1;
     }
-    if (tid == 0) {
-      V.desc[ndesc] = BandDesc{0, rows, k, 0, sp};
-      S.grp[S.ngrp] = GroupDesc{1, g, 1, ndesc};
-      S.ngrp += 1;
-    }
-    sp += (long long)rows * k;
-    ndesc += 1;
-    peak = max(peak, sp + 2LL * rows * wd);
     __syncthreads();
 
-    while (S.ngrp >= 2 && S.grp[S.ngrp - 1].level == S.grp[S.ngrp - 2].level) {
-      const GroupDesc Lg = S.grp[S.ngrp - 2], Rg = S.grp[S.ngrp - 1];
-      const int j = Lg.level, nb = Lg.nb, ng = Lg.g / 2;
+    // merge rounds: all pairs of same-level groups at the top of the stack
+    for (;;) {
+      const int ng = S.ngrp;
+      if (ng < 2) break;
+      const int lev = S.grp[ng - 1].level;
+      int run = 1;
+      while (run < ng && S.grp[ng - 1 - run].level == lev) ++run;
+      const int P = run / 2;
+      if (P == 0) break;
+      const int gb = ng - 2 * P;
+      const int nb = S.grp[gb].nb;
+      const int T = P * 2 * nb;  // ID blocks of this round, two per band of each pair
+      for (int q = 0; q < P; ++q) {
+        const GroupDesc Lg = S.grp[gb + 2 * q], Rg = S.grp[gb + 2 * q + 1];
+        if ((Lg.g & 1) || Rg.g != Lg.g + 1 || Lg.nb != nb || Rg.nb != nb) return kNoScratch;
+      }
+      if (ndesc + T > A.desc_cap) return kNoScratch;
       const long long base = sp;
-      const int d_new = ndesc;
-      if (ndesc + 2 * nb > A.desc_cap) return kNoScratch;
-      for (int beta = 0; beta < nb; ++beta) {
+      if (tid == 0) S.tmp_sp = (unsigned long long)base;
+      __syncthreads();
+      for (int t = warp; t < T; t += kWarps) {
+        const int q = t / (2 * nb), beta = (t - q * 2 * nb) >> 1, half = t & 1;
+        const GroupDesc Lg = S.grp[gb + 2 * q], Rg = S.grp[gb + 2 * q + 1];
         const BandDesc BL = V.desc[Lg.d0 + beta], BR = V.desc[Rg.d0 + beta];
         const int h = BL.r1 - BL.r0, mid = BL.r0 + h / 2, kin = BL.k + BR.k;
-        for (int half = 0; half < 2; ++half) {
-          const int rr0 = half ? mid : BL.r0, rr1 = half ? BL.r1 : mid, hh = rr1 - rr0;
-          if ((long long)hh * kin > A.buf_words || kin > l) return kNoScratch;
-          // Z = [rows rr0..rr1 of the left band's skeleton columns, then the right's]
-          for (long long t = tid; t < (long long)hh * kin; t += kThreads) {
-            const int c = (int)(t / hh), i = (int)(t - (long long)c * hh);
-            const double z = c < BL.k ? V.stack[BL.off + (long long)c * h + (rr0 - BL.r0) + i]
-                                      : V.stack[BR.off + (long long)(c - BL.k) * h + (rr0 - BL.r0) + i];
-            V.bufZ[t] = z;
-            V.bufW[t] = z;
-          }
-          __syncthreads();
-          const int k = cta_cpqr(V.bufW, hh, kin, A.eps2, V, S);
-          unsigned char* rec = reserve(A, block_record_bytes(kin, k), S);
-          if (!rec) return kNoArena;
-          write_block(rec, u, j + 1, 2 * beta + half, ng, rr0, rr1, 0, kin, k, V.bufW, hh, V);
-          if (sp + (long long)hh * k > A.stack_words) return kNoScratch;
-          for (long long t = tid; t < (long long)hh * k; t += kThreads) {
-            const int c = (int)(t / hh), i = (int)(t - (long long)c * hh);
-            V.stack[sp + t] = V.bufZ[(size_t)V.perm[c] * hh + i];
-          }
-          if (tid == 0) V.desc[ndesc] = BandDesc{rr0, rr1, k, 0, sp};
-          sp += (long long)hh * k;
-          ndesc += 1;
-          __syncthreads();
+        const int rr0 = half ? mid : BL.r0, rr1 = half ? BL.r1 : mid, hh = rr1 - rr0;
+        if ((long long)hh * kin > A.buf_words || kin > l) {
+          if (lane == 0) set_fail(S, kNoScratch);
+          continue;
         }
-      }
-      // the new group replaces L and R: move its columns and descriptors down
-      // (its words never exceed theirs: each new band keeps k <= kin columns
-      // of half the rows, so source and destination do not overlap)
-      const long long dst = V.desc[Lg.d0].off, words = sp - base, gap = base - dst;
-      if (words > gap) return kNoScratch;
-      for (long long t = tid; t < words; t += kThreads) V.stack[dst + t] = V.stack[base + t];
-      for (int t = tid; t < 2 * nb; t += kThreads) {
-        BandDesc d = V.desc[d_new + t];
-        d.off -= gap;
-        V.desc[Lg.d0 + t] = d;
+        const WarpBuf B = warp_buf(A, V, warp);
+        // Z = [rows rr0..rr1 of the left band's skeleton columns, then the right's]
+        for (long long x = lane; x < (long long)hh * kin; x += 32) {
+          const int c = (int)(x / hh), i = (int)(x - (long long)c * hh);
+          const double z = c < BL.k ? V.stack[BL.off + (long long)c * h + (rr0 - BL.r0) + i]
+                                    : V.stack[BR.off + (long long)(c - BL.k) * h + (rr0 - BL.r0) + i];
+          B.Z[x] = z;
+          B.W[x] = z;
+        }
+        __syncwarp();
+        const int k = warp_cpqr(B.W, hh, kin, A.eps2, B, lane);
+        unsigned char* rec = warp_reserve(A, block_record_bytes(kin, k), lane);
+        if (!rec) {
+          if (lane == 0) set_fail(S, kNoArena);
+          continue;
+        }
+        warp_write_block(rec, u, lev + 1, 2 * beta + half, Lg.g / 2, rr0, rr1, 0, kin, k, B.W, hh, B.perm, lane);
+        // the new band's skeleton columns go to temporary space above the stack
+        unsigned long long off = 0;
+        if (lane == 0) off = atomicAdd(&S.tmp_sp, (unsigned long long)hh * k);
+        off = __shfl_sync(kFull, off, 0);
+        if ((long long)off + (long long)hh * k > A.stack_words) {
+          if (lane == 0) set_fail(S, kNoScratch);
+          continue;
+        }
+        for (long long x = lane; x < (long long)hh * k; x += 32) {
+          const int c = (int)(x / hh), i = (int)(x - (long long)c * hh);
+          V.stack[off + x] = B.Z[(size_t)B.perm[c] * hh + i];
+        }
+        if (lane == 0) V.desc[ndesc + t] = BandDesc{rr0, rr1, k, 0, (long long)off};
       }
       __syncthreads();
-      sp = dst + words;
-      ndesc = Lg.d0 + 2 * nb;
-      peak = max(peak, sp);
+      if (S.fail) return S.fail;
+      // the new groups replace the merged ones: final offsets in band order
+      // (their words never exceed the merged groups', so every destination
+      // lies below `base` and every source above it)
+      const int d_run = S.grp[gb].d0;
       if (tid == 0) {
-        S.grp[S.ngrp - 2] = GroupDesc{j + 1, ng, 2 * nb, Lg.d0};
-        S.ngrp -= 1;
+        long long o = V.desc[d_run].off;
+        for (int t = 0; t < T; ++t) {
+          BandDesc d = V.desc[ndesc + t];
+          const long long words = (long long)(d.r1 - d.r0) * d.k;
+          d.off = o;
+          V.desc[d_run + t] = d;
+          o += words;
+        }
+        S.new_sp = o;
+        for (int q = 0; q < P; ++q) {
+          const GroupDesc Lg = S.grp[gb + 2 * q];
+          S.grp[gb + q] = GroupDesc{lev + 1, Lg.g / 2, 2 * nb, d_run + q * 2 * nb};
+        }
+        S.ngrp = gb + P;
+        if (o > base) S.fail = kNoScratch;
       }
+      __syncthreads();
+      if (S.fail) return S.fail;
+      for (int t = warp; t < T; t += kWarps) {
+        const BandDesc src = V.desc[ndesc + t], dst = V.desc[d_run + t];
+        const long long words = (long long)(src.r1 - src.r0) * src.k;
+        for (long long x = lane; x < words; x += 32) V.stack[dst.off + x] = V.stack[src.off + x];
+      }
+      sp = S.new_sp;
+      ndesc = d_run + T;
       __syncthreads();
     }
   }
   if (S.ngrp != 1) return kNoScratch;
   // the top level's bands: their stored skeleton columns are the final blocks
   const GroupDesc top = S.grp[0];
-  for (int beta = 0; beta < top.nb; ++beta) {
+  for (int beta = warp; beta < top.nb; beta += kWarps) {
     const BandDesc B = V.desc[top.d0 + beta];
     const long long words = (long long)(B.r1 - B.r0) * B.k;
     const long long bytes = pad16((long long)sizeof(RecHdr) + 8 * words);
-    unsigned char* rec = reserve(A, bytes, S);
-    if (!rec) return kNoArena;
-    if (tid == 0) {
+    unsigned char* rec = warp_reserve(A, bytes, lane);
+    if (!rec) {
+      if (lane == 0) set_fail(S, kNoArena);
+      continue;
+    }
+    if (lane == 0) {
       RecHdr t{};
       t.unit = u;
       t.kind = 1;
@@ -703,12 +766,13 @@ __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int 
       *reinterpret_cast<RecHdr*>(rec) = t;
     }
     double* Sv = reinterpret_cast<double*>(rec + sizeof(RecHdr));
-    for (long long t = tid; t < words; t += kThreads) Sv[t] = V.stack[B.off + t];
+    for (long long x = lane; x < words; x += 32) Sv[x] = V.stack[B.off + x];
   }
+  __syncthreads();
+  if (S.fail) return S.fail;
   if (tid == 0) {
     info[0] = rows;
     info[1] = lam;
-    info[2] = peak;
   }
   return kDone;
 }
@@ -721,10 +785,6 @@ __global__ void __launch_bounds__(kThreads, 4) factor_units_kernel(DevBuildArgs 
   V.cinv = reinterpret_cast<double*>(dyn);
   V.cd = V.cinv + l;
   V.cm2 = V.cd + l;
-  V.nrm = V.cm2 + l;
-  V.ref = V.nrm + l;
-  V.v = V.ref + l;
-  V.perm = reinterpret_cast<int*>(V.v + l);
   double* g = A.scratch + (long long)blockIdx.x * A.scratch_words;
   V.x2 = g;
   V.sqw = g + l;
@@ -732,9 +792,9 @@ __global__ void __launch_bounds__(kThreads, 4) factor_units_kernel(DevBuildArgs 
   V.gb = g + 3 * l;
   V.ge = reinterpret_cast<int*>(g + 4 * l);
   V.desc = reinterpret_cast<BandDesc*>(g + 5 * l);
-  V.bufZ = g + 5 * l + 3 * A.desc_cap;
-  V.bufW = V.bufZ + A.buf_words;
-  V.stack = V.bufW + A.buf_words;
+  V.warps = g + 5 * l + 3 * A.desc_cap;
+  V.warp_words = A.warp_words;
+  V.stack = V.warps + kWarps * A.warp_words;
   for (;;) {
     if (threadIdx.x == 0) S.q = (*(volatile int*)A.stop) ? A.n_queue : (int)atomicAdd(A.next, 1u);
     __syncthreads();
@@ -748,7 +808,7 @@ __global__ void __launch_bounds__(kThreads, 4) factor_units_kernel(DevBuildArgs 
   }
 }
 
-size_t dyn_smem(int l) { return (size_t)l * (6 * sizeof(double) + sizeof(int)); }
+size_t dyn_smem(int l) { return (size_t)l * 3 * sizeof(double); }
 
 int leaf_levels(int n, int rows, int C, int mbr) {
   int lam = 0;
@@ -777,10 +837,11 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
   check(cudaSetDevice(device), "cudaSetDevice");
 
   // Scratch bounds per CTA, over every unit and every number of kept rows:
-  // leaf and merge blocks hold at most (rows + 2^lam) x (leaf width) values;
-  // the stack holds one group per level, a group at level j at most
-  // rows x min(rows / 2^(j-1) + 1, 2^(j-1) x leaf width), plus the group
-  // being merged.
+  // a leaf or merge block holds at most (rows + 2^lam) x (leaf width)
+  // values; a group at level j at most rows x min(rows / 2^(j-1) + 1,
+  // 2^(j-1) x leaf width).  The stack holds one group per level, a batch of
+  // up to kBatch leaves, and the new groups of a merge round before they
+  // move down.
   long long buf_words = 1, stack_words = 1;
   int max_lam = 0;
   for (int n = 1; n <= l; ++n) {
@@ -797,12 +858,15 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
         sum += gj;
         gmax = std::max(gmax, gj);
       }
-      stack_words = std::max(stack_words, sum + gmax);
+      const long long batch = (long long)std::min(kBatch, 1 << lam) * rows * std::min(rows + 1, wd);
+      stack_words = std::max(stack_words, sum + gmax + 2 * batch);
       max_lam = std::max(max_lam, lam);
     }
   }
-  const long long desc_cap = 3LL << (max_lam + 1);
-  const long long scratch_words = 5LL * l + 3 * desc_cap + 2 * buf_words + stack_words;
+  const long long desc_cap = (4LL << (max_lam + 1)) + 4 * kBatch;
+  // per warp: Z and W (buf_words each), nrm and ref (l each), perm (l ints)
+  const long long warp_words = 2 * buf_words + 3LL * l;
+  const long long scratch_words = 5LL * l + 3 * desc_cap + kWarps * warp_words + stack_words;
 
   int sms = 0;
   check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "SM count");
@@ -843,7 +907,7 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
   check(cudaMalloc(&d_queue.p, sizeof(int) * 2 * L), "cudaMalloc queue");
   check(cudaMalloc(&d_ctl.p, 64), "cudaMalloc control");
   check(cudaMalloc(&d_status.p, sizeof(int) * 2 * L), "cudaMalloc status");
-  check(cudaMalloc(&d_info.p, sizeof(long long) * 3 * 2 * L), "cudaMalloc info");
+  check(cudaMalloc(&d_info.p, sizeof(long long) * 2 * 2 * L), "cudaMalloc info");
   check(cudaMalloc(&d_scratch.p, 8 * (size_t)scratch_words * ctas), "cudaMalloc scratch");
   check(cudaMalloc(&d_arena.p, arena_bytes), "cudaMalloc arena");
   double* dn = static_cast<double*>(d_nodes.p);
@@ -873,13 +937,14 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
   A.buf_words = buf_words;
   A.stack_words = stack_words;
   A.desc_cap = desc_cap;
+  A.warp_words = warp_words;
   A.arena = static_cast<unsigned char*>(d_arena.p);
   A.arena_bytes = arena_bytes;
   A.status = static_cast<int*>(d_status.p);
   A.info = static_cast<long long*>(d_info.p);
 
   std::vector<int> status(2 * L, kPending);
-  std::vector<long long> info(3 * 2 * L);
+  std::vector<long long> info(2 * 2 * L);
   std::vector<unsigned char> host;
   std::vector<int> pending = order;
   while (!pending.empty()) {
@@ -898,7 +963,7 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
     check(cudaDeviceSynchronize(), "factor_units_kernel");
     P.t_factor_kernel += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     check(cudaMemcpy(status.data(), d_status.p, sizeof(int) * 2 * L, cudaMemcpyDeviceToHost), "status");
-    check(cudaMemcpy(info.data(), d_info.p, sizeof(long long) * 3 * 2 * L, cudaMemcpyDeviceToHost), "info");
+    check(cudaMemcpy(info.data(), d_info.p, sizeof(long long) * 2 * 2 * L, cudaMemcpyDeviceToHost), "info");
     check(cudaMemcpy(&c0, ctl, sizeof(c0), cudaMemcpyDeviceToHost), "control");
     for (int u : pending)
       if (status[u] == kNoScratch)
@@ -936,9 +1001,8 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
           U.m = u / 2;
           U.p = u % 2;
           U.n = std::max(0, (L - U.m - U.p + 1) / 2);
-          U.rows = (int)info[3 * u];
-          U.levels = (int)info[3 * u + 1];
-          U.peak_words = info[3 * u + 2];
+          U.rows = (int)info[2 * u];
+          U.levels = (int)info[2 * u + 1];
           std::vector<FinalBlock> top;
           for (size_t off : recs[u]) {
             RecHdr h;
@@ -971,7 +1035,23 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
               top.push_back(std::move(f));
             }
           }
-          if (U.n > 0 && U.rows > 0) finish_unit(P, U, std::move(top));
+          if (U.n > 0 && U.rows > 0) {
+            // records arrive in whatever order the warps finished: put the
+            // blocks in the host's depth-first creation order (a group is
+            // made right after the last leaf under it; lower levels first)
+            // and the top bands in band order, so that the streams do not
+            // depend on timing
+            auto created = [](const IdBlock& b) {
+              return std::make_tuple(((long long)b.group + 1) << (b.level - 1), b.level, b.band);
+            };
+            std::sort(U.blocks.begin(), U.blocks.end(),
+                      [&](const IdBlock& x, const IdBlock& y) { return created(x) < created(y); });
+            std::sort(top.begin(), top.end(), [](const FinalBlock& x, const FinalBlock& y) { return x.band < y.band; });
+            // the host's depth-first order, replayed from the ranks: its
+            // peak memory (the device batches leaves, so its own differs)
+            U.peak_words = depth_first_peak(U);
+            finish_unit(P, U, std::move(top));
+          }
           out[u] = std::move(U);
         }
       } catch (const std::exception& e) {

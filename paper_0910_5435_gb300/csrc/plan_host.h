@@ -135,6 +135,11 @@ int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm,
 // indices, and stores the unit dense when that is cheaper.
 void finish_unit(const PlanHost& P, UnitFact& U, std::vector<FinalBlock>&& top);
 
+// Peak float64 words of the host's depth-first build of U (the skeleton
+// columns of the groups on its stack, plus two copies of the leaf being
+// factored), replayed from the ranks of U's ID blocks.
+long long depth_first_peak(const UnitFact& U);
+
 // Factorization of the one parity block (m, p) with threshold eps (Section 3,
 // depth-first); P needs only l, the nodes and the build options.
 UnitFact factor_single_unit(const PlanHost& P, int m, int p, double eps);

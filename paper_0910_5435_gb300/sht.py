@@ -96,6 +96,7 @@ class sht_plan_stats(ctypes.Structure):
         ("page_bytes", ctypes.c_int),
         ("t_factor", ctypes.c_double),
         ("t_factor_kernel", ctypes.c_double),
+        ("factor_flops", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -107,6 +107,8 @@ def test_device_and_host_builds_agree(sht, l, C):
     assert abs(sd["k_avg"] - sh["k_avg"]) <= 0.005 * sh["k_avg"]
     assert abs(sd["k_max"] - sh["k_max"]) <= 1
     assert abs(sd["factor_values"] - sh["factor_values"]) <= 0.01 * sh["factor_values"]
+    # the peak memory of the depth-first order, replayed from the device's ranks
+    assert abs(sd["m_max_words"] - sh["m_max_words"]) <= 0.02 * sh["m_max_words"]
     # interpolation coefficients of the same size (plain column pivoting bounds
     # them only loosely; the host's own largest is the yardstick)
     assert sd["max_abs_T"] <= 2.0 * max(sh["max_abs_T"], 1.0)

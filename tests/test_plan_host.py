@@ -120,6 +120,7 @@ def test_stats_follow_paper_columns():
     assert s["l"] == 64 and s["n_units"] == 128
     assert s["t_quad"] >= 0 and s["t_comp"] > 0
     assert s["m_max_words"] > 0
+    assert s["factor_flops"] > 0 and s["t_factor"] > 0 and s["t_factor_kernel"] == 0.0
     assert s["k_sigma"] >= 0
     assert s["max_abs_T"] < 1e3
     assert math.isfinite(s["k_avg"])
