@@ -1304,8 +1304,8 @@ void emit_streams(PlanHost& P, int prec) {
       pages += e.n_pages;
     }
     if (nvals / 16 > 0xFFFFFFFFull) throw std::runtime_error("value region exceeds 64 GB");
-    std::vector<uint8_t>().swap(S.bytes);
-    std::vector<uint8_t>().swap(S.values);
+    ByteBuf().swap(S.bytes);
+    ByteBuf().swap(S.values);
     S.bytes.resize(nbytes + PB);
     S.values.resize(nvals);
     // rebase each item's value references onto the joined value region and

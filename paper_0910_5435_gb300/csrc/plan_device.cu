@@ -945,7 +945,7 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
 
   std::vector<int> status(2 * L, kPending);
   std::vector<long long> info(2 * 2 * L);
-  std::vector<unsigned char> host;
+  ByteBuf host;
   std::vector<int> pending = order;
   while (!pending.empty()) {
     check(cudaMemcpy(d_queue.p, pending.data(), sizeof(int) * pending.size(), cudaMemcpyHostToDevice), "queue");

@@ -12,6 +12,7 @@
 #include <atomic>
 #include <memory>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "recurrence.h"
@@ -63,9 +64,32 @@ struct UnitFact {
   double cost = 0;           // estimated apply cost (bytes), for LPT ordering
 };
 
+// Allocator whose resize leaves new elements uninitialised, so that a large
+// buffer is first touched (and its pages faulted in) by the threads that
+// fill it rather than by one zeroing pass.
+template <class T>
+struct UninitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = UninitAlloc<U>;
+  };
+  UninitAlloc() = default;
+  template <class U>
+  UninitAlloc(const UninitAlloc<U>&) {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    ::new (static_cast<void*>(p)) U(std::forward<Args>(args)...);
+  }
+};
+using ByteBuf = std::vector<uint8_t, UninitAlloc<uint8_t>>;
+
 struct Stream {
-  std::vector<uint8_t> bytes;        // n_pages * page_bytes
-  std::vector<uint8_t> values;       // value region (ops with F_VALUES_APART)
+  ByteBuf bytes;                     // n_pages * page_bytes
+  ByteBuf values;                    // value region (ops with F_VALUES_APART)
   std::vector<UnitEntry> units;      // LPT order
   int max_buf_ab = 0;                // elements needed in each shared vector
   int num_vecs = 2;                  // shared vectors used
