@@ -141,6 +141,12 @@ typedef struct {
    * differ where a residual norm sits at eps_id, since the QR rounds in
    * another order.  Needs host_only = 0.  Default 0. */
   int device_build;
+  /* Device build only: the most device memory, in MB, for the records the
+   * GPU writes back (0 = automatic: half the dense operator, at most a
+   * quarter of the free memory).  Blocks that do not fit are built again in
+   * further launches, each ending with the same streams; a budget too small
+   * for the largest single block fails with SHT_ERR_INVALID_ARG. */
+  int device_build_arena_mb;
 } sht_plan_opts;
 
 typedef struct {

@@ -235,6 +235,9 @@ sht_status build_host(sht_plan_t P, int q) {
     H.t_comp += now_s() - t0;
   } catch (const std::bad_alloc&) {
     return SHT_ERR_OOM;
+  } catch (const sht::DeviceError& e) {
+    set_detail("plan build", e.what());
+    return SHT_ERR_CUDA;
   } catch (const std::exception& e) {
     set_detail("plan build", e.what());
     return SHT_ERR_INVALID_ARG;
@@ -470,6 +473,7 @@ sht_status sht_plan_opts_default(sht_plan_opts* o) {
   o->debug_unmet_dependency = 0;
   o->slot_values = 0;
   o->device_build = 0;
+  o->device_build_arena_mb = 0;
   return SHT_OK;
 }
 
@@ -493,6 +497,7 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   if (o.page_bytes < 4096 || o.page_bytes > 49152 || (o.page_bytes % 1024) != 0) return SHT_ERR_INVALID_ARG;
   if (o.num_threads < 0) return SHT_ERR_INVALID_ARG;
   if (o.device_build != 0 && (o.device_build != 1 || o.host_only)) return SHT_ERR_INVALID_ARG;
+  if (o.device_build_arena_mb < 0) return SHT_ERR_INVALID_ARG;
   if (o.consumer_warps != 0 && o.consumer_warps != 8 && o.consumer_warps != 12 && o.consumer_warps != 16)
     return SHT_ERR_INVALID_ARG;
   if (o.slot_values != 0 && (o.slot_values < sht::kMinSlotValues || o.slot_values > sht::kMaxSlotValues ||
@@ -519,6 +524,7 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   for (int q = 0; q < 3; ++q) H.values_apart[q] = (o.values_inline == 0);
   H.debug_unmet_dep = o.debug_unmet_dependency != 0;
   H.slot_values = o.slot_values ? o.slot_values : sht::kDefaultSlotValues;
+  H.device_arena_bytes = (long long)o.device_build_arena_mb << 20;
 
   if (!P->host_only) {
     int dev = 0, count = 0;

@@ -824,7 +824,7 @@ struct CudaBuf {
 };
 
 void check(cudaError_t e, const char* what) {
-  if (e != cudaSuccess) throw std::runtime_error(std::string("device build: ") + what + ": " + cudaGetErrorString(e));
+  if (e != cudaSuccess) throw DeviceError(std::string("device build: ") + what + ": " + cudaGetErrorString(e));
 }
 
 }  // namespace
@@ -889,6 +889,7 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
     for (int p = 0; p < 2; ++p) dense += (long long)l * std::max(0, (L - m - p + 1) / 2);
   unsigned long long arena_bytes =
       std::min<unsigned long long>(4ULL * dense + (64ULL << 20), free_b / 4);
+  if (P.device_arena_bytes > 0) arena_bytes = std::min<unsigned long long>(arena_bytes, P.device_arena_bytes);
   arena_bytes &= ~15ULL;
 
   // node data, as the host's column generator computes it
@@ -947,6 +948,9 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
   std::vector<long long> info(2 * 2 * L);
   ByteBuf host;
   std::vector<int> pending = order;
+  // CTAs per launch: all of them, or one when a launch finished no block
+  // (its blocks' records crowded each other out of the arena)
+  long long grid_limit = ctas;
   while (!pending.empty()) {
     check(cudaMemcpy(d_queue.p, pending.data(), sizeof(int) * pending.size(), cudaMemcpyHostToDevice), "queue");
     struct {
@@ -956,7 +960,7 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
     } c0{0, 0, 0, ~0ULL};
     check(cudaMemcpy(ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice), "control");
     A.n_queue = (int)pending.size();
-    const int grid = (int)std::min<long long>(ctas, (long long)pending.size());
+    const int grid = (int)std::min<long long>(grid_limit, (long long)pending.size());
     const auto t0 = std::chrono::steady_clock::now();
     factor_units_kernel<<<grid, kThreads, smem>>>(A);
     check(cudaGetLastError(), "launch");
@@ -985,7 +989,11 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
     }
     std::vector<int> done, next_wave;
     for (int u : pending) (status[u] == kDone ? done : next_wave).push_back(u);
-    if (done.empty()) throw std::runtime_error("device build: the output arena cannot hold one unit");
+    if (done.empty()) {
+      if (grid_limit == 1) throw std::invalid_argument("device build: the output arena cannot hold one unit");
+      grid_limit = 1;
+      continue;
+    }
 
     std::atomic<int> cursor(0);
     int nt = P.num_threads > 0 ? P.num_threads : (int)std::thread::hardware_concurrency();

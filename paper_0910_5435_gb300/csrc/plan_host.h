@@ -11,6 +11,7 @@
 #include <cmath>
 #include <atomic>
 #include <memory>
+#include <stdexcept>
 #include <string>
 #include <utility>
 #include <vector>
@@ -102,6 +103,7 @@ struct PlanHost {
   int slot_values = kDefaultSlotValues;  // cap on the values of one op kept apart
   bool values_apart[3] = {true, true, true};  // per precision: value blocks outside the pages
   bool debug_unmet_dep = false;  // plant a never-met predecessor (failure-detection tests)
+  long long device_arena_bytes = 0;  // device build: record arena limit (0 = automatic)
   // Gauss-Legendre nodes (all 2l, ascending), weights, and the angle of each
   // positive node (theta_{l+i} in (0, pi/2)).
   std::vector<double> x, w, theta_pos;
@@ -172,8 +174,15 @@ UnitFact factor_single_unit(const PlanHost& P, int m, int p, double eps);
 // (Section 3, depth-first).  fp32 selects fact32 instead of fact64.
 void build_factorizations(PlanHost& P, bool fp32);
 
+// A CUDA call failed inside a host-side builder.
+struct DeviceError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
 // As build_factorizations, computed on CUDA device `device` (plan_device.cu);
-// throws std::runtime_error if the device fails or a bound is exceeded.
+// throws DeviceError if a CUDA call fails, std::invalid_argument if the
+// record arena cannot hold a single block, std::runtime_error if a scratch
+// bound is exceeded.
 void build_factorizations_device(PlanHost& P, bool fp32, int device);
 
 // Encodes one precision's factor streams (both directions) into pages.

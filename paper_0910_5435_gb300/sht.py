@@ -63,6 +63,7 @@ class sht_plan_opts(ctypes.Structure):
         ("debug_unmet_dependency", ctypes.c_int),
         ("slot_values", ctypes.c_int),
         ("device_build", ctypes.c_int),
+        ("device_build_arena_mb", ctypes.c_int),
     ]
 
 
@@ -193,7 +194,7 @@ class Plan:
 
     def __init__(self, l, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, host_only=False,
                  num_threads=0, page_bytes=0, eps_fp32=0.0, consumer_warps=0, values_inline=0,
-                 debug_unmet_dependency=0, slot_values=0, device_build=False):
+                 debug_unmet_dependency=0, slot_values=0, device_build=False, device_build_arena_mb=0):
         L = lib()
         opts = sht_plan_opts()
         _check(L.sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
@@ -209,6 +210,7 @@ class Plan:
         opts.debug_unmet_dependency = debug_unmet_dependency
         opts.slot_values = slot_values
         opts.device_build = 1 if device_build else 0
+        opts.device_build_arena_mb = device_build_arena_mb
         h = ctypes.c_void_p()
         _check(L.sht_plan_create_ex(int(l), float(eps_id), ctypes.byref(opts), ctypes.byref(h)),
                "sht_plan_create_ex")

@@ -134,6 +134,28 @@ def test_device_build_is_reproducible(sht):
     b.close()
 
 
+def test_small_arena_builds_in_waves(sht):
+    """A 1 MB record arena cannot hold a whole l = 128 build: the device
+    builds the blocks that fit, then the rest in further launches (one CTA at
+    a time when a launch finished nothing), and the streams are those of a
+    build in one launch."""
+    a = sht.Plan(128, 1e-12, leaf_cols=16, device_build=True)
+    b = sht.Plan(128, 1e-12, leaf_cols=16, device_build=True, device_build_arena_mb=1)
+    for d in (0, 1):
+        assert all(np.array_equal(x, y) for x, y in zip(a.stream(0, d), b.stream(0, d)))
+    beta = inputs.random_beta(128, seed=16)
+    assert rel(synth(sht, b, 0, beta), oracle.legendre_synthesis(beta, 128)) < 1e-10
+    a.close()
+    b.close()
+
+
+def test_arena_too_small_for_one_block_is_an_error(sht):
+    with pytest.raises(sht.ShtError) as e:
+        sht.Plan(1024, 1e-12, leaf_cols=32, page_bytes=8192, device_build=True, device_build_arena_mb=1)
+    assert e.value.code == 1
+    assert b"cannot hold one unit" in sht.lib().sht_last_error_detail()
+
+
 def test_device_build_l1024_sampled_orders(sht):
     """The bench configuration (l = 1024, C = 32, 8 KB pages) built on the
     device, checked on sampled orders against the oracle."""
