@@ -147,6 +147,14 @@ typedef struct {
    * further launches, each ending with the same streams; a budget too small
    * for the largest single block fails with SHT_ERR_INVALID_ARG. */
   int device_build_arena_mb;
+  /* Path of a plan file used as a cache (NULL: none).  When the file exists,
+   * is intact and was made with the same l, eps_id, leaf_cols, trim and band
+   * options, the plan reads its factorizations from it instead of computing
+   * them (see sht_plan_load); otherwise it computes them and writes the file
+   * (sht_plan_save), replacing a stale or corrupt one (the reason is left in
+   * sht_last_error_detail).  A failed write fails plan creation with
+   * SHT_ERR_INVALID_ARG.  The string is read during the call only. */
+  const char* plan_cache;
 } sht_plan_opts;
 
 typedef struct {
@@ -213,6 +221,28 @@ sht_status sht_plan_get_stats(sht_plan_t plan, sht_plan_stats* out);
 /* Builds (host) and uploads (device) the factor streams of one precision.
  * Synchronous.  Idempotent. */
 sht_status sht_prepare(sht_plan_t plan, sht_precision prec);
+
+/* Plan files.  The precomputation (Sections 3 and 4: columns, IDs,
+ * depth-first merges) dominates a plan's cold start, so a plan's
+ * factorizations can be kept on disk.  A plan file holds a versioned header
+ * with the options the factorizations were computed with, a table of
+ * per-block offsets and checksums, and the factorizations (float64, and
+ * float32 if that precision was prepared).  Factor streams are not stored:
+ * they are re-encoded on load for the caller's page size and value cap. */
+
+/* Writes the plan's factorizations to path (through a temporary file renamed
+ * into place).  Synchronous; SHT_ERR_INVALID_ARG with a detail on I/O
+ * errors. */
+sht_status sht_plan_save(sht_plan_t plan, const char* path);
+
+/* Creates a plan from a plan file: l, eps_id and the factorization options
+ * (leaf_cols, trim_eps, min_band_rows, eps_fp32) come from the file, the
+ * other options (page_bytes, host_only, consumer_warps, ...) from opts (NULL:
+ * defaults).  The streams are then encoded and uploaded as by
+ * sht_plan_create_ex.  SHT_ERR_INVALID_ARG if the file cannot be opened;
+ * SHT_ERR_PLAN_CORRUPT if it is truncated, of another format version, or a
+ * checksum or size does not match. */
+sht_status sht_plan_load(const char* path, const sht_plan_opts* opts, sht_plan_t* out);
 
 /* The plan's Gauss-Legendre nodes x[2l] (ascending) and weights w[2l] (host
  * arrays owned by the caller). */

@@ -27,7 +27,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CXXFLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-function"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
 
-CPP_SOURCES = ["plan_build.cpp", "unit_stats.cpp"]
+CPP_SOURCES = ["plan_build.cpp", "unit_stats.cpp", "plan_io.cpp"]
 CU_SOURCES = ["capi.cu", "sweep.cu", "direct.cu", "phi.cu", "noalloc.cu", "batch.cu", "plan_device.cu"]
 HEADERS = ["sht_stream.h", "plan_host.h", "kernels.h", "plan_access.h", "recurrence.h"]
 

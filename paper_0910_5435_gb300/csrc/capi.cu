@@ -474,6 +474,7 @@ sht_status sht_plan_opts_default(sht_plan_opts* o) {
   o->slot_values = 0;
   o->device_build = 0;
   o->device_build_arena_mb = 0;
+  o->plan_cache = nullptr;
   return SHT_OK;
 }
 
@@ -481,7 +482,77 @@ sht_status sht_plan_create(int l, double eps_id, sht_plan_t* out) {
   return sht_plan_create_ex(l, eps_id, nullptr, out);
 }
 
+namespace {
+
+// Loads the factorizations of a plan file into P when the file was made
+// with P's factorization options (true); false when the file does not exist
+// or was made with other options.  Throws sht::PlanFileError if the file is
+// corrupt.
+bool load_plan_file(sht_plan_t P, const std::string& path) {
+  sht::PlanFileInfo info;
+  if (!sht::read_plan_file_header(path, &info)) return false;
+  const PlanHost& H = P->H;
+  if (info.l != H.l || info.eps_id != H.eps_id || info.leaf_cols != H.leaf_cols ||
+      info.min_band_rows != H.min_band_rows || info.trim_eps != H.trim_eps)
+    return false;
+  sht::load_factorizations(P->H, path);
+  if (!info.has_fp32 || info.eps_fp32 != H.eps_fp32) P->H.fact32.clear();
+  return true;
+}
+
+sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const char* must_load, sht_plan_t* out);
+
+}  // namespace
+
 sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, sht_plan_t* out) {
+  return create_plan(l, eps_id, opts, nullptr, out);
+}
+
+sht_status sht_plan_load(const char* path, const sht_plan_opts* opts, sht_plan_t* out) {
+  if (!path || !out) return SHT_ERR_INVALID_ARG;
+  *out = nullptr;
+  sht::PlanFileInfo info;
+  try {
+    if (!sht::read_plan_file_header(path, &info)) {
+      set_detail("sht_plan_load", (std::string("cannot open ") + path).c_str());
+      return SHT_ERR_INVALID_ARG;
+    }
+  } catch (const sht::PlanFileError& e) {
+    set_detail("sht_plan_load", e.what());
+    return SHT_ERR_PLAN_CORRUPT;
+  }
+  sht_plan_opts o;
+  if (opts) {
+    o = *opts;
+  } else {
+    sht_plan_opts_default(&o);
+  }
+  // the factorization options are the file's; the rest are the caller's
+  o.leaf_cols = info.leaf_cols;
+  o.min_band_rows = info.min_band_rows;
+  o.trim_eps = info.trim_eps;
+  o.eps_fp32 = info.eps_fp32;
+  o.plan_cache = nullptr;
+  return create_plan(info.l, info.eps_id, &o, path, out);
+}
+
+sht_status sht_plan_save(sht_plan_t P, const char* path) {
+  if (!P || !path) return SHT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(P->mu);
+  try {
+    sht::save_factorizations(P->H, path);
+  } catch (const std::bad_alloc&) {
+    return SHT_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_detail("sht_plan_save", e.what());
+    return SHT_ERR_INVALID_ARG;
+  }
+  return SHT_OK;
+}
+
+namespace {
+
+sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const char* must_load, sht_plan_t* out) {
   if (!out) return SHT_ERR_INVALID_ARG;
   *out = nullptr;
   sht_plan_opts o;
@@ -548,10 +619,49 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
     delete P;
     return SHT_ERR_INVALID_ARG;
   }
+  // a plan file replaces the factorization (sht_plan_load: it must; a cache
+  // file: when it was made with the same options and is intact)
+  const char* file = must_load ? must_load : o.plan_cache;
+  bool loaded = false;
+  if (file) {
+    try {
+      const double t0 = now_s();
+      loaded = load_plan_file(P, file);
+      H.t_comp += now_s() - t0;
+    } catch (const std::bad_alloc&) {
+      delete P;
+      return SHT_ERR_OOM;
+    } catch (const sht::PlanFileError& e) {
+      set_detail(must_load ? "sht_plan_load" : "plan cache (rebuilt)", e.what());
+      if (must_load) {
+        delete P;
+        return SHT_ERR_PLAN_CORRUPT;
+      }
+    } catch (const std::exception& e) {
+      set_detail(must_load ? "sht_plan_load" : "plan cache (rebuilt)", e.what());
+      if (must_load) {
+        delete P;
+        return SHT_ERR_INVALID_ARG;
+      }
+    }
+    if (must_load && !loaded) {
+      delete P;
+      return SHT_ERR_INVALID_ARG;
+    }
+  }
   sht_status s = build_host(P, sht::PREC_FP64);
   if (s != SHT_OK) {
     delete P;
     return s;
+  }
+  if (o.plan_cache && !loaded) {
+    try {
+      sht::save_factorizations(H, o.plan_cache);
+    } catch (const std::exception& e) {
+      set_detail("plan cache", e.what());
+      delete P;
+      return SHT_ERR_INVALID_ARG;
+    }
   }
   if (!P->host_only) {
     std::vector<double> invw(l), wpos(l);
@@ -596,6 +706,8 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
   *out = P;
   return SHT_OK;
 }
+
+}  // namespace
 
 sht_status sht_plan_destroy(sht_plan_t P) {
   if (!P) return SHT_OK;

@@ -185,6 +185,31 @@ struct DeviceError : std::runtime_error {
 // bound is exceeded.
 void build_factorizations_device(PlanHost& P, bool fp32, int device);
 
+// A plan file is truncated, corrupt or of another format.
+struct PlanFileError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+// The options a plan file's factorizations were computed with.
+struct PlanFileInfo {
+  int l = 0, leaf_cols = 0, min_band_rows = 0;
+  double eps_id = 0, trim_eps = 0, eps_fp32 = 0;
+  bool has_fp32 = false;
+};
+
+// Writes P's factorizations (float64, and float32 if built) to path, through
+// a temporary file renamed into place (plan_io.cpp).  Throws
+// std::runtime_error on I/O errors.
+void save_factorizations(const PlanHost& P, const std::string& path);
+
+// Reads a plan file's header: false if the file cannot be opened, throws
+// PlanFileError if it is not a valid plan file.
+bool read_plan_file_header(const std::string& path, PlanFileInfo* info);
+
+// Replaces P's factorizations by those of the file (P.l must match).  Throws
+// PlanFileError on any mismatch, std::runtime_error if it cannot be opened.
+void load_factorizations(PlanHost& P, const std::string& path);
+
 // Encodes one precision's factor streams (both directions) into pages.
 void emit_streams(PlanHost& P, int prec);
 

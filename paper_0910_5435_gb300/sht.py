@@ -35,6 +35,7 @@ EXPORTS = [
     "sht_batch_create", "sht_batch_destroy", "sht_batch_synthesize", "sht_batch_analyze",
     "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config", "sht_batch_synthesize_adjoint",
     "sht_unit_stats_compute", "sht_gauss_jacobi_nodes", "sht_unit_stats_gauss_jacobi",
+    "sht_plan_save", "sht_plan_load",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -43,7 +44,7 @@ NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
 class ShtError(RuntimeError):
     def __init__(self, code, where):
         detail = ""
-        if code in (2, 3) and _lib is not None:
+        if code in (2, 3, 4) and _lib is not None:
             detail = " (" + (_lib.sht_last_error_detail() or b"").decode(errors="replace") + ")"
         super().__init__(f"{where}: {STATUS.get(code, code)}{detail}")
         self.code = code
@@ -64,6 +65,7 @@ class sht_plan_opts(ctypes.Structure):
         ("slot_values", ctypes.c_int),
         ("device_build", ctypes.c_int),
         ("device_build_arena_mb", ctypes.c_int),
+        ("plan_cache", ctypes.c_char_p),
     ]
 
 
@@ -124,6 +126,8 @@ def lib():
     L.sht_plan_create.argtypes = [c_int, c_double, ctypes.POINTER(vp)]
     L.sht_plan_create_ex.argtypes = [c_int, c_double, ctypes.POINTER(sht_plan_opts), ctypes.POINTER(vp)]
     L.sht_plan_destroy.argtypes = [vp]
+    L.sht_plan_save.argtypes = [vp, ctypes.c_char_p]
+    L.sht_plan_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(sht_plan_opts), ctypes.POINTER(vp)]
     L.sht_plan_get_stats.argtypes = [vp, ctypes.POINTER(sht_plan_stats)]
     L.sht_prepare.argtypes = [vp, c_int]
     L.sht_plan_nodes.argtypes = [vp, vp, vp]
@@ -194,7 +198,8 @@ class Plan:
 
     def __init__(self, l, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, host_only=False,
                  num_threads=0, page_bytes=0, eps_fp32=0.0, consumer_warps=0, values_inline=0,
-                 debug_unmet_dependency=0, slot_values=0, device_build=False, device_build_arena_mb=0):
+                 debug_unmet_dependency=0, slot_values=0, device_build=False, device_build_arena_mb=0,
+                 plan_cache=None, _load=None):
         L = lib()
         opts = sht_plan_opts()
         _check(L.sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
@@ -211,12 +216,29 @@ class Plan:
         opts.slot_values = slot_values
         opts.device_build = 1 if device_build else 0
         opts.device_build_arena_mb = device_build_arena_mb
+        cache = os.fsencode(plan_cache) if plan_cache is not None else None
+        opts.plan_cache = cache
         h = ctypes.c_void_p()
-        _check(L.sht_plan_create_ex(int(l), float(eps_id), ctypes.byref(opts), ctypes.byref(h)),
-               "sht_plan_create_ex")
+        if _load is not None:
+            _check(L.sht_plan_load(os.fsencode(_load), ctypes.byref(opts), ctypes.byref(h)), "sht_plan_load")
+        else:
+            _check(L.sht_plan_create_ex(int(l), float(eps_id), ctypes.byref(opts), ctypes.byref(h)),
+                   "sht_plan_create_ex")
         self.handle = h
+        if _load is not None:
+            l = self.stats()["l"]
         self.l = int(l)
         self.host_only = host_only
+
+    @classmethod
+    def load(cls, path, **opts):
+        """A plan whose factorizations are read from a plan file (sht_plan_load);
+        opts are the run-time options (page_bytes, host_only, ...)."""
+        return cls(0, _load=path, **opts)
+
+    def save(self, path):
+        """Writes the plan's factorizations to a plan file (sht_plan_save)."""
+        _check(lib().sht_plan_save(self.handle, os.fsencode(path)), "sht_plan_save")
 
     def close(self):
         if getattr(self, "handle", None):

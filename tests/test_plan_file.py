@@ -1,0 +1,127 @@
+"""Plan files (sht_plan_save / sht_plan_load and the plan_cache option), on
+the host: a saved and reloaded plan encodes the same streams, and truncated,
+corrupted or foreign files are refused with SHT_ERR_PLAN_CORRUPT."""
+
+import os
+
+import numpy as np
+import pytest
+
+from paper_0910_5435_gb300 import sht
+
+CORRUPT, INVALID = 4, 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def same_streams(a, b, precs=(0,)):
+    return all(np.array_equal(x, y) for q in precs for d in (0, 1) for x, y in zip(a.stream(q, d), b.stream(q, d)))
+
+
+@pytest.fixture(scope="module")
+def saved(tmp_path_factory):
+    P = sht.Plan(64, 1e-12, leaf_cols=16, host_only=True)
+    P.prepare(sht.SHT_FP32)
+    path = str(tmp_path_factory.mktemp("plans") / "l64.plan")
+    P.save(path)
+    return P, path
+
+
+@pytest.mark.parametrize("l,C", [(1, 4), (2, 4), (16, 4), (128, 64)])
+def test_round_trip_gives_the_same_streams(tmp_path, l, C):
+    P = sht.Plan(l, 1e-12, leaf_cols=C, host_only=True)
+    path = str(tmp_path / "p.plan")
+    P.save(path)
+    Q = sht.Plan.load(path, host_only=True)
+    assert Q.l == l
+    assert same_streams(P, Q)
+    sp, sq = P.stats(), Q.stats()
+    for key in ("n_blocks", "k_max", "k_avg", "factor_values", "rows_kept", "m_max_words", "leaf_cols"):
+        assert sp[key] == sq[key], key
+    assert sq["t_factor"] == 0.0  # nothing was factored
+
+
+def test_float32_factorization_is_kept_and_options_come_from_the_file(saved):
+    P, path = saved
+    Q = sht.Plan.load(path, host_only=True, leaf_cols=40, page_bytes=16384)
+    s = Q.stats()
+    assert s["leaf_cols"] == 16 and s["page_bytes"] == 16384
+    Q.prepare(sht.SHT_FP32)
+    assert Q.stats()["t_factor"] == 0.0  # the float32 factorization came from the file
+    R = sht.Plan.load(path, host_only=True)
+    assert same_streams(P, R, precs=(0, 1))
+
+
+def corrupt_copy(path, tmp_path, edit):
+    data = bytearray(open(path, "rb").read())
+    data = edit(data)
+    out = str(tmp_path / "bad.plan")
+    with open(out, "wb") as f:
+        f.write(bytes(data))
+    return out
+
+
+@pytest.mark.parametrize("what", ["payload byte", "table byte", "header field", "magic", "version",
+                                  "truncated payload", "truncated header", "trailing bytes"])
+def test_damaged_files_are_refused(saved, tmp_path, what):
+    _, path = saved
+    size = os.path.getsize(path)
+
+    def edit(d):
+        if what == "payload byte":
+            d[size - 1000] ^= 0x40
+        elif what == "table byte":
+            d[128 + 30] ^= 0x01
+        elif what == "header field":
+            d[24] ^= 0x01  # min_band_rows
+        elif what == "magic":
+            d[0:8] = b"NOTAPLAN"
+        elif what == "version":
+            d[8] = 99
+        elif what == "truncated payload":
+            d = d[:size - 4096]
+        elif what == "truncated header":
+            d = d[:100]
+        elif what == "trailing bytes":
+            d = d + bytes(16)
+        return d
+
+    bad = corrupt_copy(path, tmp_path, edit)
+    with pytest.raises(sht.ShtError) as e:
+        sht.Plan.load(bad, host_only=True)
+    assert e.value.code == CORRUPT, what
+
+
+def test_missing_file_and_unwritable_path(tmp_path):
+    with pytest.raises(sht.ShtError) as e:
+        sht.Plan.load(str(tmp_path / "none.plan"), host_only=True)
+    assert e.value.code == INVALID
+    P = sht.Plan(8, 1e-12, leaf_cols=4, host_only=True)
+    with pytest.raises(sht.ShtError) as e:
+        P.save(str(tmp_path / "no_such_dir" / "p.plan"))
+    assert e.value.code == INVALID
+
+
+def test_plan_cache_builds_once_and_rebuilds_when_stale(tmp_path):
+    cache = str(tmp_path / "cache.plan")
+    a = sht.Plan(64, 1e-12, leaf_cols=16, host_only=True, plan_cache=cache)
+    assert os.path.exists(cache) and a.stats()["t_factor"] > 0
+    b = sht.Plan(64, 1e-12, leaf_cols=16, host_only=True, plan_cache=cache)
+    assert b.stats()["t_factor"] == 0.0 and same_streams(a, b)
+    # other options: the file is not used, and is replaced
+    c = sht.Plan(64, 1e-12, leaf_cols=32, host_only=True, plan_cache=cache)
+    assert c.stats()["t_factor"] > 0
+    d = sht.Plan.load(cache, host_only=True)
+    assert d.stats()["leaf_cols"] == 32
+    # a damaged cache is rebuilt (and the reason recorded)
+    data = bytearray(open(cache, "rb").read())
+    data[-100] ^= 0x10
+    open(cache, "wb").write(bytes(data))
+    e = sht.Plan(64, 1e-12, leaf_cols=32, host_only=True, plan_cache=cache)
+    assert e.stats()["t_factor"] > 0 and same_streams(c, e)
+    assert b"rebuilt" in sht.lib().sht_last_error_detail()
+    sht.Plan.load(cache, host_only=True)  # rewritten intact
