@@ -461,16 +461,40 @@ sht_status sht_batch_analyze(sht_batch_t batch, const void* const* G, void* cons
 sht_status sht_batch_synthesize_adjoint(sht_batch_t batch, const void* const* G, void* const* beta,
                                         sht_stream_t stream);
 
+/* Full synthesis of every field, coefficients -> grid: for each f the same
+ * values as sht_synthesize(plans[f], prec, beta[f], values[f],
+ * workspace[f]).  One launch runs every field's Legendre stage with the
+ * phase of eq. phis fused, writing workspace[f] (sht_workspace_bytes of plan
+ * f); then each field's complex-to-real FFTs run on stream.  beta, values and
+ * workspace are HOST arrays of nfields device pointers (read during the call;
+ * beta and workspace entries 16-byte aligned, 8-byte for SHT_FP32).  The
+ * pointer tables reach the device through a ring of four slots in stream
+ * order: a call may wait on the host for the launch made four calls earlier
+ * on this batch.  Not for stream capture (use sht_batch_synthesize and
+ * sht_phi_synthesize per field there).  Asynchronous otherwise. */
+sht_status sht_batch_synthesize_grid(sht_batch_t batch, const void* const* beta, void* const* values,
+                                     void* const* workspace, sht_stream_t stream);
+
+/* Full analysis of every field, grid -> coefficients (as sht_analyze per
+ * field): each field's real-to-complex FFTs into workspace[f], then one
+ * launch of every field's transposed butterfly with the conjugate phase and
+ * 1/(4l-1) fused into its fold.  Arrays and ordering as in
+ * sht_batch_synthesize_grid. */
+sht_status sht_batch_analyze_grid(sht_batch_t batch, const void* const* values, void* const* beta,
+                                  void* const* workspace, sht_stream_t stream);
+
 /* Device status word of the batch's launches (synchronizes stream): SHT_OK,
  * SHT_ERR_TIMEOUT (a bounded wait gave up) or SHT_ERR_INVALID_ARG (a field's
  * pointer entry was NULL or misaligned).  A non-OK status is cleared. */
 sht_status sht_batch_last_device_status(sht_batch_t batch, sht_stream_t stream);
 
-/* Times each launch shape (8 or 16 consumer warps, page ring depth 2..8,
- * whatever fits in shared memory) over reps launches of the given direction
- * (0 synthesis, 1 analysis, 2 adjoint of synthesis) with these pointer
- * arrays, and keeps the fastest
- * for that direction.  Runs the transform (writes the outputs); synchronous. */
+/* Times each launch shape (8, 12 or 16 consumer warps, page ring depth
+ * 2..8, whatever fits in shared memory) over reps launches of the given
+ * direction with these DEVICE pointer arrays, and keeps the fastest for that
+ * direction.  Directions: 0 synthesis, 1 analysis, 2 adjoint of synthesis,
+ * 3 and 4 the Legendre launches of sht_batch_synthesize_grid (beta ->
+ * workspace) and sht_batch_analyze_grid (workspace -> beta).  Runs the
+ * transform (writes the outputs); synchronous. */
 sht_status sht_batch_autotune(sht_batch_t batch, int direction, const void* const* in, void* const* out, int reps,
                               sht_stream_t stream);
 

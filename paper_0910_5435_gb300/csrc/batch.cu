@@ -37,15 +37,29 @@ struct BatchDir {
 
 }  // namespace
 
+// Device pointer tables of the grid entry points, filled from host arrays:
+// kRing slots, each the input then the output pointers of one call, copied
+// from pinned staging on the call's stream.  A slot is reused only after the
+// event recorded behind its last launch has completed.
+constexpr int kRing = 4;
+
 struct sht_batch_s {
   int n = 0;
   int q = 0;  // sht::SweepPrec
+  sht_precision prec = SHT_FP64;
   int device = 0;
   int num_sms = 0;
   int page_bytes = 0;
   size_t optin = 0;
-  BatchDir dir[3];                // synthesis, analysis, adjoint of synthesis
+  // synthesis, analysis, adjoint of synthesis; synthesis and analysis with
+  // the phase of the phi stage fused (the grid entry points)
+  BatchDir dir[5];
   unsigned* d_scratch = nullptr;  // queue counter per direction, then the status word
+  std::vector<sht_plan_t> plans;
+  void** d_tables = nullptr;  // kRing x 2n device pointers
+  void** h_stage = nullptr;   // kRing x 2n, pinned
+  cudaEvent_t ring_ev[kRing] = {};
+  int ring_next = 0;
 };
 
 namespace {
@@ -66,10 +80,14 @@ void free_batch(sht_batch_t b) {
     cudaFree(d.d_units);
   }
   cudaFree(b->d_scratch);
+  cudaFree(b->d_tables);
+  cudaFreeHost(b->h_stage);
+  for (cudaEvent_t& e : b->ring_ev)
+    if (e) cudaEventDestroy(e);
   delete b;
 }
 
-constexpr int kDirs = 3;
+constexpr int kDirs = 5;
 
 sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precision prec) {
   for (int d = 0; d < kDirs; ++d) {
@@ -78,8 +96,10 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
     BatchDir& D = b->dir[d];
     for (int f = 0; f < nfields; ++f) {
       sht::StreamView v;
-      // the adjoint runs the analysis stream with the 1/w fold prescale
-      const sht_status s = sht::stream_view(plans[f], prec, d == 2 ? 1 : d, &v);
+      // the adjoint runs the analysis stream with the 1/w fold prescale; the
+      // grid directions run the synthesis and analysis streams with the phase
+      const int stream_dir = (d == 0 || d == 3) ? 0 : 1;
+      const sht_status s = sht::stream_view(plans[f], prec, stream_dir, &v);
       if (s != SHT_OK) return s;
       if (f == 0) {
         b->device = v.device;
@@ -95,7 +115,7 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
       fields[f].pages = v.pages;
       fields[f].values = v.values;
       fields[f].prescale = d == 2 ? v.prescale : nullptr;
-      fields[f].twiddle = nullptr;
+      fields[f].twiddle = d == 3 ? v.tw_syn : d == 4 ? v.tw_ana : nullptr;
       fields[f].l = v.l;
       D.buf_ab = std::max(D.buf_ab, v.buf_ab);
       D.num_vecs = std::max(D.num_vecs, v.num_vecs);
@@ -117,6 +137,10 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
   }
   BCK(cudaMalloc(&b->d_scratch, sizeof(unsigned) * (kDirs + 1)));
   BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * (kDirs + 1)));
+  b->plans.assign(plans, plans + nfields);
+  BCK(cudaMalloc(&b->d_tables, sizeof(void*) * kRing * 2 * nfields));
+  BCK(cudaMallocHost(&b->h_stage, sizeof(void*) * kRing * 2 * nfields));
+  for (cudaEvent_t& e : b->ring_ev) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   int optin = 0;
   BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
   b->optin = (size_t)optin;
@@ -155,6 +179,29 @@ sht_status launch(sht_batch_t b, int d, const void* const* in, void* const* out,
   return SHT_OK;
 }
 
+// Copies the host pointer arrays in and out into the next ring slot (on
+// stream) and runs direction d with them.
+sht_status launch_from_host(sht_batch_t b, int d, const void* const* in, void* const* out, sht_stream_t stream) {
+  const size_t al = (b->q == sht::PREC_FP32) ? 8 : 16;
+  for (int f = 0; f < b->n; ++f)
+    if (!in[f] || !out[f] || reinterpret_cast<uintptr_t>(in[f]) % al || reinterpret_cast<uintptr_t>(out[f]) % al)
+      return SHT_ERR_INVALID_ARG;
+  const int s = b->ring_next;
+  b->ring_next = (s + 1) % kRing;
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  BCK(cudaEventSynchronize(b->ring_ev[s]));  // the slot's previous copy and launch are done
+  void** h = b->h_stage + (size_t)s * 2 * b->n;
+  void** dt = b->d_tables + (size_t)s * 2 * b->n;
+  for (int f = 0; f < b->n; ++f) {
+    h[f] = const_cast<void*>(in[f]);
+    h[b->n + f] = out[f];
+  }
+  BCK(cudaMemcpyAsync(dt, h, sizeof(void*) * 2 * b->n, cudaMemcpyHostToDevice, st));
+  const sht_status r = launch(b, d, dt, dt + b->n, stream);
+  BCK(cudaEventRecord(b->ring_ev[s], st));
+  return r;
+}
+
 }  // namespace
 
 extern "C" {
@@ -170,6 +217,7 @@ sht_status sht_batch_create(int nfields, const sht_plan_t* plans, sht_precision 
   sht_batch_t b = new (std::nothrow) sht_batch_s();
   if (!b) return SHT_ERR_OOM;
   b->n = nfields;
+  b->prec = prec;
   b->q = prec == SHT_FP64      ? sht::PREC_FP64
          : prec == SHT_FP32    ? sht::PREC_FP32
          : prec == SHT_SPLIT32 ? sht::PREC_SPLIT32
@@ -202,6 +250,37 @@ sht_status sht_batch_analyze(sht_batch_t b, const void* const* G, void* const* b
 sht_status sht_batch_synthesize_adjoint(sht_batch_t b, const void* const* G, void* const* beta,
                                         sht_stream_t stream) {
   return launch(b, 2, G, beta, stream);
+}
+
+sht_status sht_batch_synthesize_grid(sht_batch_t b, const void* const* beta, void* const* values,
+                                     void* const* workspace, sht_stream_t stream) {
+  if (!b || !beta || !values || !workspace) return SHT_ERR_INVALID_ARG;
+  for (int f = 0; f < b->n; ++f)
+    if (!values[f]) return SHT_ERR_INVALID_ARG;
+  BCK(cudaSetDevice(b->device));
+  // one launch: every field's Legendre stage with the phase, into its workspace
+  sht_status s = launch_from_host(b, 3, beta, workspace, stream);
+  if (s != SHT_OK) return s;
+  // then each field's complex-to-real FFTs
+  for (int f = 0; f < b->n && s == SHT_OK; ++f) s = sht::phi_fft_c2r(b->plans[f], b->prec, workspace[f], values[f], stream);
+  return s;
+}
+
+sht_status sht_batch_analyze_grid(sht_batch_t b, const void* const* values, void* const* beta,
+                                  void* const* workspace, sht_stream_t stream) {
+  if (!b || !beta || !values || !workspace) return SHT_ERR_INVALID_ARG;
+  const size_t al = (b->q == sht::PREC_FP32) ? 8 : 16;
+  for (int f = 0; f < b->n; ++f)
+    if (!values[f] || !workspace[f] || !beta[f] || reinterpret_cast<uintptr_t>(workspace[f]) % al ||
+        reinterpret_cast<uintptr_t>(beta[f]) % al)
+      return SHT_ERR_INVALID_ARG;
+  BCK(cudaSetDevice(b->device));
+  // each field's real-to-complex FFTs into its workspace
+  sht_status s = SHT_OK;
+  for (int f = 0; f < b->n && s == SHT_OK; ++f) s = sht::phi_fft_r2c(b->plans[f], b->prec, values[f], workspace[f], stream);
+  if (s != SHT_OK) return s;
+  // then one launch: every field's transposed butterfly with the conjugate phase
+  return launch_from_host(b, 4, workspace, beta, stream);
 }
 
 sht_status sht_batch_last_device_status(sht_batch_t b, sht_stream_t stream) {

@@ -437,6 +437,8 @@ sht_status sht::stream_view(sht_plan_t P, sht_precision prec, int dir, StreamVie
   v->consumer_warps = P->consumer_warps[q];
   v->slot_bytes = P->H.values_apart[q] ? P->H.slot_values * (q == sht::PREC_FP32 ? 4 : 8) : 0;
   v->prescale = P->d_inv_w;
+  v->tw_syn = P->d_tw_syn;
+  v->tw_ana = P->d_tw_ana;
   return SHT_OK;
 }
 
@@ -1029,3 +1031,19 @@ sht_status sht_direct_analyze(sht_plan_t P, const void* G, void* beta, sht_strea
 }
 
 }  // extern "C"
+
+// Outside the C ABI block: internal entry points for batch.cu.
+sht_status sht::phi_fft_c2r(sht_plan_t P, sht_precision prec, void* in, void* values, sht_stream_t stream) {
+  int q;
+  sht_status s = phi_args_ok(P, prec, in, values, q);
+  if (s != SHT_OK) return s;
+  return fft_c2r(P, q, in, values, stream);
+}
+
+sht_status sht::phi_fft_r2c(sht_plan_t P, sht_precision prec, const void* values, void* out, sht_stream_t stream) {
+  int q;
+  sht_status s = phi_args_ok(P, prec, values, out, q);
+  if (s != SHT_OK) return s;
+  return fft_r2c(P, q, values, out, stream);
+}
+

@@ -44,11 +44,20 @@ struct StreamView {
   int consumer_warps = 8;
   int slot_bytes = 0;                // staging slot per op (0: values in the pages)
   const double* prescale = nullptr;  // 1 / w_{l+i} (adjoint fold)
+  const double2* tw_syn = nullptr;   // e^{i pi m / (4l-1)}: the synthesis phase of eq. phis
+  const double2* tw_ana = nullptr;   // its conjugate over 4l-1: the analysis phase
 };
 
 // Fills *v, building and uploading the precision first if needed (this may
 // allocate).  dir: 0 synthesis, 1 analysis.
 sht_status stream_view(sht_plan_t plan, sht_precision prec, int dir, StreamView* v);
+
+// The phi stage's FFTs of a plan (cuFFT on stream; the plan's FFT handles are
+// made at first use): complex-to-real from the phased [2l][2l] array `in`
+// (overwritten) to the [2l][4l-1] grid, and real-to-complex from the grid to
+// `out` (before the conjugate phase).
+sht_status phi_fft_c2r(sht_plan_t plan, sht_precision prec, void* in, void* values, sht_stream_t stream);
+sht_status phi_fft_r2c(sht_plan_t plan, sht_precision prec, const void* values, void* out, sht_stream_t stream);
 
 // Sets the text returned by sht_last_error_detail on this thread.
 void set_error_detail(const char* where, const char* what);

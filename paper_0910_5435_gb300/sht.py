@@ -35,7 +35,7 @@ EXPORTS = [
     "sht_batch_create", "sht_batch_destroy", "sht_batch_synthesize", "sht_batch_analyze",
     "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config", "sht_batch_synthesize_adjoint",
     "sht_unit_stats_compute", "sht_gauss_jacobi_nodes", "sht_unit_stats_gauss_jacobi",
-    "sht_plan_save", "sht_plan_load",
+    "sht_plan_save", "sht_plan_load", "sht_batch_synthesize_grid", "sht_batch_analyze_grid",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -156,6 +156,8 @@ def lib():
     L.sht_batch_synthesize.argtypes = [vp, vp, vp, vp]
     L.sht_batch_analyze.argtypes = [vp, vp, vp, vp]
     L.sht_batch_synthesize_adjoint.argtypes = [vp, vp, vp, vp]
+    L.sht_batch_synthesize_grid.argtypes = [vp, vp, vp, vp, vp]
+    L.sht_batch_analyze_grid.argtypes = [vp, vp, vp, vp, vp]
     L.sht_batch_last_device_status.argtypes = [vp, vp]
     L.sht_batch_autotune.argtypes = [vp, c_int, vp, vp, c_int, vp]
     L.sht_batch_get_config.argtypes = [vp, c_int, vp, vp, vp, vp]
@@ -414,6 +416,26 @@ def sht_batch_analyze(batch, G_ptrs, beta_ptrs, stream=None):
 def sht_batch_synthesize_adjoint(batch, G_ptrs, beta_ptrs, stream=None):
     _check(lib().sht_batch_synthesize_adjoint(batch.handle, _ptr(G_ptrs), _ptr(beta_ptrs), _stream(stream)),
            "sht_batch_synthesize_adjoint")
+
+
+def host_pointer_array(tensors):
+    """Host array of the tensors' device addresses (the pointer arrays of the
+    grid calls, read during the call only)."""
+    return (ctypes.c_void_p * len(tensors))(*[_ptr(t) for t in tensors])
+
+
+def sht_batch_synthesize_grid(batch, betas, values, workspaces, stream=None):
+    """Full synthesis of every field (lists of device tensors, one per field)."""
+    _check(lib().sht_batch_synthesize_grid(batch.handle, host_pointer_array(betas), host_pointer_array(values),
+                                           host_pointer_array(workspaces), _stream(stream)),
+           "sht_batch_synthesize_grid")
+
+
+def sht_batch_analyze_grid(batch, values, betas, workspaces, stream=None):
+    """Full analysis of every field (lists of device tensors, one per field)."""
+    _check(lib().sht_batch_analyze_grid(batch.handle, host_pointer_array(values), host_pointer_array(betas),
+                                        host_pointer_array(workspaces), _stream(stream)),
+           "sht_batch_analyze_grid")
 
 
 def sht_batch_last_device_status(batch, stream=None):

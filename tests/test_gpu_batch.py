@@ -176,3 +176,57 @@ def test_batch_with_degenerate_and_single_fields(sht, plans):
     torch.cuda.synchronize()
     assert torch.equal(ref, Gs[0])
     one.close()
+
+
+@pytest.mark.parametrize("prec", [0, 2, 1])
+def test_batch_grid_equals_per_field_full_transforms(sht, plans, prec):
+    """sht_batch_synthesize_grid / sht_batch_analyze_grid (one batched
+    Legendre launch with the phase fused, plus each field's FFTs) give each
+    field exactly the values of sht_synthesize / sht_analyze, and match the
+    oracle's full transforms."""
+    ls = field_ls(7, 8)
+    for l in set(ls):
+        plans[l].prepare(prec)
+    B = sht.Batch([plans[l] for l in ls], prec)
+    rdt = torch.float32 if prec == 1 else torch.float64
+    betas, _ = fields(ls, prec, 9000)
+    values = [torch.full((2 * l, 4 * l - 1), float("nan"), dtype=rdt, device="cuda") for l in ls]
+    ws = [torch.empty((2 * l, 2 * l), dtype=CDT[prec], device="cuda") for l in ls]
+    for _ in range(5):  # more calls than the pointer-table ring has slots
+        sht.sht_batch_synthesize_grid(B, betas, values, ws)
+    torch.cuda.synchronize()
+    assert sht.sht_batch_last_device_status(B) == 0
+    for l, beta, v in zip(ls, betas, values):
+        ref = torch.full_like(v, float("nan"))
+        sht.sht_synthesize(plans[l], prec, beta, ref, torch.empty((2 * l, 2 * l), dtype=CDT[prec], device="cuda"))
+        torch.cuda.synchronize()
+        assert torch.equal(v, ref), l
+    f0 = ls[0]
+    fo = oracle.sht_synthesis(betas[0].cpu().numpy().astype(np.complex128), f0)
+    assert np.linalg.norm(values[0].cpu().numpy() - fo) / np.linalg.norm(fo) < TOL[prec]
+    backs = [torch.full_like(b, float("nan")) for b in betas]
+    sht.sht_batch_analyze_grid(B, values, backs, ws)
+    torch.cuda.synchronize()
+    assert sht.sht_batch_last_device_status(B) == 0
+    for l, v, back in zip(ls, values, backs):
+        ref = torch.full_like(back, float("nan"))
+        sht.sht_analyze(plans[l], prec, v, ref, torch.empty((2 * l, 2 * l), dtype=CDT[prec], device="cuda"))
+        torch.cuda.synchronize()
+        assert torch.equal(back, ref), l
+    for b, back in zip(betas, backs):
+        assert rel(back, b) < 2 * TOL[prec]
+    B.close()
+
+
+def test_batch_grid_rejects_bad_pointers(sht, plans):
+    ls = [16, 32]
+    B = sht.Batch([plans[l] for l in ls], 0)
+    betas, _ = fields(ls, 0, 9100)
+    values = [torch.empty((2 * l, 4 * l - 1), dtype=torch.float64, device="cuda") for l in ls]
+    ws = [torch.empty((2 * l, 2 * l), dtype=torch.complex128, device="cuda") for l in ls]
+    with pytest.raises(sht.ShtError) as e:
+        sht.sht_batch_synthesize_grid(B, betas, values, [ws[0], ws[1].data_ptr() + 8])
+    assert e.value.code == 1
+    sht.sht_batch_synthesize_grid(B, betas, values, ws)
+    assert sht.sht_batch_last_device_status(B) == 0
+    B.close()
