@@ -193,6 +193,8 @@ typedef struct {
                           * Remark QR_algorithm): per block of h rows, w columns and rank k,
                           * sum over steps i < k of 4 (h - i - 1)(w - i - 1) for applying
                           * the reflector, plus k^2 (w - k) for T = R11^{-1} R12 */
+  long long id_swaps;    /* skeleton/redundant exchanges of the strong rank-revealing step
+                          * (Remark QR_algorithm: coefficients at most 2), float64 IDs */
 } sht_plan_stats;
 
 /* Fills *opts with the defaults listed above. */

@@ -213,6 +213,9 @@ void fill_stats(sht_plan_t P) {
     }
   }
   s.factor_flops = flops;
+  long long swaps = 0;
+  for (const UnitFact& U : H.fact64) swaps += U.swaps;
+  s.id_swaps = swaps;
   s.smem_bytes = (int)std::max({P->smem[0], P->smem[1], P->smem[2]});
   s.page_bytes = P->H.page_bytes;
 }

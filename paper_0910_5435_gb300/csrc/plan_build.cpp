@@ -181,11 +181,13 @@ void ColumnStream::next(double* col) {
 
 // ------------------------------------------------------------------ ID
 
-int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm, std::vector<double>& T) {
+int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm, std::vector<double>& T, int* swaps) {
   perm.resize(w);
   std::iota(perm.begin(), perm.end(), 0);
   T.clear();
+  if (swaps) *swaps = 0;
   if (w == 0) return 0;
+  const std::vector<double> orig(A, A + (size_t)h * w);  // for refactoring after exchanges
   std::vector<double> nrm(w), ref(w);
   for (int j = 0; j < w; ++j) {
     const double* c = A + (size_t)j * h;
@@ -202,26 +204,8 @@ int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm, s
     for (int r = i0; r < h; ++r) s += c[r] * c[r];
     return s;
   };
-  for (int i = 0; i < kmax; ++i) {
-    int p = i;
-    for (int j = i + 1; j < w; ++j)
-      if (nrm[j] > nrm[p]) p = j;  // ties: lowest index
-    nrm[p] = exact_norm(p, i);
-    if (nrm[p] <= eps2) {
-      // the downdated norms may have drifted: recompute all before stopping
-      for (int j = i; j < w; ++j) nrm[j] = ref[j] = exact_norm(j, i);
-      p = i;
-      for (int j = i + 1; j < w; ++j)
-        if (nrm[j] > nrm[p]) p = j;
-      if (nrm[p] <= eps2) break;
-    }
-    if (p != i) {
-      std::swap_ranges(A + (size_t)i * h, A + (size_t)i * h + h, A + (size_t)p * h);
-      std::swap(nrm[i], nrm[p]);
-      std::swap(ref[i], ref[p]);
-      std::swap(perm[i], perm[p]);
-    }
-    // Householder reflector for A[i:h, i]
+  // Householder reflector for A[i:h, i], applied to columns i+1..w-1
+  auto reflect = [&](int i) {
     double* ci = A + (size_t)i * h;
     const double alpha = ci[i];
     double sigma = 0.0;
@@ -245,6 +229,27 @@ int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm, s
         for (int r = i + 1; r < h; ++r) cj[r] -= dot * ci[r];
       }
     }
+  };
+  for (int i = 0; i < kmax; ++i) {
+    int p = i;
+    for (int j = i + 1; j < w; ++j)
+      if (nrm[j] > nrm[p]) p = j;  // ties: lowest index
+    nrm[p] = exact_norm(p, i);
+    if (nrm[p] <= eps2) {
+      // the downdated norms may have drifted: recompute all before stopping
+      for (int j = i; j < w; ++j) nrm[j] = ref[j] = exact_norm(j, i);
+      p = i;
+      for (int j = i + 1; j < w; ++j)
+        if (nrm[j] > nrm[p]) p = j;
+      if (nrm[p] <= eps2) break;
+    }
+    if (p != i) {
+      std::swap_ranges(A + (size_t)i * h, A + (size_t)i * h + h, A + (size_t)p * h);
+      std::swap(nrm[i], nrm[p]);
+      std::swap(ref[i], ref[p]);
+      std::swap(perm[i], perm[p]);
+    }
+    reflect(i);
     for (int j = i + 1; j < w; ++j) {
       const double rij = A[(size_t)j * h + i];
       nrm[j] -= rij * rij;
@@ -254,16 +259,39 @@ int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm, s
   }
   // T = R11^{-1} R12 by back substitution, column by column
   const int nred = w - k;
-  T.assign((size_t)k * nred, 0.0);
-  for (int s = 0; s < nred; ++s) {
-    const double* rc = A + (size_t)(k + s) * h;
-    double* tc = T.data() + (size_t)s * k;
-    for (int t = k - 1; t >= 0; --t) {
-      double v = rc[t];
-      for (int t2 = t + 1; t2 < k; ++t2) v -= A[(size_t)t2 * h + t] * tc[t2];
-      tc[t] = v / A[(size_t)t * h + t];
+  auto solve = [&]() {
+    T.assign((size_t)k * nred, 0.0);
+    for (int s = 0; s < nred; ++s) {
+      const double* rc = A + (size_t)(k + s) * h;
+      double* tc = T.data() + (size_t)s * k;
+      for (int t = k - 1; t >= 0; --t) {
+        double v = rc[t];
+        for (int t2 = t + 1; t2 < k; ++t2) v -= A[(size_t)t2 * h + t] * tc[t2];
+        tc[t] = v / A[(size_t)t * h + t];
+      }
     }
+  };
+  solve();
+  // Strong rank-revealing step (Remark QR_algorithm: interpolation
+  // coefficients at most 2).  While some |T(t, s)| > 2, exchange skeleton
+  // column t with redundant column s and refactor the columns in the new
+  // order without pivoting.  An exchange multiplies |det R11| by at least
+  // |T(t, s)| > 2, so the loop ends; it is capped at 2k exchanges.
+  int nswap = 0;
+  while (k > 0 && nred > 0 && nswap < 2 * k) {
+    size_t best = 0;
+    for (size_t x = 1; x < T.size(); ++x)
+      if (std::fabs(T[x]) > std::fabs(T[best])) best = x;
+    if (!(std::fabs(T[best]) > 2.0)) break;
+    const int s = (int)(best / k), t = (int)(best % k);
+    std::swap(perm[t], perm[k + s]);
+    for (int j = 0; j < w; ++j)
+      std::copy(orig.begin() + (size_t)perm[j] * h, orig.begin() + (size_t)(perm[j] + 1) * h, A + (size_t)j * h);
+    for (int i = 0; i < k; ++i) reflect(i);
+    solve();
+    ++nswap;
   }
+  if (swaps) *swaps = nswap;
   // redundant columns in ascending order (T columns follow)
   std::vector<int> ord(nred);
   std::iota(ord.begin(), ord.end(), 0);
@@ -346,7 +374,9 @@ UnitFact factor_unit(const PlanHost& P, int m, int p, double eps) {
     std::vector<double> leaf((size_t)rows * wd);
     for (int j = 0; j < wd; ++j) cs.next(leaf.data() + (size_t)j * rows);
     std::vector<double> work(leaf);
-    const int k = interp_decomp(work.data(), rows, wd, eps, perm, T);
+    int sw = 0;
+    const int k = interp_decomp(work.data(), rows, wd, eps, perm, T, &sw);
+    U.swaps += sw;
     IdBlock b;
     b.level = 1;
     b.band = 0;
@@ -400,7 +430,9 @@ UnitFact factor_unit(const PlanHost& P, int m, int p, double eps) {
             std::copy(BR.Ask.begin() + (size_t)t * h + (rr0 - BL.r0), BR.Ask.begin() + (size_t)t * h + (rr1 - BL.r0),
                       Z.begin() + (size_t)(BL.k + t) * hh);
           std::vector<double> Zw(Z);
-          const int k = interp_decomp(Zw.data(), hh, kin, eps, perm, T);
+          int sw = 0;
+          const int k = interp_decomp(Zw.data(), hh, kin, eps, perm, T, &sw);
+          U.swaps += sw;
           IdBlock b;
           b.level = j + 1;
           b.band = (int)(2 * beta + half);

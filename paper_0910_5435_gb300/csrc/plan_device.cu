@@ -87,7 +87,7 @@ struct DevBuildArgs {
   unsigned long long* arena_fail;  // lowest offset of a reservation that did not fit
   int* stop;                       // the arena is full: take no further units
   int* status;                     // per unit id
-  long long* info;                 // per unit id: rows, levels
+  long long* info;                 // per unit id: rows, levels, exchanges
 };
 
 struct Shared {
@@ -96,7 +96,7 @@ struct Shared {
   int kres[kWarps];  // ranks of the leaves of the current batch
   unsigned long long tmp_sp;
   long long new_sp;
-  int q, ngrp, ecm, fail;
+  int q, ngrp, ecm, fail, swaps;
   double cm;
 };
 
@@ -464,6 +464,62 @@ __device__ int warp_cpqr(double* W, int h, int w, double eps2, const WarpBuf& B,
   return k;
 }
 
+// Householder QR of the first k columns of W without pivoting (the columns
+// are already in the wanted order), applied to all w columns: the R factor
+// after an exchange of the strong rank-revealing step.
+__device__ void warp_qr_fixed(double* W, int h, int w, int k, int lane) {
+  for (int i = 0; i < k; ++i) {
+    double e, sg;
+    pivot_sums(W, h, i, i, e, sg, lane);
+    double* ci = W + (size_t)i * h;
+    const double alpha = ci[i];
+    double tau = 0.0, beta = alpha, sc = 1.0;
+    const bool reflect = (sg != 0.0 || alpha < 0.0);
+    if (reflect) {
+      const double nx = sqrt(alpha * alpha + sg);
+      beta = (alpha <= 0.0) ? nx : -nx;
+      tau = (beta - alpha) / beta;
+      sc = 1.0 / (alpha - beta);
+    }
+    __syncwarp();
+    for (int r = lane; r < h; r += 32) {
+      if (r == i) {
+        ci[r] = beta;
+      } else if (r > i && reflect) {
+        ci[r] *= sc;
+      }
+    }
+    __syncwarp();
+    if (tau != 0.0) {
+      for (int j0 = i + 1; j0 < w; j0 += 4) {
+        const int nc = min(4, w - j0);
+        double* c0 = W + (size_t)j0 * h;
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+        for (int r = i + 1 + lane; r < h; r += 32) {
+          const double vr = ci[r];
+          d0 = fma(vr, c0[r], d0);
+          if (nc > 1) d1 = fma(vr, c0[h + r], d1);
+          if (nc > 2) d2 = fma(vr, c0[2 * h + r], d2);
+          if (nc > 3) d3 = fma(vr, c0[3 * h + r], d3);
+        }
+        reduce4(d0, d1, d2, d3, lane);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (c >= nc) break;
+          double* cj = c0 + (size_t)c * h;
+          const double rij = cj[i];
+          const double dc = c == 0 ? d0 : c == 1 ? d1 : c == 2 ? d2 : d3;
+          const double d = (dc + rij) * tau;
+          for (int r = i + 1 + lane; r < h; r += 32) cj[r] = fma(-d, ci[r], cj[r]);
+          __syncwarp();
+          if (lane == 0) cj[i] = rij - d;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 __device__ __forceinline__ long long pad16(long long b) { return (b + 15) & ~15LL; }
 
 __device__ __forceinline__ long long block_record_bytes(int nin, int k) {
@@ -526,6 +582,66 @@ __device__ void warp_write_block(unsigned char* rec, int unit, int level, int ba
   }
 }
 
+// Writes the block's record and then runs the strong rank-revealing step of
+// Remark QR_algorithm: while some |T(t, s)| > 2, exchange skeleton column t
+// with redundant column s, refactor the original columns Z in the new order
+// and rewrite the record (at most 2k exchanges; each multiplies |det R11| by
+// more than 2).  Returns the number of exchanges.
+__device__ int warp_write_strong(unsigned char* rec, int unit, int level, int band, int group, int r0, int r1,
+                                 int in_off, int nin, int k, const WarpBuf& B, int h, int lane) {
+  int nswap = 0;
+  const int nred = nin - k;
+  const int* red = reinterpret_cast<const int*>(rec + sizeof(RecHdr)) + k;
+  const double* T = reinterpret_cast<const double*>(rec + sizeof(RecHdr) + pad16(4LL * nin));
+  for (;;) {
+    warp_write_block(rec, unit, level, band, group, r0, r1, in_off, nin, k, B.W, h, B.perm, lane);
+    __syncwarp();
+    if (k == 0 || nred == 0 || nswap >= 2 * k) break;
+    long long best = -1;
+    int bi = k * nred;
+    for (int x = lane; x < k * nred; x += 32) {
+      const long long b = __double_as_longlong(fabs(T[x]));
+      if (b > best) {
+        best = b;
+        bi = x;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const long long ob = __shfl_xor_sync(kFull, best, o);
+      const int oi = __shfl_xor_sync(kFull, bi, o);
+      if (better(ob, oi, best, bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (!(__longlong_as_double(best) > 2.0)) break;
+    // T's column bi / k belongs to redundant column red[bi / k]: find it in perm
+    const int c = red[bi / k], t = bi % k;
+    int s = -1;
+    for (int x = lane; x < nred; x += 32)
+      if (B.perm[k + x] == c) s = x;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s = max(s, __shfl_xor_sync(kFull, s, o));
+    if (s < 0) break;
+    __syncwarp();
+    if (lane == 0) {
+      const int tp = B.perm[t];
+      B.perm[t] = B.perm[k + s];
+      B.perm[k + s] = tp;
+    }
+    __syncwarp();
+    for (long long x = lane; x < (long long)h * nin; x += 32) {
+      const int col = (int)(x / h), i = (int)(x - (long long)col * h);
+      B.W[x] = B.Z[(size_t)B.perm[col] * h + i];
+    }
+    __syncwarp();
+    warp_qr_fixed(B.W, h, nin, k, lane);
+    ++nswap;
+  }
+  return nswap;
+}
+
 // Marks the unit failed (first reason wins).
 __device__ __forceinline__ void set_fail(Shared& S, int why) { atomicCAS(&S.fail, 0, why); }
 
@@ -533,9 +649,9 @@ __device__ __forceinline__ void set_fail(Shared& S, int why) { atomicCAS(&S.fail
 __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int u) {
   const int m = u >> 1, p = u & 1, l = A.l, L = 2 * l, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = max(0, (L - m - p + 1) / 2);
-  long long* info = A.info + 2LL * u;
+  long long* info = A.info + 3LL * u;
   if (n == 0) {
-    if (tid == 0) info[0] = info[1] = 0;
+    if (tid == 0) info[0] = info[1] = info[2] = 0;
     return kDone;
   }
   // recurrence coefficients of the n columns, and c_m with
@@ -557,6 +673,7 @@ __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int 
     S.ecm = ecm;
     S.ngrp = 0;
     S.fail = 0;
+    S.swaps = 0;
   }
   __syncthreads();
 
@@ -586,7 +703,7 @@ __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int 
     }
   }
   if (rows == 0) {
-    if (tid == 0) info[0] = info[1] = 0;
+    if (tid == 0) info[0] = info[1] = info[2] = 0;
     return kDone;
   }
   const int C = A.C;
@@ -619,7 +736,8 @@ __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int 
       const int k = warp_cpqr(B.W, rows, wd, A.eps2, B, lane);
       unsigned char* rec = warp_reserve(A, block_record_bytes(wd, k), lane);
       if (rec) {
-        warp_write_block(rec, u, 1, 0, g, 0, rows, c0, wd, k, B.W, rows, B.perm, lane);
+        const int sw = warp_write_strong(rec, u, 1, 0, g, 0, rows, c0, wd, k, B, rows, lane);
+        if (lane == 0 && sw) atomicAdd(&S.swaps, sw);
       } else if (lane == 0) {
         set_fail(S, kNoArena);
       }
@@ -692,7 +810,8 @@ __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int 
           if (lane == 0) set_fail(S, kNoArena);
           continue;
         }
-        warp_write_block(rec, u, lev + 1, 2 * beta + half, Lg.g / 2, rr0, rr1, 0, kin, k, B.W, hh, B.perm, lane);
+        const int sw = warp_write_strong(rec, u, lev + 1, 2 * beta + half, Lg.g / 2, rr0, rr1, 0, kin, k, B, hh, lane);
+        if (lane == 0 && sw) atomicAdd(&S.swaps, sw);
         // the new band's skeleton columns go to temporary space above the stack
         unsigned long long off = 0;
         if (lane == 0) off = atomicAdd(&S.tmp_sp, (unsigned long long)hh * k);
@@ -773,6 +892,7 @@ __device__ int build_unit(const DevBuildArgs& A, const Views& V, Shared& S, int 
   if (tid == 0) {
     info[0] = rows;
     info[1] = lam;
+    info[2] = S.swaps;
   }
   return kDone;
 }
@@ -908,7 +1028,7 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
   check(cudaMalloc(&d_queue.p, sizeof(int) * 2 * L), "cudaMalloc queue");
   check(cudaMalloc(&d_ctl.p, 64), "cudaMalloc control");
   check(cudaMalloc(&d_status.p, sizeof(int) * 2 * L), "cudaMalloc status");
-  check(cudaMalloc(&d_info.p, sizeof(long long) * 2 * 2 * L), "cudaMalloc info");
+  check(cudaMalloc(&d_info.p, sizeof(long long) * 3 * 2 * L), "cudaMalloc info");
   check(cudaMalloc(&d_scratch.p, 8 * (size_t)scratch_words * ctas), "cudaMalloc scratch");
   check(cudaMalloc(&d_arena.p, arena_bytes), "cudaMalloc arena");
   double* dn = static_cast<double*>(d_nodes.p);
@@ -945,7 +1065,7 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
   A.info = static_cast<long long*>(d_info.p);
 
   std::vector<int> status(2 * L, kPending);
-  std::vector<long long> info(2 * 2 * L);
+  std::vector<long long> info(3 * 2 * L);
   ByteBuf host;
   std::vector<int> pending = order;
   // CTAs per launch: all of them, or one when a launch finished no block
@@ -967,7 +1087,7 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
     check(cudaDeviceSynchronize(), "factor_units_kernel");
     P.t_factor_kernel += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     check(cudaMemcpy(status.data(), d_status.p, sizeof(int) * 2 * L, cudaMemcpyDeviceToHost), "status");
-    check(cudaMemcpy(info.data(), d_info.p, sizeof(long long) * 2 * 2 * L, cudaMemcpyDeviceToHost), "info");
+    check(cudaMemcpy(info.data(), d_info.p, sizeof(long long) * 3 * 2 * L, cudaMemcpyDeviceToHost), "info");
     check(cudaMemcpy(&c0, ctl, sizeof(c0), cudaMemcpyDeviceToHost), "control");
     for (int u : pending)
       if (status[u] == kNoScratch)
@@ -1009,8 +1129,9 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
           U.m = u / 2;
           U.p = u % 2;
           U.n = std::max(0, (L - U.m - U.p + 1) / 2);
-          U.rows = (int)info[2 * u];
-          U.levels = (int)info[2 * u + 1];
+          U.rows = (int)info[3 * u];
+          U.levels = (int)info[3 * u + 1];
+          U.swaps = info[3 * u + 2];
           std::vector<FinalBlock> top;
           for (size_t off : recs[u]) {
             RecHdr h;

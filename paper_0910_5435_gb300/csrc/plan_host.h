@@ -62,6 +62,7 @@ struct UnitFact {
   long long values = 0;      // stored factor values
   long long idx = 0;         // stored index entries
   long long peak_words = 0;  // peak float64 words held during the depth-first build
+  long long swaps = 0;       // strong rank-revealing exchanges made by the IDs
   double cost = 0;           // estimated apply cost (bytes), for LPT ordering
 };
 
@@ -148,11 +149,14 @@ class ColumnStream {
 
 // Interpolative decomposition by column-pivoted Householder QR (Remark
 // QR_algorithm).  A is h x w column-major (destroyed).  Returns the rank k:
-// the smallest k with max remaining column norm <= eps.  perm[0..k) are
-// the skeleton columns, perm[k..w) the rest (ascending); T is k x (w-k)
+// the smallest k with max remaining column norm <= eps.  Then, as the
+// strong rank-revealing QR of that remark, skeleton and redundant columns are
+// exchanged while an interpolation coefficient exceeds 2 in magnitude (at
+// most 2k exchanges; *swaps receives the count when not null).  perm[0..k)
+// are the skeleton columns, perm[k..w) the rest (ascending); T is k x (w-k)
 // with T[s * k + t], such that A[:, perm[k+s]] ~= sum_t T(t, s) A[:, perm[t]].
 int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm,
-                  std::vector<double>& T);
+                  std::vector<double>& T, int* swaps = nullptr);
 
 // Completes a unit whose ID blocks (level, band, group, rows, leaf input
 // offsets, ranks, skeletons, interpolation matrices), rows, n and levels are

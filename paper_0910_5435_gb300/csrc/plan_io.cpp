@@ -118,6 +118,7 @@ void write_unit(const UnitFact& U, Writer& w) {
   w.put<int64_t>(U.values);
   w.put<int64_t>(U.idx);
   w.put<int64_t>(U.peak_words);
+  w.put<int64_t>(U.swaps);
   w.put<double>(U.cost);
   w.put_vec(U.D);
   w.put_vec(U.width);
@@ -148,6 +149,7 @@ void read_unit(Reader& r, UnitFact& U, int l) {
   U.values = r.get<int64_t>();
   U.idx = r.get<int64_t>();
   U.peak_words = r.get<int64_t>();
+  U.swaps = r.get<int64_t>();
   U.cost = r.get<double>();
   r.get_vec(U.D, cap);
   r.get_vec(U.width, 64);

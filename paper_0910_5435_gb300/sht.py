@@ -100,6 +100,7 @@ class sht_plan_stats(ctypes.Structure):
         ("t_factor", ctypes.c_double),
         ("t_factor_kernel", ctypes.c_double),
         ("factor_flops", ctypes.c_double),
+        ("id_swaps", ctypes.c_longlong),
     ]
 
     def as_dict(self):

@@ -122,7 +122,9 @@ def test_stats_follow_paper_columns():
     assert s["m_max_words"] > 0
     assert s["factor_flops"] > 0 and s["t_factor"] > 0 and s["t_factor_kernel"] == 0.0
     assert s["k_sigma"] >= 0
-    assert s["max_abs_T"] < 1e3
+    # the strong rank-revealing step of Remark QR_algorithm bounds the
+    # interpolation coefficients by 2
+    assert s["max_abs_T"] <= 2.0 + 1e-12
     assert math.isfinite(s["k_avg"])
 
 
