@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--paths", default="split32,split32acc64,fp32,direct,full,batched,autograd,device_build",
                     help="comma-separated legs to run beside the headline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--cpu-all-cores", type=int, default=1,
+                    help="also time the oracle over all orders on every host core (0: skip)")
     ap.add_argument("--batch-fields", type=int, default=96,
                     help="fields of the batched leg (bandlimits drawn from 64..1024); 0 skips it")
     ap.add_argument("--cpu-stride", type=int, default=8, help="oracle samples every stride-th order")
@@ -248,6 +250,35 @@ def workload_config(args, world=1):
             "l": args.l, "eps_id": args.eps, "parallelism": f"replicas x{world}",
             "l2": "no flush: every launch streams the whole factor stream (6.3 GB at l=1024), "
                   "far larger than the 129 MB L2"}
+
+
+def cpu_oracle_all_cores(l, seed, nproc):
+    """The same float64 oracle over every order of the field, split
+    round-robin over nproc single-threaded processes (one per host core);
+    returns the wall time of one synthesis plus one analysis of the whole
+    field, process start-up included."""
+    code = r"""
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+from paper_0910_5435_gb300 import inputs
+l, seed, r, n = (int(x) for x in sys.argv[2:6])
+ms = list(range(r, 2 * l, n))
+beta = inputs.random_beta(l, seed=seed, decay=True)
+Go = oracle.legendre_synthesis(beta, l, orders=ms)
+oracle.legendre_analysis(Go, l, orders=ms)
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    t0 = time.perf_counter()
+    procs = [subprocess.Popen([sys.executable, "-c", code, ROOT, str(l), str(seed), str(r), str(nproc)],
+                              stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, env=env) for r in range(nproc)]
+    errs = [p.communicate()[1] for p in procs]
+    wall = time.perf_counter() - t0
+    for p, e in zip(procs, errs):
+        if p.returncode != 0:
+            raise RuntimeError("oracle leg failed: " + e.decode(errors="replace")[-2000:])
+    return wall
 
 
 def run_reference(args):
@@ -629,6 +660,7 @@ def main():
         extras["plan_device_build"] = device_build_leg(args, sht, torch, dev, stream, plan, st, beta)
 
     cpu = None
+    cpu_all = None
     rel = {}
     if rank == 0 and world == 1 and not args.no_cpu:
         with tempfile.TemporaryDirectory() as td:
@@ -644,6 +676,12 @@ def main():
                "sample": f"{res['orders']} of {2 * l} orders (m = 0, {args.cpu_stride}, ...), synthesis + analysis, "
                          f"scaled by the stride; {res['t_synth'] + res['t_analysis']:.1f} s of CPU"}
         rel = {k: v for k, v in res.items() if k.startswith("rel_")}
+        if args.cpu_all_cores:
+            ncores = os.cpu_count() or 1
+            wall = cpu_oracle_all_cores(l, 3, ncores)
+            cpu_all = {"value": 2.0 / wall, "unit": "transforms/s", "cores": ncores, "kind": "oracle",
+                       "sample": f"all {2 * l} orders, synthesis + analysis, one single-threaded process "
+                                 f"per core; {wall:.1f} s wall including process start-up"}
     for k in list(extras):
         if k.endswith("_G") or k.endswith("_beta"):
             extras.pop(k)
@@ -657,7 +695,7 @@ def main():
             "config": workload_config(args, world),
             "ms_synthesis": ms_syn, "ms_analysis": ms_ana, "step_ms_percentiles": step_percentiles,
             "eps_inv": eps_inv64, "rel_l2_vs_oracle_sampled": rel,
-            "roofline": roofline, "cpu_baseline": cpu,
+            "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
             "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
             "gpu_launches": 2 * args.steps, "clocks": clk, "device_status": status,
