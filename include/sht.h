@@ -351,6 +351,16 @@ sht_status sht_trace_enable(sht_plan_t plan, int enable);
  * Synchronizes the device.  SHT_ERR_UNSUPPORTED if tracing is disabled. */
 sht_status sht_trace_read(sht_plan_t plan, unsigned long long* out, int reset);
 
+/* ------------------------------------------------------------ diagnostics */
+
+/* The paper has no counterpart: measures the current device's float64
+ * fused multiply-add throughput (*tflops, TFLOP/s counting 2 flops per
+ * FMA) with a register-resident loop of eight independent chains per
+ * thread on every SM, timed with CUDA events over one launch of about 50 ms
+ * after a warm-up launch.  The ceiling the float64 kernels are compared
+ * with.  Synchronous; uses the legacy default stream. */
+sht_status sht_measure_fp64_fma(double* tflops);
+
 /* ----------------------------------------------- direct float64 baseline */
 
 /* Stores the dense operator P-bar^m_{m+p+2j}(x_{l+i}) (float64, kept rows

@@ -28,7 +28,7 @@ CXXFLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-func
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
 
 CPP_SOURCES = ["plan_build.cpp", "unit_stats.cpp", "plan_io.cpp"]
-CU_SOURCES = ["capi.cu", "sweep.cu", "direct.cu", "phi.cu", "noalloc.cu", "batch.cu", "plan_device.cu"]
+CU_SOURCES = ["capi.cu", "sweep.cu", "direct.cu", "phi.cu", "noalloc.cu", "batch.cu", "plan_device.cu", "peak.cu"]
 HEADERS = ["sht_stream.h", "plan_host.h", "kernels.h", "plan_access.h", "recurrence.h"]
 
 

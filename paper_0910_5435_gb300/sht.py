@@ -36,6 +36,7 @@ EXPORTS = [
     "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config", "sht_batch_synthesize_adjoint",
     "sht_unit_stats_compute", "sht_gauss_jacobi_nodes", "sht_unit_stats_gauss_jacobi",
     "sht_plan_save", "sht_plan_load", "sht_batch_synthesize_grid", "sht_batch_analyze_grid",
+    "sht_measure_fp64_fma",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -158,6 +159,7 @@ def lib():
     L.sht_batch_analyze.argtypes = [vp, vp, vp, vp]
     L.sht_batch_synthesize_adjoint.argtypes = [vp, vp, vp, vp]
     L.sht_batch_synthesize_grid.argtypes = [vp, vp, vp, vp, vp]
+    L.sht_measure_fp64_fma.argtypes = [ctypes.POINTER(c_double)]
     L.sht_batch_analyze_grid.argtypes = [vp, vp, vp, vp, vp]
     L.sht_batch_last_device_status.argtypes = [vp, vp]
     L.sht_batch_autotune.argtypes = [vp, c_int, vp, vp, c_int, vp]
@@ -417,6 +419,14 @@ def sht_batch_analyze(batch, G_ptrs, beta_ptrs, stream=None):
 def sht_batch_synthesize_adjoint(batch, G_ptrs, beta_ptrs, stream=None):
     _check(lib().sht_batch_synthesize_adjoint(batch.handle, _ptr(G_ptrs), _ptr(beta_ptrs), _stream(stream)),
            "sht_batch_synthesize_adjoint")
+
+
+def measure_fp64_fma():
+    """Float64 FMA throughput of the current device in TFLOP/s
+    (sht_measure_fp64_fma)."""
+    t = ctypes.c_double()
+    _check(lib().sht_measure_fp64_fma(ctypes.byref(t)), "sht_measure_fp64_fma")
+    return t.value
 
 
 def host_pointer_array(tensors):
