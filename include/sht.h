@@ -113,14 +113,13 @@ typedef struct {
    * max(eps_id, 1e-7).  (FP32 cannot use ranks below its own precision.) */
   double eps_fp32;
   /* Warps per CTA of the sweep kernels that execute ops (8, 12 or 16; 0 =
-   * per precision: 8 for SHT_FP64 and SHT_SPLIT32, 16 for SHT_FP32).  A
-   * tuning knob; results do not depend on it. */
+   * 16).  A tuning knob; results do not depend on it. */
   int consumer_warps;
   /* 1: factor values travel inside the TMA-staged pages; 0 (default): they
    * sit in a separate region, the pages carry only op headers and index
    * lists, and each executing warp bulk-copies the value block of its next
-   * op into one of its two shared-memory slots while it runs the current
-   * one (ops hold at most slot_values values).  A tuning knob. */
+   * op into a shared-memory staging slot (ops hold at most slot_values
+   * values; see staging_slots).  A tuning knob. */
   int values_inline;
   /* Tests of failure detection only (default 0): 1 makes the first compute
    * op of the first order of every stream list itself as its predecessor, a
@@ -155,6 +154,13 @@ typedef struct {
    * sht_last_error_detail).  A failed write fails plan creation with
    * SHT_ERR_INVALID_ARG.  The string is read during the call only. */
   const char* plan_cache;
+  /* Staging slots per consumer warp when values are kept apart: 1 (default,
+   * also for 0) starts the copy of a warp's next op once its current op has
+   * read the slot, and leaves room for 16 consumer warps whose copies and
+   * arithmetic overlap one another; 2 lets a warp's next op's values travel
+   * while its current op runs, at twice the slot memory (8 warps at the
+   * default slot size).  A tuning knob; results do not depend on it. */
+  int staging_slots;
 } sht_plan_opts;
 
 typedef struct {
@@ -500,8 +506,9 @@ sht_status sht_batch_analyze_grid(sht_batch_t batch, const void* const* values, 
  * pointer entry was NULL or misaligned).  A non-OK status is cleared. */
 sht_status sht_batch_last_device_status(sht_batch_t batch, sht_stream_t stream);
 
-/* Times each launch shape (8, 12 or 16 consumer warps, page ring depth
- * 2..8, whatever fits in shared memory) over reps launches of the given
+/* Times each launch shape (8 consumer warps with two staging slots each,
+ * 12 or 16 with one, 16 with two; page ring depth 2..8; whatever fits in
+ * shared memory with its values staged) over reps launches of the given
  * direction with these DEVICE pointer arrays, and keeps the fastest for that
  * direction.  Directions: 0 synthesis, 1 analysis, 2 adjoint of synthesis,
  * 3 and 4 the Legendre launches of sht_batch_synthesize_grid (beta ->

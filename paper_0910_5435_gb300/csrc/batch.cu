@@ -108,6 +108,7 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
         D.quit_pages = v.pages;
         D.quit_page = v.quit_page;
         D.cfg.nw = v.consumer_warps;
+        D.cfg.warp_slots = v.warp_slots;
       } else if (v.device != b->device || v.page_bytes != b->page_bytes) {
         sht::set_error_detail("sht_batch_create", "plans differ in device or page_bytes");
         return SHT_ERR_INVALID_ARG;
@@ -146,7 +147,8 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
   b->optin = (size_t)optin;
   BCK(sht::sweep_configure(b->q, b->optin));
   for (BatchDir& D : b->dir)
-    if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, D.cfg.nw, D.slot_bytes, 0, b->optin, &D.cfg))
+    if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, D.cfg.nw, D.slot_bytes, 0, b->optin, &D.cfg,
+                           D.cfg.warp_slots))
       return SHT_ERR_UNSUPPORTED;
   return SHT_OK;
 }
@@ -169,6 +171,7 @@ sht_status launch(sht_batch_t b, int d, const void* const* in, void* const* out,
   a.num_vecs = D.num_vecs;
   a.staged = D.cfg.staged ? 1 : 0;
   a.slot_bytes = D.cfg.slot_bytes;
+  a.warp_slots = D.cfg.warp_slots;
   a.fields = D.d_fields;
   a.field_in = in;
   a.field_out = out;
@@ -310,10 +313,13 @@ sht_status sht_batch_autotune(sht_batch_t b, int direction, const void* const* i
   sht::SweepConfig best = keep;
   float best_ms = -1.f;
   sht_status result = SHT_OK;
-  for (int nw : {8, 12, 16}) {
+  for (const int shape : {8 * 4 + 2, 12 * 4 + 1, 16 * 4 + 1, 16 * 4 + 2}) {
+    const int nw = shape / 4, ws = shape % 4;  // consumer warps, staging slots per warp
     for (int nst = 2; nst <= 8 && result == SHT_OK; ++nst) {
       sht::SweepConfig c;
-      if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, nw, D.slot_bytes, nst, b->optin, &c)) continue;
+      if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, nw, D.slot_bytes, nst, b->optin, &c, ws))
+        continue;
+      if (D.slot_bytes > 0 && !c.staged) continue;  // values would not fit in the slots
       D.cfg = c;
       result = launch(b, direction, in, out, stream);  // warm-up
       if (result != SHT_OK) break;

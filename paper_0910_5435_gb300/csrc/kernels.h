@@ -39,8 +39,9 @@ struct SweepArgs {
   unsigned* status;            // device status word (0 = ok)
   unsigned long long* trace;   // kTraceSlots cycle counters accumulated over all CTAs, or nullptr
   int num_vecs;                // shared vectors (buffer ids 0 .. num_vecs-1)
-  int staged;                  // 1: each consumer warp stages op values in two shared slots
+  int staged;                  // 1: each consumer warp stages op values in shared slots
   int slot_bytes;              // bytes of one staging slot (staged launches)
+  int warp_slots;              // staging slots per consumer warp: 1, or 2 (also for 0)
   // Batched launches (fields != nullptr): units[u].m is the item's field f;
   // pages, values, l, prescale and twiddle come from fields[f], the field's
   // input and output from field_in[f] and field_out[f] (device arrays).
@@ -59,6 +60,7 @@ struct SweepConfig {
   size_t smem = 0;
   bool staged = false;
   int slot_bytes = 0;
+  int warp_slots = 2;
 };
 
 // Trace slots (clock64 cycles summed over CTAs): consumer warps executing ops,
@@ -79,14 +81,15 @@ enum TraceSlot {
 // applied with float64 accumulation (same streams as PREC_SPLIT32).
 enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2, PREC_SPLIT32_ACC64 = 3 };
 
-size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes);
+size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes,
+                        int warp_slots = 2);
 // Picks the ring depth (nstages > 0: exactly that depth) for the given warps:
 // two resident CTAs per SM with at least three pages in flight each if they
 // fit, else one CTA with the deepest ring that fits in optin bytes.  Values
 // are staged in two slots of slot_bytes per warp (0: values inline) when the
 // slots fit beside a ring of two pages.  False if nothing fits.
 bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes, int nstages,
-                  size_t optin, SweepConfig* c);
+                  size_t optin, SweepConfig* c, int warp_slots = 2);
 cudaError_t sweep_configure(int prec, size_t smem);
 // resident CTAs per SM for this shared-memory size (>= 1); nw = consumer warps (8 or 16)
 int sweep_blocks_per_sm(int prec, int nw, size_t smem);

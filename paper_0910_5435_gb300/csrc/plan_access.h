@@ -43,6 +43,7 @@ struct StreamView {
   bool values_apart = true;
   int consumer_warps = 8;
   int slot_bytes = 0;                // staging slot per op (0: values in the pages)
+  int warp_slots = 2;                // staging slots per consumer warp
   const double* prescale = nullptr;  // 1 / w_{l+i} (adjoint fold)
   const double2* tw_syn = nullptr;   // e^{i pi m / (4l-1)}: the synthesis phase of eq. phis
   const double2* tw_ana = nullptr;   // its conjugate over 4l-1: the analysis phase

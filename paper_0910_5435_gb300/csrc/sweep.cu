@@ -783,6 +783,8 @@ struct Claim {
   OpHdr h;
   int slot;            // staging slot of its values (0 / 1), or -1
   int field;           // field of its page (batched launches)
+  uint32_t vbytes;     // bytes of its value block
+  bool deferred;       // its copy waits for the warp's only slot to be read
 };
 
 template <class TR>
@@ -797,6 +799,10 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
   uint32_t slot_phase = 0u;  // bit s: parity of slot s's next completion
   uint32_t inflight = 0u;    // bit s: a copy into slot s has not been waited for
   int next_slot = 0;
+  // with one slot per warp the next op's copy starts only once the current
+  // op has read the slot (other warps cover the copy); with two it travels
+  // while the current op runs
+  const bool one_slot = A.warp_slots == 1;
 
   // Op numbers are claimed in order; an op is "opened" once it is published:
   // its header is read and (values kept apart) the bulk copy of its value
@@ -808,9 +814,19 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
     if (lane == 0) t = atomicAdd(&S->n_claimed, 1);
     return __shfl_sync(0xffffffffu, t, 0);
   };
+  auto start_copy = [&](Claim& c) {
+    if (lane == 0) {
+      fence_proxy_async();  // earlier reads of this slot precede the copy into it
+      mbar_arrive_expect_tx(my_bars + c.slot, c.vbytes);
+      const uint8_t* vals = A.fields ? A.fields[c.field].values : A.values;
+      bulk_g2s(my_slots + (size_t)c.slot * kSlotBytes, vals + (size_t)c.h.vref * 16, c.vbytes, my_bars + c.slot);
+    }
+    inflight |= 1u << c.slot;
+    c.deferred = false;
+  };
   // 1: opened, 0: t is past the end of the stream, 2: not yet published
-  // (poll only), -1: aborted
-  auto open = [&](int t, Claim& c, bool block) -> int {
+  // (poll only), -1: aborted.  holding: the warp holds an op not yet run.
+  auto open = [&](int t, Claim& c, bool block, bool holding) -> int {
     auto published = [&] {
       const int q = vload(&S->quit);
       return vload(&S->n_ready) > t || (q >= 0 && t >= q);
@@ -835,28 +851,25 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
     c.h = *reinterpret_cast<const OpHdr*>(c.op);
     c.field = A.fields ? (int)S->stage_field[c.stage] : 0;
     c.slot = -1;
-    const uint32_t vbytes = (uint32_t)((sizeof(Val) * c.h.M * c.h.K + 15) & ~size_t(15));
+    c.deferred = false;
+    c.vbytes = (uint32_t)((sizeof(Val) * c.h.M * c.h.K + 15) & ~size_t(15));
     // a block larger than a slot (not emitted by the planner) is streamed instead
-    if ((c.h.flags & F_VALUES_APART) && my_slots && vbytes <= (uint32_t)kSlotBytes) {
-      c.slot = next_slot;
+    if ((c.h.flags & F_VALUES_APART) && my_slots && c.vbytes <= (uint32_t)kSlotBytes) {
+      c.slot = one_slot ? 0 : next_slot;
       next_slot ^= 1;
-      if (lane == 0) {
-        fence_proxy_async();  // earlier reads of this slot precede the copy into it
-        mbar_arrive_expect_tx(my_bars + c.slot, vbytes);
-        const uint8_t* vals = A.fields ? A.fields[c.field].values : A.values;
-        bulk_g2s(my_slots + (size_t)c.slot * kSlotBytes, vals + (size_t)c.h.vref * 16, vbytes,
-                 my_bars + c.slot);
-      }
-      inflight |= 1u << c.slot;
+      if (one_slot && holding)
+        c.deferred = true;
+      else
+        start_copy(c);
     }
     return 1;
   };
 
   Claim cur, nxt;
-  int rc = open(claim_number(), cur, true);
+  int rc = open(claim_number(), cur, true, false);
   while (rc == 1) {
     const int tn = claim_number();
-    int rn = open(tn, nxt, false);  // the next op's values travel while this one runs
+    int rn = open(tn, nxt, false, cur.slot >= 0);  // the next op's values travel while this one runs
     if (rn < 0) break;
     const long long t1 = tracing ? clock64() : 0;
     bool ok;
@@ -918,7 +931,8 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
       c_exec += t4 - t3;
       ++n_ops;
     }
-    if (rn == 2) rn = open(tn, nxt, true);  // holds nothing now
+    if (rn == 1 && nxt.deferred) start_copy(nxt);  // the slot has been read
+    if (rn == 2) rn = open(tn, nxt, true, false);  // holds nothing now
     if (rn != 1) break;
     cur = nxt;
   }
@@ -943,7 +957,7 @@ __device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_
 // Shared-memory layout of a sweep CTA, used by the kernel and by the host
 // sizing alike: [pages: nst x pb][full, empty barriers: 2 x nst][slot
 // barriers: 2 x nw][Sched] | 128-aligned vectors | 128-aligned staging
-// slots (nw x 2 x slot_bytes).
+// slots (nw x warp_slots x slot_bytes).
 __host__ __device__ inline size_t sweep_vec_offset(int nst, size_t pb, int nw) {
   return ((size_t)nst * pb + 16 * (size_t)nst + 16 * (size_t)nw + sizeof(Sched) + 127) & ~size_t(127);
 }
@@ -991,27 +1005,29 @@ __global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const Swe
   } else if (warp == NW + 1) {
     parser_loop(A, stages, full, empty, S, lane);
   } else {
-    consumer_loop<TR>(A, stages, empty, S, V, lane, slots ? slots + (size_t)warp * 2 * A.slot_bytes : nullptr,
+    const int ws = A.warp_slots == 1 ? 1 : 2;
+    consumer_loop<TR>(A, stages, empty, S, V, lane, slots ? slots + (size_t)warp * ws * A.slot_bytes : nullptr,
                       slot_bars + 2 * warp);
   }
 }
 
 template <class TR>
-size_t smem_for(int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes) {
+size_t smem_for(int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes, int warp_slots) {
   const size_t vec_off = sweep_vec_offset(nstages, (size_t)page_bytes, nw);
   const size_t vec_bytes = sizeof(typename TR::C) * (size_t)num_vecs * (size_t)buf_ab;
   if (slot_bytes <= 0) return vec_off + vec_bytes;
-  return sweep_slot_offset(vec_off, vec_bytes) + (size_t)nw * 2 * slot_bytes;
+  return sweep_slot_offset(vec_off, vec_bytes) + (size_t)nw * (warp_slots == 1 ? 1 : 2) * slot_bytes;
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes) {
+size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes,
+                        int warp_slots) {
   switch (prec) {
-    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
-    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
-    case PREC_SPLIT32_ACC64: return smem_for<TS32A>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
-    default: return smem_for<TS32>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes);
+    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes, warp_slots);
+    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes, warp_slots);
+    case PREC_SPLIT32_ACC64: return smem_for<TS32A>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes, warp_slots);
+    default: return smem_for<TS32>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes, warp_slots);
   }
 }
 
@@ -1053,16 +1069,18 @@ int sweep_blocks_per_sm(int prec, int nw, size_t smem) {
 }
 
 bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes, int nstages,
-                  size_t optin, SweepConfig* c) {
+                  size_t optin, SweepConfig* c, int warp_slots) {
   c->nw = nw;
+  c->warp_slots = warp_slots == 1 ? 1 : 2;
   // staged values need their slots next to a ring of at least two pages
-  c->staged = slot_bytes > 0 && sweep_smem_bytes(prec, page_bytes, 2, buf_ab, num_vecs, nw, slot_bytes) <= optin;
+  c->staged = slot_bytes > 0 &&
+              sweep_smem_bytes(prec, page_bytes, 2, buf_ab, num_vecs, nw, slot_bytes, c->warp_slots) <= optin;
   c->slot_bytes = c->staged ? slot_bytes : 0;
   c->nstages = 0;
   c->ctas_per_sm = 0;
   c->smem = 0;
   for (int nst = (nstages > 0 ? nstages : 8); nst >= (nstages > 0 ? nstages : 2); --nst) {
-    const size_t sm = sweep_smem_bytes(prec, page_bytes, nst, buf_ab, num_vecs, nw, c->slot_bytes);
+    const size_t sm = sweep_smem_bytes(prec, page_bytes, nst, buf_ab, num_vecs, nw, c->slot_bytes, c->warp_slots);
     if (sm > optin) continue;
     const int ctas = std::min(2, sweep_blocks_per_sm(prec, nw, sm));
     const bool better = (ctas > c->ctas_per_sm && (nst >= 3 || c->ctas_per_sm == 0)) || c->ctas_per_sm == 0;

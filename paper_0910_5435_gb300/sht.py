@@ -67,6 +67,7 @@ class sht_plan_opts(ctypes.Structure):
         ("device_build", ctypes.c_int),
         ("device_build_arena_mb", ctypes.c_int),
         ("plan_cache", ctypes.c_char_p),
+        ("staging_slots", ctypes.c_int),
     ]
 
 
@@ -204,7 +205,7 @@ class Plan:
     def __init__(self, l, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, host_only=False,
                  num_threads=0, page_bytes=0, eps_fp32=0.0, consumer_warps=0, values_inline=0,
                  debug_unmet_dependency=0, slot_values=0, device_build=False, device_build_arena_mb=0,
-                 plan_cache=None, _load=None):
+                 plan_cache=None, staging_slots=0, _load=None):
         L = lib()
         opts = sht_plan_opts()
         _check(L.sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
@@ -223,6 +224,7 @@ class Plan:
         opts.device_build_arena_mb = device_build_arena_mb
         cache = os.fsencode(plan_cache) if plan_cache is not None else None
         opts.plan_cache = cache
+        opts.staging_slots = staging_slots
         h = ctypes.c_void_p()
         if _load is not None:
             _check(L.sht_plan_load(os.fsencode(_load), ctypes.byref(opts), ctypes.byref(h)), "sht_plan_load")

@@ -121,7 +121,7 @@ def test_batch_autotune_keeps_results(sht, plans):
     betas, Gs = fields(ls, 2, 4000)
     bp, gp = sht.pointer_array(betas), sht.pointer_array(Gs)
     cfg = sht.sht_batch_autotune(B, 0, bp, gp, reps=2)
-    assert cfg["consumer_warps"] in (8, 16) and 2 <= cfg["nstages"] <= 8
+    assert cfg["consumer_warps"] in (8, 12, 16) and 2 <= cfg["nstages"] <= 8
     Gs2 = [torch.full_like(G, float("nan")) for G in Gs]
     sht.sht_batch_synthesize(B, bp, sht.pointer_array(Gs2))
     assert sht.sht_batch_last_device_status(B) == 0

@@ -216,3 +216,21 @@ def test_l1024_bench_configuration_sampled_orders(sht):
         b = run_analysis(sht, P, prec, Gin, adjoint=True)
         assert rel(b[sel], ba[sel]) < TOL[prec], prec
     P.close()
+
+
+@pytest.mark.parametrize("prec", [0, 2, 1])
+def test_staging_modes_give_identical_outputs(sht, prec):
+    """One staging slot per warp (16 consumer warps, the default) and two
+    (8 warps) run the same ops with the same arithmetic: bit-identical
+    outputs in both directions."""
+    l = 128
+    a = sht.Plan(l, 1e-12, leaf_cols=16)
+    b = sht.Plan(l, 1e-12, leaf_cols=16, consumer_warps=8, staging_slots=2)
+    beta = inputs.random_beta(l, seed=31)
+    Gin = inputs.random_G(l, seed=32)
+    for P in (a, b):
+        P.prepare(prec)
+    assert np.array_equal(run_synth(sht, a, prec, beta), run_synth(sht, b, prec, beta))
+    assert np.array_equal(run_analysis(sht, a, prec, Gin), run_analysis(sht, b, prec, Gin))
+    a.close()
+    b.close()

@@ -101,7 +101,7 @@ def test_invalid_arguments_are_rejected(args):
 def test_invalid_options_are_rejected():
     for kw in [dict(leaf_cols=1), dict(page_bytes=1000), dict(page_bytes=65536), dict(num_threads=-1),
                dict(consumer_warps=10), dict(slot_values=100), dict(slot_values=4096), dict(slot_values=1000),
-               dict(device_build=True), dict(device_build_arena_mb=-1)]:  # a device build needs a device plan
+               dict(device_build=True), dict(device_build_arena_mb=-1), dict(staging_slots=3)]:
         with pytest.raises(sht.ShtError):
             sht.Plan(8, 1e-12, host_only=True, **kw)
 
