@@ -154,12 +154,14 @@ typedef struct {
    * sht_last_error_detail).  A failed write fails plan creation with
    * SHT_ERR_INVALID_ARG.  The string is read during the call only. */
   const char* plan_cache;
-  /* Staging slots per consumer warp when values are kept apart: 1 (default,
-   * also for 0) starts the copy of a warp's next op once its current op has
-   * read the slot, and leaves room for 16 consumer warps whose copies and
-   * arithmetic overlap one another; 2 lets a warp's next op's values travel
-   * while its current op runs, at twice the slot memory (8 warps at the
-   * default slot size).  A tuning knob; results do not depend on it. */
+  /* Staging slots per consumer warp when values are kept apart (0 = per
+   * precision: 1 for SHT_FP64 and the split formats, 2 for SHT_FP32).  1
+   * starts the copy of a warp's next op once its current op has read the
+   * slot, and leaves room for 16 consumer warps whose copies and arithmetic
+   * overlap one another; 2 lets a warp's next op's values travel while its
+   * current op runs, at twice the slot memory (8 warps at the default 8-byte
+   * slot size, 16 with float32 values).  A tuning knob; results do not depend
+   * on it. */
   int staging_slots;
 } sht_plan_opts;
 

@@ -72,7 +72,7 @@ struct sht_plan_s {
   int nstages[kNumPrec] = {4, 4, 4};
   bool staged[kNumPrec] = {false, false, false};
   int slot_bytes[kNumPrec] = {0, 0, 0};
-  int warp_slots = 2;  // staging slots per consumer warp
+  int warp_slots[kNumPrec] = {1, 1, 1};  // staging slots per consumer warp
   int num_vecs[kNumPrec] = {2, 2, 2};
   int ctas_per_sm[kNumPrec] = {1, 1, 1};
   DevStream dev[kNumPrec][2];
@@ -286,7 +286,7 @@ sht_status upload_streams(sht_plan_t P, int q) {
   sht::SweepConfig cfg;
   const int slot_bytes = P->H.values_apart[q] ? P->H.slot_values * (q == sht::PREC_FP32 ? 4 : 8) : 0;
   if (!sht::sweep_choose(q, P->H.page_bytes, buf_ab, nvecs, P->consumer_warps[q], slot_bytes, 0, (size_t)optin,
-                         &cfg, P->warp_slots))
+                         &cfg, P->warp_slots[q]))
     return SHT_ERR_UNSUPPORTED;
   P->nstages[q] = cfg.nstages;
   P->ctas_per_sm[q] = cfg.ctas_per_sm;
@@ -362,7 +362,7 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.num_vecs = P->num_vecs[q];
   a.staged = P->staged[q] ? 1 : 0;
   a.slot_bytes = P->slot_bytes[q];
-  a.warp_slots = P->warp_slots;
+  a.warp_slots = P->warp_slots[q];
   a.counter = P->d_scratch + (q * KIND_COUNT + kind);
   a.status = P->d_scratch + kNumPrec * KIND_COUNT;
   const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
@@ -410,7 +410,7 @@ sht_status sht::prepared_sweep(sht_plan_t P, sht_precision prec, int dir, const 
   a.num_vecs = P->num_vecs[q];
   a.staged = P->staged[q] ? 1 : 0;
   a.slot_bytes = P->slot_bytes[q];
-  a.warp_slots = P->warp_slots;
+  a.warp_slots = P->warp_slots[q];
   L->prec = kernel_prec(prec);
   L->consumer_warps = P->consumer_warps[q];
   L->grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
@@ -442,7 +442,7 @@ sht_status sht::stream_view(sht_plan_t P, sht_precision prec, int dir, StreamVie
   v->values_apart = P->H.values_apart[q];
   v->consumer_warps = P->consumer_warps[q];
   v->slot_bytes = P->H.values_apart[q] ? P->H.slot_values * (q == sht::PREC_FP32 ? 4 : 8) : 0;
-  v->warp_slots = P->warp_slots;
+  v->warp_slots = P->warp_slots[q];
   v->prescale = P->d_inv_w;
   v->tw_syn = P->d_tw_syn;
   v->tw_ana = P->d_tw_ana;
@@ -590,9 +590,11 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
   if (!P) return SHT_ERR_OOM;
   P->opts = o;
   P->host_only = o.host_only != 0;
-  // one staging slot per warp (the default) leaves room for 16 consumer
-  // warps, which keep the FP64 pipe busier than 8 warps with two slots
-  P->warp_slots = o.staging_slots == 2 ? 2 : 1;
+  // one staging slot per warp leaves room for 16 consumer warps, which keep
+  // the FP64 pipe busier than 8 warps with two slots; float32 slots are half
+  // the size, so 16 warps keep two by default
+  for (int q = 0; q < kNumPrec; ++q)
+    P->warp_slots[q] = o.staging_slots ? o.staging_slots : (q == sht::PREC_FP32 ? 2 : 1);
   // 0 = 16 consumer warps for every precision
   for (int q = 0; q < kNumPrec; ++q)
     P->consumer_warps[q] = o.consumer_warps ? o.consumer_warps : 16;
