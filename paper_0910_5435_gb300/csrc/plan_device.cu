@@ -30,6 +30,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <new>
 #include <stdexcept>
 #include <string>
 #include <thread>
@@ -944,6 +945,10 @@ struct CudaBuf {
 };
 
 void check(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    throw std::bad_alloc();  // reported as SHT_ERR_OOM
+  }
   if (e != cudaSuccess) throw DeviceError(std::string("device build: ") + what + ": " + cudaGetErrorString(e));
 }
 
