@@ -111,7 +111,7 @@ inline void renorm(double& v, int& e) {
 }
 }  // namespace
 
-ColumnStream::ColumnStream(const PlanHost& P, int m, int p, int rows)
+ColumnStream::ColumnStream(const PlanHost& P, int m, int p, int rows, int row0)
     : m_(m), p_(p), rows_(rows), j_(0) {
   const int l = P.l;
   x2_.resize(rows);
@@ -129,10 +129,11 @@ ColumnStream::ColumnStream(const PlanHost& P, int m, int p, int rows)
   }
   const bool custom = !P.row_x.empty();
   for (int i = 0; i < rows; ++i) {
-    const double xi = custom ? P.row_x[i] : P.x[l + i];
-    const double s = std::sin(custom ? P.row_theta[i] : P.theta_pos[i]);
+    const int g = row0 + i;
+    const double xi = custom ? P.row_x[g] : P.x[l + g];
+    const double s = std::sin(custom ? P.row_theta[g] : P.theta_pos[g]);
     x2_[i] = xi * xi;
-    sq2w_[i] = custom ? P.row_sqw[i] : std::sqrt(2.0 * P.w[l + i]);
+    sq2w_[i] = custom ? P.row_sqw[g] : std::sqrt(2.0 * P.w[l + g]);
     // s^m by binary powering with tracked exponents
     int eb;
     double base = std::frexp(s, &eb);
@@ -159,7 +160,21 @@ ColumnStream::ColumnStream(const PlanHost& P, int m, int p, int rows)
 
 void ColumnStream::next(double* col) {
   const int k = m_ + p_ + 2 * j_;
-  for (int i = 0; i < rows_; ++i) col[i] = sq2w_[i] * std::ldexp(b_[i], e_[i]);
+  // b 2^e: one product with an exact power of two where 2^e is a normal
+  // number (the same correctly rounded value as ldexp), ldexp otherwise
+  for (int i = 0; i < rows_; ++i) {
+    const int e = e_[i];
+    double s;
+    if (e >= -1022 && e <= 1023) {
+      const uint64_t bits = (uint64_t)(e + 1023) << 52;
+      double p2;
+      std::memcpy(&p2, &bits, 8);
+      s = b_[i] * p2;
+    } else {
+      s = std::ldexp(b_[i], e);
+    }
+    col[i] = sq2w_[i] * s;
+  }
   // advance P-bar_k -> P-bar_{k+2}: x^2 P_k = c_{k-2} P_{k-2} + d_k P_k + c_k P_{k+2}
   const double ck = rec_c(k, m_), dk = rec_d(k, m_);
   const double ckm2 = (j_ > 0) ? rec_c(k - 2, m_) : 0.0;  // eq. recurrence0 for j = 0
@@ -181,6 +196,27 @@ void ColumnStream::next(double* col) {
 
 // ------------------------------------------------------------------ ID
 
+namespace {
+// sum_{r < n} a[r] b[r] with four partial sums (independent add chains, so
+// the loop is not bound by the latency of one chain of additions)
+inline double dot4(const double* a, const double* b, int n) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int r = 0;
+  for (; r + 4 <= n; r += 4) {
+    s0 += a[r] * b[r];
+    s1 += a[r + 1] * b[r + 1];
+    s2 += a[r + 2] * b[r + 2];
+    s3 += a[r + 3] * b[r + 3];
+  }
+  for (; r < n; ++r) s0 += a[r] * b[r];
+  return (s0 + s1) + (s2 + s3);
+}
+// y[r] -= d x[r], r < n (y and x are different columns)
+inline void axpy_neg(double* __restrict y, const double* __restrict x, double d, int n) {
+  for (int r = 0; r < n; ++r) y[r] -= d * x[r];
+}
+}  // namespace
+
 int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm, std::vector<double>& T, int* swaps) {
   perm.resize(w);
   std::iota(perm.begin(), perm.end(), 0);
@@ -191,25 +227,20 @@ int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm, s
   std::vector<double> nrm(w), ref(w);
   for (int j = 0; j < w; ++j) {
     const double* c = A + (size_t)j * h;
-    double s = 0.0;
-    for (int r = 0; r < h; ++r) s += c[r] * c[r];
-    nrm[j] = ref[j] = s;
+    nrm[j] = ref[j] = dot4(c, c, h);
   }
   const double eps2 = eps * eps;
   const int kmax = std::min(h, w);
   int k = 0;
   auto exact_norm = [&](int j, int i0) {
-    const double* c = A + (size_t)j * h;
-    double s = 0.0;
-    for (int r = i0; r < h; ++r) s += c[r] * c[r];
-    return s;
+    const double* c = A + (size_t)j * h + i0;
+    return dot4(c, c, h - i0);
   };
   // Householder reflector for A[i:h, i], applied to columns i+1..w-1
   auto reflect = [&](int i) {
     double* ci = A + (size_t)i * h;
     const double alpha = ci[i];
-    double sigma = 0.0;
-    for (int r = i + 1; r < h; ++r) sigma += ci[r] * ci[r];
+    const double sigma = dot4(ci + i + 1, ci + i + 1, h - i - 1);
     double tau = 0.0;
     if (sigma != 0.0 || alpha < 0.0) {
       const double nx = std::sqrt(alpha * alpha + sigma);
@@ -222,11 +253,10 @@ int interp_decomp(double* A, int h, int w, double eps, std::vector<int>& perm, s
     if (tau != 0.0) {
       for (int j = i + 1; j < w; ++j) {
         double* cj = A + (size_t)j * h;
-        double dot = cj[i];
-        for (int r = i + 1; r < h; ++r) dot += ci[r] * cj[r];
+        double dot = cj[i] + dot4(ci + i + 1, cj + i + 1, h - i - 1);
         dot *= tau;
         cj[i] -= dot;
-        for (int r = i + 1; r < h; ++r) cj[r] -= dot * ci[r];
+        axpy_neg(cj + i + 1, ci + i + 1, dot, h - i - 1);
       }
     }
   };
@@ -336,20 +366,34 @@ UnitFact factor_unit(const PlanHost& P, int m, int p, double eps) {
   U.n = n;
   if (n == 0) return U;
 
-  // trimming: rows whose weighted norm is below trim/sqrt(l) (a suffix) are dropped
+  // trimming: rows whose weighted norm is below trim/sqrt(l) (a suffix) are
+  // dropped.  Only the last row that reaches the threshold matters, so rows
+  // are tried from the pole down, 64 at a time, and a chunk's columns stop
+  // once every row in it has reached the threshold (a sum only grows): the
+  // same decision as summing every row over every column.
   int rows = l;
-  std::vector<double> col(l);
   if (P.trim_eps > 0.0) {
-    ColumnStream cs(P, m, p, l);
-    std::vector<double> nr(l, 0.0);
-    for (int j = 0; j < n; ++j) {
-      cs.next(col.data());
-      for (int i = 0; i < l; ++i) nr[i] += col[i] * col[i];
-    }
     const double thr = P.trim_eps / std::sqrt((double)l);
+    const double thr2 = thr * thr;
+    constexpr int kChunk = 64;
+    std::vector<double> col(kChunk), nr(kChunk);
     rows = 0;
-    for (int i = 0; i < l; ++i)
-      if (nr[i] >= thr * thr) rows = i + 1;
+    for (int top = l; top > 0 && rows == 0; top -= kChunk) {
+      const int r0 = std::max(0, top - kChunk), nrows = top - r0;
+      ColumnStream cs(P, m, p, nrows, r0);
+      std::fill(nr.begin(), nr.end(), 0.0);
+      int reached = 0;
+      for (int j = 0; j < n && reached < nrows; ++j) {
+        cs.next(col.data());
+        reached = 0;
+        for (int i = 0; i < nrows; ++i) {
+          if (nr[i] < thr2) nr[i] += col[i] * col[i];
+          reached += nr[i] >= thr2;
+        }
+      }
+      for (int i = nrows - 1; i >= 0 && rows == 0; --i)
+        if (nr[i] >= thr2) rows = r0 + i + 1;
+    }
   }
   U.rows = rows;
   if (rows == 0) return U;

@@ -137,7 +137,8 @@ void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vec
 // (Section 4).
 class ColumnStream {
  public:
-  ColumnStream(const PlanHost& P, int m, int p, int rows);
+  // rows row0 .. row0 + rows - 1 of the block
+  ColumnStream(const PlanHost& P, int m, int p, int rows, int row0 = 0);
   // writes column next_col() into col[0..rows)
   void next(double* col);
   int next_col() const { return j_; }
