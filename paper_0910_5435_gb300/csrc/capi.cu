@@ -589,6 +589,7 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
   sht_plan_t P = new (std::nothrow) sht_plan_s();
   if (!P) return SHT_ERR_OOM;
   P->opts = o;
+  P->opts.plan_cache = nullptr;  // the caller's string outlives only this call
   P->host_only = o.host_only != 0;
   // one staging slot per warp leaves room for 16 consumer warps, which keep
   // the FP64 pipe busier than 8 warps with two slots; float32 slots are half
