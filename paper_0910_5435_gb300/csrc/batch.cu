@@ -258,8 +258,9 @@ sht_status sht_batch_synthesize_adjoint(sht_batch_t b, const void* const* G, voi
 sht_status sht_batch_synthesize_grid(sht_batch_t b, const void* const* beta, void* const* values,
                                      void* const* workspace, sht_stream_t stream) {
   if (!b || !beta || !values || !workspace) return SHT_ERR_INVALID_ARG;
+  const size_t al = (b->q == sht::PREC_FP32) ? 8 : 16;
   for (int f = 0; f < b->n; ++f)
-    if (!values[f]) return SHT_ERR_INVALID_ARG;
+    if (!values[f] || reinterpret_cast<uintptr_t>(values[f]) % al) return SHT_ERR_INVALID_ARG;
   BCK(cudaSetDevice(b->device));
   // one launch: every field's Legendre stage with the phase, into its workspace
   sht_status s = launch_from_host(b, 3, beta, workspace, stream);
@@ -275,7 +276,7 @@ sht_status sht_batch_analyze_grid(sht_batch_t b, const void* const* values, void
   const size_t al = (b->q == sht::PREC_FP32) ? 8 : 16;
   for (int f = 0; f < b->n; ++f)
     if (!values[f] || !workspace[f] || !beta[f] || reinterpret_cast<uintptr_t>(workspace[f]) % al ||
-        reinterpret_cast<uintptr_t>(beta[f]) % al)
+        reinterpret_cast<uintptr_t>(beta[f]) % al || reinterpret_cast<uintptr_t>(values[f]) % al)
       return SHT_ERR_INVALID_ARG;
   BCK(cudaSetDevice(b->device));
   // each field's real-to-complex FFTs into its workspace
