@@ -384,7 +384,7 @@ sht_status sht_direct_analyze(sht_plan_t plan, const void* G, void* beta, sht_st
 /* ---------------------------------------------------- one block, any size */
 
 /* Largest bandlimit sht_unit_stats_compute accepts. */
-#define SHT_UNIT_STATS_MAX_L 20000
+#define SHT_UNIT_STATS_MAX_L 40000
 
 typedef struct {
   int l, m, parity;

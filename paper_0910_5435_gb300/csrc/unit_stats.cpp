@@ -18,11 +18,13 @@
 // products stream the columns of A with the same x^2 recurrence, so no
 // l x n array is stored.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <exception>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/sht.h"
@@ -221,6 +223,26 @@ namespace sht {
 // keeps full relative accuracy for the small t near x = 0).  Weights: the
 // rows of sqrt(rho_i) P-bar^m_{m+p+2j}(x_i) are orthonormal (the matrix is
 // orthogonal by Lemma quadratures), so rho_i = 1 / sum_{j<n} P-bar^m_{m+p+2j}(x_i)^2.
+namespace {
+// Runs body(i), i < count, on all hardware threads.
+template <class F>
+void parallel_for(int count, F&& body) {
+  const int nt = std::max(1, std::min<int>(count, (int)std::thread::hardware_concurrency()));
+  std::atomic<int> next(0);
+  auto worker = [&]() {
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= count) break;
+      body(i);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(worker);
+  worker();
+  for (auto& t : th) t.join();
+}
+}  // namespace
+
 void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector<double>& theta,
                         std::vector<double>& rho) {
   std::vector<double> a(n), b2(n, 0.0);
@@ -242,47 +264,56 @@ void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector
     }
     return cnt;
   };
-  std::vector<double> t(n);
-  double lo_prev = 0.0;
-  for (int k = 0; k < n; ++k) {
-    double lo = lo_prev, hi = 1.0;
-    for (int it = 0; it < 56 && hi - lo > 1e-15 * hi; ++it) {
-      const double mid = 0.5 * (lo + hi);
-      if (below(mid) > k) hi = mid; else lo = mid;
-    }
-    t[k] = 0.5 * (lo + hi);
-    lo_prev = lo;
+  std::vector<double> t(n), cc(n), cm(n);
+  for (int j = 0; j < n; ++j) {
+    const int kk = m + p + 2 * j;
+    cc[j] = rec_c(kk, m);
+    cm[j] = j ? rec_c(kk - 2, m) : 0.0;
   }
-  // Newton on the degree-n polynomial of the recurrence (value and
-  // derivative, rescaled together against overflow)
-  for (int k = 0; k < n; ++k) {
-    double tk = t[k];
-    for (int it = 0; it < 4; ++it) {
-      double q0 = 0.0, dq0 = 0.0, q1 = 1.0, dq1 = 0.0;
-      for (int j = 0; j < n; ++j) {
-        const int kk = m + p + 2 * j;
-        const double c = rec_c(kk, m), cm = j ? rec_c(kk - 2, m) : 0.0;
-        const double q2 = ((tk - a[j]) * q1 - cm * q0) / c;
-        const double dq2 = ((tk - a[j]) * dq1 + q1 - cm * dq0) / c;
-        q0 = q1;
-        dq0 = dq1;
-        q1 = q2;
-        dq1 = dq2;
-        const double big = std::max(std::fabs(q1), std::fabs(dq1));
-        if (big > 1e150) {
-          q0 /= big;
-          dq0 /= big;
-          q1 /= big;
-          dq1 /= big;
-        }
+  // The eigenvalues are independent: chunks of consecutive indices run on
+  // the host threads (within a chunk, each bracket starts at the previous
+  // eigenvalue's lower end; a chunk starts at 0), so the results do not
+  // depend on the number of threads.
+  constexpr int kChunk = 64;
+  const int nchunks = (n + kChunk - 1) / kChunk;
+  parallel_for(nchunks, [&](int ch) {
+    const int k0 = ch * kChunk, k1 = std::min(n, k0 + kChunk);
+    double lo_prev = 0.0;
+    for (int k = k0; k < k1; ++k) {
+      double lo = lo_prev, hi = 1.0;
+      for (int it = 0; it < 56 && hi - lo > 1e-15 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (below(mid) > k) hi = mid; else lo = mid;
       }
-      if (dq1 == 0.0) break;
-      const double step = q1 / dq1;
-      tk -= step;
-      if (std::fabs(step) <= 1e-17 * tk) break;
+      lo_prev = lo;
+      // Newton on the degree-n polynomial of the recurrence (value and
+      // derivative, rescaled together against overflow)
+      double tk = 0.5 * (lo + hi);
+      for (int it = 0; it < 4; ++it) {
+        double q0 = 0.0, dq0 = 0.0, q1 = 1.0, dq1 = 0.0;
+        for (int j = 0; j < n; ++j) {
+          const double q2 = ((tk - a[j]) * q1 - cm[j] * q0) / cc[j];
+          const double dq2 = ((tk - a[j]) * dq1 + q1 - cm[j] * dq0) / cc[j];
+          q0 = q1;
+          dq0 = dq1;
+          q1 = q2;
+          dq1 = dq2;
+          const double big = std::max(std::fabs(q1), std::fabs(dq1));
+          if (big > 1e150) {
+            q0 /= big;
+            dq0 /= big;
+            q1 /= big;
+            dq1 /= big;
+          }
+        }
+        if (dq1 == 0.0) break;
+        const double step = q1 / dq1;
+        tk -= step;
+        if (std::fabs(step) <= 1e-17 * tk) break;
+      }
+      t[k] = tk;
     }
-    t[k] = tk;
-  }
+  });
   x.resize(n);
   theta.resize(n);
   for (int k = 0; k < n; ++k) {
@@ -295,12 +326,17 @@ void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector
   Q.row_x = x;
   Q.row_theta = theta;
   Q.row_sqw.assign(n, 1.0);
-  std::vector<double> sum(n, 0.0), col(n);
-  ColumnStream cs(Q, m, p, n);
-  for (int j = 0; j < n; ++j) {
-    cs.next(col.data());
-    for (int i = 0; i < n; ++i) sum[i] += col[i] * col[i];
-  }
+  std::vector<double> sum(n, 0.0);
+  const int rchunks = (n + kChunk - 1) / kChunk;
+  parallel_for(rchunks, [&](int ch) {
+    const int r0 = ch * kChunk, nr = std::min(n, r0 + kChunk) - r0;
+    std::vector<double> col(nr);
+    ColumnStream cs(Q, m, p, nr, r0);
+    for (int j = 0; j < n; ++j) {
+      cs.next(col.data());
+      for (int i = 0; i < nr; ++i) sum[r0 + i] += col[i] * col[i];
+    }
+  });
   rho.resize(n);
   for (int i = 0; i < n; ++i) rho[i] = sum[i] > 0.0 ? 1.0 / sum[i] : 0.0;
 }

@@ -347,7 +347,7 @@ class sht_unit_stats(ctypes.Structure):
 def unit_stats(l, m=0, parity=0, eps_id=1e-12, leaf_cols=64, trim_eps=-1.0, min_band_rows=0, seed=1,
                gauss_jacobi=False):
     """Rank statistics, costs and errors of one parity block's butterfly
-    (``sht_unit_stats_compute``; host only, any l up to 20000).  With
+    (``sht_unit_stats_compute``; host only, any l up to 40000).  With
     gauss_jacobi the block is the paper's n x n matrix at its own nodes, n = l
     (``sht_unit_stats_gauss_jacobi``)."""
     opts = sht_plan_opts()

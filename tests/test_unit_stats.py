@@ -75,5 +75,5 @@ def test_invalid_arguments():
     import ctypes
     out = sht.sht_unit_stats()
     L = sht.lib()
-    for args in [(0, 0, 0, 1e-12), (20001, 0, 0, 1e-12), (64, 128, 0, 1e-12), (64, 0, 2, 1e-12), (64, 0, 0, 0.0)]:
+    for args in [(0, 0, 0, 1e-12), (40001, 0, 0, 1e-12), (64, 128, 0, 1e-12), (64, 0, 2, 1e-12), (64, 0, 0, 0.0)]:
         assert L.sht_unit_stats_compute(*args, None, 1, ctypes.byref(out)) == 1
