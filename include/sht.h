@@ -438,6 +438,19 @@ sht_status sht_gauss_jacobi_nodes(int m, int parity, int n, double* x, double* r
 sht_status sht_unit_stats_gauss_jacobi(int n, int m, int parity, double eps_id, const sht_plan_opts* opts,
                                        unsigned long long seed, sht_unit_stats* out);
 
+/* The interpolative decomposition every butterfly block is built from
+ * (Section 2.1, eq. 2.1 and Remark QR_algorithm), on the host: column-pivoted
+ * Householder QR of the h x w column-major matrix A (host, not modified) to
+ * the rank k at which every remaining column norm is <= eps, followed by the
+ * strong rank-revealing exchanges that bound every interpolation
+ * coefficient by 2 in magnitude.  Outputs (host arrays owned by the caller):
+ * *k; perm[w], the k skeleton columns then the w - k others in ascending
+ * order; T[k * (w - k)] (at most w^2 / 4 entries), column s holding the
+ * coefficients with A[:, perm[k + s]] ~= sum_t T[s * k + t] A[:, perm[t]];
+ * *swaps (if not NULL), the exchanges made.  1 <= h, 1 <= w <= 65535,
+ * eps > 0. */
+sht_status sht_interp_decomp(const double* A, int h, int w, double eps, int* k, int* perm, double* T, int* swaps);
+
 /* ------------------------------------------------------------ many fields */
 
 /* The paper transforms one function at a time.  A batch runs the Legendre

@@ -402,3 +402,24 @@ extern "C" sht_status sht_unit_stats_compute(int l, int m, int parity, double ep
     return SHT_ERR_INVALID_ARG;
   }
 }
+
+extern "C" sht_status sht_interp_decomp(const double* A, int h, int w, double eps, int* k, int* perm, double* T,
+                                        int* swaps) {
+  if (!A || !k || !perm || !T || h < 1 || w < 1 || w > 65535 || !(eps > 0.0)) return SHT_ERR_INVALID_ARG;
+  try {
+    std::vector<double> work(A, A + (size_t)h * w);
+    std::vector<int> p;
+    std::vector<double> t;
+    int sw = 0;
+    const int kk = sht::interp_decomp(work.data(), h, w, eps, p, t, &sw);
+    *k = kk;
+    std::copy(p.begin(), p.end(), perm);
+    std::copy(t.begin(), t.end(), T);
+    if (swaps) *swaps = sw;
+  } catch (const std::bad_alloc&) {
+    return SHT_ERR_OOM;
+  } catch (...) {
+    return SHT_ERR_INVALID_ARG;
+  }
+  return SHT_OK;
+}

@@ -36,7 +36,7 @@ EXPORTS = [
     "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config", "sht_batch_synthesize_adjoint",
     "sht_unit_stats_compute", "sht_gauss_jacobi_nodes", "sht_unit_stats_gauss_jacobi",
     "sht_plan_save", "sht_plan_load", "sht_batch_synthesize_grid", "sht_batch_analyze_grid",
-    "sht_measure_fp64_fma",
+    "sht_measure_fp64_fma", "sht_interp_decomp",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -161,6 +161,8 @@ def lib():
     L.sht_batch_synthesize_adjoint.argtypes = [vp, vp, vp, vp]
     L.sht_batch_synthesize_grid.argtypes = [vp, vp, vp, vp, vp]
     L.sht_measure_fp64_fma.argtypes = [ctypes.POINTER(c_double)]
+    L.sht_interp_decomp.argtypes = [vp, c_int, c_int, c_double, ctypes.POINTER(c_int), vp, vp,
+                                    ctypes.POINTER(c_int)]
     L.sht_batch_analyze_grid.argtypes = [vp, vp, vp, vp, vp]
     L.sht_batch_last_device_status.argtypes = [vp, vp]
     L.sht_batch_autotune.argtypes = [vp, c_int, vp, vp, c_int, vp]
@@ -421,6 +423,23 @@ def sht_batch_analyze(batch, G_ptrs, beta_ptrs, stream=None):
 def sht_batch_synthesize_adjoint(batch, G_ptrs, beta_ptrs, stream=None):
     _check(lib().sht_batch_synthesize_adjoint(batch.handle, _ptr(G_ptrs), _ptr(beta_ptrs), _stream(stream)),
            "sht_batch_synthesize_adjoint")
+
+
+def interp_decomp(A, eps):
+    """Interpolative decomposition of the real matrix A (sht_interp_decomp):
+    returns (skeleton column indices, redundant column indices, T, exchanges)
+    with A[:, redundant] ~= A[:, skeleton] @ T."""
+    A = np.asfortranarray(np.asarray(A, dtype=np.float64))
+    h, w = A.shape
+    k = ctypes.c_int()
+    sw = ctypes.c_int()
+    perm = np.zeros(w, dtype=np.int32)
+    T = np.zeros(max(1, (w * w) // 4 + 1), dtype=np.float64)
+    _check(lib().sht_interp_decomp(A.ctypes.data, h, w, float(eps), ctypes.byref(k), perm.ctypes.data,
+                                   T.ctypes.data, ctypes.byref(sw)), "sht_interp_decomp")
+    kk = k.value
+    Tm = T[:kk * (w - kk)].reshape(w - kk, kk).T.copy()
+    return perm[:kk].copy(), perm[kk:].copy(), Tm, sw.value
 
 
 def measure_fp64_fma():
