@@ -141,3 +141,32 @@ def test_analysis_is_weighted_adjoint():
     lhs = np.vdot(oracle.legendre_synthesis(b, l), G).real
     rhs = np.vdot(b, oracle.legendre_adjoint(G, l)).real
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_loss_gradient_against_central_differences():
+    """The gradient convention of the differentiable synthesis: for
+    L(beta) = sum |synth(beta) - g|^2 over all orders and nodes, the gradient
+    dL/dRe beta + i dL/dIm beta equals 2 adjoint(synth(beta) - g).  Pinned by
+    central differences of L itself on every real coordinate; L is quadratic,
+    so the differences are exact up to rounding."""
+    l = 4
+    beta = inputs.random_beta(l, seed=21, decay=True)
+    g = oracle.legendre_synthesis(inputs.random_beta(l, seed=22), l)
+
+    def loss(b):
+        return float(np.sum(np.abs(oracle.legendre_synthesis(b, l) - g) ** 2))
+
+    grad = 2.0 * oracle.legendre_adjoint(oracle.legendre_synthesis(beta, l) - g, l)
+    ms, _ = inputs.triangle_index(l)
+    h = 1e-6
+    fd = np.zeros_like(beta)
+    for c in range(beta.size):
+        for unit in (1.0, 1j):
+            if unit == 1j and ms[c] == 0:
+                continue  # beta^0_k is real: no imaginary coordinate
+            e = np.zeros_like(beta)
+            e[c] = h * unit
+            d = (loss(beta + e) - loss(beta - e)) / (2 * h)
+            fd[c] += d * unit
+    assert np.all(grad.imag[ms == 0] == 0.0)
+    np.testing.assert_allclose(fd, grad, rtol=0, atol=1e-7 * np.abs(grad).max())
