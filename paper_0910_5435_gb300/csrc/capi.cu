@@ -29,6 +29,13 @@ constexpr int kNumPrec = 3;
 
 // Launch kinds that own a work-queue counter: synthesis, analysis, adjoint.
 enum { KIND_SYN = 0, KIND_ANA = 1, KIND_ADJ = 2, KIND_COUNT = 3 };
+// Counters are kept per sweep kernel variant (sht::SweepPrec), not per stream
+// format: SHT_SPLIT32 and SHT_SPLIT32_ACC64 apply the same streams but are
+// different precisions, whose launches may overlap.
+constexpr int kNumKernels = 4;
+static_assert(sht::PREC_SPLIT32_ACC64 < kNumKernels, "one counter row per sweep kernel variant");
+constexpr int kStatusWord = kNumKernels * KIND_COUNT;  // after the counters
+constexpr size_t kScratchBytes = sizeof(unsigned) * (kStatusWord + 1);
 
 struct DevStream {
   uint8_t* pages = nullptr;
@@ -85,7 +92,7 @@ struct sht_plan_s {
   cufftHandle fft_r2c[2] = {0, 0};
   bool fft_ready[2] = {false, false};
   double* d_w_pos = nullptr;   // w_{l+i}
-  unsigned* d_scratch = nullptr;  // [kNumPrec * KIND_COUNT] queue counters, then the status word
+  unsigned* d_scratch = nullptr;  // [kNumKernels * KIND_COUNT] queue counters, then the status word
   unsigned long long* d_trace = nullptr;  // sweep cycle counters while tracing is enabled
   // direct baseline
   double* d_dense = nullptr;
@@ -363,8 +370,8 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.staged = P->staged[q] ? 1 : 0;
   a.slot_bytes = P->slot_bytes[q];
   a.warp_slots = P->warp_slots[q];
-  a.counter = P->d_scratch + (q * KIND_COUNT + kind);
-  a.status = P->d_scratch + kNumPrec * KIND_COUNT;
+  a.counter = P->d_scratch + (kernel_prec(prec) * KIND_COUNT + kind);
+  a.status = P->d_scratch + kStatusWord;
   const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
   (void)cudaGetLastError();  // do not report a stale error left by an earlier call (e.g. inside cuFFT)
   CK(sht::sweep_launch(kernel_prec(prec), P->consumer_warps[q], a, grid, P->smem[q],
@@ -688,10 +695,10 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&P->d_inv_w, sizeof(double) * l);
     if (e == cudaSuccess) e = cudaMalloc(&P->d_w_pos, sizeof(double) * l);
-    if (e == cudaSuccess) e = cudaMalloc(&P->d_scratch, sizeof(unsigned) * (kNumPrec * KIND_COUNT + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_scratch, kScratchBytes);
     if (e == cudaSuccess) e = cudaMemcpy(P->d_inv_w, invw.data(), sizeof(double) * l, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->d_w_pos, wpos.data(), sizeof(double) * l, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(P->d_scratch, 0, sizeof(unsigned) * (kNumPrec * KIND_COUNT + 1));
+    if (e == cudaSuccess) e = cudaMemset(P->d_scratch, 0, kScratchBytes);
     if (e == cudaSuccess) {
       const int L = 2 * l, N = 4 * l - 1;
       std::vector<double2> ts(L), ta(L);
@@ -801,10 +808,10 @@ sht_status sht_last_device_status(sht_plan_t P, sht_stream_t stream) {
   CK(cudaSetDevice(P->device));
   CK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
   unsigned st = 0;
-  CK(cudaMemcpy(&st, P->d_scratch + kNumPrec * KIND_COUNT, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&st, P->d_scratch + kStatusWord, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (st != 0) {
     // a kernel stopped early: its queue counter may not have been reset
-    CK(cudaMemset(P->d_scratch, 0, sizeof(unsigned) * (kNumPrec * KIND_COUNT + 1)));
+    CK(cudaMemset(P->d_scratch, 0, kScratchBytes));
     return (sht_status)st;
   }
   return SHT_OK;

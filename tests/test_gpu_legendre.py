@@ -234,3 +234,27 @@ def test_staging_modes_give_identical_outputs(sht, prec):
     assert np.array_equal(run_analysis(sht, a, prec, Gin), run_analysis(sht, b, prec, Gin))
     a.close()
     b.close()
+
+
+def test_split_precisions_overlap_on_two_streams(sht):
+    """SHT_SPLIT32 and SHT_SPLIT32_ACC64 apply the same factor streams with
+    different kernels.  Each precision has its own work-queue counters, so
+    their launches may overlap on two streams; every output equals that of a
+    launch made alone (both kernels are deterministic)."""
+    l = 256
+    P = plan(sht, l, 32)
+    beta = inputs.random_beta(l, seed=12, decay=True)
+    alone = {q: run_synth(sht, P, q, beta) for q in (2, 3)}
+    b = torch.from_numpy(beta).cuda()
+    streams = {q: torch.cuda.Stream() for q in (2, 3)}
+    outs = {q: [torch.full((2 * l, 2 * l), float("nan"), dtype=torch.complex128, device="cuda")
+                for _ in range(3)] for q in (2, 3)}
+    torch.cuda.synchronize()
+    for r in range(3):
+        for q in (2, 3):
+            sht.sht_legendre_synthesize(P, q, b, outs[q][r], stream=streams[q])
+    torch.cuda.synchronize()
+    assert sht.sht_last_device_status(P) == 0
+    for q in (2, 3):
+        for r in range(3):
+            assert np.array_equal(outs[q][r].cpu().numpy(), alone[q]), (q, r)
