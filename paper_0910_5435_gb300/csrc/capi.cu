@@ -4,6 +4,7 @@
 #include <cufft.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -84,6 +85,10 @@ struct sht_plan_s {
   int ctas_per_sm[kNumPrec] = {1, 1, 1};
   DevStream dev[kNumPrec][2];
   bool dev_ready[kNumPrec] = {false, false, false};
+  // Precision q is built (and, unless host_only, uploaded) with its launch
+  // shape chosen.  Stored with release once everything it guards is written,
+  // read with acquire by the launch paths that skip the plan's mutex.
+  std::atomic<bool> ready[kNumPrec] = {false, false, false};
   size_t smem[kNumPrec] = {0, 0, 0};
   double* d_inv_w = nullptr;   // 1 / w_{l+i}: the adjoint's fold prescale
   double2* d_tw_syn = nullptr; // e^{i pi m / N}, N = 4l - 1 (phi stage, eq. phis)
@@ -325,8 +330,9 @@ sht_status upload(sht_plan_t P, int q) {
 // Makes precision q ready; cheap once it is (the launch path calls it every
 // time), statistics are refreshed only when something was built.
 sht_status ensure_prec(sht_plan_t P, int q) {
-  if (P->H.built[q] && (P->host_only || P->dev_ready[q])) return SHT_OK;
+  if (P->ready[q].load(std::memory_order_acquire)) return SHT_OK;
   std::lock_guard<std::mutex> g(P->mu);
+  if (P->ready[q].load(std::memory_order_relaxed)) return SHT_OK;
   sht_status s = build_host(P, q);
   if (s != SHT_OK) return s;
   if (!P->host_only) {
@@ -334,6 +340,7 @@ sht_status ensure_prec(sht_plan_t P, int q) {
     if (s != SHT_OK) return s;
   }
   fill_stats(P);
+  P->ready[q].store(true, std::memory_order_release);
   return SHT_OK;
 }
 
@@ -391,7 +398,7 @@ sht_status sht::prepared_sweep(sht_plan_t P, sht_precision prec, int dir, const 
   if (P->host_only) return SHT_ERR_UNSUPPORTED;
   const size_t al = (q == sht::PREC_FP32) ? 8 : 16;
   if (!aligned(in, al) || !aligned(out, al)) return SHT_ERR_INVALID_ARG;
-  if (!P->dev_ready[q]) {
+  if (!P->ready[q].load(std::memory_order_acquire)) {
     set_detail("prepared_sweep", "precision not on the device yet (sht_prepare uploads it)");
     return SHT_ERR_UNSUPPORTED;
   }
@@ -726,6 +733,7 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
     }
   }
   fill_stats(P);
+  P->ready[sht::PREC_FP64].store(true, std::memory_order_release);
   *out = P;
   return SHT_OK;
 }
