@@ -26,6 +26,8 @@
 #include <thread>
 #include <vector>
 
+#include <sys/types.h>  // off_t for fseeko / ftello
+
 #include "plan_host.h"
 
 namespace sht {
@@ -364,11 +366,21 @@ void load_factorizations(PlanHost& P, const std::string& path) {
     throw PlanFileError("plan file: unit table ends early");
   if (hash_bytes(reinterpret_cast<const uint8_t*>(table.data()), sizeof(UnitRecord) * nrec) != h.table_hash)
     throw PlanFileError("plan file: unit table checksum mismatch");
+  // The payload is the rest of the file.  Every record must fit in what is
+  // left of it, so that a forged table (its hash is not cryptographic) can
+  // neither wrap the running sum nor size an allocation beyond the file.
+  const off_t here = ftello(f.f);
+  if (here < 0 || fseeko(f.f, 0, SEEK_END) != 0) throw PlanFileError("plan file: cannot determine its size");
+  const off_t end = ftello(f.f);
+  if (end < here || fseeko(f.f, here, SEEK_SET) != 0) throw PlanFileError("plan file: cannot determine its size");
+  const uint64_t avail = (uint64_t)(end - here);
   uint64_t total = 0;
   for (const UnitRecord& r : table) {
     if (r.offset != total) throw PlanFileError("plan file: unit table is not contiguous");
+    if (r.bytes > avail - total) throw PlanFileError("plan file: payload ends early");
     total += r.bytes;
   }
+  if (total != avail) throw PlanFileError("plan file: trailing bytes after the payload");
   ByteBuf payload;
   payload.resize(total);
   if (total && std::fread(payload.data(), 1, total, f.f) != total) throw PlanFileError("plan file: payload ends early");

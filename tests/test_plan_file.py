@@ -125,3 +125,63 @@ def test_plan_cache_builds_once_and_rebuilds_when_stale(tmp_path):
     assert e.stats()["t_factor"] > 0 and same_streams(c, e)
     assert b"rebuilt" in sht.lib().sht_last_error_detail()
     sht.Plan.load(cache, host_only=True)  # rewritten intact
+
+
+def _file_hash(b):
+    """The plan file's integrity hash (64-bit multiply-xorshift over
+    little-endian 8-byte words, the tail zero-padded), restated so that a test
+    can forge a table whose checksums still match."""
+    M = (1 << 64) - 1
+    n = len(b)
+    h = 0x9E3779B97F4A7C15 ^ n
+    i = 0
+    while i + 8 <= n:
+        h = ((h ^ int.from_bytes(b[i:i + 8], "little")) * 0xFF51AFD7ED558CCD) & M
+        h ^= h >> 29
+        i += 8
+    t = int.from_bytes(bytes(b[i:n]) + bytes(8 - (n - i)), "little") if i < n else 0
+    h = ((h ^ t) * 0xC4CEB9FE1A85EC53) & M
+    return h ^ (h >> 32)
+
+
+@pytest.mark.parametrize("forgery", ["oversized record", "wrapping sizes"])
+def test_forged_unit_table_with_matching_checksums_is_refused(saved, tmp_path, forgery):
+    """Record sizes are bounded by the bytes left in the file before anything
+    is allocated or hashed: a table whose sizes exceed the file, or wrap
+    around 2^64 back to the true total, is refused even when its checksums
+    have been recomputed to match."""
+    _, path = saved
+    d = bytearray(open(path, "rb").read())
+    nfact = int.from_bytes(d[12:16], "little")
+    units = int.from_bytes(d[28:32], "little")
+    nrec = nfact * units
+    table = d[128:128 + 24 * nrec]
+    assert _file_hash(table) == int.from_bytes(d[56:64], "little")
+    hdr = d[:128]
+    hdr[64:72] = bytes(8)
+    assert _file_hash(hdr) == int.from_bytes(d[64:72], "little")
+
+    recs = [[int.from_bytes(table[24 * r + 8 * j:24 * r + 8 * j + 8], "little") for j in range(3)]
+            for r in range(nrec)]
+    M = (1 << 64) - 1
+    if forgery == "oversized record":
+        recs[0][1] += 1 << 40
+        for r in range(1, nrec):
+            recs[r][0] += 1 << 40
+    else:  # two records of about 2^63 bytes each: the sum wraps to the true total
+        recs[0][1] += 1 << 63
+        recs[1][0] = (recs[1][0] + (1 << 63)) & M
+        recs[1][1] = (recs[1][1] + (1 << 63)) & M
+    for r in range(nrec):
+        for j in range(3):
+            table[24 * r + 8 * j:24 * r + 8 * j + 8] = recs[r][j].to_bytes(8, "little")
+    d[128:128 + 24 * nrec] = table
+    d[56:64] = _file_hash(table).to_bytes(8, "little")
+    hdr = d[:128]
+    hdr[64:72] = bytes(8)
+    d[64:72] = _file_hash(hdr).to_bytes(8, "little")
+    bad = corrupt_copy(path, tmp_path, lambda _: d)
+    with pytest.raises(sht.ShtError) as e:
+        sht.Plan.load(bad, host_only=True)
+    assert e.value.code == CORRUPT
+    assert b"payload ends early" in sht.lib().sht_last_error_detail()
