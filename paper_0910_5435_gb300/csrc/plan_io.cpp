@@ -155,8 +155,13 @@ void read_unit(Reader& r, UnitFact& U, int l) {
   U.cost = r.get<double>();
   r.get_vec(U.D, cap);
   r.get_vec(U.width, 64);
+  // a serialized ID block is at least ten int32 fields and three array
+  // lengths, a final block six int32 fields and one length: counts are bounded
+  // by the bytes left in the record before anything is allocated for them
+  constexpr uint64_t kMinBlockBytes = 10 * sizeof(int32_t) + 3 * sizeof(uint64_t);
+  constexpr uint64_t kMinFinalBytes = 6 * sizeof(int32_t) + sizeof(uint64_t);
   const uint64_t nb = r.get<uint64_t>();
-  if (nb > cap) throw PlanFileError("plan file: implausible block count");
+  if (nb > cap || nb > (r.n - r.at) / kMinBlockBytes) throw PlanFileError("plan file: implausible block count");
   U.blocks.resize(nb);
   for (IdBlock& b : U.blocks) {
     int32_t f[10];
@@ -182,7 +187,7 @@ void read_unit(Reader& r, UnitFact& U, int l) {
       if (s >= b.nin) throw PlanFileError("plan file: redundant index out of range");
   }
   const uint64_t nf = r.get<uint64_t>();
-  if (nf > cap) throw PlanFileError("plan file: implausible final block count");
+  if (nf > cap || nf > (r.n - r.at) / kMinFinalBytes) throw PlanFileError("plan file: implausible final block count");
   U.finals.resize(nf);
   for (FinalBlock& f : U.finals) {
     int32_t g[6];

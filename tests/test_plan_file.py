@@ -185,3 +185,34 @@ def test_forged_unit_table_with_matching_checksums_is_refused(saved, tmp_path, f
         sht.Plan.load(bad, host_only=True)
     assert e.value.code == CORRUPT
     assert b"payload ends early" in sht.lib().sht_last_error_detail()
+
+
+def test_forged_block_count_is_refused_before_allocation(saved, tmp_path):
+    """A unit record claiming more ID blocks than its remaining bytes can hold
+    (each serialized block takes at least 64 bytes) is refused as implausible
+    before the blocks are allocated, even with every checksum recomputed."""
+    _, path = saved
+    d = bytearray(open(path, "rb").read())
+    nrec = int.from_bytes(d[12:16], "little") * int.from_bytes(d[28:32], "little")
+    t0 = 128
+    p0 = t0 + 24 * nrec  # payload start; record 0 is the float64 unit m = 0, p = 0
+    off, nbytes = (int.from_bytes(d[t0 + 8 * j:t0 + 8 * j + 8], "little") for j in range(2))
+    at = p0 + off + 6 * 4 + 4 * 8 + 8  # after m, p, n, rows, direct, levels, four counts, cost
+    nD = int.from_bytes(d[at:at + 8], "little")
+    at += 8 + 8 * nD
+    nw = int.from_bytes(d[at:at + 8], "little")
+    at += 8 + 4 * nw
+    nb = int.from_bytes(d[at:at + 8], "little")
+    assert 0 < nb < 1000  # the unit is a butterfly with a plausible block count
+    left = p0 + off + nbytes - (at + 8)
+    d[at:at + 8] = (left // 64 + 1).to_bytes(8, "little")
+    d[t0 + 16:t0 + 24] = _file_hash(d[p0 + off:p0 + off + nbytes]).to_bytes(8, "little")
+    d[56:64] = _file_hash(d[t0:p0]).to_bytes(8, "little")
+    hdr = d[:128]
+    hdr[64:72] = bytes(8)
+    d[64:72] = _file_hash(hdr).to_bytes(8, "little")
+    bad = corrupt_copy(path, tmp_path, lambda _: d)
+    with pytest.raises(sht.ShtError) as e:
+        sht.Plan.load(bad, host_only=True)
+    assert e.value.code == CORRUPT
+    assert b"implausible block count" in sht.lib().sht_last_error_detail()
