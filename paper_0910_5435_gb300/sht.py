@@ -250,6 +250,10 @@ class Plan:
         _check(lib().sht_plan_save(self.handle, os.fsencode(path)), "sht_plan_save")
 
     def close(self):
+        # batches cached on the plan (differentiable batched synthesis) point
+        # into its device memory: they go first
+        for b in self.__dict__.pop("_autograd_batches", {}).values():
+            b.close()
         if getattr(self, "handle", None):
             lib().sht_plan_destroy(self.handle)
             self.handle = None
@@ -390,6 +394,16 @@ class Batch:
             lib().sht_batch_destroy(self.handle)
             self.handle = None
 
+    def launch_handle(self):
+        """The handle for a launch.  The batch's field table points into its
+        plans' device memory, so a launch after one of them was closed would
+        read freed memory: refused here with SHT_ERR_INVALID_ARG."""
+        if not self.handle:
+            raise ShtError(1, "batch is closed")
+        if any(not p.handle for p in self.plans):
+            raise ShtError(1, "a plan of this batch was closed")
+        return self.handle
+
     def __del__(self):
         try:
             self.close()
@@ -411,17 +425,17 @@ def pointer_array(tensors, device="cuda"):
 
 
 def sht_batch_synthesize(batch, beta_ptrs, G_ptrs, stream=None):
-    _check(lib().sht_batch_synthesize(batch.handle, _ptr(beta_ptrs), _ptr(G_ptrs), _stream(stream)),
+    _check(lib().sht_batch_synthesize(batch.launch_handle(), _ptr(beta_ptrs), _ptr(G_ptrs), _stream(stream)),
            "sht_batch_synthesize")
 
 
 def sht_batch_analyze(batch, G_ptrs, beta_ptrs, stream=None):
-    _check(lib().sht_batch_analyze(batch.handle, _ptr(G_ptrs), _ptr(beta_ptrs), _stream(stream)),
+    _check(lib().sht_batch_analyze(batch.launch_handle(), _ptr(G_ptrs), _ptr(beta_ptrs), _stream(stream)),
            "sht_batch_analyze")
 
 
 def sht_batch_synthesize_adjoint(batch, G_ptrs, beta_ptrs, stream=None):
-    _check(lib().sht_batch_synthesize_adjoint(batch.handle, _ptr(G_ptrs), _ptr(beta_ptrs), _stream(stream)),
+    _check(lib().sht_batch_synthesize_adjoint(batch.launch_handle(), _ptr(G_ptrs), _ptr(beta_ptrs), _stream(stream)),
            "sht_batch_synthesize_adjoint")
 
 
@@ -458,14 +472,14 @@ def host_pointer_array(tensors):
 
 def sht_batch_synthesize_grid(batch, betas, values, workspaces, stream=None):
     """Full synthesis of every field (lists of device tensors, one per field)."""
-    _check(lib().sht_batch_synthesize_grid(batch.handle, host_pointer_array(betas), host_pointer_array(values),
+    _check(lib().sht_batch_synthesize_grid(batch.launch_handle(), host_pointer_array(betas), host_pointer_array(values),
                                            host_pointer_array(workspaces), _stream(stream)),
            "sht_batch_synthesize_grid")
 
 
 def sht_batch_analyze_grid(batch, values, betas, workspaces, stream=None):
     """Full analysis of every field (lists of device tensors, one per field)."""
-    _check(lib().sht_batch_analyze_grid(batch.handle, host_pointer_array(values), host_pointer_array(betas),
+    _check(lib().sht_batch_analyze_grid(batch.launch_handle(), host_pointer_array(values), host_pointer_array(betas),
                                         host_pointer_array(workspaces), _stream(stream)),
            "sht_batch_analyze_grid")
 
@@ -475,7 +489,7 @@ def sht_batch_last_device_status(batch, stream=None):
 
 
 def sht_batch_autotune(batch, direction, in_ptrs, out_ptrs, reps=3, stream=None):
-    _check(lib().sht_batch_autotune(batch.handle, int(direction), _ptr(in_ptrs), _ptr(out_ptrs), int(reps),
+    _check(lib().sht_batch_autotune(batch.launch_handle(), int(direction), _ptr(in_ptrs), _ptr(out_ptrs), int(reps),
                                     _stream(stream)), "sht_batch_autotune")
     return batch.config(direction)
 
