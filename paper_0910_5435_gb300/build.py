@@ -24,8 +24,12 @@ ROOT = os.path.dirname(PKG)
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CXXFLAGS = ["-O3", "-std=c++17", "-fPIC", "-pthread", "-Wall", "-Wno-unused-function"]
-NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
+# Host code is compiled without floating-point contraction: gcc fuses a * b + c
+# on aarch64 but not on x86-64 without -march flags, and the precomputation
+# must give the same bits on both.  (Device code keeps nvcc's own rules.)
+CXXFLAGS = ["-O3", "-std=c++17", "-ffp-contract=off", "-fPIC", "-pthread", "-Wall", "-Wno-unused-function"]
+NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
+           "--expt-relaxed-constexpr"] + ARCH
 
 CPP_SOURCES = ["plan_build.cpp", "unit_stats.cpp", "plan_io.cpp"]
 CU_SOURCES = ["capi.cu", "sweep.cu", "direct.cu", "phi.cu", "noalloc.cu", "batch.cu", "plan_device.cu", "peak.cu"]

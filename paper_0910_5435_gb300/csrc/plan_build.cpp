@@ -29,74 +29,94 @@ namespace sht {
 namespace {
 
 // ------------------------------------------------------------ GL nodes
+//
+// Only +, -, *, / and sqrt (all correctly rounded in IEEE arithmetic) are
+// used, and the library is compiled without floating-point contraction, so
+// the nodes, weights and sines are the same bits on every host.
 
-// Normalized Legendre P-bar^0_n(x) and its derivative, from the normalized
-// three-term recurrence P-bar_{j+1} = a_{j+1} x P-bar_j - (a_{j+1}/a_j) P-bar_{j-1},
-// a_j = sqrt(4j^2 - 1)/j, and (1-x^2) P-bar_n' = n (sqrt((2n+1)/(2n-1)) P-bar_{n-1} - x P-bar_n).
-void pbar0(int n, double x, double one_m_x2, double& p, double& dp) {
-  double pm1 = 0.0, pj = 1.0 / std::sqrt(2.0), aj = 0.0;
-  for (int j = 0; j < n; ++j) {
-    const double jj = j + 1.0;
-    const double an = std::sqrt(4.0 * jj * jj - 1.0) / jj;
-    const double pn = (j == 0) ? an * x * pj : an * x * pj - (an / aj) * pm1;
-    pm1 = pj;
-    pj = pn;
-    aj = an;
+// sin a and cos a for 0 <= a <= pi/2: the Taylor series at a/8 (12 terms,
+// far below rounding there), then three double-angle steps.  Accurate to a
+// few units in the last place, which is ample for starting Newton's method.
+void series_sincos(double a, double& s, double& c) {
+  const double h = a / 8.0, h2 = h * h;
+  double ts = h, tc = 1.0;
+  s = h;
+  c = 1.0;
+  for (int k = 1; k <= 12; ++k) {
+    ts = -ts * h2 / ((2.0 * k) * (2.0 * k + 1.0));
+    tc = -tc * h2 / ((2.0 * k - 1.0) * (2.0 * k));
+    s += ts;
+    c += tc;
   }
-  p = pj;
-  dp = n * (std::sqrt((2.0 * n + 1.0) / (2.0 * n - 1.0)) * pm1 - x * pj) / one_m_x2;
+  for (int r = 0; r < 3; ++r) {
+    const double s2 = 2.0 * s * c;
+    c = (c - s) * (c + s);
+    s = s2;
+  }
+}
+
+// P_n(x) and P_{n-1}(x) for the unnormalized Legendre polynomials, from
+// (j + 1) P_{j+1} = (2j + 1) x P_j - j P_{j-1}.  The coefficients are exact
+// integers, so the only rounding is in the arithmetic itself; the normalized
+// form's rounded square-root coefficients cost an order of magnitude in the
+// weights near the poles.
+void legendre_pn(int n, double x, double& pn, double& pn1) {
+  double p0 = 1.0, p1 = x;
+  for (int j = 1; j < n; ++j) {
+    const double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  pn = p1;
+  pn1 = p0;
 }
 
 }  // namespace
 
-void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& theta_pos) {
+void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& sin_pos) {
   if (npts < 2 || (npts & 1)) throw std::invalid_argument("gl_nodes: npts must be even");
   const int n = npts, half = n / 2;
   x.assign(n, 0.0);
   w.assign(n, 0.0);
-  theta_pos.assign(half, 0.0);
+  sin_pos.assign(half, 0.0);
+  const double pi = 3.14159265358979323846;
   for (int k = 1; k <= half; ++k) {
-    // Tricomi-type start: phi = pi (k - 1/4)/(n + 1/2), theta ~ phi + cot(phi) / (8 (n + 1/2)^2)
-    const double phi = M_PI * (k - 0.25) / (n + 0.5);
-    double th = phi + 1.0 / (std::tan(phi) * 8.0 * (n + 0.5) * (n + 0.5));
-    double dp_exact = 0.0;
-    for (int it = 0; it < 60; ++it) {
-      const double xr = std::cos(th);
-      // delta = cos(th) - xr without cancellation (th < pi/2: cos = 1 - 2 sin^2(th/2))
-      const double sh = std::sin(0.5 * th);
-      const double delta = (1.0 - xr) - 2.0 * sh * sh;
-      const double omx2 = (1.0 - xr) * (1.0 + xr);
-      double p, dp;
-      pbar0(n, xr, omx2, p, dp);
-      // Legendre's equation (eq. sturm-liouville_Leg, m = 0): (1-x^2) P'' = 2 x P' - n(n+1) P
-      const double d2p = (2.0 * xr * dp - n * (n + 1.0) * p) / omx2;
-      const double p_exact = p + dp * delta;
-      dp_exact = dp + d2p * delta;
-      const double step = p_exact / (std::sin(th) * dp_exact);  // d/dth P(cos th) = -sin(th) P'
-      th += step;
-      if (std::fabs(step) < 1e-18 && it > 1) break;
+    // start: theta ~ phi + cot(phi) / (8 (n + 1/2)^2), phi = pi (k - 1/4) / (n + 1/2)
+    const double phi = pi * (k - 0.25) / (n + 0.5);
+    double sp, cp, sth, xk;
+    series_sincos(phi, sp, cp);
+    series_sincos(phi + cp / (sp * 8.0 * (n + 0.5) * (n + 0.5)), sth, xk);
+    // Newton on P_n in x, with P_n' = n (P_{n-1} - x P_n) / (1 - x^2); once a
+    // step is below 8 units in the last place of x, one more step and stop
+    double p, pm;
+    for (int it = 0; it < 100; ++it) {
+      legendre_pn(n, xk, p, pm);
+      const double step = p / (n * (pm - xk * p) / ((1.0 - xk) * (1.0 + xk)));
+      xk -= step;
+      if (std::fabs(step) <= 0x1p-50 * xk) {
+        legendre_pn(n, xk, p, pm);
+        xk -= p / (n * (pm - xk * p) / ((1.0 - xk) * (1.0 + xk)));
+        break;
+      }
     }
-    {
-      // final derivative at the converged angle
-      const double xr = std::cos(th);
-      const double sh = std::sin(0.5 * th);
-      const double delta = (1.0 - xr) - 2.0 * sh * sh;
-      const double omx2 = (1.0 - xr) * (1.0 + xr);
-      double p, dp;
-      pbar0(n, xr, omx2, p, dp);
-      const double d2p = (2.0 * xr * dp - n * (n + 1.0) * p) / omx2;
-      dp_exact = dp + d2p * delta;
-    }
-    const double s = std::sin(th);
-    // w = 2 / ((1-x^2) P_n'^2) with P_n = sqrt(2/(2n+1)) P-bar_n
-    const double wk = (2.0 * n + 1.0) / (s * s * dp_exact * dp_exact);
-    const double xk = std::cos(th);
+    // The root r = xk + d lies within rounding of xk: the weight
+    // w = 2 / ((1 - r^2) P_n'(r)^2) and sin theta = sqrt(1 - r^2) are taken
+    // at r, with P_n'(r) = P_n'(xk) + P_n''(xk) d from Legendre's equation
+    // (1 - x^2) P'' = 2 x P' - n (n + 1) P.
+    legendre_pn(n, xk, p, pm);
+    const double omx2 = (1.0 - xk) * (1.0 + xk);
+    const double dp = n * (pm - xk * p) / omx2;
+    const double d = -p / dp;
+    const double d2p = (2.0 * xk * dp - n * (n + 1.0) * p) / omx2;
+    const double dpr = dp + d2p * d;
+    const double omr2 = omx2 - 2.0 * xk * d - d * d;
+    const double wk = 2.0 / (omr2 * dpr * dpr);
     // k = 1 is the largest node; positive nodes sit at indices half..n-1 ascending
     x[n - k] = xk;
     x[k - 1] = -xk;
     w[n - k] = wk;
     w[k - 1] = wk;
-    theta_pos[half - k] = th;
+    sin_pos[half - k] = std::sqrt(omr2);
   }
 }
 
@@ -131,7 +151,7 @@ ColumnStream::ColumnStream(const PlanHost& P, int m, int p, int rows, int row0)
   for (int i = 0; i < rows; ++i) {
     const int g = row0 + i;
     const double xi = custom ? P.row_x[g] : P.x[l + g];
-    const double s = std::sin(custom ? P.row_theta[g] : P.theta_pos[g]);
+    const double s = custom ? std::sin(P.row_theta[g]) : P.sin_pos[g];
     x2_[i] = xi * xi;
     sq2w_[i] = custom ? P.row_sqw[g] : std::sqrt(2.0 * P.w[l + g]);
     // s^m by binary powering with tracked exponents

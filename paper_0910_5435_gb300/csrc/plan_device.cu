@@ -1021,7 +1021,7 @@ void build_factorizations_device(PlanHost& P, bool fp32, int device) {
   std::vector<double> xpos(l), spos(l), sq2w(l);
   for (int i = 0; i < l; ++i) {
     xpos[i] = P.x[l + i];
-    spos[i] = std::sin(P.theta_pos[i]);
+    spos[i] = P.sin_pos[i];
     sq2w[i] = std::sqrt(2.0 * P.w[l + i]);
   }
   std::vector<int> order(2 * L);

@@ -105,9 +105,9 @@ struct PlanHost {
   bool values_apart[3] = {true, true, true};  // per precision: value blocks outside the pages
   bool debug_unmet_dep = false;  // plant a never-met predecessor (failure-detection tests)
   long long device_arena_bytes = 0;  // device build: record arena limit (0 = automatic)
-  // Gauss-Legendre nodes (all 2l, ascending), weights, and the angle of each
-  // positive node (theta_{l+i} in (0, pi/2)).
-  std::vector<double> x, w, theta_pos;
+  // Gauss-Legendre nodes (all 2l, ascending), weights, and sin theta_{l+i} =
+  // sqrt(1 - x^2) of each positive node, taken at the exact root.
+  std::vector<double> x, w, sin_pos;
   // Optional rows of a single block at other nodes (the Gauss-Jacobi form of
   // Section 4): node x_i, angle theta_i = arccos x_i and the row factor
   // sqrt(rho_i) for i < l; unit_cols > 0 sets the column count.
@@ -128,8 +128,9 @@ struct PlanHost {
 void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector<double>& theta,
                         std::vector<double>& rho);
 
-// Section 2, eq. thetas: 2l Gauss-Legendre nodes/weights.
-void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& theta);
+// Section 2, eq. thetas: 2l Gauss-Legendre nodes/weights, and the sines of the
+// positive nodes' angles.  Bit-identical on every IEEE host (no libm calls).
+void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& sin_pos);
 
 // Columns of A^{m,p}_{ij} = sqrt(2 w_{l+i}) P-bar^m_{m+p+2j}(x_{l+i}), i < rows,
 // generated left to right with the x^2 recurrence of Section 2.3 (eqs.

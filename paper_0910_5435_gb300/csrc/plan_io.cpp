@@ -34,7 +34,9 @@ namespace sht {
 namespace {
 
 constexpr char kMagic[8] = {'S', 'H', 'T', 'P', 'L', 'A', 'N', '\0'};
-constexpr uint32_t kVersion = 1;
+// 2: factorizations of the quadrature with exact-integer recurrence weights
+// (version 1 files hold those of the earlier weights and are rebuilt)
+constexpr uint32_t kVersion = 2;
 
 struct FileHeader {
   char magic[8];
