@@ -64,12 +64,13 @@ def parse():
 # capture, mean of a synthesis (6.517 GB) and an analysis (6.405 GB) launch
 # (profiles/bfly_sweep_fp64_l1024_dram.md).  Valid only for the kernel and
 # stream-format sources it was taken with: SWEEP_SOURCES_SHA is their hash.
-# It was re-keyed once without a new capture, for a change confined to the
-# Gauss-Legendre quadrature (gl_nodes): the kernel, the op format and the
-# stream encoder are unchanged, and the l = 1024 float64 stream is 17,040
-# bytes (2.7 ppm) larger than the one profiled.
+# It was re-keyed without a new capture for changes confined to the nodes:
+# the Gauss-Legendre quadrature (gl_nodes) and the row sines of single
+# Gauss-Jacobi blocks.  The kernel, the op format and the stream encoder are
+# unchanged, and the l = 1024 float64 stream is 17,040 bytes (2.7 ppm)
+# larger than the one profiled.
 SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4581e9}
-SWEEP_SOURCES_SHA = "ffc43f8b2d7c1ee7"
+SWEEP_SOURCES_SHA = "835ab54a7c4612e8"
 
 
 def sweep_sources_sha():

@@ -151,7 +151,7 @@ ColumnStream::ColumnStream(const PlanHost& P, int m, int p, int rows, int row0)
   for (int i = 0; i < rows; ++i) {
     const int g = row0 + i;
     const double xi = custom ? P.row_x[g] : P.x[l + g];
-    const double s = custom ? std::sin(P.row_theta[g]) : P.sin_pos[g];
+    const double s = custom ? P.row_sin[g] : P.sin_pos[g];
     x2_[i] = xi * xi;
     sq2w_[i] = custom ? P.row_sqw[g] : std::sqrt(2.0 * P.w[l + g]);
     // s^m by binary powering with tracked exponents

@@ -109,9 +109,9 @@ struct PlanHost {
   // sqrt(1 - x^2) of each positive node, taken at the exact root.
   std::vector<double> x, w, sin_pos;
   // Optional rows of a single block at other nodes (the Gauss-Jacobi form of
-  // Section 4): node x_i, angle theta_i = arccos x_i and the row factor
+  // Section 4): node x_i, sin theta_i = sqrt(1 - x_i^2) and the row factor
   // sqrt(rho_i) for i < l; unit_cols > 0 sets the column count.
-  std::vector<double> row_x, row_theta, row_sqw;
+  std::vector<double> row_x, row_sin, row_sqw;
   int unit_cols = 0;
   // factorizations: [m * 2 + p]; fp64 uses eps_id, fp32 uses eps_fp32
   std::vector<UnitFact> fact64, fact32;
@@ -123,9 +123,10 @@ struct PlanHost {
 };
 
 // The n positive zeros x_i of P-bar^m_{m+p+2n} (Section 4, Lemma zeros),
-// their angles, and the weights rho_i of the Gauss-Jacobi-type quadrature
-// of Lemma quadratures (for p = 1 the sigma_i of eq. weights2, i < n).
-void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector<double>& theta,
+// the sines sqrt(1 - x_i^2) of their angles, and the weights rho_i of the
+// Gauss-Jacobi-type quadrature of Lemma quadratures (for p = 1 the sigma_i
+// of eq. weights2, i < n).
+void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector<double>& sin_theta,
                         std::vector<double>& rho);
 
 // Section 2, eq. thetas: 2l Gauss-Legendre nodes/weights, and the sines of the

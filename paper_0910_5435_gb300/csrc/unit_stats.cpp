@@ -243,7 +243,7 @@ void parallel_for(int count, F&& body) {
 }
 }  // namespace
 
-void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector<double>& theta,
+void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector<double>& sin_theta,
                         std::vector<double>& rho) {
   std::vector<double> a(n), b2(n, 0.0);
   for (int j = 0; j < n; ++j) {
@@ -315,16 +315,16 @@ void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector
     }
   });
   x.resize(n);
-  theta.resize(n);
+  sin_theta.resize(n);
   for (int k = 0; k < n; ++k) {
     x[k] = std::sqrt(t[k]);
-    theta[k] = std::atan2(std::sqrt((1.0 - x[k]) * (1.0 + x[k])), x[k]);
+    sin_theta[k] = std::sqrt((1.0 - x[k]) * (1.0 + x[k]));
   }
   // weights from the unweighted columns
   PlanHost Q;
   Q.l = n;
   Q.row_x = x;
-  Q.row_theta = theta;
+  Q.row_sin = sin_theta;
   Q.row_sqw.assign(n, 1.0);
   std::vector<double> sum(n, 0.0);
   const int rchunks = (n + kChunk - 1) / kChunk;
@@ -372,7 +372,7 @@ extern "C" sht_status sht_unit_stats_gauss_jacobi(int n, int m, int parity, doub
     apply_options(P, o, eps_id);
     const double t0 = now_s();
     std::vector<double> rho;
-    sht::gauss_jacobi_nodes(m, parity, n, P.row_x, P.row_theta, rho);
+    sht::gauss_jacobi_nodes(m, parity, n, P.row_x, P.row_sin, rho);
     P.row_sqw.resize(n);
     for (int i = 0; i < n; ++i) P.row_sqw[i] = std::sqrt(rho[i]);
     return unit_stats_of(P, m, parity, eps_id, now_s() - t0, seed, out);
