@@ -80,7 +80,8 @@ void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vec
   w.assign(n, 0.0);
   sin_pos.assign(half, 0.0);
   const double pi = 3.14159265358979323846;
-  for (int k = 1; k <= half; ++k) {
+  // each node is computed on its own, so the thread count cannot change a bit
+  auto one_node = [&](int k) {
     // start: theta ~ phi + cot(phi) / (8 (n + 1/2)^2), phi = pi (k - 1/4) / (n + 1/2)
     const double phi = pi * (k - 0.25) / (n + 0.5);
     double sp, cp, sth, xk;
@@ -117,7 +118,19 @@ void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vec
     w[n - k] = wk;
     w[k - 1] = wk;
     sin_pos[half - k] = std::sqrt(omr2);
-  }
+  };
+  constexpr int kChunk = 16;
+  const int nchunks = (half + kChunk - 1) / kChunk;
+  const int nt = std::max(1, std::min({(int)std::thread::hardware_concurrency(), nchunks, 64}));
+  std::atomic<int> next(0);
+  auto worker = [&]() {
+    for (int c; (c = next.fetch_add(1)) < nchunks;)
+      for (int k = 1 + c * kChunk; k <= std::min(half, (c + 1) * kChunk); ++k) one_node(k);
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(worker);
+  worker();
+  for (auto& t : th) t.join();
 }
 
 // ------------------------------------------------------- column stream
