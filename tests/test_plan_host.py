@@ -205,3 +205,22 @@ def test_debug_unmet_dependency_plants_one_self_wait():
                     assert OP_SYN <= int(h["kind"]) <= OP_ANA
                     n += 1
             assert n == expected, (debug, d, n)
+
+
+def test_plans_do_not_depend_on_the_thread_count():
+    """Nodes, weights and the float64 and float32 streams of both directions
+    are the same bytes whether the precomputation runs on one host thread, on
+    three, or on all of them: every unit and node is computed on its own and
+    the streams are laid out in a fixed order."""
+    plans = [sht.Plan(128, 1e-12, leaf_cols=16, host_only=True, num_threads=t) for t in (1, 3, 0)]
+    ref = plans[0]
+    x0, w0 = ref.nodes()
+    for P in plans[1:]:
+        x, w = P.nodes()
+        assert np.array_equal(x, x0) and np.array_equal(w, w0)
+        for prec in (0, 1):
+            for d in (0, 1):
+                for a, b in zip(P.stream(prec, d), ref.stream(prec, d)):
+                    assert np.array_equal(a, b), (prec, d)
+    for P in plans:
+        P.close()
