@@ -70,7 +70,7 @@ def parse():
 # unchanged, and the l = 1024 float64 stream is 17,040 bytes (2.7 ppm)
 # larger than the one profiled.
 SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4581e9}
-SWEEP_SOURCES_SHA = "7e4453e89ac178f5"
+SWEEP_SOURCES_SHA = "f40ffdc2b0b6a0f3"
 
 
 def sweep_sources_sha():

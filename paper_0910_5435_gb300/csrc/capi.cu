@@ -643,7 +643,7 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
   }
   try {
     const double t0 = now_s();
-    sht::gl_nodes(2 * l, H.x, H.w, H.sin_pos);
+    sht::gl_nodes(2 * l, H.x, H.w, H.sin_pos, H.num_threads);
     H.t_quad = now_s() - t0;
   } catch (...) {
     delete P;

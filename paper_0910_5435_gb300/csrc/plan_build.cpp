@@ -73,7 +73,8 @@ void legendre_pn(int n, double x, double& pn, double& pn1) {
 
 }  // namespace
 
-void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& sin_pos) {
+void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& sin_pos,
+              int threads) {
   if (npts < 2 || (npts & 1)) throw std::invalid_argument("gl_nodes: npts must be even");
   const int n = npts, half = n / 2;
   x.assign(n, 0.0);
@@ -121,7 +122,8 @@ void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vec
   };
   constexpr int kChunk = 16;
   const int nchunks = (half + kChunk - 1) / kChunk;
-  const int nt = std::max(1, std::min({(int)std::thread::hardware_concurrency(), nchunks, 64}));
+  const int avail = threads > 0 ? threads : (int)std::thread::hardware_concurrency();
+  const int nt = std::max(1, std::min({avail, nchunks, 64}));
   std::atomic<int> next(0);
   auto worker = [&]() {
     for (int c; (c = next.fetch_add(1)) < nchunks;)

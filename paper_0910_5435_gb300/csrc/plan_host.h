@@ -131,7 +131,9 @@ void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector
 
 // Section 2, eq. thetas: 2l Gauss-Legendre nodes/weights, and the sines of the
 // positive nodes' angles.  Bit-identical on every IEEE host (no libm calls).
-void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& sin_pos);
+// threads: host threads to use (0 = all hardware threads).
+void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& sin_pos,
+              int threads = 0);
 
 // Columns of A^{m,p}_{ij} = sqrt(2 w_{l+i}) P-bar^m_{m+p+2j}(x_{l+i}), i < rows,
 // generated left to right with the x^2 recurrence of Section 2.3 (eqs.

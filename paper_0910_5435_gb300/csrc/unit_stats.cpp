@@ -394,7 +394,7 @@ extern "C" sht_status sht_unit_stats_compute(int l, int m, int parity, double ep
     P.l = l;
     apply_options(P, o, eps_id);
     const double t0 = now_s();
-    sht::gl_nodes(2 * l, P.x, P.w, P.sin_pos);
+    sht::gl_nodes(2 * l, P.x, P.w, P.sin_pos, P.num_threads);
     return unit_stats_of(P, m, parity, eps_id, now_s() - t0, seed, out);
   } catch (const std::bad_alloc&) {
     return SHT_ERR_OOM;
