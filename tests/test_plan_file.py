@@ -216,3 +216,24 @@ def test_forged_block_count_is_refused_before_allocation(saved, tmp_path):
         sht.Plan.load(bad, host_only=True)
     assert e.value.code == CORRUPT
     assert b"implausible block count" in sht.lib().sht_last_error_detail()
+
+
+def test_version_1_files_are_refused_and_rebuilt_as_a_cache(tmp_path):
+    """Files of format version 1 hold factorizations of the earlier quadrature
+    weights: with a valid header checksum they are still refused, and given as
+    a plan_cache they are rebuilt and rewritten at the current version."""
+    cache = str(tmp_path / "v1.plan")
+    a = sht.Plan(16, 1e-12, leaf_cols=4, host_only=True, plan_cache=cache)
+    d = bytearray(open(cache, "rb").read())
+    assert int.from_bytes(d[8:12], "little") == 2
+    d[8:12] = (1).to_bytes(4, "little")
+    hdr = d[:128]
+    hdr[64:72] = bytes(8)
+    d[64:72] = _file_hash(hdr).to_bytes(8, "little")
+    open(cache, "wb").write(bytes(d))
+    with pytest.raises(sht.ShtError) as e:
+        sht.Plan.load(cache, host_only=True)
+    assert e.value.code == CORRUPT and b"version" in sht.lib().sht_last_error_detail()
+    b = sht.Plan(16, 1e-12, leaf_cols=4, host_only=True, plan_cache=cache)
+    assert b.stats()["t_factor"] > 0 and same_streams(a, b)
+    assert int.from_bytes(open(cache, "rb").read()[8:12], "little") == 2
