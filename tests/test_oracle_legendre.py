@@ -3,10 +3,11 @@ library routines that share no arithmetic with the oracle's recurrence."""
 
 import math
 
-import mpmath
 import numpy as np
 import pytest
 from scipy import special
+
+mpmath = pytest.importorskip("mpmath")
 
 import oracle
 from tests._exact import pbar_exact
