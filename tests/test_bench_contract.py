@@ -47,3 +47,25 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_oracle_leg_scores_outputs_against_the_oracle(tmp_path):
+    """The CPU leg that times the oracle also scores a path's outputs: given
+    the oracle's own synthesis and analysis as that path's outputs, both
+    errors are at rounding level, and the timing sample has one order per
+    stride."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    import oracle
+    from paper_0910_5435_gb300 import inputs
+    l = 16
+    beta = inputs.random_beta(l, seed=3, decay=True)
+    G = oracle.legendre_synthesis(beta, l)
+    path = str(tmp_path / "outs.npz")
+    np.savez(path, fp64_G=G, fp64_beta=oracle.legendre_analysis(G, l))
+    res = bench.cpu_oracle_leg(l, 4, 3, path, err_stride=3)
+    assert res["orders"] == 2 * l // 4
+    assert res["rel_synth_fp64"] < 1e-15 and res["rel_analysis_fp64"] < 1e-15
+    assert res["t_full_est"] > 0
