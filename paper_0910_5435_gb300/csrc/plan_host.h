@@ -130,7 +130,8 @@ void gauss_jacobi_nodes(int m, int p, int n, std::vector<double>& x, std::vector
                         std::vector<double>& rho);
 
 // Section 2, eq. thetas: 2l Gauss-Legendre nodes/weights, and the sines of the
-// positive nodes' angles.  Bit-identical on every IEEE host (no libm calls).
+// positive nodes' angles.  No libm calls: built without floating-point
+// contraction (build.py), the results are the same bits on every IEEE host.
 // threads: host threads to use (0 = all hardware threads).
 void gl_nodes(int npts, std::vector<double>& x, std::vector<double>& w, std::vector<double>& sin_pos,
               int threads = 0);
