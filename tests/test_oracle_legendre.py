@@ -2,15 +2,19 @@
 library routines that share no arithmetic with the oracle's recurrence."""
 
 import math
+from decimal import Decimal
 
 import numpy as np
 import pytest
 from scipy import special
 
-mpmath = pytest.importorskip("mpmath")
-
 import oracle
-from tests._exact import pbar_exact
+from tests._exact import diagonal_exact, pbar_exact
+
+try:  # a library routine used as one pin; the test fails (not skips) without it
+    import mpmath
+except ImportError:  # pragma: no cover
+    mpmath = None
 
 XS = np.array([-0.97, -0.61, -0.2, 0.0, 0.13, 0.5, 0.77, 0.999])
 
@@ -43,6 +47,7 @@ def test_high_degree_against_mpmath(k, m):
     """Library routine (mpmath Ferrers function, arbitrary precision) with the
     Condon-Shortley sign removed and the eq. association normalization, at
     points where its hypergeometric evaluation converges quickly."""
+    assert mpmath is not None, "this pin needs mpmath (pip package 'mpmath')"
     mpmath.mp.dps = 40
     pts = np.array([-0.8, -0.3, 0.3, 0.6, 0.9])
     got = oracle.legendre_table(m, pts, k)[-1]
@@ -56,19 +61,15 @@ def test_high_degree_against_mpmath(k, m):
 def test_diagonal_closed_form_through_underflow(m):
     """eq. association at l = m: d^m/dx^m P_m = (2m)!/(2^m m!), so
     P-bar^m_m(x) = sqrt((2m+1)/2) sqrt((2m)!)/(2^m m!) (1-x^2)^{m/2}, evaluated
-    in 50-digit arithmetic at the l = 1024 Gauss-Legendre nodes.  Values below
+    in 50-digit decimal arithmetic at the l = 1024 Gauss-Legendre nodes.  Values below
     the float64 range must come out (near) zero; representable ones to
     (m + 10) * 4e-16 relative, which exercises the exponent tracking of Section 4."""
-    mpmath.mp.dps = 50
     x, _ = oracle.gl_nodes_weights(2048)
     pts = x[::37]
     got = oracle.legendre_table(m, pts, m)[0]
-    c = mpmath.sqrt(mpmath.mpf(2 * m + 1) / 2) * mpmath.sqrt(mpmath.factorial(2 * m)) / (
-        mpmath.mpf(2) ** m * mpmath.factorial(m))
     for xv, g in zip(pts, got):
-        xm = mpmath.mpf(xv)
-        ref = c * ((1 - xm) * (1 + xm)) ** (mpmath.mpf(m) / 2)
-        if ref > mpmath.mpf("1e-290"):
+        ref = diagonal_exact(m, float(xv))
+        if ref > Decimal("1e-290"):
             # sqrt(1-x^2) carries ~1 ulp, amplified m times by the m-th power
             assert abs(g - float(ref)) <= 4e-16 * (m + 10) * float(ref), (m, xv, g, ref)
         else:

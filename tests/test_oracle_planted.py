@@ -13,9 +13,9 @@ import oracle
 import oracle.legendre as OL
 import oracle.sht as OS
 
-TL = pytest.importorskip("tests.test_oracle_legendre")
-TQ = pytest.importorskip("tests.test_oracle_quadrature")
-TS = pytest.importorskip("tests.test_oracle_sht")
+import tests.test_oracle_legendre as TL
+import tests.test_oracle_quadrature as TQ
+import tests.test_oracle_sht as TS
 
 PINS = [
     ("closed forms", lambda: TL.test_closed_forms()),

@@ -8,6 +8,7 @@ import pytest
 from scipy import special
 
 import oracle
+from tests._exact import gl_root_and_weight
 
 
 @pytest.mark.parametrize("npts", [1, 2, 3, 4, 8, 17, 64])
@@ -26,25 +27,10 @@ def test_nodes_and_weights_in_extended_precision(npts):
     Newton on P_n from the oracle's node, then w = 2/((1-x^2) P_n'(x)^2) at the
     refined root.  Nodes to ~1 ulp; weights to n * 2e-15 relative (the degree
     recurrence's roundoff near the poles bounds the double-precision angle)."""
-    import mpmath
-    mpmath.mp.dps = 40
     xo, wo = oracle.gl_nodes_weights(npts)
     n = npts
-
-    def pp(x):
-        p0, p1 = mpmath.mpf(1), x
-        for j in range(1, n):
-            p0, p1 = p1, ((2 * j + 1) * x * p1 - j * p0) / (j + 1)
-        return p1, p0
-
     for i in sorted({0, 1, 7, n // 3, n // 2, n - 2, n - 1}):
-        x = mpmath.mpf(xo[i])
-        for _ in range(4):
-            pn, pn1 = pp(x)
-            x = x - pn / (n * (x * pn - pn1) / (x * x - 1))
-        pn, pn1 = pp(x)
-        dp = n * (x * pn - pn1) / (x * x - 1)
-        w = 2 / ((1 - x * x) * dp * dp)
+        x, w = gl_root_and_weight(n, float(xo[i]), digits=40, steps=4)
         assert abs(xo[i] - float(x)) <= 1.2e-16
         assert abs(wo[i] / float(w) - 1) <= 2e-15 * n, (i, wo[i], float(w))
 

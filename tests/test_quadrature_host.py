@@ -8,32 +8,13 @@ import numpy as np
 import pytest
 
 from paper_0910_5435_gb300 import sht
-
-mpmath = pytest.importorskip("mpmath")
+from tests._exact import gl_root_and_weight
 
 
 @pytest.fixture(scope="module", autouse=True)
 def _built():
     import __graft_entry__
     __graft_entry__.build()
-
-
-def _root_and_weight(n, x0):
-    mpmath.mp.dps = 40
-
-    def pp(x):
-        p0, p1 = mpmath.mpf(1), x
-        for j in range(1, n):
-            p0, p1 = p1, ((2 * j + 1) * x * p1 - j * p0) / (j + 1)
-        return p1, p0
-
-    x = mpmath.mpf(x0)
-    for _ in range(5):
-        a, b = pp(x)
-        x = x - a / (n * (x * a - b) / (x * x - 1))
-    a, b = pp(x)
-    dp = n * (x * a - b) / (x * x - 1)
-    return x, 2 / ((1 - x * x) * dp * dp)
 
 
 @pytest.mark.parametrize("l", [4, 64, 1024])
@@ -50,7 +31,7 @@ def test_nodes_and_weights_against_extended_precision(l):
     assert np.all(np.diff(x) > 0) and np.array_equal(x, -x[::-1]) and np.array_equal(w, w[::-1])
     sample = sorted({0, 1, 2, 3, 4, 5, 9, 15, 16, 40, n // 5, n // 3, l - 2, l - 1} & set(range(l)))
     for i in sample:
-        r, wr = _root_and_weight(n, x[i])
+        r, wr = gl_root_and_weight(n, float(x[i]), digits=40, steps=5)
         assert abs(x[i] - float(r)) <= 2 * np.spacing(abs(x[i])), (i, x[i], float(r))
         bound = (1.5e-15 if i < 16 else 1e-16) * n
         assert abs(w[i] / float(wr) - 1) <= bound, (i, w[i], float(wr))
