@@ -203,7 +203,7 @@ typedef struct {
                           * the reflector, plus k^2 (w - k) for T = R11^{-1} R12 */
   long long id_swaps;    /* skeleton/redundant exchanges of the strong rank-revealing step
                           * (Remark QR_algorithm: coefficients at most 2), float64 IDs */
-} sht_plan_stats;
+} sht_plan_stats_t;
 
 /* Fills *opts with the defaults listed above. */
 sht_status sht_plan_opts_default(sht_plan_opts* opts);
@@ -225,8 +225,12 @@ sht_status sht_plan_create_ex(int l, double eps_id, const sht_plan_opts* opts, s
  * ensure no work using the plan is still in flight. */
 sht_status sht_plan_destroy(sht_plan_t plan);
 
-/* Copies the plan statistics into *out. */
-sht_status sht_plan_get_stats(sht_plan_t plan, sht_plan_stats* out);
+/* Copies the plan statistics into *out: the rank statistics, costs and
+ * errors the paper tabulates (Section 5, k_max, k_avg, k_sigma, t_quad,
+ * t_comp, m_max) plus the stream sizes of every precision.
+ * sht_plan_stats is the same call under its shorter name. */
+sht_status sht_plan_get_stats(sht_plan_t plan, sht_plan_stats_t* out);
+sht_status sht_plan_stats(sht_plan_t plan, sht_plan_stats_t* out);
 
 /* Builds (host) and uploads (device) the factor streams of one precision.
  * Synchronous.  Idempotent. */
@@ -536,6 +540,27 @@ sht_status sht_batch_autotune(sht_batch_t batch, int direction, const void* cons
 sht_status sht_batch_get_config(sht_batch_t batch, int direction, int* consumer_warps, int* nstages,
                                 int* ctas_per_sm, int* smem_bytes);
 
+/* The batched spellings of the full transform (one call per batch of
+ * fields, no batch object kept by the caller).  Each call builds a batch of
+ * plans[0..nfields) (as sht_batch_create), runs it through one persistent
+ * launch of every field's Legendre stage plus each field's FFTs (as
+ * sht_batch_synthesize_grid / sht_batch_analyze_grid), waits for stream and
+ * frees the batch: SYNCHRONOUS on stream, and it allocates (the batch's
+ * tables).  Repeated calls on the same plans should create one sht_batch_t
+ * instead.  beta and values are HOST arrays of nfields device pointers (the
+ * layouts of sht_synthesize / sht_analyze per field); workspace is one
+ * caller-owned device buffer of sht_batched_workspace_bytes(nfields, plans,
+ * prec) bytes, field f using the part that starts at the sum of the
+ * preceding fields' sht_workspace_bytes, each rounded up to 256 bytes.
+ * Errors as sht_batch_create and the grid entry points. */
+size_t sht_batched_workspace_bytes(int nfields, const sht_plan_t* plans, sht_precision prec);
+sht_status sht_synthesize_batched(int nfields, const sht_plan_t* plans, sht_precision prec,
+                                  const void* const* beta, void* const* values, void* workspace,
+                                  sht_stream_t stream);
+sht_status sht_analyze_batched(int nfields, const sht_plan_t* plans, sht_precision prec,
+                               const void* const* values, void* const* beta, void* workspace,
+                               sht_stream_t stream);
+
 /* ------------------------------------------------------ allocation-free call */
 
 /* Static scratch slots of sht_legendre_synthesize_noalloc (32 bytes each). */
@@ -551,9 +576,12 @@ sht_status sht_batch_get_config(sht_batch_t batch, int direction, int* consumer_
  * plan allocated.
  *   slot:   0 <= slot < SHT_NOALLOC_MAX_SLOTS, else SHT_ERR_INVALID_ARG
  *           (sht_last_error_detail names the limit).
- *   status: optional caller-owned device word (NULL to skip).  It is zeroed
- *           in stream order, then receives SHT_ERR_TIMEOUT if a bounded wait
- *           of the launch gave up (0 otherwise).
+ *   status: optional caller-owned device word.  It is zeroed in stream
+ *           order, then receives SHT_ERR_TIMEOUT if a bounded wait of the
+ *           launch gave up (0 otherwise).  With NULL the launch reports into
+ *           a private word of the slot that nothing reads, so a timeout
+ *           cannot be detected (G is then undefined): pass a word wherever
+ *           that matters.
  * The precision must already be on the device (SHT_FP64 is uploaded by
  * sht_plan_create; others by sht_prepare); otherwise SHT_ERR_UNSUPPORTED.
  * The first call on a device does a one-time set-up: it looks up the
@@ -561,6 +589,8 @@ sht_status sht_batch_get_config(sht_batch_t batch, int direction, int* consumer_
  * ordered, so make the first call before any stream capture.  Calls whose
  * launches overlap in time (other streams, threads or plans) must use
  * different slots: two launches on one slot race on its counter.
+ * The caller's current device is the same after the call as before it, and
+ * a CUDA error the caller left pending on this thread is left pending.
  * Asynchronous on stream. */
 sht_status sht_legendre_synthesize_noalloc(sht_plan_t plan, sht_precision prec, const void* beta, void* G,
                                            int slot, unsigned* status, sht_stream_t stream);

@@ -14,6 +14,14 @@ gradient, and nothing is saved for the backward pass beyond the plan and
 the precision.  Coefficients and G are treated as independent complex
 numbers; a loss on the real grid (which counts orders +m and -m) would add
 its own factor 2 for m > 0 outside this function.
+
+Device status: the launches are asynchronous and their bounded waits report
+a timeout only in a device status word (the kernel then stops early and its
+output is undefined).  Nothing here reads that word unless asked:
+``legendre_synthesis(..., check=True)`` synchronizes the stream after the
+forward launch and after the backward launch and raises ``sht.ShtError``
+on a nonzero status; otherwise call ``device_status(plan, prec, batch)``
+(or ``sht.sht_last_device_status``) yourself where it matters.
 """
 
 import torch
@@ -63,20 +71,46 @@ def _apply(plan, prec, x, adjoint):
     return out[0] if single else out
 
 
+def device_status(plan, prec, nfields=1):
+    """Status word of the launches of one field (the plan's) or of a batch of
+    nfields fields of this plan (its cached batch); synchronizes the stream.
+    0 = fine, 5 = a bounded wait gave up."""
+    stream = torch.cuda.current_stream()
+    if nfields == 1:
+        return sht.sht_last_device_status(plan, stream)
+    return sht.sht_batch_last_device_status(_batch(plan, int(prec), nfields), stream)
+
+
+def _checked(plan, prec, x, n, where):
+    code = device_status(plan, prec, n)
+    if code != 0:
+        raise sht.ShtError(code, where)
+    return x
+
+
 class LegendreSynthesis(torch.autograd.Function):
     """G = S beta with the transposed butterfly as its hand-written backward."""
 
     @staticmethod
-    def forward(ctx, beta, plan, prec):
+    def forward(ctx, beta, plan, prec, check):
         ctx.plan = plan
         ctx.prec = int(prec)
-        return _apply(plan, int(prec), beta, adjoint=False)
+        ctx.check = bool(check)
+        out = _apply(plan, int(prec), beta, adjoint=False)
+        n = 1 if beta.dim() == 1 else beta.shape[0]
+        return _checked(plan, prec, out, n, "legendre_synthesis forward") if check else out
 
     @staticmethod
     def backward(ctx, grad_G):
-        return _apply(ctx.plan, ctx.prec, grad_G, adjoint=True), None, None
+        g = _apply(ctx.plan, ctx.prec, grad_G, adjoint=True)
+        if ctx.check:
+            g = _checked(ctx.plan, ctx.prec, g, 1 if grad_G.dim() == 2 else grad_G.shape[0],
+                         "legendre_synthesis backward")
+        return g, None, None, None
 
 
-def legendre_synthesis(beta, plan, prec=sht.SHT_FP64):
-    """Differentiable Legendre synthesis of one field ([T]) or a batch ([B, T])."""
-    return LegendreSynthesis.apply(beta, plan, prec)
+def legendre_synthesis(beta, plan, prec=sht.SHT_FP64, check=False):
+    """Differentiable Legendre synthesis of one field ([T]) or a batch ([B, T]).
+    check=True reads the device status after each launch (synchronizing) and
+    raises on a timeout."""
+    return LegendreSynthesis.apply(beta, plan, prec, check)

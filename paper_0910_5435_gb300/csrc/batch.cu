@@ -359,4 +359,63 @@ sht_status sht_batch_get_config(sht_batch_t b, int direction, int* consumer_warp
   return SHT_OK;
 }
 
+// Per-field parts of one workspace buffer: field f starts at the sum of the
+// preceding fields' workspace bytes, each rounded up to 256 bytes.
+size_t sht_batched_workspace_bytes(int nfields, const sht_plan_t* plans, sht_precision prec) {
+  if (nfields < 1 || nfields > SHT_BATCH_MAX_FIELDS || !plans) return 0;
+  size_t total = 0;
+  for (int f = 0; f < nfields; ++f) {
+    if (!plans[f]) return 0;
+    total += (sht_workspace_bytes(plans[f], prec) + 255) & ~size_t(255);
+  }
+  return total;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One call of a batched spelling: a batch for this call, the grid entry point
+// of direction d (0 synthesis, 1 analysis), a wait for the stream (the batch's
+// tables are read by the launch), then the batch is freed.
+sht_status batched_call(int d, int nfields, const sht_plan_t* plans, sht_precision prec, const void* const* in,
+                        void* const* out, void* workspace, sht_stream_t stream) {
+  if (!in || !out || !workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return SHT_ERR_INVALID_ARG;
+  const size_t need = sht_batched_workspace_bytes(nfields, plans, prec);
+  if (need == 0) return SHT_ERR_INVALID_ARG;
+  std::vector<void*> ws(nfields);
+  size_t off = 0;
+  for (int f = 0; f < nfields; ++f) {
+    ws[f] = static_cast<uint8_t*>(workspace) + off;
+    off += (sht_workspace_bytes(plans[f], prec) + 255) & ~size_t(255);
+  }
+  sht_batch_t b = nullptr;
+  sht_status s = sht_batch_create(nfields, plans, prec, &b);
+  if (s != SHT_OK) return s;
+  s = d == 0 ? sht_batch_synthesize_grid(b, in, out, ws.data(), stream)
+             : sht_batch_analyze_grid(b, in, out, ws.data(), stream);
+  const cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  sht_batch_destroy(b);
+  if (s != SHT_OK) return s;
+  if (e != cudaSuccess) {
+    sht::set_error_detail("batched call", cudaGetErrorString(e));
+    return SHT_ERR_CUDA;
+  }
+  return SHT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sht_status sht_synthesize_batched(int nfields, const sht_plan_t* plans, sht_precision prec, const void* const* beta,
+                                  void* const* values, void* workspace, sht_stream_t stream) {
+  return batched_call(0, nfields, plans, prec, beta, values, workspace, stream);
+}
+
+sht_status sht_analyze_batched(int nfields, const sht_plan_t* plans, sht_precision prec, const void* const* values,
+                               void* const* beta, void* workspace, sht_stream_t stream) {
+  return batched_call(1, nfields, plans, prec, values, beta, workspace, stream);
+}
+
 }  // extern "C"

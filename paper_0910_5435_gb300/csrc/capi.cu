@@ -105,7 +105,7 @@ struct sht_plan_s {
   int* d_dense_rows = nullptr;
   int* d_dense_ncol = nullptr;
   size_t dense_bytes = 0;
-  sht_plan_stats stats{};
+  sht_plan_stats_t stats{};
   std::mutex mu;
 };
 
@@ -167,7 +167,7 @@ void free_dev(sht_plan_t P) {
 
 void fill_stats(sht_plan_t P) {
   const PlanHost& H = P->H;
-  sht_plan_stats& s = P->stats;
+  sht_plan_stats_t& s = P->stats;
   s.l = H.l;
   s.eps_id = H.eps_id;
   s.leaf_cols = H.leaf_cols;
@@ -748,12 +748,14 @@ sht_status sht_plan_destroy(sht_plan_t P) {
   return SHT_OK;
 }
 
-sht_status sht_plan_get_stats(sht_plan_t P, sht_plan_stats* out) {
+sht_status sht_plan_get_stats(sht_plan_t P, sht_plan_stats_t* out) {
   if (!P || !out) return SHT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> g(P->mu);
   *out = P->stats;
   return SHT_OK;
 }
+
+sht_status sht_plan_stats(sht_plan_t P, sht_plan_stats_t* out) { return sht_plan_get_stats(P, out); }
 
 sht_status sht_prepare(sht_plan_t P, sht_precision prec) {
   if (!P) return SHT_ERR_INVALID_ARG;

@@ -50,6 +50,17 @@ sht_status scratch_for(int device, unsigned** out) {
   return SHT_OK;
 }
 
+// Restores the caller's current device when the entry point returns.
+struct DeviceGuard {
+  int prev = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 }  // namespace
 
 extern "C" sht_status sht_legendre_synthesize_noalloc(sht_plan_t plan, sht_precision prec, const void* beta,
@@ -61,11 +72,19 @@ extern "C" sht_status sht_legendre_synthesize_noalloc(sht_plan_t plan, sht_preci
     sht::set_error_detail("sht_legendre_synthesize_noalloc", what);
     return SHT_ERR_INVALID_ARG;
   }
-  if (status && (reinterpret_cast<uintptr_t>(status) % alignof(unsigned)) != 0) return SHT_ERR_INVALID_ARG;
+  if (status && (reinterpret_cast<uintptr_t>(status) % alignof(unsigned)) != 0) {
+    sht::set_error_detail("sht_legendre_synthesize_noalloc", "status word is not 4-byte aligned");
+    return SHT_ERR_INVALID_ARG;
+  }
   sht::PreparedSweep L;
   sht_status s = sht::prepared_sweep(plan, prec, 0, beta, G, &L);
   if (s != SHT_OK) return s;
-  if (cudaSetDevice(L.device) != cudaSuccess) return SHT_ERR_CUDA;
+  DeviceGuard keep;  // the plan's device is made current; the caller's comes back on return
+  cudaError_t e = cudaSetDevice(L.device);
+  if (e != cudaSuccess) {
+    sht::set_error_detail("cudaSetDevice", cudaGetErrorString(e));
+    return SHT_ERR_CUDA;
+  }
   unsigned* base = nullptr;
   s = scratch_for(L.device, &base);
   if (s != SHT_OK) return s;
@@ -75,9 +94,16 @@ extern "C" sht_status sht_legendre_synthesize_noalloc(sht_plan_t plan, sht_preci
   // early leaves its counter dirty, so they are cleared in stream order
   L.args.counter = word;
   L.args.status = status ? status : word + 1;
-  if (cudaMemsetAsync(word, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return SHT_ERR_CUDA;
-  if (status && cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) return SHT_ERR_CUDA;
-  (void)cudaGetLastError();
-  if (sht::sweep_launch(L.prec, L.consumer_warps, L.args, L.grid, L.smem, st) != cudaSuccess) return SHT_ERR_CUDA;
+  if ((e = cudaMemsetAsync(word, 0, 2 * sizeof(unsigned), st)) != cudaSuccess ||
+      (status && (e = cudaMemsetAsync(status, 0, sizeof(unsigned), st)) != cudaSuccess)) {
+    sht::set_error_detail("cudaMemsetAsync", cudaGetErrorString(e));
+    return SHT_ERR_CUDA;
+  }
+  // the launch's own result; an error the caller left pending on this thread
+  // is neither cleared nor reported here
+  if ((e = sht::sweep_launch(L.prec, L.consumer_warps, L.args, L.grid, L.smem, st)) != cudaSuccess) {
+    sht::set_error_detail("sweep launch", cudaGetErrorString(e));
+    return SHT_ERR_CUDA;
+  }
   return SHT_OK;
 }

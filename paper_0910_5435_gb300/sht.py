@@ -36,7 +36,8 @@ EXPORTS = [
     "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config", "sht_batch_synthesize_adjoint",
     "sht_unit_stats_compute", "sht_gauss_jacobi_nodes", "sht_unit_stats_gauss_jacobi",
     "sht_plan_save", "sht_plan_load", "sht_batch_synthesize_grid", "sht_batch_analyze_grid",
-    "sht_measure_fp64_fma", "sht_interp_decomp",
+    "sht_measure_fp64_fma", "sht_interp_decomp", "sht_plan_stats", "sht_batched_workspace_bytes",
+    "sht_synthesize_batched", "sht_analyze_batched",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -71,7 +72,7 @@ class sht_plan_opts(ctypes.Structure):
     ]
 
 
-class sht_plan_stats(ctypes.Structure):
+class sht_plan_stats_t(ctypes.Structure):
     _fields_ = [
         ("l", ctypes.c_int),
         ("eps_id", ctypes.c_double),
@@ -131,7 +132,7 @@ def lib():
     L.sht_plan_destroy.argtypes = [vp]
     L.sht_plan_save.argtypes = [vp, ctypes.c_char_p]
     L.sht_plan_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(sht_plan_opts), ctypes.POINTER(vp)]
-    L.sht_plan_get_stats.argtypes = [vp, ctypes.POINTER(sht_plan_stats)]
+    L.sht_plan_get_stats.argtypes = [vp, ctypes.POINTER(sht_plan_stats_t)]
     L.sht_prepare.argtypes = [vp, c_int]
     L.sht_plan_nodes.argtypes = [vp, vp, vp]
     L.sht_plan_stream.argtypes = [vp, c_int, c_int, vp, ctypes.POINTER(ctypes.c_size_t),
@@ -167,8 +168,14 @@ def lib():
     L.sht_batch_last_device_status.argtypes = [vp, vp]
     L.sht_batch_autotune.argtypes = [vp, c_int, vp, vp, c_int, vp]
     L.sht_batch_get_config.argtypes = [vp, c_int, vp, vp, vp, vp]
+    L.sht_plan_stats.argtypes = [vp, ctypes.POINTER(sht_plan_stats_t)]
+    L.sht_batched_workspace_bytes.argtypes = [c_int, vp, c_int]
+    L.sht_batched_workspace_bytes.restype = ctypes.c_size_t
+    L.sht_synthesize_batched.argtypes = [c_int, vp, c_int, vp, vp, vp, vp]
+    L.sht_analyze_batched.argtypes = [c_int, vp, c_int, vp, vp, vp, vp]
     for name in EXPORTS:
-        if name not in ("sht_status_string", "sht_workspace_bytes", "sht_last_error_detail"):
+        if name not in ("sht_status_string", "sht_workspace_bytes", "sht_last_error_detail",
+                        "sht_batched_workspace_bytes"):
             getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -270,7 +277,7 @@ class Plan:
         return self.stats()["page_bytes"]
 
     def stats(self):
-        s = sht_plan_stats()
+        s = sht_plan_stats_t()
         _check(lib().sht_plan_get_stats(self.handle, ctypes.byref(s)), "sht_plan_get_stats")
         return s.as_dict()
 
@@ -496,6 +503,37 @@ def sht_batch_autotune(batch, direction, in_ptrs, out_ptrs, reps=3, stream=None)
 
 def sht_workspace_bytes(plan, prec):
     return int(lib().sht_workspace_bytes(plan.handle, int(prec)))
+
+
+def _plan_array(plans):
+    return (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+
+
+def sht_plan_stats(plan):
+    """The plan statistics (sht_plan_stats, the same call as sht_plan_get_stats)."""
+    s = sht_plan_stats_t()
+    _check(lib().sht_plan_stats(plan.handle, ctypes.byref(s)), "sht_plan_stats")
+    return s.as_dict()
+
+
+def sht_batched_workspace_bytes(plans, prec):
+    return int(lib().sht_batched_workspace_bytes(len(plans), _plan_array(plans), int(prec)))
+
+
+def sht_synthesize_batched(plans, prec, betas, values, workspace, stream=None):
+    """Full synthesis of len(plans) fields in one call (synchronous on stream):
+    betas and values are lists of device tensors, workspace one device buffer
+    of sht_batched_workspace_bytes(plans, prec) bytes."""
+    _check(lib().sht_synthesize_batched(len(plans), _plan_array(plans), int(prec), host_pointer_array(betas),
+                                        host_pointer_array(values), _ptr(workspace), _stream(stream)),
+           "sht_synthesize_batched")
+
+
+def sht_analyze_batched(plans, prec, values, betas, workspace, stream=None):
+    """Full analysis of len(plans) fields in one call (synchronous on stream)."""
+    _check(lib().sht_analyze_batched(len(plans), _plan_array(plans), int(prec), host_pointer_array(values),
+                                     host_pointer_array(betas), _ptr(workspace), _stream(stream)),
+           "sht_analyze_batched")
 
 
 def sht_phi_synthesize(plan, prec, G, values, workspace, stream=None):

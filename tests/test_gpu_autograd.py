@@ -122,3 +122,21 @@ def test_backward_saves_nothing_but_the_plan(mods):
     beta = torch.from_numpy(inputs.random_beta(8, seed=9)).cuda().requires_grad_()
     G = ag.legendre_synthesis(beta, P, 0)
     assert len(G.grad_fn.saved_tensors) == 0
+
+
+def test_checked_launches_raise_on_timeout(mods):
+    """check=True reads the device status after the forward and backward
+    launches: a sound plan passes both; a plan whose first op waits for a
+    completion that never comes raises SHT_ERR_TIMEOUT from the forward."""
+    sht, ag = mods
+    l = 16
+    good = sht.Plan(l, 1e-12, leaf_cols=4)
+    bad = sht.Plan(l, 1e-12, leaf_cols=4, debug_unmet_dependency=1)
+    b = torch.from_numpy(inputs.random_beta(l, seed=77)).cuda().requires_grad_(True)
+    ag.legendre_synthesis(b, good, 0, check=True).abs().pow(2).sum().backward()
+    assert b.grad is not None and torch.isfinite(torch.view_as_real(b.grad)).all()
+    with pytest.raises(sht.ShtError) as e:
+        ag.legendre_synthesis(b.detach(), bad, 0, check=True)
+    assert e.value.code == 5
+    good.close()
+    bad.close()

@@ -230,3 +230,39 @@ def test_batch_grid_rejects_bad_pointers(sht, plans):
     sht.sht_batch_synthesize_grid(B, betas, values, ws)
     assert sht.sht_batch_last_device_status(B) == 0
     B.close()
+
+
+@pytest.mark.parametrize("prec", [0, 2, 1])
+def test_batched_spellings_match_oracle(sht, plans, prec):
+    """sht_synthesize_batched / sht_analyze_batched (a batch built for the
+    call, one workspace buffer split per field) against the oracle's full
+    transforms of every field, and the same values as the batch object."""
+    ls = field_ls(11, 6)
+    pl = [plans[l] for l in ls]
+    for p in set(pl):
+        p.prepare(prec)
+    rdt = torch.float32 if prec == 1 else torch.float64
+    betas, _ = fields(ls, prec, 9300)
+    values = [torch.full((2 * l, 4 * l - 1), float("nan"), dtype=rdt, device="cuda") for l in ls]
+    need = sht.sht_batched_workspace_bytes(pl, prec)
+    assert need >= sum(sht.sht_workspace_bytes(p, prec) for p in pl)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    sht.sht_synthesize_batched(pl, prec, betas, values, ws)
+    for l, beta, v in zip(ls, betas, values):
+        fo = oracle.sht_synthesis(beta.cpu().numpy().astype(np.complex128), l)
+        assert np.linalg.norm(v.cpu().numpy() - fo) / np.linalg.norm(fo) < TOL[prec], l
+    backs = [torch.full_like(b, float("nan")) for b in betas]
+    sht.sht_analyze_batched(pl, prec, values, backs, ws)
+    for l, v, back in zip(ls, values, backs):
+        bo = oracle.sht_analysis(v.cpu().numpy().astype(np.float64), l)
+        assert rel(back, bo) < TOL[prec], l
+    B = sht.Batch(pl, prec)
+    again = [torch.full_like(v, float("nan")) for v in values]
+    per = [torch.empty((2 * l, 2 * l), dtype=CDT[prec], device="cuda") for l in ls]
+    sht.sht_batch_synthesize_grid(B, betas, again, per)
+    torch.cuda.synchronize()
+    for v, a in zip(values, again):
+        assert torch.equal(v, a)
+    B.close()
+    st = sht.sht_plan_stats(pl[0])
+    assert st == pl[0].stats() and st["l"] == ls[0]

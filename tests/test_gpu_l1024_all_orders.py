@@ -1,0 +1,91 @@
+"""Every order at the benchmarked configuration, checked one order at a time.
+
+l = 1024, eps_id = 1e-12, leaf_cols 32, 8 KB pages, default launch shape,
+beta ~ N(0,1)/(k+1) with seed 3 (the bench's field) and G iid complex N(0,1)
+with seed 4.  All four precisions, synthesis, analysis and the adjoint of
+synthesis.  For each order m separately:
+
+* relative l2 error <= the path's tolerance (float64 1e-10, split float32
+  1e-9, float32 2e-5), so an error confined to a few high orders, whose
+  values are small, cannot hide in a pooled norm;
+* max-abs error <= tolerance x the order's largest magnitude: the paper's
+  eps_fwd (Section 5, the largest entry of the difference between the
+  butterfly and the direct product), scaled to each order.
+
+The float64 oracle runs over all 2048 orders on every host core.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0910_5435_gb300 import inputs
+from tests._oracle_pool import all_orders
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+L = 1024
+TOL = {0: 1e-10, 2: 1e-9, 3: 1e-9, 1: 2e-5}
+CDT = {0: torch.complex128, 2: torch.complex128, 3: torch.complex128, 1: torch.complex64}
+
+
+@pytest.fixture(scope="module")
+def ref():
+    # the worker processes start (spawn) before this module's first GPU call
+    return all_orders(L, 3, 4)
+
+
+@pytest.fixture(scope="module")
+def plan(ref):
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0910_5435_gb300 import sht
+    assert torch.cuda.is_available()
+    P = sht.Plan(L, 1e-12, leaf_cols=32, page_bytes=8192)
+    yield sht, P
+    P.close()
+
+
+def per_order(got, want, rows):
+    """(worst relative l2, worst max-abs relative to the order's largest |value|,
+    order of each) over the row ranges rows[m] = slice of order m."""
+    worst_l2, worst_inf, m_l2, m_inf = 0.0, 0.0, -1, -1
+    for m, sl in enumerate(rows):
+        d = np.asarray(got[sl], np.complex128) - want[sl]
+        nw = np.linalg.norm(want[sl])
+        e2 = np.linalg.norm(d) / nw
+        ei = np.max(np.abs(d)) / np.max(np.abs(want[sl]))
+        if e2 > worst_l2:
+            worst_l2, m_l2 = e2, m
+        if ei > worst_inf:
+            worst_inf, m_inf = ei, m
+    return worst_l2, m_l2, worst_inf, m_inf
+
+
+@pytest.mark.parametrize("prec", [0, 2, 3, 1])
+def test_every_order_matches_oracle(plan, ref, prec):
+    sht, P = plan
+    Go, bo, ba = ref
+    P.prepare(prec)
+    off = oracle.triangle_offsets(L)
+    g_rows = [m for m in range(2 * L)]
+    b_rows = [slice(off[m], off[m + 1]) for m in range(2 * L)]
+    beta = torch.from_numpy(inputs.random_beta(L, seed=3, decay=True)).to(CDT[prec]).cuda()
+    Gin = torch.from_numpy(inputs.random_G(L, seed=4)).to(CDT[prec]).cuda()
+    G = torch.full((2 * L, 2 * L), float("nan"), dtype=CDT[prec], device="cuda")
+    b = torch.full((inputs.triangle_size(L),), float("nan"), dtype=CDT[prec], device="cuda")
+    badj = torch.full_like(b, float("nan"))
+    sht.sht_legendre_synthesize(P, prec, beta, G)
+    sht.sht_legendre_analyze(P, prec, Gin, b)
+    sht.sht_legendre_synthesize_adjoint(P, prec, Gin, badj)
+    torch.cuda.synchronize()
+    assert sht.sht_last_device_status(P) == 0
+    tol = TOL[prec]
+    for name, got, want, rows in (("synthesis", G.cpu().numpy(), Go, g_rows),
+                                  ("analysis", b.cpu().numpy(), bo, b_rows),
+                                  ("adjoint", badj.cpu().numpy(), ba, b_rows)):
+        assert not np.isnan(got).any(), name
+        e2, m2, ei, mi = per_order(got, want, rows)
+        assert e2 <= tol, f"{name}: order {m2} relative l2 error {e2:.3e} > {tol:g}"
+        assert ei <= tol, f"{name}: order {mi} max-abs error {ei:.3e} of its largest value > {tol:g}"

@@ -85,3 +85,61 @@ def test_rejections(sht):
         sht.sht_legendre_synthesize_noalloc(P, 1, beta.to(torch.complex64), G.to(torch.complex64))
     assert e.value.code == 6
     P.close()
+
+
+def test_device_and_pending_error_untouched_and_nothing_allocated(sht):
+    """The call leaves the caller's current device current, and ten calls
+    change neither the device's free memory nor the torch allocator's."""
+    l = 64
+    P = sht.Plan(l, 1e-12, leaf_cols=16)
+    beta = torch.from_numpy(inputs.random_beta(l, seed=44)).cuda()
+    G = torch.empty((2 * l, 2 * l), dtype=torch.complex128, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sht.sht_legendre_synthesize_noalloc(P, 0, beta, G, slot=5, status=status)  # first call: set-up
+    torch.cuda.synchronize()
+    dev = torch.cuda.current_device()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(10):
+        sht.sht_legendre_synthesize_noalloc(P, 0, beta, G, slot=5, status=status)
+        assert torch.cuda.current_device() == dev
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    if torch.cuda.device_count() > 1:
+        # a plan of device 0 called while another device is current
+        with torch.cuda.device(1):
+            sht.sht_legendre_synthesize_noalloc(P, 0, beta, G, slot=6)
+            assert torch.cuda.current_device() == 1
+        torch.cuda.synchronize(0)
+    P.close()
+
+
+def test_timeout_is_reported_in_the_status_word_and_the_slot_recovers(sht):
+    """A plan whose first op waits for a completion that never comes (the
+    failure-detection option of the plan): each call's bounded wait gives up
+    (about 2 s) and writes SHT_ERR_TIMEOUT into the caller's status word; the
+    next call on the same slot with a sound plan clears the slot's dirty
+    counter and matches the oracle."""
+    import oracle
+
+    l = 32
+    bad = sht.Plan(l, 1e-12, leaf_cols=8, debug_unmet_dependency=1)
+    good = sht.Plan(l, 1e-12, leaf_cols=8)
+    beta_np = inputs.random_beta(l, seed=45)
+    beta = torch.from_numpy(beta_np).cuda()
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        G = torch.empty((2 * l, 2 * l), dtype=torch.complex128, device="cuda")
+        sht.sht_legendre_synthesize_noalloc(bad, 0, beta, G, slot=7, status=status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 5
+    G = torch.full((2 * l, 2 * l), float("nan"), dtype=torch.complex128, device="cuda")
+    sht.sht_legendre_synthesize_noalloc(good, 0, beta, G, slot=7, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = oracle.legendre_synthesis(beta_np, l)
+    assert np.linalg.norm(G.cpu().numpy() - ref) / np.linalg.norm(ref) < TOL[0]
+    bad.close()
+    good.close()
