@@ -129,8 +129,9 @@ typedef struct {
    * reports SHT_ERR_TIMEOUT; the context stays usable. */
   int debug_unmet_dependency;
   /* Values kept apart: the most values one op may hold, which is the size of
-   * a consumer warp's staging slot (a multiple of 32 in 128..2048; 0 =
-   * default 1024).  Smaller slots let more consumer warps fit in shared
+   * a consumer warp's staging slot (a multiple of 32 in 128..2048; 0 = one
+   * 8 KB slot's worth: 1024 values for SHT_FP64 and the split formats, 2048
+   * for SHT_FP32).  Smaller slots let more consumer warps fit in shared
    * memory, at the cost of splitting blocks into more ops.  A tuning knob. */
   int slot_values;
   /* 1: compute the factorizations (column generation, IDs, depth-first
@@ -154,14 +155,12 @@ typedef struct {
    * sht_last_error_detail).  A failed write fails plan creation with
    * SHT_ERR_INVALID_ARG.  The string is read during the call only. */
   const char* plan_cache;
-  /* Staging slots per consumer warp when values are kept apart (0 = per
-   * precision: 1 for SHT_FP64 and the split formats, 2 for SHT_FP32).  1
+  /* Staging slots per consumer warp when values are kept apart (0 = 1).  1
    * starts the copy of a warp's next op once its current op has read the
    * slot, and leaves room for 16 consumer warps whose copies and arithmetic
    * overlap one another; 2 lets a warp's next op's values travel while its
-   * current op runs, at twice the slot memory (8 warps at the default 8-byte
-   * slot size, 16 with float32 values).  A tuning knob; results do not depend
-   * on it. */
+   * current op runs, at twice the slot memory (8 warps at the default slot
+   * size).  A tuning knob; results do not depend on it. */
   int staging_slots;
 } sht_plan_opts;
 

@@ -296,7 +296,7 @@ sht_status upload_streams(sht_plan_t P, int q) {
   CK(sht::sweep_configure(q, (size_t)optin));
   if (q == sht::PREC_SPLIT32) CK(sht::sweep_configure(sht::PREC_SPLIT32_ACC64, (size_t)optin));
   sht::SweepConfig cfg;
-  const int slot_bytes = P->H.values_apart[q] ? P->H.slot_values * (q == sht::PREC_FP32 ? 4 : 8) : 0;
+  const int slot_bytes = P->H.values_apart[q] ? P->H.slot_values_for(q) * (q == sht::PREC_FP32 ? 4 : 8) : 0;
   if (!sht::sweep_choose(q, P->H.page_bytes, buf_ab, nvecs, P->consumer_warps[q], slot_bytes, 0, (size_t)optin,
                          &cfg, P->warp_slots[q]))
     return SHT_ERR_UNSUPPORTED;
@@ -455,7 +455,7 @@ sht_status sht::stream_view(sht_plan_t P, sht_precision prec, int dir, StreamVie
   v->num_sms = P->num_sms;
   v->values_apart = P->H.values_apart[q];
   v->consumer_warps = P->consumer_warps[q];
-  v->slot_bytes = P->H.values_apart[q] ? P->H.slot_values * (q == sht::PREC_FP32 ? 4 : 8) : 0;
+  v->slot_bytes = P->H.values_apart[q] ? P->H.slot_values_for(q) * (q == sht::PREC_FP32 ? 4 : 8) : 0;
   v->warp_slots = P->warp_slots[q];
   v->prescale = P->d_inv_w;
   v->tw_syn = P->d_tw_syn;
@@ -609,7 +609,7 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
   // the FP64 pipe busier than 8 warps with two slots; float32 slots are half
   // the size, so 16 warps keep two by default
   for (int q = 0; q < kNumPrec; ++q)
-    P->warp_slots[q] = o.staging_slots ? o.staging_slots : (q == sht::PREC_FP32 ? 2 : 1);
+    P->warp_slots[q] = o.staging_slots ? o.staging_slots : 1;
   // 0 = 16 consumer warps for every precision
   for (int q = 0; q < kNumPrec; ++q)
     P->consumer_warps[q] = o.consumer_warps ? o.consumer_warps : 16;
@@ -624,7 +624,7 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
   H.page_bytes = o.page_bytes;
   for (int q = 0; q < 3; ++q) H.values_apart[q] = (o.values_inline == 0);
   H.debug_unmet_dep = o.debug_unmet_dependency != 0;
-  H.slot_values = o.slot_values ? o.slot_values : sht::kDefaultSlotValues;
+  H.slot_values = o.slot_values;
   H.device_arena_bytes = (long long)o.device_build_arena_mb << 20;
 
   if (!P->host_only) {

@@ -795,7 +795,23 @@ struct Emitter {
   int seg_start = 0;  // first op of the current segment (after its JOIN)
   int positions = 0;
   int l = 0;
+  // Shared-vector placement: the ops of one parity block address its vector
+  // positions from `base`, chosen by place() so that consecutive blocks of a
+  // work item occupy disjoint ranges whenever they fit in `pool` positions;
+  // the tracker then finds no conflict between them and they run
+  // concurrently (the two parities of an order, the tail of one order with
+  // the head of the next).
+  int base = 0;
+  int cursor = 0;
+  int pool = 0;
   Emitter(PageWriter& w, int p) : W(w), prec(p), vs(value_size(p)) {}
+
+  // Chooses the base of a block using `width` positions of each vector.
+  void place(int width) {
+    if (cursor + width > pool) cursor = 0;
+    base = cursor;
+    cursor += width;
+  }
 
   OpHdr hdr(uint8_t kind, uint8_t flags = 0) {
     OpHdr h;
@@ -821,14 +837,17 @@ struct Emitter {
     auto vkey = [](int b, int pos) { return ((long long)b << 20) | pos; };
     auto gkey = [](int m, int row) { return (1LL << 40) | ((long long)m << 20) | row; };
     const int M = h.M, K = h.K;
+    const int cbase = h.a0 >> 1;  // GATHER / SCATTER / FOLD: vector base
     switch (h.kind) {
       case OP_GATHER:
       case OP_FOLD:
+        for (int j = 0; j < M; ++j) Wr.push_back(vkey(h.out_buf, cbase + h.oo + j));
+        break;
       case OP_CLEAR:
         for (int j = 0; j < M; ++j) Wr.push_back(vkey(h.out_buf, h.oo + j));
         break;
       case OP_SCATTER:
-        for (int j = 0; j < M; ++j) R.push_back(vkey(h.in_buf, h.io + j));
+        for (int j = 0; j < M; ++j) R.push_back(vkey(h.in_buf, cbase + h.io + j));
         break;
       case OP_GZERO:
         for (int j = 0; j < M; ++j) Wr.push_back(gkey(h.a1, l + h.oo + j)), Wr.push_back(gkey(h.a1, l - 1 - h.oo - j));
@@ -942,6 +961,8 @@ struct Emitter {
   void open_item(int npos) {
     positions = npos;
     next_op = 0;
+    cursor = 0;
+    base = 0;
     open_segment();
   }
 
@@ -957,6 +978,29 @@ struct Emitter {
   }
 
   void write(OpHdr h, const std::vector<uint16_t>& idx, const std::vector<double>& vals) {
+    // shift the op's vector positions to the block's base (control ops whose
+    // offsets also index coefficients or node rows carry it in a0)
+    switch (h.kind) {
+      case OP_GATHER:
+      case OP_SCATTER:
+      case OP_FOLD:
+        h.a0 = (uint16_t)(h.a0 | (base << 1));
+        break;
+      case OP_CLEAR:
+        h.oo = (uint16_t)(h.oo + base);
+        break;
+      case OP_SYN_INTERP:
+      case OP_DENSE:
+      case OP_ANA_INTERP:
+        h.io = (uint16_t)(h.io + base);
+        h.oo = (uint16_t)(h.oo + base);
+        break;
+      case OP_DENSE_G:
+        h.io = (uint16_t)(h.io + base);
+        break;
+      default:
+        break;
+    }
     // room for a fan-in JOIN and the op itself in this segment
     if (next_op + 2 - seg_start >= kMaxItemOps) open_segment();
     std::vector<long long> R, Wr;
@@ -1129,6 +1173,14 @@ std::vector<const IdBlock*> blocks_at(const UnitFact& U, int j) {
 
 using Stage = std::function<void(Emitter&)>;
 
+// Vector positions a parity block uses in either direction: its columns, its
+// kept rows and every butterfly level.
+int unit_width(const UnitFact& U) {
+  int w = std::max(U.n, U.rows);
+  for (int x : U.width) w = std::max(w, x);
+  return w;
+}
+
 // Appends the ops of order m to the emitter's current work item.
 void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
   const int l = P.l;
@@ -1190,9 +1242,11 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
         }
       };
     }
-    // shared buffers: each parity's final blocks read its top level before
-    // the next parity overwrites it
+    // each parity block at its own place in the shared vectors: where both
+    // fit, the parities run concurrently; otherwise the tracker orders the
+    // next block's writes after this one's final reads
     for (int p = 0; p < 2; ++p) {
+      E.place(unit_width(F[(size_t)m * 2 + p]));
       for (const Stage& sg : st[p]) sg(E);
       if (fin[p]) fin[p](E);
     }
@@ -1291,8 +1345,10 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
         E.control(s, 0, U.n);
       });
     }
-    for (int p = 0; p < 2; ++p)
+    for (int p = 0; p < 2; ++p) {
+      E.place(unit_width(F[(size_t)m * 2 + p]));
       for (const Stage& sg : st[p]) sg(E);
+    }
   }
 }
 
@@ -1344,7 +1400,8 @@ void emit_streams(PlanHost& P, int prec) {
       E.l = P.l;
       E.values = apart ? &vals : nullptr;
       E.plant_unmet = P.debug_unmet_dep && std::find(ms.begin(), ms.end(), 0) != ms.end();
-      E.slot_values = P.slot_values;
+      E.slot_values = P.slot_values_for(prec);
+      E.pool = positions - 1;
       E.open_item(positions);
       for (int m : ms) emit_unit(P, prec, dir, m, E);
       return E.next_op;
@@ -1357,22 +1414,28 @@ void emit_streams(PlanHost& P, int prec) {
     auto work_pages = [&](int m) { return (per[m].size() + per_vals[m].size() + PB - 1) / PB; };
     size_t total_pages = 0;
     for (int m = 0; m < L; ++m) total_pages += work_pages(m);
-    // Work items: orders in decreasing size, packed so an item has about
-    // total / (4 x 304) pages (several items per CTA for load balance, more
-    // than one order per item so the tail of one overlaps the next), and
+    // Work items: orders in decreasing size, packed with guided sizes: an
+    // item takes about remaining / (2 x 152) pages of the work not yet
+    // packed (152: the SMs of the GB300 the persistent kernel runs one CTA
+    // on each), at least 4, so the queue starts with large items and ends
+    // with small ones that even out the CTAs' finishing times; more than one
+    // order per item where they fit, so the tail of one overlaps the next;
     // fewer than kMaxItemOps ops (the completion-tag window).
-    const size_t target = std::max<size_t>(4, total_pages / (4 * 304));
+    constexpr size_t kGuideCtas = 2 * 152;
     std::vector<int> order(L);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work_pages(a) > work_pages(b); });
     std::vector<std::vector<int>> items;
     std::vector<int> cur;
-    size_t cur_pages = 0;
+    size_t cur_pages = 0, remaining = total_pages;
     int cur_ops = 0;
+    size_t target = std::max<size_t>(4, remaining / kGuideCtas);
     for (int m : order) {
       const size_t pg = work_pages(m);
       if (!cur.empty() && (cur_pages + pg > target || cur_ops + nops[m] >= kMaxItemOps)) {
         items.push_back(cur);
+        remaining -= std::min(remaining, cur_pages);
+        target = std::max<size_t>(4, remaining / kGuideCtas);
         cur.clear();
         cur_pages = 0;
         cur_ops = 0;
@@ -1449,13 +1512,8 @@ void emit_streams(PlanHost& P, int prec) {
     q.kind = OP_QUIT;
     std::memcpy(quit, &q, sizeof(q));
     std::memcpy(quit + PB - 2, &kQuitPage, 2);
-    int mx = 0;
-    for (int u = 0; u < L * 2; ++u) {
-      mx = std::max(mx, F[u].n);
-      if (dir == 1) mx = std::max(mx, F[u].rows);  // the fold writes the kept rows
-      for (int wdt : F[u].width) mx = std::max(mx, wdt);
-    }
-    S.max_buf_ab = mx;
+    // blocks are placed anywhere in the first positions - 1 elements
+    S.max_buf_ab = positions - 1;
     S.num_vecs = 2;
   }
   P.built[prec] = true;

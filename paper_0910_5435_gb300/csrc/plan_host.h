@@ -101,7 +101,12 @@ struct PlanHost {
   int l = 0;
   double eps_id = 0, eps_fp32 = 0, trim_eps = 0;
   int leaf_cols = 64, min_band_rows = 32, num_threads = 0, page_bytes = 8192;
-  int slot_values = kDefaultSlotValues;  // cap on the values of one op kept apart
+  int slot_values = 0;  // cap on the values of one op kept apart (0: per precision, below)
+  // The value cap of one precision's ops (prec 0 float64, 1 float32, 2 split):
+  // by default one 8 KB staging slot's worth (1024 8-byte or 2048 4-byte values).
+  int slot_values_for(int prec) const {
+    return slot_values ? slot_values : (prec == 1 ? 2 * kDefaultSlotValues : kDefaultSlotValues);
+  }
   bool values_apart[3] = {true, true, true};  // per precision: value blocks outside the pages
   bool debug_unmet_dep = false;  // plant a never-met predecessor (failure-detection tests)
   long long device_arena_bytes = 0;  // device build: record arena limit (0 = automatic)

@@ -45,6 +45,13 @@
 // memory, FOLD forms u_i = s_i (G[m][l+i] +- G[m][l-1-i]) (the parity fold),
 // CLEAR zeroes a shared range, GZERO zeroes node rows of G.
 //
+// Placement: each parity block's ops address the shared vectors from a base
+// position the planner chose for the block, so that consecutive blocks of a
+// work item use disjoint ranges where they fit and run concurrently.  Compute
+// ops and CLEAR carry the base in io / oo; GATHER, SCATTER and FOLD, whose
+// offsets also index coefficients or node rows, carry it in a0 >> 1 (a0 & 1
+// is the parity) and address vector position base + j for element j.
+//
 // Ordering: ops are numbered in stream order (per CTA).  Op t lists its
 // predecessors as npred deltas d (op t - d) at the start of its index area:
 // the last writer of every shared position / node row it reads or writes and
@@ -66,9 +73,9 @@ namespace sht {
 
 enum OpKind : uint8_t {
   OP_END = 0,
-  OP_GATHER = 1,      // buf[out_buf][oo + j] = beta^m_{m+p+2(oo+j)}, j < M       (a0 = p, a1 = m)
-  OP_SCATTER = 2,     // beta^m_{m+p+2(io+j)} = buf[in_buf][io + j], j < M        (a0 = p, a1 = m)
-  OP_FOLD = 3,        // buf[out_buf][oo + j] = s (G[m][l+r] + (-1)^p G[m][l-1-r]), r = oo + j, j < M
+  OP_GATHER = 1,      // buf[out_buf][b + j] = beta^m_{m+p+2j}, j in [oo, oo + M)  (a0 = p | b << 1, a1 = m)
+  OP_SCATTER = 2,     // beta^m_{m+p+2j} = buf[in_buf][b + j], j in [io, io + M)   (a0 = p | b << 1, a1 = m)
+  OP_FOLD = 3,        // buf[out_buf][b + r] = s (G[m][l+r] + (-1)^p G[m][l-1-r]), r in [oo, oo + M)
   OP_CLEAR = 4,       // buf[out_buf][oo + j] = 0, j < M
   OP_GZERO = 5,       // G[m][l+r] = G[m][l-1-r] = 0, r = oo + j, j < M            (a1 = m)
   OP_SYN_INTERP = 6,
@@ -99,7 +106,7 @@ struct alignas(16) OpHdr {
   uint16_t io;        // element offset of the input vector
   uint16_t oo;        // element offset of the output vector / start of a control range
   uint16_t npred;     // predecessor count; the deltas lead the index area (see above)
-  uint16_t a0;        // parity
+  uint16_t a0;        // GATHER / SCATTER / FOLD: parity | vector base << 1
   uint16_t idx16;     // bytes of the index area / 16
   uint32_t a1;        // order m
   uint32_t vref;      // F_VALUES_APART: offset of the value block in the value region, in

@@ -565,29 +565,30 @@ __device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, c
   const int l = A.l, L = 2 * l;
   const int m = (int)h.a1;
   const int n = h.M;
+  const int parity = h.a0 & 1, base = h.a0 >> 1;  // GATHER / SCATTER / FOLD
   switch (h.kind) {
     case OP_GATHER: {
-      const IO* beta = reinterpret_cast<const IO*>(A.in) + tri_off(m, L) + h.a0;
-      C* dst = S.buf(h.out_buf);
+      const IO* beta = reinterpret_cast<const IO*>(A.in) + tri_off(m, L) + parity;
+      C* dst = S.buf(h.out_buf) + base;
       for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::from_io(beta[2 * (size_t)j]);
       break;
     }
     case OP_SCATTER: {
-      IO* beta = reinterpret_cast<IO*>(A.out) + tri_off(m, L) + h.a0;
-      const C* src = S.buf(h.in_buf);
+      IO* beta = reinterpret_cast<IO*>(A.out) + tri_off(m, L) + parity;
+      const C* src = S.buf(h.in_buf) + base;
       for (int j = h.io + lane; j < h.io + n; j += 32) beta[2 * (size_t)j] = TR::to_io(src[j]);
       break;
     }
     case OP_FOLD: {
       const IO* G = reinterpret_cast<const IO*>(A.in) + (size_t)m * L;
-      C* dst = S.buf(h.out_buf);
+      C* dst = S.buf(h.out_buf) + base;
       for (int r = h.oo + lane; r < h.oo + n; r += 32) {
         IO gp = G[l + r], gm = G[l - 1 - r];
         if (A.twiddle) {
           gp = TR::io_cmul(gp, A.twiddle[m]);
           gm = TR::io_cmul(gm, A.twiddle[m]);
         }
-        IO e = h.a0 ? TR::io_sub(gp, gm) : TR::io_add(gp, gm);
+        IO e = parity ? TR::io_sub(gp, gm) : TR::io_add(gp, gm);
         if (A.prescale) e = TR::io_scale(e, A.prescale[r]);
         dst[r] = TR::from_io(e);
       }

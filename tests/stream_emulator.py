@@ -103,21 +103,21 @@ def emulate(stream, page_bytes, l, prec, direction, inp, prescale=None, twiddle=
     for h, idx, vals in iter_ops(stream, page_bytes):
         kind, M, K = int(h["kind"]), int(h["M"]), int(h["K"])
         io, oo = int(h["io"]), int(h["oo"])
-        m, p = int(h["a1"]), int(h["a0"])
+        m, p, cb = int(h["a1"]), int(h["a0"]) & 1, int(h["a0"]) >> 1
         src, dst = bufs[int(h["in_buf"])], bufs[int(h["out_buf"])]
         acc = bool(h["flags"] & F_ACCUM)
         tw = 1.0 if twiddle is None else twiddle[m]
         if kind == OP_JOIN:
             continue
         if kind == OP_GATHER:
-            dst[oo:oo + M] = beta[tri[m] + p + 2 * (oo + np.arange(M))]
+            dst[cb + oo:cb + oo + M] = beta[tri[m] + p + 2 * (oo + np.arange(M))]
         elif kind == OP_SCATTER:
-            beta[tri[m] + p + 2 * (io + np.arange(M))] = src[io:io + M]
+            beta[tri[m] + p + 2 * (io + np.arange(M))] = src[cb + io:cb + io + M]
         elif kind == OP_FOLD:
             r = oo + np.arange(M)
             sgn = 1.0 if p == 0 else -1.0
             s = np.ones(M) if prescale is None else prescale[r]
-            dst[oo:oo + M] = s * tw * (G[m, l + r] + sgn * G[m, l - 1 - r])
+            dst[cb + oo:cb + oo + M] = s * tw * (G[m, l + r] + sgn * G[m, l - 1 - r])
         elif kind == OP_CLEAR:
             dst[oo:oo + M] = 0
         elif kind == OP_GZERO:
@@ -165,17 +165,18 @@ def emulate(stream, page_bytes, l, prec, direction, inp, prescale=None, twiddle=
 def _access_sets(h, idx, l):
     """(reads, writes) of one op as sets of hashable locations."""
     kind, M, K = int(h["kind"]), int(h["M"]), int(h["K"])
-    io, oo, m, p = int(h["io"]), int(h["oo"]), int(h["a1"]), int(h["a0"])
+    io, oo, m = int(h["io"]), int(h["oo"]), int(h["a1"])
+    p, cb = int(h["a0"]) & 1, int(h["a0"]) >> 1
     ib, ob = int(h["in_buf"]), int(h["out_buf"])
     R, W = set(), set()
     if kind == OP_GATHER:
-        W |= {("buf", ob, oo + j) for j in range(M)}
+        W |= {("buf", ob, cb + oo + j) for j in range(M)}
         R |= {("beta", m, p + 2 * (oo + j)) for j in range(M)}
     elif kind == OP_SCATTER:
-        R |= {("buf", ib, io + j) for j in range(M)}
+        R |= {("buf", ib, cb + io + j) for j in range(M)}
         W |= {("beta", m, p + 2 * (io + j)) for j in range(M)}
     elif kind == OP_FOLD:
-        W |= {("buf", ob, oo + j) for j in range(M)}
+        W |= {("buf", ob, cb + oo + j) for j in range(M)}
         R |= {("G", m, l + oo + j) for j in range(M)} | {("G", m, l - 1 - oo - j) for j in range(M)}
     elif kind == OP_CLEAR:
         W |= {("buf", ob, oo + j) for j in range(M)}
