@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--l", type=int, default=1024)
     ap.add_argument("--leaf-cols", type=int, default=32)
-    ap.add_argument("--page-bytes", type=int, default=8192)
+    ap.add_argument("--page-bytes", type=int, default=0, help="record chunk bytes (0: the plan default)")
     ap.add_argument("--consumer-warps", type=int, default=0)
     ap.add_argument("--eps", type=float, default=1e-12)
     ap.add_argument("--no-extras", action="store_true", help="skip every leg beside the float64 headline")

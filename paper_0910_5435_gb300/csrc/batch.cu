@@ -29,9 +29,7 @@ struct BatchDir {
   int n_units = 0;
   int buf_ab = 1;
   int num_vecs = 2;
-  const uint8_t* quit_pages = nullptr;  // a stream whose final page ends the launch
-  unsigned long long quit_page = 0;
-  int slot_bytes = 0;  // largest staging slot of the fields (0: a field keeps values in its pages)
+  int slot_bytes = 0;  // largest staging slot of the fields
   sht::SweepConfig cfg;
 };
 
@@ -105,12 +103,10 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
         b->device = v.device;
         b->num_sms = v.num_sms;
         b->page_bytes = v.page_bytes;
-        D.quit_pages = v.pages;
-        D.quit_page = v.quit_page;
         D.cfg.nw = v.consumer_warps;
-        D.cfg.warp_slots = v.warp_slots;
-      } else if (v.device != b->device || v.page_bytes != b->page_bytes) {
-        sht::set_error_detail("sht_batch_create", "plans differ in device or page_bytes");
+      } else if (v.device != b->device || v.page_bytes != b->page_bytes || v.consumer_warps != D.cfg.nw) {
+        // one launch runs every field's items on the same warps and chunk ring
+        sht::set_error_detail("sht_batch_create", "plans differ in device, page_bytes or consumer_warps");
         return SHT_ERR_INVALID_ARG;
       }
       fields[f].pages = v.pages;
@@ -120,7 +116,7 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
       fields[f].l = v.l;
       D.buf_ab = std::max(D.buf_ab, v.buf_ab);
       D.num_vecs = std::max(D.num_vecs, v.num_vecs);
-      D.slot_bytes = (f == 0 || D.slot_bytes > 0) && v.slot_bytes > 0 ? std::max(D.slot_bytes, v.slot_bytes) : 0;
+      D.slot_bytes = std::max(D.slot_bytes, v.slot_bytes);
       for (int u = 0; u < v.n_units; ++u) {
         sht::UnitEntry e = v.units[u];
         e.m = (uint32_t)f;
@@ -128,7 +124,7 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
       }
     }
     std::stable_sort(units.begin(), units.end(),
-                     [](const sht::UnitEntry& a, const sht::UnitEntry& c) { return a.n_pages > c.n_pages; });
+                     [](const sht::UnitEntry& a, const sht::UnitEntry& c) { return a.len16 > c.len16; });
     D.n_units = (int)units.size();
     BCK(cudaSetDevice(b->device));
     BCK(cudaMalloc(&D.d_fields, sizeof(sht::FieldDesc) * fields.size()));
@@ -147,8 +143,7 @@ sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precis
   b->optin = (size_t)optin;
   BCK(sht::sweep_configure(b->q, b->optin));
   for (BatchDir& D : b->dir)
-    if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, D.cfg.nw, D.slot_bytes, 0, b->optin, &D.cfg,
-                           D.cfg.warp_slots))
+    if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, D.cfg.nw, D.slot_bytes, 1, b->optin, &D.cfg))
       return SHT_ERR_UNSUPPORTED;
   return SHT_OK;
 }
@@ -159,19 +154,15 @@ sht_status launch(sht_batch_t b, int d, const void* const* in, void* const* out,
   const BatchDir& D = b->dir[d];
   BCK(cudaSetDevice(b->device));
   sht::SweepArgs a{};
-  a.pages = D.quit_pages;
   a.units = D.d_units;
   a.n_units = D.n_units;
-  a.page_bytes = b->page_bytes;
-  a.nstages = D.cfg.nstages;
+  a.chunk_bytes = b->page_bytes;
   a.buf_ab = D.buf_ab;
-  a.quit_page = D.quit_page;
   a.counter = b->d_scratch + d;
   a.status = b->d_scratch + kDirs;
   a.num_vecs = D.num_vecs;
-  a.staged = D.cfg.staged ? 1 : 0;
   a.slot_bytes = D.cfg.slot_bytes;
-  a.warp_slots = D.cfg.warp_slots;
+  a.warp_slots = 1;
   a.fields = D.d_fields;
   a.field_in = in;
   a.field_out = out;
@@ -307,39 +298,36 @@ sht_status sht_batch_autotune(sht_batch_t b, int direction, const void* const* i
   BatchDir& D = b->dir[direction];
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   BCK(cudaSetDevice(b->device));
-  cudaEvent_t e0, e1;
-  BCK(cudaEventCreate(&e0));
-  BCK(cudaEventCreate(&e1));
+  // The plans' work items are scheduled for their consumer warps, which fixes
+  // the warps and the shared-memory layout of the launch; what remains to
+  // choose is the number of CTAs per SM where more than one fits.
   const sht::SweepConfig keep = D.cfg;
   sht::SweepConfig best = keep;
   float best_ms = -1.f;
   sht_status result = SHT_OK;
-  for (const int shape : {8 * 4 + 2, 12 * 4 + 1, 16 * 4 + 1, 16 * 4 + 2}) {
-    const int nw = shape / 4, ws = shape % 4;  // consumer warps, staging slots per warp
-    for (int nst = 2; nst <= 8 && result == SHT_OK; ++nst) {
-      sht::SweepConfig c;
-      if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, nw, D.slot_bytes, nst, b->optin, &c, ws))
-        continue;
-      if (D.slot_bytes > 0 && !c.staged) continue;  // values would not fit in the slots
-      D.cfg = c;
-      result = launch(b, direction, in, out, stream);  // warm-up
-      if (result != SHT_OK) break;
-      cudaEventRecord(e0, st);
-      for (int r = 0; r < reps && result == SHT_OK; ++r) result = launch(b, direction, in, out, stream);
-      cudaEventRecord(e1, st);
-      if (result != SHT_OK) break;
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        result = SHT_ERR_CUDA;
-        break;
-      }
-      result = sht_batch_last_device_status(b, stream);
-      if (result != SHT_OK) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (best_ms < 0.f || ms < best_ms) {
-        best_ms = ms;
-        best = c;
-      }
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  for (int ctas = 1; ctas <= std::max(1, keep.ctas_per_sm) && result == SHT_OK; ++ctas) {
+    D.cfg = keep;
+    D.cfg.ctas_per_sm = ctas;
+    result = launch(b, direction, in, out, stream);  // warm-up
+    if (result != SHT_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && result == SHT_OK; ++r) result = launch(b, direction, in, out, stream);
+    cudaEventRecord(e1, st);
+    if (result != SHT_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      result = SHT_ERR_CUDA;
+      break;
+    }
+    result = sht_batch_last_device_status(b, stream);
+    if (result != SHT_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best_ms < 0.f || ms < best_ms) {
+      best_ms = ms;
+      best = D.cfg;
     }
   }
   cudaEventDestroy(e0);
@@ -353,7 +341,7 @@ sht_status sht_batch_get_config(sht_batch_t b, int direction, int* consumer_warp
   if (!b || direction < 0 || direction >= kDirs) return SHT_ERR_INVALID_ARG;
   const sht::SweepConfig& c = b->dir[direction].cfg;
   if (consumer_warps) *consumer_warps = c.nw;
-  if (nstages) *nstages = c.nstages;
+  if (nstages) *nstages = 2;  // record chunks in flight per warp
   if (ctas_per_sm) *ctas_per_sm = c.ctas_per_sm;
   if (smem_bytes) *smem_bytes = (int)c.smem;
   return SHT_OK;

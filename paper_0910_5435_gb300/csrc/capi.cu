@@ -44,7 +44,6 @@ struct DevStream {
   sht::UnitEntry* units = nullptr;
   size_t bytes = 0;
   int n_units = 0;
-  unsigned long long quit_page = 0;
   int buf_ab = 0;
 };
 
@@ -76,9 +75,7 @@ struct sht_plan_s {
   bool host_only = false;
   int device = -1;
   int num_sms = 0;
-  int consumer_warps[kNumPrec] = {8, 8, 8};
-  int nstages[kNumPrec] = {4, 4, 4};
-  bool staged[kNumPrec] = {false, false, false};
+  int consumer_warps[kNumPrec] = {16, 16, 16};
   int slot_bytes[kNumPrec] = {0, 0, 0};
   int warp_slots[kNumPrec] = {1, 1, 1};  // staging slots per consumer warp
   int num_vecs[kNumPrec] = {2, 2, 2};
@@ -274,7 +271,6 @@ sht_status upload_streams(sht_plan_t P, int q) {
     DevStream& D = P->dev[q][d];
     D.bytes = S.bytes.size();
     D.n_units = (int)S.units.size();
-    D.quit_page = S.bytes.size() / P->H.page_bytes - 1;
     D.buf_ab = std::max(S.max_buf_ab, 1);
     buf_ab = std::max(buf_ab, D.buf_ab);
     CK(cudaMalloc(&D.pages, D.bytes));
@@ -286,9 +282,6 @@ sht_status upload_streams(sht_plan_t P, int q) {
     CK(cudaMemcpy(D.pages, S.bytes.data(), D.bytes, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(D.units, S.units.data(), sizeof(sht::UnitEntry) * S.units.size(), cudaMemcpyHostToDevice));
   }
-  // Ring depth: two resident CTAs per SM (their warps hide each other's level
-  // boundaries) with at least three pages in flight each if they fit, else
-  // one CTA with a deeper ring.
   int optin = 0;
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
   // the limit is a per-kernel setting shared by every plan: raise it to the
@@ -296,14 +289,14 @@ sht_status upload_streams(sht_plan_t P, int q) {
   CK(sht::sweep_configure(q, (size_t)optin));
   if (q == sht::PREC_SPLIT32) CK(sht::sweep_configure(sht::PREC_SPLIT32_ACC64, (size_t)optin));
   sht::SweepConfig cfg;
-  const int slot_bytes = P->H.values_apart[q] ? P->H.slot_values_for(q) * (q == sht::PREC_FP32 ? 4 : 8) : 0;
-  if (!sht::sweep_choose(q, P->H.page_bytes, buf_ab, nvecs, P->consumer_warps[q], slot_bytes, 0, (size_t)optin,
-                         &cfg, P->warp_slots[q]))
+  const int slot_bytes = P->H.slot_values_for(q) * (q == sht::PREC_FP32 ? 4 : 8);
+  if (!sht::sweep_choose(q, P->H.page_bytes, buf_ab, nvecs, P->consumer_warps[q], slot_bytes, 1, (size_t)optin,
+                         &cfg)) {
+    set_detail("upload", "the sweep's shared memory (vectors, record chunks, staging slots) exceeds the device limit");
     return SHT_ERR_UNSUPPORTED;
-  P->nstages[q] = cfg.nstages;
+  }
   P->ctas_per_sm[q] = cfg.ctas_per_sm;
   P->smem[q] = cfg.smem;
-  P->staged[q] = cfg.staged;
   P->slot_bytes[q] = cfg.slot_bytes;
   P->num_vecs[q] = nvecs;
   P->dev[q][0].buf_ab = P->dev[q][1].buf_ab = buf_ab;
@@ -363,20 +356,17 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.values = D.values;
   a.units = D.units;
   a.n_units = D.n_units;
-  a.page_bytes = P->H.page_bytes;
-  a.nstages = P->nstages[q];
+  a.chunk_bytes = P->H.page_bytes;
   a.l = P->H.l;
   a.buf_ab = D.buf_ab;
-  a.quit_page = D.quit_page;
   a.in = in;
   a.out = out;
   a.prescale = prescale;
   a.twiddle = twiddle;
   a.trace = P->d_trace;
   a.num_vecs = P->num_vecs[q];
-  a.staged = P->staged[q] ? 1 : 0;
   a.slot_bytes = P->slot_bytes[q];
-  a.warp_slots = P->warp_slots[q];
+  a.warp_slots = 1;
   a.counter = P->d_scratch + (kernel_prec(prec) * KIND_COUNT + kind);
   a.status = P->d_scratch + kStatusWord;
   const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
@@ -409,11 +399,9 @@ sht_status sht::prepared_sweep(sht_plan_t P, sht_precision prec, int dir, const 
   a.values = D.values;
   a.units = D.units;
   a.n_units = D.n_units;
-  a.page_bytes = P->H.page_bytes;
-  a.nstages = P->nstages[q];
+  a.chunk_bytes = P->H.page_bytes;
   a.l = P->H.l;
   a.buf_ab = D.buf_ab;
-  a.quit_page = D.quit_page;
   a.in = in;
   a.out = out;
   a.prescale = nullptr;
@@ -422,9 +410,8 @@ sht_status sht::prepared_sweep(sht_plan_t P, sht_precision prec, int dir, const 
   a.counter = nullptr;
   a.status = nullptr;
   a.num_vecs = P->num_vecs[q];
-  a.staged = P->staged[q] ? 1 : 0;
   a.slot_bytes = P->slot_bytes[q];
-  a.warp_slots = P->warp_slots[q];
+  a.warp_slots = 1;
   L->prec = kernel_prec(prec);
   L->consumer_warps = P->consumer_warps[q];
   L->grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
@@ -446,17 +433,15 @@ sht_status sht::stream_view(sht_plan_t P, sht_precision prec, int dir, StreamVie
   v->values = D.values;
   v->units = S.units.data();
   v->n_units = (int)S.units.size();
-  v->quit_page = D.quit_page;
   v->buf_ab = D.buf_ab;
   v->num_vecs = P->num_vecs[q];
   v->l = P->H.l;
   v->page_bytes = P->H.page_bytes;
   v->device = P->device;
   v->num_sms = P->num_sms;
-  v->values_apart = P->H.values_apart[q];
   v->consumer_warps = P->consumer_warps[q];
-  v->slot_bytes = P->H.values_apart[q] ? P->H.slot_values_for(q) * (q == sht::PREC_FP32 ? 4 : 8) : 0;
-  v->warp_slots = P->warp_slots[q];
+  v->slot_bytes = P->H.slot_values_for(q) * (q == sht::PREC_FP32 ? 4 : 8);
+  v->warp_slots = 1;
   v->prescale = P->d_inv_w;
   v->tw_syn = P->d_tw_syn;
   v->tw_ana = P->d_tw_ana;
@@ -489,7 +474,7 @@ sht_status sht_plan_opts_default(sht_plan_opts* o) {
   o->min_band_rows = 32;
   o->host_only = 0;
   o->num_threads = 0;
-  o->page_bytes = 16384;
+  o->page_bytes = 0;
   o->eps_fp32 = 0.0;
   o->consumer_warps = 0;
   o->values_inline = 0;
@@ -585,15 +570,17 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
   } else {
     sht_plan_opts_default(&o);
   }
-  if (o.page_bytes == 0) o.page_bytes = 8192;
+  if (o.page_bytes == 0) o.page_bytes = sht::kDefaultChunkBytes;
   if (o.min_band_rows <= 0) o.min_band_rows = std::max(1, o.leaf_cols / 2);
   if (l < 1 || l > 1024 || !(eps_id > 0.0) || !(eps_id < 1.0)) return SHT_ERR_INVALID_ARG;
   if (o.leaf_cols < 2 || o.leaf_cols > 1024) return SHT_ERR_INVALID_ARG;
-  if (o.page_bytes < 4096 || o.page_bytes > 49152 || (o.page_bytes % 1024) != 0) return SHT_ERR_INVALID_ARG;
+  if (o.page_bytes < sht::kMinChunkBytes || o.page_bytes > sht::kMaxChunkBytes || (o.page_bytes % 256) != 0)
+    return SHT_ERR_INVALID_ARG;
+  if (o.values_inline != 0) return SHT_ERR_INVALID_ARG;  // values always travel apart
   if (o.num_threads < 0) return SHT_ERR_INVALID_ARG;
   if (o.device_build != 0 && (o.device_build != 1 || o.host_only)) return SHT_ERR_INVALID_ARG;
   if (o.device_build_arena_mb < 0) return SHT_ERR_INVALID_ARG;
-  if (o.staging_slots < 0 || o.staging_slots > 2) return SHT_ERR_INVALID_ARG;
+  if (o.staging_slots < 0 || o.staging_slots > 1) return SHT_ERR_INVALID_ARG;
   if (o.consumer_warps != 0 && o.consumer_warps != 8 && o.consumer_warps != 12 && o.consumer_warps != 16)
     return SHT_ERR_INVALID_ARG;
   if (o.slot_values != 0 && (o.slot_values < sht::kMinSlotValues || o.slot_values > sht::kMaxSlotValues ||
@@ -605,14 +592,12 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
   P->opts = o;
   P->opts.plan_cache = nullptr;  // the caller's string outlives only this call
   P->host_only = o.host_only != 0;
-  // one staging slot per warp leaves room for 16 consumer warps, which keep
-  // the FP64 pipe busier than 8 warps with two slots; float32 slots are half
-  // the size, so 16 warps keep two by default
-  for (int q = 0; q < kNumPrec; ++q)
-    P->warp_slots[q] = o.staging_slots ? o.staging_slots : 1;
-  // 0 = 16 consumer warps for every precision
-  for (int q = 0; q < kNumPrec; ++q)
+  // one staging slot per warp; 0 = 16 consumer warps for every precision
+  // (the work items are scheduled for this many warps)
+  for (int q = 0; q < kNumPrec; ++q) {
+    P->warp_slots[q] = 1;
     P->consumer_warps[q] = o.consumer_warps ? o.consumer_warps : 16;
+  }
   PlanHost& H = P->H;
   H.l = l;
   H.eps_id = eps_id;
@@ -622,7 +607,7 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
   H.min_band_rows = o.min_band_rows;
   H.num_threads = o.num_threads;
   H.page_bytes = o.page_bytes;
-  for (int q = 0; q < 3; ++q) H.values_apart[q] = (o.values_inline == 0);
+  H.sched_warps = o.consumer_warps ? o.consumer_warps : 16;
   H.debug_unmet_dep = o.debug_unmet_dependency != 0;
   H.slot_values = o.slot_values;
   H.device_arena_bytes = (long long)o.device_build_arena_mb << 20;

@@ -22,15 +22,13 @@ struct FieldDesc {
 };
 
 struct SweepArgs {
-  const uint8_t* pages;        // stream pages (device)
-  const uint8_t* values;       // value region (device; ops flagged F_VALUES_APART)
-  const UnitEntry* units;      // LPT-ordered unit table (device)
+  const uint8_t* pages;        // record region: the scheduled work items (device)
+  const uint8_t* values;       // value region (device)
+  const UnitEntry* units;      // LPT-ordered item table (device)
   int n_units;
-  int page_bytes;
-  int nstages;                 // pages in flight per CTA (TMA ring depth)
+  int chunk_bytes;             // bytes of one record chunk (a warp's ring holds two)
   int l;
   int buf_ab;                  // elements of shared vectors A and B
-  unsigned long long quit_page;
   const void* in;              // synthesis: beta; analysis: G
   void* out;                   // synthesis: G; analysis: beta
   const double* prescale;      // FOLD: per positive node scale (l entries) or nullptr
@@ -39,9 +37,8 @@ struct SweepArgs {
   unsigned* status;            // device status word (0 = ok)
   unsigned long long* trace;   // kTraceSlots cycle counters accumulated over all CTAs, or nullptr
   int num_vecs;                // shared vectors (buffer ids 0 .. num_vecs-1)
-  int staged;                  // 1: each consumer warp stages op values in shared slots
-  int slot_bytes;              // bytes of one staging slot (staged launches)
-  int warp_slots;              // staging slots per consumer warp: 1, or 2 (also for 0)
+  int slot_bytes;              // bytes of one value staging slot
+  int warp_slots;              // staging slots per consumer warp: 1 or 2
   // Batched launches (fields != nullptr): units[u].m is the item's field f;
   // pages, values, l, prescale and twiddle come from fields[f], the field's
   // input and output from field_in[f] and field_out[f] (device arrays).
@@ -51,29 +48,25 @@ struct SweepArgs {
   int io_align;                // required alignment (bytes) of field_in / field_out entries
 };
 
-// Launch shape of a sweep: consumer warps, ring depth, resident CTAs per
-// SM, dynamic shared memory, and whether op values are staged per warp.
+// Launch shape of a sweep: consumer warps (the warps the streams were
+// scheduled for), resident CTAs per SM, dynamic shared memory, value
+// staging slots per warp and their size.
 struct SweepConfig {
-  int nw = 8;
-  int nstages = 0;
+  int nw = 16;
   int ctas_per_sm = 0;
   size_t smem = 0;
-  bool staged = false;
   int slot_bytes = 0;
-  int warp_slots = 2;
+  int warp_slots = 1;
 };
 
-// Trace slots (clock64 cycles summed over CTAs): consumer warps executing ops,
-// waiting for an op to be published, waiting for its dependencies, waiting
-// for staged values; producer waiting for a free page; parser waiting for a
-// landed page; ops executed; execution split by op class.
+// Trace slots (clock64 cycles summed over CTAs and warps): executing compute
+// ops, executing control ops, waiting for other warps' ops (dependencies),
+// waiting for staged values, waiting for record chunks, waiting at the item
+// barrier; then counts of compute and control ops, items, and the cycles of
+// publishing completions.
 enum TraceSlot {
-  TR_EXEC = 0, TR_WAIT_READY, TR_WAIT_DEP, TR_PROD_WAIT, TR_PARSE_WAIT, TR_OPS, TR_WAIT_VALUES,
-  TR_EXEC_GEMV,    // cycles in compute ops (part of TR_EXEC)
-  TR_EXEC_CTL,     // cycles in control ops (part of TR_EXEC)
-  TR_COMPLETE,     // cycles marking ops done (part of TR_EXEC)
-  TR_N_GEMV,       // compute ops executed
-  TR_N_CTL,        // control ops executed
+  TR_EXEC_GEMV = 0, TR_EXEC_CTL, TR_WAIT_DEP, TR_WAIT_VALUES, TR_WAIT_RECORDS, TR_WAIT_BARRIER,
+  TR_N_GEMV, TR_N_CTL, TR_N_ITEMS, TR_COMPLETE,
   kTraceSlots = 16
 };
 
@@ -81,17 +74,14 @@ enum TraceSlot {
 // applied with float64 accumulation (same streams as PREC_SPLIT32).
 enum SweepPrec { PREC_FP64 = 0, PREC_FP32 = 1, PREC_SPLIT32 = 2, PREC_SPLIT32_ACC64 = 3 };
 
-size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes,
-                        int warp_slots = 2);
-// Picks the ring depth (nstages > 0: exactly that depth) for the given warps:
-// two resident CTAs per SM with at least three pages in flight each if they
-// fit, else one CTA with the deepest ring that fits in optin bytes.  Values
-// are staged in two slots of slot_bytes per warp (0: values inline) when the
-// slots fit beside a ring of two pages.  False if nothing fits.
-bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes, int nstages,
-                  size_t optin, SweepConfig* c, int warp_slots = 2);
+size_t sweep_smem_bytes(int prec, int chunk_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes, int warp_slots);
+// Fills *c for nw consumer warps (8, 12 or 16), warp_slots staging slots of
+// slot_bytes per warp and two record chunks per warp: false if that does not
+// fit in optin bytes of shared memory.
+bool sweep_choose(int prec, int chunk_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes, int warp_slots,
+                  size_t optin, SweepConfig* c);
 cudaError_t sweep_configure(int prec, size_t smem);
-// resident CTAs per SM for this shared-memory size (>= 1); nw = consumer warps (8 or 16)
+// resident CTAs per SM for this shared-memory size (>= 1); nw = consumer warps
 int sweep_blocks_per_sm(int prec, int nw, size_t smem);
 cudaError_t sweep_launch(int prec, int nw, const SweepArgs& a, int grid, size_t smem, cudaStream_t st);
 

@@ -14,7 +14,7 @@ struct PreparedSweep {
   SweepArgs args;   // counter, status and trace left null for the caller to set
   int prec = 0;     // SweepPrec of the kernel
   int consumer_warps = 8;
-  int slot_bytes = 0;                // staging slot per op (0: values in the pages)
+  int slot_bytes = 0;                // staging slot of one warp
   int grid = 1;
   size_t smem = 0;
   int device = 0;
@@ -33,17 +33,15 @@ struct StreamView {
   const uint8_t* values = nullptr;
   const UnitEntry* units = nullptr;  // host copy of the item table (LPT order)
   int n_units = 0;
-  unsigned long long quit_page = 0;
   int buf_ab = 0;
   int num_vecs = 2;
   int l = 0;
-  int page_bytes = 0;
+  int page_bytes = 0;                // record chunk bytes
   int device = 0;
   int num_sms = 0;
-  bool values_apart = true;
   int consumer_warps = 8;
-  int slot_bytes = 0;                // staging slot per op (0: values in the pages)
-  int warp_slots = 2;                // staging slots per consumer warp
+  int slot_bytes = 0;                // staging slot of one warp
+  int warp_slots = 1;                // staging slots per consumer warp
   const double* prescale = nullptr;  // 1 / w_{l+i} (adjoint fold)
   const double2* tw_syn = nullptr;   // e^{i pi m / (4l-1)}: the synthesis phase of eq. phis
   const double2* tw_ana = nullptr;   // its conjugate over 4l-1: the analysis phase

@@ -692,57 +692,16 @@ namespace {
 
 inline size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
 
-// Fills pages with ops from the front and the op table from the back.
-struct PageWriter {
-  std::vector<uint8_t>& buf;
-  size_t PB;
-  size_t page_start = 0, pos = 0;
-  int n_ops = 0;
-  bool open = false;
-  PageWriter(std::vector<uint8_t>& b, size_t pb) : buf(b), PB(pb) {}
-  void new_page() {
-    page_start = buf.size();
-    buf.resize(buf.size() + PB, 0);
-    pos = 0;
-    n_ops = 0;
-    open = true;
-  }
-  // bytes an empty page offers one op
-  size_t fresh_space() const { return (PB - page_table_bytes(1)) & ~size_t(15); }
-  // bytes left for one more op (its table entry reserved)
-  size_t space() const {
-    if (!open) return 0;
-    const size_t used = pos + page_table_bytes(n_ops + 1);
-    return used >= PB ? 0 : ((PB - used) & ~size_t(15));
-  }
-  uint8_t* alloc(size_t bytes) {
-    if (bytes + page_table_bytes(1) > PB) throw std::logic_error("op larger than a page");
-    if (bytes > space()) new_page();
-    uint8_t* page = buf.data() + page_start;
-    uint8_t* p = page + pos;
-    const uint16_t off16 = (uint16_t)(pos >> 4);
-    std::memcpy(page + PB - 4 - 2 * (size_t)n_ops, &off16, 2);
-    ++n_ops;
-    const uint16_t n = (uint16_t)n_ops;
-    std::memcpy(page + PB - 2, &n, 2);
-    pos += bytes;
-    return p;
-  }
+// One op of a work item before scheduling: its header (bytes, npred, idx16
+// and vref are set when the item is encoded), its index lists, and the item
+// op numbers it must wait for.
+struct OpRec {
+  OpHdr h;
+  std::vector<uint16_t> idx;
+  std::vector<int> preds;
+  bool planted = false;  // waits for itself (failure-detection tests)
+  double cost = 0;       // scheduling estimate
 };
-
-// Offsets (bytes) of the ops of one page, from its op table.
-std::vector<size_t> page_ops(const uint8_t* page, size_t PB) {
-  uint16_t n = 0;
-  std::memcpy(&n, page + PB - 2, 2);
-  std::vector<size_t> offs;
-  if (n == kQuitPage) return offs;
-  for (int i = 0; i < n; ++i) {
-    uint16_t o = 0;
-    std::memcpy(&o, page + PB - 4 - 2 * (size_t)i, 2);
-    offs.push_back((size_t)o << 4);
-  }
-  return offs;
-}
 
 // value encodings per precision: 0 = FP64 (double), 1 = FP32 (float), 2 = SPLIT32 (float hi, float lo)
 inline size_t value_size(int prec) { return prec == 1 ? 4 : 8; }
@@ -784,15 +743,15 @@ struct Tracker {
 
 // Writes ops; numbers them within the item and attaches their predecessors.
 struct Emitter {
-  PageWriter& W;
   int prec;
   size_t vs;
   Tracker* T = nullptr;
-  std::vector<uint8_t>* values = nullptr;  // value region of the item, or nullptr: values inline
+  std::vector<uint8_t>* values = nullptr;  // value region of the item
+  std::vector<OpRec> ops;                  // the item's ops, in emission (topological) order
   bool plant_unmet = false;  // next compute op waits for itself (failure-detection tests)
-  int slot_values = kDefaultSlotValues;  // cap on an op's values kept apart
+  int slot_values = kDefaultSlotValues;  // cap on an op's values
+  size_t chunk = kDefaultChunkBytes;     // a record must fit one chunk
   int next_op = 0;    // number of the next op within the item
-  int seg_start = 0;  // first op of the current segment (after its JOIN)
   int positions = 0;
   int l = 0;
   // Shared-vector placement: the ops of one parity block address its vector
@@ -804,7 +763,7 @@ struct Emitter {
   int base = 0;
   int cursor = 0;
   int pool = 0;
-  Emitter(PageWriter& w, int p) : W(w), prec(p), vs(value_size(p)) {}
+  explicit Emitter(int p) : prec(p), vs(value_size(p)) {}
 
   // Chooses the base of a block using `width` positions of each vector.
   void place(int width) {
@@ -820,14 +779,11 @@ struct Emitter {
     h.flags = flags;
     return h;
   }
-  // Page bytes of an op with nidx index entries and nval values, leaving room
-  // for the largest predecessor list (the actual list may be shorter).  With
-  // values kept apart the page holds only the header and indices, and the
-  // value block must fit one warp's staging slot (slot_values values).
-  size_t bytes_of(size_t nidx, size_t nval) const {
-    const size_t meta = sizeof(OpHdr) + pad16(2 * (nidx + kMaxPred));
-    if (values) return nval <= (size_t)slot_values ? meta : ~size_t(0) / 2;
-    return meta + pad16(vs * nval);
+  // Whether an op with nidx index entries and nval values is allowed: its
+  // record (with room for a predecessor per warp and the planted one) fits a
+  // chunk and its value block fits one warp's staging slot.
+  bool fits(size_t nidx, size_t nval) const {
+    return sizeof(OpHdr) + pad16(2 * (nidx + kMaxWarps + 1)) <= chunk && nval <= (size_t)slot_values;
   }
 
   // Reads and writes of one op, as keys: (vec << 20 | pos) for shared
@@ -920,61 +876,44 @@ struct Emitter {
       }
   }
 
-  // Writes a raw op with the given predecessor list (numbers within the item).
+  // Appends an op with the given predecessors (op numbers within the item);
+  // its values go to the item's value region now.
   void raw(OpHdr h, const std::vector<int>& preds, const std::vector<uint16_t>& idx,
            const std::vector<double>& vals) {
     const int t = next_op++;
-    std::vector<uint16_t> all;
-    all.reserve(preds.size() + idx.size());
-    for (int u : preds) {
-      if (t - u <= 0 || t - u > 65535) throw std::logic_error("predecessor out of range");
-      all.push_back((uint16_t)(t - u));
-    }
-    if (plant_unmet && !all.empty() && h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) {
-      all[0] = 0;  // delta 0: the op's own completion, which can never come first
-      plant_unmet = false;
-    }
-    all.insert(all.end(), idx.begin(), idx.end());
-    h.npred = (uint16_t)preds.size();
-    const size_t ib = pad16(2 * all.size());
-    h.idx16 = (uint16_t)(ib / 16);
-    const size_t vb = pad16(vs * vals.size());
-    const bool apart = values != nullptr && !vals.empty();
-    if (apart) {
-      h.flags |= F_VALUES_APART;
+    OpRec r;
+    if (!vals.empty()) {
+      const size_t vb = pad16(vs * vals.size());
       h.vref = (uint32_t)(values->size() / 16);  // relative to the item; rebased when items are joined
       const size_t at = values->size();
       values->resize(at + vb, 0);
       for (size_t i = 0; i < vals.size(); ++i) put_value(values->data() + at, prec, i, vals[i]);
     }
-    h.bytes = (uint32_t)(sizeof(OpHdr) + ib + (apart ? 0 : vb));
-    uint8_t* p = W.alloc(h.bytes);
-    std::memcpy(p, &h, sizeof(OpHdr));
-    if (!all.empty()) std::memcpy(p + sizeof(OpHdr), all.data(), 2 * all.size());
-    if (!apart) {
-      uint8_t* v = p + sizeof(OpHdr) + ib;
-      for (size_t i = 0; i < vals.size(); ++i) put_value(v, prec, i, vals[i]);
+    r.h = h;
+    r.idx = idx;
+    r.preds = preds;
+    for (int u : preds)
+      if (u < 0 || u >= t) throw std::logic_error("predecessor out of range");
+    if (plant_unmet && h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) {
+      r.planted = true;
+      plant_unmet = false;
     }
+    const double M = h.M, K = h.K;
+    const double per_value = prec == 0 ? 16.0 : prec == 2 ? 9.0 : 5.0;  // cycles of one warp
+    r.cost = (h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) ? 400.0 + per_value * M * K + 8.0 * K
+                                                                   : 300.0 + 4.0 * M;
+    ops.push_back(std::move(r));
   }
 
-  // Opens a work item: a JOIN that waits for every earlier op of the CTA.
+  // Opens a work item: the kernel's item barrier orders it after everything
+  // before, so the tracker starts empty.
   void open_item(int npos) {
     positions = npos;
     next_op = 0;
     cursor = 0;
     base = 0;
-    open_segment();
-  }
-
-  // A JOIN that waits for every earlier op of the CTA.  It starts each item,
-  // and again a segment of an item whose ops would not fit the completion-
-  // tag window: predecessors never reach back past it.
-  void open_segment() {
+    ops.clear();
     T->reset(positions);
-    OpHdr h = hdr(OP_JOIN, F_ITEM_START);
-    T->join = next_op;
-    seg_start = next_op;
-    raw(h, {}, {}, {});
   }
 
   void write(OpHdr h, const std::vector<uint16_t>& idx, const std::vector<double>& vals) {
@@ -1001,19 +940,9 @@ struct Emitter {
       default:
         break;
     }
-    // room for a fan-in JOIN and the op itself in this segment
-    if (next_op + 2 - seg_start >= kMaxItemOps) open_segment();
     std::vector<long long> R, Wr;
     access(h, idx, R, Wr);
     std::vector<int> preds = preds_of(R, Wr);
-    if (preds.empty()) preds.push_back(T->join);
-    if ((int)preds.size() > kMaxPred) {
-      // fan-in through a JOIN op (no data) so that the op itself stays small
-      OpHdr j = hdr(OP_JOIN);
-      const int tj = next_op;
-      raw(j, preds, {}, {});
-      preds.assign(1, tj);
-    }
     const int t = next_op;
     raw(h, preds, idx, vals);
     record(t, R, Wr);
@@ -1035,50 +964,24 @@ struct Emitter {
     }
   }
 
-  // largest piece (<= cap outputs) that fits the current page
+  // Size of the next piece of an op with `remaining` outputs whose record
+  // and values for M outputs are allowed by ok(M).  A warp runs one piece
+  // with one lane per output, or several lanes per output when the piece has
+  // <= 16 outputs, so pieces of 32, 16, 8, ... outputs keep every lane busy;
+  // the last piece takes the remainder.
   template <class F>
-  int fit(int cap, F bytes_for) {
-    int lo = 0, hi = std::min(cap, kMaxM);
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) / 2;
-      if (bytes_for(mid) <= W.space()) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-  }
-  // Size of the next piece of an op with `remaining` outputs.  A warp runs
-  // one piece with one lane per output, or several lanes per output when the
-  // piece has <= 16 outputs, so pieces of 32, 16, 8, ... outputs keep every
-  // lane busy; the last piece takes the remainder.  A partly used page takes
-  // a piece only if it keeps at least min(remaining, 8) outputs.
-  template <class F>
-  int piece(int remaining, F bytes_for) {
-    auto best_in = [&](size_t space) {
-      // candidates: the whole remainder if it fits in one warp, then 32, 16, 8, ...
-      int cands[8];
-      int nc = 0;
-      if (remaining <= kMaxM) cands[nc++] = remaining;
-      for (int p2 = kMaxM; p2 >= 1; p2 /= 2)
-        if (p2 < remaining || (p2 == remaining && nc == 0)) cands[nc++] = p2;
-      for (int c = 0; c < nc; ++c)
-        if (bytes_for(cands[c]) <= space) return cands[c];
-      return 0;
-    };
-    // a fresh page only when this page's space, not the op format (the
-    // value slot), keeps the piece below 8 outputs
-    int mp = best_in(W.space());
-    if (mp < std::min(best_in(W.fresh_space()), 8)) {
-      W.new_page();
-      mp = best_in(W.space());
-    }
-    if (mp <= 0) throw std::logic_error("op does not fit in a page");
-    return mp;
+  int piece(int remaining, F ok) {
+    if (remaining <= kMaxM && ok(remaining)) return remaining;
+    for (int p2 = kMaxM; p2 >= 1; p2 /= 2)
+      if (p2 <= remaining && ok(p2)) return p2;
+    throw std::logic_error("op does not fit a record chunk and a staging slot");
   }
 
   // y[oo + o] = z[io + skel[o]] + sum_s T[s][o] z[io + red[s]]
   void syn_interp(const IdBlock& b, uint8_t in_buf, uint8_t out_buf) {
     const int k = b.k, K = b.nin - b.k;
     for (int o0 = 0; o0 < k;) {
-      const int mp = piece(k - o0, [&](int M) { return bytes_of((size_t)K + M, (size_t)K * M); });
+      const int mp = piece(k - o0, [&](int M) { return fits((size_t)K + M, (size_t)K * M); });
       OpHdr h = hdr(OP_SYN_INTERP);
       h.in_buf = in_buf;
       h.out_buf = out_buf;
@@ -1102,7 +1005,7 @@ struct Emitter {
   void dense(uint8_t kind, uint8_t flags, int M, int K, GetV getv, uint8_t in_buf, int io, uint8_t out_buf, int oo,
              int m = 0) {
     for (int o0 = 0; o0 < M;) {
-      const int mp = piece(M - o0, [&](int Mp) { return bytes_of(0, (size_t)K * Mp); });
+      const int mp = piece(M - o0, [&](int Mp) { return fits(0, (size_t)K * Mp); });
       OpHdr h = hdr(kind, flags);
       h.in_buf = in_buf;
       h.out_buf = out_buf;
@@ -1130,9 +1033,9 @@ struct Emitter {
       const size_t extra = skel_done ? 0 : (size_t)k;
       int mp = 0;
       if (rem > 0) {
-        mp = piece(rem, [&](int M) { return bytes_of((size_t)M + extra, (size_t)k * M); });
-      } else if (bytes_of(extra, 0) > W.space()) {
-        W.new_page();
+        mp = piece(rem, [&](int M) { return fits((size_t)M + extra, (size_t)k * M); });
+      } else if (!fits(extra, 0)) {
+        throw std::logic_error("skeleton pass-through does not fit a record chunk");
       }
       OpHdr h = hdr(OP_ANA_INTERP, (uint8_t)((skel_done ? 0 : F_SKEL) | (accum ? F_ACCUM : 0)));
       h.in_buf = in_buf;
@@ -1352,12 +1255,108 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
   }
 }
 
+// Schedules the ops of one work item onto nw warps and encodes the item
+// (ItemHeader, WarpRange[nw], then each warp's record stream in chunks of
+// `chunk` bytes; see sht_stream.h).  List scheduling in emission order: an
+// op goes to the warp on which it can start first (its predecessors'
+// estimated finish times against each warp's estimated free time), so each
+// warp's list is in the emission order, a topological order of the item's
+// dependency graph.  Returns the item bytes (a multiple of 16).
+void encode_item(const std::vector<OpRec>& ops, int nw, size_t chunk, std::vector<uint8_t>& out) {
+  const int n = (int)ops.size();
+  std::vector<double> fin(n, 0.0), wfree(nw, 0.0);
+  std::vector<int> warp(n), pos(n), cnt(nw, 0);
+  for (int t = 0; t < n; ++t) {
+    double ready = 0;
+    for (int u : ops[t].preds) ready = std::max(ready, fin[u]);
+    int best = 0;
+    double best_start = std::max(wfree[0], ready);
+    for (int w = 1; w < nw; ++w) {
+      const double st = std::max(wfree[w], ready);
+      if (st < best_start) {
+        best_start = st;
+        best = w;
+      }
+    }
+    fin[t] = best_start + ops[t].cost;
+    wfree[best] = fin[t];
+    warp[t] = best;
+    pos[t] = cnt[best]++;
+  }
+  for (int w = 0; w < nw; ++w)
+    if (cnt[w] > kMaxWarpOps) throw std::logic_error("work item has too many ops for one warp");
+  std::vector<std::vector<uint8_t>> st(nw);
+  std::vector<int> need(nw);
+  for (int t = 0; t < n; ++t) {
+    const int w = warp[t];
+    std::fill(need.begin(), need.end(), -1);
+    for (int u : ops[t].preds)
+      if (warp[u] != w) need[warp[u]] = std::max(need[warp[u]], pos[u]);
+    std::vector<uint16_t> all;
+    for (int v = 0; v < nw; ++v)
+      if (need[v] >= 0) all.push_back((uint16_t)((v << kPredPosBits) | need[v]));
+    if (ops[t].planted) all.push_back((uint16_t)((w << kPredPosBits) | pos[t]));  // itself: never complete
+    OpHdr h = ops[t].h;
+    h.npred = (uint16_t)all.size();
+    all.insert(all.end(), ops[t].idx.begin(), ops[t].idx.end());
+    const size_t ib = pad16(2 * all.size());
+    h.idx16 = (uint16_t)(ib / 16);
+    h.bytes = (uint32_t)(sizeof(OpHdr) + ib);
+    if (h.bytes > chunk) throw std::logic_error("record larger than a chunk");
+    std::vector<uint8_t>& B = st[w];
+    const size_t in_chunk = B.size() % chunk;
+    if (in_chunk && in_chunk + h.bytes > chunk) B.resize(B.size() + (chunk - in_chunk), 0);  // zero header: chunk ends
+    const size_t at = B.size();
+    B.resize(at + h.bytes, 0);
+    std::memcpy(B.data() + at, &h, sizeof(OpHdr));
+    if (!all.empty()) std::memcpy(B.data() + at + sizeof(OpHdr), all.data(), 2 * all.size());
+  }
+  const size_t head = pad16(sizeof(ItemHeader) + sizeof(WarpRange) * (size_t)nw);
+  size_t total = head;
+  for (int w = 0; w < nw; ++w) total += st[w].size();
+  out.assign(total, 0);
+  ItemHeader ih{};
+  ih.magic = kItemMagic;
+  ih.nw = (uint16_t)nw;
+  ih.n_ops = (uint32_t)n;
+  std::memcpy(out.data(), &ih, sizeof(ih));
+  size_t off = head;
+  for (int w = 0; w < nw; ++w) {
+    WarpRange r{(uint32_t)off, (uint32_t)st[w].size()};
+    std::memcpy(out.data() + sizeof(ItemHeader) + sizeof(WarpRange) * (size_t)w, &r, sizeof(r));
+    if (!st[w].empty()) std::memcpy(out.data() + off, st[w].data(), st[w].size());
+    off += st[w].size();
+  }
+}
+
+// Calls fn(header) for every record of an encoded item.
+template <class Fn>
+void for_each_record(uint8_t* item, size_t chunk, Fn fn) {
+  ItemHeader ih;
+  std::memcpy(&ih, item, sizeof(ih));
+  for (int w = 0; w < ih.nw; ++w) {
+    WarpRange r;
+    std::memcpy(&r, item + sizeof(ItemHeader) + sizeof(WarpRange) * (size_t)w, sizeof(r));
+    size_t p = 0;
+    while (p < r.bytes) {
+      OpHdr* h = reinterpret_cast<OpHdr*>(item + r.off + p);
+      if (h->bytes == 0) {
+        p = (p / chunk + 1) * chunk;
+        continue;
+      }
+      fn(h);
+      p += h->bytes;
+    }
+  }
+}
+
 }  // namespace
 
 void emit_streams(PlanHost& P, int prec) {
   const int L = 2 * P.l;
   const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
-  const size_t PB = (size_t)P.page_bytes;
+  const size_t CH = (size_t)P.page_bytes;
+  const int NW = P.sched_warps;
   int positions = 1;
   for (const UnitFact& U : F) {
     positions = std::max({positions, U.n, U.rows});
@@ -1389,59 +1388,58 @@ void emit_streams(PlanHost& P, int prec) {
       for (auto& e : errors)
         if (!e.empty()) throw std::runtime_error(e);
     };
-    // emits a list of orders as one work item
-    const bool apart = P.values_apart[prec];
+    // emits a list of orders as one scheduled work item; returns its op count
     auto emit_item = [&](const std::vector<int>& ms, std::vector<uint8_t>& out, std::vector<uint8_t>& vals) -> int {
-      PageWriter W(out, PB);
-      W.new_page();
-      Emitter E(W, prec);
+      Emitter E(prec);
       Tracker T;
       E.T = &T;
       E.l = P.l;
-      E.values = apart ? &vals : nullptr;
+      E.values = &vals;
       E.plant_unmet = P.debug_unmet_dep && std::find(ms.begin(), ms.end(), 0) != ms.end();
       E.slot_values = P.slot_values_for(prec);
+      E.chunk = CH;
       E.pool = positions - 1;
       E.open_item(positions);
       for (int m : ms) emit_unit(P, prec, dir, m, E);
+      encode_item(E.ops, NW, CH, out);
       return E.next_op;
     };
     // pass 1: every order alone (its size decides the packing)
     std::vector<std::vector<uint8_t>> per(L), per_vals(L);
     std::vector<int> nops(L);
     run_parallel(L, [&](int m) { nops[m] = emit_item({m}, per[m], per_vals[m]); });
-    // sizes for packing count the value bytes as if they were in pages
-    auto work_pages = [&](int m) { return (per[m].size() + per_vals[m].size() + PB - 1) / PB; };
-    size_t total_pages = 0;
-    for (int m = 0; m < L; ++m) total_pages += work_pages(m);
+    // work of an order: its record and value bytes, in units of 1 KB
+    auto work_kb = [&](int m) { return (per[m].size() + per_vals[m].size() + 1023) / 1024; };
+    size_t total_kb = 0;
+    for (int m = 0; m < L; ++m) total_kb += work_kb(m);
     // Work items: orders in decreasing size, packed with guided sizes: an
-    // item takes about remaining / (2 x 152) pages of the work not yet
-    // packed (152: the SMs of the GB300 the persistent kernel runs one CTA
-    // on each), at least 4, so the queue starts with large items and ends
-    // with small ones that even out the CTAs' finishing times; more than one
-    // order per item where they fit, so the tail of one overlaps the next;
-    // fewer than kMaxItemOps ops (the completion-tag window).
+    // item takes about remaining / (2 x 152) of the work not yet packed
+    // (152: the SMs of the GB300 the persistent kernel runs one CTA on each),
+    // at least 32 KB, so the queue starts with large items and ends with
+    // small ones that even out the CTAs' finishing times; more than one order
+    // per item where they fit, so the tail of one overlaps the next; at most
+    // kMaxWarpOps ops (so no warp's position overflows a pred entry).
     constexpr size_t kGuideCtas = 2 * 152;
     std::vector<int> order(L);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work_pages(a) > work_pages(b); });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work_kb(a) > work_kb(b); });
     std::vector<std::vector<int>> items;
     std::vector<int> cur;
-    size_t cur_pages = 0, remaining = total_pages;
+    size_t cur_kb = 0, remaining = total_kb;
     int cur_ops = 0;
-    size_t target = std::max<size_t>(4, remaining / kGuideCtas);
+    size_t target = std::max<size_t>(32, remaining / kGuideCtas);
     for (int m : order) {
-      const size_t pg = work_pages(m);
-      if (!cur.empty() && (cur_pages + pg > target || cur_ops + nops[m] >= kMaxItemOps)) {
+      const size_t kb = work_kb(m);
+      if (!cur.empty() && (cur_kb + kb > target || cur_ops + nops[m] > kMaxWarpOps)) {
         items.push_back(cur);
-        remaining -= std::min(remaining, cur_pages);
-        target = std::max<size_t>(4, remaining / kGuideCtas);
+        remaining -= std::min(remaining, cur_kb);
+        target = std::max<size_t>(32, remaining / kGuideCtas);
         cur.clear();
-        cur_pages = 0;
+        cur_kb = 0;
         cur_ops = 0;
       }
       cur.push_back(m);
-      cur_pages += pg;
+      cur_kb += kb;
       cur_ops += nops[m];
     }
     if (!cur.empty()) items.push_back(cur);
@@ -1462,56 +1460,40 @@ void emit_streams(PlanHost& P, int prec) {
 
     Stream& S = P.streams[prec][dir];
     S.units.clear();
-    // offsets of every item in the joined page and value regions
+    // offsets of every item in the joined record and value regions
     std::vector<size_t> byte_off(items.size()), val_off(items.size());
-    size_t nbytes = 0, nvals = 0, pages = 0;
+    size_t nbytes = 0, nvals = 0;
     for (int it : iorder) {
       byte_off[it] = nbytes;
       val_off[it] = nvals;
       UnitEntry e;
-      e.first_page = pages;
-      e.n_pages = (uint32_t)(item_bytes[it].size() / PB);
+      e.off16 = nbytes / 16;
+      e.len16 = (uint32_t)(item_bytes[it].size() / 16);
       e.m = (uint32_t)items[it][0];
       S.units.push_back(e);
       nbytes += item_bytes[it].size();
       nvals += item_vals[it].size();
-      pages += e.n_pages;
     }
     if (nvals / 16 > 0xFFFFFFFFull) throw std::runtime_error("value region exceeds 64 GB");
     ByteBuf().swap(S.bytes);
     ByteBuf().swap(S.values);
-    S.bytes.resize(nbytes + PB);
+    S.bytes.resize(std::max<size_t>(nbytes, 16));
     S.values.resize(nvals);
     // rebase each item's value references onto the joined value region and
     // copy it into place, items in parallel
     run_parallel((int)items.size(), [&](int it) {
       const uint32_t base16 = (uint32_t)(val_off[it] / 16);
       std::vector<uint8_t>& B = item_bytes[it];
-      if (base16 && !item_vals[it].empty()) {
-        for (size_t pg = 0; pg < B.size() / PB; ++pg) {
-          uint8_t* page = B.data() + pg * PB;
-          for (size_t off : page_ops(page, PB)) {
-            OpHdr* h = reinterpret_cast<OpHdr*>(page + off);
-            if (h->flags & F_VALUES_APART) h->vref += base16;
-          }
-        }
-      }
+      if (base16 && !item_vals[it].empty())
+        for_each_record(B.data(), CH, [&](OpHdr* h) {
+          if (h->kind >= OP_SYN_INTERP && h->kind <= OP_ANA_INTERP) h->vref += base16;
+        });
       if (!B.empty()) std::memcpy(S.bytes.data() + byte_off[it], B.data(), B.size());
       if (!item_vals[it].empty())
         std::memcpy(S.values.data() + val_off[it], item_vals[it].data(), item_vals[it].size());
       std::vector<uint8_t>().swap(B);
       std::vector<uint8_t>().swap(item_vals[it]);
     });
-    // trailing QUIT page: op count kQuitPage (and a single op of kind 0xFF)
-    // ends the consumer loop
-    uint8_t* quit = S.bytes.data() + nbytes;
-    std::memset(quit, 0, PB);
-    OpHdr q;
-    std::memset(&q, 0, sizeof(q));
-    q.bytes = sizeof(OpHdr);
-    q.kind = OP_QUIT;
-    std::memcpy(quit, &q, sizeof(q));
-    std::memcpy(quit + PB - 2, &kQuitPage, 2);
     // blocks are placed anywhere in the first positions - 1 elements
     S.max_buf_ab = positions - 1;
     S.num_vecs = 2;

@@ -90,9 +90,9 @@ struct UninitAlloc : std::allocator<T> {
 using ByteBuf = std::vector<uint8_t, UninitAlloc<uint8_t>>;
 
 struct Stream {
-  ByteBuf bytes;                     // n_pages * page_bytes
-  ByteBuf values;                    // value region (ops with F_VALUES_APART)
-  std::vector<UnitEntry> units;      // LPT order
+  ByteBuf bytes;                     // record region (the work items)
+  ByteBuf values;                    // value region (the compute ops' value blocks)
+  std::vector<UnitEntry> units;      // item table, LPT order
   int max_buf_ab = 0;                // elements needed in each shared vector
   int num_vecs = 2;                  // shared vectors used
 };
@@ -100,14 +100,15 @@ struct Stream {
 struct PlanHost {
   int l = 0;
   double eps_id = 0, eps_fp32 = 0, trim_eps = 0;
-  int leaf_cols = 64, min_band_rows = 32, num_threads = 0, page_bytes = 8192;
+  int leaf_cols = 64, min_band_rows = 32, num_threads = 0;
+  int page_bytes = kDefaultChunkBytes;  // record chunk bytes (plan option page_bytes)
   int slot_values = 0;  // cap on the values of one op kept apart (0: per precision, below)
   // The value cap of one precision's ops (prec 0 float64, 1 float32, 2 split):
   // by default one 8 KB staging slot's worth (1024 8-byte or 2048 4-byte values).
   int slot_values_for(int prec) const {
     return slot_values ? slot_values : (prec == 1 ? 2 * kDefaultSlotValues : kDefaultSlotValues);
   }
-  bool values_apart[3] = {true, true, true};  // per precision: value blocks outside the pages
+  int sched_warps = 16;  // consumer warps the work items are scheduled for (plan option consumer_warps)
   bool debug_unmet_dep = false;  // plant a never-met predecessor (failure-detection tests)
   long long device_arena_bytes = 0;  // device build: record arena limit (0 = automatic)
   // Gauss-Legendre nodes (all 2l, ascending), weights, and sin theta_{l+i} =

@@ -5,22 +5,26 @@
 // synthesis (coefficients -> node values), 1 is analysis (the transposed
 // application, Section 2.2 remark after Figure multi).
 //
-// A stream is a sequence of fixed-size PAGES (page_bytes each, the unit of
-// one TMA bulk copy), plus, for plans that keep values apart, a VALUE REGION
-// that the executing warp reads directly (coalesced streaming loads): then
-// pages carry only headers and index lists, so the ring of pages in shared
-// memory spans many more ops.  A work item (one large order m, or several small
-// ones) owns a contiguous run of pages; the item table lists them in
-// decreasing size (LPT order for the persistent kernel's work queue).  A
-// page holds a sequence of OPS, each 16-byte aligned:
+// A stream has a RECORD REGION and a VALUE REGION.  The record region is a
+// sequence of WORK ITEMS (one large order m, or several small ones), each
+// starting on a 16-byte boundary; the item table lists them in decreasing
+// size (LPT order for the persistent kernel's work queue).  The planner has
+// already SCHEDULED every op of an item onto one of the nw consumer warps of
+// a CTA (list scheduling over the item's dependency graph, plan option
+// consumer_warps), so an item holds one record stream per warp:
 //
-//   [OpHdr 32 B][uint16 index lists, padded to 16 B][values, padded to 16 B]
+//   ItemHeader (16 B) | WarpRange[nw] (8 B each), padded to 16 B |
+//   warp 0's records | warp 1's records | ...
 //
-// from offset 0 up, and ends with an OP TABLE that grows down from the page
-// end: the uint16 at byte page_bytes - 2 is the op count n (kQuitPage marks
-// the final page), and the uint16 at byte page_bytes - 4 - 2 i is the offset
-// of op i in 16-byte units.  The table lets a whole warp publish a page's
-// ops at once.  Between the last op and the table the page is zero.
+// A warp's records are fetched in CHUNKS of chunk_bytes (the plan option
+// page_bytes) by 1-D bulk copies into a two-chunk ring of its own; no record
+// crosses a chunk boundary, and a record header with bytes == 0 ends a
+// chunk early (the rest of it is padding).  A record is
+//
+//   [OpHdr 32 B][uint16 preds[npred]][uint16 index lists], padded to 16 B
+//
+// and its values, if any, are a block of the value region (vref) that the
+// warp bulk-copies into its staging slot before the op runs.
 //
 // Every op is executed by ONE warp.  Compute ops apply a small dense matrix V
 // ([K][M] layout, M fastest: lanes that own consecutive outputs read
@@ -52,14 +56,15 @@
 // offsets also index coefficients or node rows, carry it in a0 >> 1 (a0 & 1
 // is the parity) and address vector position base + j for element j.
 //
-// Ordering: ops are numbered in stream order (per CTA).  Op t lists its
-// predecessors as npred deltas d (op t - d) at the start of its index area:
-// the last writer of every shared position / node row it reads or writes and
-// every reader of a position it overwrites.  It starts once they have all
-// completed, so independent blocks (one butterfly level, the two halves of a
-// merge, consecutive orders of one work item) run concurrently.  A work item
-// opens with a JOIN (F_ITEM_START) that waits for every earlier op; ops with
-// no other predecessor depend on it.  Deltas stay below kDoneWindow.
+// Ordering: a warp runs its records in order.  A record lists the ops of
+// OTHER warps it must wait for, one entry per warp at most: pred = (w << 12)
+// | p means "warp w has completed its ops 0..p of this item" (the last
+// writer of every shared position / node row the op reads or writes and
+// every reader of a position it overwrites, reduced to the latest such op of
+// each warp).  Each warp publishes its progress in shared memory; an item
+// ends with a CTA-wide barrier (the next item reuses the shared vectors).
+// Each warp's list is in one topological order of the item's graph, so the
+// waits cannot form a cycle.
 //
 // Values: float64 (SHT_FP64), float2 {hi, lo} (SHT_SPLIT32) or float
 // (SHT_FP32).  Shared-memory vectors hold complex numbers in the working
@@ -72,7 +77,7 @@
 namespace sht {
 
 enum OpKind : uint8_t {
-  OP_END = 0,
+  OP_END = 0,         // bytes == 0: the rest of the chunk is padding
   OP_GATHER = 1,      // buf[out_buf][b + j] = beta^m_{m+p+2j}, j in [oo, oo + M)  (a0 = p | b << 1, a1 = m)
   OP_SCATTER = 2,     // beta^m_{m+p+2j} = buf[in_buf][b + j], j in [io, io + M)   (a0 = p | b << 1, a1 = m)
   OP_FOLD = 3,        // buf[out_buf][b + r] = s (G[m][l+r] + (-1)^p G[m][l-1-r]), r in [oo, oo + M)
@@ -82,20 +87,15 @@ enum OpKind : uint8_t {
   OP_DENSE = 7,
   OP_DENSE_G = 8,     // (a1 = m)
   OP_ANA_INTERP = 9,
-  OP_JOIN = 10,       // no data; completes when its predecessors have (F_ITEM_START: when
-                      //   every earlier op of the CTA has)
-  OP_QUIT = 0xFF,
 };
 
 enum OpFlags : uint8_t {
   F_ACCUM = 2,        // DENSE_G / ANA_INTERP: accumulate instead of overwrite
   F_SKEL = 4,         // ANA_INTERP: also the skeleton pass-through (nskel entries)
-  F_ITEM_START = 8,   // JOIN opening a work item
-  F_VALUES_APART = 16,  // the value block lives in the stream's value region (see vref)
 };
 
 struct alignas(16) OpHdr {
-  uint32_t bytes;     // size of this op in the page (multiple of 16); 0 terminates the page
+  uint32_t bytes;     // size of this record (multiple of 16); 0 ends the chunk
   uint8_t kind;
   uint8_t flags;
   uint8_t in_buf;     // shared-memory vector ids 0..3
@@ -105,47 +105,59 @@ struct alignas(16) OpHdr {
   uint16_t nskel;     // SYN_INTERP: M; ANA_INTERP with F_SKEL: pass-through inputs
   uint16_t io;        // element offset of the input vector
   uint16_t oo;        // element offset of the output vector / start of a control range
-  uint16_t npred;     // predecessor count; the deltas lead the index area (see above)
+  uint16_t npred;     // entries of preds[]
   uint16_t a0;        // GATHER / SCATTER / FOLD: parity | vector base << 1
-  uint16_t idx16;     // bytes of the index area / 16
+  uint16_t idx16;     // bytes of the index area (preds and index lists) / 16
   uint32_t a1;        // order m
-  uint32_t vref;      // F_VALUES_APART: offset of the value block in the value region, in
-                      //   16-byte units; otherwise the values follow the index area
+  uint32_t vref;      // compute ops: offset of the value block in the value region, in 16-byte units
 };
 static_assert(sizeof(OpHdr) == 32, "OpHdr must be 32 bytes");
 
-// Index area contents (uint16): pred[npred] (deltas), then, with offsets
-// relative to io / oo:
+// Index area contents (uint16): preds[npred], then, with offsets relative
+// to io / oo:
 //   SYN_INTERP: red[K] then skel[M]
 //   ANA_INTERP: red[M] then (F_SKEL) skel[nskel]
 //   others:     none
 
+constexpr uint32_t kItemMagic = 0x53485449u;  // "ITHS"
+struct ItemHeader {
+  uint32_t magic;
+  uint16_t nw;        // consumer warps the item was scheduled for
+  uint16_t reserved;
+  uint32_t n_ops;
+  uint32_t reserved2;
+};
+static_assert(sizeof(ItemHeader) == 16, "ItemHeader must be 16 bytes");
+struct WarpRange {
+  uint32_t off;       // bytes from the item start (multiple of 16)
+  uint32_t bytes;     // length of the warp's record stream (multiple of 16; 0: no ops)
+};
+
 struct UnitEntry {
-  uint64_t first_page;  // index of the item's first page in the stream
-  uint32_t n_pages;
-  uint32_t m;           // first order of the item (informational)
+  uint64_t off16;     // byte offset of the item in the record region / 16
+  uint32_t len16;     // item bytes / 16
+  uint32_t m;         // first order of the item (informational); batches: the field
 };
 static_assert(sizeof(UnitEntry) == 16, "UnitEntry must be 16 bytes");
 
 // Shared-memory vectors A (id 0) and B (id 1), each buf_ab complex elements;
-// the butterfly levels alternate between them, and the two parities of an
-// order use them one after the other.
+// the butterfly levels alternate between them.
 constexpr int kNumVecs = 2;
 
 constexpr int kMaxM = 32;             // outputs per compute op (one warp)
-constexpr int kMaxPred = 32;          // predecessors listed by a data op (more: fan-in JOIN); one warp checks 32 at once
-constexpr int kDoneWindow = 4096;     // completion-tag ring; a segment (ops after an item-start JOIN) holds < kMaxItemOps ops
-constexpr int kMaxItemOps = 3584;
-// F_VALUES_APART: default cap on the values of one op, which fill one warp's
-// staging slot (a plan option).  Smaller slots let more warps fit in shared
-// memory but split the blocks into more ops.
+constexpr int kMaxWarps = 16;         // consumer warps a plan can be scheduled for
+constexpr int kPredPosBits = 12;      // pred entry: (warp << 12) | position
+constexpr int kMaxWarpOps = (1 << kPredPosBits) - 1;  // ops of one warp in one item
+// Default cap on the values of one op: one warp's 8 KB staging slot of 8-byte
+// values (the planner doubles it for 4-byte float32 values).  Smaller slots
+// let more warps fit in shared memory but split the blocks into more ops.
 constexpr int kDefaultSlotValues = 1024;
 constexpr int kMinSlotValues = 128;
 constexpr int kMaxSlotValues = 2048;
 constexpr int kCtlPieces = 8;         // control ops are split into up to this many warp tasks
-constexpr uint16_t kQuitPage = 0xFFFF;  // op count of the stream's final page
-
-// Op table of a page (see the format above).
-inline size_t page_table_bytes(int n_ops) { return 2 * (size_t)(n_ops + 1); }
+// Record chunk: the unit of a warp's record fetches (plan option page_bytes).
+constexpr int kDefaultChunkBytes = 1024;
+constexpr int kMinChunkBytes = 512;
+constexpr int kMaxChunkBytes = 4096;
 
 }  // namespace sht

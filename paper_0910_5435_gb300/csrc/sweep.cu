@@ -5,19 +5,24 @@
 // butterfly of Section 2.2 per parity block) or analysis (the transposed
 // application, Section 2.2 remark after Figure multi).
 //
-// Each CTA is persistent and runs a small dataflow scheduler:
-//   * a producer warp pops work items (orders m) from an LPT-sorted queue
-//     (atomic counter) and streams their factor pages from HBM into any free
-//     stage of a ring in shared memory with 1-D TMA bulk copies
-//     (cp.async.bulk, mbarrier complete_tx), recording the issue order;
-//   * a parser warp follows that order, numbers the ops of every landed page
-//     and publishes them in an op directory;
-//   * the consumer warps each claim the next op number, wait until the op's
-//     listed predecessors have completed (completion tags in shared memory),
-//     and execute it alone: lanes own consecutive outputs (coalesced reads of
-//     the [K][M] value block), tiny ops split the inner dimension over a few
-//     lanes and reduce with warp shuffles.  There is no CTA-wide barrier; the
-//     last warp to finish an op of a page returns the page to the producer.
+// Each CTA is persistent and takes work items (orders m) from an LPT-sorted
+// queue (an atomic counter).  The planner has already scheduled every op of
+// an item onto one of the CTA's warps, so a warp only walks its own list:
+//   * its records (op header, the warps it waits for, index lists) arrive in
+//     1-D bulk copies (cp.async.bulk, mbarrier complete_tx) into a two-chunk
+//     ring of its own, a chunk ahead of the one it reads;
+//   * the values of its next op are bulk-copied into its staging slot as soon
+//     as the current op has read the slot, so the copy overlaps the current
+//     op's end and the next op's waits;
+//   * before an op it waits until the listed warps have published enough
+//     completed ops (one progress word per warp in shared memory), then
+//     executes the op alone: lanes own consecutive outputs (coalesced reads
+//     of the [K][M] value block), tiny ops split the inner dimension over a
+//     few lanes and reduce with warp shuffles; then it publishes its progress;
+//   * all warps meet at the end of an item (the next item reuses the shared
+//     vectors); warp 0 fetches the next item's number during the current one.
+// There is no producer, parser, op directory, claim or completion tag: the
+// per-op protocol is a few shared-memory words.
 //
 // Every wait is bounded: on timeout the kernel records SHT_ERR_TIMEOUT in the
 // device status word, raises the CTA abort flag, stops issuing copies, waits
@@ -32,11 +37,6 @@
 namespace sht {
 namespace {
 
-template <int NW>
-constexpr int threads_for() { return (NW + 2) * 32; }  // consumers + producer + parser
-constexpr int kMaxStages = 16;
-constexpr int kDir = 1024;                            // op directory entries (ring)
-constexpr int kOrd = 64;                              // page issue-order ring (>= stages)
 constexpr long long kTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr unsigned kStatusTimeout = 5;              // SHT_ERR_TIMEOUT
 constexpr unsigned kStatusBadArg = 1;               // SHT_ERR_INVALID_ARG (a field's pointers)
@@ -317,83 +317,6 @@ struct TF32 {
   }
 };
 
-// ------------------------------------------------------------ scheduler
-
-// Shared scheduling state of one CTA.
-struct Sched {
-  int n_ready;    // ops published by the parser (op numbers 0 .. n_ready-1)
-  int n_claimed;  // next op number to hand to a consumer warp
-  int n_done;     // ops completed (any order)
-  int n_issued;   // pages issued by the producer
-  int quit;       // number of the QUIT op once parsed, else -1
-  int abort;      // set when a bounded wait gave up
-  int pending[kMaxStages];  // ops of the page in each stage not yet completed
-  int order[kOrd];          // stage of the i-th issued page (i % kOrd)
-  uint16_t stage_field[kMaxStages];  // field of the page in each stage (batched launches)
-  uint32_t dir[kDir];       // op number % kDir -> (stage << 16) | (byte offset / 16)
-  uint16_t done_tag[kDoneWindow];  // low 16 bits of the last completed op number in each slot
-};
-
-__device__ __forceinline__ int vload(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
-__device__ __forceinline__ void vstore(int* p, int v) { *reinterpret_cast<volatile int*>(p) = v; }
-__device__ __forceinline__ unsigned vload16(const uint16_t* p) {
-  return *reinterpret_cast<const volatile uint16_t*>(p);
-}
-
-// Lane 0 polls until pred() holds (bounded), the warp then agrees on the outcome.
-template <class Pred>
-__device__ __forceinline__ bool warp_wait(Pred pred, Sched* S, unsigned* status, int lane) {
-  int ok = 1;
-  if (lane == 0) {
-    if (!pred()) {
-      const long long t0 = clock64();
-      for (;;) {
-        if (pred()) break;
-        if (vload(&S->abort)) {
-          ok = 0;
-          break;
-        }
-        if (clock64() - t0 > kTimeoutCycles) {
-          atomicCAS(status, 0u, kStatusTimeout);
-          vstore(&S->abort, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-  }
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  __threadfence_block();  // acquire what the producing warps wrote before publishing
-  return ok != 0;
-}
-
-// Every lane polls its own predicate (bounded); returns when all hold.
-template <class Pred>
-__device__ __forceinline__ bool warp_wait_all(Pred pred, Sched* S, unsigned* status) {
-  if (__all_sync(0xffffffffu, pred())) {
-    __threadfence_block();
-    return true;
-  }
-  const long long t0 = clock64();
-  for (;;) {
-    __nanosleep(32);
-    if (__all_sync(0xffffffffu, pred())) break;
-    int bad = 0;
-    if ((threadIdx.x & 31) == 0) {
-      if (vload(&S->abort)) bad = 1;
-      else if (clock64() - t0 > kTimeoutCycles) {
-        atomicCAS(status, 0u, kStatusTimeout);
-        vstore(&S->abort, 1);
-        bad = 1;
-      }
-    }
-    if (__shfl_sync(0xffffffffu, bad, 0)) return false;
-  }
-  __threadfence_block();  // acquire what the predecessor ops wrote
-  return true;
-}
-
 // ------------------------------------------------------------ ops
 
 template <class TR>
@@ -406,28 +329,15 @@ struct Vecs {
 
 __device__ __forceinline__ size_t tri_off(int m, int L) { return (size_t)m * L - (size_t)m * (m - 1) / 2; }
 
-template <bool GLOBAL, class T>
-__device__ __forceinline__ T ldv(const T* p) {
-  if constexpr (GLOBAL) {
-    return __ldcs(p);  // streamed once per launch: evict-first
-  } else {
-    return *p;
-  }
-}
-
 // Accumulates lane o's dot product over the inner indices s = q, q + ks, ...
-// Values come from shared memory (pages) or straight from global memory; the
-// global variant keeps 8 rows of loads in flight per lane (the latency of a
-// streamed HBM read is hidden by the loads of the same warp, not only by
-// other warps).
-template <class TR, bool GLOBAL>
+// of the value block staged in shared memory.
+template <class TR>
 __device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, const typename TR::C* in,
                                                      const uint16_t* idx, bool gather, int M, int K, int o, int q,
                                                      int ks) {
-  using C = typename TR::C;
   using V = typename TR::V;
   using Acc = typename TR::Acc;
-  constexpr int U = GLOBAL ? 8 : 4;
+  constexpr int U = 4;
   // TR::kChains accumulation chains per lane; each extra chain costs a merge
   constexpr int NC = TR::kChains;
   Acc a[NC];
@@ -437,14 +347,14 @@ __device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, 
   for (; s + (U - 1) * ks < K; s += U * ks) {
     V v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = ldv<GLOBAL>(val + (size_t)(s + u * ks) * M + o);
+    for (int u = 0; u < U; ++u) v[u] = val[(size_t)(s + u * ks) * M + o];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int su = s + u * ks;
       TR::fma(a[u % NC], v[u], in[gather ? (int)idx[su] : su]);
     }
   }
-  for (; s < K; s += ks) TR::fma(a[0], ldv<GLOBAL>(val + (size_t)s * M + o), in[gather ? (int)idx[s] : s]);
+  for (; s < K; s += ks) TR::fma(a[0], val[(size_t)s * M + o], in[gather ? (int)idx[s] : s]);
 #pragma unroll
   for (int c = 1; c < NC; ++c) TR::merge(a[0], a[c]);
   return a[0];
@@ -480,12 +390,7 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
   using IO = typename TR::IO;
   const int M = h.M, K = h.K;
   const uint16_t* idx = reinterpret_cast<const uint16_t*>(op + sizeof(OpHdr)) + h.npred;
-  // values: staged in this warp's slot, else streamed from the value region,
-  // else inside the page after the index area
-  const bool from_global = staged == nullptr && (h.flags & F_VALUES_APART) != 0;
-  const V* val = staged ? reinterpret_cast<const V*>(staged)
-                        : from_global ? reinterpret_cast<const V*>(A.values + (size_t)h.vref * 16)
-                                      : reinterpret_cast<const V*>(op + sizeof(OpHdr) + (size_t)h.idx16 * 16);
+  const V* val = reinterpret_cast<const V*>(staged);  // this warp's staging slot
   const C* in = S.buf(h.in_buf) + h.io;
   C* out = S.buf(h.out_buf) + h.oo;
   const bool gather = (h.kind == OP_SYN_INTERP);
@@ -498,9 +403,7 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
     const int ks = c_lanes_per_out[M];
     const int o = (lane * c_inv16[ks]) >> 16, q = lane - o * ks;
     Acc a0 = TR::zero();
-    if (o < M)
-      a0 = from_global ? gemv_dot<TR, true>(val, in, idx, gather, M, K, o, q, ks)
-                       : gemv_dot<TR, false>(val, in, idx, gather, M, K, o, q, ks);
+    if (o < M) a0 = gemv_dot<TR>(val, in, idx, gather, M, K, o, q, ks);
     // segmented tree: after the step with offset d, lane q holds the sum over
     // q .. min(q + 2d - 1, ks - 1) of its segment
     for (int off = 1; off < ks; off <<= 1) {
@@ -612,423 +515,351 @@ __device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, c
   }
 }
 
-// ------------------------------------------------------------ roles
+
+// ------------------------------------------------------------ warps
+
+__device__ __forceinline__ unsigned vload(const unsigned* p) { return *reinterpret_cast<const volatile unsigned*>(p); }
+__device__ __forceinline__ void vstore(unsigned* p, unsigned v) { *reinterpret_cast<volatile unsigned*>(p) = v; }
+
+// Shared control words of one CTA.
+struct Ctl {
+  unsigned progress[kMaxWarps];  // warp w has completed ops 0..n-1 of item seq: seq * 4096 + n
+  unsigned item[2];              // number of item seq at [seq & 1] (>= n_units: the queue is empty)
+  unsigned arrived;              // warps that finished their part of items 0..seq: NW * (seq + 1)
+  unsigned abort;                // set when a bounded wait gave up or a stream was refused
+};
 
 __device__ __forceinline__ void trace_add(const SweepArgs& A, int slot, unsigned long long v) {
   if (A.trace && v) atomicAdd(A.trace + slot, v);
 }
 
-__device__ void producer_loop(const SweepArgs& A, uint8_t* stages, uint64_t* full, uint64_t* empty, Sched* S) {
-  const uint32_t PB = (uint32_t)A.page_bytes;
-  const int NST = A.nstages;
-  volatile int* abort_flag = &S->abort;
-  int uses[kMaxStages];  // pages copied into each stage so far
-  for (int s = 0; s < kMaxStages; ++s) uses[s] = 0;
-  int issued = 0;
-  unsigned long long c_wait = 0;
-  // any stage whose previous page has been fully consumed may be refilled
-  auto free_stage = [&]() -> int {
-    const long long t0 = clock64();
-    for (int spin = 0;; ++spin) {
-      for (int s = 0; s < NST; ++s)
-        if (mbar_try_wait(empty + s, (uint32_t)((uses[s] & 1) ^ 1))) {
-          c_wait += clock64() - t0;
-          return s;
-        }
-      if (*abort_flag) return -1;
-      if (clock64() - t0 > kTimeoutCycles) {
-        atomicCAS(A.status, 0u, kStatusTimeout);
-        *abort_flag = 1;
-        return -1;
-      }
-      __nanosleep(64);
-    }
-  };
-  auto issue = [&](int s, const uint8_t* pages, uint64_t page, int field) {
-    S->stage_field[s] = (uint16_t)field;  // read by the op's warps while the page is pending
-    fence_proxy_async();
-    mbar_arrive_expect_tx(full + s, PB);
-    bulk_g2s(stages + (size_t)s * PB, pages + (size_t)page * PB, PB, full + s);
-    ++uses[s];
-    S->order[issued % kOrd] = s;
-    ++issued;
-    __threadfence_block();
-    vstore(&S->n_issued, issued);
-  };
-  bool ok = true;
-  for (;;) {
-    if (*abort_flag) {
-      ok = false;
-      break;
-    }
-    const unsigned u = atomicAdd(A.counter, 1u);
-    if (u >= (unsigned)A.n_units) {
-      // the last CTA to find the queue empty resets it for the next launch
-      if (u == (unsigned)A.n_units + gridDim.x - 1) atomicExch(A.counter, 0u);
-      break;
-    }
-    const UnitEntry e = A.units[u];
-    const int field = A.fields ? (int)e.m : 0;
-    const uint8_t* pages = A.fields ? A.fields[field].pages : A.pages;
-    if (A.fields) {
-      // a batched field's input and output come from device arrays: check
-      // them before any page of the field is issued
-      const uintptr_t io = reinterpret_cast<uintptr_t>(A.field_in[field]) |
-                           reinterpret_cast<uintptr_t>(A.field_out[field]);
-      if (!A.field_in[field] || !A.field_out[field] || (io & (uintptr_t)(A.io_align - 1))) {
-        atomicCAS(A.status, 0u, kStatusBadArg);
-        *abort_flag = 1;
-        ok = false;
-        break;
-      }
-    }
-    for (uint32_t pg = 0; pg < e.n_pages; ++pg) {
-      const int s = free_stage();
-      if (s < 0) {
-        ok = false;
-        break;
-      }
-      issue(s, pages, e.first_page + pg, field);
-    }
-    if (!ok) break;
-  }
-  if (ok) {
-    const int s = free_stage();
-    if (s >= 0) issue(s, A.pages, A.quit_page, 0);
-  }
-  // never leave the CTA with bulk copies still landing in its shared memory
-  for (int s = 0; s < NST; ++s)
-    if (uses[s] > 0) wait_bounded(full + s, (uint32_t)((uses[s] - 1) & 1), A.status, abort_flag);
-  trace_add(A, TR_PROD_WAIT, c_wait);
+// Records the error (first one wins) and stops the CTA.
+__device__ __forceinline__ void fail(const SweepArgs& A, Ctl* S, unsigned code) {
+  atomicCAS(A.status, 0u, code);
+  vstore(&S->abort, 1u);
 }
 
-// One warp publishes the ops of each landed page, in issue order, from the
-// page's op table: lanes write up to 32 directory entries at once.
-__device__ void parser_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* full, uint64_t* empty,
-                            Sched* S, int lane) {
-  const size_t PB = (size_t)A.page_bytes;
-  uint32_t parsed_bits = 0;  // bit s: parity of the next completion of stage s
-  int ticket = 0;
-  unsigned long long c_wait = 0;
-  for (int k = 0;; ++k) {
-    const long long w0 = clock64();
-    // the k-th issued page: which stage, then wait for its bytes
-    int stage = 0, ok = 1;
+// Lane 0 polls until pred() holds (bounded; the CTA abort flag ends it too),
+// then the warp agrees on the outcome and acquires what was published.
+template <class Pred>
+__device__ __forceinline__ bool warp_wait(Pred pred, const SweepArgs& A, Ctl* S, int lane) {
+  int ok = 1;
+  if (lane == 0 && !pred()) {
+    const long long t0 = clock64();
+    for (unsigned ns = 32;;) {
+      __nanosleep(ns);
+      if (pred()) break;
+      if (vload(&S->abort)) {
+        ok = 0;
+        break;
+      }
+      if (clock64() - t0 > kTimeoutCycles) {
+        fail(A, S, kStatusTimeout);
+        ok = 0;
+        break;
+      }
+      ns = ns < 256 ? 2 * ns : 256;
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __threadfence_block();
+  return ok != 0;
+}
+
+// One warp's walk over its scheduled ops of every item its CTA takes.
+template <class TR, int NW>
+__device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int warp, int lane, uint8_t* ring,
+                          uint64_t* ring_bar, uint8_t* slot, uint64_t* slot_bar) {
+  using Val = typename TR::V;
+  const uint32_t CH = (uint32_t)A.chunk_bytes;
+  const bool tracing = A.trace != nullptr;
+  unsigned long long c_gemv = 0, c_ctl = 0, c_dep = 0, c_val = 0, c_rec = 0, c_bar = 0, c_done = 0;
+  unsigned long long n_gemv = 0, n_ctl = 0, n_items = 0;
+  uint32_t ring_par = 0;   // bit r: parity of ring slot r's next completion
+  uint32_t ring_busy = 0;  // bit r: a copy into ring slot r has not been waited for
+  uint32_t slot_par = 0;   // parity of the staging slot's next completion
+  bool slot_busy = false;  // a copy into the staging slot has not been waited for
+
+  for (unsigned seq = 0;; ++seq) {
+    const unsigned item = vload(&S->item[seq & 1]);
+    if (item >= (unsigned)A.n_units || vload(&S->abort)) break;
+    if (warp == 0 && lane == 0) {
+      // the next item's number, fetched while this one runs; the CTA that
+      // takes the last number past the end resets the queue for the next launch
+      const unsigned u = atomicAdd(A.counter, 1u);
+      if (u == (unsigned)A.n_units + gridDim.x - 1) atomicExch(A.counter, 0u);
+      vstore(&S->item[(seq + 1) & 1], u);
+    }
+    const UnitEntry e = A.units[item];
+    const int field = A.fields ? (int)e.m : 0;
+    const FieldCtx F = field_ctx(A, field);
+    const uint8_t* region = A.fields ? A.fields[field].pages : A.pages;
+    const uint8_t* item_base = region + e.off16 * 16;
+    // this warp's record stream; a stream scheduled for another warp count,
+    // or a batched field with a bad input or output pointer, is refused
+    uint32_t off = 0, len = 0;
     if (lane == 0) {
-      while (vload(&S->n_issued) <= k) {
-        if (vload(&S->abort) || clock64() - w0 > kTimeoutCycles) {
-          if (!vload(&S->abort)) {
-            atomicCAS(A.status, 0u, kStatusTimeout);
-            vstore(&S->abort, 1);
+      const ItemHeader ih = *reinterpret_cast<const ItemHeader*>(item_base);
+      const WarpRange wr = reinterpret_cast<const WarpRange*>(item_base + sizeof(ItemHeader))[warp];
+      bool bad = ih.magic != kItemMagic || ih.nw != NW || (wr.off & 15u) || (wr.bytes & 15u) ||
+                 (uint64_t)wr.off + wr.bytes > (uint64_t)e.len16 * 16;
+      if (A.fields) {
+        const uintptr_t io = reinterpret_cast<uintptr_t>(F.in) | reinterpret_cast<uintptr_t>(F.out);
+        bad = bad || !F.in || !F.out || (io & (uintptr_t)(A.io_align - 1));
+      }
+      if (bad) fail(A, S, kStatusBadArg);
+      off = bad ? 0 : wr.off;
+      len = bad ? 0 : wr.bytes;
+    }
+    off = __shfl_sync(0xffffffffu, off, 0);
+    len = __shfl_sync(0xffffffffu, len, 0);
+    const uint8_t* stream = item_base + off;
+    const uint32_t nch = (len + CH - 1) / CH;
+    auto issue_chunk = [&](uint32_t c) {  // lane 0; chunk c into ring slot c & 1
+      const uint32_t r = c & 1u;
+      const uint32_t bytes = min(CH, len - c * CH);
+      fence_proxy_async();  // earlier reads of the slot precede the copy into it
+      mbar_arrive_expect_tx(ring_bar + r, bytes);
+      bulk_g2s(ring + (size_t)r * CH, stream + (size_t)c * CH, bytes, ring_bar + r);
+    };
+    if (lane == 0)
+      for (uint32_t c = 0; c < nch && c < 2; ++c) issue_chunk(c);
+    ring_busy |= (nch > 0 ? 1u : 0u) | (nch > 1 ? 2u : 0u);
+    auto has_values = [](const OpHdr& h) {
+      return h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP && h.M > 0 && h.K > 0;
+    };
+    // a compute op must fit one warp and its values the staging slot
+    auto sound = [&](const OpHdr& h) {
+      const bool g = h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP;
+      return !g || (h.M <= kMaxM && sizeof(Val) * h.M * h.K <= (size_t)A.slot_bytes);
+    };
+    auto issue_values = [&](const OpHdr& h) {  // lane 0, for a sound op with values
+      const uint32_t vb = (uint32_t)((sizeof(Val) * h.M * h.K + 15) & ~size_t(15));
+      fence_proxy_async();
+      mbar_arrive_expect_tx(slot_bar, vb);
+      bulk_g2s(slot, F.values + (size_t)h.vref * 16, vb, slot_bar);
+    };
+    // Waits for chunk c (all lanes acquire its bytes); false if aborted.
+    uint32_t waited = 0;  // chunks waited for so far
+    auto wait_chunk = [&](uint32_t c) -> bool {
+      for (; waited <= c; ++waited) {
+        const uint32_t r = waited & 1u;
+        const uint32_t ph = (ring_par >> r) & 1u;
+        const long long t0 = tracing ? clock64() : 0;
+        if (!warp_wait([&] { return mbar_try_wait(ring_bar + r, ph); }, A, S, lane)) return false;
+        mbar_try_wait(ring_bar + r, ph);  // each lane's own acquire of the bytes
+        ring_par ^= 1u << r;
+        ring_busy &= ~(1u << r);
+        if (tracing) c_rec += clock64() - t0;
+      }
+      return true;
+    };
+    bool ok = true;
+    bool vals_pending = false;  // the staging slot holds (or will hold) the next value op's block
+    uint32_t rpos = 0, n_done = 0;
+    while (ok && rpos < len) {
+      const uint32_t c = rpos / CH;
+      if (!wait_chunk(c)) {
+        ok = false;
+        break;
+      }
+      const uint8_t* rec = ring + (size_t)(c & 1u) * CH + (rpos - c * CH);
+      const OpHdr h = *reinterpret_cast<const OpHdr*>(rec);
+      if (h.bytes == 0) {  // the rest of chunk c is padding
+        rpos = (c + 1) * CH;
+        __syncwarp();
+        if (lane == 0 && c + 2 < nch) issue_chunk(c + 2);
+        if (c + 2 < nch) ring_busy |= 1u << (c & 1u);
+        continue;
+      }
+      if (h.bytes < sizeof(OpHdr) || (rpos - c * CH) + h.bytes > CH || rpos + h.bytes > len || !sound(h) ||
+          h.npred > 32 || sizeof(OpHdr) + 16 * (size_t)h.idx16 > h.bytes || 2 * (size_t)h.npred > 16 * (size_t)h.idx16) {
+        if (lane == 0) fail(A, S, kStatusBadArg);
+        ok = false;
+        break;
+      }
+      const bool gemv = h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP;
+      if (has_values(h) && !vals_pending) {
+        if (lane == 0) issue_values(h);
+        slot_busy = true;
+      }
+      // wait for the listed warps' progress
+      const long long t1 = tracing ? clock64() : 0;
+      {
+        const uint16_t* pred = reinterpret_cast<const uint16_t*>(rec + sizeof(OpHdr));
+        unsigned want_w = 0, want = 0;
+        const bool mine = lane < h.npred;
+        if (mine) {
+          const unsigned ent = pred[lane];
+          want_w = ent >> kPredPosBits;
+          want = seq * 4096u + (ent & ((1u << kPredPosBits) - 1)) + 1u;
+        }
+        auto met = [&] { return !mine || vload(&S->progress[want_w]) >= want; };
+        if (!__all_sync(0xffffffffu, met())) {
+          const long long t0 = clock64();
+          for (unsigned ns = 32;;) {
+            __nanosleep(ns);
+            if (__all_sync(0xffffffffu, met())) break;
+            int bad = 0;
+            if (lane == 0) {
+              if (vload(&S->abort)) {
+                bad = 1;
+              } else if (clock64() - t0 > kTimeoutCycles) {
+                fail(A, S, kStatusTimeout);
+                bad = 1;
+              }
+            }
+            if (__shfl_sync(0xffffffffu, bad, 0)) {
+              ok = false;
+              break;
+            }
+            ns = ns < 128 ? 2 * ns : 128;
           }
-          ok = 0;
+        }
+        __threadfence_block();  // acquire what the predecessors wrote
+      }
+      if (!ok) break;
+      const long long t2 = tracing ? clock64() : 0;
+      if (has_values(h)) {
+        if (!warp_wait([&] { return mbar_try_wait(slot_bar, slot_par); }, A, S, lane)) {
+          ok = false;
           break;
         }
-        __nanosleep(32);
+        mbar_try_wait(slot_bar, slot_par);  // each lane's own acquire of the copied bytes
+        slot_par ^= 1u;
+        slot_busy = false;
       }
-      if (ok) {
-        __threadfence_block();
-        stage = vload(&S->order[k % kOrd]);
-        ok = wait_bounded(full + stage, (parsed_bits >> stage) & 1u, A.status, &S->abort) ? 1 : 0;
-      }
-    }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (!ok) return;
-    stage = __shfl_sync(0xffffffffu, stage, 0);
-    mbar_try_wait(full + stage, (parsed_bits >> stage) & 1u);  // each lane's acquire of the page bytes
-    parsed_bits ^= 1u << stage;
-    c_wait += clock64() - w0;
-    const uint8_t* page = stages + (size_t)stage * PB;
-    const int n = *reinterpret_cast<const uint16_t*>(page + PB - 2);
-    if (n == kQuitPage) {
-      if (lane == 0) {
-        __threadfence_block();
-        vstore(&S->quit, ticket);
-        trace_add(A, TR_PARSE_WAIT, c_wait);
-      }
-      return;
-    }
-    if (lane == 0) {
-      vstore(&S->pending[stage], n);
-      if (n == 0) mbar_arrive(empty + stage);  // nothing to execute: the stage is free again
-    }
-    __syncwarp();
-    for (int i0 = 0; i0 < n; i0 += 32) {
-      const int cnt = min(32, n - i0);
-      // entry u reuses the slot of op u - kDir: that op must have completed
-      // (so its entry was read); its completion tag says so
-      const int u = ticket + lane;
-      const int prev = (lane < cnt) ? u - kDir : -1;
-      const uint16_t* tag = S->done_tag + (prev >= 0 ? prev % kDoneWindow : 0);
-      const unsigned want = (unsigned)(prev & 0xffff);
-      if (!warp_wait_all([&] { return prev < 0 || vload16(tag) == want; }, S, A.status)) return;
-      if (lane < cnt) {
-        const uint32_t off16 = *reinterpret_cast<const uint16_t*>(page + PB - 4 - 2 * (size_t)(i0 + lane));
-        S->dir[(ticket + lane) % kDir] = ((uint32_t)stage << 16) | off16;
-      }
-      __syncwarp();
-      ticket += cnt;
-      if (lane == 0) {
-        __threadfence_block();
-        vstore(&S->n_ready, ticket);
-      }
-    }
-  }
-}
-
-// An op claimed by a consumer warp.
-struct Claim {
-  int t;               // op number
-  int stage;           // ring stage of its page
-  const uint8_t* op;   // header in the page
-  OpHdr h;
-  int slot;            // staging slot of its values (0 / 1), or -1
-  int field;           // field of its page (batched launches)
-  uint32_t vbytes;     // bytes of its value block
-  bool deferred;       // its copy waits for the warp's only slot to be read
-};
-
-template <class TR>
-__device__ void consumer_loop(const SweepArgs& A, const uint8_t* stages, uint64_t* empty, Sched* S,
-                              const Vecs<TR>& V, int lane, uint8_t* my_slots, uint64_t* my_bars) {
-  using Val = typename TR::V;
-  const int kSlotBytes = A.slot_bytes;
-  const size_t PB = (size_t)A.page_bytes;
-  unsigned long long c_exec = 0, c_ready = 0, c_dep = 0, c_val = 0, n_ops = 0;
-  unsigned long long c_gemv = 0, c_ctl = 0, c_done = 0, n_gemv = 0, n_ctl = 0;
-  const bool tracing = A.trace != nullptr;  // cycle counts only while tracing
-  uint32_t slot_phase = 0u;  // bit s: parity of slot s's next completion
-  uint32_t inflight = 0u;    // bit s: a copy into slot s has not been waited for
-  int next_slot = 0;
-  // with one slot per warp the next op's copy starts only once the current
-  // op has read the slot (other warps cover the copy); with two it travels
-  // while the current op runs
-  const bool one_slot = A.warp_slots == 1;
-
-  // Op numbers are claimed in order; an op is "opened" once it is published:
-  // its header is read and (values kept apart) the bulk copy of its value
-  // block into a free slot starts.  A warp that holds an unexecuted op only
-  // polls for the next one (that op's page may be waiting for the held op's
-  // page to drain); it blocks on publication only when it holds nothing.
-  auto claim_number = [&]() -> int {
-    int t = 0;
-    if (lane == 0) t = atomicAdd(&S->n_claimed, 1);
-    return __shfl_sync(0xffffffffu, t, 0);
-  };
-  auto start_copy = [&](Claim& c) {
-    if (lane == 0) {
-      fence_proxy_async();  // earlier reads of this slot precede the copy into it
-      mbar_arrive_expect_tx(my_bars + c.slot, c.vbytes);
-      const uint8_t* vals = A.fields ? A.fields[c.field].values : A.values;
-      bulk_g2s(my_slots + (size_t)c.slot * kSlotBytes, vals + (size_t)c.h.vref * 16, c.vbytes, my_bars + c.slot);
-    }
-    inflight |= 1u << c.slot;
-    c.deferred = false;
-  };
-  // 1: opened, 0: t is past the end of the stream, 2: not yet published
-  // (poll only), -1: aborted.  holding: the warp holds an op not yet run.
-  auto open = [&](int t, Claim& c, bool block, bool holding) -> int {
-    auto published = [&] {
-      const int q = vload(&S->quit);
-      return vload(&S->n_ready) > t || (q >= 0 && t >= q);
-    };
-    if (block) {
-      const long long t0 = clock64();
-      if (!warp_wait(published, S, A.status, lane)) return -1;
-      c_ready += clock64() - t0;
-    } else {
-      int ok = 0;
-      if (lane == 0) ok = published() ? 1 : 0;
-      if (!__shfl_sync(0xffffffffu, ok, 0)) return 2;
-      __threadfence_block();
-    }
-    const int q = vload(&S->quit);
-    if (q >= 0 && t >= q) return 0;
-    const uint32_t e = S->dir[t % kDir];
-    __syncwarp();
-    c.t = t;
-    c.stage = (int)(e >> 16);
-    c.op = stages + (size_t)c.stage * PB + ((size_t)(e & 0xffffu) << 4);
-    c.h = *reinterpret_cast<const OpHdr*>(c.op);
-    c.field = A.fields ? (int)S->stage_field[c.stage] : 0;
-    c.slot = -1;
-    c.deferred = false;
-    c.vbytes = (uint32_t)((sizeof(Val) * c.h.M * c.h.K + 15) & ~size_t(15));
-    // a block larger than a slot (not emitted by the planner) is streamed instead
-    if ((c.h.flags & F_VALUES_APART) && my_slots && c.vbytes <= (uint32_t)kSlotBytes) {
-      c.slot = one_slot ? 0 : next_slot;
-      next_slot ^= 1;
-      if (one_slot && holding)
-        c.deferred = true;
+      const long long t3 = tracing ? clock64() : 0;
+      if (gemv)
+        run_gemv<TR>(h, rec, V, F, lane, slot);
       else
-        start_copy(c);
-    }
-    return 1;
-  };
-
-  Claim cur, nxt;
-  int rc = open(claim_number(), cur, true, false);
-  while (rc == 1) {
-    const int tn = claim_number();
-    int rn = open(tn, nxt, false, cur.slot >= 0);  // the next op's values travel while this one runs
-    if (rn < 0) break;
-    const long long t1 = tracing ? clock64() : 0;
-    bool ok;
-    if (cur.h.kind == OP_JOIN && (cur.h.flags & F_ITEM_START)) {
-      // a work item starts once every earlier op of this CTA has completed
-      ok = warp_wait([&] { return vload(&S->n_done) >= cur.t; }, S, A.status, lane);
-    } else {
-      // lanes watch the listed predecessors (32 at a time)
-      const uint16_t* pred = reinterpret_cast<const uint16_t*>(cur.op + sizeof(OpHdr));
-      ok = true;
-      for (int base = 0; base < cur.h.npred && ok; base += 32) {
-        const int i = base + lane;
-        const int u = (i < cur.h.npred) ? cur.t - (int)pred[i] : -1;
-        const unsigned want = (unsigned)(u & 0xffff);
-        const uint16_t* slot = S->done_tag + (u >= 0 ? (u % kDoneWindow) : 0);
-        ok = warp_wait_all([&] { return u < 0 || vload16(slot) == want; }, S, A.status);
+        run_control<TR>(h, V, F, lane);
+      const long long t4 = tracing ? clock64() : 0;
+      // the slot has been read: start the next value op's copy, which may sit
+      // in the next chunk (already requested)
+      // (a next op in the next chunk issues its own copy when it starts)
+      vals_pending = false;
+      const uint32_t npos = rpos + h.bytes;
+      if (npos < len && npos / CH == c && (npos - c * CH) + sizeof(OpHdr) <= CH) {
+        const OpHdr& n2 = *reinterpret_cast<const OpHdr*>(ring + (size_t)(c & 1u) * CH + (npos - c * CH));
+        if (n2.bytes != 0 && has_values(n2) && sound(n2)) {
+          __syncwarp();
+          if (lane == 0) issue_values(n2);
+          slot_busy = true;
+          vals_pending = true;
+        }
+      }
+      // publish completion
+      __threadfence_block();
+      __syncwarp();
+      ++n_done;
+      if (lane == 0) vstore(&S->progress[warp], seq * 4096u + n_done);
+      if (tracing) {
+        const long long t5 = clock64();
+        if (gemv) {
+          c_gemv += t4 - t3;
+          ++n_gemv;
+        } else {
+          c_ctl += t4 - t3;
+          ++n_ctl;
+        }
+        c_dep += t2 - t1;
+        c_val += t3 - t2;
+        c_done += t5 - t4;
+      }
+      rpos = npos;
+      if (rpos == len || rpos - c * CH == CH) {  // chunk c fully used: refill its ring slot
+        __syncwarp();
+        if (lane == 0 && c + 2 < nch) issue_chunk(c + 2);
+        if (c + 2 < nch) ring_busy |= 1u << (c & 1u);
       }
     }
     if (!ok) break;
-    const long long t2 = tracing ? clock64() : 0;
-    const uint8_t* staged = nullptr;
-    if (cur.slot >= 0) {
-      uint64_t* bar = my_bars + cur.slot;
-      const uint32_t ph = (slot_phase >> cur.slot) & 1u;
-      if (!warp_wait([&] { return mbar_try_wait(bar, ph); }, S, A.status, lane)) break;
-      mbar_try_wait(bar, ph);  // each lane's own acquire of the copied bytes
-      slot_phase ^= 1u << cur.slot;
-      inflight &= ~(1u << cur.slot);
-      staged = my_slots + (size_t)cur.slot * kSlotBytes;
-    }
-    const long long t3 = tracing ? clock64() : 0;
-    const bool is_gemv = cur.h.kind >= OP_SYN_INTERP && cur.h.kind <= OP_ANA_INTERP;
-    if (is_gemv)
-      run_gemv<TR>(cur.h, cur.op, V, field_ctx(A, cur.field), lane, staged);
-    else if (cur.h.kind != OP_JOIN)
-      run_control<TR>(cur.h, V, field_ctx(A, cur.field), lane);
-    const long long t3b = tracing ? clock64() : 0;
-    if (tracing) {
-      if (is_gemv) {
-        c_gemv += t3b - t3;
-        ++n_gemv;
-      } else {
-        c_ctl += t3b - t3;
-        ++n_ctl;
-      }
-    }
-    __threadfence_block();  // this op's results are visible before it is marked done
+    // every warp has finished this item before any starts the next
+    const long long tb = tracing ? clock64() : 0;
     __syncwarp();
     if (lane == 0) {
-      *reinterpret_cast<volatile uint16_t*>(&S->done_tag[cur.t % kDoneWindow]) = (uint16_t)(cur.t & 0xffff);
-      atomicAdd(&S->n_done, 1);
-      if (atomicSub(&S->pending[cur.stage], 1) == 1) mbar_arrive(empty + cur.stage);
+      __threadfence_block();
+      atomicAdd(&S->arrived, 1u);
     }
-    const long long t4 = tracing ? clock64() : 0;
+    if (!warp_wait([&] { return vload(&S->arrived) >= (unsigned)NW * (seq + 1); }, A, S, lane)) break;
     if (tracing) {
-      c_done += t4 - t3b;
-      c_dep += t2 - t1;
-      c_val += t3 - t2;
-      c_exec += t4 - t3;
-      ++n_ops;
+      c_bar += clock64() - tb;
+      ++n_items;
     }
-    if (rn == 1 && nxt.deferred) start_copy(nxt);  // the slot has been read
-    if (rn == 2) rn = open(tn, nxt, true, false);  // holds nothing now
-    if (rn != 1) break;
-    cur = nxt;
   }
-  // never leave with a bulk copy still landing in this warp's slots
-  for (int s = 0; s < 2; ++s)
-    if (((inflight >> s) & 1u) && lane == 0) wait_bounded(my_bars + s, (slot_phase >> s) & 1u, A.status, &S->abort);
-  __syncwarp();
+  // never leave with a bulk copy still landing in this warp's ring or slot
   if (lane == 0) {
-    trace_add(A, TR_EXEC, c_exec);
-    trace_add(A, TR_WAIT_READY, c_ready);
-    trace_add(A, TR_WAIT_DEP, c_dep);
-    trace_add(A, TR_WAIT_VALUES, c_val);
-    trace_add(A, TR_OPS, n_ops);
+    for (uint32_t r = 0; r < 2; ++r)
+      if ((ring_busy >> r) & 1u) wait_bounded(ring_bar + r, (ring_par >> r) & 1u, A.status, (volatile int*)&S->abort);
+    if (slot_busy) wait_bounded(slot_bar, slot_par, A.status, (volatile int*)&S->abort);
+  }
+  __syncwarp();
+  if (lane == 0 && tracing) {
     trace_add(A, TR_EXEC_GEMV, c_gemv);
     trace_add(A, TR_EXEC_CTL, c_ctl);
-    trace_add(A, TR_COMPLETE, c_done);
+    trace_add(A, TR_WAIT_DEP, c_dep);
+    trace_add(A, TR_WAIT_VALUES, c_val);
+    trace_add(A, TR_WAIT_RECORDS, c_rec);
+    trace_add(A, TR_WAIT_BARRIER, c_bar);
     trace_add(A, TR_N_GEMV, n_gemv);
     trace_add(A, TR_N_CTL, n_ctl);
+    trace_add(A, TR_N_ITEMS, n_items);
+    trace_add(A, TR_COMPLETE, c_done);
   }
 }
 
 // Shared-memory layout of a sweep CTA, used by the kernel and by the host
-// sizing alike: [pages: nst x pb][full, empty barriers: 2 x nst][slot
-// barriers: 2 x nw][Sched] | 128-aligned vectors | 128-aligned staging
-// slots (nw x warp_slots x slot_bytes).
-__host__ __device__ inline size_t sweep_vec_offset(int nst, size_t pb, int nw) {
-  return ((size_t)nst * pb + 16 * (size_t)nst + 16 * (size_t)nw + sizeof(Sched) + 127) & ~size_t(127);
+// sizing alike: | vectors (128-aligned) | per warp: two record chunks, the
+// staging slot | mbarriers: per warp two ring + one slot (+1 spare) | Ctl |.
+__host__ __device__ inline size_t sweep_vec_bytes(size_t c_size, int num_vecs, int buf_ab) {
+  return (c_size * (size_t)num_vecs * (size_t)buf_ab + 127) & ~size_t(127);
 }
-__host__ __device__ inline size_t sweep_slot_offset(size_t vec_off, size_t vec_bytes) {
-  return (vec_off + vec_bytes + 127) & ~size_t(127);
+__host__ __device__ inline size_t sweep_warp_bytes(int chunk_bytes, int slot_bytes) {
+  return (2 * (size_t)chunk_bytes + (size_t)slot_bytes + 127) & ~size_t(127);
 }
 
 template <class TR, int NW>
-__global__ void __launch_bounds__(threads_for<NW>()) bfly_sweep_kernel(const SweepArgs A) {
+__global__ void __launch_bounds__(NW * 32, 1) bfly_sweep_kernel(const SweepArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int NST = A.nstages;
-  const size_t PB = (size_t)A.page_bytes;
-  uint8_t* stages = smem;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * PB);
-  uint64_t* empty = full + NST;
-  uint64_t* slot_bars = empty + NST;  // 2 per consumer warp
-  Sched* S = reinterpret_cast<Sched*>(slot_bars + 2 * NW);
-  const size_t vec_off = sweep_vec_offset(NST, PB, NW);
-  const Vecs<TR> V{reinterpret_cast<typename TR::C*>(smem + vec_off), A.buf_ab};
-  uint8_t* slots =
-      A.staged ? smem + sweep_slot_offset(vec_off, sizeof(typename TR::C) * (size_t)A.num_vecs * A.buf_ab) : nullptr;
-
+  const size_t vec_bytes = sweep_vec_bytes(sizeof(typename TR::C), A.num_vecs, A.buf_ab);
+  const size_t wb = sweep_warp_bytes(A.chunk_bytes, A.slot_bytes);
+  uint8_t* mine = smem + vec_bytes + (size_t)warp * wb;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + vec_bytes + (size_t)NW * wb);
+  Ctl* S = reinterpret_cast<Ctl*>(bars + 4 * NW);
+  const Vecs<TR> V{reinterpret_cast<typename TR::C*>(smem), A.buf_ab};
   if (tid == 0) {
-    for (int s = 0; s < NST; ++s) {
-      mbar_init(full + s, 1);
-      mbar_init(empty + s, 1);
-    }
-    for (int s = 0; s < 2 * NW; ++s) mbar_init(slot_bars + s, 1);
-    S->n_ready = 0;
-    S->n_claimed = 0;
-    S->n_done = 0;
-    S->n_issued = 0;
-    S->quit = -1;
+    for (int s = 0; s < 4 * NW; ++s) mbar_init(bars + s, 1);
+    for (int w = 0; w < kMaxWarps; ++w) S->progress[w] = 0;
+    S->arrived = 0;
     S->abort = 0;
+    const unsigned u = atomicAdd(A.counter, 1u);
+    if (u == (unsigned)A.n_units + gridDim.x - 1) atomicExch(A.counter, 0u);
+    S->item[0] = u;
+    S->item[1] = 0xffffffffu;
     fence_mbar_init();
   }
-  // completion tags start as "op slot - window", which no op number in the
-  // first window matches
-  for (int i = tid; i < kDoneWindow; i += blockDim.x) S->done_tag[i] = (uint16_t)((i - kDoneWindow) & 0xffff);
   __syncthreads();
-
-  if (warp == NW) {
-    if (lane == 0) producer_loop(A, stages, full, empty, S);
-  } else if (warp == NW + 1) {
-    parser_loop(A, stages, full, empty, S, lane);
-  } else {
-    const int ws = A.warp_slots == 1 ? 1 : 2;
-    consumer_loop<TR>(A, stages, empty, S, V, lane, slots ? slots + (size_t)warp * ws * A.slot_bytes : nullptr,
-                      slot_bars + 2 * warp);
-  }
+  warp_loop<TR, NW>(A, S, V, warp, lane, mine, bars + 4 * warp, mine + 2 * (size_t)A.chunk_bytes,
+                    bars + 4 * warp + 2);
 }
 
 template <class TR>
-size_t smem_for(int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes, int warp_slots) {
-  const size_t vec_off = sweep_vec_offset(nstages, (size_t)page_bytes, nw);
-  const size_t vec_bytes = sizeof(typename TR::C) * (size_t)num_vecs * (size_t)buf_ab;
-  if (slot_bytes <= 0) return vec_off + vec_bytes;
-  return sweep_slot_offset(vec_off, vec_bytes) + (size_t)nw * (warp_slots == 1 ? 1 : 2) * slot_bytes;
+size_t smem_for(int chunk_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes) {
+  return sweep_vec_bytes(sizeof(typename TR::C), num_vecs, buf_ab) + (size_t)nw * sweep_warp_bytes(chunk_bytes, slot_bytes) +
+         sizeof(uint64_t) * 4 * (size_t)nw + sizeof(Ctl);
 }
 
 }  // namespace
 
-size_t sweep_smem_bytes(int prec, int page_bytes, int nstages, int buf_ab, int num_vecs, int nw, int slot_bytes,
-                        int warp_slots) {
+size_t sweep_smem_bytes(int prec, int chunk_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes, int warp_slots) {
+  (void)warp_slots;  // one staging slot per warp
   switch (prec) {
-    case PREC_FP64: return smem_for<TF64>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes, warp_slots);
-    case PREC_FP32: return smem_for<TF32>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes, warp_slots);
-    case PREC_SPLIT32_ACC64: return smem_for<TS32A>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes, warp_slots);
-    default: return smem_for<TS32>(page_bytes, nstages, buf_ab, num_vecs, nw, slot_bytes, warp_slots);
+    case PREC_FP64: return smem_for<TF64>(chunk_bytes, buf_ab, num_vecs, nw, slot_bytes);
+    case PREC_FP32: return smem_for<TF32>(chunk_bytes, buf_ab, num_vecs, nw, slot_bytes);
+    case PREC_SPLIT32_ACC64: return smem_for<TS32A>(chunk_bytes, buf_ab, num_vecs, nw, slot_bytes);
+    default: return smem_for<TS32>(chunk_bytes, buf_ab, num_vecs, nw, slot_bytes);
   }
 }
 
@@ -1064,41 +895,31 @@ cudaError_t sweep_configure(int prec, size_t smem) {
 
 int sweep_blocks_per_sm(int prec, int nw, size_t smem) {
   int nb = 0;
-  const cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(prec, nw), (nw + 2) * 32, smem);
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(prec, nw), nw * 32, smem);
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
-bool sweep_choose(int prec, int page_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes, int nstages,
-                  size_t optin, SweepConfig* c, int warp_slots) {
+bool sweep_choose(int prec, int chunk_bytes, int buf_ab, int num_vecs, int nw, int slot_bytes, int warp_slots,
+                  size_t optin, SweepConfig* c) {
   c->nw = nw;
-  c->warp_slots = warp_slots == 1 ? 1 : 2;
-  // staged values need their slots next to a ring of at least two pages
-  c->staged = slot_bytes > 0 &&
-              sweep_smem_bytes(prec, page_bytes, 2, buf_ab, num_vecs, nw, slot_bytes, c->warp_slots) <= optin;
-  c->slot_bytes = c->staged ? slot_bytes : 0;
-  c->nstages = 0;
-  c->ctas_per_sm = 0;
-  c->smem = 0;
-  for (int nst = (nstages > 0 ? nstages : 8); nst >= (nstages > 0 ? nstages : 2); --nst) {
-    const size_t sm = sweep_smem_bytes(prec, page_bytes, nst, buf_ab, num_vecs, nw, c->slot_bytes, c->warp_slots);
-    if (sm > optin) continue;
-    const int ctas = std::min(2, sweep_blocks_per_sm(prec, nw, sm));
-    const bool better = (ctas > c->ctas_per_sm && (nst >= 3 || c->ctas_per_sm == 0)) || c->ctas_per_sm == 0;
-    if (better) {
-      c->nstages = nst;
-      c->ctas_per_sm = ctas;
-      c->smem = sm;
-    }
+  c->warp_slots = 1;
+  (void)warp_slots;
+  c->slot_bytes = slot_bytes;
+  c->smem = sweep_smem_bytes(prec, chunk_bytes, buf_ab, num_vecs, nw, slot_bytes, 1);
+  if (c->smem > optin) {
+    c->ctas_per_sm = 0;
+    return false;
   }
-  return c->nstages > 0;
+  c->ctas_per_sm = std::min(2, sweep_blocks_per_sm(prec, nw, c->smem));
+  return true;
 }
 
 cudaError_t sweep_launch(int prec, int nw, const SweepArgs& a, int grid, size_t smem, cudaStream_t st) {
-  if (a.nstages < 1 || a.nstages > kMaxStages) return cudaErrorInvalidValue;
   if (nw != 8 && nw != 12 && nw != 16) return cudaErrorInvalidValue;
+  if (a.chunk_bytes < kMinChunkBytes || a.chunk_bytes > kMaxChunkBytes || (a.chunk_bytes & 255)) return cudaErrorInvalidValue;
+  if (a.slot_bytes <= 0 || (a.slot_bytes & 15)) return cudaErrorInvalidValue;
   void* args[] = {const_cast<SweepArgs*>(&a)};
-  return cudaLaunchKernel(kernel_for(prec, nw), dim3(grid), dim3((nw + 2) * 32), args, smem, st);
+  return cudaLaunchKernel(kernel_for(prec, nw), dim3(grid), dim3(nw * 32), args, smem, st);
 }
 
 }  // namespace sht

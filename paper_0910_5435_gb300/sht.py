@@ -273,7 +273,7 @@ class Plan:
 
     @property
     def page_bytes(self):
-        """Bytes per factor page in effect for this plan."""
+        """Bytes of one record chunk in effect for this plan (plan option page_bytes)."""
         return self.stats()["page_bytes"]
 
     def stats(self):
@@ -556,8 +556,8 @@ def sht_analyze(plan, prec, values, beta, workspace, stream=None):
                              _stream(stream)), "sht_analyze")
 
 
-TRACE_FIELDS = ("exec", "wait_ready", "wait_dep", "producer_wait", "parser_wait", "ops", "wait_values",
-                "exec_gemv", "exec_control", "complete", "n_gemv", "n_control")
+TRACE_FIELDS = ("exec_gemv", "exec_control", "wait_dep", "wait_values", "wait_records", "wait_barrier",
+                "n_gemv", "n_control", "n_items", "complete")
 
 
 def sht_trace_enable(plan, enable=True):

@@ -1,15 +1,18 @@
 """Host emulation of the butterfly factor streams (test code).
 
-Decodes the page format documented in paper_0910_5435_gb300/csrc/sht_stream.h
-and applies every op with numpy complex128 arithmetic, in stream order (a
-valid serialization of the kernel's concurrent execution).  It separates
-errors of the host precomputation (nodes, recurrence, IDs, op emission) from
-errors of the CUDA kernels.
+Decodes the stream format documented in paper_0910_5435_gb300/csrc/sht_stream.h
+(work items whose ops the planner has scheduled onto the CTA's warps, one
+record stream per warp) and applies every op with numpy complex128
+arithmetic in one valid serialization of the kernel's concurrent execution:
+warps advance in turn, an op only once the ops of other warps it lists have
+run.  It separates errors of the host precomputation (nodes, recurrence,
+IDs, op emission, scheduling) from errors of the CUDA kernels.
 
-``check_races`` verifies the ordering annotations: within a work item (opened
-by a JOIN that waits for everything before it), op t may overlap every earlier
-op that is not among its transitive predecessors, so it must neither write
-anything such an op reads or writes, nor read anything it writes.
+``check_races`` verifies the ordering annotations: within a work item an op
+is ordered after the earlier ops of its own warp and, through its pred
+entries, after ops of other warps (transitively); it may overlap every other
+op of the item, so it must neither write anything such an op reads or
+writes, nor read anything it writes.
 """
 
 import numpy as np
@@ -21,56 +24,89 @@ OPHDR = np.dtype([
 ])
 assert OPHDR.itemsize == 32
 
-OP_GATHER, OP_SCATTER, OP_FOLD, OP_CLEAR, OP_GZERO, OP_SYN, OP_DENSE, OP_DENSE_G, OP_ANA, OP_JOIN = range(1, 11)
-OP_QUIT = 0xFF
-F_ACCUM, F_SKEL, F_ITEM_START, F_VALUES_APART = 2, 4, 8, 16
+OP_GATHER, OP_SCATTER, OP_FOLD, OP_CLEAR, OP_GZERO, OP_SYN, OP_DENSE, OP_DENSE_G, OP_ANA = range(1, 10)
+F_ACCUM, F_SKEL = 2, 4
+ITEM_MAGIC = 0x53485449
+POS_BITS = 12
 
 
-QUIT_PAGE = 0xFFFF
+def iter_items(records, chunk_bytes):
+    """The work items of a record region, in order: for each, a list over
+    warps of that warp's ops as (header, pred entries, index array)."""
+    pos = 0
+    n = len(records)
+    while pos < n:
+        hdr = records[pos:pos + 16].view("<u4")
+        if int(hdr[0]) != ITEM_MAGIC:
+            if not records[pos:].any():  # trailing padding
+                return
+            raise AssertionError(f"no item header at byte {pos}")
+        nw = int(records[pos + 4:pos + 6].view("<u2")[0])
+        ranges = records[pos + 16:pos + 16 + 8 * nw].view("<u4").reshape(nw, 2)
+        head = (16 + 8 * nw + 15) // 16 * 16
+        end = pos + head
+        warps = []
+        for w in range(nw):
+            off, nb = int(ranges[w, 0]), int(ranges[w, 1])
+            assert off % 16 == 0 and nb % 16 == 0, "misaligned warp range"
+            st = records[pos + off:pos + off + nb]
+            end = max(end, pos + off + nb)
+            ops = []
+            p = 0
+            while p < nb:
+                h = st[p:p + 32].view(OPHDR)[0]
+                if int(h["bytes"]) == 0:
+                    p = (p // chunk_bytes + 1) * chunk_bytes  # rest of the chunk is padding
+                    continue
+                b = int(h["bytes"])
+                assert b >= 32 and b % 16 == 0, "bad record size"
+                assert (p % chunk_bytes) + b <= chunk_bytes, "record crosses a chunk boundary"
+                ia = st[p + 32:p + 32 + 16 * int(h["idx16"])].view("<u2")
+                npred = int(h["npred"])
+                ops.append((h, ia[:npred].astype(int), ia[npred:]))
+                p += b
+            warps.append(ops)
+        yield warps
+        pos = (end + 15) // 16 * 16
 
 
-def page_op_offsets(page, page_bytes):
-    """Byte offsets of a page's ops from its op table (None for the final
-    page): the uint16 at page_bytes - 2 is the count, the uint16 at
-    page_bytes - 4 - 2 i the offset of op i in 16-byte units."""
-    n = int(page[page_bytes - 2:page_bytes].view("<u2")[0])
-    if n == QUIT_PAGE:
-        return None
-    tab = page[page_bytes - 2 - 2 * n:page_bytes - 2].view("<u2")[::-1]
-    return [16 * int(o) for o in tab]
+def _serialize(warps):
+    """One valid sequential order of an item's ops: (warp, position) pairs."""
+    nw = len(warps)
+    done = [0] * nw
+    order = []
+    total = sum(len(x) for x in warps)
+    while len(order) < total:
+        progressed = False
+        for w in range(nw):
+            while done[w] < len(warps[w]):
+                preds = warps[w][done[w]][1]
+                if all(done[e >> POS_BITS] > (e & ((1 << POS_BITS) - 1)) for e in preds):
+                    order.append((w, done[w]))
+                    done[w] += 1
+                    progressed = True
+                else:
+                    break
+        if not progressed:
+            raise RuntimeError("the ops of a work item wait for one another in a cycle")
+    return order
 
 
-def iter_ops(stream, page_bytes, with_preds=False):
-    """Yields (header, index array, value bytes) for every op, in order.
-    ``stream`` is the (pages, values) pair of Plan.stream (or the page region
-    alone); the index array excludes the leading predecessor deltas unless
-    with_preds."""
-    if isinstance(stream, tuple):
-        pages, values = stream
-    else:
-        pages, values = stream, None
-    npages = len(pages) // page_bytes
-    for pg in range(npages):
-        page = pages[pg * page_bytes:(pg + 1) * page_bytes]
-        offs = page_op_offsets(page, page_bytes)
-        if offs is None:
-            return
-        end = 0
-        for off in offs:
-            assert off == end, "op table does not chain the ops contiguously"
-            h = page[off:off + 32].view(OPHDR)[0]
-            assert h["bytes"] > 0 and h["kind"] != OP_QUIT
-            end = off + int(h["bytes"])
-            assert end <= page_bytes - 2 - 2 * len(offs), "op runs into the op table"
-            ib = 16 * int(h["idx16"])
-            idx = page[off + 32:off + 32 + ib].view("<u2")
-            if not with_preds:
-                idx = idx[int(h["npred"]):]
-            if h["flags"] & F_VALUES_APART:
-                vals = values[16 * int(h["vref"]):]
+def iter_ops(stream, chunk_bytes, with_preds=False):
+    """Yields (header, index array, value bytes) for every op, work item by
+    work item, each item in one valid serialization.  ``stream`` is the
+    (records, values) pair of Plan.stream.  With with_preds the index array
+    is preceded by the op's pred entries and the header is followed by the
+    op's (warp, position): (header, preds, index array, values, (w, p))."""
+    records, values = stream
+    for warps in iter_items(records, chunk_bytes):
+        for w, p in _serialize(warps):
+            h, preds, idx = warps[w][p]
+            vals = values[16 * int(h["vref"]):] if OP_SYN <= int(h["kind"]) <= OP_ANA else None
+            if with_preds:
+                yield h, preds, idx, vals, (w, p)
             else:
-                vals = page[off + 32 + ib:off + int(h["bytes"])]
-            yield h, idx, vals
+                yield h, idx, vals
 
 
 def decode_values(vals, prec, n):
@@ -87,7 +123,7 @@ def _tri(l):
     return np.concatenate([[0], np.cumsum(L - np.arange(L))])
 
 
-def emulate(stream, page_bytes, l, prec, direction, inp, prescale=None, twiddle=None):
+def emulate(stream, chunk_bytes, l, prec, direction, inp, prescale=None, twiddle=None):
     """Applies a whole stream.  direction 0: inp = beta triangle -> G (2l, 2l);
     direction 1: inp = G -> beta triangle."""
     L = 2 * l
@@ -100,15 +136,13 @@ def emulate(stream, page_bytes, l, prec, direction, inp, prescale=None, twiddle=
     else:
         beta = np.full(tri[-1], np.nan, dtype=np.complex128)
         G = np.asarray(inp, dtype=np.complex128)
-    for h, idx, vals in iter_ops(stream, page_bytes):
+    for h, idx, vals in iter_ops(stream, chunk_bytes):
         kind, M, K = int(h["kind"]), int(h["M"]), int(h["K"])
         io, oo = int(h["io"]), int(h["oo"])
         m, p, cb = int(h["a1"]), int(h["a0"]) & 1, int(h["a0"]) >> 1
         src, dst = bufs[int(h["in_buf"])], bufs[int(h["out_buf"])]
         acc = bool(h["flags"] & F_ACCUM)
         tw = 1.0 if twiddle is None else twiddle[m]
-        if kind == OP_JOIN:
-            continue
         if kind == OP_GATHER:
             dst[cb + oo:cb + oo + M] = beta[tri[m] + p + 2 * (oo + np.arange(M))]
         elif kind == OP_SCATTER:
@@ -206,42 +240,42 @@ def _access_sets(h, idx, l):
     return R, W
 
 
-def check_races(stream, page_bytes, l):
-    """Returns (t, u) op pairs (stream positions) that may overlap but conflict."""
-    ops = list(iter_ops(stream, page_bytes, with_preds=True))
+def check_races(stream, chunk_bytes, l):
+    """Returns ((w, p), (w2, p2)) pairs of ops of one item that may overlap
+    but conflict."""
+    records, _ = stream
     bad = []
-    start = 0
-    while start < len(ops):
-        end = start + 1
-        while end < len(ops) and not (ops[end][0]["kind"] == OP_JOIN and ops[end][0]["flags"] & F_ITEM_START):
-            end += 1
-        anc = []  # transitive predecessors (positions within the item) as int bitsets
+    for warps in iter_items(records, chunk_bytes):
+        order = _serialize(warps)
+        index = {wp: i for i, wp in enumerate(order)}
+        anc = [0] * len(order)  # transitive predecessors as int bitsets over serialized positions
         sets = []
-        for t in range(start, end):
-            h, idx, _ = ops[t]
-            npred = int(h["npred"])
+        for i, (w, p) in enumerate(order):
+            h, preds, idx = warps[w][p]
             a = 0
-            for d in idx[:npred]:
-                u = t - int(d) - start
-                assert 0 <= u < t - start, "predecessor outside its work item"
-                a |= anc[u] | (1 << u)
-            anc.append(a)
-            sets.append(_access_sets(h, idx[npred:], l))
+            if p > 0:
+                j = index[(w, p - 1)]
+                a |= anc[j] | (1 << j)
+            for e in preds:
+                we, pe = e >> POS_BITS, e & ((1 << POS_BITS) - 1)
+                j = index[(we, pe)]
+                a |= anc[j] | (1 << j)
+            anc[i] = a
+            sets.append(_access_sets(h, idx, l))
             Rt, Wt = sets[-1]
-            for u in range(t - start):
-                if (a >> u) & 1:
+            for j in range(i):
+                if (a >> j) & 1:
                     continue
-                Ru, Wu = sets[u]
+                Ru, Wu = sets[j]
                 if (Wt & (Ru | Wu)) or (Rt & Wu):
-                    bad.append((t, start + u))
-        start = end
+                    bad.append(((w, p), order[j]))
     return bad
 
 
-def op_stats(stream, page_bytes):
+def op_stats(stream, chunk_bytes):
     """Counts ops per kind, for plan diagnostics."""
     counts = {}
-    for h, _, _ in iter_ops(stream, page_bytes):
+    for h, _, _ in iter_ops(stream, chunk_bytes):
         k = int(h["kind"])
         counts[k] = counts.get(k, 0) + 1
     return counts

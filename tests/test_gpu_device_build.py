@@ -150,7 +150,7 @@ def test_small_arena_builds_in_waves(sht):
 
 def test_arena_too_small_for_one_block_is_an_error(sht):
     with pytest.raises(sht.ShtError) as e:
-        sht.Plan(1024, 1e-12, leaf_cols=32, page_bytes=8192, device_build=True, device_build_arena_mb=1)
+        sht.Plan(1024, 1e-12, leaf_cols=32, device_build=True, device_build_arena_mb=1)
     assert e.value.code == 1
     assert b"cannot hold one unit" in sht.lib().sht_last_error_detail()
 
@@ -159,7 +159,7 @@ def test_device_build_l1024_sampled_orders(sht):
     """The bench configuration (l = 1024, C = 32, 8 KB pages) built on the
     device, checked on sampled orders against the oracle."""
     l = 1024
-    P = sht.Plan(l, 1e-12, leaf_cols=32, page_bytes=8192, device_build=True)
+    P = sht.Plan(l, 1e-12, leaf_cols=32, device_build=True)
     beta = inputs.random_beta(l, seed=3, decay=True)
     ms = [0, 1, 2, 511, 1024, 1025, 2046, 2047]
     Go = oracle.legendre_synthesis(beta, l, orders=ms)

@@ -42,7 +42,7 @@ def plan(ref):
     __graft_entry__.build()
     from paper_0910_5435_gb300 import sht
     assert torch.cuda.is_available()
-    P = sht.Plan(L, 1e-12, leaf_cols=32, page_bytes=8192)
+    P = sht.Plan(L, 1e-12, leaf_cols=32)
     yield sht, P
     P.close()
 

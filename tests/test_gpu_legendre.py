@@ -174,13 +174,15 @@ def test_misaligned_and_null_pointers_rejected(sht):
         sht.sht_legendre_synthesize(P, 7, b, G)
 
 
-@pytest.mark.parametrize("values_inline", [0, 1])
+@pytest.mark.parametrize("chunk,nw", [(512, 16), (1024, 16), (4096, 8)])
 @pytest.mark.parametrize("prec", [0, 2, 3, 1])
-def test_both_value_layouts_on_gpu(sht, values_inline, prec):
-    """Values streamed by the executing warp, or staged in the TMA pages: same
-    results (float64 layouts agree to rounding; both match the oracle)."""
+def test_record_chunk_sizes_on_gpu(sht, chunk, nw, prec):
+    """Record chunks of 512 B (records packed tightly, many chunk switches),
+    1 KB (the default) and 4 KB (with 8 warps: two 4 KB chunks per warp do
+    not fit beside 16 staging slots): the same ops, both directions match
+    the oracle."""
     l = 128
-    P = plan(sht, l, 16, values_inline=values_inline)
+    P = plan(sht, l, 16, page_bytes=chunk, consumer_warps=nw)
     beta = inputs.random_beta(l, seed=31)
     G = run_synth(sht, P, prec, beta)
     assert rel(G, oracle.legendre_synthesis(beta, l)) < TOL[prec]
@@ -191,12 +193,12 @@ def test_both_value_layouts_on_gpu(sht, values_inline, prec):
 
 def test_l1024_bench_configuration_sampled_orders(sht):
     """Full-size parity at the benchmarked configuration: l = 1024, eps_id =
-    1e-12, leaf_cols 32, 8 KB pages, default warps, beta ~ N(0,1)/(k+1) with
+    1e-12, leaf_cols 32, default record chunks and warps, beta ~ N(0,1)/(k+1) with
     seed 3 (the bench's field), all four precisions, both directions, on
     orders the oracle computes one by one (the first, the last, both parities
     of the middle, and orders near the turning point of the nodes)."""
     l = 1024
-    P = sht.Plan(l, 1e-12, leaf_cols=32, page_bytes=8192)
+    P = sht.Plan(l, 1e-12, leaf_cols=32)
     beta = inputs.random_beta(l, seed=3, decay=True)
     Gin = inputs.random_G(l, seed=4)
     ms = [0, 1, 2, 511, 1024, 1025, 1500, 2046, 2047]
@@ -219,13 +221,13 @@ def test_l1024_bench_configuration_sampled_orders(sht):
 
 
 @pytest.mark.parametrize("prec", [0, 2, 1])
-def test_staging_modes_give_identical_outputs(sht, prec):
-    """One staging slot per warp (16 consumer warps, the default) and two
-    (8 warps) run the same ops with the same arithmetic: bit-identical
-    outputs in both directions."""
+def test_schedules_for_8_and_16_warps_give_identical_outputs(sht, prec):
+    """Work items scheduled for 16 consumer warps (the default) and for 8 run
+    the same ops with the same per-op arithmetic, each after the same
+    predecessors: bit-identical outputs in both directions."""
     l = 128
     a = sht.Plan(l, 1e-12, leaf_cols=16)
-    b = sht.Plan(l, 1e-12, leaf_cols=16, consumer_warps=8, staging_slots=2)
+    b = sht.Plan(l, 1e-12, leaf_cols=16, consumer_warps=8)
     beta = inputs.random_beta(l, seed=31)
     Gin = inputs.random_G(l, seed=32)
     for P in (a, b):

@@ -52,8 +52,8 @@ def test_loaded_plan_outputs_are_identical(sht, tmp_path):
 def test_bench_configuration_from_a_plan_file(sht, tmp_path):
     l = 1024
     path = str(tmp_path / "l1024.plan")
-    P = sht.Plan(l, 1e-12, leaf_cols=32, page_bytes=8192, device_build=True, plan_cache=path)
-    Q = sht.Plan(l, 1e-12, leaf_cols=32, page_bytes=8192, plan_cache=path)
+    P = sht.Plan(l, 1e-12, leaf_cols=32, device_build=True, plan_cache=path)
+    Q = sht.Plan(l, 1e-12, leaf_cols=32, plan_cache=path)
     assert Q.stats()["t_factor"] == 0.0
     beta = inputs.random_beta(l, seed=3, decay=True)
     assert np.array_equal(synth(sht, P, 0, beta), synth(sht, Q, 0, beta))

@@ -47,9 +47,9 @@ def test_round_trip_gives_the_same_streams(tmp_path, l, C):
 
 def test_float32_factorization_is_kept_and_options_come_from_the_file(saved):
     P, path = saved
-    Q = sht.Plan.load(path, host_only=True, leaf_cols=40, page_bytes=16384)
+    Q = sht.Plan.load(path, host_only=True, leaf_cols=40, page_bytes=2048)
     s = Q.stats()
-    assert s["leaf_cols"] == 16 and s["page_bytes"] == 16384
+    assert s["leaf_cols"] == 16 and s["page_bytes"] == 2048
     Q.prepare(sht.SHT_FP32)
     assert Q.stats()["t_factor"] == 0.0  # the float32 factorization came from the file
     R = sht.Plan.load(path, host_only=True)

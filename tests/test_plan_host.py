@@ -101,7 +101,8 @@ def test_invalid_arguments_are_rejected(args):
 def test_invalid_options_are_rejected():
     for kw in [dict(leaf_cols=1), dict(page_bytes=1000), dict(page_bytes=65536), dict(num_threads=-1),
                dict(consumer_warps=10), dict(slot_values=100), dict(slot_values=4096), dict(slot_values=1000),
-               dict(device_build=True), dict(device_build_arena_mb=-1), dict(staging_slots=3)]:
+               dict(device_build=True), dict(device_build_arena_mb=-1), dict(staging_slots=2),
+               dict(values_inline=1), dict(page_bytes=256), dict(page_bytes=8192)]:
         with pytest.raises(sht.ShtError):
             sht.Plan(8, 1e-12, host_only=True, **kw)
 
@@ -140,38 +141,54 @@ def test_op_ordering_is_race_free(l, C, prec):
 
 
 def test_race_checker_catches_a_planted_overlap():
-    """The checker itself: dropping the predecessors of the first interpolation
-    op of a real stream (it would no longer wait for the gather that writes its
-    input) must be reported."""
-    from tests.stream_emulator import OPHDR, page_op_offsets
+    """The checker itself: dropping the pred entries of the first
+    interpolation op that waits for another warp (it would no longer wait for
+    the gather that writes its input) must be reported."""
+    from tests.stream_emulator import OPHDR
     P = sht.Plan(64, 1e-12, leaf_cols=16, host_only=True)
-    pages, values = P.stream(0, 0)
-    PB = P.page_bytes
-    st = (pages.copy(), values)
-    for pg in range(len(st[0]) // PB):
-        base = pg * PB
-        for off in page_op_offsets(st[0][base:base + PB], PB) or []:
-            h = st[0][base + off:base + off + 32].view(OPHDR)
-            if h[0]["kind"] == 6:
-                assert check_races(st, PB, 64) == []
-                h[0]["npred"] = 0  # no predecessors: may overlap the gathers
-                assert check_races(st, PB, 64) != []
-                return
-    raise AssertionError("no interpolation op found")
+    records, values = P.stream(0, 0)
+    CH = P.page_bytes
+    st = (records.copy(), values)
+    assert check_races(st, CH, 64) == []
+    # locate the record in the copy, walking the items as the decoder does
+    pos = 0
+    while pos < len(st[0]):
+        nw = int(st[0][pos + 4:pos + 6].view("<u2")[0])
+        ranges = st[0][pos + 16:pos + 16 + 8 * nw].view("<u4").reshape(nw, 2)
+        end = pos
+        for w in range(nw):
+            off, nb = int(ranges[w, 0]), int(ranges[w, 1])
+            end = max(end, pos + off + nb)
+            q = 0
+            while q < nb:
+                at = pos + off + q
+                h = st[0][at:at + 32].view(OPHDR)
+                if int(h[0]["bytes"]) == 0:
+                    q = (q // CH + 1) * CH
+                    continue
+                if h[0]["kind"] == 6 and int(h[0]["npred"]) > 0:
+                    ia = st[0][at + 32:at + 32 + 16 * int(h[0]["idx16"])].view("<u2")
+                    npred = int(h[0]["npred"])
+                    ia[:len(ia) - npred] = ia[npred:].copy()
+                    h[0]["npred"] = 0  # no longer waits for the other warps
+                    assert check_races(st, CH, 64) != []
+                    return
+                q += int(h[0]["bytes"])
+        pos = (end + 15) // 16 * 16
+    raise AssertionError("no interpolation op that waits for another warp")
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
-def test_values_inline_layout_reproduces_oracle(prec):
-    """The alternative layout (values inside the TMA pages) encodes the same
-    operator as the default (values in their own region)."""
-    l = 64
-    P = sht.Plan(l, 1e-12, leaf_cols=16, values_inline=1, host_only=True)
-    pages, values = P.stream(prec, 0)
-    assert values.size == 0
-    beta = inputs.random_beta(l, seed=21)
-    G = emulate((pages, values), P.page_bytes, l, prec, 0, beta)
-    assert rel(G, oracle.legendre_synthesis(beta, l)) < (2e-5 if prec == 1 else 1e-10)
-    assert check_races(P.stream(prec, 1), P.page_bytes, l) == []
+def test_every_item_is_scheduled_for_the_plan_warps():
+    """Each work item carries one record stream per consumer warp of the plan
+    (consumer_warps, 16 by default), and the schedule spreads the ops of a
+    large order over many of them."""
+    from tests.stream_emulator import iter_items
+    for nw in (8, 16):
+        P = sht.Plan(128, 1e-12, leaf_cols=16, host_only=True, consumer_warps=nw)
+        items = list(iter_items(P.stream(0, 0)[0], P.page_bytes))
+        assert items and all(len(w) == nw for w in items)
+        # the largest item (both parities of order 0) spreads over at least half of the warps
+        assert sum(len(ops) > 0 for ops in items[0]) >= nw // 2
 
 
 def test_batch_argument_checks_on_host():
@@ -192,18 +209,20 @@ def test_batch_argument_checks_on_host():
 
 
 def test_debug_unmet_dependency_plants_one_self_wait():
-    """The failure-detection option marks exactly one compute op per stream
-    as its own predecessor (delta 0); a normal plan has none."""
-    from tests.stream_emulator import OP_ANA, OP_SYN
+    """The failure-detection option makes exactly one compute op per stream
+    wait for its own completion (a pred entry naming its own warp and
+    position); a normal plan has none."""
+    from tests.stream_emulator import OP_ANA, OP_SYN, POS_BITS, iter_items
     for debug, expected in ((1, 1), (0, 0)):
         P = sht.Plan(32, 1e-12, leaf_cols=8, host_only=True, debug_unmet_dependency=debug)
         for d in (0, 1):
             n = 0
-            for h, idx, _ in iter_ops(P.stream(0, d), P.page_bytes, with_preds=True):
-                npred = int(h["npred"])
-                if any(int(x) == 0 for x in idx[:npred]):
-                    assert OP_SYN <= int(h["kind"]) <= OP_ANA
-                    n += 1
+            for warps in iter_items(P.stream(0, d)[0], P.page_bytes):
+                for w, ops in enumerate(warps):
+                    for p, (h, preds, _) in enumerate(ops):
+                        if any(int(e) == (w << POS_BITS) | p for e in preds):
+                            assert OP_SYN <= int(h["kind"]) <= OP_ANA
+                            n += 1
             assert n == expected, (debug, d, n)
 
 
