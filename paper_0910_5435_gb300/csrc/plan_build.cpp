@@ -898,10 +898,12 @@ struct Emitter {
       r.planted = true;
       plant_unmet = false;
     }
+    // estimated cycles of one warp (measured on GB300 at l = 1024): a fixed
+    // cost per op (its value copy, waits and completion) and a cost per value
     const double M = h.M, K = h.K;
-    const double per_value = prec == 0 ? 16.0 : prec == 2 ? 9.0 : 5.0;  // cycles of one warp
-    r.cost = (h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) ? 400.0 + per_value * M * K + 8.0 * K
-                                                                   : 300.0 + 4.0 * M;
+    const double per_value = prec == 0 ? 16.0 : prec == 2 ? 6.0 : 2.5;
+    r.cost = (h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) ? 1200.0 + per_value * M * K
+                                                                   : 800.0 + 2.0 * M;
     ops.push_back(std::move(r));
   }
 

@@ -381,9 +381,9 @@ __device__ __forceinline__ FieldCtx field_ctx(const SweepArgs& A, int f) {
 }
 
 // One compute op (SYN_INTERP, DENSE, DENSE_G, ANA_INTERP), executed by one warp.
-template <class TR>
+template <class TR, class AfterRead>
 __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, const Vecs<TR>& S, const FieldCtx& A,
-                                         int lane, const uint8_t* staged) {
+                                         int lane, const uint8_t* staged, AfterRead after_read) {
   using C = typename TR::C;
   using V = typename TR::V;
   using Acc = typename TR::Acc;
@@ -404,6 +404,7 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
     const int o = (lane * c_inv16[ks]) >> 16, q = lane - o * ks;
     Acc a0 = TR::zero();
     if (o < M) a0 = gemv_dot<TR>(val, in, idx, gather, M, K, o, q, ks);
+    after_read();  // every lane is done with the staged values
     // segmented tree: after the step with offset d, lane q holds the sum over
     // q .. min(q + 2d - 1, ks - 1) of its segment
     for (int off = 1; off < ks; off <<= 1) {
@@ -655,23 +656,45 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
       return true;
     };
     bool ok = true;
-    bool vals_pending = false;  // the staging slot holds (or will hold) the next value op's block
-    uint32_t rpos = 0, n_done = 0;
+    uint32_t pending = 0xffffffffu;  // position of the value op whose block the staging slot receives
+    uint32_t rpos = 0, n_done = 0, cur_c = 0;  // cur_c: chunk of the last record run
+    // Finds the record after position np (skipping a chunk's padding, waiting
+    // for the next chunk if it starts there): its position and header, or false.
+    auto peek = [&](uint32_t np, uint32_t& at, OpHdr& nh) -> bool {
+      while (np < len) {
+        const uint32_t cn = np / CH;
+        if (np - cn * CH + sizeof(OpHdr) > CH) {  // too little room left for a record: padding
+          np = (cn + 1) * CH;
+          continue;
+        }
+        if (!wait_chunk(cn)) return false;
+        nh = *reinterpret_cast<const OpHdr*>(ring + (size_t)(cn & 1u) * CH + (np - cn * CH));
+        if (nh.bytes == 0) {
+          np = (cn + 1) * CH;
+          continue;
+        }
+        at = np;
+        return true;
+      }
+      return false;
+    };
     while (ok && rpos < len) {
-      const uint32_t c = rpos / CH;
-      if (!wait_chunk(c)) {
-        ok = false;
+      uint32_t at;
+      OpHdr h;
+      if (!peek(rpos, at, h)) {
+        ok = !vload(&S->abort);
         break;
       }
-      const uint8_t* rec = ring + (size_t)(c & 1u) * CH + (rpos - c * CH);
-      const OpHdr h = *reinterpret_cast<const OpHdr*>(rec);
-      if (h.bytes == 0) {  // the rest of chunk c is padding
-        rpos = (c + 1) * CH;
+      // chunks before this record's are used up: refill their ring slots
+      for (uint32_t cf = cur_c; cf < at / CH; ++cf) {
         __syncwarp();
-        if (lane == 0 && c + 2 < nch) issue_chunk(c + 2);
-        if (c + 2 < nch) ring_busy |= 1u << (c & 1u);
-        continue;
+        if (lane == 0 && cf + 2 < nch) issue_chunk(cf + 2);
+        if (cf + 2 < nch) ring_busy |= 1u << (cf & 1u);
       }
+      cur_c = at / CH;
+      rpos = at;
+      const uint32_t c = rpos / CH;
+      const uint8_t* rec = ring + (size_t)(c & 1u) * CH + (rpos - c * CH);
       if (h.bytes < sizeof(OpHdr) || (rpos - c * CH) + h.bytes > CH || rpos + h.bytes > len || !sound(h) ||
           h.npred > 32 || sizeof(OpHdr) + 16 * (size_t)h.idx16 > h.bytes || 2 * (size_t)h.npred > 16 * (size_t)h.idx16) {
         if (lane == 0) fail(A, S, kStatusBadArg);
@@ -679,10 +702,30 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
         break;
       }
       const bool gemv = h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP;
-      if (has_values(h) && !vals_pending) {
+      const bool vals = has_values(h);
+      if (vals && pending != rpos) {  // not prefetched by the previous op
         if (lane == 0) issue_values(h);
         slot_busy = true;
+        pending = rpos;
       }
+      // the next record, whose values are copied into the slot as soon as
+      // this op has read it (at once if this op has no values)
+      uint32_t nat = 0;
+      OpHdr nh;
+      const bool have_next = peek(rpos + h.bytes, nat, nh) && has_values(nh) && sound(nh);
+      if (!ok || vload(&S->abort)) {
+        ok = false;
+        break;
+      }
+      auto prefetch = [&]() {
+        if (have_next && pending != nat) {
+          __syncwarp();
+          if (lane == 0) issue_values(nh);
+          slot_busy = true;
+          pending = nat;
+        }
+      };
+      if (!vals && !slot_busy) prefetch();
       // wait for the listed warps' progress
       const long long t1 = tracing ? clock64() : 0;
       {
@@ -720,7 +763,7 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
       }
       if (!ok) break;
       const long long t2 = tracing ? clock64() : 0;
-      if (has_values(h)) {
+      if (vals) {
         if (!warp_wait([&] { return mbar_try_wait(slot_bar, slot_par); }, A, S, lane)) {
           ok = false;
           break;
@@ -730,25 +773,15 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
         slot_busy = false;
       }
       const long long t3 = tracing ? clock64() : 0;
-      if (gemv)
-        run_gemv<TR>(h, rec, V, F, lane, slot);
-      else
+      if (gemv) {
+        run_gemv<TR>(h, rec, V, F, lane, slot, [&] {
+          if (!slot_busy) prefetch();
+        });
+      } else {
         run_control<TR>(h, V, F, lane);
-      const long long t4 = tracing ? clock64() : 0;
-      // the slot has been read: start the next value op's copy, which may sit
-      // in the next chunk (already requested)
-      // (a next op in the next chunk issues its own copy when it starts)
-      vals_pending = false;
-      const uint32_t npos = rpos + h.bytes;
-      if (npos < len && npos / CH == c && (npos - c * CH) + sizeof(OpHdr) <= CH) {
-        const OpHdr& n2 = *reinterpret_cast<const OpHdr*>(ring + (size_t)(c & 1u) * CH + (npos - c * CH));
-        if (n2.bytes != 0 && has_values(n2) && sound(n2)) {
-          __syncwarp();
-          if (lane == 0) issue_values(n2);
-          slot_busy = true;
-          vals_pending = true;
-        }
       }
+      if (!slot_busy) prefetch();  // ops without a value block
+      const long long t4 = tracing ? clock64() : 0;
       // publish completion
       __threadfence_block();
       __syncwarp();
@@ -767,12 +800,7 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
         c_val += t3 - t2;
         c_done += t5 - t4;
       }
-      rpos = npos;
-      if (rpos == len || rpos - c * CH == CH) {  // chunk c fully used: refill its ring slot
-        __syncwarp();
-        if (lane == 0 && c + 2 < nch) issue_chunk(c + 2);
-        if (c + 2 < nch) ring_busy |= 1u << (c & 1u);
-      }
+      rpos += h.bytes;
     }
     if (!ok) break;
     // every warp has finished this item before any starts the next
