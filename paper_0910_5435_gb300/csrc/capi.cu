@@ -574,7 +574,7 @@ sht_status create_plan(int l, double eps_id, const sht_plan_opts* opts, const ch
   if (o.min_band_rows <= 0) o.min_band_rows = std::max(1, o.leaf_cols / 2);
   if (l < 1 || l > 1024 || !(eps_id > 0.0) || !(eps_id < 1.0)) return SHT_ERR_INVALID_ARG;
   if (o.leaf_cols < 2 || o.leaf_cols > 1024) return SHT_ERR_INVALID_ARG;
-  if (o.page_bytes < sht::kMinChunkBytes || o.page_bytes > sht::kMaxChunkBytes || (o.page_bytes % 256) != 0)
+  if (o.page_bytes < sht::kMinChunkBytes || o.page_bytes > sht::kMaxChunkBytes || (o.page_bytes & (o.page_bytes - 1)))
     return SHT_ERR_INVALID_ARG;
   if (o.values_inline != 0) return SHT_ERR_INVALID_ARG;  // values always travel apart
   if (o.num_threads < 0) return SHT_ERR_INVALID_ARG;

@@ -1287,6 +1287,18 @@ void encode_item(const std::vector<OpRec>& ops, int nw, size_t chunk, std::vecto
   }
   for (int w = 0; w < nw; ++w)
     if (cnt[w] > kMaxWarpOps) throw std::logic_error("work item has too many ops for one warp");
+  // ops another warp waits for: their warps publish progress after them
+  std::vector<char> waited_for(n, 0);
+  {
+    std::vector<int> last(nw);
+    for (int t = 0; t < n; ++t) {
+      std::fill(last.begin(), last.end(), -1);
+      for (int u : ops[t].preds)
+        if (warp[u] != warp[t] && (last[warp[u]] < 0 || pos[u] > pos[last[warp[u]]])) last[warp[u]] = u;
+      for (int v = 0; v < nw; ++v)
+        if (last[v] >= 0) waited_for[last[v]] = 1;
+    }
+  }
   std::vector<std::vector<uint8_t>> st(nw);
   std::vector<int> need(nw);
   for (int t = 0; t < n; ++t) {
@@ -1299,6 +1311,7 @@ void encode_item(const std::vector<OpRec>& ops, int nw, size_t chunk, std::vecto
       if (need[v] >= 0) all.push_back((uint16_t)((v << kPredPosBits) | need[v]));
     if (ops[t].planted) all.push_back((uint16_t)((w << kPredPosBits) | pos[t]));  // itself: never complete
     OpHdr h = ops[t].h;
+    if (waited_for[t]) h.flags |= F_PUBLISH;
     h.npred = (uint16_t)all.size();
     all.insert(all.end(), ops[t].idx.begin(), ops[t].idx.end());
     const size_t ib = pad16(2 * all.size());

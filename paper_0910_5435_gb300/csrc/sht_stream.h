@@ -61,8 +61,9 @@
 // | p means "warp w has completed its ops 0..p of this item" (the last
 // writer of every shared position / node row the op reads or writes and
 // every reader of a position it overwrites, reduced to the latest such op of
-// each warp).  Each warp publishes its progress in shared memory; an item
-// ends with a CTA-wide barrier (the next item reuses the shared vectors).
+// each warp).  After an op flagged F_PUBLISH (one that another warp waits
+// for) a warp publishes its progress in shared memory; an item ends with a
+// CTA-wide barrier (the next item reuses the shared vectors).
 // Each warp's list is in one topological order of the item's graph, so the
 // waits cannot form a cycle.
 //
@@ -92,6 +93,7 @@ enum OpKind : uint8_t {
 enum OpFlags : uint8_t {
   F_ACCUM = 2,        // DENSE_G / ANA_INTERP: accumulate instead of overwrite
   F_SKEL = 4,         // ANA_INTERP: also the skeleton pass-through (nskel entries)
+  F_PUBLISH = 8,      // another warp waits for this op: publish the warp's progress after it
 };
 
 struct alignas(16) OpHdr {
@@ -155,7 +157,8 @@ constexpr int kDefaultSlotValues = 1024;
 constexpr int kMinSlotValues = 128;
 constexpr int kMaxSlotValues = 2048;
 constexpr int kCtlPieces = 8;         // control ops are split into up to this many warp tasks
-// Record chunk: the unit of a warp's record fetches (plan option page_bytes).
+// Record chunk: the unit of a warp's record fetches (plan option page_bytes,
+// a power of two).
 constexpr int kDefaultChunkBytes = 1024;
 constexpr int kMinChunkBytes = 512;
 constexpr int kMaxChunkBytes = 4096;

@@ -572,7 +572,8 @@ template <class TR, int NW>
 __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int warp, int lane, uint8_t* ring,
                           uint64_t* ring_bar, uint8_t* slot, uint64_t* slot_bar) {
   using Val = typename TR::V;
-  const uint32_t CH = (uint32_t)A.chunk_bytes;
+  const uint32_t CH = (uint32_t)A.chunk_bytes;  // a power of two
+  const uint32_t csh = (uint32_t)(__ffs(A.chunk_bytes) - 1);
   const bool tracing = A.trace != nullptr;
   unsigned long long c_gemv = 0, c_ctl = 0, c_dep = 0, c_val = 0, c_rec = 0, c_bar = 0, c_done = 0;
   unsigned long long n_gemv = 0, n_ctl = 0, n_items = 0;
@@ -615,7 +616,7 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
     off = __shfl_sync(0xffffffffu, off, 0);
     len = __shfl_sync(0xffffffffu, len, 0);
     const uint8_t* stream = item_base + off;
-    const uint32_t nch = (len + CH - 1) / CH;
+    const uint32_t nch = (len + CH - 1) >> csh;
     auto issue_chunk = [&](uint32_t c) {  // lane 0; chunk c into ring slot c & 1
       const uint32_t r = c & 1u;
       const uint32_t bytes = min(CH, len - c * CH);
@@ -657,20 +658,20 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
     };
     bool ok = true;
     uint32_t pending = 0xffffffffu;  // position of the value op whose block the staging slot receives
-    uint32_t rpos = 0, n_done = 0, cur_c = 0;  // cur_c: chunk of the last record run
-    // Finds the record after position np (skipping a chunk's padding, waiting
-    // for the next chunk if it starts there): its position and header, or false.
+    uint32_t n_done = 0, cur_c = 0;  // cur_c: chunk of the last record run
+    // Finds the record at or after position np (skipping a chunk's padding,
+    // waiting for its chunk): its position and header, or false at the end.
     auto peek = [&](uint32_t np, uint32_t& at, OpHdr& nh) -> bool {
       while (np < len) {
-        const uint32_t cn = np / CH;
-        if (np - cn * CH + sizeof(OpHdr) > CH) {  // too little room left for a record: padding
-          np = (cn + 1) * CH;
+        const uint32_t cn = np >> csh, in = np & (CH - 1);
+        if (in + sizeof(OpHdr) > CH) {  // too little room left for a record: padding
+          np = (cn + 1) << csh;
           continue;
         }
         if (!wait_chunk(cn)) return false;
-        nh = *reinterpret_cast<const OpHdr*>(ring + (size_t)(cn & 1u) * CH + (np - cn * CH));
+        nh = *reinterpret_cast<const OpHdr*>(ring + ((size_t)(cn & 1u) << csh) + in);
         if (nh.bytes == 0) {
-          np = (cn + 1) * CH;
+          np = (cn + 1) << csh;
           continue;
         }
         at = np;
@@ -678,25 +679,21 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
       }
       return false;
     };
-    while (ok && rpos < len) {
-      uint32_t at;
-      OpHdr h;
-      if (!peek(rpos, at, h)) {
-        ok = !vload(&S->abort);
-        break;
-      }
+    uint32_t rpos = 0;
+    OpHdr h;
+    bool have = peek(0, rpos, h);
+    while (have && ok) {
+      const uint32_t c = rpos >> csh, in = rpos & (CH - 1);
       // chunks before this record's are used up: refill their ring slots
-      for (uint32_t cf = cur_c; cf < at / CH; ++cf) {
+      for (uint32_t cf = cur_c; cf < c; ++cf) {
         __syncwarp();
         if (lane == 0 && cf + 2 < nch) issue_chunk(cf + 2);
         if (cf + 2 < nch) ring_busy |= 1u << (cf & 1u);
       }
-      cur_c = at / CH;
-      rpos = at;
-      const uint32_t c = rpos / CH;
-      const uint8_t* rec = ring + (size_t)(c & 1u) * CH + (rpos - c * CH);
-      if (h.bytes < sizeof(OpHdr) || (rpos - c * CH) + h.bytes > CH || rpos + h.bytes > len || !sound(h) ||
-          h.npred > 32 || sizeof(OpHdr) + 16 * (size_t)h.idx16 > h.bytes || 2 * (size_t)h.npred > 16 * (size_t)h.idx16) {
+      cur_c = c;
+      const uint8_t* rec = ring + ((size_t)(c & 1u) << csh) + in;
+      if (h.bytes < sizeof(OpHdr) || in + h.bytes > CH || rpos + h.bytes > len || !sound(h) || h.npred > 32 ||
+          sizeof(OpHdr) + 16 * (uint32_t)h.idx16 > h.bytes || 2u * h.npred > 16u * h.idx16) {
         if (lane == 0) fail(A, S, kStatusBadArg);
         ok = false;
         break;
@@ -708,17 +705,18 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
         slot_busy = true;
         pending = rpos;
       }
-      // the next record, whose values are copied into the slot as soon as
-      // this op has read it (at once if this op has no values)
+      // the next record: its values are copied into the slot as soon as this
+      // op has read it (at once if this op has no values)
       uint32_t nat = 0;
       OpHdr nh;
-      const bool have_next = peek(rpos + h.bytes, nat, nh) && has_values(nh) && sound(nh);
-      if (!ok || vload(&S->abort)) {
+      const bool have_next = peek(rpos + h.bytes, nat, nh);
+      if (vload(&S->abort)) {
         ok = false;
         break;
       }
+      const bool next_vals = have_next && has_values(nh) && sound(nh);
       auto prefetch = [&]() {
-        if (have_next && pending != nat) {
+        if (next_vals && pending != nat) {
           __syncwarp();
           if (lane == 0) issue_values(nh);
           slot_busy = true;
@@ -728,7 +726,7 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
       if (!vals && !slot_busy) prefetch();
       // wait for the listed warps' progress
       const long long t1 = tracing ? clock64() : 0;
-      {
+      if (h.npred) {
         const uint16_t* pred = reinterpret_cast<const uint16_t*>(rec + sizeof(OpHdr));
         unsigned want_w = 0, want = 0;
         const bool mine = lane < h.npred;
@@ -760,8 +758,8 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
           }
         }
         __threadfence_block();  // acquire what the predecessors wrote
+        if (!ok) break;
       }
-      if (!ok) break;
       const long long t2 = tracing ? clock64() : 0;
       if (vals) {
         if (!warp_wait([&] { return mbar_try_wait(slot_bar, slot_par); }, A, S, lane)) {
@@ -782,11 +780,12 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
       }
       if (!slot_busy) prefetch();  // ops without a value block
       const long long t4 = tracing ? clock64() : 0;
-      // publish completion
-      __threadfence_block();
-      __syncwarp();
       ++n_done;
-      if (lane == 0) vstore(&S->progress[warp], seq * 4096u + n_done);
+      if (h.flags & F_PUBLISH) {  // another warp waits for this op: publish
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) vstore(&S->progress[warp], seq * 4096u + n_done);
+      }
       if (tracing) {
         const long long t5 = clock64();
         if (gemv) {
@@ -800,16 +799,16 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
         c_val += t3 - t2;
         c_done += t5 - t4;
       }
-      rpos += h.bytes;
+      rpos = nat;
+      h = nh;
+      have = have_next;
     }
     if (!ok) break;
     // every warp has finished this item before any starts the next
     const long long tb = tracing ? clock64() : 0;
+    __threadfence_block();  // this warp's writes of the item precede its arrival
     __syncwarp();
-    if (lane == 0) {
-      __threadfence_block();
-      atomicAdd(&S->arrived, 1u);
-    }
+    if (lane == 0) atomicAdd(&S->arrived, 1u);
     if (!warp_wait([&] { return vload(&S->arrived) >= (unsigned)NW * (seq + 1); }, A, S, lane)) break;
     if (tracing) {
       c_bar += clock64() - tb;
