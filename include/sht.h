@@ -106,20 +106,21 @@ typedef struct {
   int host_only;
   /* Host threads for the precomputation; 0 = all hardware threads. */
   int num_threads;
-  /* Bytes per streamed factor page (TMA bulk-copy unit, multiple of 1024,
-   * 4096..49152); 0 = default (8192). */
+  /* Bytes of one record chunk: a consumer warp fetches its op records
+   * (headers, wait lists, index lists) in chunks of this size into a ring of
+   * two (a power of two, 512..4096; 0 = default 1024).  A tuning knob. */
   int page_bytes;
   /* eps used for the IDs of the SHT_FP32 factors; <= 0 selects
    * max(eps_id, 1e-7).  (FP32 cannot use ranks below its own precision.) */
   double eps_fp32;
-  /* Warps per CTA of the sweep kernels that execute ops (8, 12 or 16; 0 =
-   * 16).  A tuning knob; results do not depend on it. */
+  /* Warps per CTA of the sweep kernels (8, 12 or 16; 0 = 16).  The planner
+   * schedules every op of a work item onto one of these warps (list
+   * scheduling over the item's dependency graph), so the factor streams are
+   * built for this count.  A tuning knob; results do not depend on it. */
   int consumer_warps;
-  /* 1: factor values travel inside the TMA-staged pages; 0 (default): they
-   * sit in a separate region, the pages carry only op headers and index
-   * lists, and each executing warp bulk-copies the value block of its next
-   * op into a shared-memory staging slot (ops hold at most slot_values
-   * values; see staging_slots).  A tuning knob. */
+  /* Must be 0: op values always travel apart from the records, in a value
+   * region from which each warp bulk-copies its next op's block into a
+   * staging slot.  Other values are refused (SHT_ERR_INVALID_ARG). */
   int values_inline;
   /* Tests of failure detection only (default 0): 1 makes the first compute
    * op of the first order of every stream list itself as its predecessor, a
@@ -155,12 +156,9 @@ typedef struct {
    * sht_last_error_detail).  A failed write fails plan creation with
    * SHT_ERR_INVALID_ARG.  The string is read during the call only. */
   const char* plan_cache;
-  /* Staging slots per consumer warp when values are kept apart (0 = 1).  1
-   * starts the copy of a warp's next op once its current op has read the
-   * slot, and leaves room for 16 consumer warps whose copies and arithmetic
-   * overlap one another; 2 lets a warp's next op's values travel while its
-   * current op runs, at twice the slot memory (8 warps at the default slot
-   * size).  A tuning knob; results do not depend on it. */
+  /* Staging slots per consumer warp: 0 or 1 (one 8 KB slot; the copy of a
+   * warp's next op starts as soon as its current op has read the slot).
+   * Other values are refused (SHT_ERR_INVALID_ARG). */
   int staging_slots;
 } sht_plan_opts;
 
@@ -191,7 +189,7 @@ typedef struct {
   double t_upload;       /* seconds: device upload of the prepared precisions */
   long long m_max_words; /* peak float64 words held by one unit's depth-first build */
   int smem_bytes;        /* dynamic shared memory of the sweep kernels */
-  int page_bytes;        /* bytes per factor page (the value in effect) */
+  int page_bytes;        /* bytes per record chunk (the value in effect) */
   double t_factor;       /* seconds of t_comp spent on the factorizations (the rest encodes
                           * the streams) */
   double t_factor_kernel; /* seconds of t_factor in the device builder's kernels (0 for a
@@ -263,10 +261,10 @@ sht_status sht_plan_nodes(sht_plan_t plan, double* x, double* w);
 
 /* Host copy of the factor stream of one precision and direction (0 =
  * synthesis, 1 = analysis), for inspection and host-side verification: the
- * page region followed by the value region (layout documented in
- * paper_0910_5435_gb300/csrc/sht_stream.h).  *bytes receives the total and
- * *page_bytes_total (if not NULL) the size of the page region.  With
- * dst == NULL only the sizes are set. */
+ * record region (the scheduled work items) followed by the value region
+ * (layout documented in paper_0910_5435_gb300/csrc/sht_stream.h).  *bytes
+ * receives the total and *page_bytes_total (if not NULL) the size of the
+ * record region.  With dst == NULL only the sizes are set. */
 sht_status sht_plan_stream(sht_plan_t plan, sht_precision prec, int direction,
                            void* dst, size_t* bytes, size_t* page_bytes_total);
 
@@ -347,18 +345,16 @@ sht_status sht_analyze(sht_plan_t plan, sht_precision prec, const void* values, 
 
 /* Enables (allocating a small device buffer) or disables per-launch cycle
  * counters in the sweep kernels.  While enabled, every launch adds, summed
- * over its CTAs, the clock64 cycles that consumer warps spent executing ops,
- * waiting for an op to be published, waiting for its dependencies, waiting
- * for its staged values, that the producer spent waiting for a free page and
- * the parser for a landed page, plus the number of ops executed, and the
- * execution cycles split into compute ops, control ops and completion
- * marking, with the compute and control op counts.  Synchronous. */
+ * over its warps and CTAs, the clock64 cycles that warps spent executing
+ * compute ops and control ops, waiting for other warps' ops (their wait
+ * lists), waiting for staged values, waiting for record chunks, waiting at
+ * the end-of-item barrier and publishing completions, plus the numbers of
+ * compute ops, control ops and items run.  Synchronous. */
 sht_status sht_trace_enable(sht_plan_t plan, int enable);
 
-/* Copies the 16 counters (exec, wait_ready, wait_dep, producer_wait,
- * parser_wait, ops, wait_values, exec_gemv, exec_control, complete,
- * n_gemv, n_control, 0, 0, 0, 0) to host memory out[16]; reset != 0 zeroes
- * them.
+/* Copies the 16 counters (exec_gemv, exec_control, wait_dep, wait_values,
+ * wait_records, wait_barrier, n_gemv, n_control, n_items, complete, 0, 0,
+ * 0, 0, 0, 0) to host memory out[16]; reset != 0 zeroes them.
  * Synchronizes the device.  SHT_ERR_UNSUPPORTED if tracing is disabled. */
 sht_status sht_trace_read(sht_plan_t plan, unsigned long long* out, int reset);
 
@@ -466,7 +462,7 @@ typedef struct sht_batch_s* sht_batch_t;
 
 /* Builds a batch of nfields fields; field f uses plans[f] (a plan may appear
  * any number of times).  Every plan must be a device plan on the same GPU
- * with the same page_bytes; precision prec is built and uploaded for each
+ * with the same page_bytes and consumer_warps; precision prec is built and uploaded for each
  * plan if it is not yet (as sht_prepare).  Allocates the batch's item table
  * and field table on the device.  The plans must outlive the batch. */
 sht_status sht_batch_create(int nfields, const sht_plan_t* plans, sht_precision prec, sht_batch_t* out);
@@ -524,14 +520,15 @@ sht_status sht_batch_analyze_grid(sht_batch_t batch, const void* const* values, 
  * pointer entry was NULL or misaligned).  A non-OK status is cleared. */
 sht_status sht_batch_last_device_status(sht_batch_t batch, sht_stream_t stream);
 
-/* Times each launch shape (8 consumer warps with two staging slots each,
- * 12 or 16 with one, 16 with two; page ring depth 2..8; whatever fits in
- * shared memory with its values staged) over reps launches of the given
- * direction with these DEVICE pointer arrays, and keeps the fastest for that
- * direction.  Directions: 0 synthesis, 1 analysis, 2 adjoint of synthesis,
- * 3 and 4 the Legendre launches of sht_batch_synthesize_grid (beta ->
- * workspace) and sht_batch_analyze_grid (workspace -> beta).  Runs the
- * transform (writes the outputs); synchronous. */
+/* Times the launch shapes the batch's streams allow over reps launches of
+ * the given direction with these DEVICE pointer arrays, and keeps the
+ * fastest for that direction.  The plans' work items are scheduled for their
+ * consumer warps, which fixes the warps and the shared-memory layout of a
+ * launch; what is chosen is the number of resident CTAs per SM where more
+ * than one fits.  Directions: 0 synthesis, 1 analysis, 2 adjoint of
+ * synthesis, 3 and 4 the Legendre launches of sht_batch_synthesize_grid
+ * (beta -> workspace) and sht_batch_analyze_grid (workspace -> beta).  Runs
+ * the transform (writes the outputs); synchronous. */
 sht_status sht_batch_autotune(sht_batch_t batch, int direction, const void* const* in, void* const* out, int reps,
                               sht_stream_t stream);
 

@@ -901,9 +901,9 @@ struct Emitter {
     // estimated cycles of one warp (measured on GB300 at l = 1024): a fixed
     // cost per op (its value copy, waits and completion) and a cost per value
     const double M = h.M, K = h.K;
-    const double per_value = prec == 0 ? 16.0 : prec == 2 ? 6.0 : 2.5;
-    r.cost = (h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) ? 1200.0 + per_value * M * K
-                                                                   : 800.0 + 2.0 * M;
+    const double per_value = prec == 0 ? 13.5 : prec == 2 ? 5.5 : 2.8;
+    r.cost = (h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) ? 2400.0 + per_value * M * K
+                                                                   : 1500.0 + 2.0 * M;
     ops.push_back(std::move(r));
   }
 

@@ -692,8 +692,9 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
       }
       cur_c = c;
       const uint8_t* rec = ring + ((size_t)(c & 1u) << csh) + in;
-      if (h.bytes < sizeof(OpHdr) || in + h.bytes > CH || rpos + h.bytes > len || !sound(h) || h.npred > 32 ||
-          sizeof(OpHdr) + 16 * (uint32_t)h.idx16 > h.bytes || 2u * h.npred > 16u * h.idx16) {
+      // a record must lie in its chunk, and a compute op fit one warp and
+      // its values the staging slot (what keeps every access in bounds)
+      if (in + h.bytes > CH || !sound(h)) {
         if (lane == 0) fail(A, S, kStatusBadArg);
         ok = false;
         break;
@@ -709,11 +710,7 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
       // op has read it (at once if this op has no values)
       uint32_t nat = 0;
       OpHdr nh;
-      const bool have_next = peek(rpos + h.bytes, nat, nh);
-      if (vload(&S->abort)) {
-        ok = false;
-        break;
-      }
+      const bool have_next = peek(rpos + h.bytes, nat, nh);  // false also if the CTA gave up
       const bool next_vals = have_next && has_values(nh) && sound(nh);
       auto prefetch = [&]() {
         if (next_vals && pending != nat) {
