@@ -557,6 +557,13 @@ sht_status sht_analyze_batched(int nfields, const sht_plan_t* plans, sht_precisi
                                const void* const* values, void* const* beta, void* workspace,
                                sht_stream_t stream);
 
+/* Field groups of a direction (0..4 as in sht_batch_autotune): fields of a
+ * batch that share a plan are applied together, each op's values staged
+ * once for the whole group (as many fields per group as fit one CTA's shared
+ * vectors, at most 4; sht_batch_autotune may lower the cap).  Receives the
+ * largest group size class in use (1, 2 or 4) and the number of groups. */
+sht_status sht_batch_get_groups(sht_batch_t batch, int direction, int* max_fields_per_group, int* groups);
+
 /* ------------------------------------------------------ allocation-free call */
 
 /* Static scratch slots of sht_legendre_synthesize_noalloc (32 bytes each). */

@@ -23,14 +23,28 @@
 
 namespace {
 
-struct BatchDir {
+// One launch of a direction: the field groups of one size class (1, 2 or up
+// to 4 fields sharing a plan), their item table (LPT over all groups) and
+// their field lists.
+struct SubLaunch {
   sht::FieldDesc* d_fields = nullptr;
+  int* d_group_fields = nullptr;
   sht::UnitEntry* d_units = nullptr;
   int n_units = 0;
-  int buf_ab = 1;
-  int num_vecs = 2;
-  int slot_bytes = 0;  // largest staging slot of the fields
+  int n_groups = 0;
+  int capacity = 1;  // max over groups of nf * buf_ab (elements of each shared vector)
   sht::SweepConfig cfg;
+};
+
+constexpr int kClasses = 3;  // groups of 1, 2, and 3 or 4 fields
+inline int class_fg(int c) { return c == 0 ? 1 : c == 1 ? 2 : 4; }
+inline int class_of(int nf) { return nf <= 1 ? 0 : nf == 2 ? 1 : 2; }
+
+struct BatchDir {
+  SubLaunch sub[kClasses];
+  int slot_bytes = 0;  // largest staging slot of the fields
+  int nw = 16;
+  int fcap = 4;        // most fields per group
 };
 
 }  // namespace
@@ -71,12 +85,11 @@ namespace {
     }                                                                   \
   } while (0)
 
+void free_dir(BatchDir& D);
+
 void free_batch(sht_batch_t b) {
   if (!b) return;
-  for (BatchDir& d : b->dir) {
-    cudaFree(d.d_fields);
-    cudaFree(d.d_units);
-  }
+  for (BatchDir& d : b->dir) free_dir(d);
   cudaFree(b->d_scratch);
   cudaFree(b->d_tables);
   cudaFreeHost(b->h_stage);
@@ -87,89 +100,166 @@ void free_batch(sht_batch_t b) {
 
 constexpr int kDirs = 5;
 
-sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precision prec) {
-  for (int d = 0; d < kDirs; ++d) {
-    std::vector<sht::FieldDesc> fields(nfields);
-    std::vector<sht::UnitEntry> units;
+// Groups the fields that share a plan (in order of first appearance), as
+// many per group as fit the shared vectors of one CTA next to its warps'
+// record chunks and staging slots (at most 4; the groups of one plan are of
+// balanced sizes), and lays out one launch per group size class.
+void free_dir(BatchDir& D) {
+  for (SubLaunch& u : D.sub) {
+    cudaFree(u.d_fields);
+    cudaFree(u.d_group_fields);
+    cudaFree(u.d_units);
+    u = SubLaunch();
+  }
+}
+
+// Builds direction d with at most fcap fields per group (1, 2 or 4).
+sht_status build_dir(sht_batch_t b, int d, int nfields, const sht_plan_t* plans, sht_precision prec, int fcap) {
+  int optin = 0;
+  const size_t csize = (b->q == sht::PREC_FP32) ? 8 : 16;  // one complex of the shared vectors
+  {
     BatchDir& D = b->dir[d];
+    free_dir(D);
+    D.fcap = fcap;
+    // the adjoint runs the analysis stream with the 1/w fold prescale; the
+    // grid directions run the synthesis and analysis streams with the phase
+    const int stream_dir = (d == 0 || d == 3) ? 0 : 1;
+    std::vector<sht_plan_t> order;
+    std::vector<std::vector<int>> members;
+    std::vector<sht::StreamView> views;
     for (int f = 0; f < nfields; ++f) {
-      sht::StreamView v;
-      // the adjoint runs the analysis stream with the 1/w fold prescale; the
-      // grid directions run the synthesis and analysis streams with the phase
-      const int stream_dir = (d == 0 || d == 3) ? 0 : 1;
-      const sht_status s = sht::stream_view(plans[f], prec, stream_dir, &v);
-      if (s != SHT_OK) return s;
-      if (f == 0) {
-        b->device = v.device;
-        b->num_sms = v.num_sms;
-        b->page_bytes = v.page_bytes;
-        D.cfg.nw = v.consumer_warps;
-      } else if (v.device != b->device || v.page_bytes != b->page_bytes || v.consumer_warps != D.cfg.nw) {
-        // one launch runs every field's items on the same warps and chunk ring
-        sht::set_error_detail("sht_batch_create", "plans differ in device, page_bytes or consumer_warps");
-        return SHT_ERR_INVALID_ARG;
+      size_t k = 0;
+      while (k < order.size() && order[k] != plans[f]) ++k;
+      if (k == order.size()) {
+        sht::StreamView v;
+        const sht_status s = sht::stream_view(plans[f], prec, stream_dir, &v);
+        if (s != SHT_OK) return s;
+        if (order.empty()) {
+          b->device = v.device;
+          b->num_sms = v.num_sms;
+          b->page_bytes = v.page_bytes;
+          D.nw = v.consumer_warps;
+        } else if (v.device != b->device || v.page_bytes != b->page_bytes || v.consumer_warps != D.nw) {
+          // one launch runs every field's items on the same warps and chunk ring
+          sht::set_error_detail("sht_batch_create", "plans differ in device, page_bytes or consumer_warps");
+          return SHT_ERR_INVALID_ARG;
+        }
+        D.slot_bytes = std::max(D.slot_bytes, v.slot_bytes);
+        order.push_back(plans[f]);
+        members.emplace_back();
+        views.push_back(v);
       }
-      fields[f].pages = v.pages;
-      fields[f].values = v.values;
-      fields[f].prescale = d == 2 ? v.prescale : nullptr;
-      fields[f].twiddle = d == 3 ? v.tw_syn : d == 4 ? v.tw_ana : nullptr;
-      fields[f].l = v.l;
-      D.buf_ab = std::max(D.buf_ab, v.buf_ab);
-      D.num_vecs = std::max(D.num_vecs, v.num_vecs);
-      D.slot_bytes = std::max(D.slot_bytes, v.slot_bytes);
-      for (int u = 0; u < v.n_units; ++u) {
-        sht::UnitEntry e = v.units[u];
-        e.m = (uint32_t)f;
-        units.push_back(e);
+      members[k].push_back(f);
+    }
+    if (optin == 0) {
+      BCK(cudaSetDevice(b->device));
+      BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
+    }
+    // shared-vector capacity (elements of each of A and B) left beside the warps
+    const size_t fixed = sht::sweep_smem_bytes(b->q, b->page_bytes, 0, 2, D.nw, D.slot_bytes, 1);
+    const size_t cap_max = (size_t)optin > fixed + 128 ? ((size_t)optin - fixed - 128) / (2 * csize) : 0;
+    std::vector<sht::FieldDesc> gdesc[kClasses];
+    std::vector<int> gfields[kClasses];
+    std::vector<sht::UnitEntry> units[kClasses];
+    for (size_t k = 0; k < order.size(); ++k) {
+      const sht::StreamView& v = views[k];
+      const int n = (int)members[k].size();
+      int F = 1;
+      if (D.nw == 16 && v.buf_ab > 0)
+        F = (int)std::min<size_t>((size_t)fcap, std::max<size_t>(1, cap_max / (size_t)v.buf_ab));
+      F = std::min(F, n);
+      const int ng = (n + F - 1) / F;
+      for (int g = 0, at = 0; g < ng; ++g) {
+        const int nf = n / ng + (g < n % ng ? 1 : 0);  // balanced group sizes
+        const int c = class_of(nf);
+        sht::FieldDesc fd{};
+        fd.pages = v.pages;
+        fd.values = v.values;
+        fd.prescale = d == 2 ? v.prescale : nullptr;
+        fd.twiddle = d == 3 ? v.tw_syn : d == 4 ? v.tw_ana : nullptr;
+        fd.l = v.l;
+        fd.buf_ab = v.buf_ab;
+        fd.f0 = (int)gfields[c].size();
+        fd.nf = nf;
+        for (int j = 0; j < nf; ++j) gfields[c].push_back(members[k][at + j]);
+        at += nf;
+        const uint32_t gi = (uint32_t)gdesc[c].size();
+        gdesc[c].push_back(fd);
+        for (int u = 0; u < v.n_units; ++u) {
+          sht::UnitEntry e = v.units[u];
+          e.m = gi;
+          units[c].push_back(e);
+        }
+        D.sub[c].capacity = std::max(D.sub[c].capacity, nf * v.buf_ab);
       }
     }
-    std::stable_sort(units.begin(), units.end(),
-                     [](const sht::UnitEntry& a, const sht::UnitEntry& c) { return a.len16 > c.len16; });
-    D.n_units = (int)units.size();
-    BCK(cudaSetDevice(b->device));
-    BCK(cudaMalloc(&D.d_fields, sizeof(sht::FieldDesc) * fields.size()));
-    BCK(cudaMalloc(&D.d_units, sizeof(sht::UnitEntry) * std::max<size_t>(1, units.size())));
-    BCK(cudaMemcpy(D.d_fields, fields.data(), sizeof(sht::FieldDesc) * fields.size(), cudaMemcpyHostToDevice));
-    BCK(cudaMemcpy(D.d_units, units.data(), sizeof(sht::UnitEntry) * units.size(), cudaMemcpyHostToDevice));
+    for (int c = 0; c < kClasses; ++c) {
+      SubLaunch& U = D.sub[c];
+      if (gdesc[c].empty()) continue;
+      std::stable_sort(units[c].begin(), units[c].end(),
+                       [](const sht::UnitEntry& x, const sht::UnitEntry& y) { return x.len16 > y.len16; });
+      U.n_units = (int)units[c].size();
+      U.n_groups = (int)gdesc[c].size();
+      BCK(cudaMalloc(&U.d_fields, sizeof(sht::FieldDesc) * gdesc[c].size()));
+      BCK(cudaMalloc(&U.d_group_fields, sizeof(int) * gfields[c].size()));
+      BCK(cudaMalloc(&U.d_units, sizeof(sht::UnitEntry) * std::max<size_t>(1, units[c].size())));
+      BCK(cudaMemcpy(U.d_fields, gdesc[c].data(), sizeof(sht::FieldDesc) * gdesc[c].size(), cudaMemcpyHostToDevice));
+      BCK(cudaMemcpy(U.d_group_fields, gfields[c].data(), sizeof(int) * gfields[c].size(), cudaMemcpyHostToDevice));
+      BCK(cudaMemcpy(U.d_units, units[c].data(), sizeof(sht::UnitEntry) * units[c].size(), cudaMemcpyHostToDevice));
+    }
+    b->optin = (size_t)optin;
+    BCK(sht::sweep_configure(b->q, b->optin));
+    for (SubLaunch& U : D.sub)
+      if (U.n_groups && !sht::sweep_choose(b->q, b->page_bytes, U.capacity, 2, D.nw, D.slot_bytes, 1, b->optin, &U.cfg))
+        return SHT_ERR_UNSUPPORTED;
   }
-  BCK(cudaMalloc(&b->d_scratch, sizeof(unsigned) * (kDirs + 1)));
-  BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * (kDirs + 1)));
+  return SHT_OK;
+}
+
+sht_status build(sht_batch_t b, int nfields, const sht_plan_t* plans, sht_precision prec) {
+  for (int d = 0; d < kDirs; ++d) {
+    const sht_status s = build_dir(b, d, nfields, plans, prec, 4);
+    if (s != SHT_OK) return s;
+  }
+  BCK(cudaMalloc(&b->d_scratch, sizeof(unsigned) * (kDirs * kClasses + 1)));
+  BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * (kDirs * kClasses + 1)));
   b->plans.assign(plans, plans + nfields);
   BCK(cudaMalloc(&b->d_tables, sizeof(void*) * kRing * 2 * nfields));
   BCK(cudaMallocHost(&b->h_stage, sizeof(void*) * kRing * 2 * nfields));
   for (cudaEvent_t& e : b->ring_ev) BCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  int optin = 0;
-  BCK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device));
-  b->optin = (size_t)optin;
-  BCK(sht::sweep_configure(b->q, b->optin));
-  for (BatchDir& D : b->dir)
-    if (!sht::sweep_choose(b->q, b->page_bytes, D.buf_ab, D.num_vecs, D.cfg.nw, D.slot_bytes, 1, b->optin, &D.cfg))
-      return SHT_ERR_UNSUPPORTED;
   return SHT_OK;
 }
 
+// The launches of direction d, one per non-empty group size class, in order
+// on stream.
 sht_status launch(sht_batch_t b, int d, const void* const* in, void* const* out, sht_stream_t stream) {
   if (!b || !in || !out) return SHT_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) % alignof(void*)) return SHT_ERR_INVALID_ARG;
   const BatchDir& D = b->dir[d];
   BCK(cudaSetDevice(b->device));
-  sht::SweepArgs a{};
-  a.units = D.d_units;
-  a.n_units = D.n_units;
-  a.chunk_bytes = b->page_bytes;
-  a.buf_ab = D.buf_ab;
-  a.counter = b->d_scratch + d;
-  a.status = b->d_scratch + kDirs;
-  a.num_vecs = D.num_vecs;
-  a.slot_bytes = D.cfg.slot_bytes;
-  a.warp_slots = 1;
-  a.fields = D.d_fields;
-  a.field_in = in;
-  a.field_out = out;
-  a.io_align = (b->q == sht::PREC_FP32) ? 8 : 16;
-  const int grid = std::max(1, std::min(b->num_sms * D.cfg.ctas_per_sm, D.n_units));
-  (void)cudaGetLastError();
-  BCK(sht::sweep_launch(b->q, D.cfg.nw, a, grid, D.cfg.smem, reinterpret_cast<cudaStream_t>(stream)));
+  for (int c = 0; c < kClasses; ++c) {
+    const SubLaunch& U = D.sub[c];
+    if (!U.n_groups) continue;
+    sht::SweepArgs a{};
+    a.units = U.d_units;
+    a.n_units = U.n_units;
+    a.chunk_bytes = b->page_bytes;
+    a.buf_ab = U.capacity;
+    a.counter = b->d_scratch + d * kClasses + c;
+    a.status = b->d_scratch + kDirs * kClasses;
+    a.num_vecs = 2;
+    a.slot_bytes = U.cfg.slot_bytes;
+    a.warp_slots = 1;
+    a.fields = U.d_fields;
+    a.group_fields = U.d_group_fields;
+    a.field_in = in;
+    a.field_out = out;
+    a.io_align = (b->q == sht::PREC_FP32) ? 8 : 16;
+    a.fg = class_fg(c);
+    const int grid = std::max(1, std::min(b->num_sms * U.cfg.ctas_per_sm, U.n_units));
+    (void)cudaGetLastError();
+    BCK(sht::sweep_launch(b->q, D.nw, a, grid, U.cfg.smem, reinterpret_cast<cudaStream_t>(stream)));
+  }
   return SHT_OK;
 }
 
@@ -283,10 +373,10 @@ sht_status sht_batch_last_device_status(sht_batch_t b, sht_stream_t stream) {
   BCK(cudaSetDevice(b->device));
   BCK(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
   unsigned st = 0;
-  BCK(cudaMemcpy(&st, b->d_scratch + kDirs, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  BCK(cudaMemcpy(&st, b->d_scratch + kDirs * kClasses, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (st != 0) {
-    // a launch stopped early: its queue counter may not have been reset
-    BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * (kDirs + 1)));
+    // a launch stopped early: its queue counters may not have been reset
+    BCK(cudaMemset(b->d_scratch, 0, sizeof(unsigned) * (kDirs * kClasses + 1)));
     return (sht_status)st;
   }
   return SHT_OK;
@@ -295,22 +385,21 @@ sht_status sht_batch_last_device_status(sht_batch_t b, sht_stream_t stream) {
 sht_status sht_batch_autotune(sht_batch_t b, int direction, const void* const* in, void* const* out, int reps,
                               sht_stream_t stream) {
   if (!b || direction < 0 || direction >= kDirs || reps < 1) return SHT_ERR_INVALID_ARG;
-  BatchDir& D = b->dir[direction];
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   BCK(cudaSetDevice(b->device));
   // The plans' work items are scheduled for their consumer warps, which fixes
-  // the warps and the shared-memory layout of the launch; what remains to
-  // choose is the number of CTAs per SM where more than one fits.
-  const sht::SweepConfig keep = D.cfg;
-  sht::SweepConfig best = keep;
+  // the warps and the shared-memory layout of a launch; what is tuned is how
+  // many fields of one plan share a launch's reading of its factor stream
+  // (at most 1, 2 or 4 per group, as far as their vectors fit).
+  int best_cap = b->dir[direction].fcap;
   float best_ms = -1.f;
   sht_status result = SHT_OK;
   cudaEvent_t e0, e1;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
-  for (int ctas = 1; ctas <= std::max(1, keep.ctas_per_sm) && result == SHT_OK; ++ctas) {
-    D.cfg = keep;
-    D.cfg.ctas_per_sm = ctas;
+  for (int fcap : {1, 2, 4}) {
+    result = build_dir(b, direction, b->n, b->plans.data(), b->prec, fcap);
+    if (result != SHT_OK) break;
     result = launch(b, direction, in, out, stream);  // warm-up
     if (result != SHT_OK) break;
     cudaEventRecord(e0, st);
@@ -327,23 +416,44 @@ sht_status sht_batch_autotune(sht_batch_t b, int direction, const void* const* i
     cudaEventElapsedTime(&ms, e0, e1);
     if (best_ms < 0.f || ms < best_ms) {
       best_ms = ms;
-      best = D.cfg;
+      best_cap = fcap;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  D.cfg = (result == SHT_OK) ? best : keep;
-  return result;
+  const sht_status rebuilt = build_dir(b, direction, b->n, b->plans.data(), b->prec, best_cap);
+  return result != SHT_OK ? result : rebuilt;
 }
 
 sht_status sht_batch_get_config(sht_batch_t b, int direction, int* consumer_warps, int* nstages, int* ctas_per_sm,
                                 int* smem_bytes) {
   if (!b || direction < 0 || direction >= kDirs) return SHT_ERR_INVALID_ARG;
-  const sht::SweepConfig& c = b->dir[direction].cfg;
-  if (consumer_warps) *consumer_warps = c.nw;
+  const BatchDir& D = b->dir[direction];
+  int ctas = 0;
+  size_t smem = 0;
+  for (const SubLaunch& U : D.sub)
+    if (U.n_groups) {
+      ctas = ctas ? std::min(ctas, U.cfg.ctas_per_sm) : U.cfg.ctas_per_sm;
+      smem = std::max(smem, U.cfg.smem);
+    }
+  if (consumer_warps) *consumer_warps = D.nw;
   if (nstages) *nstages = 2;  // record chunks in flight per warp
-  if (ctas_per_sm) *ctas_per_sm = c.ctas_per_sm;
-  if (smem_bytes) *smem_bytes = (int)c.smem;
+  if (ctas_per_sm) *ctas_per_sm = ctas;
+  if (smem_bytes) *smem_bytes = (int)smem;
+  return SHT_OK;
+}
+
+sht_status sht_batch_get_groups(sht_batch_t b, int direction, int* max_fields_per_group, int* groups) {
+  if (!b || direction < 0 || direction >= kDirs) return SHT_ERR_INVALID_ARG;
+  const BatchDir& D = b->dir[direction];
+  int mx = 0, n = 0;
+  for (int c = 0; c < kClasses; ++c)
+    if (D.sub[c].n_groups) {
+      mx = std::max(mx, class_fg(c));
+      n += D.sub[c].n_groups;
+    }
+  if (max_fields_per_group) *max_fields_per_group = mx;
+  if (groups) *groups = n;
   return SHT_OK;
 }
 

@@ -367,6 +367,7 @@ sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, con
   a.num_vecs = P->num_vecs[q];
   a.slot_bytes = P->slot_bytes[q];
   a.warp_slots = 1;
+  a.fg = 1;
   a.counter = P->d_scratch + (kernel_prec(prec) * KIND_COUNT + kind);
   a.status = P->d_scratch + kStatusWord;
   const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));
@@ -412,6 +413,7 @@ sht_status sht::prepared_sweep(sht_plan_t P, sht_precision prec, int dir, const 
   a.num_vecs = P->num_vecs[q];
   a.slot_bytes = P->slot_bytes[q];
   a.warp_slots = 1;
+  a.fg = 1;
   L->prec = kernel_prec(prec);
   L->consumer_warps = P->consumer_warps[q];
   L->grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], D.n_units));

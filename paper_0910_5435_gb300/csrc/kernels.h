@@ -12,13 +12,18 @@ namespace sht {
 // the Legendre stage for every order m).
 // One field of a batched launch: its plan's factor stream (device memory,
 // set when the batch is created).
+// One field group of a batched launch: its plan's factor stream (device
+// memory, set when the batch is created) and the nf fields it applies it to
+// (group_fields[f0 .. f0 + nf), indices into the launch's pointer arrays).
 struct FieldDesc {
   const uint8_t* pages;
   const uint8_t* values;
   const double* prescale;      // FOLD prescale or nullptr
   const double2* twiddle;      // per-order phase or nullptr
   int l;
-  int pad;
+  int buf_ab;                  // elements of each field's shared vectors A and B
+  int f0;
+  int nf;
 };
 
 struct SweepArgs {
@@ -39,13 +44,17 @@ struct SweepArgs {
   int num_vecs;                // shared vectors (buffer ids 0 .. num_vecs-1)
   int slot_bytes;              // bytes of one value staging slot
   int warp_slots;              // staging slots per consumer warp: 1 or 2
-  // Batched launches (fields != nullptr): units[u].m is the item's field f;
-  // pages, values, l, prescale and twiddle come from fields[f], the field's
-  // input and output from field_in[f] and field_out[f] (device arrays).
+  // Batched launches (fields != nullptr): units[u].m is the item's field
+  // group g; pages, values, l, prescale, twiddle and the group's fields come
+  // from fields[g], each field k's input and output from field_in[k] and
+  // field_out[k] (device arrays).  buf_ab is then the launch's capacity:
+  // nf * buf_ab of every group fits in it.
   const FieldDesc* fields;
+  const int* group_fields;
   const void* const* field_in;
   void* const* field_out;
   int io_align;                // required alignment (bytes) of field_in / field_out entries
+  int fg;                      // fields per group the kernel handles (1; batched launches 1, 2 or 4)
 };
 
 // Launch shape of a sweep: consumer warps (the warps the streams were

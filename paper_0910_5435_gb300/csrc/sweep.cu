@@ -319,12 +319,14 @@ struct TF32 {
 
 // ------------------------------------------------------------ ops
 
+// The shared vectors of one item: for each field f of its group, vectors
+// A and B of buf_ab elements (field-major: [f][A, B][buf_ab]).
 template <class TR>
 struct Vecs {
   using C = typename TR::C;
   C* base;
   int buf_ab;
-  __device__ C* buf(int id) const { return base + (size_t)id * buf_ab; }
+  __device__ C* buf(int id, int f = 0) const { return base + ((size_t)f * kNumVecs + id) * buf_ab; }
 };
 
 __device__ __forceinline__ size_t tri_off(int m, int L) { return (size_t)m * L - (size_t)m * (m - 1) / 2; }
@@ -360,39 +362,120 @@ __device__ __forceinline__ typename TR::Acc gemv_dot(const typename TR::V* val, 
   return a[0];
 }
 
+// The same for the fields 0..nf-1 of a group (nf <= FG): each staged value
+// is loaded once and applied to every field's input, in the same order and
+// with the same chains per field as gemv_dot (the results are the same bits).
+template <class TR, int FG>
+__device__ __forceinline__ void gemv_dot_fields(const typename TR::V* val, const typename TR::C* const* in,
+                                                const uint16_t* idx, bool gather, int M, int K, int o, int q,
+                                                int ks, int nf, typename TR::Acc (&out)[FG]) {
+  using V = typename TR::V;
+  using Acc = typename TR::Acc;
+  constexpr int U = 4;
+  constexpr int NC = TR::kChains;
+  Acc a[FG][NC];
+#pragma unroll
+  for (int f = 0; f < FG; ++f)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) a[f][c] = TR::zero();
+  int s = q;
+  for (; s + (U - 1) * ks < K; s += U * ks) {
+    V v[U];
+    int xi[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int su = s + u * ks;
+      v[u] = val[(size_t)su * M + o];
+      xi[u] = gather ? (int)idx[su] : su;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int f = 0; f < FG; ++f)
+        if (f < nf) TR::fma(a[f][u % NC], v[u], in[f][xi[u]]);
+  }
+  for (; s < K; s += ks) {
+    const V v = val[(size_t)s * M + o];
+    const int xi = gather ? (int)idx[s] : s;
+#pragma unroll
+    for (int f = 0; f < FG; ++f)
+      if (f < nf) TR::fma(a[f][0], v, in[f][xi]);
+  }
+#pragma unroll
+  for (int f = 0; f < FG; ++f) {
+#pragma unroll
+    for (int c = 1; c < NC; ++c) TR::merge(a[f][0], a[f][c]);
+    out[f] = a[f][0];
+  }
+}
+
 // floor(32 / M) for M = 0..32, and ceil(65536 / d) for d = 0..32.
 __constant__ unsigned char c_lanes_per_out[33] = {0, 32, 16, 10, 8, 6, 5, 4, 4, 3, 3, 2, 2, 2, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 __constant__ unsigned c_inv16[33] = {0, 65536, 32768, 21846, 16384, 13108, 10923, 9363, 8192, 7282, 6554, 5958, 5462, 5042, 4682, 4370, 4096, 3856, 3641, 3450, 3277, 3121, 2979, 2850, 2731, 2622, 2521, 2428, 2341, 2260, 2185, 2115, 2048};
 
 // What an op needs of its field: the launch's own arguments, or one field
 // of a batched launch.
+// What an op needs of its fields: the launch's own arguments (one field), or
+// one group of a batched launch (nf fields sharing a plan, whose inputs and
+// outputs come from the device pointer arrays, listed by group_fields).
+template <int FG>
 struct FieldCtx {
   const uint8_t* values;
-  const void* in;
-  void* out;
+  const void* in[FG];
+  void* out[FG];
   const double* prescale;
   const double2* twiddle;
   int l;
+  int nf;
+  int buf_ab;
 };
-__device__ __forceinline__ FieldCtx field_ctx(const SweepArgs& A, int f) {
-  if (!A.fields) return {A.values, A.in, A.out, A.prescale, A.twiddle, A.l};
-  const FieldDesc& d = A.fields[f];
-  return {d.values, A.field_in[f], A.field_out[f], d.prescale, d.twiddle, d.l};
+template <int FG>
+__device__ __forceinline__ FieldCtx<FG> field_ctx(const SweepArgs& A, int g) {
+  FieldCtx<FG> c;
+  if (!A.fields) {
+    c.values = A.values;
+    c.prescale = A.prescale;
+    c.twiddle = A.twiddle;
+    c.l = A.l;
+    c.nf = 1;
+    c.buf_ab = A.buf_ab;
+#pragma unroll
+    for (int f = 0; f < FG; ++f) {
+      c.in[f] = A.in;
+      c.out[f] = A.out;
+    }
+    return c;
+  }
+  const FieldDesc& d = A.fields[g];
+  c.values = d.values;
+  c.prescale = d.prescale;
+  c.twiddle = d.twiddle;
+  c.l = d.l;
+  c.nf = min(d.nf, FG);
+  c.buf_ab = d.buf_ab;
+#pragma unroll
+  for (int f = 0; f < FG; ++f) {
+    const int k = A.group_fields[d.f0 + (f < c.nf ? f : 0)];
+    c.in[f] = A.field_in[k];
+    c.out[f] = A.field_out[k];
+  }
+  return c;
 }
 
-// One compute op (SYN_INTERP, DENSE, DENSE_G, ANA_INTERP), executed by one warp.
-template <class TR, class AfterRead>
-__device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, const Vecs<TR>& S, const FieldCtx& A,
-                                         int lane, const uint8_t* staged, AfterRead after_read) {
+// One compute op (SYN_INTERP, DENSE, DENSE_G, ANA_INTERP), executed by one
+// warp for every field of the item's group.
+template <class TR, int FG, class AfterRead>
+__device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, const Vecs<TR>& S,
+                                         const FieldCtx<FG>& A, int lane, const uint8_t* staged,
+                                         AfterRead after_read) {
   using C = typename TR::C;
   using V = typename TR::V;
   using Acc = typename TR::Acc;
   using IO = typename TR::IO;
   const int M = h.M, K = h.K;
+  const int nf = A.nf;
   const uint16_t* idx = reinterpret_cast<const uint16_t*>(op + sizeof(OpHdr)) + h.npred;
   const V* val = reinterpret_cast<const V*>(staged);  // this warp's staging slot
-  const C* in = S.buf(h.in_buf) + h.io;
-  C* out = S.buf(h.out_buf) + h.oo;
   const bool gather = (h.kind == OP_SYN_INTERP);
   const bool accum = (h.flags & F_ACCUM) != 0;
   if (M > 0) {
@@ -402,117 +485,144 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
     // for lane < 32 and ks <= 32.
     const int ks = c_lanes_per_out[M];
     const int o = (lane * c_inv16[ks]) >> 16, q = lane - o * ks;
-    Acc a0 = TR::zero();
-    if (o < M) a0 = gemv_dot<TR>(val, in, idx, gather, M, K, o, q, ks);
-    after_read();  // every lane is done with the staged values
-    // segmented tree: after the step with offset d, lane q holds the sum over
-    // q .. min(q + 2d - 1, ks - 1) of its segment
-    for (int off = 1; off < ks; off <<= 1) {
-      const Acc b = TR::shfl_down(a0, off);
-      if (q + off < ks) TR::merge(a0, b);
+    Acc a[FG];
+    if constexpr (FG == 1) {
+      a[0] = TR::zero();
+      if (o < M) a[0] = gemv_dot<TR>(val, S.buf(h.in_buf) + h.io, idx, gather, M, K, o, q, ks);
+    } else {
+      const C* inp[FG];
+#pragma unroll
+      for (int f = 0; f < FG; ++f) inp[f] = S.buf(h.in_buf, f) + h.io;
+      if (o < M) {
+        gemv_dot_fields<TR, FG>(val, inp, idx, gather, M, K, o, q, ks, nf, a);
+      } else {
+#pragma unroll
+        for (int f = 0; f < FG; ++f) a[f] = TR::zero();
+      }
     }
-    if (q == 0 && o < M) {
-      switch (h.kind) {
-        case OP_SYN_INTERP:
-          TR::add(a0, in[idx[K + o]]);
-          out[o] = TR::to_c(a0);
-          break;
-        case OP_DENSE:
-          out[o] = TR::to_c(a0);
-          break;
-        case OP_ANA_INTERP: {
-          const int pos = idx[o];
-          if (accum) TR::add(a0, out[pos]);
-          out[pos] = TR::to_c(a0);
-          break;
-        }
-        case OP_DENSE_G: {
-          const int l = A.l;
-          const int i = h.oo + o;
-          IO v = TR::to_io(TR::to_c(a0));
-          if (A.twiddle) v = TR::io_cmul(v, A.twiddle[h.a1]);
-          IO* G = reinterpret_cast<IO*>(A.out) + (size_t)h.a1 * (2 * l);
-          if (accum) {
-            G[l + i] = TR::io_add(G[l + i], v);
-            G[l - 1 - i] = TR::io_sub(G[l - 1 - i], v);
-          } else {
-            G[l + i] = v;
-            G[l - 1 - i] = v;
+    after_read();  // every lane is done with the staged values
+#pragma unroll
+    for (int f = 0; f < FG; ++f) {
+      if (f >= nf) break;
+      Acc a0 = a[f];
+      // segmented tree: after the step with offset d, lane q holds the sum
+      // over q .. min(q + 2d - 1, ks - 1) of its segment
+      for (int off = 1; off < ks; off <<= 1) {
+        const Acc b = TR::shfl_down(a0, off);
+        if (q + off < ks) TR::merge(a0, b);
+      }
+      if (q == 0 && o < M) {
+        const C* in = S.buf(h.in_buf, f) + h.io;
+        C* out = S.buf(h.out_buf, f) + h.oo;
+        switch (h.kind) {
+          case OP_SYN_INTERP:
+            TR::add(a0, in[idx[K + o]]);
+            out[o] = TR::to_c(a0);
+            break;
+          case OP_DENSE:
+            out[o] = TR::to_c(a0);
+            break;
+          case OP_ANA_INTERP: {
+            const int pos = idx[o];
+            if (accum) TR::add(a0, out[pos]);
+            out[pos] = TR::to_c(a0);
+            break;
           }
-          break;
+          case OP_DENSE_G: {
+            const int l = A.l;
+            const int i = h.oo + o;
+            IO v = TR::to_io(TR::to_c(a0));
+            if (A.twiddle) v = TR::io_cmul(v, A.twiddle[h.a1]);
+            IO* G = reinterpret_cast<IO*>(A.out[f]) + (size_t)h.a1 * (2 * l);
+            if (accum) {
+              G[l + i] = TR::io_add(G[l + i], v);
+              G[l - 1 - i] = TR::io_sub(G[l - 1 - i], v);
+            } else {
+              G[l + i] = v;
+              G[l - 1 - i] = v;
+            }
+            break;
+          }
+          default:
+            break;
         }
-        default:
-          break;
       }
     }
   }
   if (h.kind == OP_ANA_INTERP && (h.flags & F_SKEL)) {
     const uint16_t* skel = idx + M;
-    for (int t = lane; t < h.nskel; t += 32) {
-      const int pos = skel[t];
-      if (accum) {
-        Acc r = TR::from_c(out[pos]);
-        TR::add(r, in[t]);
-        out[pos] = TR::to_c(r);
-      } else {
-        out[pos] = in[t];
+    for (int f = 0; f < nf; ++f) {
+      const C* in = S.buf(h.in_buf, f) + h.io;
+      C* out = S.buf(h.out_buf, f) + h.oo;
+      for (int t = lane; t < h.nskel; t += 32) {
+        const int pos = skel[t];
+        if (accum) {
+          Acc r = TR::from_c(out[pos]);
+          TR::add(r, in[t]);
+          out[pos] = TR::to_c(r);
+        } else {
+          out[pos] = in[t];
+        }
       }
     }
   }
 }
 
-// One control op over the element range [oo, oo + M), executed by one warp.
-template <class TR>
-__device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, const FieldCtx& A, int lane) {
+// One control op over the element range [oo, oo + M), executed by one warp
+// for every field of the item's group.
+template <class TR, int FG>
+__device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, const FieldCtx<FG>& A, int lane) {
   using C = typename TR::C;
   using IO = typename TR::IO;
   const int l = A.l, L = 2 * l;
   const int m = (int)h.a1;
   const int n = h.M;
   const int parity = h.a0 & 1, base = h.a0 >> 1;  // GATHER / SCATTER / FOLD
-  switch (h.kind) {
-    case OP_GATHER: {
-      const IO* beta = reinterpret_cast<const IO*>(A.in) + tri_off(m, L) + parity;
-      C* dst = S.buf(h.out_buf) + base;
-      for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::from_io(beta[2 * (size_t)j]);
-      break;
-    }
-    case OP_SCATTER: {
-      IO* beta = reinterpret_cast<IO*>(A.out) + tri_off(m, L) + parity;
-      const C* src = S.buf(h.in_buf) + base;
-      for (int j = h.io + lane; j < h.io + n; j += 32) beta[2 * (size_t)j] = TR::to_io(src[j]);
-      break;
-    }
-    case OP_FOLD: {
-      const IO* G = reinterpret_cast<const IO*>(A.in) + (size_t)m * L;
-      C* dst = S.buf(h.out_buf) + base;
-      for (int r = h.oo + lane; r < h.oo + n; r += 32) {
-        IO gp = G[l + r], gm = G[l - 1 - r];
-        if (A.twiddle) {
-          gp = TR::io_cmul(gp, A.twiddle[m]);
-          gm = TR::io_cmul(gm, A.twiddle[m]);
+  for (int f = 0; f < A.nf; ++f) {
+    switch (h.kind) {
+      case OP_GATHER: {
+        const IO* beta = reinterpret_cast<const IO*>(A.in[f]) + tri_off(m, L) + parity;
+        C* dst = S.buf(h.out_buf, f) + base;
+        for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::from_io(beta[2 * (size_t)j]);
+        break;
+      }
+      case OP_SCATTER: {
+        IO* beta = reinterpret_cast<IO*>(A.out[f]) + tri_off(m, L) + parity;
+        const C* src = S.buf(h.in_buf, f) + base;
+        for (int j = h.io + lane; j < h.io + n; j += 32) beta[2 * (size_t)j] = TR::to_io(src[j]);
+        break;
+      }
+      case OP_FOLD: {
+        const IO* G = reinterpret_cast<const IO*>(A.in[f]) + (size_t)m * L;
+        C* dst = S.buf(h.out_buf, f) + base;
+        for (int r = h.oo + lane; r < h.oo + n; r += 32) {
+          IO gp = G[l + r], gm = G[l - 1 - r];
+          if (A.twiddle) {
+            gp = TR::io_cmul(gp, A.twiddle[m]);
+            gm = TR::io_cmul(gm, A.twiddle[m]);
+          }
+          IO e = parity ? TR::io_sub(gp, gm) : TR::io_add(gp, gm);
+          if (A.prescale) e = TR::io_scale(e, A.prescale[r]);
+          dst[r] = TR::from_io(e);
         }
-        IO e = parity ? TR::io_sub(gp, gm) : TR::io_add(gp, gm);
-        if (A.prescale) e = TR::io_scale(e, A.prescale[r]);
-        dst[r] = TR::from_io(e);
+        break;
       }
-      break;
-    }
-    case OP_CLEAR: {
-      C* dst = S.buf(h.out_buf);
-      for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::czero();
-      break;
-    }
-    case OP_GZERO: {
-      IO* G = reinterpret_cast<IO*>(A.out) + (size_t)m * L;
-      for (int r = h.oo + lane; r < h.oo + n; r += 32) {
-        G[l + r] = TR::io_zero();
-        G[l - 1 - r] = TR::io_zero();
+      case OP_CLEAR: {
+        C* dst = S.buf(h.out_buf, f);
+        for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::czero();
+        break;
       }
-      break;
+      case OP_GZERO: {
+        IO* G = reinterpret_cast<IO*>(A.out[f]) + (size_t)m * L;
+        for (int r = h.oo + lane; r < h.oo + n; r += 32) {
+          G[l + r] = TR::io_zero();
+          G[l - 1 - r] = TR::io_zero();
+        }
+        break;
+      }
+      default:
+        break;
     }
-    default:
-      break;
   }
 }
 
@@ -568,8 +678,8 @@ __device__ __forceinline__ bool warp_wait(Pred pred, const SweepArgs& A, Ctl* S,
 }
 
 // One warp's walk over its scheduled ops of every item its CTA takes.
-template <class TR, int NW>
-__device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int warp, int lane, uint8_t* ring,
+template <class TR, int NW, int FG>
+__device__ void warp_loop(const SweepArgs& A, Ctl* S, typename TR::C* vec_base, int warp, int lane, uint8_t* ring,
                           uint64_t* ring_bar, uint8_t* slot, uint64_t* slot_bar) {
   using Val = typename TR::V;
   const uint32_t CH = (uint32_t)A.chunk_bytes;  // a power of two
@@ -593,8 +703,9 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
       vstore(&S->item[(seq + 1) & 1], u);
     }
     const UnitEntry e = A.units[item];
-    const int field = A.fields ? (int)e.m : 0;
-    const FieldCtx F = field_ctx(A, field);
+    const int field = A.fields ? (int)e.m : 0;  // batched launches: the item's field group
+    const FieldCtx<FG> F = field_ctx<FG>(A, field);
+    const Vecs<TR> V{vec_base, F.buf_ab};
     const uint8_t* region = A.fields ? A.fields[field].pages : A.pages;
     const uint8_t* item_base = region + e.off16 * 16;
     // this warp's record stream; a stream scheduled for another warp count,
@@ -605,10 +716,11 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
       const WarpRange wr = reinterpret_cast<const WarpRange*>(item_base + sizeof(ItemHeader))[warp];
       bool bad = ih.magic != kItemMagic || ih.nw != NW || (wr.off & 15u) || (wr.bytes & 15u) ||
                  (uint64_t)wr.off + wr.bytes > (uint64_t)e.len16 * 16;
-      if (A.fields) {
-        const uintptr_t io = reinterpret_cast<uintptr_t>(F.in) | reinterpret_cast<uintptr_t>(F.out);
-        bad = bad || !F.in || !F.out || (io & (uintptr_t)(A.io_align - 1));
-      }
+      if (A.fields)
+        for (int f = 0; f < F.nf; ++f) {
+          const uintptr_t io = reinterpret_cast<uintptr_t>(F.in[f]) | reinterpret_cast<uintptr_t>(F.out[f]);
+          bad = bad || !F.in[f] || !F.out[f] || (io & (uintptr_t)(A.io_align - 1));
+        }
       if (bad) fail(A, S, kStatusBadArg);
       off = bad ? 0 : wr.off;
       len = bad ? 0 : wr.bytes;
@@ -769,11 +881,11 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, const Vecs<TR>& V, int war
       }
       const long long t3 = tracing ? clock64() : 0;
       if (gemv) {
-        run_gemv<TR>(h, rec, V, F, lane, slot, [&] {
+        run_gemv<TR, FG>(h, rec, V, F, lane, slot, [&] {
           if (!slot_busy) prefetch();
         });
       } else {
-        run_control<TR>(h, V, F, lane);
+        run_control<TR, FG>(h, V, F, lane);
       }
       if (!slot_busy) prefetch();  // ops without a value block
       const long long t4 = tracing ? clock64() : 0;
@@ -843,7 +955,7 @@ __host__ __device__ inline size_t sweep_warp_bytes(int chunk_bytes, int slot_byt
   return (2 * (size_t)chunk_bytes + (size_t)slot_bytes + 127) & ~size_t(127);
 }
 
-template <class TR, int NW>
+template <class TR, int NW, int FG>
 __global__ void __launch_bounds__(NW * 32, 1) bfly_sweep_kernel(const SweepArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -852,7 +964,7 @@ __global__ void __launch_bounds__(NW * 32, 1) bfly_sweep_kernel(const SweepArgs 
   uint8_t* mine = smem + vec_bytes + (size_t)warp * wb;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + vec_bytes + (size_t)NW * wb);
   Ctl* S = reinterpret_cast<Ctl*>(bars + 4 * NW);
-  const Vecs<TR> V{reinterpret_cast<typename TR::C*>(smem), A.buf_ab};
+
   if (tid == 0) {
     for (int s = 0; s < 4 * NW; ++s) mbar_init(bars + s, 1);
     for (int w = 0; w < kMaxWarps; ++w) S->progress[w] = 0;
@@ -865,8 +977,8 @@ __global__ void __launch_bounds__(NW * 32, 1) bfly_sweep_kernel(const SweepArgs 
     fence_mbar_init();
   }
   __syncthreads();
-  warp_loop<TR, NW>(A, S, V, warp, lane, mine, bars + 4 * warp, mine + 2 * (size_t)A.chunk_bytes,
-                    bars + 4 * warp + 2);
+  warp_loop<TR, NW, FG>(A, S, reinterpret_cast<typename TR::C*>(smem), warp, lane, mine, bars + 4 * warp,
+                        mine + 2 * (size_t)A.chunk_bytes, bars + 4 * warp + 2);
 }
 
 template <class TR>
@@ -889,37 +1001,43 @@ size_t sweep_smem_bytes(int prec, int chunk_bytes, int buf_ab, int num_vecs, int
 
 namespace {
 
-// Host dispatch over (precision, consumer warps).
+// Host dispatch over (precision, consumer warps, fields per group); groups
+// of 2 or 4 fields run with 16 warps only.
 template <class TR>
-const void* kernel_ptr(int nw) {
+const void* kernel_ptr(int nw, int fg) {
+  if (nw == 16 && fg == 4) return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 16, 4>);
+  if (nw == 16 && fg == 2) return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 16, 2>);
   switch (nw) {
-    case 8: return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 8>);
-    case 12: return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 12>);
-    default: return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 16>);
+    case 8: return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 8, 1>);
+    case 12: return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 12, 1>);
+    default: return reinterpret_cast<const void*>(bfly_sweep_kernel<TR, 16, 1>);
   }
 }
-const void* kernel_for(int prec, int nw) {
+const void* kernel_for(int prec, int nw, int fg) {
   switch (prec) {
-    case PREC_FP64: return kernel_ptr<TF64>(nw);
-    case PREC_FP32: return kernel_ptr<TF32>(nw);
-    case PREC_SPLIT32_ACC64: return kernel_ptr<TS32A>(nw);
-    default: return kernel_ptr<TS32>(nw);
+    case PREC_FP64: return kernel_ptr<TF64>(nw, fg);
+    case PREC_FP32: return kernel_ptr<TF32>(nw, fg);
+    case PREC_SPLIT32_ACC64: return kernel_ptr<TS32A>(nw, fg);
+    default: return kernel_ptr<TS32>(nw, fg);
   }
 }
 
 }  // namespace
 
 cudaError_t sweep_configure(int prec, size_t smem) {
-  for (int nw : {8, 12, 16}) {
-    cudaError_t e = cudaFuncSetAttribute(kernel_for(prec, nw), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  for (int nw : {8, 12, 16})
+    for (int fg : {1, 2, 4}) {
+      if (fg > 1 && nw != 16) continue;
+      cudaError_t e =
+          cudaFuncSetAttribute(kernel_for(prec, nw, fg), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
   return cudaSuccess;
 }
 
 int sweep_blocks_per_sm(int prec, int nw, size_t smem) {
   int nb = 0;
-  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(prec, nw), nw * 32, smem);
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(prec, nw, 1), nw * 32, smem);
   return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
@@ -942,8 +1060,9 @@ cudaError_t sweep_launch(int prec, int nw, const SweepArgs& a, int grid, size_t 
   if (nw != 8 && nw != 12 && nw != 16) return cudaErrorInvalidValue;
   if (a.chunk_bytes < kMinChunkBytes || a.chunk_bytes > kMaxChunkBytes || (a.chunk_bytes & 255)) return cudaErrorInvalidValue;
   if (a.slot_bytes <= 0 || (a.slot_bytes & 15)) return cudaErrorInvalidValue;
+  if (a.fg != 1 && !(nw == 16 && (a.fg == 2 || a.fg == 4) && a.fields)) return cudaErrorInvalidValue;
   void* args[] = {const_cast<SweepArgs*>(&a)};
-  return cudaLaunchKernel(kernel_for(prec, nw), dim3(grid), dim3(nw * 32), args, smem, st);
+  return cudaLaunchKernel(kernel_for(prec, nw, a.fg), dim3(grid), dim3(nw * 32), args, smem, st);
 }
 
 }  // namespace sht

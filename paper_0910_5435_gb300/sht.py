@@ -37,7 +37,7 @@ EXPORTS = [
     "sht_unit_stats_compute", "sht_gauss_jacobi_nodes", "sht_unit_stats_gauss_jacobi",
     "sht_plan_save", "sht_plan_load", "sht_batch_synthesize_grid", "sht_batch_analyze_grid",
     "sht_measure_fp64_fma", "sht_interp_decomp", "sht_plan_stats", "sht_batched_workspace_bytes",
-    "sht_synthesize_batched", "sht_analyze_batched",
+    "sht_synthesize_batched", "sht_analyze_batched", "sht_batch_get_groups",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -169,6 +169,7 @@ def lib():
     L.sht_batch_autotune.argtypes = [vp, c_int, vp, vp, c_int, vp]
     L.sht_batch_get_config.argtypes = [vp, c_int, vp, vp, vp, vp]
     L.sht_plan_stats.argtypes = [vp, ctypes.POINTER(sht_plan_stats_t)]
+    L.sht_batch_get_groups.argtypes = [vp, c_int, vp, vp]
     L.sht_batched_workspace_bytes.argtypes = [c_int, vp, c_int]
     L.sht_batched_workspace_bytes.restype = ctypes.c_size_t
     L.sht_synthesize_batched.argtypes = [c_int, vp, c_int, vp, vp, vp, vp]
@@ -416,6 +417,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def groups(self, direction):
+        """(largest group size class, number of groups) of a direction
+        (sht_batch_get_groups): fields sharing a plan are applied together."""
+        mx, n = ctypes.c_int(), ctypes.c_int()
+        _check(lib().sht_batch_get_groups(self.handle, int(direction), ctypes.byref(mx), ctypes.byref(n)),
+               "sht_batch_get_groups")
+        return mx.value, n.value
 
     def config(self, direction):
         v = [ctypes.c_int() for _ in range(4)]

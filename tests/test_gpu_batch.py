@@ -266,3 +266,42 @@ def test_batched_spellings_match_oracle(sht, plans, prec):
     B.close()
     st = sht.sht_plan_stats(pl[0])
     assert st == pl[0].stats() and st["l"] == ls[0]
+
+
+@pytest.mark.parametrize("prec", [0, 2, 3, 1])
+def test_fields_sharing_a_plan_run_in_groups(sht, plans, prec):
+    """Fields that share a plan run in groups: each op's values are staged
+    once and applied to every field of the group.  Nine fields of one plan
+    form three groups of three (balanced, at most four per group), a plan
+    that appears once stays alone; every field equals its per-field call bit
+    for bit in both directions, also after the autotuner has chosen the cap
+    on fields per group."""
+    pl = [plans[64]] * 9 + [plans[128]]
+    ls = [64] * 9 + [128]
+    for p in set(pl):
+        p.prepare(prec)
+    B = sht.Batch(pl, prec)
+    assert B.groups(0) == (4, 4)  # three groups of three fields, one of one
+    betas, Gs = fields(ls, prec, 9500)
+    Gin = [torch.from_numpy(inputs.random_G(l, seed=9600 + f)).to(CDT[prec]).cuda() for f, l in enumerate(ls)]
+    backs = [torch.full_like(b, float("nan")) for b in betas]
+
+    def check():
+        sht.sht_batch_synthesize(B, sht.pointer_array(betas), sht.pointer_array(Gs))
+        sht.sht_batch_analyze(B, sht.pointer_array(Gin), sht.pointer_array(backs))
+        assert sht.sht_batch_last_device_status(B) == 0
+        for p, beta, G, g, back in zip(pl, betas, Gs, Gin, backs):
+            ref = torch.full_like(G, float("nan"))
+            sht.sht_legendre_synthesize(p, prec, beta, ref)
+            rb = torch.full_like(back, float("nan"))
+            sht.sht_legendre_analyze(p, prec, g, rb)
+            torch.cuda.synchronize()
+            assert torch.equal(G, ref) and torch.equal(back, rb)
+        l = ls[0]
+        assert rel(Gs[0], oracle.legendre_synthesis(betas[0].cpu().numpy().astype(np.complex128), l)) < TOL[prec]
+
+    check()
+    sht.sht_batch_autotune(B, 0, sht.pointer_array(betas), sht.pointer_array(Gs), reps=2)
+    assert B.groups(0)[0] in (1, 2, 4)
+    check()
+    B.close()
