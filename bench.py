@@ -59,13 +59,16 @@ def parse():
     return ap.parse_args()
 
 
-# DRAM traffic of one float64 sweep launch at l = 1024 (leaf_cols 32, 8 KB
-# pages), dram__bytes_read.sum + dram__bytes_write.sum from a one-pass ncu
-# capture, mean of a synthesis (6.517 GB) and an analysis (6.405 GB) launch.
-# Valid only for the kernel and stream-format sources it was taken with:
-# SWEEP_SOURCES_SHA is their hash.
-SWEEP_TRAFFIC_BYTES = {"l": 1024, "leaf_cols": 32, "page_bytes": 8192, "bytes": 6.4581e9}
-SWEEP_SOURCES_SHA = "f40ffdc2b0b6a0f3"
+# DRAM traffic of the float64 sweep, from a small capture: dram__bytes_read.sum
+# + dram__bytes_write.sum of one synthesis and one analysis launch at l = 512
+# (leaf_cols 32, the default record chunk), both per launch, beside that
+# plan's float64 stream bytes.  A launch at another l is credited with the
+# same bytes per stream byte (traffic scales with the stream: every value is
+# read once, beta and G are under 1 % of it).  Valid only for the kernel and
+# stream-format sources the capture was taken with (sources_sha); None when
+# no capture matches.
+SWEEP_TRAFFIC_CAPTURE = {"l": 512, "leaf_cols": 32, "page_bytes": 0, "stream_bytes": None,
+                         "dram_bytes_syn": None, "dram_bytes_ana": None, "sources_sha": None}
 
 
 def sweep_sources_sha():
@@ -229,11 +232,33 @@ if path != "-":
     Ge = oracle.legendre_synthesis(beta, l, orders=me)  # untimed: the scored orders
     off = oracle.triangle_offsets(l)
     sel = np.concatenate([np.arange(off[m], off[m + 1]) for m in me])
-    for name in sorted({k.rsplit("_", 1)[0] for k in d.files}):
-        G, b = d[name + "_G"], d[name + "_beta"]
-        out["rel_synth_" + name] = float(np.linalg.norm(G[me] - Ge[me]) / np.linalg.norm(Ge[me]))
-        ba = oracle.legendre_analysis(G, l, orders=me)
-        out["rel_analysis_" + name] = float(np.linalg.norm(b[sel] - ba[sel]) / np.linalg.norm(ba[sel]))
+    def score(tag, G, b, lf, bf):
+        mf = list(range(0, 2 * lf, err_stride))
+        Gf = Ge if (lf, bf) == (l, "main") else oracle.legendre_synthesis(bf, lf, orders=mf)
+        of = oracle.triangle_offsets(lf)
+        sf = np.concatenate([np.arange(of[m], of[m + 1]) for m in mf])
+        out["rel_synth_" + tag] = float(np.linalg.norm(G[mf] - Gf[mf]) / np.linalg.norm(Gf[mf]))
+        ba = oracle.legendre_analysis(G, lf, orders=mf)
+        out["rel_analysis_" + tag] = float(np.linalg.norm(b[sf] - ba[sf]) / np.linalg.norm(ba[sf]))
+    names = sorted({k.rsplit("_", 1)[0] for k in d.files})
+    for name in names:
+        if name.startswith("bt_"):  # one field of the batched leg: bt_<l>_<seed>
+            _, lf, sd = name.split("_")
+            lf, sd = int(lf), int(sd)
+            score("batched_l%d" % lf, d[name + "_G"], d[name + "_beta"], lf,
+                  inputs.random_beta(lf, seed=sd, decay=True))
+        elif name.startswith("ag_"):  # autograd gradient of field 0: ag_<path>_<l>
+            _, pname, lf = name.split("_")
+            lf = int(lf)
+            gr = d[name + "_grad"]
+            mf = list(range(0, 2 * lf, err_stride))
+            of = oracle.triangle_offsets(lf)
+            sf = np.concatenate([np.arange(of[m], of[m + 1]) for m in mf])
+            db = inputs.random_beta(lf, seed=5000, decay=True) - inputs.random_beta(lf, seed=6000, decay=True)
+            ref = 2.0 * oracle.legendre_adjoint(oracle.legendre_synthesis(db, lf, orders=mf), lf, orders=mf)
+            out["rel_grad_" + pname] = float(np.linalg.norm(gr[sf] - ref[sf]) / np.linalg.norm(ref[sf]))
+        else:
+            score(name, d[name + "_G"], d[name + "_beta"], l, "main")
 print(json.dumps(out))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
@@ -381,13 +406,22 @@ def batched_leg(args, sht, inputs, torch, dev, stream, plan, rank=0, world=1, di
         ms_loop = timed(loop, steps)
         same = all(torch.equal(a, b) for a, b in zip(Gb, Gs)) and all(torch.equal(a, b) for a, b in zip(kb, backs))
         eps_inv = max(float(torch.linalg.vector_norm(k - b) / torch.linalg.vector_norm(b)) for k, b in zip(kb, betas))
+        first = {}
+        for i, f in enumerate(mine):
+            first.setdefault(all_ls[f], (i, f))
+        for lf, (i, f) in first.items():
+            samples[f"bt_{lf}_{1000 + f}_G"] = Gb[i].cpu().numpy()
+            samples[f"bt_{lf}_{1000 + f}_beta"] = kb[i].cpu().numpy()
+        groups = [B.groups(0), B.groups(1)]
         B.close()
-        return ms_batch, ms_loop, eps_inv, same, status, cfg_syn, cfg_ana, t_plans
+        return ms_batch, ms_loop, eps_inv, same, status, cfg_syn, cfg_ana, t_plans, groups
 
+    samples = {}
     if ls:
-        ms_batch, ms_loop, eps_inv, same, status, cfg_syn, cfg_ana, t_plans = run_local()
+        ms_batch, ms_loop, eps_inv, same, status, cfg_syn, cfg_ana, t_plans, groups = run_local()
     else:  # more ranks than fields: this rank has nothing to do
-        ms_batch, ms_loop, eps_inv, same, status, cfg_syn, cfg_ana, t_plans = 0.0, 0.0, 0.0, True, 0, None, None, 0.0
+        ms_batch, ms_loop, eps_inv, same, status, cfg_syn, cfg_ana, t_plans, groups = (
+            0.0, 0.0, 0.0, True, 0, None, None, 0.0, None)
     ms_batch = max_over_ranks(ms_batch, world, dist, dev)
     ms_loop = max_over_ranks(ms_loop, world, dist, dev)
     eps_inv = max_over_ranks(eps_inv, world, dist, dev)
@@ -400,6 +434,7 @@ def batched_leg(args, sht, inputs, torch, dev, stream, plan, rank=0, world=1, di
         "speedup_vs_loop": ms_loop / ms_batch, "batch_equals_loop": same, "max_eps_inv": eps_inv,
         "device_status": status, "autotuned": {"synthesis": cfg_syn, "analysis": cfg_ana},
         "launches": {"batched": 2, "loop": 2 * len(ls)}, "cuda_graph": True, "t_plans_s": t_plans,
+        "field_groups": groups, "_samples": samples,
     }
 
 
@@ -445,8 +480,8 @@ def autograd_leg(args, sht, inputs, torch, dev, stream):
     ||synthesize(beta) - g||^2 with g the synthesis of an independent
     band-limited beta_g (seeds 5000 + f and 6000 + f); forward plus the
     hand-written backward (the transposed butterfly) timed for the float64
-    and split float32 paths.  Gradient accuracy against the oracle and
-    finite differences is covered by the test suite."""
+    and split float32 paths.  The gradient of field 0 is scored against the
+    oracle's 2 S^T S (beta_5000 - beta_6000) on sampled orders (cpu leg)."""
     from paper_0910_5435_gb300 import autograd as ag
     l, nb = 512, 16
     P = sht.Plan(l, args.eps, leaf_cols=args.leaf_cols, page_bytes=args.page_bytes,
@@ -480,6 +515,7 @@ def autograd_leg(args, sht, inputs, torch, dev, stream):
         out[name] = {"ms_forward_backward": ms, "field_fwd_bwd_per_s": nb / (ms / 1e3)}
     out["rel_grad_split32_vs_fp64"] = float(torch.linalg.vector_norm(grads["split32"] - grads["fp64"])
                                             / torch.linalg.vector_norm(grads["fp64"]))
+    out["_samples"] = {f"ag_{name}_{l}_grad": gr[0].cpu().numpy() for name, gr in grads.items()}
     P.close()
     return out
 
@@ -601,14 +637,16 @@ def main():
     hbm = peaks.get("hbm_gbs") if peaks else None
     stream_gbs = st["stream_bytes_fp64"] / (0.5 * (ms_syn + ms_ana) / 1e3) / 1e9
     traffic = None
-    if (sweep_sources_sha() == SWEEP_SOURCES_SHA and l == SWEEP_TRAFFIC_BYTES["l"]
-            and args.leaf_cols == SWEEP_TRAFFIC_BYTES["leaf_cols"] and args.page_bytes == SWEEP_TRAFFIC_BYTES["page_bytes"]):
-        traffic = SWEEP_TRAFFIC_BYTES["bytes"]
+    cap = SWEEP_TRAFFIC_CAPTURE
+    if (cap["sources_sha"] is not None and sweep_sources_sha() == cap["sources_sha"]
+            and args.leaf_cols == cap["leaf_cols"] and args.page_bytes == cap["page_bytes"]):
+        traffic = 0.5 * (cap["dram_bytes_syn"] + cap["dram_bytes_ana"]) / cap["stream_bytes"] * st["stream_bytes_fp64"]
     # this device's float64 FMA loop (after the timed region): the reachable ceiling
     dfma_loop = sht.measure_fp64_fma()
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum at l=512, "
+                                "scaled by the float64 stream size)",
                 "algorithmic_bytes_per_launch": st["stream_bytes_fp64"] + nbytes + G.numel() * G.element_size(),
                 "kernel": "bfly_sweep_kernel<TF64>",
                 "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flops",
@@ -685,6 +723,9 @@ def main():
                 if k + "_G" in extras:
                     arrays[k + "_G"] = extras[k + "_G"]
                     arrays[k + "_beta"] = extras[k + "_beta"]
+            for leg in extras.values():
+                if isinstance(leg, dict):
+                    arrays.update(leg.get("_samples", {}))
             np.savez(op, **arrays)
             res = cpu_oracle_leg(l, args.cpu_stride, 3, op)
         cpu = {"value": 2.0 / res["t_full_est"], "unit": "transforms/s", "cores": 1, "kind": "oracle",
@@ -701,6 +742,17 @@ def main():
     for k in list(extras):
         if k.endswith("_G") or k.endswith("_beta"):
             extras.pop(k)
+    for leg in extras.values():
+        if isinstance(leg, dict):
+            leg.pop("_samples", None)
+    # each leg carries its own scores against the oracle
+    rel_main = {k: v for k, v in rel.items() if "batched_l" not in k and not k.startswith("rel_grad_")}
+    if "batched_split32" in extras and rel:
+        extras["batched_split32"]["rel_l2_vs_oracle_sampled"] = {
+            k: v for k, v in rel.items() if "batched_l" in k}
+    if "autograd_l512_b16" in extras and rel:
+        extras["autograd_l512_b16"]["rel_l2_vs_oracle_sampled"] = {
+            k: v for k, v in rel.items() if k.startswith("rel_grad_")}
 
     if rank == 0:
         line = {
@@ -710,7 +762,7 @@ def main():
             "dtype": "f64", "data": "synthetic",
             "config": workload_config(args, world),
             "ms_synthesis": ms_syn, "ms_analysis": ms_ana, "step_ms_percentiles": step_percentiles,
-            "eps_inv": eps_inv64, "rel_l2_vs_oracle_sampled": rel,
+            "eps_inv": eps_inv64, "rel_l2_vs_oracle_sampled": rel_main,
             "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
             "e2e": {"value": e2e_value, "unit": "transforms/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes},
