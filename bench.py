@@ -234,7 +234,7 @@ if path != "-":
     sel = np.concatenate([np.arange(off[m], off[m + 1]) for m in me])
     def score(tag, G, b, lf, bf):
         mf = list(range(0, 2 * lf, err_stride))
-        Gf = Ge if (lf, bf) == (l, "main") else oracle.legendre_synthesis(bf, lf, orders=mf)
+        Gf = Ge if bf is None else oracle.legendre_synthesis(bf, lf, orders=mf)
         of = oracle.triangle_offsets(lf)
         sf = np.concatenate([np.arange(of[m], of[m + 1]) for m in mf])
         out["rel_synth_" + tag] = float(np.linalg.norm(G[mf] - Gf[mf]) / np.linalg.norm(Gf[mf]))
@@ -258,7 +258,7 @@ if path != "-":
             ref = 2.0 * oracle.legendre_adjoint(oracle.legendre_synthesis(db, lf, orders=mf), lf, orders=mf)
             out["rel_grad_" + pname] = float(np.linalg.norm(gr[sf] - ref[sf]) / np.linalg.norm(ref[sf]))
         else:
-            score(name, d[name + "_G"], d[name + "_beta"], l, "main")
+            score(name, d[name + "_G"], d[name + "_beta"], l, None)
 print(json.dumps(out))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")

@@ -17,6 +17,10 @@ Everything is float64 numpy, written for readability:
   of eq. alternate_expansion at the Gauss-Legendre nodes (the Legendre
   stage), their transpose (analysis), and the sums over m at the equispaced
   phis of eq. phis as a naive DFT.
+* ``oracle.gauss_jacobi`` -- the paper's own per-order matrices of Section
+  4: the zeros of P-bar^m_{m+2n} (resp. P-bar^m_{m+2n+1}) found by sign
+  changes and bisection on the x recurrence, the weights of Lemma
+  quadratures, and the direct transforms of eqs. transform and transform2.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 identities and library routines that do not share its arithmetic.
@@ -35,3 +39,4 @@ from .sht import (  # noqa: F401
     phis,
     unit_matrix,
 )
+from .gauss_jacobi import gj_forward, gj_inverse, gj_matrix, gj_nodes_weights, gj_sigma_n  # noqa: F401

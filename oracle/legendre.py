@@ -79,26 +79,10 @@ def _legendre_p_pair(n, x):
     return p, p_prev
 
 
-def legendre_table(m, x, kmax):
-    """P-bar^m_k(x) for k = m..kmax, as an array of shape (kmax - m + 1, len(x)).
-
-    Section 2.3, eq. association.  Evaluation:
-
-    * diagonal: P-bar^0_0 = 1/sqrt(2) and
-      P-bar^j_j = sqrt((2j+1)/(2j)) sqrt(1-x^2) P-bar^{j-1}_{j-1};
-    * degree recurrence for fixed m:
-      P-bar^m_{k+1} = a_{k+1} x P-bar^m_k - (a_{k+1}/a_k) P-bar^m_{k-1},
-      a_k = sqrt((4k^2 - 1)/(k^2 - m^2)) (the second term is absent for k = m);
-    * every node carries (mantissa, binary exponent); the mantissas are
-      renormalized whenever they leave [2^-600, 2^600], and values are
-      converted with ldexp at the end (flushing to 0 below the float64 range),
-      as Section 4 prescribes for countering underflow.
-    """
-    m = int(m)
-    kmax = int(kmax)
-    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
-    if m < 0 or kmax < m:
-        return np.zeros((0, x.size))
+def _degree_walk(m, x, kmax):
+    """Yields (k, mantissa of P-bar^m_k, mantissa of P-bar^m_{k-1}, exponent)
+    for k = m..kmax: the values are ldexp(mantissa, exponent) with the one
+    exponent per node that the two live mantissas share (legendre_table)."""
     s = np.sqrt((1.0 - x) * (1.0 + x))
 
     # diagonal P-bar^m_m with its own exponent per node
@@ -108,10 +92,8 @@ def legendre_table(m, x, kmax):
         mant = mant * (np.sqrt((2.0 * j + 1.0) / (2.0 * j)) * s)
         mant, e = np.frexp(mant)
         expo += e
-
-    out = np.zeros((kmax - m + 1, x.size))
-    out[0] = np.ldexp(mant, expo)
     p_prev = np.zeros_like(mant)
+    yield m, mant, p_prev, expo
     p_cur = mant
     a_prev = None
     for k in range(m, kmax):
@@ -132,8 +114,46 @@ def legendre_table(m, x, kmax):
             p_prev = np.ldexp(p_prev, -sh)
             p_cur = np.ldexp(p_cur, -sh)
             expo = expo + sh
-        out[k + 1 - m] = np.ldexp(p_cur, expo)
+        yield k + 1, p_cur, p_prev, expo
+
+
+def legendre_table(m, x, kmax):
+    """P-bar^m_k(x) for k = m..kmax, as an array of shape (kmax - m + 1, len(x)).
+
+    Section 2.3, eq. association.  Evaluation:
+
+    * diagonal: P-bar^0_0 = 1/sqrt(2) and
+      P-bar^j_j = sqrt((2j+1)/(2j)) sqrt(1-x^2) P-bar^{j-1}_{j-1};
+    * degree recurrence for fixed m:
+      P-bar^m_{k+1} = a_{k+1} x P-bar^m_k - (a_{k+1}/a_k) P-bar^m_{k-1},
+      a_k = sqrt((4k^2 - 1)/(k^2 - m^2)) (the second term is absent for k = m);
+    * every node carries (mantissa, binary exponent); the mantissas are
+      renormalized whenever they leave [2^-600, 2^600], and values are
+      converted with ldexp at the end (flushing to 0 below the float64 range),
+      as Section 4 prescribes for countering underflow.
+    """
+    m = int(m)
+    kmax = int(kmax)
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    if m < 0 or kmax < m:
+        return np.zeros((0, x.size))
+    out = np.zeros((kmax - m + 1, x.size))
+    for k, mant, _, expo in _degree_walk(m, x, kmax):
+        out[k - m] = np.ldexp(mant, expo)
     return out
+
+
+def legendre_top_pair(m, N, x):
+    """P-bar^m_N(x) and P-bar^m_{N-1}(x) by the recurrence of legendre_table,
+    keeping only the last two degrees: (mantissa_N, mantissa_{N-1},
+    exponent), the values being ldexp(mantissa, exponent) (N >= m + 1)."""
+    m, N = int(m), int(N)
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    if N < m + 1:
+        raise ValueError("N must exceed m")
+    for _, cur, prev, expo in _degree_walk(m, x, N):
+        pass
+    return cur, prev, expo
 
 
 def legendre_value(m, k, x):

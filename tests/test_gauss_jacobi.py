@@ -71,6 +71,17 @@ def test_nodes_are_zeros_and_matrix_is_orthogonal(m, p, n):
     assert np.max(np.abs(A.T @ A - np.eye(n))) < 1e-12
 
 
+@pytest.mark.parametrize("m,p,n", [(0, 0, 40), (0, 1, 40), (7, 1, 64), (200, 0, 90), (300, 1, 300)])
+def test_nodes_and_weights_match_oracle(m, p, n):
+    """The product's nodes (eigenvalues of the x^2 Jacobi matrix, Newton on
+    the x^2 recurrence) and weights (1 / sum of squares) against the
+    oracle's (bisection on the x recurrence, eqs. weights1 / weights2)."""
+    x, rho = sht.gauss_jacobi_nodes(m, p, n)
+    xo, wo = oracle.gj_nodes_weights(m, p, n)
+    assert np.max(np.abs(x - xo)) < 2e-15
+    assert np.max(np.abs(rho - wo) / wo) < 1e-12
+
+
 def test_butterfly_errors_at_id_precision():
     for p in (0, 1):
         s = sht.unit_stats(300, 300, p, eps_id=1e-12, leaf_cols=32, gauss_jacobi=True)
