@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--consumer-warps", type=int, default=0)
     ap.add_argument("--eps", type=float, default=1e-12)
     ap.add_argument("--no-extras", action="store_true", help="skip every leg beside the float64 headline")
-    ap.add_argument("--paths", default="split32,split32acc64,fp32,direct,full,batched,autograd,device_build",
+    ap.add_argument("--paths", default="split32,split32acc64,fp32,direct,full,batched,autograd,device_build,"
+                                       "gauss_jacobi",
                     help="comma-separated legs to run beside the headline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--cpu-all-cores", type=int, default=1,
@@ -107,6 +108,50 @@ def device_build_leg(args, sht, torch, dev, stream, plan, st, beta):
            "rel_synthesis_vs_host_plan": float(torch.linalg.vector_norm(gd - gh) / torch.linalg.vector_norm(gh)),
            "device_status": int(sht.sht_last_device_status(pd))}
     pd.close()
+    return out
+
+
+def gauss_jacobi_leg(args, sht, torch, dev, stream):
+    """The paper's own matrices (Section 4, eq. transform; Tables evens_time /
+    evens_pre at m = n): one single-block plan per n (C = 60, IDs to 1e-15 as
+    the paper's "nearly machine precision"), the forward and inverse
+    transforms of two unit-norm U(-1, 1) vectors on the GPU (float64),
+    timed with CUDA events over 20 calls each, and eps_inv (forward then
+    inverse, largest entry error).  Parity against the oracle is in the
+    test suite."""
+    out = []
+    for n in (1250, 2500, 5000, 10000):
+        t0 = time.perf_counter()
+        P = sht.GJPlan(n, n, 0, eps_id=1e-15, leaf_cols=60)
+        t_plan = time.perf_counter() - t0
+        st = P.stats()
+        rng = np.random.default_rng(n)
+        v = rng.uniform(-1, 1, (n, 2))
+        v /= np.linalg.norm(v, axis=0)
+        x = torch.from_numpy(v[:, 0] + 1j * v[:, 1]).to(dev)
+        y = torch.empty_like(x)
+        z = torch.empty_like(x)
+
+        def timed(fn, reps=20):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        ms_f = timed(lambda: sht.sht_gj_forward(P, sht.SHT_FP64, x, y, stream))
+        ms_i = timed(lambda: sht.sht_gj_inverse(P, sht.SHT_FP64, y, z, stream))
+        torch.cuda.synchronize()
+        out.append({"n": n, "m": n, "parity": 0, "t_fwd_s": ms_f / 1e3, "t_inv_s": ms_i / 1e3,
+                    "launches": [P.launches(0, 0), P.launches(0, 1)], "t_quad_s": st["t_quad"],
+                    "t_comp_s": st["t_comp"], "t_plan_s": t_plan, "k_max": st["k_max"], "k_avg": st["k_avg"],
+                    "eps_inv": float((z - x).abs().max()), "device_status": sht.sht_last_device_status(P, stream)})
+        P.close()
     return out
 
 
@@ -709,6 +754,8 @@ def main():
         extras["batched_split32"] = batched_leg(args, sht, inputs, torch, dev, stream, plan, rank, world, dist)
     if rank == 0 and "autograd" in legs:
         extras["autograd_l512_b16"] = autograd_leg(args, sht, inputs, torch, dev, stream)
+    if rank == 0 and "gauss_jacobi" in legs:
+        extras["gauss_jacobi_m_eq_n"] = gauss_jacobi_leg(args, sht, torch, dev, stream)
     if rank == 0 and "device_build" in legs:
         extras["plan_device_build"] = device_build_leg(args, sht, torch, dev, stream, plan, st, beta)
 

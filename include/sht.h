@@ -437,6 +437,48 @@ sht_status sht_gauss_jacobi_nodes(int m, int parity, int n, double* x, double* r
 sht_status sht_unit_stats_gauss_jacobi(int n, int m, int parity, double eps_id, const sht_plan_opts* opts,
                                        unsigned long long seed, sht_unit_stats* out);
 
+/* ------------------------------------------- the paper's matrices on the GPU */
+
+/* Largest size of a single-block plan. */
+#define SHT_GJ_MAX_N 40000
+
+/* A plan for the paper's own n x n matrix of order m (Section 4):
+ *   parity 0, eq. transform:  A[i][j] = sqrt(rho_i)   P-bar^m_{m+2j}(x_i),
+ *   parity 1, eq. transform2: A[i][j] = sqrt(sigma_i) P-bar^m_{m+2j+1}(y_i),
+ * i, j < n, at the nodes and weights of sht_gauss_jacobi_nodes (Lemma zeros,
+ * Lemma quadratures).  The block is factored into the butterfly of Section
+ * 2.2 on the host (depth-first, Section 3; eps_id as for sht_plan_create_ex)
+ * and applied on the GPU level by level: each butterfly level is one launch
+ * of the sweep kernel whose work items (groups of that level's blocks) spread
+ * over the GPU, the vectors between levels in global memory owned by the
+ * plan.  Options as sht_plan_create_ex (opts may be NULL) except that
+ * device_build, plan_cache and debug_unmet_dependency must be 0 / NULL; 1 <=
+ * n <= SHT_GJ_MAX_N, 0 <= m <= SHT_GJ_MAX_N.  Destroy with sht_plan_destroy;
+ * sht_prepare, sht_plan_get_stats, sht_plan_stream, sht_trace_enable and
+ * sht_last_device_status apply.  The order-based entry points (Legendre
+ * stage, phi stage, direct baseline, batches, sht_plan_nodes, sht_plan_save)
+ * refuse such a plan with SHT_ERR_UNSUPPORTED.  Returns SHT_ERR_INVALID_ARG
+ * also when a butterfly level is wider than 65535 elements. */
+sht_status sht_gj_plan_create(int n, int m, int parity, double eps_id, const sht_plan_opts* opts, sht_plan_t* out);
+
+/* The forward transform alpha = A beta (eqs. transform / transform2) and the
+ * inverse transform beta = A^T alpha (A is orthogonal, Lemma quadratures).
+ * beta and alpha are DEVICE arrays of n complex numbers (complex128 for
+ * SHT_FP64, SHT_SPLIT32 and SHT_SPLIT32_ACC64, 16-byte aligned; complex64
+ * for SHT_FP32, 8-byte aligned): the real and imaginary parts are two real
+ * vectors transformed together (a real vector: imaginary parts 0).  The
+ * input and output may be the same array.  Asynchronous on `stream`, one
+ * launch per butterfly level (sht_gj_launches); a bounded wait that gives
+ * up is reported by sht_last_device_status.  Calls on one plan must not
+ * overlap on the GPU (they share the plan's vectors and work counters). */
+sht_status sht_gj_forward(sht_plan_t plan, sht_precision prec, const void* beta, void* alpha, sht_stream_t stream);
+sht_status sht_gj_inverse(sht_plan_t plan, sht_precision prec, const void* alpha, void* beta, sht_stream_t stream);
+
+/* Launches one call of sht_gj_forward (direction 0) or sht_gj_inverse
+ * (direction 1) makes in precision prec (building that precision's streams
+ * on the host if needed). */
+sht_status sht_gj_launches(sht_plan_t plan, sht_precision prec, int direction, int* launches);
+
 /* The interpolative decomposition every butterfly block is built from
  * (Section 2.1, eq. 2.1 and Remark QR_algorithm), on the host: column-pivoted
  * Householder QR of the h x w column-major matrix A (host, not modified) to

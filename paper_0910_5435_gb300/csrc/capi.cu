@@ -102,6 +102,10 @@ struct sht_plan_s {
   int* d_dense_rows = nullptr;
   int* d_dense_ncol = nullptr;
   size_t dense_bytes = 0;
+  // single-block (Gauss-Jacobi) plans: the vectors A and B of the
+  // level-by-level launches, in global memory
+  void* d_gvec = nullptr;
+  size_t gvec_bytes = 0;
   sht_plan_stats_t stats{};
   std::mutex mu;
 };
@@ -151,6 +155,9 @@ void free_dev(sht_plan_t P) {
   cudaFree(P->d_scratch);
   cudaFree(P->d_trace);
   P->d_trace = nullptr;
+  cudaFree(P->d_gvec);
+  P->d_gvec = nullptr;
+  P->gvec_bytes = 0;
   cudaFree(P->d_dense);
   cudaFree(P->d_dense_off);
   cudaFree(P->d_dense_rows);
@@ -168,7 +175,7 @@ void fill_stats(sht_plan_t P) {
   s.l = H.l;
   s.eps_id = H.eps_id;
   s.leaf_cols = H.leaf_cols;
-  s.n_units = 2 * H.l;
+  s.n_units = H.gj ? 1 : 2 * H.l;
   long long nb = 0, sumk = 0, dense = 0, fv = 0, ib = 0, rows = 0, kept = 0, peak = 0;
   double sumk2 = 0, maxT = 0;
   int kmax = 0, lev = 0, ndir = 0;
@@ -238,7 +245,9 @@ sht_status build_host(sht_plan_t P, int q) {
     const double t0 = now_s();
     const bool fp32 = (q == sht::PREC_FP32);
     if ((fp32 ? H.fact32 : H.fact64).empty()) {
-      if (P->opts.device_build)
+      if (H.gj)
+        sht::build_gj_factorization(H, fp32);
+      else if (P->opts.device_build)
         sht::build_factorizations_device(H, fp32, P->device);
       else
         sht::build_factorizations(H, fp32);
@@ -290,8 +299,21 @@ sht_status upload_streams(sht_plan_t P, int q) {
   if (q == sht::PREC_SPLIT32) CK(sht::sweep_configure(sht::PREC_SPLIT32_ACC64, (size_t)optin));
   sht::SweepConfig cfg;
   const int slot_bytes = P->H.slot_values_for(q) * (q == sht::PREC_FP32 ? 4 : 8);
-  if (!sht::sweep_choose(q, P->H.page_bytes, buf_ab, nvecs, P->consumer_warps[q], slot_bytes, 1, (size_t)optin,
-                         &cfg)) {
+  if (P->H.gj) {
+    // single-block plans keep their vectors in global memory: one pair for
+    // the plan, sized for its widest precision
+    const size_t need = (size_t)nvecs * buf_ab * (q == sht::PREC_FP32 ? 8 : 16);
+    if (need > P->gvec_bytes) {
+      CK(cudaDeviceSynchronize());  // launches of another precision may still use the old pair
+      cudaFree(P->d_gvec);
+      P->d_gvec = nullptr;
+      P->gvec_bytes = 0;
+      CK(cudaMalloc(&P->d_gvec, need));
+      P->gvec_bytes = need;
+    }
+  }
+  if (!sht::sweep_choose(q, P->H.page_bytes, P->H.gj ? 0 : buf_ab, nvecs, P->consumer_warps[q], slot_bytes, 1,
+                         (size_t)optin, &cfg)) {
     set_detail("upload", "the sweep's shared memory (vectors, record chunks, staging slots) exceeds the device limit");
     return SHT_ERR_UNSUPPORTED;
   }
@@ -339,9 +361,17 @@ sht_status ensure_prec(sht_plan_t P, int q) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// The order-based entry points refuse a single-block (Gauss-Jacobi) plan.
+bool refuse_gj(sht_plan_t P, const char* where) {
+  if (!P->H.gj) return false;
+  set_detail(where, "a single-block (Gauss-Jacobi) plan: use sht_gj_forward / sht_gj_inverse");
+  return true;
+}
+
 sht_status launch_sweep(sht_plan_t P, sht_precision prec, int dir, int kind, const void* in, void* out,
                         const double* prescale, sht_stream_t stream, const double2* twiddle = nullptr) {
   if (!P || !in || !out) return SHT_ERR_INVALID_ARG;
+  if (refuse_gj(P, "Legendre stage")) return SHT_ERR_UNSUPPORTED;
   const int q = prec_index(prec);
   if (q < 0) return SHT_ERR_INVALID_ARG;
   if (P->host_only) return SHT_ERR_UNSUPPORTED;
@@ -386,7 +416,7 @@ sht_status sht::prepared_sweep(sht_plan_t P, sht_precision prec, int dir, const 
   if (!P || !in || !out || !L || (dir != 0 && dir != 1)) return SHT_ERR_INVALID_ARG;
   const int q = prec_index(prec);
   if (q < 0) return SHT_ERR_INVALID_ARG;
-  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  if (P->host_only || refuse_gj(P, "prepared_sweep")) return SHT_ERR_UNSUPPORTED;
   const size_t al = (q == sht::PREC_FP32) ? 8 : 16;
   if (!aligned(in, al) || !aligned(out, al)) return SHT_ERR_INVALID_ARG;
   if (!P->ready[q].load(std::memory_order_acquire)) {
@@ -426,7 +456,7 @@ sht_status sht::stream_view(sht_plan_t P, sht_precision prec, int dir, StreamVie
   if (!P || !v || (dir != 0 && dir != 1)) return SHT_ERR_INVALID_ARG;
   const int q = prec_index(prec);
   if (q < 0) return SHT_ERR_INVALID_ARG;
-  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  if (P->host_only || refuse_gj(P, "batch")) return SHT_ERR_UNSUPPORTED;
   sht_status s = ensure_prec(P, q);
   if (s != SHT_OK) return s;
   const DevStream& D = P->dev[q][dir];
@@ -549,6 +579,7 @@ sht_status sht_plan_load(const char* path, const sht_plan_opts* opts, sht_plan_t
 
 sht_status sht_plan_save(sht_plan_t P, const char* path) {
   if (!P || !path) return SHT_ERR_INVALID_ARG;
+  if (refuse_gj(P, "sht_plan_save")) return SHT_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> g(P->mu);
   try {
     sht::save_factorizations(P->H, path);
@@ -753,6 +784,7 @@ sht_status sht_prepare(sht_plan_t P, sht_precision prec) {
 
 sht_status sht_plan_nodes(sht_plan_t P, double* x, double* w) {
   if (!P || !x || !w) return SHT_ERR_INVALID_ARG;
+  if (refuse_gj(P, "sht_plan_nodes")) return SHT_ERR_UNSUPPORTED;
   std::memcpy(x, P->H.x.data(), sizeof(double) * P->H.x.size());
   std::memcpy(w, P->H.w.data(), sizeof(double) * P->H.w.size());
   return SHT_OK;
@@ -869,7 +901,7 @@ static sht_status phi_args_ok(sht_plan_t P, sht_precision prec, const void* a, c
   if (!P || !a || !b) return SHT_ERR_INVALID_ARG;
   q = prec_index(prec);
   if (q < 0) return SHT_ERR_INVALID_ARG;
-  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  if (P->host_only || refuse_gj(P, "phi stage")) return SHT_ERR_UNSUPPORTED;
   const size_t al = (q == sht::PREC_FP32) ? 8 : 16;
   if (!aligned(a, al) || !aligned(b, al)) return SHT_ERR_INVALID_ARG;
   if (cudaSetDevice(P->device) != cudaSuccess) return SHT_ERR_CUDA;
@@ -958,6 +990,7 @@ sht_status sht_trace_read(sht_plan_t P, unsigned long long* out, int reset) {
 sht_status sht_direct_prepare(sht_plan_t P) {
   if (!P) return SHT_ERR_INVALID_ARG;
   if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  if (refuse_gj(P, "sht_direct_prepare")) return SHT_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> g(P->mu);
   if (P->d_dense) return SHT_OK;
   const PlanHost& H = P->H;
@@ -1045,6 +1078,188 @@ sht_status sht_direct_analyze(sht_plan_t P, const void* G, void* beta, sht_strea
   CK(cudaSetDevice(P->device));
   (void)cudaGetLastError();
   CK(sht::direct_analysis_launch(direct_args(P, G, beta), reinterpret_cast<cudaStream_t>(stream)));
+  return SHT_OK;
+}
+
+// ------------------------------------------------ single blocks (Section 4)
+
+namespace {
+
+sht_status create_gj_plan(int n, int m, int parity, double eps_id, const sht_plan_opts* opts, sht_plan_t* out) {
+  if (!out) return SHT_ERR_INVALID_ARG;
+  *out = nullptr;
+  sht_plan_opts o;
+  if (opts) {
+    o = *opts;
+  } else {
+    sht_plan_opts_default(&o);
+  }
+  if (o.page_bytes == 0) o.page_bytes = sht::kDefaultChunkBytes;
+  if (o.min_band_rows <= 0) o.min_band_rows = std::max(1, o.leaf_cols / 2);
+  if (n < 1 || n > SHT_GJ_MAX_N || m < 0 || m > SHT_GJ_MAX_N || (parity != 0 && parity != 1) || !(eps_id > 0.0) ||
+      !(eps_id < 1.0))
+    return SHT_ERR_INVALID_ARG;
+  if (o.leaf_cols < 2 || o.leaf_cols > 1024) return SHT_ERR_INVALID_ARG;
+  if (o.page_bytes < sht::kMinChunkBytes || o.page_bytes > sht::kMaxChunkBytes || (o.page_bytes & (o.page_bytes - 1)))
+    return SHT_ERR_INVALID_ARG;
+  if (o.values_inline != 0 || o.num_threads < 0 || o.device_build != 0 || o.plan_cache != nullptr ||
+      o.debug_unmet_dependency != 0 || o.staging_slots < 0 || o.staging_slots > 1)
+    return SHT_ERR_INVALID_ARG;
+  if (o.consumer_warps != 0 && o.consumer_warps != 8 && o.consumer_warps != 12 && o.consumer_warps != 16)
+    return SHT_ERR_INVALID_ARG;
+  if (o.slot_values != 0 && (o.slot_values < sht::kMinSlotValues || o.slot_values > sht::kMaxSlotValues ||
+                             o.slot_values % 32 != 0))
+    return SHT_ERR_INVALID_ARG;
+  sht_plan_t P = new (std::nothrow) sht_plan_s();
+  if (!P) return SHT_ERR_OOM;
+  P->opts = o;
+  P->host_only = o.host_only != 0;
+  for (int q = 0; q < kNumPrec; ++q) {
+    P->warp_slots[q] = 1;
+    P->consumer_warps[q] = o.consumer_warps ? o.consumer_warps : 16;
+  }
+  PlanHost& H = P->H;
+  H.gj = true;
+  H.gj_m = m;
+  H.gj_p = parity;
+  H.l = n;
+  H.unit_cols = n;
+  H.eps_id = eps_id;
+  H.eps_fp32 = o.eps_fp32 > 0.0 ? o.eps_fp32 : std::max(eps_id, 1e-7);
+  H.trim_eps = 0.0;  // every node of the block is kept
+  H.leaf_cols = o.leaf_cols;
+  H.min_band_rows = o.min_band_rows;
+  H.num_threads = o.num_threads;
+  H.page_bytes = o.page_bytes;
+  H.sched_warps = o.consumer_warps ? o.consumer_warps : 16;
+  H.slot_values = o.slot_values;
+  if (!P->host_only) {
+    int dev = 0, count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+      delete P;
+      return SHT_ERR_NO_DEVICE;
+    }
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      delete P;
+      return SHT_ERR_CUDA;
+    }
+    P->device = dev;
+    cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  try {
+    const double t0 = now_s();
+    std::vector<double> rho;
+    sht::gauss_jacobi_nodes(m, parity, n, H.row_x, H.row_sin, rho);
+    H.row_sqw.resize(n);
+    for (int i = 0; i < n; ++i) H.row_sqw[i] = std::sqrt(rho[i]);
+    H.t_quad = now_s() - t0;
+  } catch (const std::bad_alloc&) {
+    delete P;
+    return SHT_ERR_OOM;
+  } catch (...) {
+    delete P;
+    return SHT_ERR_INVALID_ARG;
+  }
+  sht_status s = build_host(P, sht::PREC_FP64);
+  if (s != SHT_OK) {
+    delete P;
+    return s;
+  }
+  if (!P->host_only) {
+    cudaError_t e = cudaMalloc(&P->d_scratch, kScratchBytes);
+    if (e == cudaSuccess) e = cudaMemset(P->d_scratch, 0, kScratchBytes);
+    if (e != cudaSuccess) {
+      free_dev(P);
+      delete P;
+      return cuda_status(e);
+    }
+    s = upload(P, sht::PREC_FP64);
+    if (s != SHT_OK) {
+      free_dev(P);
+      delete P;
+      return s;
+    }
+  }
+  fill_stats(P);
+  P->ready[sht::PREC_FP64].store(true, std::memory_order_release);
+  *out = P;
+  return SHT_OK;
+}
+
+// One direction of a single block: one launch per stage of the
+// level-by-level stream, in order on the caller's stream.
+sht_status launch_gj(sht_plan_t P, sht_precision prec, int dir, const void* in, void* out, sht_stream_t stream) {
+  if (!P || !in || !out) return SHT_ERR_INVALID_ARG;
+  if (!P->H.gj) {
+    set_detail("sht_gj_forward / sht_gj_inverse", "not a single-block plan (sht_gj_plan_create)");
+    return SHT_ERR_UNSUPPORTED;
+  }
+  const int q = prec_index(prec);
+  if (q < 0) return SHT_ERR_INVALID_ARG;
+  if (P->host_only) return SHT_ERR_UNSUPPORTED;
+  const size_t al = (q == sht::PREC_FP32) ? 8 : 16;
+  if (!aligned(in, al) || !aligned(out, al)) return SHT_ERR_INVALID_ARG;
+  sht_status s = ensure_prec(P, q);
+  if (s != SHT_OK) return s;
+  CK(cudaSetDevice(P->device));
+  const DevStream& D = P->dev[q][dir];
+  const std::vector<uint32_t>& stages = P->H.streams[q][dir].stage_begin;
+  (void)cudaGetLastError();  // do not report a stale error left by an earlier call
+  for (size_t st = 0; st + 1 < stages.size(); ++st) {
+    const int n_units = (int)(stages[st + 1] - stages[st]);
+    if (n_units == 0) continue;
+    sht::SweepArgs a{};
+    a.pages = D.pages;
+    a.values = D.values;
+    a.units = D.units + stages[st];
+    a.n_units = n_units;
+    a.chunk_bytes = P->H.page_bytes;
+    a.l = P->H.l;
+    a.buf_ab = D.buf_ab;
+    a.in = in;
+    a.out = out;
+    a.trace = P->d_trace;
+    a.num_vecs = P->num_vecs[q];
+    a.slot_bytes = P->slot_bytes[q];
+    a.warp_slots = 1;
+    a.fg = 1;
+    a.plain = 1;
+    a.gvec = P->d_gvec;
+    a.counter = P->d_scratch + (kernel_prec(prec) * KIND_COUNT + (dir ? KIND_ANA : KIND_SYN));
+    a.status = P->d_scratch + kStatusWord;
+    const int grid = std::max(1, std::min(P->num_sms * P->ctas_per_sm[q], n_units));
+    CK(sht::sweep_launch(kernel_prec(prec), P->consumer_warps[q], a, grid, P->smem[q],
+                         reinterpret_cast<cudaStream_t>(stream)));
+  }
+  return SHT_OK;
+}
+
+}  // namespace
+
+sht_status sht_gj_plan_create(int n, int m, int parity, double eps_id, const sht_plan_opts* opts, sht_plan_t* out) {
+  return create_gj_plan(n, m, parity, eps_id, opts, out);
+}
+
+sht_status sht_gj_forward(sht_plan_t P, sht_precision prec, const void* beta, void* alpha, sht_stream_t stream) {
+  return launch_gj(P, prec, 0, beta, alpha, stream);
+}
+
+sht_status sht_gj_inverse(sht_plan_t P, sht_precision prec, const void* alpha, void* beta, sht_stream_t stream) {
+  return launch_gj(P, prec, 1, alpha, beta, stream);
+}
+
+sht_status sht_gj_launches(sht_plan_t P, sht_precision prec, int direction, int* launches) {
+  if (!P || !launches || direction < 0 || direction > 1) return SHT_ERR_INVALID_ARG;
+  if (!P->H.gj) return SHT_ERR_UNSUPPORTED;
+  const int q = prec_index(prec);
+  if (q < 0) return SHT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> g(P->mu);
+  sht_status s = build_host(P, q);
+  if (s != SHT_OK) return s;
+  const std::vector<uint32_t>& st = P->H.streams[q][direction].stage_begin;
+  int c = 0;
+  for (size_t i = 0; i + 1 < st.size(); ++i) c += st[i + 1] > st[i];
+  *launches = c;
   return SHT_OK;
 }
 

@@ -55,6 +55,16 @@ struct SweepArgs {
   void* const* field_out;
   int io_align;                // required alignment (bytes) of field_in / field_out entries
   int fg;                      // fields per group the kernel handles (1; batched launches 1, 2 or 4)
+  // Single-block transforms (the Gauss-Jacobi form, eqs. transform and
+  // transform2): plain != 0 makes GATHER / SCATTER read and write element j
+  // of a plain vector (no coefficient triangle, no parity interleave), FOLD
+  // read node value r as is, and DENSE_G / GZERO write node value i (no
+  // parity unfold, no order row).  gvec != nullptr holds the vectors A and B
+  // (num_vecs * buf_ab elements) in global memory, shared by all CTAs of the
+  // launch, instead of in shared memory; the launch is then one stage of a
+  // level-by-level schedule (no two ops of a launch touch the same element).
+  int plain;
+  void* gvec;
 };
 
 // Launch shape of a sweep: consumer warps (the warps the streams were

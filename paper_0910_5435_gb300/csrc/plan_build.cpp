@@ -701,6 +701,7 @@ struct OpRec {
   std::vector<int> preds;
   bool planted = false;  // waits for itself (failure-detection tests)
   double cost = 0;       // scheduling estimate
+  int stage = 0;         // emission stage (a butterfly level, a gather, ...)
 };
 
 // value encodings per precision: 0 = FP64 (double), 1 = FP32 (float), 2 = SPLIT32 (float hi, float lo)
@@ -763,6 +764,10 @@ struct Emitter {
   int base = 0;
   int cursor = 0;
   int pool = 0;
+  // Stage counter: emit_unit starts a new stage before each set of mutually
+  // independent ops (a gather, one butterfly level, the final blocks, ...);
+  // level-by-level schedules launch each stage on its own.
+  int stage = 0;
   explicit Emitter(int p) : prec(p), vs(value_size(p)) {}
 
   // Chooses the base of a block using `width` positions of each vector.
@@ -904,6 +909,7 @@ struct Emitter {
     const double per_value = prec == 0 ? 13.5 : prec == 2 ? 5.5 : 2.8;
     r.cost = (h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) ? 2400.0 + per_value * M * K
                                                                    : 1500.0 + 2.0 * M;
+    r.stage = stage;
     ops.push_back(std::move(r));
   }
 
@@ -1087,14 +1093,24 @@ int unit_width(const UnitFact& U) {
 }
 
 // Appends the ops of order m to the emitter's current work item.
+//
+// The blocks factor A_ij = sqrt(2 w_i) P-bar(x_i) over the positive nodes:
+// the synthesis divides the rows by sqrt(2 w_i) (E_i and O_i at x_i), the
+// analysis multiplies them by sqrt(w_i / 2) (the weighted, folded sums).  A
+// single-block (gj) plan applies its block A = diag(sqrt(rho)) P-bar as it
+// is (eqs. transform and transform2: forward A, inverse A^T), so both
+// scales are 1; its one parity neither accumulates nor unfolds.
 void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
   const int l = P.l;
   const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
-  std::vector<double> inv_sq2w(l), sqw2(l);
-  for (int i = 0; i < l; ++i) {
-    inv_sq2w[i] = 1.0 / std::sqrt(2.0 * P.w[l + i]);
-    sqw2[i] = std::sqrt(0.5 * P.w[l + i]);
-  }
+  std::vector<double> inv_sq2w(l, 1.0), sqw2(l, 1.0);
+  if (!P.gj)
+    for (int i = 0; i < l; ++i) {
+      inv_sq2w[i] = 1.0 / std::sqrt(2.0 * P.w[l + i]);
+      sqw2[i] = std::sqrt(0.5 * P.w[l + i]);
+    }
+  // the first parity with columns writes the node rows, the other adds
+  const int first_p = F[(size_t)m * 2].n > 0 ? 0 : 1;
   std::vector<Stage> st[2];
   if (dir == 0) {
     // synthesis: gather, butterfly levels, then the final blocks write node
@@ -1104,7 +1120,7 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
       const UnitFact& U = F[(size_t)m * 2 + p];
       if (U.n == 0) continue;
       const uint8_t A = kBufA;
-      const uint8_t gflags = p ? F_ACCUM : 0;
+      const uint8_t gflags = p != first_p ? F_ACCUM : 0;
       st[p].push_back([&U, A, p, m](Emitter& E) {
         OpHdr g = E.hdr(OP_GATHER);
         g.a0 = (uint16_t)p;
@@ -1119,7 +1135,7 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
               if (b->k > 0) E.syn_interp(*b, j == 1 ? kBufA : level_buf(j - 1), level_buf(j));
           });
       }
-      fin[p] = [&U, A, p, m, l, gflags, &inv_sq2w](Emitter& E) {
+      fin[p] = [&U, A, p, m, l, gflags, first_p, &inv_sq2w](Emitter& E) {
         if (U.rows > 0 && U.direct) {
           // E_i = sum_j P-bar(x_i) x_j: weighted values divided by sqrt(2 w_i)
           E.dense(OP_DENSE_G, gflags, U.rows, U.n,
@@ -1139,7 +1155,7 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
                     A, f->r0, m);
           }
         }
-        if (p == 0 && U.rows < l) {
+        if (p == first_p && U.rows < l) {
           // node rows past the kept ones hold no even part
           OpHdr z = E.hdr(OP_GZERO);
           z.a1 = (uint32_t)m;
@@ -1152,8 +1168,14 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
     // next block's writes after this one's final reads
     for (int p = 0; p < 2; ++p) {
       E.place(unit_width(F[(size_t)m * 2 + p]));
-      for (const Stage& sg : st[p]) sg(E);
-      if (fin[p]) fin[p](E);
+      for (const Stage& sg : st[p]) {
+        ++E.stage;
+        sg(E);
+      }
+      if (fin[p]) {
+        ++E.stage;
+        fin[p](E);
+      }
     }
   } else {
     for (int p = 0; p < 2; ++p) {
@@ -1252,7 +1274,10 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
     }
     for (int p = 0; p < 2; ++p) {
       E.place(unit_width(F[(size_t)m * 2 + p]));
-      for (const Stage& sg : st[p]) sg(E);
+      for (const Stage& sg : st[p]) {
+        ++E.stage;
+        sg(E);
+      }
     }
   }
 }
@@ -1367,7 +1392,102 @@ void for_each_record(uint8_t* item, size_t chunk, Fn fn) {
 
 }  // namespace
 
+namespace {
+
+// Level-by-level streams of a single-block (gj) plan.  The block is emitted
+// as one order (emit_unit), then its ops are cut at the stage boundaries:
+// the ops of one stage (the gather, one butterfly level, the final blocks,
+// ...) touch disjoint vector elements, so every stage becomes one launch of
+// independent work items, its vectors in global memory and its items spread
+// over the GPU; the launches run in stage order.  An op whose predecessor
+// lies in its own stage would break that, and is refused.
+void emit_gj_streams(PlanHost& P, int prec) {
+  const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
+  if (F.size() != 2) throw std::logic_error("single-block plan without its factorization");
+  const size_t CH = (size_t)P.page_bytes;
+  const int NW = P.sched_warps;
+  const UnitFact& U = F[(size_t)P.gj_p];
+  const int positions = unit_width(U) + 1;
+  if (positions > 65535) throw std::runtime_error("block too wide: vector positions exceed 16 bits");
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<uint8_t> vals;
+    Emitter E(prec);
+    Tracker T;
+    E.T = &T;
+    E.l = P.l;
+    E.values = &vals;
+    E.slot_values = P.slot_values_for(prec);
+    E.chunk = CH;
+    E.pool = positions - 1;
+    E.open_item(positions);
+    emit_unit(P, prec, dir, 0, E);
+    const std::vector<OpRec>& ops = E.ops;
+    for (const OpRec& r : ops)
+      for (int u : r.preds)
+        if (ops[(size_t)u].stage >= r.stage) throw std::logic_error("dependency inside a stage");
+    Stream& S = P.streams[prec][dir];
+    S.units.clear();
+    S.stage_begin.clear();
+    std::vector<uint8_t> bytes, item;
+    constexpr double kGuideCtas = 2 * 152;  // items per stage to aim for (two per SM of a GB300)
+    constexpr double kMinItemCost = 40000;  // estimated warp cycles below which an item is not split
+    const size_t max_ops = (size_t)NW * 256;
+    size_t t = 0;
+    while (t < ops.size()) {
+      size_t t1 = t;
+      double cost = 0;
+      while (t1 < ops.size() && ops[t1].stage == ops[t].stage) cost += ops[t1++].cost;
+      const double target = std::max(cost / kGuideCtas, kMinItemCost);
+      S.stage_begin.push_back((uint32_t)S.units.size());
+      std::vector<OpRec> cur;
+      double cc = 0;
+      auto flush = [&]() {
+        encode_item(cur, NW, CH, item);
+        UnitEntry e;
+        e.off16 = bytes.size() / 16;
+        e.len16 = (uint32_t)(item.size() / 16);
+        e.m = (uint32_t)P.gj_m;
+        S.units.push_back(e);
+        bytes.insert(bytes.end(), item.begin(), item.end());
+        cur.clear();
+        cc = 0;
+      };
+      for (size_t u = t; u < t1; ++u) {
+        if (!cur.empty() && (cc + ops[u].cost > target || cur.size() >= max_ops)) flush();
+        cur.push_back(ops[u]);
+        cur.back().preds.clear();  // earlier stages: ordered by the launches
+        cc += ops[u].cost;
+      }
+      if (!cur.empty()) flush();
+      t = t1;
+    }
+    S.stage_begin.push_back((uint32_t)S.units.size());
+    if (vals.size() / 16 > 0xFFFFFFFFull) throw std::runtime_error("value region exceeds 64 GB");
+    ByteBuf().swap(S.bytes);
+    ByteBuf().swap(S.values);
+    S.bytes.resize(std::max<size_t>(bytes.size(), 16), 0);
+    if (!bytes.empty()) std::memcpy(S.bytes.data(), bytes.data(), bytes.size());
+    S.values.resize(vals.size());
+    if (!vals.empty()) std::memcpy(S.values.data(), vals.data(), vals.size());
+    S.max_buf_ab = positions - 1;
+    S.num_vecs = 2;
+  }
+  P.built[prec] = true;
+}
+
+}  // namespace
+
+void build_gj_factorization(PlanHost& P, bool fp32) {
+  std::vector<UnitFact>& out = fp32 ? P.fact32 : P.fact64;
+  out.assign(2, UnitFact());
+  out[(size_t)P.gj_p] = factor_single_unit(P, P.gj_m, P.gj_p, fp32 ? P.eps_fp32 : P.eps_id);
+}
+
 void emit_streams(PlanHost& P, int prec) {
+  if (P.gj) {
+    emit_gj_streams(P, prec);
+    return;
+  }
   const int L = 2 * P.l;
   const std::vector<UnitFact>& F = (prec == 1) ? P.fact32 : P.fact64;
   const size_t CH = (size_t)P.page_bytes;

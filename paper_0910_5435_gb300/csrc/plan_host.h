@@ -95,6 +95,10 @@ struct Stream {
   std::vector<UnitEntry> units;      // item table, LPT order
   int max_buf_ab = 0;                // elements needed in each shared vector
   int num_vecs = 2;                  // shared vectors used
+  // Single-block (Gauss-Jacobi) streams only: the items of stage s are
+  // units[stage_begin[s] .. stage_begin[s + 1]); each stage is one launch
+  // with the vectors in global memory.  Empty for the orders of an SHT plan.
+  std::vector<uint32_t> stage_begin;
 };
 
 struct PlanHost {
@@ -119,6 +123,13 @@ struct PlanHost {
   // sqrt(rho_i) for i < l; unit_cols > 0 sets the column count.
   std::vector<double> row_x, row_sin, row_sqw;
   int unit_cols = 0;
+  // A single-block plan of the Gauss-Jacobi form (eq. transform for parity
+  // 0, eq. transform2 for parity 1): l = n nodes and columns, the rows above
+  // (row_sqw = sqrt(rho_i)), order gj_m; its factorization is unit gj_p of
+  // fact64 / fact32 (the other parity empty) and its streams are staged
+  // level by level (Stream::stage_begin).
+  bool gj = false;
+  int gj_m = 0, gj_p = 0;
   // factorizations: [m * 2 + p]; fp64 uses eps_id, fp32 uses eps_fp32
   std::vector<UnitFact> fact64, fact32;
   // streams: [prec][direction]; prec 0 = FP64, 1 = FP32, 2 = SPLIT32
@@ -227,6 +238,11 @@ bool read_plan_file_header(const std::string& path, PlanFileInfo* info);
 void load_factorizations(PlanHost& P, const std::string& path);
 
 // Encodes one precision's factor streams (both directions) into pages.
+// A single-block (gj) plan gets its level-by-level streams.
 void emit_streams(PlanHost& P, int prec);
+
+// Factorization of a single-block (gj) plan's block with eps_id (fp32:
+// eps_fp32), into fact64 / fact32.
+void build_gj_factorization(PlanHost& P, bool fp32);
 
 }  // namespace sht

@@ -428,10 +428,12 @@ struct FieldCtx {
   int l;
   int nf;
   int buf_ab;
+  int plain;  // single-block I/O (SweepArgs::plain)
 };
 template <int FG>
 __device__ __forceinline__ FieldCtx<FG> field_ctx(const SweepArgs& A, int g) {
   FieldCtx<FG> c;
+  c.plain = A.plain;
   if (!A.fields) {
     c.values = A.values;
     c.prescale = A.prescale;
@@ -532,6 +534,11 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
             const int l = A.l;
             const int i = h.oo + o;
             IO v = TR::to_io(TR::to_c(a0));
+            if (A.plain) {  // node value i of a single block
+              IO* y = reinterpret_cast<IO*>(A.out[f]);
+              y[i] = accum ? TR::io_add(y[i], v) : v;
+              break;
+            }
             if (A.twiddle) v = TR::io_cmul(v, A.twiddle[h.a1]);
             IO* G = reinterpret_cast<IO*>(A.out[f]) + (size_t)h.a1 * (2 * l);
             if (accum) {
@@ -578,30 +585,39 @@ __device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, c
   const int m = (int)h.a1;
   const int n = h.M;
   const int parity = h.a0 & 1, base = h.a0 >> 1;  // GATHER / SCATTER / FOLD
+  // coefficient j of this parity: element 2j of order m's triangle row, or
+  // element j of a plain vector (single blocks)
+  const size_t c0 = A.plain ? 0 : tri_off(m, L) + parity;
+  const int cs = A.plain ? 1 : 2;
   for (int f = 0; f < A.nf; ++f) {
     switch (h.kind) {
       case OP_GATHER: {
-        const IO* beta = reinterpret_cast<const IO*>(A.in[f]) + tri_off(m, L) + parity;
+        const IO* beta = reinterpret_cast<const IO*>(A.in[f]) + c0;
         C* dst = S.buf(h.out_buf, f) + base;
-        for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::from_io(beta[2 * (size_t)j]);
+        for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::from_io(beta[cs * (size_t)j]);
         break;
       }
       case OP_SCATTER: {
-        IO* beta = reinterpret_cast<IO*>(A.out[f]) + tri_off(m, L) + parity;
+        IO* beta = reinterpret_cast<IO*>(A.out[f]) + c0;
         const C* src = S.buf(h.in_buf, f) + base;
-        for (int j = h.io + lane; j < h.io + n; j += 32) beta[2 * (size_t)j] = TR::to_io(src[j]);
+        for (int j = h.io + lane; j < h.io + n; j += 32) beta[cs * (size_t)j] = TR::to_io(src[j]);
         break;
       }
       case OP_FOLD: {
-        const IO* G = reinterpret_cast<const IO*>(A.in[f]) + (size_t)m * L;
+        const IO* G = reinterpret_cast<const IO*>(A.in[f]) + (A.plain ? 0 : (size_t)m * L);
         C* dst = S.buf(h.out_buf, f) + base;
         for (int r = h.oo + lane; r < h.oo + n; r += 32) {
-          IO gp = G[l + r], gm = G[l - 1 - r];
-          if (A.twiddle) {
-            gp = TR::io_cmul(gp, A.twiddle[m]);
-            gm = TR::io_cmul(gm, A.twiddle[m]);
+          IO e;
+          if (A.plain) {
+            e = G[r];  // node value r of a single block: nothing to fold
+          } else {
+            IO gp = G[l + r], gm = G[l - 1 - r];
+            if (A.twiddle) {
+              gp = TR::io_cmul(gp, A.twiddle[m]);
+              gm = TR::io_cmul(gm, A.twiddle[m]);
+            }
+            e = parity ? TR::io_sub(gp, gm) : TR::io_add(gp, gm);
           }
-          IO e = parity ? TR::io_sub(gp, gm) : TR::io_add(gp, gm);
           if (A.prescale) e = TR::io_scale(e, A.prescale[r]);
           dst[r] = TR::from_io(e);
         }
@@ -613,6 +629,11 @@ __device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, c
         break;
       }
       case OP_GZERO: {
+        if (A.plain) {
+          IO* y = reinterpret_cast<IO*>(A.out[f]);
+          for (int r = h.oo + lane; r < h.oo + n; r += 32) y[r] = TR::io_zero();
+          break;
+        }
         IO* G = reinterpret_cast<IO*>(A.out[f]) + (size_t)m * L;
         for (int r = h.oo + lane; r < h.oo + n; r += 32) {
           G[l + r] = TR::io_zero();
@@ -946,8 +967,9 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, typename TR::C* vec_base, 
 }
 
 // Shared-memory layout of a sweep CTA, used by the kernel and by the host
-// sizing alike: | vectors (128-aligned) | per warp: two record chunks, the
-// staging slot | mbarriers: per warp two ring + one slot (+1 spare) | Ctl |.
+// sizing alike: | vectors (128-aligned; none when they are in global memory)
+// | per warp: two record chunks, the staging slot | mbarriers: per warp two
+// ring + one slot (+1 spare) | Ctl |.
 __host__ __device__ inline size_t sweep_vec_bytes(size_t c_size, int num_vecs, int buf_ab) {
   return (c_size * (size_t)num_vecs * (size_t)buf_ab + 127) & ~size_t(127);
 }
@@ -959,7 +981,8 @@ template <class TR, int NW, int FG>
 __global__ void __launch_bounds__(NW * 32, 1) bfly_sweep_kernel(const SweepArgs A) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const size_t vec_bytes = sweep_vec_bytes(sizeof(typename TR::C), A.num_vecs, A.buf_ab);
+  // vectors in shared memory, or in global memory for the whole launch
+  const size_t vec_bytes = A.gvec ? 0 : sweep_vec_bytes(sizeof(typename TR::C), A.num_vecs, A.buf_ab);
   const size_t wb = sweep_warp_bytes(A.chunk_bytes, A.slot_bytes);
   uint8_t* mine = smem + vec_bytes + (size_t)warp * wb;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + vec_bytes + (size_t)NW * wb);
@@ -977,7 +1000,8 @@ __global__ void __launch_bounds__(NW * 32, 1) bfly_sweep_kernel(const SweepArgs 
     fence_mbar_init();
   }
   __syncthreads();
-  warp_loop<TR, NW, FG>(A, S, reinterpret_cast<typename TR::C*>(smem), warp, lane, mine, bars + 4 * warp,
+  typename TR::C* vecs = A.gvec ? reinterpret_cast<typename TR::C*>(A.gvec) : reinterpret_cast<typename TR::C*>(smem);
+  warp_loop<TR, NW, FG>(A, S, vecs, warp, lane, mine, bars + 4 * warp,
                         mine + 2 * (size_t)A.chunk_bytes, bars + 4 * warp + 2);
 }
 

@@ -38,6 +38,7 @@ EXPORTS = [
     "sht_plan_save", "sht_plan_load", "sht_batch_synthesize_grid", "sht_batch_analyze_grid",
     "sht_measure_fp64_fma", "sht_interp_decomp", "sht_plan_stats", "sht_batched_workspace_bytes",
     "sht_synthesize_batched", "sht_analyze_batched", "sht_batch_get_groups",
+    "sht_gj_plan_create", "sht_gj_forward", "sht_gj_inverse", "sht_gj_launches",
 ]
 
 NOALLOC_MAX_SLOTS = 32  # SHT_NOALLOC_MAX_SLOTS
@@ -174,6 +175,10 @@ def lib():
     L.sht_batched_workspace_bytes.restype = ctypes.c_size_t
     L.sht_synthesize_batched.argtypes = [c_int, vp, c_int, vp, vp, vp, vp]
     L.sht_analyze_batched.argtypes = [c_int, vp, c_int, vp, vp, vp, vp]
+    L.sht_gj_plan_create.argtypes = [c_int, c_int, c_int, c_double, ctypes.POINTER(sht_plan_opts), ctypes.POINTER(vp)]
+    L.sht_gj_forward.argtypes = [vp, c_int, vp, vp, vp]
+    L.sht_gj_inverse.argtypes = [vp, c_int, vp, vp, vp]
+    L.sht_gj_launches.argtypes = [vp, c_int, c_int, ctypes.POINTER(c_int)]
     for name in EXPORTS:
         if name not in ("sht_status_string", "sht_workspace_bytes", "sht_last_error_detail",
                         "sht_batched_workspace_bytes"):
@@ -301,6 +306,44 @@ class Plan:
         _check(lib().sht_plan_stream(self.handle, int(prec), int(direction), buf.ctypes.data, ctypes.byref(n),
                                      ctypes.byref(npg)), "sht_plan_stream")
         return buf[:npg.value], buf[npg.value:]
+
+
+class GJPlan(Plan):
+    """Owns a single-block plan of the paper's Section 4 matrices
+    (``sht_gj_plan_create``): order m, parity 0 (eq. transform) or 1 (eq.
+    transform2), size n."""
+
+    def __init__(self, n, m, parity, eps_id=1e-12, leaf_cols=64, host_only=False, page_bytes=0, eps_fp32=0.0,
+                 consumer_warps=0, num_threads=0):
+        L = lib()
+        opts = sht_plan_opts()
+        _check(L.sht_plan_opts_default(ctypes.byref(opts)), "sht_plan_opts_default")
+        opts.leaf_cols = leaf_cols
+        opts.host_only = 1 if host_only else 0
+        opts.page_bytes = page_bytes
+        opts.eps_fp32 = eps_fp32
+        opts.consumer_warps = consumer_warps
+        opts.num_threads = num_threads
+        h = ctypes.c_void_p()
+        _check(L.sht_gj_plan_create(int(n), int(m), int(parity), float(eps_id), ctypes.byref(opts), ctypes.byref(h)),
+               "sht_gj_plan_create")
+        self.handle = h
+        self.l = self.n = int(n)
+        self.m, self.parity = int(m), int(parity)
+        self.host_only = host_only
+
+    def launches(self, prec, direction):
+        c = ctypes.c_int()
+        _check(lib().sht_gj_launches(self.handle, int(prec), int(direction), ctypes.byref(c)), "sht_gj_launches")
+        return c.value
+
+
+def sht_gj_forward(plan, prec, beta, alpha, stream=None):
+    _check(lib().sht_gj_forward(plan.handle, int(prec), _ptr(beta), _ptr(alpha), _stream(stream)), "sht_gj_forward")
+
+
+def sht_gj_inverse(plan, prec, alpha, beta, stream=None):
+    _check(lib().sht_gj_inverse(plan.handle, int(prec), _ptr(alpha), _ptr(beta), _stream(stream)), "sht_gj_inverse")
 
 
 def sht_legendre_synthesize(plan, prec, beta, G, stream=None):

@@ -15,7 +15,7 @@ def pytest_configure(config):
 # nothing, so a skip inside these modules (a missing package, say) is
 # reported as a failure instead.
 _PIN_MODULES = ("test_oracle_legendre.py", "test_oracle_quadrature.py", "test_oracle_sht.py",
-                "test_oracle_planted.py", "test_quadrature_host.py")
+                "test_oracle_planted.py", "test_quadrature_host.py", "test_oracle_gauss_jacobi.py")
 
 
 def pytest_runtest_makereport(item, call):

@@ -123,19 +123,35 @@ def _tri(l):
     return np.concatenate([[0], np.cumsum(L - np.arange(L))])
 
 
-def emulate(stream, chunk_bytes, l, prec, direction, inp, prescale=None, twiddle=None):
+def emulate(stream, chunk_bytes, l, prec, direction, inp, prescale=None, twiddle=None, plain=False):
     """Applies a whole stream.  direction 0: inp = beta triangle -> G (2l, 2l);
-    direction 1: inp = G -> beta triangle."""
+    direction 1: inp = G -> beta triangle.  plain=True applies a single-block
+    stream (sht_gj_plan_create: l = n) to vectors of n entries: coefficient
+    j and node value r are elements j and r, with no parity interleave,
+    fold or unfold (the stages run in their order in the stream)."""
     L = 2 * l
-    size = 8 * L + 64
+    size = 64 * L + 4096
     bufs = [np.zeros(size, dtype=np.complex128) for _ in range(4)]
     tri = _tri(l)
+    if plain:
+        tri = np.zeros(L + 1, dtype=np.int64)
     if direction == 0:
         G = np.full((L, L), np.nan, dtype=np.complex128)
         beta = np.asarray(inp, dtype=np.complex128)
     else:
         beta = np.full(tri[-1], np.nan, dtype=np.complex128)
         G = np.asarray(inp, dtype=np.complex128)
+    if plain:
+        # a vector of n: the "row" of order 0 at columns l + r, and the
+        # coefficients at 2j (p = 0) of a flat array
+        if direction == 0:
+            y = np.full(l, np.nan, dtype=np.complex128)
+            beta2 = np.zeros(2 * l, dtype=np.complex128)
+            beta2[0::2] = beta
+            beta = beta2
+        else:
+            y = np.asarray(inp, dtype=np.complex128)
+            beta = np.full(2 * l, np.nan, dtype=np.complex128)
     for h, idx, vals in iter_ops(stream, chunk_bytes):
         kind, M, K = int(h["kind"]), int(h["M"]), int(h["K"])
         io, oo = int(h["io"]), int(h["oo"])
@@ -143,7 +159,18 @@ def emulate(stream, chunk_bytes, l, prec, direction, inp, prescale=None, twiddle
         src, dst = bufs[int(h["in_buf"])], bufs[int(h["out_buf"])]
         acc = bool(h["flags"] & F_ACCUM)
         tw = 1.0 if twiddle is None else twiddle[m]
-        if kind == OP_GATHER:
+        if plain:
+            p, m, tw = 0, 0, 1.0
+        if plain and kind == OP_FOLD:
+            r = oo + np.arange(M)
+            dst[cb + oo:cb + oo + M] = y[r]
+        elif plain and kind == OP_GZERO:
+            y[oo + np.arange(M)] = 0
+        elif plain and kind == OP_DENSE_G:
+            V = decode_values(vals, prec, K * M).reshape(K, M)
+            r = oo + np.arange(M)
+            y[r] = (y[r] if acc else 0) + V.T @ src[io:io + K]
+        elif kind == OP_GATHER:
             dst[cb + oo:cb + oo + M] = beta[tri[m] + p + 2 * (oo + np.arange(M))]
         elif kind == OP_SCATTER:
             beta[tri[m] + p + 2 * (io + np.arange(M))] = src[cb + io:cb + io + M]
@@ -193,6 +220,8 @@ def emulate(stream, chunk_bytes, l, prec, direction, inp, prescale=None, twiddle
                     dst[oo + skel] = src[io:io + nsk]
         else:
             raise ValueError(f"unknown op kind {kind}")
+    if plain:
+        return y if direction == 0 else beta[0::2]
     return G if direction == 0 else beta
 
 

@@ -118,3 +118,50 @@ def test_invalid_arguments():
     assert L.sht_gauss_jacobi_nodes(0, 0, 0, x.ctypes.data, x.ctypes.data) == 1
     out = sht.sht_unit_stats()
     assert L.sht_unit_stats_gauss_jacobi(0, 0, 0, 1e-12, None, 1, ctypes.byref(out)) == 1
+
+
+@pytest.mark.parametrize("n,m,p", [(200, 0, 0), (129, 7, 1), (300, 300, 1)])
+def test_single_block_streams_match_oracle_on_host(n, m, p):
+    """The level-by-level streams of a single-block plan (sht_gj_plan_create),
+    decoded and applied on the host (tests/stream_emulator.py, stage by
+    stage), against the oracle's A beta and A^T alpha."""
+    from tests.stream_emulator import emulate
+
+    P = sht.GJPlan(n, m, p, eps_id=1e-12, leaf_cols=32, host_only=True)
+    A = oracle.gj_matrix(m, p, n)
+    rng = np.random.default_rng(3)
+    b = rng.uniform(-1, 1, n) + 1j * rng.uniform(-1, 1, n)
+    tol = {0: 1e-11, 2: 1e-11, 1: 1e-6}
+    for prec in (0, 2, 1):
+        P.prepare(prec)
+        a = emulate(P.stream(prec, 0), P.page_bytes, n, prec, 0, b, plain=True)
+        assert np.linalg.norm(a - A @ b) / np.linalg.norm(A @ b) < tol[prec]
+        bb = emulate(P.stream(prec, 1), P.page_bytes, n, prec, 1, a, plain=True)
+        assert np.linalg.norm(bb - A.T @ a) / np.linalg.norm(b) < tol[prec]
+        assert P.launches(prec, 0) >= 3 and P.launches(prec, 1) >= 3
+    P.close()
+
+
+def test_single_block_plan_refused_by_order_entry_points():
+    import ctypes
+
+    L = sht.lib()
+    P = sht.GJPlan(64, 64, 0, leaf_cols=16, host_only=True)
+    x = np.zeros(4)
+    assert L.sht_legendre_synthesize(P.handle, 0, x.ctypes.data, x.ctypes.data, None) == 6  # SHT_ERR_UNSUPPORTED
+    assert L.sht_plan_nodes(P.handle, x.ctypes.data, x.ctypes.data) == 6
+    assert L.sht_plan_save(P.handle, b"/nonexistent/x") == 6
+    Q = sht.Plan(8, 1e-12, host_only=True)
+    assert L.sht_gj_forward(Q.handle, 0, x.ctypes.data, x.ctypes.data, None) == 6
+    c = ctypes.c_int()
+    assert L.sht_gj_launches(Q.handle, 0, 0, ctypes.byref(c)) == 6
+    out = ctypes.c_void_p()
+    assert L.sht_gj_plan_create(0, 0, 0, 1e-12, None, ctypes.byref(out)) == 1
+    assert L.sht_gj_plan_create(10, 0, 2, 1e-12, None, ctypes.byref(out)) == 1
+    assert L.sht_gj_plan_create(sht_max_n() + 1, 0, 0, 1e-12, None, ctypes.byref(out)) == 1
+    P.close()
+    Q.close()
+
+
+def sht_max_n():
+    return 40000  # SHT_GJ_MAX_N
