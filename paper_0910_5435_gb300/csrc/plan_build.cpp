@@ -1284,31 +1284,78 @@ void emit_unit(PlanHost& P, int prec, int dir, int m, Emitter& E) {
 
 // Schedules the ops of one work item onto nw warps and encodes the item
 // (ItemHeader, WarpRange[nw], then each warp's record stream in chunks of
-// `chunk` bytes; see sht_stream.h).  List scheduling in emission order: an
-// op goes to the warp on which it can start first (its predecessors'
-// estimated finish times against each warp's estimated free time), so each
-// warp's list is in the emission order, a topological order of the item's
-// dependency graph.  Returns the item bytes (a multiple of 16).
+// `chunk` bytes; see sht_stream.h).  Event-driven list scheduling on the
+// estimated costs: whenever a warp falls free, it takes, among the ops whose
+// predecessors are all scheduled, the most critical one that can start now
+// (the longest estimated path to the end of the item), or else the one that
+// can start soonest.  An op is scheduled only after its predecessors, so each
+// warp's list is a topological order and a wait on another warp's earlier
+// position can never close a cycle.  Returns the item bytes (a multiple of 16).
 void encode_item(const std::vector<OpRec>& ops, int nw, size_t chunk, std::vector<uint8_t>& out) {
   const int n = (int)ops.size();
-  std::vector<double> fin(n, 0.0), wfree(nw, 0.0);
-  std::vector<int> warp(n), pos(n), cnt(nw, 0);
-  for (int t = 0; t < n; ++t) {
-    double ready = 0;
-    for (int u : ops[t].preds) ready = std::max(ready, fin[u]);
-    int best = 0;
-    double best_start = std::max(wfree[0], ready);
-    for (int w = 1; w < nw; ++w) {
-      const double st = std::max(wfree[w], ready);
-      if (st < best_start) {
-        best_start = st;
-        best = w;
+  std::vector<int> warp(n), pos(n), cnt(nw, 0), order;
+  order.reserve(n);
+  {
+    // successors and bottom levels (longest estimated path to the item's end)
+    std::vector<std::vector<int>> succ(n);
+    std::vector<int> npend(n, 0);
+    for (int t = 0; t < n; ++t) {
+      npend[t] = (int)ops[t].preds.size();
+      for (int u : ops[t].preds) succ[u].push_back(t);
+    }
+    std::vector<double> blevel(n, 0.0);
+    for (int t = n - 1; t >= 0; --t) {
+      double b = 0;
+      for (int v : succ[t]) b = std::max(b, blevel[v]);
+      blevel[t] = ops[t].cost + b;
+    }
+    std::vector<double> ready_at(n, 0.0), wfree(nw, 0.0);
+    std::vector<int> cand;
+    for (int t = 0; t < n; ++t)
+      if (npend[t] == 0) cand.push_back(t);
+    for (int done = 0; done < n; ++done) {
+      int w = 0;
+      for (int v = 1; v < nw; ++v)
+        if (wfree[v] < wfree[w]) w = v;
+      const double now = wfree[w];
+      // the most critical op that is ready now, else the one ready soonest
+      int best = -1;
+      bool best_ready = false;
+      for (int i = 0; i < (int)cand.size(); ++i) {
+        const int t = cand[i];
+        const bool r = ready_at[t] <= now;
+        if (best < 0) {
+          best = i;
+          best_ready = r;
+          continue;
+        }
+        const int b = cand[best];
+        bool better;
+        if (r != best_ready) {
+          better = r;
+        } else if (r) {
+          better = blevel[t] > blevel[b] || (blevel[t] == blevel[b] && t < b);
+        } else {
+          better = ready_at[t] < ready_at[b] || (ready_at[t] == ready_at[b] && blevel[t] > blevel[b]);
+        }
+        if (better) {
+          best = i;
+          best_ready = r;
+        }
+      }
+      const int t = cand[best];
+      cand[best] = cand.back();
+      cand.pop_back();
+      const double fin = std::max(now, ready_at[t]) + ops[t].cost;
+      wfree[w] = fin;
+      warp[t] = w;
+      pos[t] = cnt[w]++;
+      order.push_back(t);
+      for (int v : succ[t]) {
+        ready_at[v] = std::max(ready_at[v], fin);
+        if (--npend[v] == 0) cand.push_back(v);
       }
     }
-    fin[t] = best_start + ops[t].cost;
-    wfree[best] = fin[t];
-    warp[t] = best;
-    pos[t] = cnt[best]++;
   }
   for (int w = 0; w < nw; ++w)
     if (cnt[w] > kMaxWarpOps) throw std::logic_error("work item has too many ops for one warp");
@@ -1326,7 +1373,7 @@ void encode_item(const std::vector<OpRec>& ops, int nw, size_t chunk, std::vecto
   }
   std::vector<std::vector<uint8_t>> st(nw);
   std::vector<int> need(nw);
-  for (int t = 0; t < n; ++t) {
+  for (int t : order) {
     const int w = warp[t];
     std::fill(need.begin(), need.end(), -1);
     for (int u : ops[t].preds)

@@ -133,8 +133,10 @@ def test_l512_sampled_orders_match_oracle(sht):
         assert rel(b[sel], bo[sel]) < TOL[prec], prec
 
 
-def test_direct_fp64_matches_oracle(sht):
-    l = 64
+@pytest.mark.parametrize("l", [64, 200])
+def test_direct_fp64_matches_oracle(sht, l):
+    """The direct comparator against the oracle; at l = 200 the analysis
+    splits the units of small m into column tiles of 64 (200 = 3 * 64 + 8)."""
     P = sht.Plan(l, 1e-12, leaf_cols=16)
     sht.sht_direct_prepare(P)
     beta = inputs.random_beta(l, seed=9)
