@@ -903,12 +903,16 @@ struct Emitter {
       r.planted = true;
       plant_unmet = false;
     }
-    // estimated cycles of one warp (measured on GB300 at l = 1024): a fixed
-    // cost per op (its value copy, waits and completion) and a cost per value
+    // estimated cycles of one warp, fitted to the sweep's cycle counters on
+    // GB300 at l = 1024 (two value caps per precision): a compute op costs a
+    // fixed part (setup, value copy wait, reduction, completion) plus a part
+    // per value; a control op a part per precision, a fold (two node values
+    // per element, from global memory) about 2.4 times as much
     const double M = h.M, K = h.K;
-    const double per_value = prec == 0 ? 13.5 : prec == 2 ? 5.5 : 2.8;
-    r.cost = (h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) ? 2400.0 + per_value * M * K
-                                                                   : 1500.0 + 2.0 * M;
+    const double fixed = prec == 0 ? 1650.0 : prec == 2 ? 2100.0 : 1800.0;
+    const double per_value = prec == 0 ? 15.2 : prec == 2 ? 4.6 : 1.25;
+    const double ctl = (prec == 0 ? 2300.0 : prec == 2 ? 3800.0 : 1700.0) * (h.kind == OP_FOLD ? 2.4 : 1.0);
+    r.cost = (h.kind >= OP_SYN_INTERP && h.kind <= OP_ANA_INTERP) ? fixed + per_value * M * K : ctl + 2.0 * M;
     r.stage = stage;
     ops.push_back(std::move(r));
   }

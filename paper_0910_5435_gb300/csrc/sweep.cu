@@ -698,6 +698,27 @@ __device__ __forceinline__ bool warp_wait(Pred pred, const SweepArgs& A, Ctl* S,
   return ok != 0;
 }
 
+// Every lane polls the mbarrier phase itself, so each lane's successful
+// try_wait is its own acquire of the copied bytes; bounded like warp_wait.
+__device__ __forceinline__ bool warp_poll_mbar(uint64_t* bar, uint32_t parity, const SweepArgs& A, Ctl* S,
+                                               int lane) {
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    int bad = 0;
+    if (lane == 0) {
+      if (vload(&S->abort)) {
+        bad = 1;
+      } else if (clock64() - t0 > kTimeoutCycles) {
+        fail(A, S, kStatusTimeout);
+        bad = 1;
+      }
+    }
+    if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+  }
+}
+
 // One warp's walk over its scheduled ops of every item its CTA takes.
 template <class TR, int NW, int FG>
 __device__ void warp_loop(const SweepArgs& A, Ctl* S, typename TR::C* vec_base, int warp, int lane, uint8_t* ring,
@@ -781,8 +802,7 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, typename TR::C* vec_base, 
         const uint32_t r = waited & 1u;
         const uint32_t ph = (ring_par >> r) & 1u;
         const long long t0 = tracing ? clock64() : 0;
-        if (!warp_wait([&] { return mbar_try_wait(ring_bar + r, ph); }, A, S, lane)) return false;
-        mbar_try_wait(ring_bar + r, ph);  // each lane's own acquire of the bytes
+        if (!warp_poll_mbar(ring_bar + r, ph, A, S, lane)) return false;
         ring_par ^= 1u << r;
         ring_busy &= ~(1u << r);
         if (tracing) c_rec += clock64() - t0;
@@ -892,11 +912,10 @@ __device__ void warp_loop(const SweepArgs& A, Ctl* S, typename TR::C* vec_base, 
       }
       const long long t2 = tracing ? clock64() : 0;
       if (vals) {
-        if (!warp_wait([&] { return mbar_try_wait(slot_bar, slot_par); }, A, S, lane)) {
+        if (!warp_poll_mbar(slot_bar, slot_par, A, S, lane)) {
           ok = false;
           break;
         }
-        mbar_try_wait(slot_bar, slot_par);  // each lane's own acquire of the copied bytes
         slot_par ^= 1u;
         slot_busy = false;
       }
