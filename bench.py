@@ -68,8 +68,9 @@ def parse():
 # read once, beta and G are under 1 % of it).  Valid only for the kernel and
 # stream-format sources the capture was taken with (sources_sha); None when
 # no capture matches.
-SWEEP_TRAFFIC_CAPTURE = {"l": 512, "leaf_cols": 32, "page_bytes": 0, "stream_bytes": None,
-                         "dram_bytes_syn": None, "dram_bytes_ana": None, "sources_sha": None}
+SWEEP_TRAFFIC_CAPTURE = {"l": 512, "leaf_cols": 32, "page_bytes": 0, "stream_bytes": 1087871856,
+                         "dram_bytes_syn": 1.097982e9 + 20.359424e6, "dram_bytes_ana": 1.093350e9 + 15.659008e6,
+                         "sources_sha": "cf3674ba319e8197"}
 
 
 def sweep_sources_sha():
