@@ -69,8 +69,8 @@ def parse():
 # stream-format sources the capture was taken with (sources_sha); None when
 # no capture matches.
 SWEEP_TRAFFIC_CAPTURE = {"l": 512, "leaf_cols": 32, "page_bytes": 0, "stream_bytes": 1087871856,
-                         "dram_bytes_syn": 1.097982e9 + 20.359424e6, "dram_bytes_ana": 1.093350e9 + 15.659008e6,
-                         "sources_sha": "cf3674ba319e8197"}
+                         "dram_bytes_syn": 1.098086e9 + 20.595712e6, "dram_bytes_ana": 1.093210e9 + 16.140544e6,
+                         "sources_sha": "e69d3acd1850279b"}
 
 
 def sweep_sources_sha():

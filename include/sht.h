@@ -566,8 +566,9 @@ sht_status sht_batch_last_device_status(sht_batch_t batch, sht_stream_t stream);
  * the given direction with these DEVICE pointer arrays, and keeps the
  * fastest for that direction.  The plans' work items are scheduled for their
  * consumer warps, which fixes the warps and the shared-memory layout of a
- * launch; what is chosen is the number of resident CTAs per SM where more
- * than one fits.  Directions: 0 synthesis, 1 analysis, 2 adjoint of
+ * launch; what is chosen is how many fields that share a plan are applied
+ * together (at most 1, 2 or 4 per group, as far as their vectors fit in
+ * shared memory).  Directions: 0 synthesis, 1 analysis, 2 adjoint of
  * synthesis, 3 and 4 the Legendre launches of sht_batch_synthesize_grid
  * (beta -> workspace) and sht_batch_analyze_grid (workspace -> beta).  Runs
  * the transform (writes the outputs); synchronous. */

@@ -15,6 +15,12 @@ the precision.  Coefficients and G are treated as independent complex
 numbers; a loss on the real grid (which counts orders +m and -m) would add
 its own factor 2 for m > 0 outside this function.
 
+Batches of fields (beta of shape [B, T]) run as one launch per direction;
+the first launch of each direction on a cached batch first runs the batch
+autotuner (synchronous, a few launches) to choose how many fields share a
+reading of the factor stream.  Make that first call outside any CUDA graph
+capture.
+
 Device status: the launches are asynchronous and their bounded waits report
 a timeout only in a device status word (the kernel then stops early and its
 output is undefined).  Nothing here reads that word unless asked:
@@ -41,6 +47,16 @@ def _batch(plan, prec, n):
     return cache[key]
 
 
+def _tune_once(B, direction, ip, op, stream):
+    """The batch autotuner (fields per group) on the first launch of each
+    direction, with that launch's own pointers (its outputs are overwritten
+    by the launch that follows)."""
+    done = B.__dict__.setdefault("_tuned", set())
+    if direction not in done:
+        sht.sht_batch_autotune(B, direction, ip, op, reps=2, stream=stream)
+        done.add(direction)
+
+
 def _apply(plan, prec, x, adjoint):
     l = plan.l
     T = (2 * l) * (2 * l + 1) // 2
@@ -63,6 +79,7 @@ def _apply(plan, prec, x, adjoint):
         B = _batch(plan, prec, n)
         ip = sht.pointer_array(list(xs), device=x.device)
         op = sht.pointer_array(list(out), device=x.device)
+        _tune_once(B, 2 if adjoint else 0, ip, op, stream)  # batch directions: 0 synthesis, 2 its adjoint
         fn = sht.sht_batch_synthesize_adjoint if adjoint else sht.sht_batch_synthesize
         fn(B, ip, op, stream)
         # the pointer arrays must live until the launch has read them

@@ -103,6 +103,8 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, uns
 
 // float64 factors and arithmetic; complex128 I/O.
 struct TF64 {
+  // the reduction tree splits the components between lane pairs (run_gemv)
+  static constexpr bool kSplitComponents = true;
   // one accumulation chain: a full-warp DFMA holds the scheduler's FP64 pipe
   // longer than its latency, so a second chain only adds merge work
   static constexpr int kChains = 1;
@@ -151,6 +153,7 @@ struct TF64 {
 // dropped); sums use Knuth's TwoSum.  The _rn intrinsics keep the compiler
 // from contracting the error-free transformations.
 struct TS32 {
+  static constexpr bool kSplitComponents = false;
   static constexpr int kChains = 2;
   using V = float2;  // {hi, lo}
   using C = float4;  // {re_hi, re_lo, im_hi, im_lo}
@@ -274,6 +277,7 @@ struct TS32A : TS32 {
 
 // float32 factors and arithmetic; complex64 I/O.
 struct TF32 {
+  static constexpr bool kSplitComponents = false;
   static constexpr int kChains = 2;
   using V = float;
   using C = float2;
@@ -507,6 +511,80 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
     for (int f = 0; f < FG; ++f) {
       if (f >= nf) break;
       Acc a0 = a[f];
+      if constexpr (TR::kSplitComponents) {
+        if (ks >= 2 && (ks & (ks - 1)) == 0) {
+          // float64, ks a power of two: the same tree with the components
+          // split between lane pairs.  Lanes q and q ^ 1 first exchange one
+          // component each, so that even lanes carry the real sums and odd
+          // lanes the imaginary ones; every further step adds one double
+          // instead of two (the FP64 pipe is the bound).  Each sum is the
+          // plain tree's, operand for operand, so the results are the same
+          // bits.  Lane q = 0 ends with the real part, q = 1 with the
+          // imaginary part.
+          const int comp = q & 1;
+          double v = comp ? a0.im : a0.re;
+          const double give = comp ? a0.re : a0.im;
+          v += __shfl_xor_sync(0xffffffffu, give, 1);
+          for (int off = 2; off < ks; off <<= 1) {
+            const double b = __shfl_down_sync(0xffffffffu, v, off);
+            if (q + off < ks) v += b;
+          }
+          if (h.kind == OP_DENSE_G && A.twiddle && !A.plain) {
+            // the phase mixes the components: lane q = 0 takes both
+            const double w = __shfl_xor_sync(0xffffffffu, v, 1);
+            if (q == 0 && o < M) {
+              const int l = A.l;
+              const int i = h.oo + o;
+              IO z = TR::io_cmul(make_double2(v, w), A.twiddle[h.a1]);
+              IO* G = reinterpret_cast<IO*>(A.out[f]) + (size_t)h.a1 * (2 * l);
+              if (accum) {
+                G[l + i] = TR::io_add(G[l + i], z);
+                G[l - 1 - i] = TR::io_sub(G[l - 1 - i], z);
+              } else {
+                G[l + i] = z;
+                G[l - 1 - i] = z;
+              }
+            }
+          } else if (q < 2 && o < M) {
+            const double* in = reinterpret_cast<const double*>(S.buf(h.in_buf, f) + h.io);
+            double* out = reinterpret_cast<double*>(S.buf(h.out_buf, f) + h.oo);
+            switch (h.kind) {
+              case OP_SYN_INTERP:
+                out[2 * o + comp] = v + in[2 * idx[K + o] + comp];
+                break;
+              case OP_DENSE:
+                out[2 * o + comp] = v;
+                break;
+              case OP_ANA_INTERP: {
+                const int pos = idx[o];
+                out[2 * pos + comp] = accum ? v + out[2 * pos + comp] : v;
+                break;
+              }
+              case OP_DENSE_G: {
+                const int l = A.l;
+                const int i = h.oo + o;
+                if (A.plain) {
+                  double* y = reinterpret_cast<double*>(A.out[f]);
+                  y[2 * i + comp] = accum ? y[2 * i + comp] + v : v;
+                  break;
+                }
+                double* G = reinterpret_cast<double*>(reinterpret_cast<IO*>(A.out[f]) + (size_t)h.a1 * (2 * l));
+                if (accum) {
+                  G[2 * (l + i) + comp] = G[2 * (l + i) + comp] + v;
+                  G[2 * (l - 1 - i) + comp] = G[2 * (l - 1 - i) + comp] - v;
+                } else {
+                  G[2 * (l + i) + comp] = v;
+                  G[2 * (l - 1 - i) + comp] = v;
+                }
+                break;
+              }
+              default:
+                break;
+            }
+          }
+          continue;
+        }
+      }
       // segmented tree: after the step with offset d, lane q holds the sum
       // over q .. min(q + 2d - 1, ks - 1) of its segment
       for (int off = 1; off < ks; off <<= 1) {
