@@ -458,7 +458,7 @@ sht_status sht_unit_stats_gauss_jacobi(int n, int m, int parity, double eps_id, 
  * sht_last_device_status apply.  The order-based entry points (Legendre
  * stage, phi stage, direct baseline, batches, sht_plan_nodes, sht_plan_save)
  * refuse such a plan with SHT_ERR_UNSUPPORTED.  Returns SHT_ERR_INVALID_ARG
- * also when a butterfly level is wider than 65535 elements. */
+ * also when a butterfly level is wider than 2^20 elements. */
 sht_status sht_gj_plan_create(int n, int m, int parity, double eps_id, const sht_plan_opts* opts, sht_plan_t* out);
 
 /* The forward transform alpha = A beta (eqs. transform / transform2) and the

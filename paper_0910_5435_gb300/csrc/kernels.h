@@ -63,6 +63,8 @@ struct SweepArgs {
   // (num_vecs * buf_ab elements) in global memory, shared by all CTAs of the
   // launch, instead of in shared memory; the launch is then one stage of a
   // level-by-level schedule (no two ops of a launch touch the same element).
+  // In plain mode an op's a1 carries the bits of its vector positions io and
+  // oo above 16 (the levels of a large block are wider than 65535).
   int plain;
   void* gvec;
 };

@@ -768,7 +768,21 @@ struct Emitter {
   // independent ops (a gather, one butterfly level, the final blocks, ...);
   // level-by-level schedules launch each stage on its own.
   int stage = 0;
+  // Vector positions are 16 bits in io / oo.  A wide emitter (single-block
+  // streams, whose ops address no order) keeps the bits above in a1: io's
+  // in its low half, oo's in its high half.
+  bool wide = false;
   explicit Emitter(int p) : prec(p), vs(value_size(p)) {}
+
+  void set_io_oo(OpHdr& h, long long io, long long oo) const {
+    if (io < 0 || oo < 0 || (!wide && (io > 0xFFFF || oo > 0xFFFF)) || io >= (1LL << 20) || oo >= (1LL << 20))
+      throw std::runtime_error("vector position out of range");
+    h.io = (uint16_t)(io & 0xFFFF);
+    h.oo = (uint16_t)(oo & 0xFFFF);
+    if (wide) h.a1 = (uint32_t)((io >> 16) | ((oo >> 16) << 16));
+  }
+  long long full_io(const OpHdr& h) const { return h.io + (wide ? (long long)(h.a1 & 0xFFFF) << 16 : 0); }
+  long long full_oo(const OpHdr& h) const { return h.oo + (wide ? (long long)(h.a1 >> 16) << 16 : 0); }
 
   // Chooses the base of a block using `width` positions of each vector.
   void place(int width) {
@@ -795,45 +809,47 @@ struct Emitter {
   // vectors, (1 << 40 | m << 20 | row) for node rows of G.
   void access(const OpHdr& h, const std::vector<uint16_t>& idx, std::vector<long long>& R,
               std::vector<long long>& Wr) const {
-    auto vkey = [](int b, int pos) { return ((long long)b << 20) | pos; };
+    auto vkey = [](int b, long long pos) { return ((long long)b << 20) | pos; };
     auto gkey = [](int m, int row) { return (1LL << 40) | ((long long)m << 20) | row; };
     const int M = h.M, K = h.K;
     const int cbase = h.a0 >> 1;  // GATHER / SCATTER / FOLD: vector base
+    const long long io = full_io(h), oo = full_oo(h);
+    const uint32_t m = wide ? 0u : h.a1;  // a wide stream's ops address no order
     switch (h.kind) {
       case OP_GATHER:
       case OP_FOLD:
-        for (int j = 0; j < M; ++j) Wr.push_back(vkey(h.out_buf, cbase + h.oo + j));
+        for (int j = 0; j < M; ++j) Wr.push_back(vkey(h.out_buf, cbase + oo + j));
         break;
       case OP_CLEAR:
-        for (int j = 0; j < M; ++j) Wr.push_back(vkey(h.out_buf, h.oo + j));
+        for (int j = 0; j < M; ++j) Wr.push_back(vkey(h.out_buf, oo + j));
         break;
       case OP_SCATTER:
-        for (int j = 0; j < M; ++j) R.push_back(vkey(h.in_buf, cbase + h.io + j));
+        for (int j = 0; j < M; ++j) R.push_back(vkey(h.in_buf, cbase + io + j));
         break;
       case OP_GZERO:
-        for (int j = 0; j < M; ++j) Wr.push_back(gkey(h.a1, l + h.oo + j)), Wr.push_back(gkey(h.a1, l - 1 - h.oo - j));
+        for (int j = 0; j < M; ++j) Wr.push_back(gkey(m, l + oo + j)), Wr.push_back(gkey(m, l - 1 - oo - j));
         break;
       case OP_SYN_INTERP:
-        for (int s = 0; s < K + M; ++s) R.push_back(vkey(h.in_buf, h.io + idx[s]));
-        for (int o = 0; o < M; ++o) Wr.push_back(vkey(h.out_buf, h.oo + o));
+        for (int s = 0; s < K + M; ++s) R.push_back(vkey(h.in_buf, io + idx[s]));
+        for (int o = 0; o < M; ++o) Wr.push_back(vkey(h.out_buf, oo + o));
         break;
       case OP_DENSE:
-        for (int s = 0; s < K; ++s) R.push_back(vkey(h.in_buf, h.io + s));
-        for (int o = 0; o < M; ++o) Wr.push_back(vkey(h.out_buf, h.oo + o));
+        for (int s = 0; s < K; ++s) R.push_back(vkey(h.in_buf, io + s));
+        for (int o = 0; o < M; ++o) Wr.push_back(vkey(h.out_buf, oo + o));
         break;
       case OP_DENSE_G:
-        for (int s = 0; s < K; ++s) R.push_back(vkey(h.in_buf, h.io + s));
+        for (int s = 0; s < K; ++s) R.push_back(vkey(h.in_buf, io + s));
         for (int o = 0; o < M; ++o) {
-          Wr.push_back(gkey(h.a1, l + h.oo + o));
-          Wr.push_back(gkey(h.a1, l - 1 - h.oo - o));
+          Wr.push_back(gkey(m, l + oo + o));
+          Wr.push_back(gkey(m, l - 1 - oo - o));
         }
         if (h.flags & F_ACCUM) R.insert(R.end(), Wr.begin(), Wr.end());
         break;
       case OP_ANA_INTERP: {
-        for (int s = 0; s < K; ++s) R.push_back(vkey(h.in_buf, h.io + s));
-        for (int o = 0; o < M; ++o) Wr.push_back(vkey(h.out_buf, h.oo + idx[o]));
+        for (int s = 0; s < K; ++s) R.push_back(vkey(h.in_buf, io + s));
+        for (int o = 0; o < M; ++o) Wr.push_back(vkey(h.out_buf, oo + idx[o]));
         if (h.flags & F_SKEL)
-          for (int t = 0; t < h.nskel; ++t) Wr.push_back(vkey(h.out_buf, h.oo + idx[M + t]));
+          for (int t = 0; t < h.nskel; ++t) Wr.push_back(vkey(h.out_buf, oo + idx[M + t]));
         if (h.flags & F_ACCUM) R.insert(R.end(), Wr.begin(), Wr.end());
         break;
       }
@@ -929,6 +945,7 @@ struct Emitter {
   }
 
   void write(OpHdr h, const std::vector<uint16_t>& idx, const std::vector<double>& vals) {
+    if (wide && base) throw std::logic_error("a wide stream places its one block at 0");
     // shift the op's vector positions to the block's base (control ops whose
     // offsets also index coefficients or node rows carry it in a0)
     switch (h.kind) {
@@ -970,8 +987,7 @@ struct Emitter {
       if (b <= a) continue;
       OpHdr h = base;
       h.M = (uint16_t)(b - a);
-      h.oo = (uint16_t)a;
-      h.io = (uint16_t)a;
+      set_io_oo(h, a, a);
       write(h, {}, {});
     }
   }
@@ -1000,8 +1016,7 @@ struct Emitter {
       h.M = (uint16_t)mp;
       h.K = (uint16_t)K;
       h.nskel = (uint16_t)mp;
-      h.io = (uint16_t)b.in_off;
-      h.oo = (uint16_t)(b.out_off + o0);
+      set_io_oo(h, b.in_off, b.out_off + o0);
       std::vector<uint16_t> idx(b.red.begin(), b.red.end());
       idx.insert(idx.end(), b.skel.begin() + o0, b.skel.begin() + o0 + mp);
       std::vector<double> vals((size_t)K * mp);
@@ -1023,9 +1038,8 @@ struct Emitter {
       h.out_buf = out_buf;
       h.M = (uint16_t)mp;
       h.K = (uint16_t)K;
-      h.io = (uint16_t)io;
-      h.oo = (uint16_t)(oo + o0);
-      h.a1 = (uint32_t)m;
+      set_io_oo(h, io, oo + o0);
+      if (!wide) h.a1 = (uint32_t)m;
       std::vector<double> vals((size_t)K * mp);
       for (int s = 0; s < K; ++s)
         for (int o = 0; o < mp; ++o) vals[(size_t)s * mp + o] = getv(s, o0 + o);
@@ -1055,8 +1069,7 @@ struct Emitter {
       h.M = (uint16_t)mp;
       h.K = (uint16_t)k;
       h.nskel = (uint16_t)(skel_done ? 0 : k);
-      h.io = (uint16_t)b.out_off;
-      h.oo = (uint16_t)b.in_off;
+      set_io_oo(h, b.out_off, b.in_off);
       std::vector<uint16_t> idx(b.red.begin() + o0, b.red.begin() + o0 + mp);
       if (!skel_done) idx.insert(idx.end(), b.skel.begin(), b.skel.end());
       std::vector<double> vals((size_t)k * mp);
@@ -1459,7 +1472,7 @@ void emit_gj_streams(PlanHost& P, int prec) {
   const int NW = P.sched_warps;
   const UnitFact& U = F[(size_t)P.gj_p];
   const int positions = unit_width(U) + 1;
-  if (positions > 65535) throw std::runtime_error("block too wide: vector positions exceed 16 bits");
+  if (positions > (1 << 20)) throw std::runtime_error("block too wide: vector positions exceed 20 bits");
   for (int dir = 0; dir < 2; ++dir) {
     std::vector<uint8_t> vals;
     Emitter E(prec);
@@ -1470,6 +1483,7 @@ void emit_gj_streams(PlanHost& P, int prec) {
     E.slot_values = P.slot_values_for(prec);
     E.chunk = CH;
     E.pool = positions - 1;
+    E.wide = true;
     E.open_item(positions);
     emit_unit(P, prec, dir, 0, E);
     const std::vector<OpRec>& ops = E.ops;

@@ -110,7 +110,7 @@ struct alignas(16) OpHdr {
   uint16_t npred;     // entries of preds[]
   uint16_t a0;        // GATHER / SCATTER / FOLD: parity | vector base << 1
   uint16_t idx16;     // bytes of the index area (preds and index lists) / 16
-  uint32_t a1;        // order m
+  uint32_t a1;        // order m; single-block (plain) streams: the bits of io (low half) and oo (high half) above 16
   uint32_t vref;      // compute ops: offset of the value block in the value region, in 16-byte units
 };
 static_assert(sizeof(OpHdr) == 32, "OpHdr must be 32 bytes");

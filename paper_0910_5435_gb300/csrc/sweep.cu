@@ -484,6 +484,9 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
   const V* val = reinterpret_cast<const V*>(staged);  // this warp's staging slot
   const bool gather = (h.kind == OP_SYN_INTERP);
   const bool accum = (h.flags & F_ACCUM) != 0;
+  // vector positions: 16 bits, plus the bits above in a1 for single blocks
+  const int io = h.io + (A.plain ? (int)(h.a1 & 0xFFFFu) << 16 : 0);
+  const int oo = h.oo + (A.plain ? (int)(h.a1 >> 16) << 16 : 0);
   if (M > 0) {
     // ks = floor(32 / M) lanes per output (not only powers of two, so that
     // up to 32 - ks + 1 lanes work); lane = o * ks + q.  Both divisions come
@@ -494,11 +497,11 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
     Acc a[FG];
     if constexpr (FG == 1) {
       a[0] = TR::zero();
-      if (o < M) a[0] = gemv_dot<TR>(val, S.buf(h.in_buf) + h.io, idx, gather, M, K, o, q, ks);
+      if (o < M) a[0] = gemv_dot<TR>(val, S.buf(h.in_buf) + io, idx, gather, M, K, o, q, ks);
     } else {
       const C* inp[FG];
 #pragma unroll
-      for (int f = 0; f < FG; ++f) inp[f] = S.buf(h.in_buf, f) + h.io;
+      for (int f = 0; f < FG; ++f) inp[f] = S.buf(h.in_buf, f) + io;
       if (o < M) {
         gemv_dot_fields<TR, FG>(val, inp, idx, gather, M, K, o, q, ks, nf, a);
       } else {
@@ -534,7 +537,7 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
             const double w = __shfl_xor_sync(0xffffffffu, v, 1);
             if (q == 0 && o < M) {
               const int l = A.l;
-              const int i = h.oo + o;
+              const int i = oo + o;
               IO z = TR::io_cmul(make_double2(v, w), A.twiddle[h.a1]);
               IO* G = reinterpret_cast<IO*>(A.out[f]) + (size_t)h.a1 * (2 * l);
               if (accum) {
@@ -546,8 +549,8 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
               }
             }
           } else if (q < 2 && o < M) {
-            const double* in = reinterpret_cast<const double*>(S.buf(h.in_buf, f) + h.io);
-            double* out = reinterpret_cast<double*>(S.buf(h.out_buf, f) + h.oo);
+            const double* in = reinterpret_cast<const double*>(S.buf(h.in_buf, f) + io);
+            double* out = reinterpret_cast<double*>(S.buf(h.out_buf, f) + oo);
             switch (h.kind) {
               case OP_SYN_INTERP:
                 out[2 * o + comp] = v + in[2 * idx[K + o] + comp];
@@ -562,7 +565,7 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
               }
               case OP_DENSE_G: {
                 const int l = A.l;
-                const int i = h.oo + o;
+                const int i = oo + o;
                 if (A.plain) {
                   double* y = reinterpret_cast<double*>(A.out[f]);
                   y[2 * i + comp] = accum ? y[2 * i + comp] + v : v;
@@ -592,8 +595,8 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
         if (q + off < ks) TR::merge(a0, b);
       }
       if (q == 0 && o < M) {
-        const C* in = S.buf(h.in_buf, f) + h.io;
-        C* out = S.buf(h.out_buf, f) + h.oo;
+        const C* in = S.buf(h.in_buf, f) + io;
+        C* out = S.buf(h.out_buf, f) + oo;
         switch (h.kind) {
           case OP_SYN_INTERP:
             TR::add(a0, in[idx[K + o]]);
@@ -610,7 +613,7 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
           }
           case OP_DENSE_G: {
             const int l = A.l;
-            const int i = h.oo + o;
+            const int i = oo + o;
             IO v = TR::to_io(TR::to_c(a0));
             if (A.plain) {  // node value i of a single block
               IO* y = reinterpret_cast<IO*>(A.out[f]);
@@ -637,8 +640,8 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
   if (h.kind == OP_ANA_INTERP && (h.flags & F_SKEL)) {
     const uint16_t* skel = idx + M;
     for (int f = 0; f < nf; ++f) {
-      const C* in = S.buf(h.in_buf, f) + h.io;
-      C* out = S.buf(h.out_buf, f) + h.oo;
+      const C* in = S.buf(h.in_buf, f) + io;
+      C* out = S.buf(h.out_buf, f) + oo;
       for (int t = lane; t < h.nskel; t += 32) {
         const int pos = skel[t];
         if (accum) {
@@ -663,6 +666,10 @@ __device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, c
   const int m = (int)h.a1;
   const int n = h.M;
   const int parity = h.a0 & 1, base = h.a0 >> 1;  // GATHER / SCATTER / FOLD
+  // element offsets: 16 bits, plus the bits above in a1 for single blocks
+  // (only a clear of a level vector needs them there)
+  const int io = h.io + (A.plain ? (int)(h.a1 & 0xFFFFu) << 16 : 0);
+  const int oo = h.oo + (A.plain ? (int)(h.a1 >> 16) << 16 : 0);
   // coefficient j of this parity: element 2j of order m's triangle row, or
   // element j of a plain vector (single blocks)
   const size_t c0 = A.plain ? 0 : tri_off(m, L) + parity;
@@ -672,19 +679,19 @@ __device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, c
       case OP_GATHER: {
         const IO* beta = reinterpret_cast<const IO*>(A.in[f]) + c0;
         C* dst = S.buf(h.out_buf, f) + base;
-        for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::from_io(beta[cs * (size_t)j]);
+        for (int j = oo + lane; j < oo + n; j += 32) dst[j] = TR::from_io(beta[cs * (size_t)j]);
         break;
       }
       case OP_SCATTER: {
         IO* beta = reinterpret_cast<IO*>(A.out[f]) + c0;
         const C* src = S.buf(h.in_buf, f) + base;
-        for (int j = h.io + lane; j < h.io + n; j += 32) beta[cs * (size_t)j] = TR::to_io(src[j]);
+        for (int j = io + lane; j < io + n; j += 32) beta[cs * (size_t)j] = TR::to_io(src[j]);
         break;
       }
       case OP_FOLD: {
         const IO* G = reinterpret_cast<const IO*>(A.in[f]) + (A.plain ? 0 : (size_t)m * L);
         C* dst = S.buf(h.out_buf, f) + base;
-        for (int r = h.oo + lane; r < h.oo + n; r += 32) {
+        for (int r = oo + lane; r < oo + n; r += 32) {
           IO e;
           if (A.plain) {
             e = G[r];  // node value r of a single block: nothing to fold
@@ -703,17 +710,17 @@ __device__ __forceinline__ void run_control(const OpHdr& h, const Vecs<TR>& S, c
       }
       case OP_CLEAR: {
         C* dst = S.buf(h.out_buf, f);
-        for (int j = h.oo + lane; j < h.oo + n; j += 32) dst[j] = TR::czero();
+        for (int j = oo + lane; j < oo + n; j += 32) dst[j] = TR::czero();
         break;
       }
       case OP_GZERO: {
         if (A.plain) {
           IO* y = reinterpret_cast<IO*>(A.out[f]);
-          for (int r = h.oo + lane; r < h.oo + n; r += 32) y[r] = TR::io_zero();
+          for (int r = oo + lane; r < oo + n; r += 32) y[r] = TR::io_zero();
           break;
         }
         IO* G = reinterpret_cast<IO*>(A.out[f]) + (size_t)m * L;
-        for (int r = h.oo + lane; r < h.oo + n; r += 32) {
+        for (int r = oo + lane; r < oo + n; r += 32) {
           G[l + r] = TR::io_zero();
           G[l - 1 - r] = TR::io_zero();
         }

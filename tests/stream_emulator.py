@@ -135,7 +135,10 @@ def emulate(stream, chunk_bytes, l, prec, direction, inp, prescale=None, twiddle
     tri = _tri(l)
     if plain:
         tri = np.zeros(L + 1, dtype=np.int64)
-    if direction == 0:
+    if plain:
+        G = None  # single blocks write their node values to y below
+        beta = np.asarray(inp, dtype=np.complex128) if direction == 0 else None
+    elif direction == 0:
         G = np.full((L, L), np.nan, dtype=np.complex128)
         beta = np.asarray(inp, dtype=np.complex128)
     else:
@@ -160,6 +163,10 @@ def emulate(stream, chunk_bytes, l, prec, direction, inp, prescale=None, twiddle
         acc = bool(h["flags"] & F_ACCUM)
         tw = 1.0 if twiddle is None else twiddle[m]
         if plain:
+            # single blocks: no order; a1 holds the bits of io / oo above 16
+            a1 = int(h["a1"])
+            io += (a1 & 0xFFFF) << 16
+            oo += (a1 >> 16) << 16
             p, m, tw = 0, 0, 1.0
         if plain and kind == OP_FOLD:
             r = oo + np.arange(M)
