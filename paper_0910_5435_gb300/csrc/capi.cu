@@ -237,7 +237,7 @@ void fill_stats(sht_plan_t P) {
   s.page_bytes = P->H.page_bytes;
 }
 
-// Host build of one precision's streams (factorization + page encoding).
+// Host build of one precision's streams (factorization + record encoding).
 sht_status build_host(sht_plan_t P, int q) {
   PlanHost& H = P->H;
   if (H.built[q]) return SHT_OK;

@@ -6,7 +6,8 @@
 //   interp_decomp         Section 2.1, Remark QR_algorithm (pivoted-QR ID)
 //   factor_unit           Section 2.2 eqs. 1-6, top, bottom (butterfly) built in
 //                         the depth-first order of Section 3
-//   emit_streams          page encoding of sht_stream.h
+//   emit_streams          record and value encoding of sht_stream.h (scheduled
+//                         work items; staged streams for single blocks)
 //
 // All arithmetic is float64; nothing here runs on the hot path.
 
@@ -723,10 +724,10 @@ inline void put_value(uint8_t* dst, int prec, size_t i, double v) {
 // its predecessors explicitly: the last writer of every shared-memory
 // position or node row it reads or writes (RAW, WAW) and every reader of a
 // position it overwrites since that position was last written (WAR).  Ops
-// with no predecessor depend on the item's opening JOIN, which itself waits
-// for everything before the item; so blocks of one butterfly level, and the
-// tail of one order with the head of the next order of the same item, run
-// concurrently.
+// with no predecessor wait for nothing inside the item (the kernel's barrier
+// at the end of every item orders it after the items before); so blocks of
+// one butterfly level, and the tail of one order with the head of the next
+// order of the same item, run concurrently.
 struct Tracker {
   std::vector<int> last_w[kNumVecs];
   std::vector<std::vector<int>> readers[kNumVecs];

@@ -2,7 +2,7 @@
 //
 // Everything here runs on the host in float64 (the precomputation of Section
 // 3 and Section 4 is not on the hot path); the results are encoded into the
-// page streams of sht_stream.h and uploaded by capi.cu.
+// factor streams of sht_stream.h and uploaded by capi.cu.
 #pragma once
 
 #include <stdint.h>

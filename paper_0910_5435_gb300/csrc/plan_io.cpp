@@ -3,8 +3,8 @@
 // The precomputation of Section 3 (with the nodes of Section 4) dominates a
 // plan's cold start, so a plan's factorizations can be written to a file and
 // read back instead of recomputed.  The factor streams are not stored: they
-// depend on run-time options (page size, value cap) and are re-encoded from
-// the factorizations on load.
+// depend on run-time options (record chunk size, value cap, warps) and are
+// re-encoded from the factorizations on load.
 //
 // File layout (little-endian, as the host writes it):
 //   header (FileHeader, 128 bytes): magic, format version, the options that

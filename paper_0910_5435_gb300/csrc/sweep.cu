@@ -17,12 +17,16 @@
 //   * before an op it waits until the listed warps have published enough
 //     completed ops (one progress word per warp in shared memory), then
 //     executes the op alone: lanes own consecutive outputs (coalesced reads
-//     of the [K][M] value block), tiny ops split the inner dimension over a
-//     few lanes and reduce with warp shuffles; then it publishes its progress;
+//     of the [K][M] value block), ops with fewer outputs split the inner
+//     dimension over a few lanes and reduce with warp shuffles (in float64
+//     with the real and imaginary sums split between lane pairs); then it
+//     publishes its progress if another warp waits for it;
 //   * all warps meet at the end of an item (the next item reuses the shared
 //     vectors); warp 0 fetches the next item's number during the current one.
 // There is no producer, parser, op directory, claim or completion tag: the
-// per-op protocol is a few shared-memory words.
+// per-op protocol is a few shared-memory words.  A single-block launch (the
+// Gauss-Jacobi form) runs one stage of a level-by-level schedule instead,
+// with plain vector I/O and the vectors in global memory (SweepArgs).
 //
 // Every wait is bounded: on timeout the kernel records SHT_ERR_TIMEOUT in the
 // device status word, raises the CTA abort flag, stops issuing copies, waits
