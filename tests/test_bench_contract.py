@@ -69,3 +69,37 @@ def test_oracle_leg_scores_outputs_against_the_oracle(tmp_path):
     assert res["orders"] == 2 * l // 4
     assert res["rel_synth_fp64"] < 1e-15 and res["rel_analysis_fp64"] < 1e-15
     assert res["t_full_est"] > 0
+
+
+def test_oracle_leg_scores_batched_fields_and_gradients(tmp_path):
+    """The batched and autograd legs' samples are scored too: a field of the
+    batch at the headline's own bandlimit and one at another, and the
+    gradient 2 S^T S (beta_5000 - beta_6000) of field 0.  Exact oracle
+    outputs score at rounding level, a planted error in one node row of one
+    field shows in that field's score only."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    import oracle
+    from paper_0910_5435_gb300 import inputs
+    l = 16
+    beta = inputs.random_beta(l, seed=3, decay=True)
+    G = oracle.legendre_synthesis(beta, l)
+    arrays = {"fp64_G": G, "fp64_beta": oracle.legendre_analysis(G, l)}
+    for lf, seed in ((16, 1004), (8, 1007)):
+        bf = inputs.random_beta(lf, seed=seed, decay=True)
+        Gf = oracle.legendre_synthesis(bf, lf)
+        if lf == 8:
+            Gf[2] *= 1.01  # planted: one order's node row off by 1 %
+        arrays[f"bt_{lf}_{seed}_G"] = Gf
+        arrays[f"bt_{lf}_{seed}_beta"] = oracle.legendre_analysis(Gf, lf)
+    db = inputs.random_beta(8, seed=5000, decay=True) - inputs.random_beta(8, seed=6000, decay=True)
+    arrays["ag_fp64_8_grad"] = 2 * oracle.legendre_adjoint(oracle.legendre_synthesis(db, 8), 8)
+    path = str(tmp_path / "outs.npz")
+    np.savez(path, **arrays)
+    res = bench.cpu_oracle_leg(l, 4, 3, path, err_stride=1)
+    assert res["rel_synth_fp64"] < 1e-15
+    assert res["rel_synth_batched_l16"] < 1e-15 and res["rel_analysis_batched_l16"] < 1e-15
+    assert res["rel_synth_batched_l8"] > 1e-4 and res["rel_analysis_batched_l8"] < 1e-15
+    assert res["rel_grad_fp64"] < 1e-15
