@@ -19,8 +19,10 @@
 //     executes the op alone: lanes own consecutive outputs (coalesced reads
 //     of the [K][M] value block), ops with fewer outputs split the inner
 //     dimension over a few lanes and reduce with warp shuffles (in float64
-//     with the real and imaginary sums split between lane pairs); then it
-//     publishes its progress if another warp waits for it;
+//     with the real and imaginary sums split between lane pairs, and float64
+//     ops whose outputs would leave lanes idle cut into 32 equal chunks of
+//     products instead); then it publishes its progress if another warp
+//     waits for it;
 //   * all warps meet at the end of an item (the next item reuses the shared
 //     vectors); warp 0 fetches the next item's number during the current one.
 // There is no producer, parser, op directory, claim or completion tag: the
@@ -139,6 +141,9 @@ struct TF64 {
   }
   __device__ static Acc shfl_down(const Acc& a, int off) {
     return {__shfl_down_sync(0xffffffffu, a.re, off), __shfl_down_sync(0xffffffffu, a.im, off)};
+  }
+  __device__ static Acc shfl_idx(const Acc& a, int src) {
+    return {__shfl_sync(0xffffffffu, a.re, src), __shfl_sync(0xffffffffu, a.im, src)};
   }
   __device__ static C from_io(const IO& v) { return v; }
   __device__ static IO to_io(const C& c) { return c; }
@@ -417,6 +422,86 @@ __device__ __forceinline__ void gemv_dot_fields(const typename TR::V* val, const
   }
 }
 
+// Flattened lane mapping (float64 ops whose outputs do not fill the lanes):
+// the op's M x K products, taken output by output (w = o K + s), are cut into
+// 32 contiguous chunks of c = ceil(M K / 32), one per lane.  As c <= K, a
+// chunk meets at most two outputs: the lane sums the part of its first output
+// in head and the part of the next one in tail (zero if the chunk does not
+// reach it).  Every lane then runs c products, against ceil(K / floor(32 / M))
+// with one or more lanes per output; the outputs' sums are put together in
+// flat_combine.
+template <class TR, int FG>
+__device__ __forceinline__ void flat_dot(const typename TR::V* val, const typename TR::C* const* in,
+                                         const uint16_t* idx, bool gather, int M, int K, int lane, int nf,
+                                         typename TR::Acc (&head)[FG], typename TR::Acc (&tail)[FG]) {
+  using V = typename TR::V;
+  const int W = M * K, c = (W + 31) >> 5;
+  const int w0 = min(lane * c, W), w1 = min(w0 + c, W);
+  int o = w0 / K, s = w0 - o * K;
+  bool crossed = false;
+#pragma unroll
+  for (int f = 0; f < FG; ++f) tail[f] = TR::zero();
+  for (int w = w0; w < w1; ++w) {
+    const V v = val[s * M + o];
+    const int xi = gather ? (int)idx[s] : s;
+#pragma unroll
+    for (int f = 0; f < FG; ++f)
+      if (f < nf) TR::fma(tail[f], v, in[f][xi]);
+    if (++s == K) {  // the chunk passes into the next output
+      s = 0;
+      ++o;
+      if (!crossed) {
+#pragma unroll
+        for (int f = 0; f < FG; ++f) {
+          head[f] = tail[f];
+          tail[f] = TR::zero();
+        }
+        crossed = true;
+      }
+    }
+  }
+  if (!crossed) {
+#pragma unroll
+    for (int f = 0; f < FG; ++f) {
+      head[f] = tail[f];
+      tail[f] = TR::zero();
+    }
+  }
+}
+
+// The total of output o = lane (lanes o < M): the tail of the lane whose
+// chunk reaches into o from the previous output, then the heads of the
+// lanes whose chunks start in o, in lane (that is, product) order.  At most
+// ceil(32 / M) chunks start in one output; kFlatHeads bounds that for M >= 11.
+constexpr int kFlatHeads = 3;
+template <class TR>
+__device__ __forceinline__ typename TR::Acc flat_combine(const typename TR::Acc& head, const typename TR::Acc& tail,
+                                                         int M, int K, int lane) {
+  using Acc = typename TR::Acc;
+  const int W = M * K, c = (W + 31) >> 5;
+  const int o = lane;
+  const int la = (o * K + c - 1) / c;            // first lane starting in output o
+  const int lb = ((o + 1) * K + c - 1) / c - 1;  // last lane starting in output o
+  const Acc t = TR::shfl_idx(tail, max(la - 1, 0));
+  Acc tot = (la >= 1 && la * c > o * K) ? t : TR::zero();
+#pragma unroll
+  for (int r = 0; r < kFlatHeads; ++r) {
+    const Acc hv = TR::shfl_idx(head, min(la + r, 31));
+    if (la + r <= lb) TR::merge(tot, hv);
+  }
+  return tot;
+}
+
+// Whether the flattened mapping costs fewer FP64 instructions for an op of
+// M outputs and K inputs: c products per lane plus the combining adds,
+// against ceil(K / ks) products per lane plus the reduction tree's adds.
+__device__ __forceinline__ bool flat_pays(int M, int K, int ks) {
+  if (M < 11 || M > 32) return false;
+  const int tree = 2 * ((K + ks - 1) / ks) + (ks == 2 ? 2 : 0);
+  const int flat = 2 * ((M * K + 31) >> 5) + 2 * (kFlatHeads + 1);
+  return flat < tree;
+}
+
 // floor(32 / M) for M = 0..32, and ceil(65536 / d) for d = 0..32.
 __constant__ unsigned char c_lanes_per_out[33] = {0, 32, 16, 10, 8, 6, 5, 4, 4, 3, 3, 2, 2, 2, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 __constant__ unsigned c_inv16[33] = {0, 65536, 32768, 21846, 16384, 13108, 10923, 9363, 8192, 7282, 6554, 5958, 5462, 5042, 4682, 4370, 4096, 3856, 3641, 3450, 3277, 3121, 2979, 2850, 2731, 2622, 2521, 2428, 2341, 2260, 2185, 2115, 2048};
@@ -492,11 +577,72 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
   const int io = h.io + (A.plain ? (int)(h.a1 & 0xFFFFu) << 16 : 0);
   const int oo = h.oo + (A.plain ? (int)(h.a1 >> 16) << 16 : 0);
   if (M > 0) {
+    // stores output o of field f from its total a0 (the lane that owns o)
+    auto store = [&](int f, Acc a0, int o) {
+      const C* in = S.buf(h.in_buf, f) + io;
+      C* out = S.buf(h.out_buf, f) + oo;
+      switch (h.kind) {
+        case OP_SYN_INTERP:
+          TR::add(a0, in[idx[K + o]]);
+          out[o] = TR::to_c(a0);
+          break;
+        case OP_DENSE:
+          out[o] = TR::to_c(a0);
+          break;
+        case OP_ANA_INTERP: {
+          const int pos = idx[o];
+          if (accum) TR::add(a0, out[pos]);
+          out[pos] = TR::to_c(a0);
+          break;
+        }
+        case OP_DENSE_G: {
+          const int l = A.l;
+          const int i = oo + o;
+          IO v = TR::to_io(TR::to_c(a0));
+          if (A.plain) {  // node value i of a single block
+            IO* y = reinterpret_cast<IO*>(A.out[f]);
+            y[i] = accum ? TR::io_add(y[i], v) : v;
+            break;
+          }
+          if (A.twiddle) v = TR::io_cmul(v, A.twiddle[h.a1]);
+          IO* G = reinterpret_cast<IO*>(A.out[f]) + (size_t)h.a1 * (2 * l);
+          if (accum) {
+            G[l + i] = TR::io_add(G[l + i], v);
+            G[l - 1 - i] = TR::io_sub(G[l - 1 - i], v);
+          } else {
+            G[l + i] = v;
+            G[l - 1 - i] = v;
+          }
+          break;
+        }
+        default:
+          break;
+      }
+    };
     // ks = floor(32 / M) lanes per output (not only powers of two, so that
     // up to 32 - ks + 1 lanes work); lane = o * ks + q.  Both divisions come
     // from a table: lane / ks = (lane * ceil(2^16 / ks)) >> 16 holds exactly
     // for lane < 32 and ks <= 32.
     const int ks = c_lanes_per_out[M];
+    if constexpr (TR::kSplitComponents) {
+      // float64 ops whose outputs leave lanes idle: the flattened mapping
+      if (flat_pays(M, K, ks)) {
+        const C* inp[FG];
+#pragma unroll
+        for (int f = 0; f < FG; ++f) inp[f] = S.buf(h.in_buf, f) + io;
+        Acc head[FG], tail[FG];
+        flat_dot<TR, FG>(val, inp, idx, gather, M, K, lane, nf, head, tail);
+        after_read();  // every lane is done with the staged values
+#pragma unroll
+        for (int f = 0; f < FG; ++f) {
+          if (f >= nf) break;
+          const Acc a0 = flat_combine<TR>(head[f], tail[f], M, K, lane);
+          if (lane < M) store(f, a0, lane);
+        }
+        goto skel;
+      }
+    }
+    {
     const int o = (lane * c_inv16[ks]) >> 16, q = lane - o * ks;
     Acc a[FG];
     if constexpr (FG == 1) {
@@ -598,49 +744,11 @@ __device__ __forceinline__ void run_gemv(const OpHdr& h, const uint8_t* op, cons
         const Acc b = TR::shfl_down(a0, off);
         if (q + off < ks) TR::merge(a0, b);
       }
-      if (q == 0 && o < M) {
-        const C* in = S.buf(h.in_buf, f) + io;
-        C* out = S.buf(h.out_buf, f) + oo;
-        switch (h.kind) {
-          case OP_SYN_INTERP:
-            TR::add(a0, in[idx[K + o]]);
-            out[o] = TR::to_c(a0);
-            break;
-          case OP_DENSE:
-            out[o] = TR::to_c(a0);
-            break;
-          case OP_ANA_INTERP: {
-            const int pos = idx[o];
-            if (accum) TR::add(a0, out[pos]);
-            out[pos] = TR::to_c(a0);
-            break;
-          }
-          case OP_DENSE_G: {
-            const int l = A.l;
-            const int i = oo + o;
-            IO v = TR::to_io(TR::to_c(a0));
-            if (A.plain) {  // node value i of a single block
-              IO* y = reinterpret_cast<IO*>(A.out[f]);
-              y[i] = accum ? TR::io_add(y[i], v) : v;
-              break;
-            }
-            if (A.twiddle) v = TR::io_cmul(v, A.twiddle[h.a1]);
-            IO* G = reinterpret_cast<IO*>(A.out[f]) + (size_t)h.a1 * (2 * l);
-            if (accum) {
-              G[l + i] = TR::io_add(G[l + i], v);
-              G[l - 1 - i] = TR::io_sub(G[l - 1 - i], v);
-            } else {
-              G[l + i] = v;
-              G[l - 1 - i] = v;
-            }
-            break;
-          }
-          default:
-            break;
-        }
-      }
+      if (q == 0 && o < M) store(f, a0, o);
+    }
     }
   }
+skel:
   if (h.kind == OP_ANA_INTERP && (h.flags & F_SKEL)) {
     const uint16_t* skel = idx + M;
     for (int f = 0; f < nf; ++f) {
