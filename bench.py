@@ -694,6 +694,9 @@ def main():
         traffic = 0.5 * (cap["dram_bytes_syn"] + cap["dram_bytes_ana"]) / cap["stream_bytes"] * st["stream_bytes_fp64"]
     # this device's float64 FMA loop (after the timed region): the reachable ceiling
     dfma_loop = sht.measure_fp64_fma()
+    # and its float64 tensor-core (warp MMA) loop: whether block GEMMs over
+    # several right-hand sides could beat the FMA pipe on this part
+    dmma_loop = sht.measure_fp64_mma()
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum at l=512, "
@@ -703,6 +706,7 @@ def main():
                 "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2 flops",
                 "dfma_loop_tflops": dfma_loop,
                 "frac_of_dfma_loop": achieved / dfma_loop if dfma_loop > 0 else None,
+                "dmma_loop_tflops": dmma_loop,
                 "hbm_view": {"stream_bytes_per_launch": st["stream_bytes_fp64"], "achieved_gbs": stream_gbs,
                              "peak_gbs": hbm or HBM_FALLBACK_GBS,
                              "frac": stream_gbs / (hbm or HBM_FALLBACK_GBS),

@@ -368,6 +368,14 @@ sht_status sht_trace_read(sht_plan_t plan, unsigned long long* out, int reset);
  * with.  Synchronous; uses the legacy default stream. */
 sht_status sht_measure_fp64_fma(double* tflops);
 
+/* The paper has no counterpart: measures the current device's float64
+ * tensor-core throughput (*tflops, 2 flops per FMA) with a register-resident
+ * loop of the 8x8x4 float64 warp MMA, eight independent accumulations per
+ * warp on every SM, timed like sht_measure_fp64_fma.  It tells whether block
+ * products over several right-hand sides could run faster on tensor cores
+ * than on the FP64 FMA pipe.  Synchronous; uses the legacy default stream. */
+sht_status sht_measure_fp64_mma(double* tflops);
+
 /* ----------------------------------------------- direct float64 baseline */
 
 /* Stores the dense operator P-bar^m_{m+p+2j}(x_{l+i}) (float64, kept rows

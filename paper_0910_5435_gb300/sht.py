@@ -36,7 +36,7 @@ EXPORTS = [
     "sht_batch_last_device_status", "sht_batch_autotune", "sht_batch_get_config", "sht_batch_synthesize_adjoint",
     "sht_unit_stats_compute", "sht_gauss_jacobi_nodes", "sht_unit_stats_gauss_jacobi",
     "sht_plan_save", "sht_plan_load", "sht_batch_synthesize_grid", "sht_batch_analyze_grid",
-    "sht_measure_fp64_fma", "sht_interp_decomp", "sht_plan_stats", "sht_batched_workspace_bytes",
+    "sht_measure_fp64_fma", "sht_measure_fp64_mma", "sht_interp_decomp", "sht_plan_stats", "sht_batched_workspace_bytes",
     "sht_synthesize_batched", "sht_analyze_batched", "sht_batch_get_groups",
     "sht_gj_plan_create", "sht_gj_forward", "sht_gj_inverse", "sht_gj_launches",
 ]
@@ -163,6 +163,7 @@ def lib():
     L.sht_batch_synthesize_adjoint.argtypes = [vp, vp, vp, vp]
     L.sht_batch_synthesize_grid.argtypes = [vp, vp, vp, vp, vp]
     L.sht_measure_fp64_fma.argtypes = [ctypes.POINTER(c_double)]
+    L.sht_measure_fp64_mma.argtypes = [ctypes.POINTER(c_double)]
     L.sht_interp_decomp.argtypes = [vp, c_int, c_int, c_double, ctypes.POINTER(c_int), vp, vp,
                                     ctypes.POINTER(c_int)]
     L.sht_batch_analyze_grid.argtypes = [vp, vp, vp, vp, vp]
@@ -520,6 +521,14 @@ def measure_fp64_fma():
     (sht_measure_fp64_fma)."""
     t = ctypes.c_double()
     _check(lib().sht_measure_fp64_fma(ctypes.byref(t)), "sht_measure_fp64_fma")
+    return t.value
+
+
+def measure_fp64_mma():
+    """Float64 tensor-core (8x8x4 warp MMA) throughput of the current device
+    in TFLOP/s (sht_measure_fp64_mma)."""
+    t = ctypes.c_double()
+    _check(lib().sht_measure_fp64_mma(ctypes.byref(t)), "sht_measure_fp64_mma")
     return t.value
 
 
