@@ -52,3 +52,6 @@ def test_null_arguments_rejected(lib):
     assert lib.sht_plan_destroy(None) == 0
     assert lib.sht_plan_get_stats(None, None) == 1
     assert lib.sht_legendre_synthesize(None, 0, None, None, None) == 1
+    # the device-rate loops check their output pointer before touching the device
+    assert lib.sht_measure_fp64_fma(None) == 1
+    assert lib.sht_measure_fp64_mma(None) == 1
