@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip every leg beside the float64 headline")
     ap.add_argument("--paths", default="split32,split32acc64,fp32,direct,full,batched,autograd,device_build,"
                                        "gauss_jacobi",
-                    help="comma-separated legs to run beside the headline")
+                    help="comma-separated legs to run beside the headline (also: trace, the sweep's "
+                         "per-op trace shares)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--cpu-all-cores", type=int, default=1,
                     help="also time the oracle over all orders on every host core (0: skip)")
@@ -158,6 +159,45 @@ def gauss_jacobi_leg(args, sht, torch, dev, stream):
                     "t_comp_s": st["t_comp"], "t_plan_s": t_plan, "k_max": st["k_max"], "k_avg": st["k_avg"],
                     "eps_inv": float((z - x).abs().max()), "device_status": sht.sht_last_device_status(P, stream)})
         P.close()
+    return out
+
+
+TRACE_KEYS = ("exec_gemv", "exec_control", "wait_dep", "wait_values", "wait_records", "wait_barrier", "complete")
+
+
+def trace_leg(args, sht, torch, dev, stream, plan, beta):
+    """Per-op trace of the sweep (sht_trace_enable): for float64, split and
+    float32, one traced synthesis and one traced analysis after the timed
+    ones, as shares of the warps' cycles (executing compute ops, control ops,
+    waiting for other warps, for staged values, for record chunks, at the
+    item barrier, publishing) and the mean cycles per compute op."""
+    l = args.l
+    out = {}
+    for name, prec, cdt in (("fp64", sht.SHT_FP64, torch.complex128), ("split32", sht.SHT_SPLIT32, torch.complex128),
+                            ("fp32", sht.SHT_FP32, torch.complex64)):
+        plan.prepare(prec)
+        b = beta.to(cdt)
+        g = torch.empty((2 * l, 2 * l), dtype=cdt, device=dev)
+        bk = torch.empty_like(b)
+        res = {}
+        for direction, fn in (("synthesis", lambda: sht.sht_legendre_synthesize(plan, prec, b, g, stream)),
+                              ("analysis", lambda: sht.sht_legendre_analyze(plan, prec, g, bk, stream))):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize(dev)
+            sht.sht_trace_enable(plan, True)
+            try:
+                sht.sht_trace_read(plan, reset=True)
+                fn()
+                torch.cuda.synchronize(dev)
+                t = sht.sht_trace_read(plan, reset=True)
+            finally:
+                sht.sht_trace_enable(plan, False)
+            tot = sum(t[k] for k in TRACE_KEYS)
+            res[direction] = {"share": {k: t[k] / tot for k in TRACE_KEYS},
+                              "compute_ops": int(t["n_gemv"]), "control_ops": int(t["n_control"]),
+                              "cycles_per_compute_op": t["exec_gemv"] / max(1, t["n_gemv"])}
+        out[name] = res
     return out
 
 
@@ -768,6 +808,8 @@ def main():
         extras["gauss_jacobi_m_eq_n"] = gauss_jacobi_leg(args, sht, torch, dev, stream)
     if rank == 0 and "device_build" in legs:
         extras["plan_device_build"] = device_build_leg(args, sht, torch, dev, stream, plan, st, beta)
+    if rank == 0 and "trace" in legs:
+        extras["sweep_trace"] = trace_leg(args, sht, torch, dev, stream, plan, beta)
 
     cpu = None
     cpu_all = None
