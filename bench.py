@@ -70,8 +70,8 @@ def parse():
 # stream-format sources the capture was taken with (sources_sha); None when
 # no capture matches.
 SWEEP_TRAFFIC_CAPTURE = {"l": 512, "leaf_cols": 32, "page_bytes": 0, "stream_bytes": 1087871856,
-                         "dram_bytes_syn": 1.098041e9 + 20.620800e6, "dram_bytes_ana": 1.093416e9 + 15.911680e6,
-                         "sources_sha": "7f75d2111d6c4575"}
+                         "dram_bytes_syn": 1.098007e9 + 20.198400e6, "dram_bytes_ana": 1.093494e9 + 12.580608e6,
+                         "sources_sha": "d3e72f6c3621d35e"}
 
 
 def sweep_sources_sha():

@@ -1006,11 +1006,62 @@ struct Emitter {
     throw std::logic_error("op does not fit a record chunk and a staging slot");
   }
 
+  // The piece sizes of an op with n outputs over K inputs, the first piece
+  // allowed by ok_first(M), the others by ok(M).  Float64 and float32 take
+  // the pieces of piece().  The split format's ops cost mostly a fixed part
+  // (its reduction trees and per-op latency), so it takes the partition that
+  // minimises an estimate of the warp's cycles per piece: 1800 fixed, 147
+  // per inner step (ceil(K / ks) steps with ks = floor(32 / M) lanes per
+  // output) and 280 per level of the reduction tree, the per-step figure
+  // being the fitted cost per value of a full warp (4.6 x 32).
+  template <class F1, class F2>
+  std::vector<int> pieces(int n, int K, F1 ok_first, F2 ok) {
+    std::vector<int> out;
+    if (n <= 0) return out;
+    if (prec != 2) {
+      for (int o0 = 0; o0 < n;) {
+        const int mp = o0 == 0 ? piece(n, ok_first) : piece(n - o0, ok);
+        out.push_back(mp);
+        o0 += mp;
+      }
+      return out;
+    }
+    auto t = [&](int M) {
+      const int ks = kMaxM / M;
+      int levels = 0;
+      while ((1 << levels) < ks) ++levels;
+      return 1800.0 + 147.0 * ((K + ks - 1) / ks) + 280.0 * levels;
+    };
+    // best[j]: the cheapest cover of the last j outputs by pieces allowed by ok
+    const double inf = 1e300;
+    std::vector<double> best(n + 1, inf);
+    std::vector<int> pick(n + 1, 0);
+    best[0] = 0.0;
+    for (int j = 1; j <= n; ++j)
+      for (int M = 1; M <= std::min(kMaxM, j); ++M)
+        if (best[j - M] < inf && ok(M) && best[j - M] + t(M) < best[j]) {
+          best[j] = best[j - M] + t(M);
+          pick[j] = M;
+        }
+    int first = 0;
+    double bf = inf;
+    for (int M = 1; M <= std::min(kMaxM, n); ++M)
+      if (best[n - M] < inf && ok_first(M) && t(M) + best[n - M] < bf) {
+        bf = t(M) + best[n - M];
+        first = M;
+      }
+    if (first == 0) throw std::logic_error("op does not fit a record chunk and a staging slot");
+    out.push_back(first);
+    for (int j = n - first; j > 0; j -= pick[j]) out.push_back(pick[j]);
+    return out;
+  }
+
   // y[oo + o] = z[io + skel[o]] + sum_s T[s][o] z[io + red[s]]
   void syn_interp(const IdBlock& b, uint8_t in_buf, uint8_t out_buf) {
     const int k = b.k, K = b.nin - b.k;
-    for (int o0 = 0; o0 < k;) {
-      const int mp = piece(k - o0, [&](int M) { return fits((size_t)K + M, (size_t)K * M); });
+    auto ok = [&](int M) { return fits((size_t)K + M, (size_t)K * M); };
+    int o0 = 0;
+    for (const int mp : pieces(k, K, ok, ok)) {
       OpHdr h = hdr(OP_SYN_INTERP);
       h.in_buf = in_buf;
       h.out_buf = out_buf;
@@ -1032,8 +1083,9 @@ struct Emitter {
   template <class GetV>
   void dense(uint8_t kind, uint8_t flags, int M, int K, GetV getv, uint8_t in_buf, int io, uint8_t out_buf, int oo,
              int m = 0) {
-    for (int o0 = 0; o0 < M;) {
-      const int mp = piece(M - o0, [&](int Mp) { return fits(0, (size_t)K * Mp); });
+    auto ok = [&](int Mp) { return fits(0, (size_t)K * Mp); };
+    int o0 = 0;
+    for (const int mp : pieces(M, K, ok, ok)) {
       OpHdr h = hdr(kind, flags);
       h.in_buf = in_buf;
       h.out_buf = out_buf;
@@ -1053,17 +1105,18 @@ struct Emitter {
   void ana_interp(const IdBlock& b, uint8_t in_buf, uint8_t out_buf, bool accum) {
     const int k = b.k, nred = b.nin - b.k;
     if (k == 0) return;
+    // the first op also carries the skeleton pass-through (k more indices);
+    // with no redundant rows it is that alone
+    std::vector<int> ps = pieces(
+        nred, k, [&](int M) { return fits((size_t)M + k, (size_t)k * M); },
+        [&](int M) { return fits((size_t)M, (size_t)k * M); });
+    if (ps.empty()) {
+      if (!fits((size_t)k, 0)) throw std::logic_error("skeleton pass-through does not fit a record chunk");
+      ps.push_back(0);
+    }
     bool skel_done = false;
     int o0 = 0;
-    do {
-      const int rem = nred - o0;
-      const size_t extra = skel_done ? 0 : (size_t)k;
-      int mp = 0;
-      if (rem > 0) {
-        mp = piece(rem, [&](int M) { return fits((size_t)M + extra, (size_t)k * M); });
-      } else if (!fits(extra, 0)) {
-        throw std::logic_error("skeleton pass-through does not fit a record chunk");
-      }
+    for (const int mp : ps) {
       OpHdr h = hdr(OP_ANA_INTERP, (uint8_t)((skel_done ? 0 : F_SKEL) | (accum ? F_ACCUM : 0)));
       h.in_buf = in_buf;
       h.out_buf = out_buf;
@@ -1079,7 +1132,7 @@ struct Emitter {
       write(h, idx, vals);
       skel_done = true;
       o0 += mp;
-    } while (o0 < nred);
+    }
   }
 };
 

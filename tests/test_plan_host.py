@@ -130,12 +130,14 @@ def test_stats_follow_paper_columns():
 
 
 @pytest.mark.parametrize("l,C", [(4, 2), (16, 4), (64, 16), (64, 64)])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_op_ordering_is_race_free(l, C, prec):
     """Race detection for the concurrent sweep: every op may overlap the ops
     its `dep` field names; none of them may write what it reads or writes,
-    nor read what it writes (sht_stream.h ordering rule)."""
+    nor read what it writes (sht_stream.h ordering rule).  The split format
+    has streams of its own (its ops are cut into other pieces)."""
     P = sht.Plan(l, 1e-12, leaf_cols=C, host_only=True)
+    P.prepare(prec)
     for d in (0, 1):
         assert check_races(P.stream(prec, d), P.page_bytes, l) == []
 
