@@ -245,3 +245,25 @@ def test_plans_do_not_depend_on_the_thread_count():
                     assert np.array_equal(a, b), (prec, d)
     for P in plans:
         P.close()
+
+
+@pytest.mark.parametrize("l,C", [(200, 32), (256, 32)])
+def test_split_pieces_need_no_more_ops_than_power_of_two_pieces(l, C):
+    """The split format cuts each block into the op pieces its cost estimate
+    prefers, float64 into 32, 16, 8, ... outputs, over the same blocks: the
+    split streams hold at most as many compute ops (fewer once blocks exceed
+    a staging slot), and the same values."""
+    from tests.stream_emulator import iter_ops, OP_SYN, OP_ANA
+    P = sht.Plan(l, 1e-12, leaf_cols=C, host_only=True)
+    P.prepare(2)
+    fewer = False
+    for d in (0, 1):
+        counts, values = [], []
+        for prec in (0, 2):
+            ops = [h for h, _, _ in iter_ops(P.stream(prec, d), P.page_bytes) if OP_SYN <= int(h["kind"]) <= OP_ANA]
+            counts.append(len(ops))
+            values.append(sum(int(h["M"]) * int(h["K"]) for h in ops))
+        assert counts[1] <= counts[0]
+        assert values[1] == values[0]
+        fewer |= counts[1] < counts[0]
+    assert fewer
